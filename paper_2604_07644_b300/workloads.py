@@ -1,0 +1,518 @@
+"""Seeded synthetic inputs for the LTV-QP and SLS workloads.
+
+This module only draws problem data.  It holds none of the solver's arithmetic
+(no Riccati step, no scan combine, no ADMM update), so both the CPU oracle and
+the CUDA path may take their inputs from here.
+
+Every draw goes through numpy's counter-based Philox bit generator keyed by the
+seed, so a (workload, seed) pair always gives the same arrays on any machine.
+
+Problem layout (row-major, time-major, float64), following the LTV-QP of
+Sec. III-B (eq. sqp_qp):
+    A  [N, nx, nx]   B [N, nx, nu]   c [N, nx]  (the paper's b_k)
+    Q  [N+1, nx, nx] (Q[N] is the terminal Q_N)
+    R  [N, nu, nu]   S [N, nu, nx]   q [N+1, nx]   r [N, nu]
+    C  [N, nc, nx]   D [N, nc, nu]   CN [nf, nx]
+    lo, hi [N*nc + nf]  two-sided bounds on G(dx, du); +-inf allowed
+    x0 [nx]          the fixed initial state deviation
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+INF = float("inf")
+
+
+def rng(*key: int) -> np.random.Generator:
+    """Philox generator keyed by a tuple of non-negative ints (the tuple is
+    hashed to the 128-bit Philox key by numpy's SeedSequence)."""
+    return np.random.Generator(np.random.Philox(np.random.SeedSequence([int(v) for v in key])))
+
+
+@dataclass
+class QP:
+    """One horizon-structured, inequality-constrained LQ program."""
+    A: np.ndarray
+    B: np.ndarray
+    c: np.ndarray
+    Q: np.ndarray
+    R: np.ndarray
+    S: np.ndarray
+    q: np.ndarray
+    r: np.ndarray
+    C: np.ndarray
+    D: np.ndarray
+    CN: np.ndarray
+    lo: np.ndarray
+    hi: np.ndarray
+    x0: np.ndarray
+    name: str = ""
+    features: np.ndarray | None = None
+
+    @property
+    def nx(self) -> int:
+        return self.A.shape[1]
+
+    @property
+    def nu(self) -> int:
+        return self.B.shape[2]
+
+    @property
+    def N(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def nc(self) -> int:
+        return self.C.shape[1]
+
+    @property
+    def nf(self) -> int:
+        return self.CN.shape[0]
+
+    @property
+    def m(self) -> int:
+        """Number of constraint rows, N*nc + nf."""
+        return self.N * self.nc + self.nf
+
+    def dims(self) -> tuple[int, int, int, int, int]:
+        return (self.nx, self.nu, self.N, self.nc, self.nf)
+
+
+@dataclass
+class SLSProblem:
+    """Data of the SLS controller problem (eq. fastsls_qp) and its margins."""
+    A: np.ndarray      # [N, nx, nx]
+    B: np.ndarray      # [N, nx, nu]
+    E: np.ndarray      # [N, nx, nx]   disturbance scaling E_j
+    Qbar: np.ndarray   # [nx, nx]
+    Rbar: np.ndarray   # [nu, nu]
+    QbarN: np.ndarray  # [nx, nx]
+    C: np.ndarray      # [N, nc, nx]
+    D: np.ndarray      # [N, nc, nu]
+    CN: np.ndarray     # [nf, nx]
+    tau: np.ndarray | None = None  # [N+1, N, max(nc, nf)]; row k=N uses the first nf entries
+    name: str = ""
+
+    @property
+    def nx(self) -> int:
+        return self.A.shape[1]
+
+    @property
+    def nu(self) -> int:
+        return self.B.shape[2]
+
+    @property
+    def N(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def nc(self) -> int:
+        return self.C.shape[1]
+
+    @property
+    def nf(self) -> int:
+        return self.CN.shape[0]
+
+
+# ----------------------------------------------------------------------------
+# helpers (input construction only)
+# ----------------------------------------------------------------------------
+
+def _unit_rows(g: np.random.Generator, n_rows: int, dim: int) -> np.ndarray:
+    M = g.standard_normal((n_rows, dim))
+    return M / np.linalg.norm(M, axis=1, keepdims=True)
+
+
+def _open_loop(A: np.ndarray, c: np.ndarray, x0: np.ndarray) -> np.ndarray:
+    """Zero-input state sequence x_{k+1} = A_k x_k + c_k (problem data only)."""
+    N, nx = A.shape[0], A.shape[1]
+    X = np.zeros((N + 1, nx))
+    X[0] = x0
+    for k in range(N):
+        X[k + 1] = A[k] @ X[k] + c[k]
+    return X
+
+
+def _raise_offsets(C: np.ndarray, hi: np.ndarray, X: np.ndarray, rows: np.ndarray, margin: float) -> None:
+    """Raise one-sided offsets that the zero-input trajectory would come within
+    `margin` of, so that u = 0 is strictly feasible (a feasibility guarantee by
+    construction; rows lists the one-sided row indices of each stage)."""
+    N = C.shape[0]
+    nc = C.shape[1]
+    for k in range(N):
+        v = C[k] @ X[k]
+        for i in rows:
+            j = k * nc + i
+            if v[i] + margin > hi[j]:
+                hi[j] = v[i] + margin
+
+
+def _empty(nx, nu, N):
+    return dict(
+        S=np.zeros((N, nu, nx)),
+        c=np.zeros((N, nx)),
+        r=np.zeros((N, nu)),
+    )
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+
+def plain_4d(seed: int = 0, N: int = 32) -> QP:
+    """Plain FP64 QP: nx=4, nu=2, N=32, LTI A = I + 0.05 G, B ~ N(0, 0.1),
+    Q = I, R = 0.1 I, |x| <= 5, |u| <= 1 (two-sided rows), terminal |x_N| <= 5,
+    x0 ~ U[-2, 2]."""
+    g = rng(1, seed)
+    nx, nu = 4, 2
+    # Rejection sampling on the problem data alone: redraw (G, x0) until the
+    # zero-input trajectory stays inside |x| <= 4.5, which makes u = 0 a
+    # strictly feasible point (with |u| <= 1 and B ~ 0.1, an unstable draw
+    # would otherwise often be infeasible).
+    for _ in range(1000):
+        G = g.standard_normal((nx, nx))
+        x0 = g.uniform(-2.0, 2.0, nx)
+        A1 = np.eye(nx) + 0.05 * G
+        X = _open_loop(np.repeat(A1[None], N, axis=0), np.zeros((N, nx)), x0)
+        if np.max(np.abs(X)) <= 4.5:
+            break
+    Bm = 0.1 * g.standard_normal((nx, nu))
+    A = np.repeat(A1[None], N, axis=0)
+    B = np.repeat(Bm[None], N, axis=0)
+    Q = np.repeat(np.eye(nx)[None], N + 1, axis=0)
+    R = np.repeat(0.1 * np.eye(nu)[None], N, axis=0)
+    C1 = np.vstack([np.eye(nx), np.zeros((nu, nx))])
+    D1 = np.vstack([np.zeros((nx, nu)), np.eye(nu)])
+    C = np.repeat(C1[None], N, axis=0)
+    D = np.repeat(D1[None], N, axis=0)
+    CN = np.eye(nx)
+    nc = nx + nu
+    hi = np.concatenate([np.tile(np.r_[5.0 * np.ones(nx), np.ones(nu)], N), 5.0 * np.ones(nx)])
+    lo = -hi.copy()
+    e = _empty(nx, nu, N)
+    assert nc == C.shape[1]
+    return QP(A=A, B=B, c=e["c"], Q=Q, R=R, S=e["S"], q=np.zeros((N + 1, nx)), r=e["r"],
+              C=C, D=D, CN=CN, lo=lo, hi=hi, x0=x0, name=f"plain4d-N{N}-s{seed}")
+
+
+def quadrotor_12d(seed: int = 0, N: int = 64) -> QP:
+    """Quadrotor-shaped QP: nx=12, nu=4, N=64, A_k = I + 0.02 G_k,
+    B_k ~ N(0, 0.05), Q = diag U[0.5, 2], R = diag U[0.01, 0.1], 24 unit
+    half-spaces per stage on (x, u) with offsets U[1, 3], no terminal rows,
+    x0 ~ U[-0.5, 0.5], a goal x_ref of norm 1.5 (q_k = -Q x_ref)."""
+    g = rng(2, seed)
+    nx, nu, nc = 12, 4, 24
+    A = np.eye(nx)[None] + 0.02 * g.standard_normal((N, nx, nx))
+    B = 0.05 * g.standard_normal((N, nx, nu))
+    qd = g.uniform(0.5, 2.0, nx)
+    rd = g.uniform(0.01, 0.1, nu)
+    Q = np.repeat(np.diag(qd)[None], N + 1, axis=0)
+    R = np.repeat(np.diag(rd)[None], N, axis=0)
+    rows = _unit_rows(g, N * nc, nx + nu).reshape(N, nc, nx + nu)
+    C = rows[:, :, :nx].copy()
+    D = rows[:, :, nx:].copy()
+    hi = np.concatenate([g.uniform(1.0, 3.0, N * nc), np.zeros(0)])
+    lo = -INF * np.ones(N * nc)
+    x0 = g.uniform(-0.5, 0.5, nx)
+    xref = g.standard_normal(nx)
+    xref *= 1.5 / np.linalg.norm(xref)
+    q = -(Q @ xref)
+    e = _empty(nx, nu, N)
+    _raise_offsets(C, hi, _open_loop(A, e["c"], x0), np.arange(nc), 0.25)
+    return QP(A=A, B=B, c=e["c"], Q=Q, R=R, S=e["S"], q=q, r=e["r"], C=C, D=D,
+              CN=np.zeros((0, nx)), lo=lo, hi=hi, x0=x0, name=f"quad12d-N{N}-s{seed}")
+
+
+def legged(seed: int = 0, nx: int = 61, nu: int = 12, N: int = 100, n_obs: int = 8,
+           terminal_obstacles: bool = True, tag: int = 3) -> QP:
+    """Legged-robot-shaped SQP inner QP (quadruped 61D/12u by default; the
+    humanoid is nx=75, nu=21): A_k = I + 0.01 G_k, B_k ~ N(0, 0.02),
+    Q = diag U[0.5, 2], R = diag U[0.01, 0.1]; per stage |u| <= 1 (nu two-sided
+    rows) and n_obs unit half-spaces on the CoM plane (x_0, x_1) with offsets
+    U[1, 3]; the same obstacle rows on x_N.  x0 ~ U[-0.5, 0.5]; a goal at radius
+    2 in the CoM plane pulls the trajectory into the obstacles
+    (q_k = -Q x_ref)."""
+    g = rng(tag, seed, nx, N)
+    A = np.eye(nx)[None] + 0.01 * g.standard_normal((N, nx, nx))
+    B = 0.02 * g.standard_normal((N, nx, nu))
+    qd = g.uniform(0.5, 2.0, nx)
+    rd = g.uniform(0.01, 0.1, nu)
+    Q = np.repeat(np.diag(qd)[None], N + 1, axis=0)
+    R = np.repeat(np.diag(rd)[None], N, axis=0)
+    nc = nu + n_obs
+    C = np.zeros((N, nc, nx))
+    D = np.zeros((N, nc, nu))
+    D[:, :nu, :] = np.eye(nu)[None]
+    dirs = _unit_rows(g, N * n_obs, 2).reshape(N, n_obs, 2)
+    C[:, nu:, 0:2] = dirs
+    f_obs = g.uniform(1.0, 3.0, (N, n_obs))
+    hi_st = np.concatenate([np.ones((N, nu)), f_obs], axis=1)
+    lo_st = np.concatenate([-np.ones((N, nu)), -INF * np.ones((N, n_obs))], axis=1)
+    if terminal_obstacles:
+        CN = np.zeros((n_obs, nx))
+        CN[:, 0:2] = _unit_rows(g, n_obs, 2)
+        fN = g.uniform(1.0, 3.0, n_obs)
+    else:
+        CN = np.zeros((0, nx))
+        fN = np.zeros(0)
+    hi = np.concatenate([hi_st.ravel(), fN])
+    lo = np.concatenate([lo_st.ravel(), -INF * np.ones(CN.shape[0])])
+    x0 = g.uniform(-0.5, 0.5, nx)
+    phi = g.uniform(0.0, 2.0 * math.pi)
+    xref = np.zeros(nx)
+    xref[0], xref[1] = 2.0 * math.cos(phi), 2.0 * math.sin(phi)
+    q = -(Q @ xref)
+    e = _empty(nx, nu, N)
+    X = _open_loop(A, e["c"], x0)
+    _raise_offsets(C, hi, X, np.arange(nu, nc), 0.25)
+    if CN.shape[0]:
+        v = CN @ X[N]
+        base = N * nc
+        for i in range(CN.shape[0]):
+            if v[i] + 0.25 > hi[base + i]:
+                hi[base + i] = v[i] + 0.25
+    return QP(A=A, B=B, c=e["c"], Q=Q, R=R, S=e["S"], q=q, r=e["r"], C=C, D=D,
+              CN=CN, lo=lo, hi=hi, x0=x0, name=f"legged{nx}d-N{N}-s{seed}")
+
+
+def quadruped_61d(seed: int = 0, N: int = 100) -> QP:
+    """Quadruped-shaped inner QP: nx=61, nu=12, N=100, nc=20 (12 box + 8
+    obstacles), nf=8."""
+    return legged(seed, 61, 12, N)
+
+
+def humanoid_75d(seed: int = 0, N: int = 40) -> QP:
+    """Humanoid-shaped QP: nx=75, nu=21, N=40, nc=29, nf=8."""
+    return legged(seed, 75, 21, N, tag=4)
+
+
+def tiny(seed: int = 0, nx: int = 2, nu: int = 1, N: int = 3, box_u: float = 0.3,
+         n_half: int = 1, S_nonzero: bool = True, b_nonzero: bool = True) -> QP:
+    """Tiny random QP for brute-force pins: dense random A, B, SPD Q, R, random
+    S (small enough that the stage Hessian stays SPD), affine term b, two-sided
+    |u| <= box_u rows and n_half random half-spaces per stage, one terminal
+    half-space."""
+    g = rng(9, seed, nx, nu, N)
+    A = g.standard_normal((N, nx, nx)) * 0.6 + np.eye(nx)[None] * 0.5
+    B = g.standard_normal((N, nx, nu))
+    Q = np.zeros((N + 1, nx, nx))
+    R = np.zeros((N, nu, nu))
+    S = np.zeros((N, nu, nx))
+    for k in range(N + 1):
+        M = g.standard_normal((nx, nx))
+        Q[k] = M @ M.T / nx + 0.5 * np.eye(nx)
+    for k in range(N):
+        M = g.standard_normal((nu, nu))
+        R[k] = M @ M.T / nu + 0.5 * np.eye(nu)
+        if S_nonzero:
+            S[k] = 0.2 * g.standard_normal((nu, nx))
+    c = 0.3 * g.standard_normal((N, nx)) if b_nonzero else np.zeros((N, nx))
+    q = g.standard_normal((N + 1, nx))
+    r = g.standard_normal((N, nu))
+    nc = nu + n_half
+    C = np.zeros((N, nc, nx))
+    D = np.zeros((N, nc, nu))
+    D[:, :nu, :] = np.eye(nu)[None]
+    rows = _unit_rows(g, N * n_half, nx + nu).reshape(N, n_half, nx + nu)
+    C[:, nu:, :] = rows[:, :, :nx]
+    D[:, nu:, :] = rows[:, :, nx:]
+    f = g.uniform(0.2, 1.0, (N, n_half))
+    hi = np.concatenate([np.concatenate([box_u * np.ones((N, nu)), f], axis=1).ravel(),
+                         g.uniform(0.5, 1.5, 1)])
+    lo = np.concatenate([np.concatenate([-box_u * np.ones((N, nu)), -INF * np.ones((N, n_half))], axis=1).ravel(),
+                         -INF * np.ones(1)])
+    CN = _unit_rows(g, 1, nx)
+    x0 = g.uniform(-0.5, 0.5, nx)
+    X = _open_loop(A, c, x0)
+    _raise_offsets(C, hi, X, np.arange(nu, nc), 0.2)
+    v = CN @ X[N]
+    if v[0] + 0.2 > hi[N * nc]:
+        hi[N * nc] = v[0] + 0.2
+    return QP(A=A, B=B, c=c, Q=Q, R=R, S=S, q=q, r=r, C=C, D=D, CN=CN, lo=lo, hi=hi,
+              x0=x0, name=f"tiny-{nx}-{nu}-{N}-s{seed}")
+
+
+def random_general(seed: int, nx: int, nu: int, N: int, nc: int, nf: int,
+                   active_scale: float = 1.0) -> QP:
+    """General random QP with every term present (S, b, q, r nonzero, two-sided
+    and one-sided rows); used for kernel parity across ragged sizes."""
+    g = rng(11, seed, nx, nu, N)
+    A = np.eye(nx)[None] + 0.1 * g.standard_normal((N, nx, nx)) / math.sqrt(nx)
+    B = 0.3 * g.standard_normal((N, nx, nu))
+    Q = np.zeros((N + 1, nx, nx))
+    R = np.zeros((N, nu, nu))
+    S = np.zeros((N, nu, nx))
+    for k in range(N + 1):
+        M = g.standard_normal((nx, nx)) / math.sqrt(nx)
+        Q[k] = M @ M.T + 0.5 * np.eye(nx)
+    for k in range(N):
+        M = g.standard_normal((nu, nu)) / math.sqrt(nu)
+        R[k] = M @ M.T + 0.5 * np.eye(nu)
+        S[k] = 0.1 * g.standard_normal((nu, nx))
+    c = 0.05 * g.standard_normal((N, nx))
+    q = 0.5 * g.standard_normal((N + 1, nx))
+    r = 0.5 * g.standard_normal((N, nu))
+    rows = _unit_rows(g, N * nc, nx + nu).reshape(N, nc, nx + nu) if nc else np.zeros((N, 0, nx + nu))
+    C = rows[:, :, :nx].copy()
+    D = rows[:, :, nx:].copy()
+    CN = _unit_rows(g, nf, nx) if nf else np.zeros((0, nx))
+    hi_st = g.uniform(0.3, 1.0, (N, nc)) * active_scale
+    lo_st = -g.uniform(0.3, 1.0, (N, nc)) * active_scale
+    # every third row one-sided (lo = -inf)
+    lo_st[:, ::3] = -INF
+    hi = np.concatenate([hi_st.ravel(), g.uniform(0.5, 1.5, nf)])
+    lo = np.concatenate([lo_st.ravel(), -INF * np.ones(nf)])
+    x0 = g.uniform(-0.3, 0.3, nx)
+    X = _open_loop(A, c, x0)
+    for k in range(N):
+        v = C[k] @ X[k]
+        for i in range(nc):
+            j = k * nc + i
+            if v[i] + 0.2 > hi[j]:
+                hi[j] = v[i] + 0.2
+            if v[i] - 0.2 < lo[j]:
+                lo[j] = v[i] - 0.2
+    if nf:
+        v = CN @ X[N]
+        for i in range(nf):
+            j = N * nc + i
+            if v[i] + 0.2 > hi[j]:
+                hi[j] = v[i] + 0.2
+    return QP(A=A, B=B, c=c, Q=Q, R=R, S=S, q=q, r=r, C=C, D=D, CN=CN, lo=lo, hi=hi,
+              x0=x0, name=f"general-{nx}-{nu}-{N}-{nc}-{nf}-s{seed}")
+
+
+def serving_mix(seed: int = 0, count: int = 256) -> list[QP]:
+    """Batched serving mix: nx family uniform over (12,4)/(61,12)/(75,21),
+    N ~ U{16..128}; 12D drawn as the quadrotor recipe, 61D/75D as the legged
+    recipe."""
+    g = rng(5, seed)
+    out = []
+    for i in range(count):
+        fam = int(g.integers(0, 3))
+        N = int(g.integers(16, 129))
+        s = int(g.integers(0, 2**31 - 1))
+        if fam == 0:
+            out.append(quadrotor_12d(s, N))
+        elif fam == 1:
+            out.append(legged(s, 61, 12, N))
+        else:
+            out.append(legged(s, 75, 21, N, tag=4))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# learned warm-start family: one base linearization, per-instance x0 and a
+# low-dimensional perturbation theta of the linearization and the goal
+# ----------------------------------------------------------------------------
+
+N_THETA = 8
+
+
+@dataclass
+class Family:
+    base: QP
+    M: np.ndarray = field(repr=False)        # [N_THETA, nx, nx] perturbation directions of A
+    goal_dirs: np.ndarray = field(repr=False)  # [N_THETA, 2]
+
+    def instance(self, i: int) -> QP:
+        """Instance i: x0 ~ U[-0.5, 0.5]^nx, theta ~ U[-1, 1]^8,
+        A_k(theta) = A_k + 0.002 sum_l theta_l M_l, goal angle set by theta."""
+        b = self.base
+        g = rng(77, i, b.nx)
+        x0 = g.uniform(-0.5, 0.5, b.nx)
+        th = g.uniform(-1.0, 1.0, N_THETA)
+        dA = 0.002 * np.tensordot(th, self.M, axes=(0, 0))
+        A = b.A + dA[None]
+        gd = th @ self.goal_dirs
+        xref = np.zeros(b.nx)
+        nrm = np.linalg.norm(gd)
+        gd = gd / nrm if nrm > 1e-9 else np.array([1.0, 0.0])
+        xref[0], xref[1] = 2.0 * gd[0], 2.0 * gd[1]
+        q = -(b.Q @ xref)
+        hi = b.hi.copy()
+        X = _open_loop(A, b.c, x0)
+        nc = b.nc
+        one_sided = [i for i in range(nc) if not np.isfinite(b.lo[i])]
+        _raise_offsets(b.C, hi, X, np.array(one_sided, dtype=int), 0.25)
+        if b.nf:
+            v = b.CN @ X[b.N]
+            for j in range(b.nf):
+                jj = b.N * nc + j
+                if v[j] + 0.25 > hi[jj]:
+                    hi[jj] = v[j] + 0.25
+        return QP(A=A, B=b.B, c=b.c, Q=b.Q, R=b.R, S=b.S, q=q, r=b.r, C=b.C, D=b.D,
+                  CN=b.CN, lo=b.lo, hi=hi, x0=x0, name=f"{b.name}-inst{i}",
+                  features=np.concatenate([x0, th]))
+
+
+def family(seed: int = 0, nx: int = 61, nu: int = 12, N: int = 100) -> Family:
+    base = legged(seed, nx, nu, N, tag=6)
+    g = rng(78, seed, nx)
+    M = g.standard_normal((N_THETA, nx, nx)) / math.sqrt(nx)
+    goal_dirs = g.standard_normal((N_THETA, 2))
+    return Family(base=base, M=M, goal_dirs=goal_dirs)
+
+
+# ----------------------------------------------------------------------------
+# SLS workloads
+# ----------------------------------------------------------------------------
+
+def sls_problem(seed: int = 0, nx: int = 75, nu: int = 21, N: int = 40, n_obs: int = 8,
+                tau_mode: str = "zero") -> SLSProblem:
+    """Humanoid-shaped SLS reachability problem generated as the legged QP:
+    E = diag U[0.001, 0.01] (time-invariant), Qbar = I, Rbar = I, QbarN = I;
+    tau either zero (None) or U[0, 1] per (k, j, row)."""
+    qp = legged(seed, nx, nu, N, n_obs, tag=4)
+    g = rng(8, seed, nx, N)
+    w = g.uniform(0.001, 0.01, nx)
+    E = np.repeat(np.diag(w)[None], N, axis=0)
+    tau = None
+    if tau_mode == "uniform":
+        tau = g.uniform(0.0, 1.0, (N + 1, N, max(qp.nc, qp.nf)))
+    return SLSProblem(A=qp.A, B=qp.B, E=E, Qbar=np.eye(nx), Rbar=np.eye(nu), QbarN=np.eye(nx),
+                      C=qp.C, D=qp.D, CN=qp.CN, tau=tau, name=f"sls{nx}d-N{N}-{tau_mode}-s{seed}")
+
+
+def sls_small(seed: int = 0, nx: int = 3, nu: int = 2, N: int = 5, nc: int = 3, nf: int = 2,
+              tau_mode: str = "uniform") -> SLSProblem:
+    """Small random SLS problem for pins and parity (every term present)."""
+    g = rng(10, seed, nx, nu, N)
+    A = np.eye(nx)[None] + 0.3 * g.standard_normal((N, nx, nx))
+    B = g.standard_normal((N, nx, nu))
+    E = 0.1 * g.standard_normal((N, nx, nx))
+    M = g.standard_normal((nx, nx))
+    Qbar = M @ M.T / nx + 0.5 * np.eye(nx)
+    M = g.standard_normal((nu, nu))
+    Rbar = M @ M.T / nu + 0.5 * np.eye(nu)
+    M = g.standard_normal((nx, nx))
+    QbarN = M @ M.T / nx + 0.5 * np.eye(nx)
+    C = g.standard_normal((N, nc, nx))
+    D = g.standard_normal((N, nc, nu))
+    CN = g.standard_normal((nf, nx))
+    tau = g.uniform(0.0, 1.0, (N + 1, N, max(nc, nf))) if tau_mode == "uniform" else None
+    return SLSProblem(A=A, B=B, E=E, Qbar=Qbar, Rbar=Rbar, QbarN=QbarN, C=C, D=D, CN=CN,
+                      tau=tau, name=f"sls-small-{nx}-{nu}-{N}-s{seed}")
+
+
+# ----------------------------------------------------------------------------
+# MLP initial weights (input to both the GPU trainer and the oracle)
+# ----------------------------------------------------------------------------
+
+def mlp_init(n_in: int, hidden: int, n_out: int, seed: int = 0):
+    """He-uniform initial weights [W1, b1, W2, b2, W3, b3] (float64); the last
+    layer is scaled by 0.1 so that an untrained network predicts near zero."""
+    g = rng(1234, seed, n_in, n_out)
+
+    def lin(o, i):
+        lim = np.sqrt(6.0 / i)
+        return g.uniform(-lim, lim, (o, i)), np.zeros(o)
+
+    W1, b1 = lin(hidden, n_in)
+    W2, b2 = lin(hidden, hidden)
+    W3, b3 = lin(n_out, hidden)
+    W3 *= 0.1
+    return [W1, b1, W2, b2, W3, b3]
