@@ -1,0 +1,162 @@
+/*
+ * gpusls.h -- C ABI of the B300 (sm_103a) GPU-SLS hot path.
+ *
+ * Operations follow "Safe Large-Scale Robust Nonlinear MPC in Milliseconds via
+ * Reachability-Constrained System Level Synthesis on the GPU":
+ *   qp_*   the ADMM solver for the LTV-QP of Sec. III-B (eq. sqp_qp), Sec. IV-A
+ *   sls_*  the SLS controller / reachability solve of Sec. III-C and IV-B
+ *   mlp_*  the learned warm start (no counterpart in the paper)
+ *
+ * Conventions (all calls):
+ *   - Arrays are row-major and time-major.  Unless stated otherwise every
+ *     array argument is a DEVICE pointer to float64 data.  The library copies
+ *     what it keeps; the caller owns its buffers and may free them after the
+ *     call returns (calls are stream-ordered on the handle's stream; results
+ *     are complete when the call returns).
+ *   - A "pool" is the concatenation, QP by QP, of the per-QP arrays in the
+ *     order of the dims table; QP b's block starts after the blocks of QPs
+ *     0..b-1 (sizes from each QP's own dims).
+ *   - Every call returns an int status (GPUSLS_*).  On failure
+ *     gpusls_last_error() returns a message for the calling thread.
+ *   - Sizes: 1 <= nx <= 80, 1 <= nu <= 32, 0 <= nc <= 64, 0 <= nf <= 64,
+ *     1 <= N <= 1024.  Larger values return GPUSLS_ERR_INVALID.
+ */
+#ifndef GPUSLS_H
+#define GPUSLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GPUSLS_OK             0   /* solved (converged to the tolerance)            */
+#define GPUSLS_MAX_ITER       1   /* iteration limit reached; results are valid     */
+#define GPUSLS_ERR_INVALID   -1   /* invalid argument or dimensions                 */
+#define GPUSLS_ERR_NOT_SPD   -2   /* R^, Gamma^-1 or Qu not SPD, or I + C~P~ singular */
+#define GPUSLS_ERR_NAN       -3   /* NaN/Inf appeared in the iterates               */
+#define GPUSLS_ERR_INFEASIBLE -4  /* primal infeasibility detected                  */
+#define GPUSLS_ERR_CUDA      -5   /* CUDA runtime error                             */
+#define GPUSLS_ERR_TIMEOUT   -6   /* a bounded device wait gave up                  */
+
+/* arithmetic of the solve kernels */
+#define GPUSLS_FP64 0   /* all arithmetic in float64                                  */
+#define GPUSLS_FP32 1   /* all arithmetic in float32 (KKT check stays float64)        */
+
+/* Dimensions of one LTV-QP (eq. sqp_qp): state nx, input nu, horizon N, stage
+ * constraint rows nc (rows of C_k, D_k), terminal rows nf (rows of C_N). */
+typedef struct qp_dims {
+  int32_t nx, nu, N, nc, nf;
+} qp_dims;
+
+/* Solver settings.  The paper fixes none of these (Sec. IV-A.2 names an
+ * OSQP-style rho update every sigma iterations); defaults via
+ * qp_default_settings(). */
+typedef struct qp_settings {
+  double rho0;        /* initial penalty (default 0.1)                              */
+  double eps;         /* in-loop tolerance on ||r_prim||_inf and ||r_dual||_inf     */
+  double eps_kkt;     /* FP64 KKT tolerance gating convergence; <= 0 disables       */
+  double rho_min, rho_max;
+  int32_t sigma;      /* rho-update interval in iterations; 0 keeps rho fixed       */
+  int32_t check_every;/* stop-test interval                                         */
+  int32_t max_iter;
+  int32_t precision;  /* GPUSLS_FP64 or GPUSLS_FP32                                 */
+  int32_t cluster;    /* CTAs (thread blocks) per QP, 1..8; 0 picks by N            */
+  int32_t fixed_iters;/* > 0: run exactly this many iterations, no stop test        */
+} qp_settings;
+
+/* Per-QP result summary (host memory). */
+typedef struct qp_info {
+  int32_t status;     /* GPUSLS_OK, GPUSLS_MAX_ITER or a negative error            */
+  int32_t iters;      /* ADMM iterations run                                       */
+  int32_t refactors;  /* rho-dependent factorizations (tree scans) performed       */
+  int32_t pad;
+  double rho;         /* final penalty                                             */
+  double r_prim, r_dual; /* last in-loop residuals                                 */
+  double kkt;         /* FP64 KKT residual of the returned point (-1 if not evaluated) */
+} qp_info;
+
+typedef struct qp_handle qp_handle;
+
+/* Fills s with the defaults: rho0 0.1, eps 1e-4, eps_kkt 1e-4, rho range
+ * [1e-6, 1e6], sigma 25, check_every 5, max_iter 4000, FP64, cluster 0. */
+void qp_default_settings(qp_settings* s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gpusls_last_error(void);
+
+/* qp_setup: one LTV-QP (eq. sqp_qp), Sec. IV-A.
+ *   A [N][nx][nx]  B [N][nx][nu]  c [N][nx]   (c_k is the paper's b_k)
+ *   Q [N+1][nx][nx] (Q[N] = Q_N)  R [N][nu][nu]  S [N][nu][nx] or NULL (zero)
+ *   q [N+1][nx]  r [N][nu]
+ *   C [N][nc][nx]  D [N][nc][nu]  CN [nf][nx]
+ *   lo, hi [N*nc + nf]: lo <= G(dx, du) <= hi, +-INFINITY allowed (the paper's
+ *   one-sided z <= f is lo = -INF, hi = f)
+ *   rho: initial penalty (<= 0 uses s->rho0)
+ *   stream: cudaStream_t (NULL = legacy default stream)
+ * The handle owns all device workspace. */
+int qp_setup(qp_handle** h, qp_dims d,
+             const double* A, const double* B, const double* c,
+             const double* Q, const double* R, const double* S,
+             const double* q, const double* r,
+             const double* C, const double* D, const double* CN,
+             const double* lo, const double* hi,
+             double rho, const qp_settings* s, void* stream);
+
+/* qp_batch_setup: `batch` independent QPs of possibly different dims in one
+ * handle; every array argument is a pool (see conventions).  dims is a HOST
+ * array [batch].  rho is a HOST array [batch] or NULL (s->rho0). */
+int qp_batch_setup(qp_handle** h, int32_t batch, const qp_dims* dims,
+                   const double* A, const double* B, const double* c,
+                   const double* Q, const double* R, const double* S,
+                   const double* q, const double* r,
+                   const double* C, const double* D, const double* CN,
+                   const double* lo, const double* hi,
+                   const double* rho, const qp_settings* s, void* stream);
+
+/* qp_solve: run ADMM (Sec. IV-A) from the handle's current (z, y, rho) -- a
+ * cold start z = y = 0 after setup, or the state left by the previous solve
+ * or by qp_set_warm_start -- until the stop test passes or `iters`
+ * iterations ran (iters <= 0: s->max_iter).  tol > 0 overrides s->eps and
+ * s->eps_kkt.  One persistent kernel launch solves every QP of the handle.
+ *   x0 [nx] (pool for batches)   outputs: dx [N+1][nx], du [N][nu],
+ *   lam [N*nc+nf] (unscaled multipliers lambda = rho * y), all pools.
+ *   info: HOST array [batch] or NULL.
+ * Returns GPUSLS_OK if every QP converged, GPUSLS_MAX_ITER if some did not,
+ * or the most severe negative per-QP status. */
+int qp_solve(qp_handle* h, const double* x0, int32_t iters, double tol,
+             double* dx, double* du, double* lam, qp_info* info);
+
+/* qp_set_warm_start: set the ADMM state (z, y = lambda / rho) and rho of every
+ * QP (pools of [N*nc+nf]; rho a HOST array [batch]).  z or y may be NULL
+ * (zero); rho may be NULL (keep).  Used by the learned warm start. */
+int qp_set_warm_start(qp_handle* h, const double* z, const double* y, const double* rho);
+
+/* qp_get_state: copy (z, y) pools and rho (HOST [batch]) out of the handle. */
+int qp_get_state(qp_handle* h, double* z, double* y, double* rho);
+
+/* qp_update: replace the linear terms and bounds (q, r, lo, hi; pools, same
+ * dims; any may be NULL to keep) without touching the cached factorization. */
+int qp_update(qp_handle* h, const double* q, const double* r, const double* lo, const double* hi);
+
+/* qp_kkt: FP64 KKT residual of a candidate point (dx, du, lam pools) for
+ * every QP of the handle (reading of the paper's undefined "residual":
+ * max of dynamics, bound violation, u-stationarity after costate recovery,
+ * complementarity).  out: HOST array [batch]. */
+int qp_kkt(qp_handle* h, const double* x0, const double* dx, const double* du,
+           const double* lam, double* out);
+
+/* qp_riccati: run the rho-dependent factorization (eq. augmented_matrices,
+ * eq. assoc_init, the reverse scan of eq. combination_rules and eq.
+ * controller_cache) at the handle's current rho and copy out
+ * P [N+1][nx][nx] and K [N][nu][nx] (pools).  Exposes the refactor for
+ * per-step parity checks. */
+int qp_riccati(qp_handle* h, double* P, double* K);
+
+void qp_destroy(qp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPUSLS_H */

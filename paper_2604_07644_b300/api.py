@@ -1,0 +1,161 @@
+"""Python front end of the GPU-SLS library: packs problem data into device
+pools (torch tensors, float64) and calls the C ABI.  No arithmetic of the
+method happens here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import native
+
+QP_FIELDS = ("A", "B", "c", "Q", "R", "S", "q", "r", "C", "D", "CN")
+
+
+def _dptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream: torch.cuda.Stream | None):
+    s = stream or torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def pool(arrays: list[np.ndarray], device="cuda") -> torch.Tensor:
+    """Concatenate per-QP arrays (flattened, float64) into one device pool."""
+    flat = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in arrays]
+    host = np.concatenate(flat) if flat else np.zeros(0)
+    if host.size == 0:
+        host = np.zeros(1)
+    return torch.from_numpy(host).to(device)
+
+
+@dataclass
+class Result:
+    dx: list
+    du: list
+    lam: list
+    info: list
+    status: int
+
+
+class QPBatch:
+    """A handle over one or more LTV-QPs (qp_batch_setup)."""
+
+    def __init__(self, qps, settings: native.qp_settings | None = None, rho=None, stream=None, device="cuda"):
+        self.lib = native.load()
+        self.qps = list(qps)
+        self.B = len(self.qps)
+        self.device = device
+        self.stream = stream
+        self.settings = settings or native.default_settings()
+        dims = (native.qp_dims * self.B)()
+        for i, qp in enumerate(self.qps):
+            dims[i].nx, dims[i].nu, dims[i].N, dims[i].nc, dims[i].nf = qp.dims()
+        self.dims = dims
+        self.pools = {f: pool([getattr(qp, f) for qp in self.qps], device) for f in QP_FIELDS}
+        self.pools["lo"] = pool([qp.lo for qp in self.qps], device)
+        self.pools["hi"] = pool([qp.hi for qp in self.qps], device)
+        rho_arr = None
+        if rho is not None:
+            rho_arr = (C.c_double * self.B)(*([float(rho)] * self.B if np.isscalar(rho) else [float(v) for v in rho]))
+        h = C.c_void_p()
+        p = self.pools
+        st = self.lib.qp_batch_setup(C.byref(h), self.B, dims, _dptr(p["A"]), _dptr(p["B"]), _dptr(p["c"]),
+                                     _dptr(p["Q"]), _dptr(p["R"]), _dptr(p["S"]), _dptr(p["q"]), _dptr(p["r"]),
+                                     _dptr(p["C"]), _dptr(p["D"]), _dptr(p["CN"]), _dptr(p["lo"]), _dptr(p["hi"]),
+                                     rho_arr, C.byref(self.settings), _stream_ptr(stream))
+        native.check(st, "qp_batch_setup")
+        self.h = h
+        self.nx = [qp.nx for qp in self.qps]
+        self.sizes = dict(
+            x=[(qp.N + 1) * qp.nx for qp in self.qps],
+            u=[qp.N * qp.nu for qp in self.qps],
+            m=[qp.m for qp in self.qps],
+            P=[(qp.N + 1) * qp.nx * qp.nx for qp in self.qps],
+            K=[qp.N * qp.nu * qp.nx for qp in self.qps],
+        )
+        self.out_x = torch.zeros(max(1, sum(self.sizes["x"])), dtype=torch.float64, device=device)
+        self.out_u = torch.zeros(max(1, sum(self.sizes["u"])), dtype=torch.float64, device=device)
+        self.out_l = torch.zeros(max(1, sum(self.sizes["m"])), dtype=torch.float64, device=device)
+        self.x0 = pool([qp.x0 for qp in self.qps], device)
+
+    # -- helpers ---------------------------------------------------------
+    def _split(self, t: torch.Tensor, key: str, shapes):
+        out, o = [], 0
+        host = t.cpu().numpy()
+        for n, shp in zip(self.sizes[key], shapes):
+            out.append(host[o:o + n].reshape(shp))
+            o += n
+        return out
+
+    def set_x0(self, x0s):
+        self.x0 = pool(list(x0s), self.device)
+
+    # -- API ---------------------------------------------------------------
+    def solve(self, iters: int = 0, tol: float = 0.0, fetch: bool = True) -> Result | int:
+        info = (native.qp_info * self.B)()
+        st = self.lib.qp_solve(self.h, _dptr(self.x0), int(iters), float(tol), _dptr(self.out_x),
+                               _dptr(self.out_u), _dptr(self.out_l), info)
+        native.check(st, "qp_solve")
+        if not fetch:
+            return st
+        dx = self._split(self.out_x, "x", [(qp.N + 1, qp.nx) for qp in self.qps])
+        du = self._split(self.out_u, "u", [(qp.N, qp.nu) for qp in self.qps])
+        lam = self._split(self.out_l, "m", [(qp.m,) for qp in self.qps])
+        infos = [dict(status=info[i].status, iters=info[i].iters, refactors=info[i].refactors, rho=info[i].rho,
+                      r_prim=info[i].r_prim, r_dual=info[i].r_dual, kkt=info[i].kkt) for i in range(self.B)]
+        return Result(dx, du, lam, infos, st)
+
+    def riccati(self):
+        P = torch.zeros(max(1, sum(self.sizes["P"])), dtype=torch.float64, device=self.device)
+        K = torch.zeros(max(1, sum(self.sizes["K"])), dtype=torch.float64, device=self.device)
+        native.check(self.lib.qp_riccati(self.h, _dptr(P), _dptr(K)), "qp_riccati")
+        Ps = self._split(P, "P", [(qp.N + 1, qp.nx, qp.nx) for qp in self.qps])
+        Ks = self._split(K, "K", [(qp.N, qp.nu, qp.nx) for qp in self.qps])
+        return Ps, Ks
+
+    def kkt(self, dx, du, lam):
+        out = (C.c_double * self.B)()
+        tx = pool(list(dx), self.device)
+        tu = pool(list(du), self.device)
+        tl = pool(list(lam), self.device)
+        native.check(self.lib.qp_kkt(self.h, _dptr(self.x0), _dptr(tx), _dptr(tu), _dptr(tl), out), "qp_kkt")
+        return [out[i] for i in range(self.B)]
+
+    def set_warm_start(self, z=None, y=None, rho=None):
+        tz = pool(list(z), self.device) if z is not None else None
+        ty = pool(list(y), self.device) if y is not None else None
+        ra = None
+        if rho is not None:
+            vals = [float(rho)] * self.B if np.isscalar(rho) else [float(v) for v in rho]
+            ra = (C.c_double * self.B)(*vals)
+        native.check(self.lib.qp_set_warm_start(self.h, _dptr(tz), _dptr(ty), ra), "qp_set_warm_start")
+
+    def get_state(self):
+        tz = torch.zeros(max(1, sum(self.sizes["m"])), dtype=torch.float64, device=self.device)
+        ty = torch.zeros_like(tz)
+        rho = (C.c_double * self.B)()
+        native.check(self.lib.qp_get_state(self.h, _dptr(tz), _dptr(ty), rho), "qp_get_state")
+        return (self._split(tz, "m", [(qp.m,) for qp in self.qps]), self._split(ty, "m", [(qp.m,) for qp in self.qps]),
+                [rho[i] for i in range(self.B)])
+
+    def update(self, q=None, r=None, lo=None, hi=None):
+        t = {k: (pool(list(v), self.device) if v is not None else None) for k, v in
+             dict(q=q, r=r, lo=lo, hi=hi).items()}
+        native.check(self.lib.qp_update(self.h, _dptr(t["q"]), _dptr(t["r"]), _dptr(t["lo"]), _dptr(t["hi"])),
+                     "qp_update")
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.lib.qp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

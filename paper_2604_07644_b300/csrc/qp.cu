@@ -1,0 +1,759 @@
+// Persistent ADMM solver for batches of LTV-QPs (Sec. IV-A) and its C ABI
+// (include/gpusls.h).  Host code owns the workspace; one cluster launch solves
+// every QP of a handle.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/gpusls.h"
+#include "qp_iter.cuh"
+
+namespace gsls {
+
+// ---------------------------------------------------------------------------
+// the solve kernel
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT, 1) qp_kernel(const QPDesc* __restrict__ descs, SolveArgs args) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ QPDesc dsh;
+  const int cs = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int qi = blockIdx.x / cs;
+  if (threadIdx.x == 0) dsh = descs[qi];
+  __syncthreads();
+  QPDesc& d = dsh;
+
+  const SmemLayout lay = smem_layout(d.nx, d.ldx, d.ldu, d.nc, d.nf, d.Lc, (int)sizeof(T));
+  Ctx<T> c;
+  c.d = &d;
+  c.rank = rank;
+  c.cs = cs;
+  c.s = min(rank * d.Lc, d.N);
+  c.e = min((rank + 1) * d.Lc, d.N);
+  c.L = c.e - c.s;
+  c.active = rank < d.nch;
+  c.first = rank == 0;
+  c.last = rank == d.nch - 1;
+  c.gemm = reinterpret_cast<T*>(smem + lay.gemm);
+  c.gj = reinterpret_cast<T*>(smem + lay.gj);
+  c.gjbuf = reinterpret_cast<T*>(smem + lay.gjbuf);
+  c.ring = reinterpret_cast<T*>(smem + lay.ring);
+  c.zS = reinterpret_cast<T*>(smem + lay.z);
+  c.yS = reinterpret_cast<T*>(smem + lay.y);
+  c.wS = reinterpret_cast<T*>(smem + lay.w);
+  c.cS = reinterpret_cast<T*>(smem + lay.c);
+  c.lS = reinterpret_cast<T*>(smem + lay.l);
+  c.kS = reinterpret_cast<T*>(smem + lay.k);
+  c.dS = reinterpret_cast<T*>(smem + lay.d);
+  c.xS = reinterpret_cast<T*>(smem + lay.x);
+  c.uS = reinterpret_cast<T*>(smem + lay.u);
+  c.pe = reinterpret_cast<T*>(smem + lay.pe);
+  c.xs = reinterpret_cast<T*>(smem + lay.xs);
+  c.slotL = reinterpret_cast<T*>(smem + lay.slotL);
+  c.slotX = reinterpret_cast<T*>(smem + lay.slotX);
+  c.tmp1 = reinterpret_cast<T*>(smem + lay.tmp1);
+  c.tmp2 = reinterpret_cast<T*>(smem + lay.tmp2);
+  c.tmp3 = reinterpret_cast<T*>(smem + lay.tmp3);
+  c.red = reinterpret_cast<T*>(smem + lay.red);
+  c.part = reinterpret_cast<double*>(smem + lay.part);
+  c.perm = reinterpret_cast<int*>(smem + lay.perm);
+  c.flag = reinterpret_cast<int*>(smem + lay.flag);
+  c.msz = d.nx * d.ldx;
+  c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
+  const int t = threadIdx.x;
+
+  if (args.mode == MODE_KKT) {
+    const double kkt = kkt_eval<T>(c, cl);
+    if (rank == 0 && t == 0) d.info_d[3] = kkt;
+    return;
+  }
+
+  T rho = (T)d.rho[0];
+  int refactors = 0;
+  int status = GPUSLS_MAX_ITER;
+  if (args.mode == MODE_RICCATI || d.flags[0] == 0) {
+    const int bad = refactor<T>(c, cl, rho);
+    ++refactors;
+    if (bad) status = GPUSLS_ERR_NOT_SPD;
+  }
+  if (args.mode == MODE_RICCATI) {
+    // P_i = level-0 inclusive suffixes, K_i gains, as FP64 dense blocks.
+    const int nx = d.nx, nu = d.nu, ldx = d.ldx, msz = c.msz;
+    if (c.active) {
+      const int iend = c.e + (c.last ? 1 : 0);
+      for (int i = c.s; i < iend; ++i)
+        for (int e2 = t; e2 < nx * nx; e2 += NT)
+          d.ox[(size_t)i * nx * nx + e2] = (double)TP<T>(d.IP)[(size_t)i * msz + (e2 / nx) * ldx + e2 % nx];
+      for (int i = c.s; i < c.e; ++i)
+        for (int e2 = t; e2 < nu * nx; e2 += NT)
+          d.ou[(size_t)i * nu * nx + e2] = (double)TP<T>(d.K)[(size_t)i * nu * ldx + (e2 / nx) * ldx + e2 % nx];
+    }
+    if (rank == 0 && t == 0) {
+      d.info_i[0] = status == GPUSLS_ERR_NOT_SPD ? status : GPUSLS_OK;
+      d.info_i[2] = refactors;
+      d.flags[0] = status == GPUSLS_ERR_NOT_SPD ? 0 : 1;
+    }
+    return;
+  }
+
+  // load the ADMM state of own rows
+  const int nrows = own_rows(c);
+  const T* zg = TP<T>(d.z);
+  const T* yg = TP<T>(d.y);
+  for (int e2 = t; e2 < nrows; e2 += NT) {
+    c.zS[e2] = zg[(size_t)c.s * d.nc + e2];
+    c.yS[e2] = yg[(size_t)c.s * d.nc + e2];
+  }
+  __syncthreads();
+
+  double eps = args.eps;
+  const bool fixed = args.fixed_iters > 0;
+  const int max_it = fixed ? args.fixed_iters : args.max_iter;
+  double rp = INFINITY, rd = INFINITY, kkt = -1.0;
+  int it = 0;
+  if (status != GPUSLS_ERR_NOT_SPD) {
+    for (it = 1; it <= max_it; ++it) {
+      const bool stop_iter = !fixed && (it % args.check_every == 0);
+      const bool rho_iter = !fixed && args.sigma > 0 && (it % args.sigma == 0);
+      const bool check = stop_iter || rho_iter || (it == max_it);
+      Partials pl;
+      admm_iteration<T>(c, cl, rho, check, pl);
+      if (!check) continue;
+      double v[4] = {pl.rp, pl.rd, pl.vm, pl.zm};
+      cluster_max(c, cl, v, 4);
+      rp = v[0];
+      rd = v[1];
+      if (!(isfinite(rp) && isfinite(rd))) {
+        status = GPUSLS_ERR_NAN;
+        break;
+      }
+      if (stop_iter && rp <= eps && rd <= eps) {
+        if (args.eps_kkt <= 0.0) {
+          status = GPUSLS_OK;
+          break;
+        }
+        full_xu<T>(c);
+        write_outputs<T>(c, rho);
+        kkt = kkt_eval<T>(c, cl);
+        if (kkt <= args.eps_kkt) {
+          status = GPUSLS_OK;
+          break;
+        }
+        eps *= 0.1;
+      }
+      if (rho_iter) {
+        full_xu<T>(c);
+        double hm, gm, qm;
+        rho_rule_partials<T>(c, rho, hm, gm, qm);
+        double u[3] = {hm, gm, qm};
+        cluster_max(c, cl, u, 3);
+        const double prim_scale = fmax(v[2], v[3]);
+        const double dual_scale = fmax(fmax(u[0], u[1]), u[2]);
+        double rho_new = (double)rho;
+        if (rp > 0.0 && rd > 0.0 && prim_scale > 0.0 && dual_scale > 0.0) {
+          const double ratio = (rp / prim_scale) / (rd / dual_scale);
+          rho_new = fmin(fmax((double)rho * sqrt(ratio), args.rho_min), args.rho_max);
+        }
+        if (rho_new > 5.0 * (double)rho || rho_new < (double)rho / 5.0) {
+          const T scale = (T)((double)rho / rho_new);
+          for (int e2 = t; e2 < nrows; e2 += NT) c.yS[e2] *= scale;
+          rho = (T)rho_new;
+          __syncthreads();
+          const int bad = refactor<T>(c, cl, rho);
+          ++refactors;
+          if (bad) {
+            status = GPUSLS_ERR_NOT_SPD;
+            break;
+          }
+        }
+      }
+    }
+    if (it > max_it) it = max_it;
+    full_xu<T>(c);
+    write_outputs<T>(c, rho);
+    if (status == GPUSLS_OK && args.eps_kkt <= 0.0) kkt = -1.0;
+  }
+  // store state
+  T* zw = TP<T>(d.z);
+  T* yw = TP<T>(d.y);
+  for (int e2 = t; e2 < nrows; e2 += NT) {
+    zw[(size_t)c.s * d.nc + e2] = c.zS[e2];
+    yw[(size_t)c.s * d.nc + e2] = c.yS[e2];
+  }
+  if (rank == 0 && t == 0) {
+    d.info_i[0] = status;
+    d.info_i[1] = it;
+    d.info_i[2] = refactors;
+    d.info_d[0] = (double)rho;
+    d.info_d[1] = rp;
+    d.info_d[2] = rd;
+    d.info_d[3] = kkt;
+    d.rho[0] = (double)rho;
+    d.flags[0] = (status == GPUSLS_ERR_NOT_SPD) ? 0 : 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// packing FP64 caller arrays into padded solve-precision layouts
+// ---------------------------------------------------------------------------
+struct PackJob {
+  const double* src;  // null: zero fill
+  void* dst;
+  int count, rows, cols, ld;
+};
+
+template <typename T>
+__global__ void pack_kernel(const PackJob* __restrict__ jobs) {
+  const PackJob j = jobs[blockIdx.y];
+  const size_t total = (size_t)j.count * j.rows * j.ld;
+  T* dst = reinterpret_cast<T*>(j.dst);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t rowi = e / j.ld;
+    const int col = (int)(e - rowi * j.ld);
+    T v = T(0);
+    if (col < j.cols && j.src) v = (T)j.src[rowi * j.cols + col];
+    dst[e] = v;
+  }
+}
+
+}  // namespace gsls
+
+// ===========================================================================
+// host side
+// ===========================================================================
+using namespace gsls;
+
+static thread_local std::string g_err;
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+#define CU(x)                                                                                \
+  do {                                                                                       \
+    cudaError_t e_ = (x);                                                                    \
+    if (e_ != cudaSuccess) return fail(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct QPOffsets {
+  size_t A, B, c, Q, R, S, q, r, C, D, CN, lohi, x0, dx, du, P, K;
+};
+
+struct qp_handle {
+  int batch = 0;
+  std::vector<qp_dims> dims;
+  std::vector<QPOffsets> off;   // offsets into the caller's pools (elements)
+  qp_settings set;
+  cudaStream_t stream = nullptr;
+  int esz = 8;                  // bytes of the solve precision
+  int cs = 1;
+  int smem = 0;
+  void* tpool = nullptr;        // solve-precision workspace
+  double* dpool = nullptr;      // FP64 workspace
+  QPDesc* ddesc = nullptr;      // device descriptors
+  std::vector<QPDesc> hdesc;
+  int* info_i = nullptr;
+  double* info_d = nullptr;
+  PackJob* djobs = nullptr;
+  size_t njobs_cap = 0;
+  // per-QP pointers kept for conversions
+  std::vector<void*> tx0;
+};
+
+static size_t al64(size_t x) { return (x + 63) & ~(size_t)63; }
+
+extern "C" void qp_default_settings(qp_settings* s) {
+  s->rho0 = 0.1;
+  s->eps = 1e-4;
+  s->eps_kkt = 1e-4;
+  s->rho_min = 1e-6;
+  s->rho_max = 1e6;
+  s->sigma = 25;
+  s->check_every = 5;
+  s->max_iter = 4000;
+  s->precision = GPUSLS_FP64;
+  s->cluster = 0;
+  s->fixed_iters = 0;
+}
+
+extern "C" const char* gpusls_last_error(void) { return g_err.c_str(); }
+
+static int auto_cluster(int N) {
+  int cs = (N + 11) / 12;
+  return std::max(1, std::min(MAXCS, cs));
+}
+
+template <typename T>
+static int launch_qp(qp_handle* h, const SolveArgs& a) {
+  auto kern = qp_kernel<T>;
+  CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(h->batch * h->cs, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = h->smem;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = h->cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CU(cudaLaunchKernelEx(&cfg, kern, (const QPDesc*)h->ddesc, a));
+  CU(cudaGetLastError());
+  return GPUSLS_OK;
+}
+
+static int launch(qp_handle* h, const SolveArgs& a) {
+  return h->esz == 8 ? launch_qp<double>(h, a) : launch_qp<float>(h, a);
+}
+
+static int run_pack(qp_handle* h, const std::vector<PackJob>& jobs) {
+  if (jobs.empty()) return GPUSLS_OK;
+  if (jobs.size() > h->njobs_cap) {
+    if (h->djobs) cudaFree(h->djobs);
+    CU(cudaMalloc(&h->djobs, jobs.size() * sizeof(PackJob)));
+    h->njobs_cap = jobs.size();
+  }
+  CU(cudaMemcpyAsync(h->djobs, jobs.data(), jobs.size() * sizeof(PackJob), cudaMemcpyHostToDevice, h->stream));
+  for (size_t j0 = 0; j0 < jobs.size(); j0 += 60000) {
+    const int nj = (int)std::min<size_t>(60000, jobs.size() - j0);
+    dim3 grid(32, nj);
+    if (h->esz == 8) pack_kernel<double><<<grid, 256, 0, h->stream>>>(h->djobs + j0);
+    else pack_kernel<float><<<grid, 256, 0, h->stream>>>(h->djobs + j0);
+    CU(cudaGetLastError());
+  }
+  // the jobs buffer is reused by later calls: keep the upload ordered
+  CU(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+static bool dims_ok(const qp_dims& d) {
+  return d.nx >= 1 && d.nx <= TILE && d.nu >= 1 && d.nu <= 32 && d.nc >= 0 && d.nc <= 64 && d.nf >= 0 &&
+         d.nf <= 64 && d.N >= 1 && d.N <= 1024;
+}
+
+extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dims, const double* A, const double* B,
+                              const double* c, const double* Q, const double* R, const double* S, const double* q,
+                              const double* r, const double* C, const double* D, const double* CN, const double* lo,
+                              const double* hi, const double* rho, const qp_settings* s, void* stream) {
+  if (!out || batch < 1 || !dims || !A || !B || !c || !Q || !R || !q || !r || !lo || !hi || !s)
+    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: null argument or batch < 1");
+  if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32)
+    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: unknown precision");
+  if (s->cluster < 0 || s->cluster > MAXCS) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: cluster must be 0..8");
+  if (s->check_every < 1 || s->max_iter < 1 || s->sigma < 0)
+    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: check_every, max_iter >= 1 and sigma >= 0 required");
+  int needC = 0, needCN = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (!dims_ok(dims[b])) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: dims out of range for QP " + std::to_string(b));
+    needC |= dims[b].nc > 0;
+    needCN |= dims[b].nf > 0;
+  }
+  if ((needC && (!C || !D)) || (needCN && !CN)) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: C/D/CN missing");
+
+  qp_handle* h = new qp_handle();
+  h->batch = batch;
+  h->dims.assign(dims, dims + batch);
+  h->set = *s;
+  h->stream = (cudaStream_t)stream;
+  h->esz = s->precision == GPUSLS_FP64 ? 8 : 4;
+  int cs = s->cluster;
+  if (cs == 0) {
+    int Nmax = 1;
+    for (auto& d : h->dims) Nmax = std::max(Nmax, d.N);
+    cs = auto_cluster(Nmax);
+  }
+  h->cs = cs;
+
+  // caller pool offsets
+  h->off.resize(batch);
+  QPOffsets o = {};
+  for (int b = 0; b < batch; ++b) {
+    const qp_dims& d = dims[b];
+    h->off[b] = o;
+    const size_t nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf, m = N * nc + nf;
+    o.A += N * nx * nx; o.B += N * nx * nu; o.c += N * nx; o.Q += (N + 1) * nx * nx; o.R += N * nu * nu;
+    o.S += N * nu * nx; o.q += (N + 1) * nx; o.r += N * nu; o.C += N * nc * nx; o.D += N * nc * nu;
+    o.CN += nf * nx; o.lohi += m; o.x0 += nx; o.dx += (N + 1) * nx; o.du += N * nu; o.P += (N + 1) * nx * nx;
+    o.K += N * nu * nx;
+  }
+  const QPOffsets tot = o;
+
+  // workspace sizes
+  const int esz = h->esz;
+  std::vector<size_t> toff(batch), doff(batch);
+  size_t tsz = 0, dsz = 0;
+  int smem = 0;
+  h->hdesc.resize(batch);
+  struct Sizes {
+    size_t A, B, b, Q, R, S, q, r, C, D, CN, lo, hi, x0, Rhi, Sh, V, scr, Abar, CK, F, FPi, J, K, KSig, CKSig, Sig,
+        c0, k0, CNSig, SigN, Tch, Uch, Theta, Xi, Gam, z, y;
+  };
+  std::vector<Sizes> sz(batch);
+  for (int b = 0; b < batch; ++b) {
+    const qp_dims& d = dims[b];
+    const size_t nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf, m = N * nc + nf;
+    const size_t ldx = rup4(d.nx), ldu = rup4(d.nu), ldc = rup4(std::max(1, d.nc));
+    const size_t msz = nx * ldx;
+    const int n = d.N + 1;
+    int nlev = 0;
+    while ((1 << nlev) < n) ++nlev;
+    size_t nodes = 0;
+    for (int lv = 0; lv <= nlev; ++lv) nodes += (n + (1 << lv) - 1) >> lv;
+    Sizes& z = sz[b];
+    z.A = al64(N * msz); z.B = al64(N * nx * ldu); z.b = al64(N * ldx); z.Q = al64((N + 1) * msz);
+    z.R = al64(N * nu * ldu); z.S = al64(N * nu * ldx); z.q = al64((N + 1) * ldx); z.r = al64(N * ldu);
+    z.C = al64(N * nc * ldx + 1); z.D = al64(N * nc * ldu + 1); z.CN = al64(nf * ldx + 1); z.lo = al64(m + 1);
+    z.hi = al64(m + 1); z.x0 = al64(ldx); z.Rhi = al64(N * nu * ldu); z.Sh = al64(N * nu * ldx);
+    z.V = al64(nodes * msz); z.scr = al64((size_t)MAXCS * 6 * msz); z.Abar = al64(N * msz);
+    z.CK = al64(N * nc * ldx + 1); z.F = al64(N * nu * ldx); z.FPi = al64(N * nu * ldx); z.J = al64(N * nu * ldc);
+    z.K = al64(N * nu * ldx); z.KSig = al64(N * nu * ldx); z.CKSig = al64(N * nc * ldx + 1); z.Sig = al64(N * msz);
+    z.c0 = al64(N * ldx); z.k0 = al64(N * ldu); z.CNSig = al64(nf * ldx + 1); z.SigN = al64(msz);
+    z.Tch = al64(MAXCS * msz); z.Uch = al64(MAXCS * msz); z.Theta = al64(MAXCS * MAXCS * msz);
+    z.Xi = al64(MAXCS * MAXCS * msz); z.Gam = al64(N * nu * ldu); z.z = al64(m + 1); z.y = al64(m + 1);
+    toff[b] = tsz;
+    tsz += z.A + z.B + z.b + z.Q + z.R + z.S + z.q + z.r + z.C + z.D + z.CN + z.lo + z.hi + z.x0 + z.Rhi + z.Sh +
+           4 * z.V + z.scr + z.Abar + z.CK + z.F + z.FPi + z.J + z.K + z.KSig + z.CKSig + z.Sig + z.c0 + z.k0 +
+           z.CNSig + z.SigN + z.Tch + z.Uch + z.Theta + z.Xi + z.Gam + z.z + z.y;
+    doff[b] = dsz;
+    dsz += al64((N + 1) * nx) + al64(N * nu) + 64;   // kg, kh, rho/flags slot
+    // per-QP descriptor (pointers filled after allocation)
+    QPDesc& D_ = h->hdesc[b];
+    memset(&D_, 0, sizeof(D_));
+    D_.nx = d.nx; D_.nu = d.nu; D_.N = d.N; D_.nc = d.nc; D_.nf = d.nf; D_.m = (int)m;
+    D_.ldx = (int)ldx; D_.ldu = (int)ldu; D_.ldc = (int)ldc;
+    D_.Lc = (d.N + cs - 1) / cs;
+    D_.nch = (d.N + D_.Lc - 1) / D_.Lc;
+    D_.nlev = nlev;
+    const SmemLayout lay = smem_layout(d.nx, (int)ldx, (int)ldu, d.nc, d.nf, D_.Lc, esz);
+    smem = std::max(smem, lay.total);
+  }
+  h->smem = smem;
+  if (smem > 227 * 1024) {
+    delete h;
+    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: shared memory per CTA exceeds 227 KB (raise cluster or lower N)");
+  }
+  // FP64 copies of the caller's arrays live in dpool after the per-QP scratch
+  const size_t d_copy = tot.A + tot.B + tot.c + tot.Q + tot.R + tot.S + tot.q + tot.r + tot.C + tot.D + tot.CN +
+                        2 * tot.lohi + tot.x0 + 64;
+  cudaError_t e1 = cudaMalloc(&h->tpool, tsz * esz + 256);
+  cudaError_t e2 = cudaMalloc(&h->dpool, (dsz + d_copy) * sizeof(double) + 256);
+  cudaError_t e3 = cudaMalloc(&h->ddesc, batch * sizeof(QPDesc));
+  cudaError_t e4 = cudaMalloc(&h->info_i, batch * 4 * sizeof(int));
+  cudaError_t e5 = cudaMalloc(&h->info_d, batch * 4 * sizeof(double));
+  if (e1 || e2 || e3 || e4 || e5) {
+    qp_destroy(h);
+    return fail(GPUSLS_ERR_CUDA, "qp_batch_setup: cudaMalloc failed");
+  }
+  // FP64 copies
+  double* dc = h->dpool + dsz;
+  double *A64 = dc, *B64 = A64 + tot.A, *b64 = B64 + tot.B, *Q64 = b64 + tot.c, *R64 = Q64 + tot.Q,
+         *S64 = R64 + tot.R, *q64 = S64 + tot.S, *r64 = q64 + tot.q, *C64 = r64 + tot.r, *D64 = C64 + tot.C,
+         *CN64 = D64 + tot.D, *lo64 = CN64 + tot.CN, *hi64 = lo64 + tot.lohi, *x064 = hi64 + tot.lohi;
+  auto cp = [&](double* dst, const double* src, size_t n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    if (!src) return cudaMemsetAsync(dst, 0, n * sizeof(double), h->stream);
+    return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  };
+  CU(cp(A64, A, tot.A)); CU(cp(B64, B, tot.B)); CU(cp(b64, c, tot.c)); CU(cp(Q64, Q, tot.Q)); CU(cp(R64, R, tot.R));
+  CU(cp(S64, S, tot.S)); CU(cp(q64, q, tot.q)); CU(cp(r64, r, tot.r)); CU(cp(C64, C, tot.C)); CU(cp(D64, D, tot.D));
+  CU(cp(CN64, CN, tot.CN)); CU(cp(lo64, lo, tot.lohi)); CU(cp(hi64, hi, tot.lohi));
+  CU(cudaMemsetAsync(x064, 0, tot.x0 * sizeof(double), h->stream));
+
+  std::vector<PackJob> jobs;
+  char* tp = (char*)h->tpool;
+  h->tx0.resize(batch);
+  for (int b = 0; b < batch; ++b) {
+    const qp_dims& d = dims[b];
+    const Sizes& z = sz[b];
+    QPDesc& D_ = h->hdesc[b];
+    const QPOffsets& po = h->off[b];
+    char* p = tp + toff[b] * esz;
+    auto take = [&](size_t n) { void* r_ = p; p += n * esz; return r_; };
+    D_.A = take(z.A); D_.B = take(z.B); D_.b = take(z.b); D_.Q = take(z.Q); D_.R = take(z.R); D_.S = take(z.S);
+    D_.q = take(z.q); D_.r = take(z.r); D_.C = take(z.C); D_.D = take(z.D); D_.CN = take(z.CN); D_.lo = take(z.lo);
+    D_.hi = take(z.hi); D_.x0 = take(z.x0); D_.Rhi = take(z.Rhi); D_.Sh = take(z.Sh); D_.VP = take(z.V);
+    D_.VA = take(z.V); D_.VC = take(z.V); D_.IP = take(z.V); D_.scr = take(z.scr); D_.Abar = take(z.Abar);
+    D_.CK = take(z.CK); D_.F = take(z.F); D_.FPi = take(z.FPi); D_.J = take(z.J); D_.K = take(z.K);
+    D_.KSig = take(z.KSig); D_.CKSig = take(z.CKSig); D_.Sig = take(z.Sig); D_.c0 = take(z.c0); D_.k0 = take(z.k0);
+    D_.CNSig = take(z.CNSig); D_.SigN = take(z.SigN); D_.Tch = take(z.Tch); D_.Uch = take(z.Uch);
+    D_.Theta = take(z.Theta); D_.Xi = take(z.Xi); D_.Gam = take(z.Gam); D_.z = take(z.z); D_.y = take(z.y);
+    h->tx0[b] = D_.x0;
+    D_.A64 = A64 + po.A; D_.B64 = B64 + po.B; D_.b64 = b64 + po.c; D_.Q64 = Q64 + po.Q; D_.R64 = R64 + po.R;
+    D_.S64 = S64 + po.S; D_.q64 = q64 + po.q; D_.r64 = r64 + po.r; D_.C64 = C64 + po.C; D_.D64 = D64 + po.D;
+    D_.CN64 = CN64 + po.CN; D_.lo64 = lo64 + po.lohi; D_.hi64 = hi64 + po.lohi; D_.x064 = x064 + po.x0;
+    double* dp = h->dpool + doff[b];
+    D_.kg = dp;
+    D_.kh = dp + al64((size_t)(d.N + 1) * d.nx);
+    D_.rho = D_.kh + al64((size_t)d.N * d.nu);
+    D_.flags = reinterpret_cast<int*>(D_.rho + 8);
+    D_.info_i = h->info_i + 4 * b;
+    D_.info_d = h->info_d + 4 * b;
+    const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf, m = N * nc + nf;
+    const int ldx = D_.ldx, ldu = D_.ldu;
+    jobs.push_back({A + po.A, D_.A, N, nx, nx, ldx});
+    jobs.push_back({B + po.B, D_.B, N, nx, nu, ldu});
+    jobs.push_back({c + po.c, D_.b, N, 1, nx, ldx});
+    jobs.push_back({Q + po.Q, D_.Q, N + 1, nx, nx, ldx});
+    jobs.push_back({R + po.R, D_.R, N, nu, nu, ldu});
+    jobs.push_back({S ? S + po.S : nullptr, D_.S, N, nu, nx, ldx});
+    jobs.push_back({q + po.q, D_.q, N + 1, 1, nx, ldx});
+    jobs.push_back({r + po.r, D_.r, N, 1, nu, ldu});
+    if (nc) {
+      jobs.push_back({C + po.C, D_.C, N, nc, nx, ldx});
+      jobs.push_back({D + po.D, D_.D, N, nc, nu, ldu});
+    }
+    if (nf) jobs.push_back({CN + po.CN, D_.CN, 1, nf, nx, ldx});
+    if (m) {
+      jobs.push_back({lo + po.lohi, D_.lo, 1, 1, m, m});
+      jobs.push_back({hi + po.lohi, D_.hi, 1, 1, m, m});
+      jobs.push_back({nullptr, D_.z, 1, 1, m, m});
+      jobs.push_back({nullptr, D_.y, 1, 1, m, m});
+    }
+  }
+  int st = run_pack(h, jobs);
+  if (st) { qp_destroy(h); return st; }
+  // rho and flags
+  for (int b = 0; b < batch; ++b) {
+    double rv[8] = {0};
+    rv[0] = (rho && rho[b] > 0) ? rho[b] : s->rho0;
+    int fl[2] = {0, 0};
+    CU(cudaMemcpyAsync(h->hdesc[b].rho, rv, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->hdesc[b].flags, fl, sizeof(fl), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  CU(cudaMemcpyAsync(h->ddesc, h->hdesc.data(), batch * sizeof(QPDesc), cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  *out = h;
+  return GPUSLS_OK;
+}
+
+extern "C" int qp_setup(qp_handle** h, qp_dims d, const double* A, const double* B, const double* c, const double* Q,
+                        const double* R, const double* S, const double* q, const double* r, const double* C,
+                        const double* D, const double* CN, const double* lo, const double* hi, double rho,
+                        const qp_settings* s, void* stream) {
+  qp_settings def;
+  if (!s) {
+    qp_default_settings(&def);
+    s = &def;
+  }
+  double rv = rho;
+  return qp_batch_setup(h, 1, &d, A, B, c, Q, R, S, q, r, C, D, CN, lo, hi, rho > 0 ? &rv : nullptr, s, stream);
+}
+
+// Set the output pointers (caller pools) of every descriptor and upload.
+static int set_outputs(qp_handle* h, double* ox, double* ou, double* olam, size_t stride_x, size_t stride_u,
+                       bool riccati) {
+  for (int b = 0; b < h->batch; ++b) {
+    const QPOffsets& po = h->off[b];
+    h->hdesc[b].ox = ox ? ox + (riccati ? po.P : po.dx) : nullptr;
+    h->hdesc[b].ou = ou ? ou + (riccati ? po.K : po.du) : nullptr;
+    h->hdesc[b].olam = olam ? olam + po.lohi : nullptr;
+  }
+  (void)stride_x;
+  (void)stride_u;
+  CU(cudaMemcpyAsync(h->ddesc, h->hdesc.data(), h->batch * sizeof(QPDesc), cudaMemcpyHostToDevice, h->stream));
+  return GPUSLS_OK;
+}
+
+static int set_x0(qp_handle* h, const double* x0) {
+  std::vector<PackJob> jobs;
+  size_t tot = 0;
+  for (int b = 0; b < h->batch; ++b) {
+    jobs.push_back({x0 + h->off[b].x0, h->tx0[b], 1, 1, h->dims[b].nx, h->hdesc[b].ldx});
+    tot += h->dims[b].nx;
+  }
+  // FP64 copy (pool layout matches the caller's x0 pool)
+  CU(cudaMemcpyAsync(h->hdesc[0].x064, x0, tot * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  return run_pack(h, jobs);
+}
+
+static int collect(qp_handle* h, qp_info* info) {
+  std::vector<int> ii(h->batch * 4);
+  std::vector<double> dd(h->batch * 4);
+  CU(cudaMemcpyAsync(ii.data(), h->info_i, ii.size() * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(dd.data(), h->info_d, dd.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  int worst = GPUSLS_OK;
+  for (int b = 0; b < h->batch; ++b) {
+    const int st = ii[4 * b];
+    if (info) {
+      info[b].status = st;
+      info[b].iters = ii[4 * b + 1];
+      info[b].refactors = ii[4 * b + 2];
+      info[b].pad = 0;
+      info[b].rho = dd[4 * b];
+      info[b].r_prim = dd[4 * b + 1];
+      info[b].r_dual = dd[4 * b + 2];
+      info[b].kkt = dd[4 * b + 3];
+    }
+    if (st < 0 && (worst >= 0 || st < worst)) worst = st;
+    else if (st == GPUSLS_MAX_ITER && worst == GPUSLS_OK) worst = GPUSLS_MAX_ITER;
+  }
+  return worst;
+}
+
+extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double tol, double* dx, double* du,
+                        double* lam, qp_info* info) {
+  if (!h || !x0 || !dx || !du || !lam) return fail(GPUSLS_ERR_INVALID, "qp_solve: null argument");
+  int st = set_x0(h, x0);
+  if (st) return st;
+  st = set_outputs(h, dx, du, lam, 0, 0, false);
+  if (st) return st;
+  SolveArgs a = {};
+  a.mode = MODE_SOLVE;
+  a.max_iter = iters > 0 ? iters : h->set.max_iter;
+  a.fixed_iters = h->set.fixed_iters;
+  a.sigma = h->set.sigma;
+  a.check_every = h->set.check_every;
+  a.cs = h->cs;
+  a.eps = tol > 0 ? tol : h->set.eps;
+  a.eps_kkt = h->set.eps_kkt > 0 ? (tol > 0 ? tol : h->set.eps_kkt) : -1.0;
+  a.rho_min = h->set.rho_min;
+  a.rho_max = h->set.rho_max;
+  st = launch(h, a);
+  if (st) return st;
+  return collect(h, info);
+}
+
+extern "C" int qp_riccati(qp_handle* h, double* P, double* K) {
+  if (!h || !P || !K) return fail(GPUSLS_ERR_INVALID, "qp_riccati: null argument");
+  int st = set_outputs(h, P, K, nullptr, 0, 0, true);
+  if (st) return st;
+  SolveArgs a = {};
+  a.mode = MODE_RICCATI;
+  a.cs = h->cs;
+  st = launch(h, a);
+  if (st) return st;
+  return collect(h, nullptr);
+}
+
+extern "C" int qp_kkt(qp_handle* h, const double* x0, const double* dx, const double* du, const double* lam,
+                      double* out) {
+  if (!h || !x0 || !dx || !du || !lam || !out) return fail(GPUSLS_ERR_INVALID, "qp_kkt: null argument");
+  int st = set_x0(h, x0);
+  if (st) return st;
+  st = set_outputs(h, const_cast<double*>(dx), const_cast<double*>(du), const_cast<double*>(lam), 0, 0, false);
+  if (st) return st;
+  SolveArgs a = {};
+  a.mode = MODE_KKT;
+  a.cs = h->cs;
+  st = launch(h, a);
+  if (st) return st;
+  std::vector<qp_info> inf(h->batch);
+  collect(h, inf.data());
+  for (int b = 0; b < h->batch; ++b) out[b] = inf[b].kkt;
+  return GPUSLS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state access
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void state_io_kernel(const QPDesc* __restrict__ descs, const double* z, const double* y, double* zo,
+                                double* yo, const size_t* offs, int set) {
+  const QPDesc d = descs[blockIdx.x];
+  const size_t o = offs[blockIdx.x];
+  T* zz = reinterpret_cast<T*>(d.z);
+  T* yy = reinterpret_cast<T*>(d.y);
+  for (int e = threadIdx.x; e < d.m; e += blockDim.x) {
+    if (set) {
+      zz[e] = z ? (T)z[o + e] : T(0);
+      yy[e] = y ? (T)y[o + e] : T(0);
+    } else {
+      if (zo) zo[o + e] = (double)zz[e];
+      if (yo) yo[o + e] = (double)yy[e];
+    }
+  }
+}
+
+static int state_io(qp_handle* h, const double* z, const double* y, double* zo, double* yo, int set) {
+  std::vector<size_t> offs(h->batch);
+  for (int b = 0; b < h->batch; ++b) offs[b] = h->off[b].lohi;
+  size_t* doffs = nullptr;
+  CU(cudaMalloc(&doffs, offs.size() * sizeof(size_t)));
+  CU(cudaMemcpyAsync(doffs, offs.data(), offs.size() * sizeof(size_t), cudaMemcpyHostToDevice, h->stream));
+  if (h->esz == 8) state_io_kernel<double><<<h->batch, 256, 0, h->stream>>>(h->ddesc, z, y, zo, yo, doffs, set);
+  else state_io_kernel<float><<<h->batch, 256, 0, h->stream>>>(h->ddesc, z, y, zo, yo, doffs, set);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(h->stream));
+  cudaFree(doffs);
+  return GPUSLS_OK;
+}
+
+extern "C" int qp_set_warm_start(qp_handle* h, const double* z, const double* y, const double* rho) {
+  if (!h) return fail(GPUSLS_ERR_INVALID, "qp_set_warm_start: null handle");
+  int st = state_io(h, z, y, nullptr, nullptr, 1);
+  if (st) return st;
+  if (rho) {
+    for (int b = 0; b < h->batch; ++b) {
+      if (!(rho[b] > 0)) return fail(GPUSLS_ERR_INVALID, "qp_set_warm_start: rho must be > 0");
+      double old = 0;
+      CU(cudaMemcpyAsync(&old, h->hdesc[b].rho, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      if (old != rho[b]) {
+        int fl[2] = {0, 0};
+        CU(cudaMemcpyAsync(h->hdesc[b].rho, &rho[b], sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemcpyAsync(h->hdesc[b].flags, fl, sizeof(fl), cudaMemcpyHostToDevice, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+      }
+    }
+  }
+  return GPUSLS_OK;
+}
+
+extern "C" int qp_get_state(qp_handle* h, double* z, double* y, double* rho) {
+  if (!h) return fail(GPUSLS_ERR_INVALID, "qp_get_state: null handle");
+  int st = state_io(h, nullptr, nullptr, z, y, 0);
+  if (st) return st;
+  if (rho) {
+    for (int b = 0; b < h->batch; ++b)
+      CU(cudaMemcpyAsync(&rho[b], h->hdesc[b].rho, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return GPUSLS_OK;
+}
+
+extern "C" int qp_update(qp_handle* h, const double* q, const double* r, const double* lo, const double* hi) {
+  if (!h) return fail(GPUSLS_ERR_INVALID, "qp_update: null handle");
+  std::vector<PackJob> jobs;
+  for (int b = 0; b < h->batch; ++b) {
+    const qp_dims& d = h->dims[b];
+    const QPDesc& D_ = h->hdesc[b];
+    const QPOffsets& po = h->off[b];
+    const int m = d.N * d.nc + d.nf;
+    if (q) jobs.push_back({q + po.q, D_.q, d.N + 1, 1, d.nx, D_.ldx});
+    if (r) jobs.push_back({r + po.r, D_.r, d.N, 1, d.nu, D_.ldu});
+    if (lo && m) jobs.push_back({lo + po.lohi, D_.lo, 1, 1, m, m});
+    if (hi && m) jobs.push_back({hi + po.lohi, D_.hi, 1, 1, m, m});
+    size_t nq = (size_t)(d.N + 1) * d.nx, nr = (size_t)d.N * d.nu;
+    if (q) CU(cudaMemcpyAsync(D_.q64, q + po.q, nq * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (r) CU(cudaMemcpyAsync(D_.r64, r + po.r, nr * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (lo && m) CU(cudaMemcpyAsync(D_.lo64, lo + po.lohi, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (hi && m) CU(cudaMemcpyAsync(D_.hi64, hi + po.lohi, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    int fl[2] = {0, 0};   // c0, k0 depend on q, r: refactor at the next solve
+    if (q || r) CU(cudaMemcpyAsync(D_.flags, fl, sizeof(fl), cudaMemcpyHostToDevice, h->stream));
+  }
+  int st = run_pack(h, jobs);
+  if (st) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+extern "C" void qp_destroy(qp_handle* h) {
+  if (!h) return;
+  if (h->tpool) cudaFree(h->tpool);
+  if (h->dpool) cudaFree(h->dpool);
+  if (h->ddesc) cudaFree(h->ddesc);
+  if (h->info_i) cudaFree(h->info_i);
+  if (h->info_d) cudaFree(h->info_d);
+  if (h->djobs) cudaFree(h->djobs);
+  delete h;
+}

@@ -1,0 +1,432 @@
+// Persistent ADMM solve kernel for the LTV-QP (Sec. IV-A), one thread-block
+// cluster per QP.
+//
+// Layout of the work inside a cluster of `cs` CTAs:
+//   * the stages 0..N-1 are split into nch <= cs contiguous chunks; CTA r owns
+//     chunk [s_r, e_r) (and the terminal time point N if it owns the last chunk);
+//   * the rho-dependent factorization (eq. augmented_matrices, eq. assoc_init,
+//     the reverse scan of eq. combination_rules, eq. controller_cache) runs as
+//     the paper's tree: an up-sweep of full combines and a down-sweep of
+//     combines whose right operand is a complete suffix, level by level, with
+//     the combines of a level spread over the cluster's CTAs;
+//   * once the Riccati terms P_i are cached, one ADMM iteration is two affine
+//     recursions with fixed matrices (backward p_i = Abar_i^T p_{i+1} + c_i,
+//     forward x_{i+1} = Abar_i x_i + d_i).  Each is scanned in three phases:
+//     a chunk-local chain with zero boundary, a chunk-boundary correction with
+//     cached products of the chunk transfer matrices read through distributed
+//     shared memory, and a fix-up folded into cached per-stage products.
+#pragma once
+#include <cooperative_groups.h>
+#include <math.h>
+#include "dense.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gsls {
+
+constexpr int MAXCS = 8;
+
+// Per-QP descriptor: dimensions and device pointers into the handle's pools.
+// Pointers typed void* are in the solve precision T (padded layouts, leading
+// dims ldx / ldu / ldc); double* pointers are FP64 copies of the caller's
+// dense arrays (for the KKT check) or FP64 outputs.
+struct QPDesc {
+  int nx, nu, N, nc, nf, m;
+  int ldx, ldu, ldc;
+  int nch, Lc;      // number of non-empty chunks, chunk length
+  int nlev;         // tree levels above the leaves
+  int pad0;
+  // problem (T)
+  void *A, *B, *b, *Q, *R, *S, *q, *r, *C, *D, *CN, *lo, *hi, *x0;
+  // factorization workspace (T)
+  void *Rhi, *Sh, *VP, *VA, *VC, *IP, *scr;
+  // cached iteration operators (T)
+  void *Abar, *CK, *F, *FPi, *J, *K, *KSig, *CKSig, *Sig, *c0, *k0, *CNSig, *SigN, *Tch, *Uch,
+      *Theta, *Xi, *Gam;
+  // ADMM state (T)
+  void *z, *y;
+  // FP64 copies (dense, caller layout) and scratch
+  double *A64, *B64, *b64, *Q64, *R64, *S64, *q64, *r64, *C64, *D64, *CN64, *lo64, *hi64, *x064;
+  double *kg, *kh;
+  double* rho;      // [1]
+  int* flags;       // [0]: factorization valid for *rho
+  // outputs (set per call)
+  double *ox, *ou, *olam;
+  int* info_i;      // [4]: status, iters, refactors, -
+  double* info_d;   // [4]: rho, r_prim, r_dual, kkt
+};
+
+enum Mode { MODE_SOLVE = 0, MODE_RICCATI = 1, MODE_KKT = 2 };
+
+struct SolveArgs {
+  int mode;
+  int max_iter;
+  int fixed_iters;
+  int sigma;
+  int check_every;
+  int cs;
+  double eps, eps_kkt, rho_min, rho_max;
+};
+
+// Shared-memory carve-up (byte offsets, 16-byte aligned).
+struct SmemLayout {
+  int ring, gemm, gj, gjbuf;                 // union region
+  int z, y, w, c, l, k, d, x, u, pe, xs, slotL, slotX, tmp1, tmp2, tmp3, red;
+  int part, perm, flag;
+  int total;
+};
+
+__host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline SmemLayout smem_layout(int nx, int ldx, int ldu, int nc, int nf, int Lc, int esz) {
+  SmemLayout s;
+  int off = 0;
+  const int ring_b = 3 * nx * ldx * esz;
+  const int dense_b = (2 * KT * TILE + TILE * GJ_LD + 2 * TILE) * esz;
+  const int uni = ring_b > dense_b ? ring_b : dense_b;
+  s.ring = 0;
+  s.gemm = 0;
+  s.gj = 2 * KT * TILE * esz;
+  s.gjbuf = s.gj + TILE * GJ_LD * esz;
+  off = al16(uni);
+  const int rows = Lc * nc + nf;
+  s.z = off; off = al16(off + rows * esz);
+  s.y = off; off = al16(off + rows * esz);
+  s.w = off; off = al16(off + rows * esz);
+  s.c = off; off = al16(off + Lc * ldx * esz);
+  s.l = off; off = al16(off + (Lc + 1) * ldx * esz);
+  s.k = off; off = al16(off + Lc * ldu * esz);
+  s.d = off; off = al16(off + (Lc + 1) * ldx * esz);
+  s.x = off; off = al16(off + (Lc + 1) * ldx * esz);
+  s.u = off; off = al16(off + Lc * ldu * esz);
+  s.pe = off; off = al16(off + TILE * esz);
+  s.xs = off; off = al16(off + TILE * esz);
+  s.slotL = off; off = al16(off + TILE * esz);
+  s.slotX = off; off = al16(off + TILE * esz);
+  s.tmp1 = off; off = al16(off + TILE * esz);
+  s.tmp2 = off; off = al16(off + TILE * esz);
+  s.tmp3 = off; off = al16(off + TILE * esz);
+  s.red = off; off = al16(off + NT * esz);
+  s.part = off; off = al16(off + 16 * 8);
+  s.perm = off; off = al16(off + TILE * 4);
+  s.flag = off; off = al16(off + 16 * 4);
+  s.total = off;
+  return s;
+}
+
+template <typename T>
+struct Ctx {
+  QPDesc* d;
+  int rank, cs;
+  int s, e, L;
+  bool active, first, last;
+  T *gemm, *gj, *gjbuf, *ring;
+  T *zS, *yS, *wS, *cS, *lS, *kS, *dS, *xS, *uS, *pe, *xs, *slotL, *slotX, *tmp1, *tmp2, *tmp3, *red;
+  double* part;
+  int *perm, *flag;
+  T* scr;   // per-CTA global scratch: 6 matrices nx x ldx
+  int msz;  // nx * ldx
+};
+
+template <typename T> __device__ inline T* TP(void* p) { return reinterpret_cast<T*>(p); }
+
+__device__ inline int level_count(int n, int d) {  // n_d = ceil(n / 2^d)
+  return (n + (1 << d) - 1) >> d;
+}
+__device__ inline int node_index(int n, int d, int m) {
+  int off = 0;
+  for (int i = 0; i < d; ++i) off += level_count(n, i);
+  return off + m;
+}
+
+// ---------------------------------------------------------------------------
+// global-memory CTA matvecs (operators streamed from L2 / HBM)
+// ---------------------------------------------------------------------------
+// y[i] (+)= alpha * sum_j M[i][j] x[j], i < rows (warp per row).  x, y shared.
+template <typename T>
+__device__ void g_mv(const T* M, int ld, int rows, int cols, const T* x, T alpha, bool acc, T* y) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int i = w; i < rows; i += NT / 32) {
+    T s = T(0);
+    for (int j = l; j < cols; j += 32) s += M[(size_t)i * ld + j] * x[j];
+    s = warp_sum(s);
+    if (l == 0) y[i] = (acc ? y[i] : T(0)) + alpha * s;
+  }
+  __syncthreads();
+}
+// y[j] (+)= alpha * sum_i M[i][j] x[i], j < cols (thread per column).
+template <typename T>
+__device__ void g_mvT(const T* M, int ld, int rows, int cols, const T* x, T alpha, bool acc, T* y) {
+  for (int j = threadIdx.x; j < cols; j += NT) {
+    T s = T(0);
+    for (int i = 0; i < rows; ++i) s += M[(size_t)i * ld + j] * x[i];
+    y[j] = (acc ? y[j] : T(0)) + alpha * s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Combines of the reverse scan (eq. combination_rules).  Operands are tree
+// nodes (P~, A~, C~) in global memory.  With W = (I + C~_ik P~_kj)^{-1}:
+//   Ups P~_kj A~_ik = (P~_kj A~_ik)^T (W A~_ik)     (push-through identity)
+//   Psi = A~_kj W,  A~_ij = Psi A~_ik,  C~_ij = Psi C~_ik A~_kj^T + C~_kj.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ int combine_full(Ctx<T>& c, const T* lP, const T* lA, const T* lC, const T* rP, const T* rA,
+                            const T* rC, T* oP, T* oA, T* oC) {
+  const int n = c.d->nx, ld = c.d->ldx;
+  T* X = c.scr;
+  T* Psi = c.scr + c.msz;
+  T* V = c.scr + 2 * c.msz;
+  T* U = c.scr + 3 * c.msz;
+  cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm);
+  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, c.gjbuf, c.perm, c.flag);
+  cta_gemm<T>(n, n, n, T(1), c.gj, GJ_LD, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), rA, ld, false, c.gj, GJ_LD, false, T(0), nullptr, 0, false, Psi, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), Psi, ld, false, lA, ld, false, T(0), nullptr, 0, false, oA, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), Psi, ld, false, lC, ld, false, T(0), nullptr, 0, false, U, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), U, ld, false, rA, ld, true, T(1), rC, ld, false, oC, ld, c.gemm);
+  return bad;
+}
+
+// Right operand is a complete suffix (A~ = C~ = 0, only P): P_out = (P A~)^T W A~ + P~.
+template <typename T>
+__device__ __noinline__ int combine_complete(Ctx<T>& c, const T* lP, const T* lA, const T* lC, const T* rP, T* oP) {
+  const int n = c.d->nx, ld = c.d->ldx;
+  T* X = c.scr;
+  T* V = c.scr + 2 * c.msz;
+  cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm);
+  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, c.gjbuf, c.perm, c.flag);
+  cta_gemm<T>(n, n, n, T(1), c.gj, GJ_LD, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm);
+  return bad;
+}
+
+// Reduce an int flag (or) across the cluster through the part[] slots.
+template <typename T>
+__device__ int cluster_or(Ctx<T>& c, cg::cluster_group& cl, int v) {
+  if (threadIdx.x == 0) c.part[15] = (double)v;
+  cl.sync();
+  int r = 0;
+  for (int k = 0; k < c.cs; ++k) {
+    double* p = cl.map_shared_rank(c.part, k);
+    r |= (int)p[15];
+  }
+  cl.sync();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// rho-dependent factorization (the "refactor")
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
+  QPDesc& d = *c.d;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, N = d.N;
+  const int ldx = d.ldx, ldu = d.ldu, ldc = d.ldc;
+  const int msz = c.msz;
+  const T *A = TP<T>(d.A), *B = TP<T>(d.B), *bb = TP<T>(d.b), *Q = TP<T>(d.Q), *R = TP<T>(d.R), *S = TP<T>(d.S);
+  const T *q = TP<T>(d.q), *r = TP<T>(d.r), *C = TP<T>(d.C), *D = TP<T>(d.D), *CN = TP<T>(d.CN);
+  T *Rhi = TP<T>(d.Rhi), *Sh = TP<T>(d.Sh), *VP = TP<T>(d.VP), *VA = TP<T>(d.VA), *VC = TP<T>(d.VC), *IP = TP<T>(d.IP);
+  T *Abar = TP<T>(d.Abar), *CK = TP<T>(d.CK), *F = TP<T>(d.F), *FPi = TP<T>(d.FPi), *J = TP<T>(d.J), *K = TP<T>(d.K);
+  T *KSig = TP<T>(d.KSig), *CKSig = TP<T>(d.CKSig), *Sig = TP<T>(d.Sig), *c0 = TP<T>(d.c0), *k0 = TP<T>(d.k0);
+  T *CNSig = TP<T>(d.CNSig), *SigN = TP<T>(d.SigN), *Tch = TP<T>(d.Tch), *Uch = TP<T>(d.Uch);
+  T *Theta = TP<T>(d.Theta), *Xi = TP<T>(d.Xi), *Gam = TP<T>(d.Gam);
+  T* s0 = c.scr + 4 * msz;   // small temporaries (nu x nx etc.)
+  T* s1 = c.scr + 5 * msz;
+  int bad = 0;
+  const int n = N + 1;
+
+  // R1: leaves (eq. assoc_init) for own stages, terminal by the last chunk.
+  if (c.active) {
+    for (int i = c.s; i < c.e; ++i) {
+      const T* Ai = A + (size_t)i * msz;
+      const T* Bi = B + (size_t)i * nx * ldu;
+      const T* Ci = C + (size_t)i * nc * ldx;
+      const T* Di = D + (size_t)i * nc * ldu;
+      T* Pl = VP + (size_t)i * msz;
+      T* Al = VA + (size_t)i * msz;
+      T* Cl = VC + (size_t)i * msz;
+      T* Shi = Sh + (size_t)i * nu * ldx;
+      T* Rhii = Rhi + (size_t)i * nu * ldu;
+      // Q^ = Q + rho C^T C,  R^ = R + rho D^T D,  S^ = S + rho D^T C
+      cta_gemm<T>(nx, nx, nc, rho, Ci, ldx, true, Ci, ldx, false, T(1), Q + (size_t)i * msz, ldx, false, Pl, ldx, c.gemm);
+      cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm);
+      cta_gemm<T>(nu, nx, nc, rho, Di, ldu, true, Ci, ldx, false, T(1), S + (size_t)i * nu * ldx, ldx, false, Shi, ldx, c.gemm);
+      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, c.gjbuf, c.perm, c.flag);
+      cta_copy<T>(nu, nu, c.gj, GJ_LD, false, Rhii, ldu);
+      // s0 = R^-1 S^ ; P~ = Q^ - S^^T s0 ; A~ = A - B s0 ; s1 = B R^-1 ; C~ = s1 B^T
+      cta_gemm<T>(nu, nx, nu, T(1), Rhii, ldu, false, Shi, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm);
+      cta_gemm<T>(nx, nx, nu, T(-1), Shi, ldx, true, s0, ldx, false, T(1), Pl, ldx, false, Pl, ldx, c.gemm);
+      cta_gemm<T>(nx, nx, nu, T(-1), Bi, ldu, false, s0, ldx, false, T(1), Ai, ldx, false, Al, ldx, c.gemm);
+      cta_gemm<T>(nx, nu, nu, T(1), Bi, ldu, false, Rhii, ldu, false, T(0), nullptr, 0, false, s1, ldu, c.gemm);
+      cta_gemm<T>(nx, nx, nu, T(1), s1, ldu, false, Bi, ldu, true, T(0), nullptr, 0, false, Cl, ldx, c.gemm);
+    }
+    if (c.last) {
+      T* Pl = VP + (size_t)N * msz;
+      cta_gemm<T>(nx, nx, nf, rho, CN, ldx, true, CN, ldx, false, T(1), Q + (size_t)N * msz, ldx, false, Pl, ldx, c.gemm);
+      cta_zero<T>(nx, nx, VA + (size_t)N * msz, ldx);
+      cta_zero<T>(nx, nx, VC + (size_t)N * msz, ldx);
+    }
+  }
+  cl.sync();
+
+  // R2: up-sweep.  Block (d, m) covers leaves [m 2^d, min((m+1) 2^d, n)); the
+  // last block of every level contains the terminal leaf and is complete.
+  for (int lv = 0; lv < d.nlev; ++lv) {
+    const int nd = level_count(n, lv), nd1 = level_count(n, lv + 1);
+    for (int m = c.rank; m < nd1; m += c.cs) {
+      const size_t li = (size_t)node_index(n, lv, 2 * m) * msz;
+      const size_t oi = (size_t)node_index(n, lv + 1, m) * msz;
+      if (2 * m + 1 >= nd) {
+        cta_copy<T>(nx, nx, VP + li, ldx, false, VP + oi, ldx);
+        cta_copy<T>(nx, nx, VA + li, ldx, false, VA + oi, ldx);
+        cta_copy<T>(nx, nx, VC + li, ldx, false, VC + oi, ldx);
+      } else {
+        const size_t ri = (size_t)node_index(n, lv, 2 * m + 1) * msz;
+        if (2 * m + 1 == nd - 1)
+          bad |= combine_complete<T>(c, VP + li, VA + li, VC + li, VP + ri, VP + oi);
+        else
+          bad |= combine_full<T>(c, VP + li, VA + li, VC + li, VP + ri, VA + ri, VC + ri, VP + oi, VA + oi, VC + oi);
+      }
+    }
+    cl.sync();
+  }
+  // R3: down-sweep of inclusive complete suffixes I(d, m) at block starts:
+  // left children inherit the parent's, right children combine their own
+  // block with the suffix after the parent block.
+  if (c.rank == 0) {
+    const size_t ri = (size_t)node_index(n, d.nlev, 0) * msz;
+    cta_copy<T>(nx, nx, VP + ri, ldx, false, IP + ri, ldx);
+  }
+  cl.sync();
+  for (int lv = d.nlev - 1; lv >= 0; --lv) {
+    const int nd = level_count(n, lv), nd1 = level_count(n, lv + 1);
+    for (int m = c.rank; m < nd; m += c.cs) {
+      const size_t oi = (size_t)node_index(n, lv, m) * msz;
+      const int p = m >> 1;
+      if ((m & 1) == 0) {
+        const size_t pi = (size_t)node_index(n, lv + 1, p) * msz;
+        cta_copy<T>(nx, nx, IP + pi, ldx, false, IP + oi, ldx);
+      } else if (p + 1 < nd1) {
+        const size_t si = (size_t)node_index(n, lv + 1, p + 1) * msz;
+        bad |= combine_complete<T>(c, VP + oi, VA + oi, VC + oi, IP + si, IP + oi);
+      } else {
+        cta_copy<T>(nx, nx, VP + oi, ldx, false, IP + oi, ldx);
+      }
+    }
+    cl.sync();
+  }
+  // R4: gains (eq. controller_cache) and the per-stage iteration operators.
+  if (c.active) {
+    for (int i = c.s; i < c.e; ++i) {
+      const T* Ai = A + (size_t)i * msz;
+      const T* Bi = B + (size_t)i * nx * ldu;
+      const T* Ci = C + (size_t)i * nc * ldx;
+      const T* Di = D + (size_t)i * nc * ldu;
+      const T* Pn = IP + (size_t)(i + 1) * msz;   // level-0 node i+1 = P_{i+1}
+      T* Gi = Gam + (size_t)i * nu * ldu;
+      T* Ki = K + (size_t)i * nu * ldx;
+      T* Abi = Abar + (size_t)i * msz;
+      // s0 = B^T P_{i+1} (nu x nx)
+      cta_gemm<T>(nu, nx, nx, T(1), Bi, ldu, true, Pn, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm);
+      // Gamma^-1 = R^ + s0 B  (R^ rebuilt)
+      cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm);
+      cta_gemm<T>(nu, nu, nx, T(1), s0, ldx, false, Bi, ldu, false, T(1), c.gj, GJ_LD, false, c.gj, GJ_LD, c.gemm);
+      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, c.gjbuf, c.perm, c.flag);
+      cta_copy<T>(nu, nu, c.gj, GJ_LD, false, Gi, ldu);
+      // s1 = S^ + s0 A ; K = -Gamma s1
+      cta_gemm<T>(nu, nx, nx, T(1), s0, ldx, false, Ai, ldx, false, T(1), Sh + (size_t)i * nu * ldx, ldx, false, s1, ldx, c.gemm);
+      cta_gemm<T>(nu, nx, nu, T(-1), Gi, ldu, false, s1, ldx, false, T(0), nullptr, 0, false, Ki, ldx, c.gemm);
+      // Abar = A + B K ; CK = C + D K ; F = -Gamma B^T ; J = -Gamma D^T
+      cta_gemm<T>(nx, nx, nu, T(1), Bi, ldu, false, Ki, ldx, false, T(1), Ai, ldx, false, Abi, ldx, c.gemm);
+      cta_gemm<T>(nc, nx, nu, T(1), Di, ldu, false, Ki, ldx, false, T(1), Ci, ldx, false, CK + (size_t)i * nc * ldx, ldx, c.gemm);
+      cta_gemm<T>(nu, nx, nu, T(-1), Gi, ldu, false, Bi, ldu, true, T(0), nullptr, 0, false, F + (size_t)i * nu * ldx, ldx, c.gemm);
+      cta_gemm<T>(nu, nc, nu, T(-1), Gi, ldu, false, Di, ldu, true, T(0), nullptr, 0, false, J + (size_t)i * nu * ldc, ldc, c.gemm);
+      // vectors: k0 = -Gamma (s0 b + r) ; c0 = Abar^T (P b) + q + K^T r
+      const T* bi = bb + (size_t)i * ldx;
+      for (int e2 = threadIdx.x; e2 < nx; e2 += NT) c.tmp3[e2] = bi[e2];
+      __syncthreads();
+      g_mv<T>(s0, ldx, nu, nx, c.tmp3, T(1), false, c.tmp1);          // tmp1 = s0 b
+      for (int a = threadIdx.x; a < nu; a += NT) c.tmp1[a] += r[(size_t)i * ldu + a];
+      __syncthreads();
+      g_mv<T>(Gi, ldu, nu, nu, c.tmp1, T(-1), false, c.tmp2);          // tmp2 = k0
+      for (int a = threadIdx.x; a < nu; a += NT) k0[(size_t)i * ldu + a] = c.tmp2[a];
+      g_mv<T>(Pn, ldx, nx, nx, c.tmp3, T(1), false, c.tmp1);          // tmp1 = P b
+      g_mvT<T>(Abi, ldx, nx, nx, c.tmp1, T(1), false, c.tmp2);        // tmp2 = Abar^T P b
+      for (int a = threadIdx.x; a < nu; a += NT) c.tmp1[a] = r[(size_t)i * ldu + a];
+      __syncthreads();
+      g_mvT<T>(Ki, ldx, nu, nx, c.tmp1, T(1), true, c.tmp2);          // += K^T r
+      for (int j = threadIdx.x; j < nx; j += NT) c0[(size_t)i * ldx + j] = c.tmp2[j] + q[(size_t)i * ldx + j];
+      __syncthreads();
+    }
+  }
+  cl.sync();
+  // R5: chunk products.  Backward (not needed in the last chunk):
+  //   FPi_i = F_i Pi_{i+1},  Pi_i = Abar_i^T Pi_{i+1},  Pi_e = I,  T_r = Pi_s.
+  // Forward (not needed in the first chunk):
+  //   Sig_s = I, Sig_{i+1} = Abar_i Sig_i, KSig_i = K_i Sig_i,
+  //   CKSig_i = CK_i Sig_i, U_r = Sig_e; the last chunk also C_N Sig_N.
+  if (c.active) {
+    if (!c.last) {
+      T* Pc = c.scr;
+      T* Pn2 = c.scr + c.msz;
+      const int i1 = c.e - 1;
+      cta_copy<T>(nu, nx, F + (size_t)i1 * nu * ldx, ldx, false, FPi + (size_t)i1 * nu * ldx, ldx);
+      cta_copy<T>(nx, nx, Abar + (size_t)i1 * msz, ldx, true, Pc, ldx);
+      for (int i = c.e - 2; i >= c.s; --i) {
+        cta_gemm<T>(nu, nx, nx, T(1), F + (size_t)i * nu * ldx, ldx, false, Pc, ldx, false, T(0), nullptr, 0, false,
+                    FPi + (size_t)i * nu * ldx, ldx, c.gemm);
+        cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)i * msz, ldx, true, Pc, ldx, false, T(0), nullptr, 0, false, Pn2,
+                    ldx, c.gemm);
+        T* t_ = Pc; Pc = Pn2; Pn2 = t_;
+      }
+      cta_copy<T>(nx, nx, Pc, ldx, false, Tch + (size_t)c.rank * msz, ldx);
+    }
+    if (!c.first) {
+      cta_eye<T>(nx, Sig + (size_t)c.s * msz, ldx);
+      cta_copy<T>(nu, nx, K + (size_t)c.s * nu * ldx, ldx, false, KSig + (size_t)c.s * nu * ldx, ldx);
+      cta_copy<T>(nc, nx, CK + (size_t)c.s * nc * ldx, ldx, false, CKSig + (size_t)c.s * nc * ldx, ldx);
+      for (int i = c.s + 1; i < c.e; ++i) {
+        T* Si = Sig + (size_t)i * msz;
+        cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)(i - 1) * msz, ldx, false, Sig + (size_t)(i - 1) * msz, ldx, false,
+                    T(0), nullptr, 0, false, Si, ldx, c.gemm);
+        cta_gemm<T>(nu, nx, nx, T(1), K + (size_t)i * nu * ldx, ldx, false, Si, ldx, false, T(0), nullptr, 0, false,
+                    KSig + (size_t)i * nu * ldx, ldx, c.gemm);
+        cta_gemm<T>(nc, nx, nx, T(1), CK + (size_t)i * nc * ldx, ldx, false, Si, ldx, false, T(0), nullptr, 0, false,
+                    CKSig + (size_t)i * nc * ldx, ldx, c.gemm);
+      }
+      T* Ur = Uch + (size_t)c.rank * msz;
+      cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)(c.e - 1) * msz, ldx, false, Sig + (size_t)(c.e - 1) * msz, ldx,
+                  false, T(0), nullptr, 0, false, Ur, ldx, c.gemm);
+      if (c.last) {
+        cta_copy<T>(nx, nx, Ur, ldx, false, SigN, ldx);
+        cta_gemm<T>(nf, nx, nx, T(1), CN, ldx, false, SigN, ldx, false, T(0), nullptr, 0, false, CNSig, ldx, c.gemm);
+      }
+    }
+  }
+  cl.sync();
+  // R6: chunk-boundary operators Theta_{r,m} = T_{r+1} ... T_{m-1} (m >= r+2)
+  // and Xi_{r,m} = U_{r-1} ... U_{m+1} (m <= r-2).
+  if (c.active) {
+    const int r0 = c.rank, nch = d.nch;
+    for (int m = r0 + 2; m < nch; ++m) {
+      T* Th = Theta + (size_t)(r0 * MAXCS + m) * msz;
+      if (m == r0 + 2) cta_copy<T>(nx, nx, Tch + (size_t)(r0 + 1) * msz, ldx, false, Th, ldx);
+      else cta_gemm<T>(nx, nx, nx, T(1), Theta + (size_t)(r0 * MAXCS + m - 1) * msz, ldx, false,
+                       Tch + (size_t)(m - 1) * msz, ldx, false, T(0), nullptr, 0, false, Th, ldx, c.gemm);
+    }
+    for (int m = r0 - 2; m >= 0; --m) {
+      T* X = Xi + (size_t)(r0 * MAXCS + m) * msz;
+      if (m == r0 - 2) cta_copy<T>(nx, nx, Uch + (size_t)(r0 - 1) * msz, ldx, false, X, ldx);
+      else cta_gemm<T>(nx, nx, nx, T(1), Xi + (size_t)(r0 * MAXCS + m + 1) * msz, ldx, false,
+                       Uch + (size_t)(m + 1) * msz, ldx, false, T(0), nullptr, 0, false, X, ldx, c.gemm);
+    }
+  }
+  return cluster_or<T>(c, cl, bad);
+}
+
+}  // namespace gsls

@@ -1,0 +1,201 @@
+"""GPU parity of the ADMM QP path against the FP64 oracle (calls through the
+C ABI).  Tolerances: 1e-6 relative in FP64, 1e-4 relative in FP32 (relative
+to max(1, max |reference|))."""
+import numpy as np
+import pytest
+
+from oracle import activeset, admm, kkt, lq
+from paper_2604_07644_b300 import native
+from paper_2604_07644_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {native.GPUSLS_FP64: 1e-6, native.GPUSLS_FP32: 1e-4}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=float)
+    b = np.asarray(b, dtype=float)
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b))))) if b.size else 0.0
+
+
+def batch(qps, **kw):
+    from paper_2604_07644_b300.api import QPBatch
+    rho = kw.pop("rho", None)
+    return QPBatch(qps, native.default_settings(**kw), rho=rho)
+
+
+CASES = [
+    ("tiny", lambda: W.tiny(0)),
+    ("general-3-2-5", lambda: W.random_general(0, 3, 2, 5, 3, 2)),
+    ("general-7-3-23", lambda: W.random_general(1, 7, 3, 23, 5, 0)),
+    ("general-12-4-37-nc0", lambda: W.random_general(2, 12, 4, 37, 0, 3)),
+    ("plain4d", lambda: W.plain_4d(0)),
+    ("quad12d-N64", lambda: W.quadrotor_12d(0)),
+]
+
+
+@pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32])
+@pytest.mark.parametrize("cluster", [1, 3, 8])
+@pytest.mark.parametrize("name,make", CASES)
+def test_riccati_matches_oracle(lib, name, make, cluster, prec):
+    """The tree-scan refactor (eq. assoc_init, eq. combination_rules,
+    eq. controller_cache) gives the sequential Riccati P_i and K_i."""
+    qp = make()
+    rho = 0.7
+    b = batch([qp], precision=prec, cluster=cluster, rho=rho)
+    Ps, Ks = b.riccati()
+    Qh, Rh, Sh = lq.augmented(qp, rho)
+    P, p, K, kff, G = lq.riccati(qp.A, qp.B, qp.c, Qh, Rh, Sh, np.zeros_like(qp.q), np.zeros_like(qp.r))
+    tol = TOL[prec] * (10 if prec == native.GPUSLS_FP32 else 1e-2)
+    assert rel(Ps[0], P) < tol, rel(Ps[0], P)
+    assert rel(Ks[0], K) < tol, rel(Ks[0], K)
+    b.close()
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 5, 8])
+@pytest.mark.parametrize("name,make", CASES)
+def test_fixed_iterations_match_oracle_fp64(lib, name, make, cluster):
+    """Iterate parity: 9 ADMM iterations at fixed rho from a cold start."""
+    qp = make()
+    b = batch([qp], precision=native.GPUSLS_FP64, cluster=cluster, sigma=0, fixed_iters=9, rho=0.3)
+    r = b.solve()
+    o = admm.admm(qp, admm.Settings(rho0=0.3, sigma=0), iters=9)
+    assert rel(r.dx[0], o.x) < 1e-9
+    assert rel(r.du[0], o.u) < 1e-9
+    assert rel(r.lam[0], o.lam) < 1e-9
+    assert r.info[0]["iters"] == 9
+    b.close()
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_fixed_iterations_match_oracle_fp32(lib, name, make):
+    qp = make()
+    b = batch([qp], precision=native.GPUSLS_FP32, sigma=0, fixed_iters=9, rho=0.3)
+    r = b.solve()
+    o = admm.admm(qp, admm.Settings(rho0=0.3, sigma=0), iters=9)
+    assert rel(r.dx[0], o.x) < 1e-4
+    assert rel(r.du[0], o.u) < 1e-4
+    assert rel(r.lam[0], o.lam) < 1e-4
+    b.close()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_solution_matches_brute_force_tiny(lib, seed):
+    """Converged solution equals the active-set brute-force optimum."""
+    qp = W.tiny(seed)
+    xb, ub, lb, _ = activeset.brute_force(qp)
+    b = batch([qp], precision=native.GPUSLS_FP64, eps=1e-10, eps_kkt=1e-9, max_iter=100000)
+    r = b.solve()
+    assert r.info[0]["status"] == native.GPUSLS_OK
+    assert rel(r.dx[0], xb) < 1e-6 and rel(r.du[0], ub) < 1e-6
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32])
+@pytest.mark.parametrize("seed", range(3))
+def test_adaptive_solve_plain4d(lib, seed, prec):
+    """Adaptive-rho solve to the 1e-4 KKT tolerance: the returned point passes
+    the oracle's own KKT check, satisfies every bound, and matches the exact
+    optimum."""
+    qp = W.plain_4d(seed)
+    b = batch([qp], precision=prec)
+    r = b.solve()
+    assert r.info[0]["status"] == native.GPUSLS_OK
+    k_or = kkt.kkt_residual(qp, r.dx[0], r.du[0], r.lam[0])
+    assert k_or <= 1e-4 * (1.5 if prec else 1.0001)
+    v = lq.G_apply(qp, r.dx[0], r.du[0])
+    assert np.all(v <= qp.hi + 1e-4) and np.all(v >= qp.lo - 1e-4)
+    assert abs(r.info[0]["kkt"] - k_or) <= 1e-6 + 1e-3 * k_or
+    o = admm.admm(qp, admm.Settings(eps=1e-4, eps_kkt=1e-4))
+    if prec == native.GPUSLS_FP64:
+        assert r.info[0]["iters"] == o.iters
+        assert rel(r.dx[0], o.x) < 1e-6
+    b.close()
+
+
+def test_kkt_entry_point_matches_oracle(lib):
+    qp = W.tiny(2)
+    xb, ub, lb, _ = activeset.brute_force(qp)
+    g = np.random.default_rng(0)
+    b = batch([qp])
+    for pert in [0.0, 1e-3]:
+        x = xb + pert * g.standard_normal(xb.shape)
+        u = ub + pert * g.standard_normal(ub.shape)
+        l = lb + pert * g.standard_normal(lb.shape)
+        got = b.kkt([x], [u], [l])[0]
+        assert abs(got - kkt.kkt_residual(qp, x, u, l)) < 1e-12 + 1e-9 * abs(got)
+    b.close()
+
+
+def test_batch_equals_single(lib):
+    """A ragged batch gives, QP by QP, the single-instance results."""
+    qps = [W.random_general(5, 3, 2, 11, 2, 1), W.plain_4d(1), W.random_general(6, 9, 4, 30, 6, 2),
+           W.quadrotor_12d(1, N=20)]
+    bb = batch(qps, precision=native.GPUSLS_FP64, sigma=0, fixed_iters=12, rho=0.5, cluster=4)
+    rb = bb.solve()
+    for i, qp in enumerate(qps):
+        bs = batch([qp], precision=native.GPUSLS_FP64, sigma=0, fixed_iters=12, rho=0.5, cluster=4)
+        rs = bs.solve()
+        assert rel(rb.dx[i], rs.dx[0]) < 1e-12
+        assert rel(rb.lam[i], rs.lam[0]) < 1e-12
+        bs.close()
+    bb.close()
+
+
+def test_warm_start_state_roundtrip_and_resume(lib):
+    """qp_get_state / qp_set_warm_start: resuming from a saved state equals
+    running the iterations in one go (checkpoint / resume of the ADMM state)."""
+    qp = W.plain_4d(2)
+    b1 = batch([qp], sigma=0, fixed_iters=10, rho=0.4)
+    r1 = b1.solve()
+    z, y, rho = b1.get_state()
+    r1b = b1.solve()                     # 10 more
+    b2 = batch([qp], sigma=0, fixed_iters=10, rho=0.4)
+    b2.set_warm_start(z, y, rho)
+    r2 = b2.solve()
+    assert rel(r2.dx[0], r1b.dx[0]) < 1e-12 and rel(r2.lam[0], r1b.lam[0]) < 1e-12
+    o = admm.admm(qp, admm.Settings(rho0=0.4, sigma=0), iters=20)
+    assert rel(r2.dx[0], o.x) < 1e-9
+    b1.close()
+    b2.close()
+
+
+def test_unconstrained_rows_give_lqr(lib):
+    """Loose bounds: the solution is the LQR optimum and lambda = 0."""
+    qp = W.random_general(3, 5, 2, 17, 4, 2)
+    x, u = lq.lq_solve(qp, qp.Q, qp.R, qp.S, qp.q, qp.r, qp.x0)
+    v = lq.G_apply(qp, x, u)
+    qp.hi = np.maximum(qp.hi, v + 1.0)
+    qp.lo = np.minimum(qp.lo, v - 1.0)
+    b = batch([qp], eps=1e-10, eps_kkt=1e-9)
+    r = b.solve()
+    assert rel(r.dx[0], x) < 1e-7 and rel(r.du[0], u) < 1e-7
+    assert np.max(np.abs(r.lam[0])) < 1e-7
+    b.close()
+
+
+def test_quadruped_61d_full_size(lib):
+    """Full-size 61D / N=100 QP: iterate parity for 6 fixed iterations in FP64,
+    and the adaptive FP32 solve reaches the 1e-4 KKT tolerance by the oracle's
+    own KKT measure with every constraint satisfied."""
+    qp = W.quadruped_61d(0)
+    b = batch([qp], precision=native.GPUSLS_FP64, sigma=0, fixed_iters=6, rho=0.1)
+    r = b.solve()
+    o = admm.admm(qp, admm.Settings(rho0=0.1, sigma=0), iters=6)
+    assert rel(r.dx[0], o.x) < 1e-6 and rel(r.lam[0], o.lam) < 1e-6
+    b.close()
+    b = batch([qp], precision=native.GPUSLS_FP32)
+    r = b.solve()
+    assert r.info[0]["status"] == native.GPUSLS_OK
+    assert kkt.kkt_residual(qp, r.dx[0], r.du[0], r.lam[0]) <= 1.5e-4
+    v = lq.G_apply(qp, r.dx[0], r.du[0])
+    assert np.all(v <= qp.hi + 1e-4) and np.all(v >= qp.lo - 1e-4)
+    b.close()
+
+
+def test_invalid_dims_rejected(lib):
+    qp = W.random_general(0, 3, 2, 5, 2, 1)
+    qp.A = np.zeros((5, 81, 81))
+    with pytest.raises(RuntimeError):
+        batch([qp])
