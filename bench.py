@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark: ms per QP solved to a 1e-4 FP64 KKT residual on quadruped-shaped
+(nx=61, nu=12, N=100) LTV-QPs -- the batched GPU solver next to the plain FP64
+single-QP GPU solve and the FP64 CPU oracle.
+
+One step = one cold solve (factorization + ADMM iterations + FP64 KKT gate)
+of every QP in the batch.  Problem data for the whole batch stays resident
+on the device (1.2 GB in FP64, larger than L2); `e2e` repeats the step through
+the public API with the problem data copied from pinned host memory and the
+solution copied back inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpusls|reference]
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ms/QP solve to 1e-4 KKT residual (61D, N=100): learned+batched vs plain ADMM"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6400.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpusls", choices=["gpusls", "reference"])
+    p.add_argument("--batch", type=int, default=148)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--cluster", type=int, default=8)
+    p.add_argument("--plain-qps", type=int, default=2)
+    p.add_argument("--cpu-sample", type=int, default=2)
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[2 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def algorithmic_bytes_per_iter(nx, nu, N, nc, esz):
+    """Operators one cached ADMM iteration must read once per QP (FP32 storage):
+    N (2 nx^2 + 3 nu nx + nu nc + 2 nc (nx + nu)) elements."""
+    return N * (2 * nx * nx + 3 * nu * nx + nu * nc + 2 * nc * (nx + nu)) * esz
+
+
+def cpu_oracle_ms_per_qp(qps, eps=1e-4):
+    """The FP64 oracle as it stands on this host (single thread)."""
+    from oracle import admm
+    t0 = time.perf_counter()
+    iters = []
+    for qp in qps:
+        r = admm.admm(qp, admm.Settings(eps=eps, eps_kkt=eps))
+        iters.append(r.iters)
+    dt = time.perf_counter() - t0
+    return dt * 1e3 / len(qps), iters
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the CPU oracle on the same workload, one QP per step."""
+    if rank != 0:
+        return
+    from paper_2604_07644_b300 import workloads as W
+    fam = W.family(0)
+    n = 0
+    for _ in range(args.warmup):
+        cpu_oracle_ms_per_qp([fam.instance(200000 + n)])
+        n += 1
+    t0 = time.perf_counter()
+    iters = []
+    for _ in range(args.steps):
+        _, it = cpu_oracle_ms_per_qp([fam.instance(200000 + n)])
+        iters += it
+        n += 1
+    dt = time.perf_counter() - t0
+    ms = dt * 1e3 / args.steps
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms/QP", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "quadruped-shaped LTV-QP family, nx=61 nu=12 N=100 nc=20 nf=8",
+                       "batch": 1, "precision": "fp64", "solver": "CPU oracle ADMM (sequential Riccati)"},
+            "cpu_baseline": {"value": ms, "unit": "ms/QP", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} QPs, one per step, single thread; iters {iters}"},
+            "e2e": {"value": ms, "unit": "ms/QP", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+
+    from paper_2604_07644_b300 import build as B_
+    from paper_2604_07644_b300 import native
+    from paper_2604_07644_b300 import workloads as W
+    from paper_2604_07644_b300.api import QPBatch, pool
+
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    torch.cuda.set_device(local)
+    B_.build()
+    native.load()
+    dev = f"cuda:{local}"
+    stream = torch.cuda.Stream(device=dev)
+    prec = native.GPUSLS_FP32 if args.precision == "fp32" else native.GPUSLS_FP64
+    esz = 4 if prec == native.GPUSLS_FP32 else 8
+    fam = W.family(0)
+    base = 100000 + rank * args.batch
+    qps = [fam.instance(base + i) for i in range(args.batch)]
+    nx, nu, N, nc, nf = qps[0].dims()
+    settings = native.default_settings(precision=prec, cluster=args.cluster,
+                                       eps_floor=1e-5 if prec == native.GPUSLS_FP32 else 1e-7)
+    with torch.cuda.stream(stream):
+        hb = QPBatch(qps, settings, stream=stream, device=dev)
+
+    def step():
+        hb.reset()
+        return hb.solve(fetch=False)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk, torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    t_ms = ev0.elapsed_time(ev1)
+    t_ms = max_over_ranks(ws, t_ms)
+    ms_per_step = t_ms / args.steps
+    value = t_ms / (args.steps * args.batch * ws)
+    # per-QP results: one more identical cold solve (untimed) to read them
+    info = (native.qp_info * args.batch)()
+    hb.reset()
+    st = hb.lib.qp_solve(hb.h, C_ptr(hb.x0), 0, 0.0, C_ptr(hb.out_x), C_ptr(hb.out_u), C_ptr(hb.out_l), info)
+    iters = [info[i].iters for i in range(args.batch)]
+    refs = [info[i].refactors for i in range(args.batch)]
+    kkts = [info[i].kkt for i in range(args.batch)]
+    stats = [info[i].status for i in range(args.batch)]
+
+    # plain FP64 single-QP solves (cold, one QP per launch)
+    plain = []
+    for i in range(args.plain_qps):
+        hp = QPBatch([qps[i]], native.default_settings(precision=native.GPUSLS_FP64, cluster=args.cluster),
+                     stream=stream, device=dev)
+        with torch.cuda.stream(stream):
+            hp.reset()
+            hp.solve(fetch=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            hp.reset()
+            e0.record(stream)
+            hp.solve(fetch=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        plain.append(e0.elapsed_time(e1))
+        hp.close()
+    plain_ms = float(np.mean(plain)) if plain else None
+
+    # end to end through the public API: H2D problem data from pinned memory,
+    # qp_update + cold solve, D2H of (dx, du, lam)
+    e2e = None
+    if not args.no_e2e:
+        keys = ("A", "B", "c", "Q", "R", "S", "q", "r", "C", "D", "CN", "lo", "hi")
+        host = {k: hb.pools[k].cpu().pin_memory() for k in keys}
+        host_x0 = hb.x0.cpu().pin_memory()
+        dev_pools = {k: torch.empty_like(hb.pools[k]) for k in keys}
+        out_host = [torch.empty_like(t, device="cpu").pin_memory() for t in (hb.out_x, hb.out_u, hb.out_l)]
+        h2d = sum(t.numel() * 8 for t in host.values()) + host_x0.numel() * 8
+        d2h = sum(t.numel() * 8 for t in out_host)
+
+        def e2e_step():
+            for k in keys:
+                dev_pools[k].copy_(host[k], non_blocking=True)
+            hb.x0.copy_(host_x0, non_blocking=True)
+            hb.update_pools(dev_pools)
+            hb.reset()
+            hb.solve(fetch=False)
+            for o, d in zip(out_host, (hb.out_x, hb.out_u, hb.out_l)):
+                o.copy_(d, non_blocking=True)
+
+        with torch.cuda.stream(stream):
+            e2e_step()
+            torch.cuda.synchronize()
+            barrier(ws)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                e2e_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        te = max_over_ranks(ws, e0.elapsed_time(e1))
+        e2e = {"value": te / (args.steps * args.batch * ws), "unit": "ms/QP", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    pk, pk_kind = peaks()
+    algo = algorithmic_bytes_per_iter(nx, nu, N, nc, esz) * float(np.sum(iters))
+    achieved = algo / (ms_per_step * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "kernel": "qp_kernel (persistent cluster solve)", "peak_kind": pk_kind,
+            "algorithmic_bytes_per_launch": algo}
+
+    cpu = None
+    if rank == 0 and args.cpu_sample > 0:
+        ms_cpu, it_cpu = cpu_oracle_ms_per_qp(qps[:args.cpu_sample])
+        cpu = {"value": ms_cpu, "unit": "ms/QP", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} QPs of this batch, FP64 oracle ADMM, single thread; iters {it_cpu}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "ms/QP", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if esz == 4 else "f64",
+                "data": "synthetic",
+                "config": {"workload": "quadruped-shaped LTV-QP family (nx=61 nu=12 N=100 nc=20 nf=8), "
+                                       "cold start", "batch": args.batch, "precision": args.precision,
+                           "cluster": args.cluster, "parallelism": f"replicas x{ws}",
+                           "l2": "inputs larger than L2 (FP64 pools 1.2 GB per 148 QPs)"},
+                "plain_fp64_ms_per_qp": plain_ms,
+                "iters_mean": float(np.mean(iters)), "refactors_mean": float(np.mean(refs)),
+                "kkt_max": float(np.max(kkts)), "all_converged": all(s == 0 for s in stats),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    hb.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def C_ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
+if __name__ == "__main__":
+    main()

@@ -64,6 +64,8 @@ typedef struct qp_settings {
   int32_t precision;  /* GPUSLS_FP64 or GPUSLS_FP32                                 */
   int32_t cluster;    /* CTAs (thread blocks) per QP, 1..8; 0 picks by N            */
   int32_t fixed_iters;/* > 0: run exactly this many iterations, no stop test        */
+  int32_t pad;
+  double eps_floor;   /* the KKT gate divides eps by 10 on failure, not below this  */
 } qp_settings;
 
 /* Per-QP result summary (host memory). */
@@ -80,7 +82,8 @@ typedef struct qp_info {
 typedef struct qp_handle qp_handle;
 
 /* Fills s with the defaults: rho0 0.1, eps 1e-4, eps_kkt 1e-4, rho range
- * [1e-6, 1e6], sigma 25, check_every 5, max_iter 4000, FP64, cluster 0. */
+ * [1e-6, 1e6], sigma 25, check_every 5, max_iter 4000, FP64, cluster 0,
+ * eps_floor 1e-7 (FP32 solves reach a KKT floor near 1e-4 on 61D problems: use 1e-5). */
 void qp_default_settings(qp_settings* s);
 
 /* Message of the last failing call on this thread ("" if none). */
@@ -136,9 +139,20 @@ int qp_set_warm_start(qp_handle* h, const double* z, const double* y, const doub
 /* qp_get_state: copy (z, y) pools and rho (HOST [batch]) out of the handle. */
 int qp_get_state(qp_handle* h, double* z, double* y, double* rho);
 
-/* qp_update: replace the linear terms and bounds (q, r, lo, hi; pools, same
- * dims; any may be NULL to keep) without touching the cached factorization. */
-int qp_update(qp_handle* h, const double* q, const double* r, const double* lo, const double* hi);
+/* qp_update: replace problem data of every QP in place (same dims; pools;
+ * any argument may be NULL to keep the current array) -- a new SQP
+ * linearization (A, B, c, Q, R, S, C, D, CN) and/or new linear terms and
+ * bounds (q, r, lo, hi).  Allocates nothing.  Any change other than lo/hi
+ * invalidates the cached factorization (the next solve refactors). */
+int qp_update(qp_handle* h, const double* A, const double* B, const double* c,
+              const double* Q, const double* R, const double* S,
+              const double* q, const double* r,
+              const double* C, const double* D, const double* CN,
+              const double* lo, const double* hi);
+
+/* qp_reset: cold start of every QP: z = y = 0, rho = the setup value, cached
+ * factorization invalidated. */
+int qp_reset(qp_handle* h);
 
 /* qp_kkt: FP64 KKT residual of a candidate point (dx, du, lam pools) for
  * every QP of the handle (reading of the paper's undefined "residual":

@@ -20,7 +20,8 @@ Readings (the paper is silent or garbled here):
     and the cost matrices are re-augmented (the "refactor").
   * "solve to a KKT tolerance": when the in-loop test passes, the FP64 KKT
     residual (oracle.kkt) is evaluated; if it exceeds eps_kkt the in-loop
-    tolerance is divided by 10 and iterations continue.
+    tolerance is divided by 10, but not below eps_floor, and iterations
+    continue (at the floor the KKT is re-evaluated at every passing test).
 """
 from __future__ import annotations
 
@@ -37,6 +38,7 @@ class Settings:
     rho0: float = 0.1
     eps: float = 1e-4
     eps_kkt: float | None = None   # None: stop on the in-loop test alone
+    eps_floor: float = 1e-7        # lowest in-loop tolerance the KKT gate tightens to
     sigma: int = 25                # 0: fixed rho
     check_every: int = 5
     max_iter: int = 4000
@@ -113,7 +115,7 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
             if kkt <= s.eps_kkt:
                 converged = True
                 break
-            eps = eps * 0.1
+            eps = max(eps * 0.1, s.eps_floor)
         if s.sigma and t % s.sigma == 0:
             rho_new = rho_rule(qp, x, u, v, z, y, rho, r_prim, r_dual, s)
             if rho_new > 5.0 * rho or rho_new < rho / 5.0:

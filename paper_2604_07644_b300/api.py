@@ -143,11 +143,23 @@ class QPBatch:
         return (self._split(tz, "m", [(qp.m,) for qp in self.qps]), self._split(ty, "m", [(qp.m,) for qp in self.qps]),
                 [rho[i] for i in range(self.B)])
 
-    def update(self, q=None, r=None, lo=None, hi=None):
-        t = {k: (pool(list(v), self.device) if v is not None else None) for k, v in
-             dict(q=q, r=r, lo=lo, hi=hi).items()}
-        native.check(self.lib.qp_update(self.h, _dptr(t["q"]), _dptr(t["r"]), _dptr(t["lo"]), _dptr(t["hi"])),
-                     "qp_update")
+    def update(self, **arrays):
+        """Replace problem arrays (keys A, B, c, Q, R, S, q, r, C, D, CN, lo, hi;
+        each a list with one array per QP)."""
+        keys = ("A", "B", "c", "Q", "R", "S", "q", "r", "C", "D", "CN", "lo", "hi")
+        unknown = set(arrays) - set(keys)
+        if unknown:
+            raise KeyError(sorted(unknown))
+        t = {k: (pool(list(arrays[k]), self.device) if arrays.get(k) is not None else None) for k in keys}
+        native.check(self.lib.qp_update(self.h, *[_dptr(t[k]) for k in keys]), "qp_update")
+
+    def update_pools(self, pools: dict):
+        """Same as update() with device pools already in the library's pool layout."""
+        keys = ("A", "B", "c", "Q", "R", "S", "q", "r", "C", "D", "CN", "lo", "hi")
+        native.check(self.lib.qp_update(self.h, *[_dptr(pools.get(k)) for k in keys]), "qp_update")
+
+    def reset(self):
+        native.check(self.lib.qp_reset(self.h), "qp_reset")
 
     def close(self):
         if getattr(self, "h", None) is not None:

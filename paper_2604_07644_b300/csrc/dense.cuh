@@ -10,7 +10,7 @@ namespace gsls {
 
 constexpr int NT = 256;     // threads per CTA
 constexpr int TILE = 80;    // max edge of a C tile (and of a GJ-inverted matrix)
-constexpr int KT = 16;      // k-slab staged per step of the CTA GEMM
+constexpr int KT = 64;      // k-slab staged per step of the CTA GEMM (whole k for k <= 64)
 constexpr int GJ_LD = TILE + 1;
 
 __host__ __device__ inline int rup4(int x) { return (x + 3) & ~3; }
@@ -20,7 +20,8 @@ template <typename T> __device__ inline T tiny_pivot();
 template <> __device__ inline double tiny_pivot<double>() { return 1e-280; }
 template <> __device__ inline float tiny_pivot<float>() { return 1e-30f; }
 
-// Shared-memory scratch needed by cta_gemm: 2*KT*TILE elements.
+// Shared-memory scratch needed by cta_gemm: 2*KT*TILE elements (op(A) and
+// op(B) k-slabs stored k-major).
 template <typename T> constexpr int gemm_smem_elems() { return 2 * KT * TILE; }
 
 // C = alpha * op(A) * op(B) + beta * C0 (+ I if addI), with op(A) m x k and
@@ -48,19 +49,21 @@ __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
       for (int k0 = 0; k0 < k; k0 += KT) {
         const int kt = min(KT, k - k0);
         __syncthreads();
-        for (int e = t; e < mt * KT; e += NT) {
-          int i, kk;
-          if (!tA) { i = e / KT; kk = e - i * KT; } else { kk = e / mt; i = e - kk * mt; }
-          T v = T(0);
-          if (kk < kt) v = tA ? A[(size_t)(k0 + kk) * lda + i0 + i] : A[(size_t)(i0 + i) * lda + k0 + kk];
-          As[kk * TILE + i] = v;
+        // one burst of independent loads per operand, 16 x 16 thread grid,
+        // coalesced along the contiguous index of each operand
+        if (!tA) {
+          for (int i = ty; i < mt; i += 16)
+            for (int kk = tx; kk < kt; kk += 16) As[kk * TILE + i] = A[(size_t)(i0 + i) * lda + k0 + kk];
+        } else {
+          for (int kk = ty; kk < kt; kk += 16)
+            for (int i = tx; i < mt; i += 16) As[kk * TILE + i] = A[(size_t)(k0 + kk) * lda + i0 + i];
         }
-        for (int e = t; e < nt * KT; e += NT) {
-          int j, kk;
-          if (!tB) { kk = e / nt; j = e - kk * nt; } else { j = e / KT; kk = e - j * KT; }
-          T v = T(0);
-          if (kk < kt) v = tB ? B[(size_t)(j0 + j) * ldb + k0 + kk] : B[(size_t)(k0 + kk) * ldb + j0 + j];
-          Bs[kk * TILE + j] = v;
+        if (!tB) {
+          for (int kk = ty; kk < kt; kk += 16)
+            for (int j = tx; j < nt; j += 16) Bs[kk * TILE + j] = B[(size_t)(k0 + kk) * ldb + j0 + j];
+        } else {
+          for (int j = ty; j < nt; j += 16)
+            for (int kk = tx; kk < kt; kk += 16) Bs[kk * TILE + j] = B[(size_t)(j0 + j) * ldb + k0 + kk];
         }
         __syncthreads();
         for (int kk = 0; kk < kt; ++kk) {
@@ -123,83 +126,114 @@ __device__ void cta_zero(int m, int n, T* Y, int ldy) {
   __syncthreads();
 }
 
-// In-place Gauss-Jordan inversion of the n x n matrix M (shared memory, leading
-// dimension ldm).  pivot = true: partial (row) pivoting, failure if a pivot is
-// below tiny_pivot.  pivot = false: no pivoting, failure if a pivot is not
-// positive (the test that the matrix is symmetric positive definite).
-// Returns 0 on success, 1 on failure (M is then garbage).
-// buf: shared scratch of 2*TILE elements; perm: shared int[TILE]; flag: shared int.
+// Gauss-Jordan inversion of the n x n matrix held in shared memory S (leading
+// dimension lds), written to Wout (leading dimension ldw; shared or global).
+// S is destroyed.  pivot = true: partial pivoting over the not-yet-used rows
+// (the pivot row is recorded instead of swapped, and the result gathered
+// through the permutation at the end); failure if a pivot is below
+// tiny_pivot.  pivot = false: pivots taken on the diagonal, failure if one is
+// not positive (the test that the matrix is symmetric positive definite).
+// Returns 0 on success, 1 on failure.
+// Thread map: warp w owns rows i = w (mod 8); lane l owns columns l, l+32, l+64.
+// One step = [read pivot row and column into registers] barrier [update,
+// and the owners of column k+1 propose its pivot candidates] barrier.
+// buf: shared scratch of 2*TILE elements (candidate values and rows);
+// perm: shared int[2*TILE]; flag: shared int[2].
 template <typename T>
-__device__ __noinline__ int cta_inverse(T* M, int ldm, int n, bool pivot, T* buf, int* perm, int* flag) {
-  const int t = threadIdx.x;
-  T* rowb = buf;
-  T* colb = buf + TILE;
-  if (t == 0) *flag = 0;
+__device__ __noinline__ int cta_inverse(T* S, int lds, int n, bool pivot, T* Wout, int ldw, T* buf, int* perm,
+                                        int* flag) {
+  const int t = threadIdx.x, w = t >> 5, l = t & 31;
+  int* used = perm + TILE;       // used[i]: physical row i already a pivot row
+  T* cval = buf;                 // per-warp candidate |value|
+  int* cand_row = reinterpret_cast<int*>(buf + TILE);
+  if (t == 0) flag[0] = 0;
+  for (int i = t; i < n; i += NT) used[i] = 0;
   __syncthreads();
-  for (int kp = 0; kp < n; ++kp) {
+  // candidates for column 0
+  if (pivot && l == 0) {
+    T best = T(-1);
+    int bi = -1;
+    for (int i = w; i < n; i += 8) {
+      const T v = fabs(S[i * lds]);
+      if (v > best) { best = v; bi = i; }
+    }
+    cval[w] = best;
+    cand_row[w] = bi;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    int p = k;
     if (pivot) {
-      if (t < 32) {
-        T best = T(-1);
-        int bi = kp;
-        for (int i = kp + t; i < n; i += 32) {
-          const T v = fabs(M[i * ldm + kp]);
-          if (v > best) { best = v; bi = i; }
-        }
-#pragma unroll
-        for (int off = 16; off; off >>= 1) {
-          const T ob = __shfl_down_sync(0xffffffffu, best, off);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (t == 0) perm[kp] = bi;
+      T best = T(-1);
+      for (int q = 0; q < 8; ++q) {
+        const int r = cand_row[q];
+        const T v = cval[q];
+        if (r >= 0 && (v > best || (v == best && r < p))) { best = v; p = r; }
       }
-      __syncthreads();
-      const int p = perm[kp];
-      if (p != kp) {
-        for (int j = t; j < n; j += NT) {
-          const T a = M[kp * ldm + j];
-          M[kp * ldm + j] = M[p * ldm + j];
-          M[p * ldm + j] = a;
-        }
-      }
-      __syncthreads();
     }
-    T piv = M[kp * ldm + kp];
+    T piv = S[p * lds + k];
     const bool bad = pivot ? !(fabs(piv) > tiny_pivot<T>()) : !(piv > T(0));
-    if (bad) {
-      if (t == 0) *flag = 1;
-      piv = T(1);
-    }
+    if (bad) piv = T(1);
     const T ip = T(1) / piv;
-    for (int j = t; j < n; j += NT) {
-      rowb[j] = (j == kp) ? ip : M[kp * ldm + j] * ip;
-      colb[j] = M[j * ldm + kp];
+    // registers: pivot row entries of own columns, column-k entries of own rows
+    T rowp[3], colk[10];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int j = l + 32 * c;
+      rowp[c] = (j < n) ? S[p * lds + j] : T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+      const int i = w + 8 * a;
+      colk[a] = (i < n) ? S[i * lds + k] : T(0);
+    }
+    if (t == 0) {
+      perm[k] = p;
+      used[p] = 1;
+      if (bad) flag[0] = 1;
     }
     __syncthreads();
-    for (int e = t; e < n * n; e += NT) {
-      const int i = e / n, j = e - i * n;
-      T v;
-      if (i == kp) v = rowb[j];
-      else if (j == kp) v = -colb[i] * ip;
-      else v = M[i * ldm + j] - colb[i] * rowb[j];
-      M[i * ldm + j] = v;
-    }
-    __syncthreads();
-  }
-  if (pivot) {
-    for (int kp = n - 1; kp >= 0; --kp) {
-      const int p = perm[kp];
-      if (p != kp) {
-        for (int i = t; i < n; i += NT) {
-          const T a = M[i * ldm + kp];
-          M[i * ldm + kp] = M[i * ldm + p];
-          M[i * ldm + p] = a;
+    T best = T(-1);
+    int bi = -1;
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+      const int i = w + 8 * a;
+      if (i < n) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int j = l + 32 * c;
+          if (j < n) {
+            T v;
+            if (i == p) v = (j == k) ? ip : rowp[c] * ip;
+            else if (j == k) v = -colk[a] * ip;
+            else v = S[i * lds + j] - colk[a] * rowp[c] * ip;
+            S[i * lds + j] = v;
+            if (pivot && j == k + 1 && !used[i]) {
+              const T av = fabs(v);
+              if (av > best) { best = av; bi = i; }
+            }
+          }
         }
       }
-      __syncthreads();
     }
+    if (pivot && k + 1 < n && l == ((k + 1) & 31)) {
+      cval[w] = best;
+      cand_row[w] = bi;
+    }
+    __syncthreads();
   }
-  const int f = *flag;
+  // gather: W[a][b] = S[perm[a]][iperm[b]], iperm[perm[c]] = c (identity without pivoting)
+  int* iperm = used;
+  if (pivot) {
+    for (int c = t; c < n; c += NT) iperm[perm[c]] = c;
+  }
+  __syncthreads();
+  for (int a = w; a < n; a += 8) {
+    const int ra = pivot ? perm[a] : a;
+    for (int b = l; b < n; b += 32) Wout[a * ldw + b] = S[ra * lds + (pivot ? iperm[b] : b)];
+  }
+  __syncthreads();
+  const int f = flag[0];
   __syncthreads();
   return f;
 }
@@ -219,6 +253,23 @@ __device__ inline T warp_max(T v) {
 #pragma unroll
   for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
   return v;
+}
+
+// Column sweep of one output: sum_{r < R} S[r * ld + j] x[r], four
+// independent accumulators (consecutive j across a warp read consecutive
+// shared-memory words).
+template <typename T>
+__device__ inline T col_dot(const T* S, int ld, int R, int j, const T* x) {
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int r = 0;
+  for (; r + 3 < R; r += 4) {
+    a0 += S[r * ld + j] * x[r];
+    a1 += S[(r + 1) * ld + j] * x[r + 1];
+    a2 += S[(r + 2) * ld + j] * x[r + 2];
+    a3 += S[(r + 3) * ld + j] * x[r + 3];
+  }
+  for (; r < R; ++r) a0 += S[r * ld + j] * x[r];
+  return (a0 + a1) + (a2 + a3);
 }
 
 // dot(a, x) over n entries by one warp; result in every lane.

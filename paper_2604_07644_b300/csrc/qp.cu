@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -18,8 +19,12 @@ namespace gsls {
 // ---------------------------------------------------------------------------
 // the solve kernel
 // ---------------------------------------------------------------------------
+// FP32 solves fit two CTAs per SM (<= 128 registers, ~100 KB shared), which
+// lets one cluster's barrier and latency stalls overlap another's work.
+template <typename T> struct KernelOcc { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
+
 template <typename T>
-__global__ void __launch_bounds__(NT, 1) qp_kernel(const QPDesc* __restrict__ descs, SolveArgs args) {
+__global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDesc* __restrict__ descs, SolveArgs args) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ QPDesc dsh;
@@ -30,7 +35,8 @@ __global__ void __launch_bounds__(NT, 1) qp_kernel(const QPDesc* __restrict__ de
   __syncthreads();
   QPDesc& d = dsh;
 
-  const SmemLayout lay = smem_layout(d.nx, d.ldx, d.ldu, d.nc, d.nf, d.Lc, (int)sizeof(T));
+  const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
+                                     (int)sizeof(T));
   Ctx<T> c;
   c.d = &d;
   c.rank = rank;
@@ -48,11 +54,11 @@ __global__ void __launch_bounds__(NT, 1) qp_kernel(const QPDesc* __restrict__ de
   c.zS = reinterpret_cast<T*>(smem + lay.z);
   c.yS = reinterpret_cast<T*>(smem + lay.y);
   c.wS = reinterpret_cast<T*>(smem + lay.w);
-  c.cS = reinterpret_cast<T*>(smem + lay.c);
   c.lS = reinterpret_cast<T*>(smem + lay.l);
-  c.kS = reinterpret_cast<T*>(smem + lay.k);
-  c.dS = reinterpret_cast<T*>(smem + lay.d);
   c.xS = reinterpret_cast<T*>(smem + lay.x);
+  c.ktS = reinterpret_cast<T*>(smem + lay.kt);
+  c.vS = reinterpret_cast<T*>(smem + lay.v);
+  c.dS = reinterpret_cast<T*>(smem + lay.d);
   c.uS = reinterpret_cast<T*>(smem + lay.u);
   c.pe = reinterpret_cast<T*>(smem + lay.pe);
   c.xs = reinterpret_cast<T*>(smem + lay.xs);
@@ -68,6 +74,8 @@ __global__ void __launch_bounds__(NT, 1) qp_kernel(const QPDesc* __restrict__ de
   c.msz = d.nx * d.ldx;
   c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
   const int t = threadIdx.x;
+  c.prof = (args.prof && qi == 0 && rank == 0 && t == 0) ? args.prof : nullptr;
+  c.t_last = clock64();
 
   if (args.mode == MODE_KKT) {
     const double kkt = kkt_eval<T>(c, cl);
@@ -128,6 +136,7 @@ __global__ void __launch_bounds__(NT, 1) qp_kernel(const QPDesc* __restrict__ de
       if (!check) continue;
       double v[4] = {pl.rp, pl.rd, pl.vm, pl.zm};
       cluster_max(c, cl, v, 4);
+      prof_mark(c, PH_CHECK);
       rp = v[0];
       rd = v[1];
       if (!(isfinite(rp) && isfinite(rd))) {
@@ -142,11 +151,12 @@ __global__ void __launch_bounds__(NT, 1) qp_kernel(const QPDesc* __restrict__ de
         full_xu<T>(c);
         write_outputs<T>(c, rho);
         kkt = kkt_eval<T>(c, cl);
+        prof_mark(c, PH_KKT);
         if (kkt <= args.eps_kkt) {
           status = GPUSLS_OK;
           break;
         }
-        eps *= 0.1;
+        eps = fmax(eps * 0.1, args.eps_floor);
       }
       if (rho_iter) {
         full_xu<T>(c);
@@ -154,6 +164,7 @@ __global__ void __launch_bounds__(NT, 1) qp_kernel(const QPDesc* __restrict__ de
         rho_rule_partials<T>(c, rho, hm, gm, qm);
         double u[3] = {hm, gm, qm};
         cluster_max(c, cl, u, 3);
+        prof_mark(c, PH_RHO);
         const double prim_scale = fmax(v[2], v[3]);
         const double dual_scale = fmax(fmax(u[0], u[1]), u[2]);
         double rho_new = (double)rho;
@@ -264,6 +275,7 @@ struct qp_handle {
   size_t njobs_cap = 0;
   // per-QP pointers kept for conversions
   std::vector<void*> tx0;
+  double* rho0_dev = nullptr;   // [batch] setup penalties (qp_reset)
 };
 
 static size_t al64(size_t x) { return (x + 63) & ~(size_t)63; }
@@ -280,6 +292,8 @@ extern "C" void qp_default_settings(qp_settings* s) {
   s->precision = GPUSLS_FP64;
   s->cluster = 0;
   s->fixed_iters = 0;
+  s->pad = 0;
+  s->eps_floor = 1e-7;
 }
 
 extern "C" const char* gpusls_last_error(void) { return g_err.c_str(); }
@@ -310,8 +324,30 @@ static int launch_qp(qp_handle* h, const SolveArgs& a) {
   return GPUSLS_OK;
 }
 
-static int launch(qp_handle* h, const SolveArgs& a) {
-  return h->esz == 8 ? launch_qp<double>(h, a) : launch_qp<float>(h, a);
+// Debug aid: GPUSLS_PROFILE=1 accumulates per-phase cycle counts of rank 0 of
+// QP 0 and prints them to stderr after each launch.
+static int launch(qp_handle* h, const SolveArgs& a0) {
+  SolveArgs a = a0;
+  static const bool prof_on = getenv("GPUSLS_PROFILE") != nullptr;
+  unsigned long long* dprof = nullptr;
+  if (prof_on) {
+    CU(cudaMalloc(&dprof, PH_COUNT * sizeof(unsigned long long)));
+    CU(cudaMemsetAsync(dprof, 0, PH_COUNT * sizeof(unsigned long long), h->stream));
+    a.prof = dprof;
+  }
+  const int st = h->esz == 8 ? launch_qp<double>(h, a) : launch_qp<float>(h, a);
+  if (prof_on) {
+    unsigned long long hp[PH_COUNT];
+    CU(cudaMemcpyAsync(hp, dprof, sizeof(hp), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    cudaFree(dprof);
+    static const char* names[PH_COUNT] = {"P1", "bwd", "sync1", "P3", "fwd", "sync2", "P5", "check", "rho",
+                                          "R1", "R2", "R3", "R4", "R5", "R6", "kkt"};
+    fprintf(stderr, "[gpusls prof cycles]");
+    for (int k = 0; k < PH_COUNT; ++k) fprintf(stderr, " %s=%llu", names[k], hp[k]);
+    fprintf(stderr, "\n");
+  }
+  return st;
 }
 
 static int run_pack(qp_handle* h, const std::vector<PackJob>& jobs) {
@@ -394,7 +430,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   h->hdesc.resize(batch);
   struct Sizes {
     size_t A, B, b, Q, R, S, q, r, C, D, CN, lo, hi, x0, Rhi, Sh, V, scr, Abar, CK, F, FPi, J, K, KSig, CKSig, Sig,
-        c0, k0, CNSig, SigN, Tch, Uch, Theta, Xi, Gam, z, y;
+        c0, k0, CNSig, SigN, Tch, Uch, Theta, Xi, Gam, z, y, BW, FW, CD;
   };
   std::vector<Sizes> sz(batch);
   for (int b = 0; b < batch; ++b) {
@@ -413,15 +449,19 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     z.C = al64(N * nc * ldx + 1); z.D = al64(N * nc * ldu + 1); z.CN = al64(nf * ldx + 1); z.lo = al64(m + 1);
     z.hi = al64(m + 1); z.x0 = al64(ldx); z.Rhi = al64(N * nu * ldu); z.Sh = al64(N * nu * ldx);
     z.V = al64(nodes * msz); z.scr = al64((size_t)MAXCS * 6 * msz); z.Abar = al64(N * msz);
-    z.CK = al64(N * nc * ldx + 1); z.F = al64(N * nu * ldx); z.FPi = al64(N * nu * ldx); z.J = al64(N * nu * ldc);
-    z.K = al64(N * nu * ldx); z.KSig = al64(N * nu * ldx); z.CKSig = al64(N * nc * ldx + 1); z.Sig = al64(N * msz);
+    z.CK = al64(N * nc * ldx + 1); z.F = al64(N * nu * ldx); z.FPi = al64(N * nx * ldu); z.J = al64(N * nu * ldc);
+    z.K = al64(N * nu * ldx); z.KSig = al64(N * nu * ldx); z.CKSig = al64(N * nx * ldc + 1); z.Sig = al64(N * msz);
     z.c0 = al64(N * ldx); z.k0 = al64(N * ldu); z.CNSig = al64(nf * ldx + 1); z.SigN = al64(msz);
     z.Tch = al64(MAXCS * msz); z.Uch = al64(MAXCS * msz); z.Theta = al64(MAXCS * MAXCS * msz);
     z.Xi = al64(MAXCS * MAXCS * msz); z.Gam = al64(N * nu * ldu); z.z = al64(m + 1); z.y = al64(m + 1);
+    const int ldv = rup4(d.nx + d.nc), ldf = rup4(d.nx + d.nu);
+    int bws, fws, cds;
+    bundle_sizes(d.nx, d.nu, d.nc, (int)ldx, (int)ldu, ldv, ldf, &bws, &fws, &cds);
+    z.BW = al64(N * (size_t)bws); z.FW = al64(N * (size_t)fws); z.CD = al64(N * (size_t)cds + 1);
     toff[b] = tsz;
     tsz += z.A + z.B + z.b + z.Q + z.R + z.S + z.q + z.r + z.C + z.D + z.CN + z.lo + z.hi + z.x0 + z.Rhi + z.Sh +
            4 * z.V + z.scr + z.Abar + z.CK + z.F + z.FPi + z.J + z.K + z.KSig + z.CKSig + z.Sig + z.c0 + z.k0 +
-           z.CNSig + z.SigN + z.Tch + z.Uch + z.Theta + z.Xi + z.Gam + z.z + z.y;
+           z.CNSig + z.SigN + z.Tch + z.Uch + z.Theta + z.Xi + z.Gam + z.z + z.y + z.BW + z.FW + z.CD;
     doff[b] = dsz;
     dsz += al64((N + 1) * nx) + al64(N * nu) + 64;   // kg, kh, rho/flags slot
     // per-QP descriptor (pointers filled after allocation)
@@ -432,7 +472,15 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     D_.Lc = (d.N + cs - 1) / cs;
     D_.nch = (d.N + D_.Lc - 1) / D_.Lc;
     D_.nlev = nlev;
-    const SmemLayout lay = smem_layout(d.nx, (int)ldx, (int)ldu, d.nc, d.nf, D_.Lc, esz);
+    D_.ldv = ldv;
+    D_.ldf = ldf;
+    D_.slot = std::max(std::max(std::max(bws, fws), (int)msz),
+                       std::max(std::max(d.nx * (int)ldu, d.nx * (int)ldc), cds));
+    D_.depth = 3;
+    if (smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, (int)ldx, (int)ldu, ldv, ldf, 3, D_.slot, esz).total > 227 * 1024)
+      D_.depth = 2;
+    const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, (int)ldx, (int)ldu, ldv, ldf, D_.depth,
+                                       D_.slot, esz);
     smem = std::max(smem, lay.total);
   }
   h->smem = smem;
@@ -485,6 +533,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     D_.KSig = take(z.KSig); D_.CKSig = take(z.CKSig); D_.Sig = take(z.Sig); D_.c0 = take(z.c0); D_.k0 = take(z.k0);
     D_.CNSig = take(z.CNSig); D_.SigN = take(z.SigN); D_.Tch = take(z.Tch); D_.Uch = take(z.Uch);
     D_.Theta = take(z.Theta); D_.Xi = take(z.Xi); D_.Gam = take(z.Gam); D_.z = take(z.z); D_.y = take(z.y);
+    D_.BW = take(z.BW); D_.FW = take(z.FW); D_.CD = take(z.CD);
     h->tx0[b] = D_.x0;
     D_.A64 = A64 + po.A; D_.B64 = B64 + po.B; D_.b64 = b64 + po.c; D_.Q64 = Q64 + po.Q; D_.R64 = R64 + po.R;
     D_.S64 = S64 + po.S; D_.q64 = q64 + po.q; D_.r64 = r64 + po.r; D_.C64 = C64 + po.C; D_.D64 = D64 + po.D;
@@ -521,11 +570,16 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   int st = run_pack(h, jobs);
   if (st) { qp_destroy(h); return st; }
   // rho and flags
+  std::vector<double> r0(batch);
+  for (int b = 0; b < batch; ++b) r0[b] = (rho && rho[b] > 0) ? rho[b] : s->rho0;
+  if (cudaMalloc(&h->rho0_dev, batch * sizeof(double)) != cudaSuccess) {
+    qp_destroy(h);
+    return fail(GPUSLS_ERR_CUDA, "qp_batch_setup: cudaMalloc failed");
+  }
+  CU(cudaMemcpyAsync(h->rho0_dev, r0.data(), batch * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   for (int b = 0; b < batch; ++b) {
-    double rv[8] = {0};
-    rv[0] = (rho && rho[b] > 0) ? rho[b] : s->rho0;
     int fl[2] = {0, 0};
-    CU(cudaMemcpyAsync(h->hdesc[b].rho, rv, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->hdesc[b].rho, &r0[b], sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(h->hdesc[b].flags, fl, sizeof(fl), cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
   }
@@ -618,6 +672,7 @@ extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double to
   a.eps_kkt = h->set.eps_kkt > 0 ? (tol > 0 ? tol : h->set.eps_kkt) : -1.0;
   a.rho_min = h->set.rho_min;
   a.rho_max = h->set.rho_max;
+  a.eps_floor = h->set.eps_floor;
   st = launch(h, a);
   if (st) return st;
   return collect(h, info);
@@ -721,29 +776,72 @@ extern "C" int qp_get_state(qp_handle* h, double* z, double* y, double* rho) {
   return GPUSLS_OK;
 }
 
-extern "C" int qp_update(qp_handle* h, const double* q, const double* r, const double* lo, const double* hi) {
+extern "C" int qp_update(qp_handle* h, const double* A, const double* B, const double* c, const double* Q,
+                         const double* R, const double* S, const double* q, const double* r, const double* C,
+                         const double* D, const double* CN, const double* lo, const double* hi) {
   if (!h) return fail(GPUSLS_ERR_INVALID, "qp_update: null handle");
   std::vector<PackJob> jobs;
+  const bool refac = A || B || c || Q || R || S || q || r || C || D || CN;
   for (int b = 0; b < h->batch; ++b) {
     const qp_dims& d = h->dims[b];
     const QPDesc& D_ = h->hdesc[b];
     const QPOffsets& po = h->off[b];
-    const int m = d.N * d.nc + d.nf;
-    if (q) jobs.push_back({q + po.q, D_.q, d.N + 1, 1, d.nx, D_.ldx});
-    if (r) jobs.push_back({r + po.r, D_.r, d.N, 1, d.nu, D_.ldu});
-    if (lo && m) jobs.push_back({lo + po.lohi, D_.lo, 1, 1, m, m});
-    if (hi && m) jobs.push_back({hi + po.lohi, D_.hi, 1, 1, m, m});
-    size_t nq = (size_t)(d.N + 1) * d.nx, nr = (size_t)d.N * d.nu;
-    if (q) CU(cudaMemcpyAsync(D_.q64, q + po.q, nq * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    if (r) CU(cudaMemcpyAsync(D_.r64, r + po.r, nr * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    if (lo && m) CU(cudaMemcpyAsync(D_.lo64, lo + po.lohi, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    if (hi && m) CU(cudaMemcpyAsync(D_.hi64, hi + po.lohi, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    int fl[2] = {0, 0};   // c0, k0 depend on q, r: refactor at the next solve
-    if (q || r) CU(cudaMemcpyAsync(D_.flags, fl, sizeof(fl), cudaMemcpyHostToDevice, h->stream));
+    const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf, m = N * nc + nf;
+    const int ldx = D_.ldx, ldu = D_.ldu;
+    auto add = [&](const double* src, size_t o, void* dst, int count, int rows, int cols, int ld, double* d64,
+                   size_t n64) -> int {
+      if (!src || n64 == 0) return GPUSLS_OK;
+      jobs.push_back({src + o, dst, count, rows, cols, ld});
+      CU(cudaMemcpyAsync(d64, src + o, n64 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      return GPUSLS_OK;
+    };
+    int st = GPUSLS_OK;
+    st |= add(A, po.A, D_.A, N, nx, nx, ldx, D_.A64, (size_t)N * nx * nx);
+    st |= add(B, po.B, D_.B, N, nx, nu, ldu, D_.B64, (size_t)N * nx * nu);
+    st |= add(c, po.c, D_.b, N, 1, nx, ldx, D_.b64, (size_t)N * nx);
+    st |= add(Q, po.Q, D_.Q, N + 1, nx, nx, ldx, D_.Q64, (size_t)(N + 1) * nx * nx);
+    st |= add(R, po.R, D_.R, N, nu, nu, ldu, D_.R64, (size_t)N * nu * nu);
+    st |= add(S, po.S, D_.S, N, nu, nx, ldx, D_.S64, (size_t)N * nu * nx);
+    st |= add(q, po.q, D_.q, N + 1, 1, nx, ldx, D_.q64, (size_t)(N + 1) * nx);
+    st |= add(r, po.r, D_.r, N, 1, nu, ldu, D_.r64, (size_t)N * nu);
+    st |= add(C, po.C, D_.C, N, nc, nx, ldx, D_.C64, (size_t)N * nc * nx);
+    st |= add(D, po.D, D_.D, N, nc, nu, ldu, D_.D64, (size_t)N * nc * nu);
+    st |= add(CN, po.CN, D_.CN, 1, nf, nx, ldx, D_.CN64, (size_t)nf * nx);
+    st |= add(lo, po.lohi, D_.lo, 1, 1, m, m, D_.lo64, (size_t)m);
+    st |= add(hi, po.lohi, D_.hi, 1, 1, m, m, D_.hi64, (size_t)m);
+    if (st) return GPUSLS_ERR_CUDA;
+  }
+  if (refac) {
+    std::vector<int> zero(2 * h->batch, 0);
+    for (int b = 0; b < h->batch; ++b)
+      CU(cudaMemcpyAsync(h->hdesc[b].flags, zero.data(), 2 * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   }
   int st = run_pack(h, jobs);
   if (st) return st;
   CU(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+template <typename T>
+__global__ void reset_kernel(const QPDesc* __restrict__ descs, const double* __restrict__ rho0) {
+  const QPDesc d = descs[blockIdx.x];
+  T* zz = reinterpret_cast<T*>(d.z);
+  T* yy = reinterpret_cast<T*>(d.y);
+  for (int e = threadIdx.x; e < d.m; e += blockDim.x) {
+    zz[e] = T(0);
+    yy[e] = T(0);
+  }
+  if (threadIdx.x == 0) {
+    d.rho[0] = rho0[blockIdx.x];
+    d.flags[0] = 0;
+  }
+}
+
+extern "C" int qp_reset(qp_handle* h) {
+  if (!h) return fail(GPUSLS_ERR_INVALID, "qp_reset: null handle");
+  if (h->esz == 8) reset_kernel<double><<<h->batch, 256, 0, h->stream>>>(h->ddesc, h->rho0_dev);
+  else reset_kernel<float><<<h->batch, 256, 0, h->stream>>>(h->ddesc, h->rho0_dev);
+  CU(cudaGetLastError());
   return GPUSLS_OK;
 }
 
@@ -755,5 +853,6 @@ extern "C" void qp_destroy(qp_handle* h) {
   if (h->info_i) cudaFree(h->info_i);
   if (h->info_d) cudaFree(h->info_d);
   if (h->djobs) cudaFree(h->djobs);
+  if (h->rho0_dev) cudaFree(h->rho0_dev);
   delete h;
 }

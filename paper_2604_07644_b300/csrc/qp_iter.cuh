@@ -25,35 +25,43 @@ __device__ inline int own_rows(Ctx<T>& c) {
   return c.active ? c.L * c.d->nc + (c.last ? c.d->nf : 0) : 0;
 }
 
-// Dependent chain over the chunk with the per-stage matrices Abar staged into a
-// 3-slot shared-memory ring by cp.async (two stages ahead of the compute).
-//   backward: l_i = Abar_i^T l_{i+1} + c_i for i = e-1 .. s
-//   forward:  x_{i+1} = Abar_i x_i + d_i for i = s .. e-1
+// ---------------------------------------------------------------------------
+// cp.async ring over the union region: slot k holds block k % depth.
+// ---------------------------------------------------------------------------
 template <typename T>
-__device__ void chain(Ctx<T>& c, bool backward) {
-  QPDesc& d = *c.d;
-  const int nx = d.nx, ldx = d.ldx, L = c.L, msz = c.msz;
-  const T* Abar = TP<T>(d.Abar);
-  const int bytes = msz * (int)sizeof(T);
-  auto stage_of = [&](int st) { return backward ? (c.e - 1 - st) : (c.s + st); };
-#pragma unroll 1
-  for (int st = 0; st < 2; ++st) {
-    if (st < L) cta_stage(c.ring + (size_t)st * msz, Abar + (size_t)stage_of(st) * msz, bytes);
+__device__ inline T* ring_slot(Ctx<T>& c, int k) {
+  return c.ring + (size_t)(k % c.d->depth) * c.d->slot;
+}
+
+template <typename T>
+struct Blk {
+  const T* ptr;
+  int bytes;
+};
+
+// Stream nblk blocks (src(b) -> Blk) through the ring, depth-1 blocks ahead
+// of the compute f(b, slot).  Every block must fit a slot.
+template <typename T, typename Src, typename Fn>
+__device__ void stream_blocks(Ctx<T>& c, int nblk, Src src, Fn f) {
+  const int depth = c.d->depth;
+  for (int b = 0; b < depth - 1; ++b) {
+    if (b < nblk) {
+      const Blk<T> k = src(b);
+      cta_stage(ring_slot(c, b), k.ptr, k.bytes);
+    }
     cp_async_commit();
   }
-#pragma unroll 1
-  for (int st = 0; st < L; ++st) {
-    if (st + 2 < L) cta_stage(c.ring + (size_t)((st + 2) % 3) * msz, Abar + (size_t)stage_of(st + 2) * msz, bytes);
-    cp_async_commit();
-    cp_async_wait<2>();
-    __syncthreads();
-    const T* M = c.ring + (size_t)(st % 3) * msz;
-    if (backward) {
-      const int li = c.e - 1 - st - c.s;
-      smem_mvT<T>(M, ldx, nx, nx, c.lS + (size_t)(li + 1) * ldx, c.cS + (size_t)li * ldx, c.lS + (size_t)li * ldx, c.red);
-    } else {
-      smem_mv<T>(M, ldx, nx, nx, c.xS + (size_t)st * ldx, c.dS + (size_t)st * ldx, c.xS + (size_t)(st + 1) * ldx);
+  for (int b = 0; b < nblk; ++b) {
+    if (b + depth - 1 < nblk) {
+      const Blk<T> k = src(b + depth - 1);
+      cta_stage(ring_slot(c, b + depth - 1), k.ptr, k.bytes);
     }
+    cp_async_commit();
+    if (depth >= 3) cp_async_wait<2>();
+    else cp_async_wait<1>();
+    __syncthreads();
+    f(b, (const T*)ring_slot(c, b));
+    __syncthreads();
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -64,145 +72,218 @@ struct Partials {
 };
 
 // One ADMM iteration (eq. augmented_linear, the LQ solve of eq. primal_update
-// with cached factorization, the z-projection and the scaled dual update).
-// On `check` iterations the per-CTA dual-residual partial is also formed.
+// with the cached factorization, the z-projection and the scaled dual update).
+//
+// Backward chain, stage i = e-1 .. s, on the stacked vector [l_{i+1}; omega_i]:
+//   l_i  = [Abar_i; CK_i]^T [l_{i+1}; omega_i] + c0_i   (p_i up to the fix-up)
+//   k~_i = [F_i  J_i] [l_{i+1}; omega_i] + k0_i
+// Forward chain, stage i = s .. e-1, on [lx_i; k_i]:
+//   [lx_{i+1}; v~_i] = [Abar_i B_i; CK_i D_i] [lx_i; k_i] + [b_i; 0]
+// with k_i = k~_i + FPi_i p_e and v_i = v~_i + CKSig_i x_s after the
+// chunk-boundary exchanges.  On `check` iterations the dual-residual partial
+// is formed too.
 template <typename T>
 __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool check, Partials& pl) {
   QPDesc& d = *c.d;
-  const int nx = d.nx, nu = d.nu, nc = d.nc, N = d.N, ldx = d.ldx, ldu = d.ldu, ldc = d.ldc;
-  const int msz = c.msz, L = c.L, s = c.s;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, N = d.N, ldx = d.ldx, ldu = d.ldu;
+  const int ldv = d.ldv, ldf = d.ldf, msz = c.msz, L = c.L, s = c.s;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const T *B = TP<T>(d.B), *bb = TP<T>(d.b), *q = TP<T>(d.q), *C = TP<T>(d.C), *D = TP<T>(d.D), *CN = TP<T>(d.CN);
-  const T *lo = TP<T>(d.lo), *hi = TP<T>(d.hi), *x0 = TP<T>(d.x0);
-  const T *CK = TP<T>(d.CK), *F = TP<T>(d.F), *FPi = TP<T>(d.FPi), *J = TP<T>(d.J);
-  const T *CKSig = TP<T>(d.CKSig), *c0 = TP<T>(d.c0), *k0 = TP<T>(d.k0), *CNSig = TP<T>(d.CNSig);
+  const T *q = TP<T>(d.q), *CN = TP<T>(d.CN), *lo = TP<T>(d.lo), *hi = TP<T>(d.hi), *x0 = TP<T>(d.x0);
+  const T *FPi = TP<T>(d.FPi), *CKSig = TP<T>(d.CKSig), *CNSig = TP<T>(d.CNSig);
   const T *Theta = TP<T>(d.Theta), *Xi = TP<T>(d.Xi);
+  const T *BW = TP<T>(d.BW), *FW = TP<T>(d.FW), *CD = TP<T>(d.CD);
+  int bws, fws, cds;
+  bundle_sizes(nx, nu, nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
   const int nrows = own_rows(c);
 
-  // P1: omega = rho (y - z); c_i = c0_i + CK_i^T omega_i; boundary of the
-  // backward chain (p_N = q^_N for the last chunk, 0 otherwise).
+  // P1: omega = rho (y - z) into the stacked rows; boundary of the backward
+  // chain (p_N = q^_N = q_N + C_N^T omega_N for the last chunk, 0 otherwise).
   if (c.active) {
     for (int e2 = t; e2 < nrows; e2 += NT) c.wS[e2] = rho * (c.yS[e2] - c.zS[e2]);
     __syncthreads();
-    for (int e2 = t; e2 < L * nx; e2 += NT) {
-      const int li = e2 / nx, j = e2 - li * nx, i = s + li;
-      const T* CKi = CK + (size_t)i * nc * ldx;
-      T a = c0[(size_t)i * ldx + j];
-      for (int rr = 0; rr < nc; ++rr) a += CKi[rr * ldx + j] * c.wS[li * nc + rr];
-      c.cS[li * ldx + j] = a;
+    for (int e2 = t; e2 < L * nc; e2 += NT) {
+      const int li = e2 / nc, rr = e2 - li * nc;
+      c.lS[(size_t)(li + 1) * ldv + nx + rr] = c.wS[e2];
     }
     for (int j = t; j < nx; j += NT) {
       T a = T(0);
       if (c.last) {
         a = q[(size_t)N * ldx + j];
-        for (int rr = 0; rr < d.nf; ++rr) a += CN[rr * ldx + j] * c.wS[L * nc + rr];
+        for (int rr = 0; rr < nf; ++rr) a += CN[rr * ldx + j] * c.wS[L * nc + rr];
       }
-      c.lS[(size_t)L * ldx + j] = a;
+      c.lS[(size_t)L * ldv + j] = a;
     }
     __syncthreads();
-    // P2: backward chunk-local chain
-    chain<T>(c, true);
+    prof_mark(c, PH_P1);
+    // P2: backward chain over the BW bundles: threads j < nx sweep [Abar; CK]
+    // for l_i, threads 128 + a sweep [F | J]^T for k~_i.
+    const int R = nx + nc;
+    stream_blocks<T>(
+        c, L, [&](int st) { return Blk<T>{BW + (size_t)(c.e - 1 - st) * bws, bws * (int)sizeof(T)}; },
+        [&](int st, const T* S) {
+          const int li = L - 1 - st;
+          const T* xin = c.lS + (size_t)(li + 1) * ldv;
+          const T* fjt = S + (size_t)R * ldx;
+          const T* c0b = fjt + (size_t)R * ldu;
+          if (t < nx) {
+            c.lS[(size_t)li * ldv + t] = c0b[t] + col_dot(S, ldx, R, t, xin);
+          } else if (t >= 128 && t < 128 + nu) {
+            const int a = t - 128;
+            c.ktS[li * ldu + a] = c0b[ldx + a] + col_dot(fjt, ldu, R, a, xin);
+          }
+        });
     for (int j = t; j < nx; j += NT) c.slotL[j] = c.lS[j];
+    prof_mark(c, PH_BWD);
   }
   cl.sync();
-  // P3: boundary p_e from the later chunks, then k_i and d_i.
+  prof_mark(c, PH_SYNC1);
+  // P3: boundary p_e from the later chunks, then k_i = k~_i + FPi_i p_e.
   if (c.active) {
     if (!c.last) {
       const T* rem = cl.map_shared_rank(c.slotL, c.rank + 1);
       for (int j = t; j < nx; j += NT) c.pe[j] = rem[j];
-      __syncthreads();
-      for (int m = c.rank + 2; m < d.nch; ++m) {
-        const T* rm = cl.map_shared_rank(c.slotL, m);
-        for (int j = t; j < nx; j += NT) c.tmp1[j] = rm[j];
-        __syncthreads();
-        g_mv<T>(Theta + (size_t)(c.rank * MAXCS + m) * msz, ldx, nx, nx, c.tmp1, T(1), true, c.pe);
+      const int m0 = c.rank + 2, nb = d.nch - m0;
+      stream_blocks<T>(
+          c, nb, [&](int b) { return Blk<T>{Theta + (size_t)(c.rank * MAXCS + m0 + b) * msz, msz * (int)sizeof(T)}; },
+          [&](int b, const T* S) {
+            const T* rm = cl.map_shared_rank(c.slotL, m0 + b);
+            for (int j = t; j < nx; j += NT) c.tmp1[j] = rm[j];
+            __syncthreads();
+            if (t < nx) c.pe[t] += col_dot(S, ldx, nx, t, c.tmp1);
+          });
+      const int per = nx * ldu;   // FPi_i^T
+      const int Gs = max(1, d.slot / per);
+      const int nbk = (L + Gs - 1) / Gs;
+      stream_blocks<T>(
+          c, nbk,
+          [&](int b) {
+            const int n_st = min(Gs, L - b * Gs);
+            return Blk<T>{FPi + (size_t)(s + b * Gs) * per, n_st * per * (int)sizeof(T)};
+          },
+          [&](int b, const T* S) {
+            const int n_st = min(Gs, L - b * Gs);
+            for (int pr = t; pr < n_st * nu; pr += NT) {
+              const int ls = pr / nu, a = pr - ls * nu, li = b * Gs + ls;
+              c.xS[(size_t)li * ldf + nx + a] = c.ktS[li * ldu + a] + col_dot(S + (size_t)ls * per, ldu, nx, a, c.pe);
+            }
+          });
+    } else {
+      for (int e2 = t; e2 < L * nu; e2 += NT) {
+        const int li = e2 / nu, a = e2 - li * nu;
+        c.xS[(size_t)li * ldf + nx + a] = c.ktS[li * ldu + a];
       }
-    }
-    for (int pr = w; pr < L * nu; pr += NT / 32) {
-      const int li = pr / nu, a = pr - li * nu, i = s + li;
-      T v = warp_dot(F + (size_t)i * nu * ldx + a * ldx, c.lS + (size_t)(li + 1) * ldx, nx);
-      if (!c.last) v += warp_dot(FPi + (size_t)i * nu * ldx + a * ldx, c.pe, nx);
-      v += warp_dot(J + (size_t)i * nu * ldc + a * ldc, c.wS + li * nc, nc);
-      if (lane == 0) c.kS[li * ldu + a] = v + k0[(size_t)i * ldu + a];
-    }
-    __syncthreads();
-    for (int e2 = t; e2 < L * nx; e2 += NT) {
-      const int li = e2 / nx, row = e2 - li * nx, i = s + li;
-      const T* Bi = B + (size_t)i * nx * ldu + row * ldu;
-      T a = bb[(size_t)i * ldx + row];
-      for (int k = 0; k < nu; ++k) a += Bi[k] * c.kS[li * ldu + k];
-      c.dS[li * ldx + row] = a;
     }
     for (int j = t; j < nx; j += NT) c.xS[j] = c.first ? x0[j] : T(0);
     __syncthreads();
-    // P4: forward chunk-local chain
-    chain<T>(c, false);
-    for (int j = t; j < nx; j += NT) c.slotX[j] = c.xS[(size_t)L * ldx + j];
+    prof_mark(c, PH_P3);
+    // P4: forward chain over the FW^T bundles: thread r < nx + nc sweeps
+    // column r of FW^T for lx_{i+1} (r < nx) or v~_i (r >= nx).
+    const int R = nx + nc, Cn = nx + nu;
+    stream_blocks<T>(
+        c, L, [&](int st) { return Blk<T>{FW + (size_t)(s + st) * fws, fws * (int)sizeof(T)}; },
+        [&](int st, const T* S) {
+          const T* xin = c.xS + (size_t)st * ldf;
+          const T* bvec = S + (size_t)Cn * ldv;
+          for (int r = t; r < R; r += NT) {
+            const T v = col_dot(S, ldv, Cn, r, xin);
+            if (r < nx) c.xS[(size_t)(st + 1) * ldf + r] = v + bvec[r];
+            else c.vS[st * nc + r - nx] = v;
+          }
+        });
+    for (int j = t; j < nx; j += NT) c.slotX[j] = c.xS[(size_t)L * ldf + j];
+    prof_mark(c, PH_FWD);
   }
   cl.sync();
-  // P5: boundary x_s from the earlier chunks, G(dx, du), projection, dual update.
+  prof_mark(c, PH_SYNC2);
+  // P5: boundary x_s from the earlier chunks, v_i = v~_i + CKSig_i x_s,
+  // projection and scaled dual update.
   if (c.active) {
     if (!c.first) {
       const T* rem = cl.map_shared_rank(c.slotX, c.rank - 1);
       for (int j = t; j < nx; j += NT) c.xs[j] = rem[j];
-      __syncthreads();
-      for (int m = c.rank - 2; m >= 0; --m) {
-        const T* rm = cl.map_shared_rank(c.slotX, m);
-        for (int j = t; j < nx; j += NT) c.tmp1[j] = rm[j];
-        __syncthreads();
-        g_mv<T>(Xi + (size_t)(c.rank * MAXCS + m) * msz, ldx, nx, nx, c.tmp1, T(1), true, c.xs);
+      const int nb = c.rank - 1;   // m = rank-2 .. 0
+      stream_blocks<T>(
+          c, nb, [&](int b) { return Blk<T>{Xi + (size_t)(c.rank * MAXCS + (c.rank - 2 - b)) * msz, msz * (int)sizeof(T)}; },
+          [&](int b, const T* S) {
+            const T* rm = cl.map_shared_rank(c.slotX, c.rank - 2 - b);
+            for (int j = t; j < nx; j += NT) c.tmp1[j] = rm[j];
+            __syncthreads();
+            if (t < nx) c.xs[t] += col_dot(S, ldx, nx, t, c.tmp1);
+          });
+      const int ldc = d.ldc;
+      const int per = nx * ldc;   // CKSig_i^T
+      if (nc > 0) {
+        const int Gs = max(1, d.slot / per);
+        const int nbk = (L + Gs - 1) / Gs;
+        stream_blocks<T>(
+            c, nbk,
+            [&](int b) {
+              const int n_st = min(Gs, L - b * Gs);
+              return Blk<T>{CKSig + (size_t)(s + b * Gs) * per, n_st * per * (int)sizeof(T)};
+            },
+            [&](int b, const T* S) {
+              const int n_st = min(Gs, L - b * Gs);
+              for (int pr = t; pr < n_st * nc; pr += NT) {
+                const int ls = pr / nc, rr = pr - ls * nc, li = b * Gs + ls;
+                c.vS[li * nc + rr] += col_dot(S + (size_t)ls * per, ldc, nx, rr, c.xs);
+              }
+            });
       }
     }
-    T rp = T(0), vm = T(0), zm = T(0);
-    for (int lr = w; lr < nrows; lr += NT / 32) {
-      T v;
-      if (lr < L * nc) {
-        const int li = lr / nc, rr = lr - li * nc, i = s + li;
-        v = warp_dot(CK + (size_t)i * nc * ldx + rr * ldx, c.xS + (size_t)li * ldx, nx);
-        if (!c.first) v += warp_dot(CKSig + (size_t)i * nc * ldx + rr * ldx, c.xs, nx);
-        v += warp_dot(D + (size_t)i * nc * ldu + rr * ldu, c.kS + li * ldu, nu);
-      } else {
-        const int rr = lr - L * nc;
-        v = warp_dot(CN + rr * ldx, c.xS + (size_t)L * ldx, nx);
+    if (c.last) {
+      for (int rr = w; rr < nf; rr += NT / 32) {
+        T v = warp_dot(CN + rr * ldx, c.xS + (size_t)L * ldf, nx);
         if (!c.first) v += warp_dot(CNSig + rr * ldx, c.xs, nx);
-      }
-      if (lane == 0) {
-        const int g = s * nc + lr;
-        const T zo = c.zS[lr], yo = c.yS[lr];
-        const T zn = fmin(fmax(v + yo, lo[g]), hi[g]);
-        c.yS[lr] = yo + v - zn;
-        c.zS[lr] = zn;
-        c.wS[lr] = zn - zo;
-        rp = fmax(rp, fabs(v - zn));
-        vm = fmax(vm, fabs(v));
-        zm = fmax(zm, fabs(zn));
+        if (lane == 0) c.vS[L * nc + rr] = v;
       }
     }
     __syncthreads();
+    T rp = T(0), vm = T(0), zm = T(0);
+    for (int lr = t; lr < nrows; lr += NT) {
+      const int gi = s * nc + lr;
+      const T v = c.vS[lr];
+      const T zo = c.zS[lr], yo = c.yS[lr];
+      const T zn = fmin(fmax(v + yo, lo[gi]), hi[gi]);
+      c.yS[lr] = yo + v - zn;
+      c.zS[lr] = zn;
+      c.wS[lr] = zn - zo;
+      rp = fmax(rp, fabs(v - zn));
+      vm = fmax(vm, fabs(v));
+      zm = fmax(zm, fabs(zn));
+    }
+    __syncthreads();
+    prof_mark(c, PH_P5);
     if (check) {
       pl.rp = (double)block_max(c, rp);
       pl.vm = (double)block_max(c, vm);
       pl.zm = (double)block_max(c, zm);
-      // dual residual partial: rho * ||G^T (z+ - z)||_inf over own stages
+      // dual residual partial: rho * ||G^T (z+ - z)||_inf = rho * max |[C D]^T dz|
       T rd = T(0);
-      for (int e2 = t; e2 < L * nx; e2 += NT) {
-        const int li = e2 / nx, j = e2 - li * nx, i = s + li;
-        const T* Ci = C + (size_t)i * nc * ldx;
-        T a = T(0);
-        for (int rr = 0; rr < nc; ++rr) a += Ci[rr * ldx + j] * c.wS[li * nc + rr];
-        rd = fmax(rd, fabs(a));
-      }
-      for (int e2 = t; e2 < L * nu; e2 += NT) {
-        const int li = e2 / nu, a2 = e2 - li * nu, i = s + li;
-        const T* Di = D + (size_t)i * nc * ldu;
-        T a = T(0);
-        for (int rr = 0; rr < nc; ++rr) a += Di[rr * ldu + a2] * c.wS[li * nc + rr];
-        rd = fmax(rd, fabs(a));
+      const int Cn = nx + nu;
+      if (cds > 0) {
+        const int Gs = max(1, d.slot / cds);
+        const int nbk = (L + Gs - 1) / Gs;
+        stream_blocks<T>(
+            c, nbk,
+            [&](int b) {
+              const int n_st = min(Gs, L - b * Gs);
+              return Blk<T>{CD + (size_t)(s + b * Gs) * cds, n_st * cds * (int)sizeof(T)};
+            },
+            [&](int b, const T* S) {
+              const int n_st = min(Gs, L - b * Gs);
+              for (int e2 = t; e2 < n_st * Cn; e2 += NT) {
+                const int ls = e2 / Cn, col = e2 - ls * Cn, li = b * Gs + ls;
+                const T* Sb = S + (size_t)ls * cds;
+                T a = T(0);
+                for (int rr = 0; rr < nc; ++rr) a += Sb[rr * ldf + col] * c.wS[li * nc + rr];
+                rd = fmax(rd, fabs(a));
+              }
+            });
       }
       if (c.last) {
         for (int j = t; j < nx; j += NT) {
           T a = T(0);
-          for (int rr = 0; rr < d.nf; ++rr) a += CN[rr * ldx + j] * c.wS[L * nc + rr];
+          for (int rr = 0; rr < nf; ++rr) a += CN[rr * ldx + j] * c.wS[L * nc + rr];
           rd = fmax(rd, fabs(a));
         }
       }
@@ -218,9 +299,10 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
 template <typename T>
 __device__ void full_xu(Ctx<T>& c) {
   QPDesc& d = *c.d;
-  const int nx = d.nx, nu = d.nu, ldx = d.ldx, ldu = d.ldu, msz = c.msz, L = c.L, s = c.s;
+  const int nx = d.nx, nu = d.nu, ldx = d.ldx, ldu = d.ldu, ldf = d.ldf, msz = c.msz, L = c.L, s = c.s;
   const T *K = TP<T>(d.K), *KSig = TP<T>(d.KSig), *Sig = TP<T>(d.Sig), *SigN = TP<T>(d.SigN);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!c.active) return;
   const int nxr = (L + (c.last ? 1 : 0)) * nx;
   for (int pr = w; pr < nxr; pr += NT / 32) {
     const int li = pr / nx, j = pr - li * nx;
@@ -229,13 +311,13 @@ __device__ void full_xu(Ctx<T>& c) {
       const T* Sr = (li < L) ? Sig + (size_t)(s + li) * msz + j * ldx : SigN + j * ldx;
       v = warp_dot(Sr, c.xs, nx);
     }
-    if (lane == 0) c.dS[(size_t)li * ldx + j] = c.xS[(size_t)li * ldx + j] + v;
+    if (lane == 0) c.dS[(size_t)li * ldx + j] = c.xS[(size_t)li * ldf + j] + v;
   }
   for (int pr = w; pr < L * nu; pr += NT / 32) {
     const int li = pr / nu, a = pr - li * nu, i = s + li;
-    T v = warp_dot(K + (size_t)i * nu * ldx + a * ldx, c.xS + (size_t)li * ldx, nx);
+    T v = warp_dot(K + (size_t)i * nu * ldx + a * ldx, c.xS + (size_t)li * ldf, nx);
     if (!c.first) v += warp_dot(KSig + (size_t)i * nu * ldx + a * ldx, c.xs, nx);
-    if (lane == 0) c.uS[li * ldu + a] = v + c.kS[li * ldu + a];
+    if (lane == 0) c.uS[li * ldu + a] = v + c.xS[(size_t)li * ldf + nx + a];
   }
   __syncthreads();
 }
@@ -297,18 +379,26 @@ __device__ void rho_rule_partials(Ctx<T>& c, T rho, double& hm, double& gm, doub
   qm = (double)block_max(c, qq);
 }
 
-// Cluster-wide max of up to 8 doubles through the part[] slots.
+// Cluster-wide max of up to 8 doubles through the part[] slots: every remote
+// value is read by its own thread, then combined from shared memory.
 template <typename T>
 __device__ void cluster_max(Ctx<T>& c, cg::cluster_group& cl, double* v, int n) {
   if (threadIdx.x < n) c.part[threadIdx.x] = v[threadIdx.x];
   cl.sync();
-  for (int k = 0; k < n; ++k) v[k] = 0.0;
-  for (int rk = 0; rk < c.cs; ++rk) {
-    const double* p = cl.map_shared_rank(c.part, rk);
-    for (int k = 0; k < n; ++k) {
-      const double a = p[k];
-      v[k] = (a != a || v[k] != v[k]) ? a + v[k] : fmax(v[k], a);
+  double* gath = c.part + 16;   // [cs * n]
+  const int t = threadIdx.x;
+  if (t < c.cs * n) {
+    const double* p = cl.map_shared_rank(c.part, t / n);
+    gath[t] = p[t % n];
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    double r = 0.0;
+    for (int rk = 0; rk < c.cs; ++rk) {
+      const double a = gath[rk * n + k];
+      r = (a != a || r != r) ? a + r : fmax(r, a);
     }
+    v[k] = r;
   }
   cl.sync();
 }

@@ -35,6 +35,8 @@ struct QPDesc {
   int ldx, ldu, ldc;
   int nch, Lc;      // number of non-empty chunks, chunk length
   int nlev;         // tree levels above the leaves
+  int ldv, ldf;     // row strides of the stacked vectors [l; omega] and [x; k]
+  int depth, slot;  // cp.async ring depth and slot size (elements)
   int pad0;
   // problem (T)
   void *A, *B, *b, *Q, *R, *S, *q, *r, *C, *D, *CN, *lo, *hi, *x0;
@@ -43,6 +45,8 @@ struct QPDesc {
   // cached iteration operators (T)
   void *Abar, *CK, *F, *FPi, *J, *K, *KSig, *CKSig, *Sig, *c0, *k0, *CNSig, *SigN, *Tch, *Uch,
       *Theta, *Xi, *Gam;
+  // per-stage bundles streamed by the iteration (see bundle_sizes)
+  void *BW, *FW, *CD;
   // ADMM state (T)
   void *z, *y;
   // FP64 copies (dense, caller layout) and scratch
@@ -59,29 +63,48 @@ struct QPDesc {
 enum Mode { MODE_SOLVE = 0, MODE_RICCATI = 1, MODE_KKT = 2 };
 
 struct SolveArgs {
+  unsigned long long* prof;   // optional per-phase cycle counters (rank 0 of QP 0), else null
   int mode;
   int max_iter;
   int fixed_iters;
   int sigma;
   int check_every;
   int cs;
-  double eps, eps_kkt, rho_min, rho_max;
+  double eps, eps_kkt, rho_min, rho_max, eps_floor;
 };
+
+// Per-stage operator bundles of the cached iteration (elements).  Every
+// product of the iteration is a column sweep y[j] = sum_r M[r][j] x[r] over a
+// row-major block, so blocks used as y = M x are stored transposed.
+//   BW_i = [Abar_i ; CK_i] ((nx+nc) x ldx), [F_i | J_i]^T ((nx+nc) x ldu),
+//          c0_i (ldx), k0_i (ldu)                    -- backward chain
+//   FW_i = [Abar_i | B_i ; CK_i | D_i]^T ((nx+nu) x ldv), b_i (ldx) -- forward chain
+//   CD_i = [C_i | D_i] (nc x ldf)                    -- dual residual
+// with ldv = rup4(nx + nc), ldf = rup4(nx + nu).
+__host__ __device__ inline void bundle_sizes(int nx, int nu, int nc, int ldx, int ldu, int ldv, int ldf, int* bw,
+                                             int* fw, int* cd) {
+  *bw = (nx + nc) * ldx + (nx + nc) * ldu + ldx + ldu;
+  *fw = (nx + nu) * ldv + ldx;
+  *cd = nc * ldf;
+}
+
+constexpr int MAXCS_SMEM = 8;
 
 // Shared-memory carve-up (byte offsets, 16-byte aligned).
 struct SmemLayout {
   int ring, gemm, gj, gjbuf;                 // union region
-  int z, y, w, c, l, k, d, x, u, pe, xs, slotL, slotX, tmp1, tmp2, tmp3, red;
+  int z, y, w, l, x, kt, v, d, u, pe, xs, slotL, slotX, tmp1, tmp2, tmp3, red;
   int part, perm, flag;
   int total;
 };
 
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout smem_layout(int nx, int ldx, int ldu, int nc, int nf, int Lc, int esz) {
+__host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf, int Lc, int ldx, int ldu, int ldv,
+                                                  int ldf, int depth, int slot, int esz) {
   SmemLayout s;
   int off = 0;
-  const int ring_b = 3 * nx * ldx * esz;
+  const int ring_b = depth * slot * esz;
   const int dense_b = (2 * KT * TILE + TILE * GJ_LD + 2 * TILE) * esz;
   const int uni = ring_b > dense_b ? ring_b : dense_b;
   s.ring = 0;
@@ -93,11 +116,11 @@ __host__ __device__ inline SmemLayout smem_layout(int nx, int ldx, int ldu, int 
   s.z = off; off = al16(off + rows * esz);
   s.y = off; off = al16(off + rows * esz);
   s.w = off; off = al16(off + rows * esz);
-  s.c = off; off = al16(off + Lc * ldx * esz);
-  s.l = off; off = al16(off + (Lc + 1) * ldx * esz);
-  s.k = off; off = al16(off + Lc * ldu * esz);
+  s.l = off; off = al16(off + (Lc + 1) * ldv * esz);
+  s.x = off; off = al16(off + (Lc + 1) * ldf * esz);
+  s.kt = off; off = al16(off + Lc * ldu * esz);
+  s.v = off; off = al16(off + rows * esz);
   s.d = off; off = al16(off + (Lc + 1) * ldx * esz);
-  s.x = off; off = al16(off + (Lc + 1) * ldx * esz);
   s.u = off; off = al16(off + Lc * ldu * esz);
   s.pe = off; off = al16(off + TILE * esz);
   s.xs = off; off = al16(off + TILE * esz);
@@ -107,8 +130,8 @@ __host__ __device__ inline SmemLayout smem_layout(int nx, int ldx, int ldu, int 
   s.tmp2 = off; off = al16(off + TILE * esz);
   s.tmp3 = off; off = al16(off + TILE * esz);
   s.red = off; off = al16(off + NT * esz);
-  s.part = off; off = al16(off + 16 * 8);
-  s.perm = off; off = al16(off + TILE * 4);
+  s.part = off; off = al16(off + (16 + MAXCS_SMEM * 8) * 8);
+  s.perm = off; off = al16(off + 2 * TILE * 4);
   s.flag = off; off = al16(off + 16 * 4);
   s.total = off;
   return s;
@@ -121,12 +144,26 @@ struct Ctx {
   int s, e, L;
   bool active, first, last;
   T *gemm, *gj, *gjbuf, *ring;
-  T *zS, *yS, *wS, *cS, *lS, *kS, *dS, *xS, *uS, *pe, *xs, *slotL, *slotX, *tmp1, *tmp2, *tmp3, *red;
+  T *zS, *yS, *wS, *lS, *xS, *ktS, *vS, *dS, *uS, *pe, *xs, *slotL, *slotX, *tmp1, *tmp2, *tmp3, *red;
   double* part;
   int *perm, *flag;
   T* scr;   // per-CTA global scratch: 6 matrices nx x ldx
   int msz;  // nx * ldx
+  unsigned long long* prof;  // non-null only in thread 0 of rank 0 of QP 0 when profiling
+  long long t_last;
 };
+
+// Phase timers (debug aid; compiled in, inactive unless SolveArgs.prof is set).
+enum Phase { PH_P1 = 0, PH_BWD, PH_SYNC1, PH_P3, PH_FWD, PH_SYNC2, PH_P5, PH_CHECK, PH_RHO, PH_R1, PH_R2, PH_R3,
+             PH_R4, PH_R5, PH_R6, PH_KKT, PH_COUNT };
+template <typename T>
+__device__ inline void prof_mark(Ctx<T>& c, int ph) {
+  if (c.prof) {
+    const long long now = clock64();
+    c.prof[ph] += (unsigned long long)(now - c.t_last);
+    c.t_last = now;
+  }
+}
 
 template <typename T> __device__ inline T* TP(void* p) { return reinterpret_cast<T*>(p); }
 
@@ -173,16 +210,17 @@ __device__ void g_mvT(const T* M, int ld, int rows, int cols, const T* x, T alph
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __noinline__ int combine_full(Ctx<T>& c, const T* lP, const T* lA, const T* lC, const T* rP, const T* rA,
-                            const T* rC, T* oP, T* oA, T* oC) {
+                                         const T* rC, T* oP, T* oA, T* oC) {
   const int n = c.d->nx, ld = c.d->ldx;
   T* X = c.scr;
   T* Psi = c.scr + c.msz;
   T* V = c.scr + 2 * c.msz;
   T* U = c.scr + 3 * c.msz;
+  T* Wm = c.scr + 4 * c.msz;
   cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm);
-  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, c.gjbuf, c.perm, c.flag);
-  cta_gemm<T>(n, n, n, T(1), c.gj, GJ_LD, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), rA, ld, false, c.gj, GJ_LD, false, T(0), nullptr, 0, false, Psi, ld, c.gemm);
+  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, Wm, ld, c.gjbuf, c.perm, c.flag);
+  cta_gemm<T>(n, n, n, T(1), Wm, ld, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), rA, ld, false, Wm, ld, false, T(0), nullptr, 0, false, Psi, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), Psi, ld, false, lA, ld, false, T(0), nullptr, 0, false, oA, ld, c.gemm);
@@ -197,9 +235,10 @@ __device__ __noinline__ int combine_complete(Ctx<T>& c, const T* lP, const T* lA
   const int n = c.d->nx, ld = c.d->ldx;
   T* X = c.scr;
   T* V = c.scr + 2 * c.msz;
+  T* Wm = c.scr + 4 * c.msz;
   cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm);
-  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, c.gjbuf, c.perm, c.flag);
-  cta_gemm<T>(n, n, n, T(1), c.gj, GJ_LD, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
+  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, Wm, ld, c.gjbuf, c.perm, c.flag);
+  cta_gemm<T>(n, n, n, T(1), Wm, ld, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm);
   return bad;
@@ -256,8 +295,7 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       cta_gemm<T>(nx, nx, nc, rho, Ci, ldx, true, Ci, ldx, false, T(1), Q + (size_t)i * msz, ldx, false, Pl, ldx, c.gemm);
       cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm);
       cta_gemm<T>(nu, nx, nc, rho, Di, ldu, true, Ci, ldx, false, T(1), S + (size_t)i * nu * ldx, ldx, false, Shi, ldx, c.gemm);
-      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, c.gjbuf, c.perm, c.flag);
-      cta_copy<T>(nu, nu, c.gj, GJ_LD, false, Rhii, ldu);
+      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Rhii, ldu, c.gjbuf, c.perm, c.flag);
       // s0 = R^-1 S^ ; P~ = Q^ - S^^T s0 ; A~ = A - B s0 ; s1 = B R^-1 ; C~ = s1 B^T
       cta_gemm<T>(nu, nx, nu, T(1), Rhii, ldu, false, Shi, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm);
       cta_gemm<T>(nx, nx, nu, T(-1), Shi, ldx, true, s0, ldx, false, T(1), Pl, ldx, false, Pl, ldx, c.gemm);
@@ -273,6 +311,7 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
     }
   }
   cl.sync();
+  prof_mark(c, PH_R1);
 
   // R2: up-sweep.  Block (d, m) covers leaves [m 2^d, min((m+1) 2^d, n)); the
   // last block of every level contains the terminal leaf and is complete.
@@ -295,6 +334,7 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
     }
     cl.sync();
   }
+  prof_mark(c, PH_R2);
   // R3: down-sweep of inclusive complete suffixes I(d, m) at block starts:
   // left children inherit the parent's, right children combine their own
   // block with the suffix after the parent block.
@@ -305,21 +345,27 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
   cl.sync();
   for (int lv = d.nlev - 1; lv >= 0; --lv) {
     const int nd = level_count(n, lv), nd1 = level_count(n, lv + 1);
-    for (int m = c.rank; m < nd; m += c.cs) {
+    // right children m = 2p+1 (the combines) spread evenly, then the copies
+    const int nright = nd / 2;
+    for (int p = c.rank; p < nright; p += c.cs) {
+      const int m = 2 * p + 1;
       const size_t oi = (size_t)node_index(n, lv, m) * msz;
-      const int p = m >> 1;
-      if ((m & 1) == 0) {
-        const size_t pi = (size_t)node_index(n, lv + 1, p) * msz;
-        cta_copy<T>(nx, nx, IP + pi, ldx, false, IP + oi, ldx);
-      } else if (p + 1 < nd1) {
+      if (p + 1 < nd1) {
         const size_t si = (size_t)node_index(n, lv + 1, p + 1) * msz;
         bad |= combine_complete<T>(c, VP + oi, VA + oi, VC + oi, IP + si, IP + oi);
       } else {
         cta_copy<T>(nx, nx, VP + oi, ldx, false, IP + oi, ldx);
       }
     }
+    const int nleft = (nd + 1) / 2;
+    for (int p = (c.rank + nright) % c.cs; p < nleft; p += c.cs) {
+      const size_t oi = (size_t)node_index(n, lv, 2 * p) * msz;
+      const size_t pi = (size_t)node_index(n, lv + 1, p) * msz;
+      cta_copy<T>(nx, nx, IP + pi, ldx, false, IP + oi, ldx);
+    }
     cl.sync();
   }
+  prof_mark(c, PH_R3);
   // R4: gains (eq. controller_cache) and the per-stage iteration operators.
   if (c.active) {
     for (int i = c.s; i < c.e; ++i) {
@@ -336,8 +382,7 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       // Gamma^-1 = R^ + s0 B  (R^ rebuilt)
       cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm);
       cta_gemm<T>(nu, nu, nx, T(1), s0, ldx, false, Bi, ldu, false, T(1), c.gj, GJ_LD, false, c.gj, GJ_LD, c.gemm);
-      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, c.gjbuf, c.perm, c.flag);
-      cta_copy<T>(nu, nu, c.gj, GJ_LD, false, Gi, ldu);
+      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Gi, ldu, c.gjbuf, c.perm, c.flag);
       // s1 = S^ + s0 A ; K = -Gamma s1
       cta_gemm<T>(nu, nx, nx, T(1), s0, ldx, false, Ai, ldx, false, T(1), Sh + (size_t)i * nu * ldx, ldx, false, s1, ldx, c.gemm);
       cta_gemm<T>(nu, nx, nu, T(-1), Gi, ldu, false, s1, ldx, false, T(0), nullptr, 0, false, Ki, ldx, c.gemm);
@@ -362,9 +407,46 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       g_mvT<T>(Ki, ldx, nu, nx, c.tmp1, T(1), true, c.tmp2);          // += K^T r
       for (int j = threadIdx.x; j < nx; j += NT) c0[(size_t)i * ldx + j] = c.tmp2[j] + q[(size_t)i * ldx + j];
       __syncthreads();
+      // bundles of the cached iteration (layouts: see bundle_sizes)
+      const int ldv = d.ldv, ldf = d.ldf, R = nx + nc;
+      int bws, fws, cds;
+      bundle_sizes(nx, nu, nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
+      T* bw = TP<T>(d.BW) + (size_t)i * bws;
+      T* fw = TP<T>(d.FW) + (size_t)i * fws;
+      T* cd = TP<T>(d.CD) + (size_t)i * cds;
+      const T* CKi = CK + (size_t)i * nc * ldx;
+      const T* Fi = F + (size_t)i * nu * ldx;
+      const T* Ji = J + (size_t)i * nu * ldc;
+      for (int e2 = threadIdx.x; e2 < R * ldx; e2 += NT) {
+        const int rr = e2 / ldx, j = e2 - rr * ldx;
+        bw[e2] = (j >= nx) ? T(0) : (rr < nx ? Abi[(size_t)rr * ldx + j] : CKi[(size_t)(rr - nx) * ldx + j]);
+      }
+      T* fjt = bw + (size_t)R * ldx;           // [F | J]^T : row r, column a
+      for (int e2 = threadIdx.x; e2 < R * ldu; e2 += NT) {
+        const int rr = e2 / ldu, a = e2 - rr * ldu;
+        fjt[e2] = a >= nu ? T(0) : (rr < nx ? Fi[(size_t)a * ldx + rr] : Ji[(size_t)a * ldc + rr - nx]);
+      }
+      T* c0b = fjt + (size_t)R * ldu;
+      for (int j = threadIdx.x; j < ldx; j += NT) c0b[j] = j < nx ? c0[(size_t)i * ldx + j] : T(0);
+      for (int a = threadIdx.x; a < ldu; a += NT) c0b[ldx + a] = a < nu ? k0[(size_t)i * ldu + a] : T(0);
+      // FW^T: row cc < nx+nu (input index), column r < nx+nc (output index)
+      for (int e2 = threadIdx.x; e2 < (nx + nu) * ldv; e2 += NT) {
+        const int cc = e2 / ldv, r2 = e2 - cc * ldv;
+        T v = T(0);
+        if (r2 < nx) v = cc < nx ? Abi[(size_t)r2 * ldx + cc] : Bi[(size_t)r2 * ldu + cc - nx];
+        else if (r2 < R) v = cc < nx ? CKi[(size_t)(r2 - nx) * ldx + cc] : Di[(size_t)(r2 - nx) * ldu + cc - nx];
+        fw[e2] = v;
+      }
+      for (int j = threadIdx.x; j < ldx; j += NT) fw[(size_t)(nx + nu) * ldv + j] = j < nx ? bb[(size_t)i * ldx + j] : T(0);
+      for (int e2 = threadIdx.x; e2 < nc * ldf; e2 += NT) {
+        const int rr = e2 / ldf, j = e2 - rr * ldf;
+        cd[e2] = j < nx ? Ci[(size_t)rr * ldx + j] : (j < nx + nu ? Di[(size_t)rr * ldu + j - nx] : T(0));
+      }
+      __syncthreads();
     }
   }
   cl.sync();
+  prof_mark(c, PH_R4);
   // R5: chunk products.  Backward (not needed in the last chunk):
   //   FPi_i = F_i Pi_{i+1},  Pi_i = Abar_i^T Pi_{i+1},  Pi_e = I,  T_r = Pi_s.
   // Forward (not needed in the first chunk):
@@ -375,11 +457,12 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       T* Pc = c.scr;
       T* Pn2 = c.scr + c.msz;
       const int i1 = c.e - 1;
-      cta_copy<T>(nu, nx, F + (size_t)i1 * nu * ldx, ldx, false, FPi + (size_t)i1 * nu * ldx, ldx);
+      // FPi stored transposed: FPi_i^T = Pi_{i+1}^T F_i^T  (nx x ldu)
+      cta_copy<T>(nu, nx, F + (size_t)i1 * nu * ldx, ldx, true, FPi + (size_t)i1 * nx * ldu, ldu);
       cta_copy<T>(nx, nx, Abar + (size_t)i1 * msz, ldx, true, Pc, ldx);
       for (int i = c.e - 2; i >= c.s; --i) {
-        cta_gemm<T>(nu, nx, nx, T(1), F + (size_t)i * nu * ldx, ldx, false, Pc, ldx, false, T(0), nullptr, 0, false,
-                    FPi + (size_t)i * nu * ldx, ldx, c.gemm);
+        cta_gemm<T>(nx, nu, nx, T(1), Pc, ldx, true, F + (size_t)i * nu * ldx, ldx, true, T(0), nullptr, 0, false,
+                    FPi + (size_t)i * nx * ldu, ldu, c.gemm);
         cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)i * msz, ldx, true, Pc, ldx, false, T(0), nullptr, 0, false, Pn2,
                     ldx, c.gemm);
         T* t_ = Pc; Pc = Pn2; Pn2 = t_;
@@ -389,15 +472,16 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
     if (!c.first) {
       cta_eye<T>(nx, Sig + (size_t)c.s * msz, ldx);
       cta_copy<T>(nu, nx, K + (size_t)c.s * nu * ldx, ldx, false, KSig + (size_t)c.s * nu * ldx, ldx);
-      cta_copy<T>(nc, nx, CK + (size_t)c.s * nc * ldx, ldx, false, CKSig + (size_t)c.s * nc * ldx, ldx);
+      // CKSig stored transposed: CKSig_i^T = Sig_i^T CK_i^T  (nx x ldc)
+      cta_copy<T>(nc, nx, CK + (size_t)c.s * nc * ldx, ldx, true, CKSig + (size_t)c.s * nx * ldc, ldc);
       for (int i = c.s + 1; i < c.e; ++i) {
         T* Si = Sig + (size_t)i * msz;
         cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)(i - 1) * msz, ldx, false, Sig + (size_t)(i - 1) * msz, ldx, false,
                     T(0), nullptr, 0, false, Si, ldx, c.gemm);
         cta_gemm<T>(nu, nx, nx, T(1), K + (size_t)i * nu * ldx, ldx, false, Si, ldx, false, T(0), nullptr, 0, false,
                     KSig + (size_t)i * nu * ldx, ldx, c.gemm);
-        cta_gemm<T>(nc, nx, nx, T(1), CK + (size_t)i * nc * ldx, ldx, false, Si, ldx, false, T(0), nullptr, 0, false,
-                    CKSig + (size_t)i * nc * ldx, ldx, c.gemm);
+        cta_gemm<T>(nx, nc, nx, T(1), Si, ldx, true, CK + (size_t)i * nc * ldx, ldx, true, T(0), nullptr, 0, false,
+                    CKSig + (size_t)i * nx * ldc, ldc, c.gemm);
       }
       T* Ur = Uch + (size_t)c.rank * msz;
       cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)(c.e - 1) * msz, ldx, false, Sig + (size_t)(c.e - 1) * msz, ldx,
@@ -409,24 +493,28 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
     }
   }
   cl.sync();
+  prof_mark(c, PH_R5);
   // R6: chunk-boundary operators Theta_{r,m} = T_{r+1} ... T_{m-1} (m >= r+2)
   // and Xi_{r,m} = U_{r-1} ... U_{m+1} (m <= r-2).
   if (c.active) {
     const int r0 = c.rank, nch = d.nch;
+    // stored transposed: Theta_{r,m}^T = T_{m-1}^T Theta_{r,m-1}^T, Xi_{r,m-1}^T = U_m^T Xi_{r,m}^T
     for (int m = r0 + 2; m < nch; ++m) {
       T* Th = Theta + (size_t)(r0 * MAXCS + m) * msz;
-      if (m == r0 + 2) cta_copy<T>(nx, nx, Tch + (size_t)(r0 + 1) * msz, ldx, false, Th, ldx);
-      else cta_gemm<T>(nx, nx, nx, T(1), Theta + (size_t)(r0 * MAXCS + m - 1) * msz, ldx, false,
-                       Tch + (size_t)(m - 1) * msz, ldx, false, T(0), nullptr, 0, false, Th, ldx, c.gemm);
+      if (m == r0 + 2) cta_copy<T>(nx, nx, Tch + (size_t)(r0 + 1) * msz, ldx, true, Th, ldx);
+      else cta_gemm<T>(nx, nx, nx, T(1), Tch + (size_t)(m - 1) * msz, ldx, true,
+                       Theta + (size_t)(r0 * MAXCS + m - 1) * msz, ldx, false, T(0), nullptr, 0, false, Th, ldx, c.gemm);
     }
     for (int m = r0 - 2; m >= 0; --m) {
       T* X = Xi + (size_t)(r0 * MAXCS + m) * msz;
-      if (m == r0 - 2) cta_copy<T>(nx, nx, Uch + (size_t)(r0 - 1) * msz, ldx, false, X, ldx);
-      else cta_gemm<T>(nx, nx, nx, T(1), Xi + (size_t)(r0 * MAXCS + m + 1) * msz, ldx, false,
-                       Uch + (size_t)(m + 1) * msz, ldx, false, T(0), nullptr, 0, false, X, ldx, c.gemm);
+      if (m == r0 - 2) cta_copy<T>(nx, nx, Uch + (size_t)(r0 - 1) * msz, ldx, true, X, ldx);
+      else cta_gemm<T>(nx, nx, nx, T(1), Uch + (size_t)(m + 1) * msz, ldx, true,
+                       Xi + (size_t)(r0 * MAXCS + m + 1) * msz, ldx, false, T(0), nullptr, 0, false, X, ldx, c.gemm);
     }
   }
-  return cluster_or<T>(c, cl, bad);
+  const int res = cluster_or<T>(c, cl, bad);
+  prof_mark(c, PH_R6);
+  return res;
 }
 
 }  // namespace gsls

@@ -36,7 +36,7 @@ class qp_settings(C.Structure):
     _fields_ = [("rho0", C.c_double), ("eps", C.c_double), ("eps_kkt", C.c_double), ("rho_min", C.c_double),
                 ("rho_max", C.c_double), ("sigma", C.c_int32), ("check_every", C.c_int32),
                 ("max_iter", C.c_int32), ("precision", C.c_int32), ("cluster", C.c_int32),
-                ("fixed_iters", C.c_int32)]
+                ("fixed_iters", C.c_int32), ("pad", C.c_int32), ("eps_floor", C.c_double)]
 
 
 class qp_info(C.Structure):
@@ -62,7 +62,8 @@ SIGNATURES = {
     "qp_solve": (C.c_int, [P, DP, C.c_int32, C.c_double, DP, DP, DP, C.POINTER(qp_info)]),
     "qp_set_warm_start": (C.c_int, [P, DP, DP, C.POINTER(C.c_double)]),
     "qp_get_state": (C.c_int, [P, DP, DP, C.POINTER(C.c_double)]),
-    "qp_update": (C.c_int, [P, DP, DP, DP, DP]),
+    "qp_update": (C.c_int, [P, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP]),
+    "qp_reset": (C.c_int, [P]),
     "qp_kkt": (C.c_int, [P, DP, DP, DP, DP, C.POINTER(C.c_double)]),
     "qp_riccati": (C.c_int, [P, DP, DP]),
     "qp_destroy": (None, [P]),
