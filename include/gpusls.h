@@ -170,6 +170,40 @@ int qp_riccati(qp_handle* h, double* P, double* K);
 
 void qp_destroy(qp_handle* h);
 
+/* ------------------------------------------------------------------------ */
+/* SLS controller synthesis and reachability margins (Sec. III-C, IV-B)     */
+/* ------------------------------------------------------------------------ */
+typedef struct sls_handle sls_handle;
+
+/* sls_setup: workspace for SLS problems of dims d (nx, nu, N, nc stage rows,
+ * nf terminal rows).  per_j_tau != 0 prepares one controller problem per
+ * disturbance index j (costs depending on tau_{k,j}, eq.
+ * sls_cost_matrices_tau); per_j_tau == 0 shares one problem (tau = 0).
+ * precision: GPUSLS_FP64 or GPUSLS_FP32.  Allocates all device memory. */
+int sls_setup(sls_handle** h, qp_dims d, int32_t precision, int32_t per_j_tau, void* stream);
+
+/* sls_solve: the SLS controller QP (eq. fastsls_qp) by per-j reverse scans
+ * (eq. robust_combin, eq. backward_prop) and forward propagation
+ * (eq. forward_prop), plus the margins of Sec. III-C.
+ *   A [N][nx][nx]  B [N][nx][nu]  E [N][nx][nx] (disturbance scaling E_j)
+ *   Qbar [nx][nx]  Rbar [nu][nu]  QbarN [nx][nx]   (SPD)
+ *   C [N][nc][nx]  D [N][nc][nu]  CN [nf][nx]
+ *   tau [N+1][N][max(nc, nf)] or NULL (zero): tau[k][j][:nc] for stage k < N,
+ *       tau[N][j][:nf] terminal; requires a per_j_tau handle when non-NULL.
+ * Outputs (any may be NULL):
+ *   Phi_x [N*nx][N*nx]: block row k-1 (k = 1..N), block column j = Phi_x_{k,j}
+ *         (zero for k <= j; Phi_x_{j+1,j} = E_j)
+ *   Phi_u [N*nu][N*nx]: block row k (k = 0..N-1), block column j = Phi_u_{k,j}
+ *   h [N][nc]: h_k = sum_{j<k} ||C_k Phi_x_{k,j} + D_k Phi_u_{k,j}||_{2,row}
+ *   hf [nf]:   h^f = sum_{j<N} ||C_N Phi_x_{N,j}||_{2,row}
+ * All arrays are device float64. */
+int sls_solve(sls_handle* h, const double* A, const double* B, const double* E,
+              const double* Qbar, const double* Rbar, const double* QbarN,
+              const double* C, const double* D, const double* CN, const double* tau,
+              double* Phi_x, double* Phi_u, double* hk, double* hf);
+
+void sls_destroy(sls_handle* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -171,3 +171,46 @@ class QPBatch:
             self.close()
         except Exception:
             pass
+
+
+class SLS:
+    """SLS controller synthesis and reachability margins (sls_setup / sls_solve)."""
+
+    def __init__(self, nx, nu, N, nc, nf, per_j_tau: bool, precision=native.GPUSLS_FP64, stream=None,
+                 device="cuda"):
+        self.lib = native.load()
+        self.dims = (nx, nu, N, nc, nf)
+        self.device = device
+        d = native.qp_dims(nx, nu, N, nc, nf)
+        h = C.c_void_p()
+        native.check(self.lib.sls_setup(C.byref(h), d, int(precision), int(bool(per_j_tau)), _stream_ptr(stream)),
+                     "sls_setup")
+        self.h = h
+
+    def solve(self, sp, fetch=True):
+        nx, nu, N, nc, nf = self.dims
+        f = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(self.device)
+        t = dict(A=f(sp.A), B=f(sp.B), E=f(sp.E), Qbar=f(sp.Qbar), Rbar=f(sp.Rbar), QbarN=f(sp.QbarN),
+                 C=f(sp.C), D=f(sp.D), CN=f(sp.CN), tau=f(sp.tau))
+        Phix = torch.empty(N * nx, N * nx, dtype=torch.float64, device=self.device)
+        Phiu = torch.empty(N * nu, N * nx, dtype=torch.float64, device=self.device)
+        h = torch.empty(max(1, N * nc), dtype=torch.float64, device=self.device)
+        hf = torch.empty(max(1, nf), dtype=torch.float64, device=self.device)
+        native.check(self.lib.sls_solve(self.h, *[_dptr(t[k]) for k in ("A", "B", "E", "Qbar", "Rbar", "QbarN", "C",
+                                                                          "D", "CN", "tau")],
+                                        _dptr(Phix), _dptr(Phiu), _dptr(h), _dptr(hf)), "sls_solve")
+        if not fetch:
+            return None
+        return (Phix.cpu().numpy(), Phiu.cpu().numpy(), h.cpu().numpy()[:N * nc].reshape(N, nc),
+                hf.cpu().numpy()[:nf])
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.lib.sls_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,51 @@
+// Host-side internals shared by the solver and the SLS front end (not part
+// of the public C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gpusls.h"
+#include "qp_kernel.cuh"
+
+namespace gsls {
+
+struct PackJob {
+  const double* src;  // null: zero fill
+  void* dst;
+  int count, rows, cols, ld;
+};
+
+struct QPOffsets {
+  size_t A, B, c, Q, R, S, q, r, C, D, CN, lohi, x0, dx, du, P, K;
+};
+
+}  // namespace gsls
+
+struct qp_handle {
+  int batch = 0;
+  std::vector<qp_dims> dims;
+  std::vector<gsls::QPOffsets> off;   // offsets into the caller's pools (elements)
+  qp_settings set;
+  cudaStream_t stream = nullptr;
+  int esz = 8;                  // bytes of the solve precision
+  int cs = 1;
+  int smem = 0;
+  void* tpool = nullptr;        // solve-precision workspace
+  double* dpool = nullptr;      // FP64 workspace
+  gsls::QPDesc* ddesc = nullptr;      // device descriptors
+  std::vector<gsls::QPDesc> hdesc;
+  int* info_i = nullptr;
+  double* info_d = nullptr;
+  gsls::PackJob* djobs = nullptr;
+  size_t njobs_cap = 0;
+  std::vector<void*> tx0;       // per-QP x0 (solve precision)
+  double* rho0_dev = nullptr;   // [batch] setup penalties (qp_reset)
+};
+
+namespace gsls {
+int set_error(int code, const std::string& msg);
+// Factorization only (MODE_RICCATI) without copying results out.
+int qp_refactor_internal(qp_handle* h);
+}  // namespace gsls

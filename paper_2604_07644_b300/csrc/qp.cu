@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/gpusls.h"
+#include "internal.h"
 #include "qp_iter.cuh"
 
 namespace gsls {
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   if (args.mode == MODE_RICCATI) {
     // P_i = level-0 inclusive suffixes, K_i gains, as FP64 dense blocks.
     const int nx = d.nx, nu = d.nu, ldx = d.ldx, msz = c.msz;
-    if (c.active) {
+    if (c.active && d.ox && d.ou) {
       const int iend = c.e + (c.last ? 1 : 0);
       for (int i = c.s; i < iend; ++i)
         for (int e2 = t; e2 < nx * nx; e2 += NT)
@@ -214,11 +215,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
 // ---------------------------------------------------------------------------
 // packing FP64 caller arrays into padded solve-precision layouts
 // ---------------------------------------------------------------------------
-struct PackJob {
-  const double* src;  // null: zero fill
-  void* dst;
-  int count, rows, cols, ld;
-};
+
 
 template <typename T>
 __global__ void pack_kernel(const PackJob* __restrict__ jobs) {
@@ -246,37 +243,12 @@ static int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+int gsls::set_error(int code, const std::string& msg) { return fail(code, msg); }
 #define CU(x)                                                                                \
   do {                                                                                       \
     cudaError_t e_ = (x);                                                                    \
     if (e_ != cudaSuccess) return fail(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
-
-struct QPOffsets {
-  size_t A, B, c, Q, R, S, q, r, C, D, CN, lohi, x0, dx, du, P, K;
-};
-
-struct qp_handle {
-  int batch = 0;
-  std::vector<qp_dims> dims;
-  std::vector<QPOffsets> off;   // offsets into the caller's pools (elements)
-  qp_settings set;
-  cudaStream_t stream = nullptr;
-  int esz = 8;                  // bytes of the solve precision
-  int cs = 1;
-  int smem = 0;
-  void* tpool = nullptr;        // solve-precision workspace
-  double* dpool = nullptr;      // FP64 workspace
-  QPDesc* ddesc = nullptr;      // device descriptors
-  std::vector<QPDesc> hdesc;
-  int* info_i = nullptr;
-  double* info_d = nullptr;
-  PackJob* djobs = nullptr;
-  size_t njobs_cap = 0;
-  // per-QP pointers kept for conversions
-  std::vector<void*> tx0;
-  double* rho0_dev = nullptr;   // [batch] setup penalties (qp_reset)
-};
 
 static size_t al64(size_t x) { return (x + 63) & ~(size_t)63; }
 
@@ -681,6 +653,17 @@ extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double to
 extern "C" int qp_riccati(qp_handle* h, double* P, double* K) {
   if (!h || !P || !K) return fail(GPUSLS_ERR_INVALID, "qp_riccati: null argument");
   int st = set_outputs(h, P, K, nullptr, 0, 0, true);
+  if (st) return st;
+  SolveArgs a = {};
+  a.mode = MODE_RICCATI;
+  a.cs = h->cs;
+  st = launch(h, a);
+  if (st) return st;
+  return collect(h, nullptr);
+}
+
+int gsls::qp_refactor_internal(qp_handle* h) {
+  int st = set_outputs(h, nullptr, nullptr, nullptr, 0, 0, true);
   if (st) return st;
   SolveArgs a = {};
   a.mode = MODE_RICCATI;

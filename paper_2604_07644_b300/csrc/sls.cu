@@ -1,0 +1,382 @@
+// SLS controller synthesis and reachability margins (Sec. III-C, Sec. IV-B)
+// on top of the batched tree-scan factorization of qp.cu.
+//
+//   1. sls_build_kernel forms, for every disturbance index j, the LQR data of
+//      the j-th controller problem (eq. fastsls_qp): stages k = j+1 .. N-1
+//      with costs Qx = Qbar + C^T diag(tau) C, Qu = Rbar + D^T diag(tau) D,
+//      Qux = D^T diag(tau) C and terminal Qx_N = QbarN + C_N^T diag(tau) C_N
+//      (eq. sls_cost_matrices_tau).  With tau = 0 the costs do not depend on j
+//      and one problem over stages 1 .. N-1 serves every j.
+//   2. The reverse scans over the horizon (eq. robust_combin, the homogeneous
+//      case of eq. combination_rules) and the gains K_k^(j) (eq. backward_prop)
+//      run as one batched launch of the QP factorization kernel, one cluster
+//      per problem.
+//   3. sls_phi_kernel, one CTA per j, propagates Phi_x_{k+1,j} =
+//      (A_k + B_k K_k^(j)) Phi_x_{k,j} from Phi_x_{j+1,j} = E_j and
+//      Phi_u_{k,j} = K_k^(j) Phi_x_{k,j} (eq. forward_prop), and the row norms
+//      of C_k Phi_x_{k,j} + D_k Phi_u_{k,j}; sls_margin_kernel sums them over j
+//      in a fixed order into h_k and h^f (the tightenings of Sec. III-C).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/gpusls.h"
+#include "dense.cuh"
+#include "internal.h"
+
+using namespace gsls;
+
+#define CUS(x)                                                                                      \
+  do {                                                                                              \
+    cudaError_t e_ = (x);                                                                           \
+    if (e_ != cudaSuccess) return set_error(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct sls_handle {
+  qp_dims d{};
+  int precision = 0;
+  int per_j = 0;
+  int esz = 8;
+  cudaStream_t stream = nullptr;
+  qp_handle* qh = nullptr;   // internal batch of LQR problems (nc = nf = 0)
+  int nq = 0;
+  // FP64 pools of the internal problems (dense layouts)
+  double *pA = nullptr, *pB = nullptr, *pQ = nullptr, *pR = nullptr, *pS = nullptr, *dummy = nullptr;
+  size_t nA = 0, nB = 0, nQ = 0, nR = 0, nS = 0;
+  // solve-precision copies of E, C, D, CN (padded) and per-j scratch
+  void *ET = nullptr, *CT = nullptr, *DT = nullptr, *CNT = nullptr, *scr = nullptr;
+  double *rn = nullptr, *rnf = nullptr;   // row norms [N][N][nc], [N][nf]
+  int ldx = 0, ldu = 0;
+};
+
+namespace gsls {
+
+struct SLSBuild {
+  const double *A, *B, *Qbar, *Rbar, *QbarN, *C, *D, *CN, *tau;
+  double *pA, *pB, *pQ, *pR, *pS;
+  int nx, nu, N, nc, nf, tw, per_j, nq;
+};
+
+// One CTA per (problem q, local stage i <= N_q): copies A_k, B_k and forms the
+// cost blocks of stage k = first(q) + i (i == N_q: terminal) in FP64.
+__global__ void sls_build_kernel(SLSBuild a) {
+  const int q = blockIdx.y, i = blockIdx.x;
+  const int first = a.per_j ? q + 1 : 1;
+  const int Nq = a.N - first;
+  if (i > Nq) return;
+  const int j = a.per_j ? q : 0;
+  const int nx = a.nx, nu = a.nu, nc = a.nc, nf = a.nf;
+  // offsets of problem q in the pools: problems are laid out in order
+  size_t oA = 0, oQ = 0, oR = 0;
+  for (int qq = 0; qq < q; ++qq) {
+    const int n = a.N - (a.per_j ? qq + 1 : 1);
+    oA += (size_t)n;
+    oQ += (size_t)n + 1;
+  }
+  oR = oA;
+  const int k = first + i;
+  const double* tau = nullptr;
+  if (a.tau) tau = a.tau + ((size_t)k * a.N + j) * a.tw;
+  const int t = threadIdx.x;
+  if (i < Nq) {
+    double* Ad = a.pA + (oA + i) * nx * nx;
+    double* Bd = a.pB + (oA + i) * nx * nu;
+    for (int e = t; e < nx * nx; e += blockDim.x) Ad[e] = a.A[(size_t)k * nx * nx + e];
+    for (int e = t; e < nx * nu; e += blockDim.x) Bd[e] = a.B[(size_t)k * nx * nu + e];
+    const double* Ck = a.C + (size_t)k * nc * nx;
+    const double* Dk = a.D + (size_t)k * nc * nu;
+    double* Qd = a.pQ + (oQ + i) * nx * nx;
+    double* Rd = a.pR + (oR + i) * nu * nu;
+    double* Sd = a.pS + (oR + i) * nu * nx;
+    for (int e = t; e < nx * nx; e += blockDim.x) {
+      const int r = e / nx, c = e - r * nx;
+      double v = a.Qbar[e];
+      if (tau)
+        for (int l = 0; l < nc; ++l) v += Ck[l * nx + r] * tau[l] * Ck[l * nx + c];
+      Qd[e] = v;
+    }
+    for (int e = t; e < nu * nu; e += blockDim.x) {
+      const int r = e / nu, c = e - r * nu;
+      double v = a.Rbar[e];
+      if (tau)
+        for (int l = 0; l < nc; ++l) v += Dk[l * nu + r] * tau[l] * Dk[l * nu + c];
+      Rd[e] = v;
+    }
+    for (int e = t; e < nu * nx; e += blockDim.x) {
+      const int r = e / nx, c = e - r * nx;
+      double v = 0.0;
+      if (tau)
+        for (int l = 0; l < nc; ++l) v += Dk[l * nu + r] * tau[l] * Ck[l * nx + c];
+      Sd[e] = v;
+    }
+  } else {
+    double* Qd = a.pQ + (oQ + Nq) * nx * nx;
+    for (int e = t; e < nx * nx; e += blockDim.x) {
+      const int r = e / nx, c = e - r * nx;
+      double v = a.QbarN[e];
+      if (tau)
+        for (int l = 0; l < nf; ++l) v += a.CN[l * nx + r] * tau[l] * a.CN[l * nx + c];
+      Qd[e] = v;
+    }
+  }
+}
+
+// FP64 dense [count][rows][cols] -> solve precision [count][rows][ld] (zero padded)
+template <typename T>
+__global__ void sls_convert_kernel(const double* __restrict__ src, T* __restrict__ dst, int count, int rows, int cols,
+                                   int ld) {
+  const size_t total = (size_t)count * rows * ld;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t ri = e / ld;
+    const int c = (int)(e - ri * ld);
+    dst[e] = c < cols ? (T)src[ri * cols + c] : T(0);
+  }
+}
+
+struct SLSPhi {
+  const QPDesc* descs;
+  const void *ET, *CT, *DT, *CNT;
+  void* scr;
+  double *Phix, *Phiu, *rn, *rnf;
+  int nx, nu, N, nc, nf, ldx, ldu, per_j;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 1) sls_phi_kernel(SLSPhi a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* gm = reinterpret_cast<T*>(smem);
+  const int j = blockIdx.x;
+  const int nx = a.nx, nu = a.nu, N = a.N, nc = a.nc, nf = a.nf, ldx = a.ldx, ldu = a.ldu;
+  const int msz = nx * ldx;
+  const int NX = N * nx;
+  const int t = threadIdx.x, w = t >> 5, l = t & 31;
+  T* X0 = reinterpret_cast<T*>(a.scr) + (size_t)j * (2 * msz + (nc > nf ? nc : nf) * ldx + nu * ldx + 16);
+  T* X1 = X0 + msz;
+  T* Xu = X1 + msz;
+  T* M = Xu + nu * ldx;
+  const T* ET = reinterpret_cast<const T*>(a.ET);
+  const T* CT = reinterpret_cast<const T*>(a.CT);
+  const T* DT = reinterpret_cast<const T*>(a.DT);
+  const T* CNT = reinterpret_cast<const T*>(a.CNT);
+  // Phi_x_{j+1,j} = E_j
+  cta_copy<T>(nx, nx, ET + (size_t)j * msz, ldx, false, X0, ldx);
+  const int q = a.per_j ? j : 0;
+  const int first = a.per_j ? j + 1 : 1;
+  const QPDesc* dq = (j + 1 < N || !a.per_j) ? &a.descs[q] : nullptr;
+  T* cur = X0;
+  T* nxt = X1;
+  for (int k = j + 1; k <= N; ++k) {
+    // write Phi_x_{k,j} (block row k-1, block column j)
+    if (a.Phix)
+      for (int e = t; e < nx * nx; e += NT) {
+        const int r = e / nx, c = e - r * nx;
+        a.Phix[(size_t)((k - 1) * nx + r) * NX + (size_t)j * nx + c] = (double)cur[r * ldx + c];
+      }
+    if (k == N) {
+      // terminal margin rows: C_N Phi_x_{N,j}
+      if (nf > 0) {
+        cta_gemm<T>(nf, nx, nx, T(1), CNT, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, M, ldx, gm);
+        for (int r = w; r < nf; r += NT / 32) {
+          T s2 = T(0);
+          for (int c = l; c < nx; c += 32) s2 += M[r * ldx + c] * M[r * ldx + c];
+          s2 = warp_sum(s2);
+          if (l == 0) a.rnf[(size_t)j * nf + r] = sqrt((double)s2);
+        }
+        __syncthreads();
+      }
+      break;
+    }
+    const int i = k - first;   // local stage of problem q
+    const T* Kk = reinterpret_cast<const T*>(dq->K) + (size_t)i * nu * ldx;
+    const T* Ab = reinterpret_cast<const T*>(dq->Abar) + (size_t)i * msz;
+    // Phi_u_{k,j} = K_k^(j) Phi_x_{k,j}
+    cta_gemm<T>(nu, nx, nx, T(1), Kk, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, Xu, ldx, gm);
+    if (a.Phiu)
+      for (int e = t; e < nu * nx; e += NT) {
+        const int r = e / nx, c = e - r * nx;
+        a.Phiu[(size_t)(k * nu + r) * NX + (size_t)j * nx + c] = (double)Xu[r * ldx + c];
+      }
+    // margin rows: C_k Phi_x + D_k Phi_u
+    if (nc > 0) {
+      cta_gemm<T>(nc, nx, nx, T(1), CT + (size_t)k * nc * ldx, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, M,
+                  ldx, gm);
+      cta_gemm<T>(nc, nx, nu, T(1), DT + (size_t)k * nc * ldu, ldu, false, Xu, ldx, false, T(1), M, ldx, false, M, ldx,
+                  gm);
+      for (int r = w; r < nc; r += NT / 32) {
+        T s2 = T(0);
+        for (int c = l; c < nx; c += 32) s2 += M[r * ldx + c] * M[r * ldx + c];
+        s2 = warp_sum(s2);
+        if (l == 0) a.rn[((size_t)k * N + j) * nc + r] = sqrt((double)s2);
+      }
+      __syncthreads();
+    }
+    // Phi_x_{k+1,j} = (A_k + B_k K_k^(j)) Phi_x_{k,j}
+    cta_gemm<T>(nx, nx, nx, T(1), Ab, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, nxt, ldx, gm);
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+}
+
+// h_k[c] = sum_{j<k} rn[k][j][c] (j ascending), h^f[c] = sum_j rnf[j][c].
+__global__ void sls_margin_kernel(const double* __restrict__ rn, const double* __restrict__ rnf, double* h, double* hf,
+                                  int N, int nc, int nf) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < N * nc) {
+    const int k = e / nc, c = e - k * nc;
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += rn[((size_t)k * N + j) * nc + c];
+    if (h) h[e] = s;
+  } else if (e < N * nc + nf) {
+    const int c = e - N * nc;
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) s += rnf[(size_t)j * nf + c];
+    if (hf) hf[c] = s;
+  }
+}
+
+}  // namespace gsls
+
+extern "C" int sls_setup(sls_handle** out, qp_dims d, int32_t precision, int32_t per_j_tau, void* stream) {
+  if (!out) return set_error(GPUSLS_ERR_INVALID, "sls_setup: null handle pointer");
+  if (d.nx < 1 || d.nx > TILE || d.nu < 1 || d.nu > 32 || d.nc < 0 || d.nc > 64 || d.nf < 0 || d.nf > 64 || d.N < 1 ||
+      d.N > 512)
+    return set_error(GPUSLS_ERR_INVALID, "sls_setup: dims out of range");
+  if (precision != GPUSLS_FP64 && precision != GPUSLS_FP32)
+    return set_error(GPUSLS_ERR_INVALID, "sls_setup: unknown precision");
+  sls_handle* h = new sls_handle();
+  h->d = d;
+  h->precision = precision;
+  h->per_j = per_j_tau ? 1 : 0;
+  h->esz = precision == GPUSLS_FP64 ? 8 : 4;
+  h->stream = (cudaStream_t)stream;
+  h->ldx = rup4(d.nx);
+  h->ldu = rup4(d.nu);
+  const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf;
+  h->nq = N >= 2 ? (h->per_j ? N - 1 : 1) : 0;
+  std::vector<qp_dims> dims;
+  for (int q = 0; q < h->nq; ++q) {
+    const int first = h->per_j ? q + 1 : 1;
+    dims.push_back({nx, nu, N - first, 0, 0});
+    h->nA += (size_t)(N - first);
+    h->nQ += (size_t)(N - first) + 1;
+  }
+  auto alloc = [&](double** p, size_t n) { return cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(double)); };
+  const int esz = h->esz;
+  cudaError_t e = cudaSuccess;
+  e = (cudaError_t)(e | alloc(&h->pA, h->nA * nx * nx));
+  e = (cudaError_t)(e | alloc(&h->pB, h->nA * nx * nu));
+  e = (cudaError_t)(e | alloc(&h->pQ, h->nQ * nx * nx));
+  e = (cudaError_t)(e | alloc(&h->pR, h->nA * nu * nu));
+  e = (cudaError_t)(e | alloc(&h->pS, h->nA * nu * nx));
+  const size_t nzero = std::max<size_t>(std::max(h->nQ * nx, h->nA * nu), (size_t)std::max(N * nx, 16));
+  e = (cudaError_t)(e | alloc(&h->dummy, nzero));
+  e = (cudaError_t)(e | cudaMalloc(&h->ET, (size_t)N * nx * h->ldx * esz + 256));
+  e = (cudaError_t)(e | cudaMalloc(&h->CT, (size_t)N * std::max(nc, 1) * h->ldx * esz + 256));
+  e = (cudaError_t)(e | cudaMalloc(&h->DT, (size_t)N * std::max(nc, 1) * h->ldu * esz + 256));
+  e = (cudaError_t)(e | cudaMalloc(&h->CNT, (size_t)std::max(nf, 1) * h->ldx * esz + 256));
+  e = (cudaError_t)(e | cudaMalloc(&h->scr, (size_t)N * (2 * nx * h->ldx + std::max(nc, nf) * h->ldx + nu * h->ldx + 16) *
+                                                   esz + 256));
+  e = (cudaError_t)(e | alloc(&h->rn, (size_t)N * N * std::max(nc, 1)));
+  e = (cudaError_t)(e | alloc(&h->rnf, (size_t)N * std::max(nf, 1)));
+  if (e != cudaSuccess) {
+    sls_destroy(h);
+    return set_error(GPUSLS_ERR_CUDA, "sls_setup: cudaMalloc failed");
+  }
+  cudaMemsetAsync(h->pA, 0, std::max<size_t>(h->nA * nx * nx, 1) * sizeof(double), h->stream);
+  cudaMemsetAsync(h->pB, 0, std::max<size_t>(h->nA * nx * nu, 1) * sizeof(double), h->stream);
+  cudaMemsetAsync(h->pQ, 0, std::max<size_t>(h->nQ * nx * nx, 1) * sizeof(double), h->stream);
+  cudaMemsetAsync(h->pR, 0, std::max<size_t>(h->nA * nu * nu, 1) * sizeof(double), h->stream);
+  cudaMemsetAsync(h->pS, 0, std::max<size_t>(h->nA * nu * nx, 1) * sizeof(double), h->stream);
+  cudaMemsetAsync(h->dummy, 0, nzero * sizeof(double), h->stream);
+  if (h->nq > 0) {
+    qp_settings s;
+    qp_default_settings(&s);
+    s.precision = precision;
+    s.cluster = 0;
+    // placeholder data (zeros); every solve overwrites all problem data and
+    // refactors before any use
+    int st = qp_batch_setup(&h->qh, h->nq, dims.data(), h->pA, h->pB, h->dummy, h->pQ, h->pR, h->pS, h->dummy,
+                            h->dummy, nullptr, nullptr, nullptr, h->dummy, h->dummy, nullptr, &s, stream);
+    if (st) {
+      sls_destroy(h);
+      return st;
+    }
+  }
+  *out = h;
+  return GPUSLS_OK;
+}
+
+extern "C" int sls_solve(sls_handle* h, const double* A, const double* B, const double* E, const double* Qbar,
+                         const double* Rbar, const double* QbarN, const double* C, const double* D, const double* CN,
+                         const double* tau, double* Phi_x, double* Phi_u, double* hk, double* hf) {
+  if (!h || !A || !B || !E || !Qbar || !Rbar || !QbarN) return set_error(GPUSLS_ERR_INVALID, "sls_solve: null argument");
+  const qp_dims d = h->d;
+  const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf;
+  if ((nc > 0 && (!C || !D)) || (nf > 0 && !CN)) return set_error(GPUSLS_ERR_INVALID, "sls_solve: C/D/CN missing");
+  if (tau && !h->per_j) return set_error(GPUSLS_ERR_INVALID, "sls_solve: tau given to a handle set up without per-j tau");
+  cudaStream_t st = h->stream;
+  const size_t NX = (size_t)N * nx;
+  if (Phi_x) CUS(cudaMemsetAsync(Phi_x, 0, NX * NX * sizeof(double), st));
+  if (Phi_u) CUS(cudaMemsetAsync(Phi_u, 0, (size_t)N * nu * NX * sizeof(double), st));
+  // 1. LQR data of every controller problem (cost blocks from tau)
+  if (h->nq > 0) {
+    SLSBuild a = {A, B, Qbar, Rbar, QbarN, C, D, CN, tau, h->pA, h->pB, h->pQ, h->pR, h->pS,
+                  nx, nu, N, nc, nf, std::max(nc, nf), h->per_j, h->nq};
+    dim3 grid(N, h->nq);
+    sls_build_kernel<<<grid, 256, 0, st>>>(a);
+    CUS(cudaGetLastError());
+    int s2 = qp_update(h->qh, h->pA, h->pB, nullptr, h->pQ, h->pR, h->pS, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       nullptr, nullptr);
+    if (s2) return s2;
+    // 2. reverse scans over the horizon and gains for every problem
+    s2 = qp_refactor_internal(h->qh);
+    if (s2) return s2;
+  }
+  // solve-precision copies of E, C, D, CN
+  const int ldx = h->ldx, ldu = h->ldu;
+  auto conv = [&](const double* src, void* dst, int count, int rows, int cols, int ld) {
+    if (!src || count * rows == 0) return;
+    if (h->esz == 8)
+      sls_convert_kernel<double><<<64, 256, 0, st>>>(src, (double*)dst, count, rows, cols, ld);
+    else
+      sls_convert_kernel<float><<<64, 256, 0, st>>>(src, (float*)dst, count, rows, cols, ld);
+  };
+  conv(E, h->ET, N, nx, nx, ldx);
+  conv(C, h->CT, N, nc, nx, ldx);
+  conv(D, h->DT, N, nc, nu, ldu);
+  conv(CN, h->CNT, 1, nf, nx, ldx);
+  CUS(cudaGetLastError());
+  // 3. Phi and margin row norms, one CTA per disturbance index j
+  SLSPhi p = {h->qh ? h->qh->ddesc : nullptr, h->ET, h->CT, h->DT, h->CNT, h->scr, Phi_x, Phi_u, h->rn, h->rnf,
+              nx, nu, N, nc, nf, ldx, ldu, h->per_j};
+  const int smem = 2 * KT * TILE * h->esz;
+  if (h->esz == 8) {
+    CUS(cudaFuncSetAttribute(sls_phi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    sls_phi_kernel<double><<<N, NT, smem, st>>>(p);
+  } else {
+    CUS(cudaFuncSetAttribute(sls_phi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    sls_phi_kernel<float><<<N, NT, smem, st>>>(p);
+  }
+  CUS(cudaGetLastError());
+  const int tot = N * nc + nf;
+  if (tot > 0) {
+    sls_margin_kernel<<<(tot + 255) / 256, 256, 0, st>>>(h->rn, h->rnf, hk, hf, N, nc, nf);
+    CUS(cudaGetLastError());
+  }
+  CUS(cudaStreamSynchronize(st));
+  return GPUSLS_OK;
+}
+
+extern "C" void sls_destroy(sls_handle* h) {
+  if (!h) return;
+  if (h->qh) qp_destroy(h->qh);
+  for (double* p : {h->pA, h->pB, h->pQ, h->pR, h->pS, h->dummy, h->rn, h->rnf})
+    if (p) cudaFree(p);
+  for (void* p : {h->ET, h->CT, h->DT, h->CNT, h->scr})
+    if (p) cudaFree(p);
+  delete h;
+}

@@ -44,10 +44,6 @@ class qp_info(C.Structure):
                 ("rho", C.c_double), ("r_prim", C.c_double), ("r_dual", C.c_double), ("kkt", C.c_double)]
 
 
-class sls_dims(C.Structure):
-    _fields_ = [("nx", C.c_int32), ("nu", C.c_int32), ("N", C.c_int32), ("nc", C.c_int32), ("nf", C.c_int32)]
-
-
 P = C.c_void_p
 DP = C.c_void_p   # device pointer to double
 
@@ -67,6 +63,9 @@ SIGNATURES = {
     "qp_kkt": (C.c_int, [P, DP, DP, DP, DP, C.POINTER(C.c_double)]),
     "qp_riccati": (C.c_int, [P, DP, DP]),
     "qp_destroy": (None, [P]),
+    "sls_setup": (C.c_int, [C.POINTER(P), qp_dims, C.c_int32, C.c_int32, P]),
+    "sls_solve": (C.c_int, [P, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP]),
+    "sls_destroy": (None, [P]),
 }
 
 _lock = threading.Lock()

@@ -17,7 +17,7 @@ def libpath():
 def test_library_loads_and_exports_header_symbols(libpath):
     lib = ctypes.CDLL(libpath)
     names = native.header_symbols()
-    assert "qp_setup" in names and "qp_solve" in names
+    assert "qp_setup" in names and "qp_solve" in names and "sls_solve" in names
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, f"declared in gpusls.h but not exported: {missing}"
 
