@@ -204,6 +204,44 @@ int sls_solve(sls_handle* h, const double* A, const double* B, const double* E,
 
 void sls_destroy(sls_handle* h);
 
+/* ------------------------------------------------------------------------ */
+/* Learned warm start (no counterpart in the paper)                         */
+/* ------------------------------------------------------------------------ */
+/* A two-hidden-layer ReLU MLP  h1 = relu(X W1^T + b1), h2 = relu(h1 W2^T + b2),
+ * Y = h2 W3^T + b3, trained on the GPU with the MSE loss (1/2B) sum (Y - T)^2
+ * on normalized inputs/targets and Adam (beta 0.9/0.999, eps 1e-8).  Every
+ * GEMM runs on the tensor cores with BF16 operands (rounded to nearest even
+ * from the FP32 values) and FP32 accumulation; weights, biases and Adam
+ * moments are FP32.  All float arrays below are DEVICE float32, row-major:
+ * W1 [hidden][n_in], W2 [hidden][hidden], W3 [n_out][hidden], X [B][n_in],
+ * T, Y [B][n_out].  Errors: GPUSLS_ERR_INVALID for bad sizes/pointers,
+ * GPUSLS_ERR_CUDA for runtime failures. */
+typedef struct mlp_handle mlp_handle;
+
+int mlp_create(mlp_handle** h, int32_t n_in, int32_t hidden, int32_t n_out, int32_t max_batch, void* stream);
+/* copy parameters in (restarts Adam) / out (NULL entries skipped) */
+int mlp_set_params(mlp_handle* h, const float* W1, const float* b1, const float* W2, const float* b2,
+                   const float* W3, const float* b3);
+int mlp_get_params(mlp_handle* h, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3);
+/* per-column mean / standard deviation of X [count][n_in] and T [count][n_out]
+ * used to normalize inputs and targets (identity until called) */
+int mlp_fit_normalization(mlp_handle* h, const float* X, const float* T, int32_t count);
+/* Y = denormalized network output for raw inputs X (B <= max_batch) */
+int mlp_forward(mlp_handle* h, const float* X, int32_t B, float* Y);
+/* gradients of the loss at ALREADY-normalized (Xn, Tn) into grads (device,
+ * the concatenation W1, b1, W2, b2, W3, b3) and the loss (HOST float*, may be NULL) */
+int mlp_gradients(mlp_handle* h, const float* Xn, const float* Tn, int32_t B, float* grads, float* loss);
+/* one Adam step on a minibatch of raw (X, T); loss: HOST float* or NULL */
+int mlp_train_step(mlp_handle* h, const float* X, const float* T, int32_t B, float lr, float* loss);
+void mlp_destroy(mlp_handle* h);
+
+/* qp_warm_start_mlp: evaluate the network on features [batch][n_in] (one row
+ * per QP of q; n_out must be 2 m + 1 with m = N nc + nf) and set every QP's
+ * ADMM state: z = clamp(Y[0:m], lo, hi), rho = clamp(exp(Y[2m]), rho_min,
+ * rho_max), y = Y[m:2m] / rho (Y[m:2m] predicts the unscaled multiplier).
+ * Runs on the network's stream; give both handles the same stream. */
+int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max);
+
 #ifdef __cplusplus
 }
 #endif

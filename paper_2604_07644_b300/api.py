@@ -214,3 +214,72 @@ class SLS:
             self.close()
         except Exception:
             pass
+
+
+class MLP:
+    """The warm-start network (mlp_* in include/gpusls.h); FP32 device tensors."""
+
+    def __init__(self, n_in, hidden, n_out, max_batch, stream=None, device="cuda"):
+        self.lib = native.load()
+        self.n_in, self.hidden, self.n_out, self.max_batch = n_in, hidden, n_out, max_batch
+        self.device = device
+        self.stream = stream
+        h = C.c_void_p()
+        native.check(self.lib.mlp_create(C.byref(h), n_in, hidden, n_out, max_batch, _stream_ptr(stream)),
+                     "mlp_create")
+        self.h = h
+
+    def shapes(self):
+        i, hdn, o = self.n_in, self.hidden, self.n_out
+        return [(hdn, i), (hdn,), (hdn, hdn), (hdn,), (o, hdn), (o,)]
+
+    def set_params(self, params):
+        ts = [torch.as_tensor(np.ascontiguousarray(p, dtype=np.float32)).to(self.device) for p in params]
+        native.check(self.lib.mlp_set_params(self.h, *[_dptr(t) for t in ts]), "mlp_set_params")
+
+    def get_params(self):
+        ts = [torch.empty(shp, dtype=torch.float32, device=self.device) for shp in self.shapes()]
+        native.check(self.lib.mlp_get_params(self.h, *[_dptr(t) for t in ts]), "mlp_get_params")
+        return [t.cpu().numpy() for t in ts]
+
+    def fit_normalization(self, X: torch.Tensor, T: torch.Tensor):
+        native.check(self.lib.mlp_fit_normalization(self.h, _dptr(X), _dptr(T), X.shape[0]), "mlp_fit_normalization")
+
+    def forward(self, X: torch.Tensor) -> torch.Tensor:
+        Y = torch.empty(X.shape[0], self.n_out, dtype=torch.float32, device=self.device)
+        native.check(self.lib.mlp_forward(self.h, _dptr(X), X.shape[0], _dptr(Y)), "mlp_forward")
+        return Y
+
+    def gradients(self, Xn: torch.Tensor, Tn: torch.Tensor):
+        n = sum(int(np.prod(s)) for s in self.shapes())
+        g = torch.empty(n, dtype=torch.float32, device=self.device)
+        loss = C.c_float()
+        native.check(self.lib.mlp_gradients(self.h, _dptr(Xn), _dptr(Tn), Xn.shape[0], _dptr(g), C.byref(loss)),
+                     "mlp_gradients")
+        out, o, host = [], 0, g.cpu().numpy()
+        for shp in self.shapes():
+            k = int(np.prod(shp))
+            out.append(host[o:o + k].reshape(shp))
+            o += k
+        return out, loss.value
+
+    def train_step(self, X: torch.Tensor, T: torch.Tensor, lr: float) -> float:
+        loss = C.c_float()
+        native.check(self.lib.mlp_train_step(self.h, _dptr(X), _dptr(T), X.shape[0], float(lr), C.byref(loss)),
+                     "mlp_train_step")
+        return loss.value
+
+    def warm_start(self, qb: "QPBatch", features: torch.Tensor, rho_min=1e-3, rho_max=1e3):
+        native.check(self.lib.qp_warm_start_mlp(qb.h, self.h, _dptr(features), rho_min, rho_max),
+                     "qp_warm_start_mlp")
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.lib.mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

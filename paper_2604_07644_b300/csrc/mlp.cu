@@ -1,0 +1,460 @@
+// Learned ADMM warm start: a 2-hidden-layer ReLU MLP trained and evaluated on
+// the GPU by the library's own kernels (no counterpart in the paper).
+//
+//   h1 = relu(X W1^T + b1), h2 = relu(h1 W2^T + b2), Y = h2 W3^T + b3
+//   loss = (1 / 2B) sum (Y - T)^2 on normalized inputs/targets
+//
+// Every GEMM runs on the tensor cores (mma.sync m16n8k16, BF16 operands,
+// FP32 accumulation): operands are FP32 in global memory and rounded to BF16
+// (round to nearest even) when staged in shared memory.  Master weights and
+// the Adam moments stay FP32.  The network maps the features of a QP
+// instance (x0 and linearization parameters) to (z, lambda, log rho); the
+// warm-start kernel projects z onto the bounds, clamps rho and sets
+// y = lambda / rho in the QP handle's ADMM state.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/gpusls.h"
+#include "internal.h"
+
+using namespace gsls;
+
+#define CUM(x)                                                                                      \
+  do {                                                                                              \
+    cudaError_t e_ = (x);                                                                           \
+    if (e_ != cudaSuccess) return set_error(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct mlp_handle {
+  int n_in = 0, hid = 0, n_out = 0, maxb = 0;
+  cudaStream_t stream = nullptr;
+  float* P = nullptr;   // params: W1 [hid][n_in], b1, W2 [hid][hid], b2, W3 [n_out][hid], b3
+  float* G = nullptr;   // gradients (same layout)
+  float* Mm = nullptr;  // Adam first moment
+  float* Vm = nullptr;  // Adam second moment
+  size_t np = 0;
+  size_t oW1, ob1, oW2, ob2, oW3, ob3;
+  int step = 0;
+  // activations [maxb][.]
+  float *Xn, *Z1, *H1, *Z2, *H2, *Y, *dY, *dH, *dZ;
+  float *xm, *xs, *ym, *ys;   // normalization
+  float* loss;                // [1]
+};
+
+namespace gsls {
+
+// ---------------------------------------------------------------------------
+// BF16 tensor-core GEMM (mma.sync m16n8k16), generic strides:
+//   C[m][n] = alpha * sum_k A(m,k) B(k,n) + beta * Cin[m][n] + bias[n]
+//   A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], all FP32 in memory.
+// 64 x 64 tile per CTA, 4 warps of 32 x 32, k-slab 32.
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+  const float* A;
+  const float* B;
+  const float* Cin;
+  const float* bias;
+  float* C;
+  int M, N, K;
+  long long sam, sak, sbk, sbn;
+  int ldc, ldcin;
+  float alpha, beta;
+};
+
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__device__ inline unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat16 a = __float2bfloat16_rn(lo);
+  const __nv_bfloat16 b = __float2bfloat16_rn(hi);
+  return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
+}
+
+__global__ void __launch_bounds__(128) mlp_gemm_kernel(GemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int wm = w >> 1, wn = w & 1;
+  const int gid = lane >> 2, tq = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  for (int k0 = 0; k0 < g.K; k0 += GBK) {
+    // stage A tile (m, k) and B tile (n, k) as BF16
+    for (int e = t; e < GBM * GBK; e += 128) {
+      int m, kk;
+      if (g.sak == 1) { m = e / GBK; kk = e % GBK; } else { kk = e / GBM; m = e % GBM; }
+      const int gm = m0 + m, gk = k0 + kk;
+      float v = 0.f;
+      if (gm < g.M && gk < g.K) v = g.A[gm * g.sam + gk * g.sak];
+      As[m][kk] = __float2bfloat16_rn(v);
+    }
+    for (int e = t; e < GBN * GBK; e += 128) {
+      int n, kk;
+      if (g.sbk == 1) { n = e / GBK; kk = e % GBK; } else { kk = e / GBN; n = e % GBN; }
+      const int gn = n0 + n, gk = k0 + kk;
+      float v = 0.f;
+      if (gn < g.N && gk < g.K) v = g.B[gk * g.sbk + gn * g.sbn];
+      Bs[n][kk] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < GBK; ks += 16) {
+      unsigned af[2][4], bfr[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int r = wm * 32 + mi * 16 + gid;
+        af[mi][0] = *reinterpret_cast<const unsigned*>(&As[r][ks + 2 * tq]);
+        af[mi][1] = *reinterpret_cast<const unsigned*>(&As[r + 8][ks + 2 * tq]);
+        af[mi][2] = *reinterpret_cast<const unsigned*>(&As[r][ks + 2 * tq + 8]);
+        af[mi][3] = *reinterpret_cast<const unsigned*>(&As[r + 8][ks + 2 * tq + 8]);
+      }
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const int c = wn * 32 + ni * 8 + gid;
+        bfr[ni][0] = *reinterpret_cast<const unsigned*>(&Bs[c][ks + 2 * tq]);
+        bfr[ni][1] = *reinterpret_cast<const unsigned*>(&Bs[c][ks + 2 * tq + 8]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};\n"
+              : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+              : "r"(af[mi][0]), "r"(af[mi][1]), "r"(af[mi][2]), "r"(af[mi][3]), "r"(bfr[ni][0]), "r"(bfr[ni][1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int m = m0 + wm * 32 + mi * 16 + gid + (c >= 2 ? 8 : 0);
+        const int n = n0 + wn * 32 + ni * 8 + 2 * tq + (c & 1);
+        if (m < g.M && n < g.N) {
+          float v = g.alpha * acc[mi][ni][c];
+          if (g.Cin) v += g.beta * g.Cin[(size_t)m * g.ldcin + n];
+          if (g.bias) v += g.bias[n];
+          g.C[(size_t)m * g.ldc + n] = v;
+        }
+      }
+}
+
+// elementwise helpers
+__global__ void relu_kernel(const float* __restrict__ Z, float* __restrict__ H, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    H[i] = fmaxf(Z[i], 0.f);
+}
+__global__ void relu_mask_kernel(const float* __restrict__ dH, const float* __restrict__ Z, float* __restrict__ dZ,
+                                 size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dZ[i] = Z[i] > 0.f ? dH[i] : 0.f;
+}
+// column sums of an [rows][cols] matrix into out[cols] (fixed order per column)
+__global__ void colsum_kernel(const float* __restrict__ X, float* __restrict__ out, int rows, int cols) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.f;
+  for (int r = 0; r < rows; ++r) s += X[(size_t)r * cols + c];
+  out[c] = s;
+}
+// normalize rows: out = (X - mean) / std, or out = X * std + mean (inverse)
+__global__ void affine_rows_kernel(const float* __restrict__ X, float* __restrict__ out, const float* __restrict__ mean,
+                                   const float* __restrict__ sd, int rows, int cols, int inverse) {
+  const size_t n = (size_t)rows * cols;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % cols);
+    out[i] = inverse ? X[i] * sd[c] + mean[c] : (X[i] - mean[c]) / sd[c];
+  }
+}
+// dY = (Y - T) / B ; loss partial sums of (Y - T)^2 (one block, fixed order)
+__global__ void mse_kernel(const float* __restrict__ Y, const float* __restrict__ T, float* __restrict__ dY,
+                           float* loss, int B, int n) {
+  __shared__ float red[256];
+  const size_t tot = (size_t)B * n;
+  float s = 0.f;
+  for (size_t i = threadIdx.x; i < tot; i += blockDim.x) {
+    const float d = Y[i] - T[i];
+    dY[i] = d / (float)B;
+    s += d * d;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = 0.5f * red[0] / (float)B;
+}
+__global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
+                            float* __restrict__ V, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float g = G[i];
+    const float m = b1 * M[i] + (1.f - b1) * g;
+    const float v = b2 * V[i] + (1.f - b2) * g * g;
+    M[i] = m;
+    V[i] = v;
+    P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+  }
+}
+// per-column mean and standard deviation over rows (std floored at 1e-6)
+__global__ void moments_kernel(const float* __restrict__ X, float* mean, float* sd, int rows, int cols) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double s = 0.0, s2 = 0.0;
+  for (int r = 0; r < rows; ++r) {
+    const double v = X[(size_t)r * cols + c];
+    s += v;
+    s2 += v * v;
+  }
+  const double mu = s / rows;
+  const double var = fmax(s2 / rows - mu * mu, 0.0);
+  mean[c] = (float)mu;
+  sd[c] = (float)fmax(sqrt(var), 1e-6);
+}
+
+}  // namespace gsls
+
+static int gemm(cudaStream_t st, const float* A, long long sam, long long sak, const float* B, long long sbk,
+                long long sbn, float* C, int ldc, int M, int N, int K, const float* bias = nullptr,
+                const float* Cin = nullptr, int ldcin = 0, float alpha = 1.f, float beta = 0.f) {
+  GemmArgs g = {A, B, Cin, bias, C, M, N, K, sam, sak, sbk, sbn, ldc, ldcin, alpha, beta};
+  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+  mlp_gemm_kernel<<<grid, 128, 0, st>>>(g);
+  CUM(cudaGetLastError());
+  return GPUSLS_OK;
+}
+
+static int blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); }
+
+// forward on normalized inputs Xn [B][n_in] -> h->Y (normalized outputs)
+static int forward(mlp_handle* h, const float* Xn, int B) {
+  const float* P = h->P;
+  int st = 0;
+  st |= gemm(h->stream, Xn, h->n_in, 1, P + h->oW1, 1, h->n_in, h->Z1, h->hid, B, h->hid, h->n_in, P + h->ob1);
+  relu_kernel<<<blocks((size_t)B * h->hid), 256, 0, h->stream>>>(h->Z1, h->H1, (size_t)B * h->hid);
+  st |= gemm(h->stream, h->H1, h->hid, 1, P + h->oW2, 1, h->hid, h->Z2, h->hid, B, h->hid, h->hid, P + h->ob2);
+  relu_kernel<<<blocks((size_t)B * h->hid), 256, 0, h->stream>>>(h->Z2, h->H2, (size_t)B * h->hid);
+  st |= gemm(h->stream, h->H2, h->hid, 1, P + h->oW3, 1, h->hid, h->Y, h->n_out, B, h->n_out, h->hid, P + h->ob3);
+  CUM(cudaGetLastError());
+  return st ? GPUSLS_ERR_CUDA : GPUSLS_OK;
+}
+
+// gradients of the MSE loss for normalized (Xn, Tn) into h->G
+static int backward(mlp_handle* h, const float* Xn, const float* Tn, int B) {
+  const float* P = h->P;
+  float* G = h->G;
+  int st = forward(h, Xn, B);
+  mse_kernel<<<1, 256, 0, h->stream>>>(h->Y, Tn, h->dY, h->loss, B, h->n_out);
+  // layer 3: gW3 = dY^T H2 [n_out][hid], gb3 = colsum dY, dH2 = dY W3 [B][hid]
+  st |= gemm(h->stream, h->dY, 1, h->n_out, h->H2, h->hid, 1, G + h->oW3, h->hid, h->n_out, h->hid, B);
+  colsum_kernel<<<(h->n_out + 255) / 256, 256, 0, h->stream>>>(h->dY, G + h->ob3, B, h->n_out);
+  st |= gemm(h->stream, h->dY, h->n_out, 1, P + h->oW3, h->hid, 1, h->dH, h->hid, B, h->hid, h->n_out);
+  relu_mask_kernel<<<blocks((size_t)B * h->hid), 256, 0, h->stream>>>(h->dH, h->Z2, h->dZ, (size_t)B * h->hid);
+  // layer 2
+  st |= gemm(h->stream, h->dZ, 1, h->hid, h->H1, h->hid, 1, G + h->oW2, h->hid, h->hid, h->hid, B);
+  colsum_kernel<<<(h->hid + 255) / 256, 256, 0, h->stream>>>(h->dZ, G + h->ob2, B, h->hid);
+  st |= gemm(h->stream, h->dZ, h->hid, 1, P + h->oW2, h->hid, 1, h->dH, h->hid, B, h->hid, h->hid);
+  relu_mask_kernel<<<blocks((size_t)B * h->hid), 256, 0, h->stream>>>(h->dH, h->Z1, h->dZ, (size_t)B * h->hid);
+  // layer 1
+  st |= gemm(h->stream, h->dZ, 1, h->hid, Xn, h->n_in, 1, G + h->oW1, h->n_in, h->hid, h->n_in, B);
+  colsum_kernel<<<(h->hid + 255) / 256, 256, 0, h->stream>>>(h->dZ, G + h->ob1, B, h->hid);
+  CUM(cudaGetLastError());
+  return st ? GPUSLS_ERR_CUDA : GPUSLS_OK;
+}
+
+extern "C" int mlp_create(mlp_handle** out, int32_t n_in, int32_t hidden, int32_t n_out, int32_t max_batch,
+                          void* stream) {
+  if (!out || n_in < 1 || hidden < 1 || n_out < 1 || max_batch < 1)
+    return set_error(GPUSLS_ERR_INVALID, "mlp_create: invalid dimensions");
+  mlp_handle* h = new mlp_handle();
+  h->n_in = n_in;
+  h->hid = hidden;
+  h->n_out = n_out;
+  h->maxb = max_batch;
+  h->stream = (cudaStream_t)stream;
+  h->oW1 = 0;
+  h->ob1 = h->oW1 + (size_t)hidden * n_in;
+  h->oW2 = h->ob1 + hidden;
+  h->ob2 = h->oW2 + (size_t)hidden * hidden;
+  h->oW3 = h->ob2 + hidden;
+  h->ob3 = h->oW3 + (size_t)n_out * hidden;
+  h->np = h->ob3 + n_out;
+  const size_t B = max_batch;
+  size_t act = B * n_in + 4 * B * hidden + 2 * B * n_out + 2 * B * std::max(hidden, n_out);
+  float* base = nullptr;
+  const size_t tot = 4 * h->np + act + 2 * (size_t)n_in + 2 * (size_t)n_out + 16;
+  if (cudaMalloc(&base, tot * sizeof(float)) != cudaSuccess) {
+    delete h;
+    return set_error(GPUSLS_ERR_CUDA, "mlp_create: cudaMalloc failed");
+  }
+  cudaMemsetAsync(base, 0, tot * sizeof(float), h->stream);
+  float* p = base;
+  auto take = [&](size_t n) { float* r = p; p += n; return r; };
+  h->P = take(h->np); h->G = take(h->np); h->Mm = take(h->np); h->Vm = take(h->np);
+  h->Xn = take(B * n_in); h->Z1 = take(B * hidden); h->H1 = take(B * hidden); h->Z2 = take(B * hidden);
+  h->H2 = take(B * hidden); h->Y = take(B * n_out); h->dY = take(B * n_out);
+  h->dH = take(B * std::max(hidden, n_out)); h->dZ = take(B * std::max(hidden, n_out));
+  h->xm = take(n_in); h->xs = take(n_in); h->ym = take(n_out); h->ys = take(n_out); h->loss = take(16);
+  // identity normalization until mlp_fit_normalization / mlp_set_normalization
+  std::vector<float> ones(std::max(n_in, n_out), 1.f);
+  cudaMemcpyAsync(h->xs, ones.data(), n_in * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+  cudaMemcpyAsync(h->ys, ones.data(), n_out * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+  cudaStreamSynchronize(h->stream);
+  *out = h;
+  return GPUSLS_OK;
+}
+
+static int params_io(mlp_handle* h, float* const* dst, const float* const* src, bool set) {
+  const size_t offs[6] = {h->oW1, h->ob1, h->oW2, h->ob2, h->oW3, h->ob3};
+  const size_t cnt[6] = {(size_t)h->hid * h->n_in, (size_t)h->hid, (size_t)h->hid * h->hid, (size_t)h->hid,
+                         (size_t)h->n_out * h->hid, (size_t)h->n_out};
+  for (int i = 0; i < 6; ++i) {
+    if (set) {
+      if (!src[i]) return set_error(GPUSLS_ERR_INVALID, "mlp_set_params: null parameter");
+      CUM(cudaMemcpyAsync(h->P + offs[i], src[i], cnt[i] * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    } else if (dst[i]) {
+      CUM(cudaMemcpyAsync(dst[i], h->P + offs[i], cnt[i] * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    }
+  }
+  if (set) {   // new parameters restart the optimizer state
+    CUM(cudaMemsetAsync(h->Mm, 0, h->np * sizeof(float), h->stream));
+    CUM(cudaMemsetAsync(h->Vm, 0, h->np * sizeof(float), h->stream));
+    h->step = 0;
+  }
+  CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+extern "C" int mlp_set_params(mlp_handle* h, const float* W1, const float* b1, const float* W2, const float* b2,
+                              const float* W3, const float* b3) {
+  if (!h) return set_error(GPUSLS_ERR_INVALID, "mlp_set_params: null handle");
+  const float* src[6] = {W1, b1, W2, b2, W3, b3};
+  return params_io(h, nullptr, src, true);
+}
+
+extern "C" int mlp_get_params(mlp_handle* h, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3) {
+  if (!h) return set_error(GPUSLS_ERR_INVALID, "mlp_get_params: null handle");
+  float* dst[6] = {W1, b1, W2, b2, W3, b3};
+  return params_io(h, dst, nullptr, false);
+}
+
+extern "C" int mlp_fit_normalization(mlp_handle* h, const float* X, const float* T, int32_t count) {
+  if (!h || !X || !T || count < 1) return set_error(GPUSLS_ERR_INVALID, "mlp_fit_normalization: invalid argument");
+  moments_kernel<<<(h->n_in + 127) / 128, 128, 0, h->stream>>>(X, h->xm, h->xs, count, h->n_in);
+  moments_kernel<<<(h->n_out + 127) / 128, 128, 0, h->stream>>>(T, h->ym, h->ys, count, h->n_out);
+  CUM(cudaGetLastError());
+  CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+extern "C" int mlp_forward(mlp_handle* h, const float* X, int32_t B, float* Y) {
+  if (!h || !X || !Y || B < 1 || B > h->maxb) return set_error(GPUSLS_ERR_INVALID, "mlp_forward: invalid argument");
+  affine_rows_kernel<<<blocks((size_t)B * h->n_in), 256, 0, h->stream>>>(X, h->Xn, h->xm, h->xs, B, h->n_in, 0);
+  int st = forward(h, h->Xn, B);
+  if (st) return st;
+  affine_rows_kernel<<<blocks((size_t)B * h->n_out), 256, 0, h->stream>>>(h->Y, Y, h->ym, h->ys, B, h->n_out, 1);
+  CUM(cudaGetLastError());
+  CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+extern "C" int mlp_gradients(mlp_handle* h, const float* Xn, const float* Tn, int32_t B, float* grads, float* loss) {
+  if (!h || !Xn || !Tn || B < 1 || B > h->maxb) return set_error(GPUSLS_ERR_INVALID, "mlp_gradients: invalid argument");
+  int st = backward(h, Xn, Tn, B);
+  if (st) return st;
+  if (grads) CUM(cudaMemcpyAsync(grads, h->G, h->np * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  if (loss) CUM(cudaMemcpyAsync(loss, h->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+extern "C" int mlp_train_step(mlp_handle* h, const float* X, const float* T, int32_t B, float lr, float* loss) {
+  if (!h || !X || !T || B < 1 || B > h->maxb) return set_error(GPUSLS_ERR_INVALID, "mlp_train_step: invalid argument");
+  // normalized inputs and targets (targets into dH scratch region sized B * max(hid, n_out))
+  affine_rows_kernel<<<blocks((size_t)B * h->n_in), 256, 0, h->stream>>>(X, h->Xn, h->xm, h->xs, B, h->n_in, 0);
+  float* Tn = h->dZ;   // reuse: backward() overwrites dZ only after mse_kernel consumed Tn
+  affine_rows_kernel<<<blocks((size_t)B * h->n_out), 256, 0, h->stream>>>(T, Tn, h->ym, h->ys, B, h->n_out, 0);
+  int st = backward(h, h->Xn, Tn, B);
+  if (st) return st;
+  h->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
+  adam_kernel<<<blocks(h->np), 256, 0, h->stream>>>(h->P, h->G, h->Mm, h->Vm, h->np, lr, b1, b2, 1e-8f, c1, c2);
+  CUM(cudaGetLastError());
+  if (loss) CUM(cudaMemcpyAsync(loss, h->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+extern "C" void mlp_destroy(mlp_handle* h) {
+  if (!h) return;
+  if (h->P) cudaFree(h->P);
+  delete h;
+}
+
+// ---------------------------------------------------------------------------
+// warm start of a QP handle from the network's output
+// ---------------------------------------------------------------------------
+namespace gsls {
+template <typename T>
+__global__ void warm_assemble_kernel(const QPDesc* __restrict__ descs, const float* __restrict__ Y, int ldy,
+                                     double rho_lo, double rho_hi) {
+  const QPDesc d = descs[blockIdx.x];
+  const float* y = Y + (size_t)blockIdx.x * ldy;
+  const int m = d.m;
+  double rho = exp((double)y[2 * m]);
+  rho = fmin(fmax(rho, rho_lo), rho_hi);
+  T* z = reinterpret_cast<T*>(d.z);
+  T* yy = reinterpret_cast<T*>(d.y);
+  const T* lo = reinterpret_cast<const T*>(d.lo);
+  const T* hi = reinterpret_cast<const T*>(d.hi);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const T zz = fmin(fmax((T)y[i], lo[i]), hi[i]);
+    z[i] = zz;
+    yy[i] = (T)((double)y[m + i] / rho);
+  }
+  if (threadIdx.x == 0) {
+    if (d.rho[0] != rho) d.flags[0] = 0;
+    d.rho[0] = rho;
+  }
+}
+}  // namespace gsls
+
+extern "C" int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max) {
+  if (!q || !h || !features) return set_error(GPUSLS_ERR_INVALID, "qp_warm_start_mlp: null argument");
+  if (q->batch > h->maxb) return set_error(GPUSLS_ERR_INVALID, "qp_warm_start_mlp: batch exceeds the network's max batch");
+  for (int b = 0; b < q->batch; ++b) {
+    const int m = q->dims[b].N * q->dims[b].nc + q->dims[b].nf;
+    if (2 * m + 1 != h->n_out)
+      return set_error(GPUSLS_ERR_INVALID, "qp_warm_start_mlp: network output size must be 2 m + 1 for every QP");
+  }
+  affine_rows_kernel<<<blocks((size_t)q->batch * h->n_in), 256, 0, h->stream>>>(features, h->Xn, h->xm, h->xs,
+                                                                                  q->batch, h->n_in, 0);
+  int st = forward(h, h->Xn, q->batch);
+  if (st) return st;
+  float* Yd = h->dY;   // denormalized outputs
+  affine_rows_kernel<<<blocks((size_t)q->batch * h->n_out), 256, 0, h->stream>>>(h->Y, Yd, h->ym, h->ys, q->batch,
+                                                                                   h->n_out, 1);
+  if (q->esz == 8)
+    warm_assemble_kernel<double><<<q->batch, 256, 0, h->stream>>>(q->ddesc, Yd, h->n_out, rho_min, rho_max);
+  else
+    warm_assemble_kernel<float><<<q->batch, 256, 0, h->stream>>>(q->ddesc, Yd, h->n_out, rho_min, rho_max);
+  CUM(cudaGetLastError());
+  CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}

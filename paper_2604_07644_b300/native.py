@@ -66,6 +66,15 @@ SIGNATURES = {
     "sls_setup": (C.c_int, [C.POINTER(P), qp_dims, C.c_int32, C.c_int32, P]),
     "sls_solve": (C.c_int, [P, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP]),
     "sls_destroy": (None, [P]),
+    "mlp_create": (C.c_int, [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32, C.c_int32, P]),
+    "mlp_set_params": (C.c_int, [P, DP, DP, DP, DP, DP, DP]),
+    "mlp_get_params": (C.c_int, [P, DP, DP, DP, DP, DP, DP]),
+    "mlp_fit_normalization": (C.c_int, [P, DP, DP, C.c_int32]),
+    "mlp_forward": (C.c_int, [P, DP, C.c_int32, DP]),
+    "mlp_gradients": (C.c_int, [P, DP, DP, C.c_int32, DP, C.POINTER(C.c_float)]),
+    "mlp_train_step": (C.c_int, [P, DP, DP, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
+    "mlp_destroy": (None, [P]),
+    "qp_warm_start_mlp": (C.c_int, [P, P, DP, C.c_double, C.c_double]),
 }
 
 _lock = threading.Lock()
