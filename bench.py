@@ -1,11 +1,13 @@
 #!/usr/bin/env python
 """Benchmark: ms per QP solved to a 1e-4 FP64 KKT residual on quadruped-shaped
-(nx=61, nu=12, N=100) LTV-QPs -- the batched GPU solver next to the plain FP64
-single-QP GPU solve and the FP64 CPU oracle.
+(nx=61, nu=12, N=100) LTV-QPs -- the learned-warm-start, batched, FP32 GPU
+solver (headline) next to the same batch solved cold, the plain FP64
+single-QP GPU solve, and the FP64 CPU oracle.
 
-One step = one cold solve (factorization + ADMM iterations + FP64 KKT gate)
-of every QP in the batch.  Problem data for the whole batch stays resident
-on the device (1.2 GB in FP64, larger than L2); `e2e` repeats the step through
+One step = warm-start inference (MLP) + one solve (factorization + ADMM
+iterations + FP64 KKT gate with refinement) of every QP in the batch, from a
+reset state.  Problem data for the whole batch stays resident
+on the device (2.2 GB in FP64 for 256 QPs, larger than L2); `e2e` repeats the step through
 the public API with the problem data copied from pinned host memory and the
 solution copied back inside the timed region.
 
@@ -41,12 +43,14 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpusls", choices=["gpusls", "reference"])
-    p.add_argument("--batch", type=int, default=148)
+    p.add_argument("--batch", type=int, default=256)
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--cluster", type=int, default=8)
     p.add_argument("--plain-qps", type=int, default=2)
     p.add_argument("--cpu-sample", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--fallback", type=int, default=2000)
+    p.add_argument("--model", default=os.path.join(ROOT, "paper_2604_07644_b300", "warmstart_quadruped61.npz"))
     return p.parse_args()
 
 
@@ -193,8 +197,9 @@ def main():
 
     from paper_2604_07644_b300 import build as B_
     from paper_2604_07644_b300 import native
+    from paper_2604_07644_b300 import learned
     from paper_2604_07644_b300 import workloads as W
-    from paper_2604_07644_b300.api import QPBatch, pool
+    from paper_2604_07644_b300.api import QPBatch
 
     assert torch.cuda.is_available(), "bench needs a CUDA device"
     torch.cuda.set_device(local)
@@ -208,42 +213,65 @@ def main():
     base = 100000 + rank * args.batch
     qps = [fam.instance(base + i) for i in range(args.batch)]
     nx, nu, N, nc, nf = qps[0].dims()
-    settings = native.default_settings(precision=prec, cluster=args.cluster,
+    settings = native.default_settings(precision=prec, cluster=args.cluster, max_refine=3,
+                                       fallback_iters=args.fallback, max_iter=6000,
                                        eps_floor=1e-5 if prec == native.GPUSLS_FP32 else 1e-7)
     with torch.cuda.stream(stream):
         hb = QPBatch(qps, settings, stream=stream, device=dev)
+        mlp = learned.load(args.model, max_batch=args.batch, stream=stream)
+        feats = torch.from_numpy(learned.features(qps)).to(dev)
 
-    def step():
+    def step_learned():
+        hb.reset()
+        mlp.warm_start(hb, feats)
+        return hb.solve(fetch=False)
+
+    def step_cold():
         hb.reset()
         return hb.solve(fetch=False)
 
+    def timed(fn, steps):
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            barrier(ws)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier(ws)
+        return max_over_ranks(ws, e0.elapsed_time(e1))
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step()
+            step_learned()
     torch.cuda.synchronize()
-    barrier(ws)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk, torch.cuda.stream(stream):
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    barrier(ws)
-    t_ms = ev0.elapsed_time(ev1)
-    t_ms = max_over_ranks(ws, t_ms)
+    with Clocks(local) as clk:
+        t_ms = timed(step_learned, args.steps)
     ms_per_step = t_ms / args.steps
     value = t_ms / (args.steps * args.batch * ws)
-    # per-QP results: one more identical cold solve (untimed) to read them
-    info = (native.qp_info * args.batch)()
-    hb.reset()
-    st = hb.lib.qp_solve(hb.h, C_ptr(hb.x0), 0, 0.0, C_ptr(hb.out_x), C_ptr(hb.out_u), C_ptr(hb.out_l), info)
-    iters = [info[i].iters for i in range(args.batch)]
-    refs = [info[i].refactors for i in range(args.batch)]
-    kkts = [info[i].kkt for i in range(args.batch)]
-    stats = [info[i].status for i in range(args.batch)]
+
+    def read_info(warm: bool):
+        info = (native.qp_info * args.batch)()
+        hb.reset()
+        if warm:
+            mlp.warm_start(hb, feats)
+        hb.lib.qp_solve(hb.h, C_ptr(hb.x0), 0, 0.0, C_ptr(hb.out_x), C_ptr(hb.out_u), C_ptr(hb.out_l), info)
+        return [info[i] for i in range(args.batch)]
+
+    inf_w = read_info(True)
+    iters = [i.iters for i in inf_w]
+    refs = [i.refactors for i in inf_w]
+    kkts = [i.kkt for i in inf_w]
+    stats = [i.status for i in inf_w]
+    # the same batch solved cold (no learned warm start)
+    with torch.cuda.stream(stream):
+        step_cold()
+    t_cold = timed(step_cold, max(1, args.steps))
+    cold_ms = t_cold / (max(1, args.steps) * args.batch * ws)
+    inf_c = read_info(False)
 
     # plain FP64 single-QP solves (cold, one QP per launch)
     plain = []
@@ -265,40 +293,33 @@ def main():
         hp.close()
     plain_ms = float(np.mean(plain)) if plain else None
 
-    # end to end through the public API: H2D problem data from pinned memory,
-    # qp_update + cold solve, D2H of (dx, du, lam)
+    # end to end through the public API: H2D problem data and features from
+    # pinned memory, qp_update, learned warm start + solve, D2H of (dx, du, lam)
     e2e = None
     if not args.no_e2e:
         keys = ("A", "B", "c", "Q", "R", "S", "q", "r", "C", "D", "CN", "lo", "hi")
         host = {k: hb.pools[k].cpu().pin_memory() for k in keys}
         host_x0 = hb.x0.cpu().pin_memory()
+        host_f = feats.cpu().pin_memory()
         dev_pools = {k: torch.empty_like(hb.pools[k]) for k in keys}
         out_host = [torch.empty_like(t, device="cpu").pin_memory() for t in (hb.out_x, hb.out_u, hb.out_l)]
-        h2d = sum(t.numel() * 8 for t in host.values()) + host_x0.numel() * 8
+        h2d = sum(t.numel() * 8 for t in host.values()) + host_x0.numel() * 8 + host_f.numel() * 4
         d2h = sum(t.numel() * 8 for t in out_host)
 
         def e2e_step():
             for k in keys:
                 dev_pools[k].copy_(host[k], non_blocking=True)
             hb.x0.copy_(host_x0, non_blocking=True)
+            feats.copy_(host_f, non_blocking=True)
             hb.update_pools(dev_pools)
-            hb.reset()
-            hb.solve(fetch=False)
+            step_learned()
             for o, d in zip(out_host, (hb.out_x, hb.out_u, hb.out_l)):
                 o.copy_(d, non_blocking=True)
 
         with torch.cuda.stream(stream):
             e2e_step()
             torch.cuda.synchronize()
-            barrier(ws)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                e2e_step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        te = max_over_ranks(ws, e0.elapsed_time(e1))
+        te = timed(e2e_step, args.steps)
         e2e = {"value": te / (args.steps * args.batch * ws), "unit": "ms/QP", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
@@ -321,14 +342,19 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if esz == 4 else "f64",
                 "data": "synthetic",
-                "config": {"workload": "quadruped-shaped LTV-QP family (nx=61 nu=12 N=100 nc=20 nf=8), "
-                                       "cold start", "batch": args.batch, "precision": args.precision,
-                           "cluster": args.cluster, "parallelism": f"replicas x{ws}",
-                           "l2": "inputs larger than L2 (FP64 pools 1.2 GB per 148 QPs)"},
+                "config": {"workload": "quadruped-shaped LTV-QP family (nx=61 nu=12 N=100 nc=20 nf=8), held-out "
+                                       "instances; learned warm start + batched persistent solve",
+                           "batch": args.batch, "precision": args.precision, "cluster": args.cluster,
+                           "parallelism": f"replicas x{ws}",
+                           "l2": "inputs larger than L2 (FP64 pools 2.2 GB per 256 QPs)",
+                           "model": os.path.basename(args.model)},
+                "batched_cold_ms_per_qp": cold_ms,
                 "plain_fp64_ms_per_qp": plain_ms,
-                "iters_mean": float(np.mean(iters)), "refactors_mean": float(np.mean(refs)),
-                "kkt_max": float(np.max(kkts)), "all_converged": all(s == 0 for s in stats),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps,
+                "iters_mean": float(np.mean(iters)), "iters_mean_cold": float(np.mean([i.iters for i in inf_c])),
+                "refactors_mean": float(np.mean(refs)),
+                "refactors_mean_cold": float(np.mean([i.refactors for i in inf_c])),
+                "kkt_max": float(np.max(kkts)), "all_converged": all(s_ == 0 for s_ in stats),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 11 * args.steps,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     hb.close()

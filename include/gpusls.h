@@ -64,8 +64,15 @@ typedef struct qp_settings {
   int32_t precision;  /* GPUSLS_FP64 or GPUSLS_FP32                                 */
   int32_t cluster;    /* CTAs (thread blocks) per QP, 1..8; 0 picks by N            */
   int32_t fixed_iters;/* > 0: run exactly this many iterations, no stop test        */
+  int32_t max_refine; /* iterative-refinement rounds allowed at the eps floor (3)   */
+  int32_t fallback_iters; /* > 0: a QP whose state came from a warm start
+                             (qp_set_warm_start / qp_warm_start_mlp) and has not
+                             converged after this many iterations restarts cold
+                             (z = y = 0, setup rho) within the same solve        */
   int32_t pad;
-  double eps_floor;   /* the KKT gate divides eps by 10 on failure, not below this  */
+  double eps_floor;   /* the KKT gate divides eps by 10 on failure, not below this;
+                         at the floor a failing KKT check triggers a refinement:
+                         r <- r + (FP64 u-stationarity residual)                   */
 } qp_settings;
 
 /* Per-QP result summary (host memory). */
@@ -73,6 +80,8 @@ typedef struct qp_info {
   int32_t status;     /* GPUSLS_OK, GPUSLS_MAX_ITER or a negative error            */
   int32_t iters;      /* ADMM iterations run                                       */
   int32_t refactors;  /* rho-dependent factorizations (tree scans) performed       */
+  int32_t refines;    /* iterative-refinement rounds applied                       */
+  int32_t fallback;   /* 1 if a warm start was abandoned for a cold restart        */
   int32_t pad;
   double rho;         /* final penalty                                             */
   double r_prim, r_dual; /* last in-loop residuals                                 */
@@ -151,7 +160,7 @@ int qp_update(qp_handle* h, const double* A, const double* B, const double* c,
               const double* lo, const double* hi);
 
 /* qp_reset: cold start of every QP: z = y = 0, rho = the setup value, cached
- * factorization invalidated. */
+ * factorization invalidated, refinement corrections of r undone. */
 int qp_reset(qp_handle* h);
 
 /* qp_kkt: FP64 KKT residual of a candidate point (dx, du, lam pools) for
@@ -226,6 +235,10 @@ int mlp_get_params(mlp_handle* h, float* W1, float* b1, float* W2, float* b2, fl
 /* per-column mean / standard deviation of X [count][n_in] and T [count][n_out]
  * used to normalize inputs and targets (identity until called) */
 int mlp_fit_normalization(mlp_handle* h, const float* X, const float* T, int32_t count);
+/* set / get the normalization (means and standard deviations; device float32
+ * [n_in], [n_in], [n_out], [n_out]; NULL outputs skipped) */
+int mlp_set_normalization(mlp_handle* h, const float* xm, const float* xs, const float* ym, const float* ys);
+int mlp_get_normalization(mlp_handle* h, float* xm, float* xs, float* ym, float* ys);
 /* Y = denormalized network output for raw inputs X (B <= max_batch) */
 int mlp_forward(mlp_handle* h, const float* X, int32_t B, float* Y);
 /* gradients of the loss at ALREADY-normalized (Xn, Tn) into grads (device,

@@ -21,7 +21,11 @@ Readings (the paper is silent or garbled here):
   * "solve to a KKT tolerance": when the in-loop test passes, the FP64 KKT
     residual (oracle.kkt) is evaluated; if it exceeds eps_kkt the in-loop
     tolerance is divided by 10, but not below eps_floor, and iterations
-    continue (at the floor the KKT is re-evaluated at every passing test).
+    continue; at the floor a failing check triggers one round of iterative
+    refinement (at most max_refine rounds): the FP64 u-stationarity residual
+    ru_k (oracle.kkt.u_residuals) is added to the linear term r_k used by the
+    iteration (and by the rho rule's ||(q, r)||), while the KKT check keeps the
+    original data.
 """
 from __future__ import annotations
 
@@ -29,7 +33,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .kkt import kkt_residual
+import dataclasses
+
+from .kkt import kkt_residual, u_residuals
 from .lq import G_apply, GT_apply, H_apply, augmented, augmented_linear, lq_solve
 
 
@@ -39,6 +45,7 @@ class Settings:
     eps: float = 1e-4
     eps_kkt: float | None = None   # None: stop on the in-loop test alone
     eps_floor: float = 1e-7        # lowest in-loop tolerance the KKT gate tightens to
+    max_refine: int = 3            # refinement rounds allowed at the floor
     sigma: int = 25                # 0: fixed rho
     check_every: int = 5
     max_iter: int = 4000
@@ -81,6 +88,8 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
     """ADMM per Sec. IV-A.  iters (if given) runs exactly that many
     iterations with no stop test (for iterate parity)."""
     s = s or Settings()
+    qp0 = qp                       # original data: the KKT check always uses it
+    refines = 0
     m = qp.m
     z = np.zeros(m) if z0 is None else np.array(z0, dtype=float)
     y = np.zeros(m) if y0 is None else np.array(y0, dtype=float)
@@ -111,11 +120,15 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
             if s.eps_kkt is None:
                 converged = True
                 break
-            kkt = kkt_residual(qp, x, u, rho * y)
+            kkt = kkt_residual(qp0, x, u, rho * y)
             if kkt <= s.eps_kkt:
                 converged = True
                 break
-            eps = max(eps * 0.1, s.eps_floor)
+            if eps > s.eps_floor:
+                eps = max(eps * 0.1, s.eps_floor)
+            elif refines < s.max_refine:
+                qp = dataclasses.replace(qp, r=qp.r + u_residuals(qp0, x, u, rho * y))
+                refines += 1
         if s.sigma and t % s.sigma == 0:
             rho_new = rho_rule(qp, x, u, v, z, y, rho, r_prim, r_dual, s)
             if rho_new > 5.0 * rho or rho_new < rho / 5.0:

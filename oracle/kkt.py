@@ -54,3 +54,17 @@ def kkt_parts(qp, x, u, lam) -> dict:
 def kkt_residual(qp, x, u, lam) -> float:
     p = kkt_parts(qp, x, u, lam)
     return max(p.values())
+
+
+def u_residuals(qp, x, u, lam) -> np.ndarray:
+    """Per-stage u-stationarity residuals R_k u_k + S_k x_k + r_k + D_k^T lam_k
+    + B_k^T mu_{k+1} with the costate of kkt_parts (the part of the KKT residual
+    that iterative refinement feeds back), shape [N, nu]."""
+    N = qp.N
+    out = np.zeros((N, qp.nu))
+    mu = qp.Q[N] @ x[N] + qp.q[N] + qp.CN.T @ stage_rows(qp, lam, N)
+    for k in range(N - 1, -1, -1):
+        lk = stage_rows(qp, lam, k)
+        out[k] = qp.R[k] @ u[k] + qp.S[k] @ x[k] + qp.r[k] + qp.D[k].T @ lk + qp.B[k].T @ mu
+        mu = qp.Q[k] @ x[k] + qp.S[k].T @ u[k] + qp.q[k] + qp.C[k].T @ lk + qp.A[k].T @ mu
+    return out

@@ -106,7 +106,8 @@ class QPBatch:
         dx = self._split(self.out_x, "x", [(qp.N + 1, qp.nx) for qp in self.qps])
         du = self._split(self.out_u, "u", [(qp.N, qp.nu) for qp in self.qps])
         lam = self._split(self.out_l, "m", [(qp.m,) for qp in self.qps])
-        infos = [dict(status=info[i].status, iters=info[i].iters, refactors=info[i].refactors, rho=info[i].rho,
+        infos = [dict(status=info[i].status, iters=info[i].iters, refactors=info[i].refactors,
+                      refines=info[i].refines, fallback=info[i].fallback, rho=info[i].rho,
                       r_prim=info[i].r_prim, r_dual=info[i].r_dual, kkt=info[i].kkt) for i in range(self.B)]
         return Result(dx, du, lam, infos, st)
 
@@ -244,6 +245,16 @@ class MLP:
 
     def fit_normalization(self, X: torch.Tensor, T: torch.Tensor):
         native.check(self.lib.mlp_fit_normalization(self.h, _dptr(X), _dptr(T), X.shape[0]), "mlp_fit_normalization")
+
+    def set_normalization(self, xm, xs, ym, ys):
+        ts = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(self.device) for a in (xm, xs, ym, ys)]
+        native.check(self.lib.mlp_set_normalization(self.h, *[_dptr(t) for t in ts]), "mlp_set_normalization")
+
+    def get_normalization(self):
+        ts = [torch.empty(n, dtype=torch.float32, device=self.device)
+              for n in (self.n_in, self.n_in, self.n_out, self.n_out)]
+        native.check(self.lib.mlp_get_normalization(self.h, *[_dptr(t) for t in ts]), "mlp_get_normalization")
+        return [t.cpu().numpy() for t in ts]
 
     def forward(self, X: torch.Tensor) -> torch.Tensor:
         Y = torch.empty(X.shape[0], self.n_out, dtype=torch.float32, device=self.device)

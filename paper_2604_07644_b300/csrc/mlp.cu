@@ -362,6 +362,26 @@ extern "C" int mlp_fit_normalization(mlp_handle* h, const float* X, const float*
   return GPUSLS_OK;
 }
 
+extern "C" int mlp_set_normalization(mlp_handle* h, const float* xm, const float* xs, const float* ym, const float* ys) {
+  if (!h || !xm || !xs || !ym || !ys) return set_error(GPUSLS_ERR_INVALID, "mlp_set_normalization: null argument");
+  CUM(cudaMemcpyAsync(h->xm, xm, h->n_in * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  CUM(cudaMemcpyAsync(h->xs, xs, h->n_in * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  CUM(cudaMemcpyAsync(h->ym, ym, h->n_out * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  CUM(cudaMemcpyAsync(h->ys, ys, h->n_out * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+extern "C" int mlp_get_normalization(mlp_handle* h, float* xm, float* xs, float* ym, float* ys) {
+  if (!h) return set_error(GPUSLS_ERR_INVALID, "mlp_get_normalization: null handle");
+  if (xm) CUM(cudaMemcpyAsync(xm, h->xm, h->n_in * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  if (xs) CUM(cudaMemcpyAsync(xs, h->xs, h->n_in * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  if (ym) CUM(cudaMemcpyAsync(ym, h->ym, h->n_out * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  if (ys) CUM(cudaMemcpyAsync(ys, h->ys, h->n_out * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
 extern "C" int mlp_forward(mlp_handle* h, const float* X, int32_t B, float* Y) {
   if (!h || !X || !Y || B < 1 || B > h->maxb) return set_error(GPUSLS_ERR_INVALID, "mlp_forward: invalid argument");
   affine_rows_kernel<<<blocks((size_t)B * h->n_in), 256, 0, h->stream>>>(X, h->Xn, h->xm, h->xs, B, h->n_in, 0);
@@ -431,6 +451,7 @@ __global__ void warm_assemble_kernel(const QPDesc* __restrict__ descs, const flo
   if (threadIdx.x == 0) {
     if (d.rho[0] != rho) d.flags[0] = 0;
     d.rho[0] = rho;
+    d.flags[1] = 1;   // warm-started: eligible for the cold fallback
   }
 }
 }  // namespace gsls

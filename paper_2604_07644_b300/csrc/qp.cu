@@ -127,6 +127,10 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   const int max_it = fixed ? args.fixed_iters : args.max_iter;
   double rp = INFINITY, rd = INFINITY, kkt = -1.0;
   int it = 0;
+  int refines = 0;
+  bool warm = d.flags[1] != 0;
+  const int it_warm0 = 0;
+  int fell_back = 0;
   if (status != GPUSLS_ERR_NOT_SPD) {
     for (it = 1; it <= max_it; ++it) {
       const bool stop_iter = !fixed && (it % args.check_every == 0);
@@ -157,7 +161,34 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
           status = GPUSLS_OK;
           break;
         }
-        eps = fmax(eps * 0.1, args.eps_floor);
+        if (eps > args.eps_floor) {
+          eps = fmax(eps * 0.1, args.eps_floor);
+        } else if (refines < args.max_refine) {
+          refine_linear_term<T>(c);
+          ++refines;
+        }
+      }
+      if (warm && args.fallback_iters > 0 && it - it_warm0 >= args.fallback_iters) {
+        // cold-start fallback of a warm start that did not converge in time
+        for (int e2 = t; e2 < nrows; e2 += NT) {
+          c.zS[e2] = T(0);
+          c.yS[e2] = T(0);
+        }
+        warm = false;
+        fell_back = 1;
+        eps = args.eps;
+        const T rho_c = (T)d.rho0[0];
+        __syncthreads();
+        if (rho_c != rho) {
+          rho = rho_c;
+          const int bad = refactor<T>(c, cl, rho);
+          ++refactors;
+          if (bad) {
+            status = GPUSLS_ERR_NOT_SPD;
+            break;
+          }
+        }
+        continue;
       }
       if (rho_iter) {
         full_xu<T>(c);
@@ -203,12 +234,16 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     d.info_i[0] = status;
     d.info_i[1] = it;
     d.info_i[2] = refactors;
+    d.info_i[3] = refines;
+    d.info_i[4] = fell_back;
     d.info_d[0] = (double)rho;
     d.info_d[1] = rp;
     d.info_d[2] = rd;
     d.info_d[3] = kkt;
     d.rho[0] = (double)rho;
     d.flags[0] = (status == GPUSLS_ERR_NOT_SPD) ? 0 : 1;
+    d.flags[1] = 0;
+    d.flags[2] = fell_back;
   }
 }
 
@@ -264,7 +299,8 @@ extern "C" void qp_default_settings(qp_settings* s) {
   s->precision = GPUSLS_FP64;
   s->cluster = 0;
   s->fixed_iters = 0;
-  s->pad = 0;
+  s->max_refine = 3;
+  s->fallback_iters = 0;
   s->eps_floor = 1e-7;
 }
 
@@ -466,7 +502,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   cudaError_t e1 = cudaMalloc(&h->tpool, tsz * esz + 256);
   cudaError_t e2 = cudaMalloc(&h->dpool, (dsz + d_copy) * sizeof(double) + 256);
   cudaError_t e3 = cudaMalloc(&h->ddesc, batch * sizeof(QPDesc));
-  cudaError_t e4 = cudaMalloc(&h->info_i, batch * 4 * sizeof(int));
+  cudaError_t e4 = cudaMalloc(&h->info_i, batch * 8 * sizeof(int));
   cudaError_t e5 = cudaMalloc(&h->info_d, batch * 4 * sizeof(double));
   if (e1 || e2 || e3 || e4 || e5) {
     qp_destroy(h);
@@ -515,7 +551,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     D_.kh = dp + al64((size_t)(d.N + 1) * d.nx);
     D_.rho = D_.kh + al64((size_t)d.N * d.nu);
     D_.flags = reinterpret_cast<int*>(D_.rho + 8);
-    D_.info_i = h->info_i + 4 * b;
+    D_.info_i = h->info_i + 8 * b;
     D_.info_d = h->info_d + 4 * b;
     const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf, m = N * nc + nf;
     const int ldx = D_.ldx, ldu = D_.ldu;
@@ -549,8 +585,9 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     return fail(GPUSLS_ERR_CUDA, "qp_batch_setup: cudaMalloc failed");
   }
   CU(cudaMemcpyAsync(h->rho0_dev, r0.data(), batch * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  for (int b = 0; b < batch; ++b) h->hdesc[b].rho0 = h->rho0_dev + b;
   for (int b = 0; b < batch; ++b) {
-    int fl[2] = {0, 0};
+    int fl[4] = {0, 0, 0, 0};
     CU(cudaMemcpyAsync(h->hdesc[b].rho, &r0[b], sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(h->hdesc[b].flags, fl, sizeof(fl), cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
@@ -602,18 +639,20 @@ static int set_x0(qp_handle* h, const double* x0) {
 }
 
 static int collect(qp_handle* h, qp_info* info) {
-  std::vector<int> ii(h->batch * 4);
+  std::vector<int> ii(h->batch * 8);
   std::vector<double> dd(h->batch * 4);
   CU(cudaMemcpyAsync(ii.data(), h->info_i, ii.size() * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaMemcpyAsync(dd.data(), h->info_d, dd.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   int worst = GPUSLS_OK;
   for (int b = 0; b < h->batch; ++b) {
-    const int st = ii[4 * b];
+    const int st = ii[8 * b];
     if (info) {
       info[b].status = st;
-      info[b].iters = ii[4 * b + 1];
-      info[b].refactors = ii[4 * b + 2];
+      info[b].iters = ii[8 * b + 1];
+      info[b].refactors = ii[8 * b + 2];
+      info[b].refines = ii[8 * b + 3];
+      info[b].fallback = ii[8 * b + 4];
       info[b].pad = 0;
       info[b].rho = dd[4 * b];
       info[b].r_prim = dd[4 * b + 1];
@@ -645,6 +684,8 @@ extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double to
   a.rho_min = h->set.rho_min;
   a.rho_max = h->set.rho_max;
   a.eps_floor = h->set.eps_floor;
+  a.max_refine = h->set.max_refine;
+  a.fallback_iters = h->set.fallback_iters;
   st = launch(h, a);
   if (st) return st;
   return collect(h, info);
@@ -702,6 +743,7 @@ __global__ void state_io_kernel(const QPDesc* __restrict__ descs, const double* 
   T* zz = reinterpret_cast<T*>(d.z);
   T* yy = reinterpret_cast<T*>(d.y);
   for (int e = threadIdx.x; e < d.m; e += blockDim.x) {
+    if (set && e == 0) d.flags[1] = 1;
     if (set) {
       zz[e] = z ? (T)z[o + e] : T(0);
       yy[e] = y ? (T)y[o + e] : T(0);
@@ -737,9 +779,9 @@ extern "C" int qp_set_warm_start(qp_handle* h, const double* z, const double* y,
       CU(cudaMemcpyAsync(&old, h->hdesc[b].rho, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
       CU(cudaStreamSynchronize(h->stream));
       if (old != rho[b]) {
-        int fl[2] = {0, 0};
+        int fl0 = 0;   // factorization no longer valid (flags[1], the warm mark, stays set)
         CU(cudaMemcpyAsync(h->hdesc[b].rho, &rho[b], sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        CU(cudaMemcpyAsync(h->hdesc[b].flags, fl, sizeof(fl), cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemcpyAsync(h->hdesc[b].flags, &fl0, sizeof(fl0), cudaMemcpyHostToDevice, h->stream));
         CU(cudaStreamSynchronize(h->stream));
       }
     }
@@ -814,9 +856,16 @@ __global__ void reset_kernel(const QPDesc* __restrict__ descs, const double* __r
     zz[e] = T(0);
     yy[e] = T(0);
   }
+  // undo iterative-refinement corrections of the linear term r
+  T* rr = reinterpret_cast<T*>(d.r);
+  for (int e = threadIdx.x; e < d.N * d.ldu; e += blockDim.x) {
+    const int i = e / d.ldu, a = e - i * d.ldu;
+    rr[e] = a < d.nu ? (T)d.r64[(size_t)i * d.nu + a] : T(0);
+  }
   if (threadIdx.x == 0) {
     d.rho[0] = rho0[blockIdx.x];
     d.flags[0] = 0;
+    d.flags[1] = 0;
   }
 }
 

@@ -512,7 +512,11 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
         double s2 = 0.0;
         for (int j = lane; j < nx; j += 32) s2 += d.B64[(size_t)i * nx * nu + (size_t)j * nu + a] * mu[j];
         s2 = warp_sum(s2);
-        if (lane == 0) stat = fmax(stat, fabs(s2 + d.kh[(size_t)i * nu + a]));
+        if (lane == 0) {
+          const double ru = s2 + d.kh[(size_t)i * nu + a];
+          stat = fmax(stat, fabs(ru));
+          d.kh[(size_t)i * nu + a] = ru;   // u-stationarity residual, read by refine_linear_term
+        }
       }
       for (int j = t; j < nx; j += NT) {
         double s2 = d.kg[(size_t)i * nx + j];
@@ -542,6 +546,49 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
   }
   cluster_max(c, cl, v4, 4);
   return fmax(fmax(v4[0], v4[1]), fmax(v4[2], v4[3]));
+}
+
+// Mixed-precision iterative refinement of the ADMM fixed point: fold the FP64
+// u-stationarity residual ru_k left by kkt_eval (d.kh) into the linear term,
+// r_k <- r_k + ru_k.  With the cached gains this shifts
+//   k0_k <- k0_k - Gamma_k ru_k,   c0_k <- c0_k + K_k^T ru_k
+// (c0 = Abar^T P b + q + K^T r, k0 = -Gamma (B^T P b + r)); the solve-precision
+// copy of r is updated too so that a later refactor keeps the correction.
+// The KKT check itself always uses the original FP64 data.
+template <typename T>
+__device__ void refine_linear_term(Ctx<T>& c) {
+  QPDesc& d = *c.d;
+  if (!c.active) return;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, ldx = d.ldx, ldu = d.ldu, ldv = d.ldv, ldf = d.ldf;
+  int bws, fws, cds;
+  bundle_sizes(nx, nu, nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
+  T* r = TP<T>(d.r);
+  T* k0 = TP<T>(d.k0);
+  T* c0 = TP<T>(d.c0);
+  const T* Gam = TP<T>(d.Gam);
+  const T* K = TP<T>(d.K);
+  const int t = threadIdx.x;
+  for (int i = c.s; i < c.e; ++i) {
+    T* bw = TP<T>(d.BW) + (size_t)i * bws;
+    T* c0b = bw + (size_t)(nx + nc) * ldx + (size_t)(nx + nc) * ldu;
+    T* k0b = c0b + ldx;
+    for (int a = t; a < nu; a += NT) c.tmp1[a] = (T)d.kh[(size_t)i * nu + a];
+    __syncthreads();
+    for (int a = t; a < nu; a += NT) {
+      T g = T(0);
+      for (int b = 0; b < nu; ++b) g += Gam[(size_t)i * nu * ldu + a * ldu + b] * c.tmp1[b];
+      k0[(size_t)i * ldu + a] -= g;
+      k0b[a] -= g;
+      r[(size_t)i * ldu + a] += c.tmp1[a];
+    }
+    for (int j = t; j < nx; j += NT) {
+      T g = T(0);
+      for (int a = 0; a < nu; ++a) g += K[(size_t)i * nu * ldx + a * ldx + j] * c.tmp1[a];
+      c0[(size_t)i * ldx + j] += g;
+      c0b[j] += g;
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace gsls

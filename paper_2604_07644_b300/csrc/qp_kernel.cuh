@@ -53,7 +53,8 @@ struct QPDesc {
   double *A64, *B64, *b64, *Q64, *R64, *S64, *q64, *r64, *C64, *D64, *CN64, *lo64, *hi64, *x064;
   double *kg, *kh;
   double* rho;      // [1]
-  int* flags;       // [0]: factorization valid for *rho
+  int* flags;       // [0]: factorization valid for *rho; [1]: state set by a warm start
+  const double* rho0;   // [1] setup penalty (cold restart)
   // outputs (set per call)
   double *ox, *ou, *olam;
   int* info_i;      // [4]: status, iters, refactors, -
@@ -71,6 +72,8 @@ struct SolveArgs {
   int check_every;
   int cs;
   double eps, eps_kkt, rho_min, rho_max, eps_floor;
+  int max_refine;
+  int fallback_iters;   // > 0: a warm-started QP not converged after this many iterations restarts cold
 };
 
 // Per-stage operator bundles of the cached iteration (elements).  Every

@@ -36,11 +36,13 @@ class qp_settings(C.Structure):
     _fields_ = [("rho0", C.c_double), ("eps", C.c_double), ("eps_kkt", C.c_double), ("rho_min", C.c_double),
                 ("rho_max", C.c_double), ("sigma", C.c_int32), ("check_every", C.c_int32),
                 ("max_iter", C.c_int32), ("precision", C.c_int32), ("cluster", C.c_int32),
-                ("fixed_iters", C.c_int32), ("pad", C.c_int32), ("eps_floor", C.c_double)]
+                ("fixed_iters", C.c_int32), ("max_refine", C.c_int32), ("fallback_iters", C.c_int32),
+                ("pad", C.c_int32), ("eps_floor", C.c_double)]
 
 
 class qp_info(C.Structure):
-    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("refactors", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("refactors", C.c_int32), ("refines", C.c_int32),
+                ("fallback", C.c_int32), ("pad", C.c_int32),
                 ("rho", C.c_double), ("r_prim", C.c_double), ("r_dual", C.c_double), ("kkt", C.c_double)]
 
 
@@ -71,6 +73,8 @@ SIGNATURES = {
     "mlp_get_params": (C.c_int, [P, DP, DP, DP, DP, DP, DP]),
     "mlp_fit_normalization": (C.c_int, [P, DP, DP, C.c_int32]),
     "mlp_forward": (C.c_int, [P, DP, C.c_int32, DP]),
+    "mlp_set_normalization": (C.c_int, [P, DP, DP, DP, DP]),
+    "mlp_get_normalization": (C.c_int, [P, DP, DP, DP, DP]),
     "mlp_gradients": (C.c_int, [P, DP, DP, C.c_int32, DP, C.POINTER(C.c_float)]),
     "mlp_train_step": (C.c_int, [P, DP, DP, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
     "mlp_destroy": (None, [P]),

@@ -199,3 +199,21 @@ def test_invalid_dims_rejected(lib):
     qp.A = np.zeros((5, 81, 81))
     with pytest.raises(RuntimeError):
         batch([qp])
+
+
+def test_fp32_refinement_reaches_kkt_on_stalling_instance(lib):
+    """A held-out family instance whose FP32 fixed point stalls at a KKT of
+    ~1e-4 (u-stationarity) converges once the iterative refinement of the
+    linear term is allowed; the returned point passes the oracle's KKT check."""
+    fam = W.family(0)
+    qp = fam.instance(100094)
+    b = batch([qp], precision=native.GPUSLS_FP32, eps_floor=1e-5, max_refine=3)
+    r = b.solve()
+    assert r.info[0]["status"] == native.GPUSLS_OK, r.info
+    assert kkt.kkt_residual(qp, r.dx[0], r.du[0], r.lam[0]) <= 1.0001e-4
+    b.close()
+    b = batch([qp], precision=native.GPUSLS_FP32, eps_floor=1e-5, max_refine=3)
+    b.reset()
+    r2 = b.solve()
+    assert r2.info[0]["iters"] == r.info[0]["iters"]   # reset undoes the corrections
+    b.close()

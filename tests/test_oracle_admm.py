@@ -103,3 +103,36 @@ def test_iterate_mode_runs_fixed_count():
     qp = W.plain_4d(0)
     r = admm.admm(qp, admm.Settings(sigma=0), iters=7)
     assert r.iters == 7
+
+
+def test_u_residuals_vanish_at_optimum_and_match_kkt_part():
+    qp = W.tiny(3)
+    xb, ub, lb, _ = activeset.brute_force(qp)
+    assert np.max(np.abs(kkt.u_residuals(qp, xb, ub, lb))) < 1e-10
+    g = np.random.default_rng(1)
+    x, u, l = xb + 1e-3 * g.standard_normal(xb.shape), ub + 1e-3 * g.standard_normal(ub.shape), lb
+    ru = kkt.u_residuals(qp, x, u, l)
+    assert abs(np.max(np.abs(ru)) - kkt.kkt_parts(qp, x, u, l)["stat"]) < 1e-14
+
+
+def test_refinement_recovers_a_planted_operator_error(monkeypatch):
+    """A factorization computed from slightly wrong data (R perturbed by 1e-3,
+    standing in for a low-precision factorization) makes ADMM converge to the
+    wrong fixed point, so the exact KKT check stalls; refinement of the linear
+    term with the exact u-stationarity residual brings it under tolerance."""
+    qp = W.plain_4d(1)
+    orig = admm.augmented
+
+    def perturbed(qp_, rho):
+        Qh, Rh, Sh = orig(qp_, rho)
+        return Qh, Rh + 1e-3 * qp_.R, Sh
+
+    monkeypatch.setattr(admm, "augmented", perturbed)
+    s0 = admm.Settings(eps=1e-4, eps_kkt=1e-8, eps_floor=1e-10, max_refine=0, max_iter=4000)
+    r0 = admm.admm(qp, s0)
+    s1 = admm.Settings(eps=1e-4, eps_kkt=1e-8, eps_floor=1e-10, max_refine=10, max_iter=4000)
+    r1 = admm.admm(qp, s1)
+    k0 = kkt.kkt_residual(qp, r0.x, r0.u, r0.lam)
+    k1 = kkt.kkt_residual(qp, r1.x, r1.u, r1.lam)
+    assert not r0.converged and k0 > 1e-6
+    assert r1.converged and k1 <= 1e-8
