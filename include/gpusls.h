@@ -255,6 +255,37 @@ void mlp_destroy(mlp_handle* h);
  * Runs on the network's stream; give both handles the same stream. */
 int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free KKT residual (the paper has no counterpart)              */
+/* ------------------------------------------------------------------------ */
+/* Largest scratch (in doubles) gpusls_kkt_noalloc can use: it needs
+ * (N+1)*nx + N*nu doubles, so e.g. nx = 75, nu = 21, N <= 1364. */
+#define GPUSLS_NOALLOC_MAX_SCRATCH 131072
+
+/* gpusls_kkt_noalloc: the FP64 KKT residual of qp_kkt for ONE QP, for callers
+ * that cannot allocate device memory when they need it (a real-time control
+ * loop where cudaMalloc may block or synchronize the device, a context that
+ * forbids allocation, or a host runtime that owns all device buffers).  It
+ * needs no handle and calls no allocator.
+ *   Inputs are device float64 arrays in the qp_setup layouts (S may be NULL)
+ *   plus the candidate point x0 [nx], dx [N+1][nx], du [N][nu], lam [N*nc+nf];
+ *   out: device float64 [5] receiving (kkt, dynamics, bound violation,
+ *   u-stationarity, complementarity).  Runs asynchronously on `stream`.
+ * Scratch: a fixed device array of GPUSLS_NOALLOC_MAX_SCRATCH doubles, held by
+ * every GPU that loads the library until the process exits.  Problems needing
+ * more return GPUSLS_ERR_INVALID with the sizes in gpusls_last_error().  The
+ * array's device address is looked up on the first call on each device, so
+ * make that first call before any stream capture.  Every call uses the same
+ * array (it is fully rewritten before it is read): calls whose executions
+ * overlap on a device -- e.g. on two streams at once -- race on it. */
+int gpusls_kkt_noalloc(qp_dims d, const double* A, const double* B, const double* c,
+                       const double* Q, const double* R, const double* S,
+                       const double* q, const double* r,
+                       const double* C, const double* D, const double* CN,
+                       const double* lo, const double* hi,
+                       const double* x0, const double* dx, const double* du, const double* lam,
+                       double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,7 @@ SIGNATURES = {
     "mlp_train_step": (C.c_int, [P, DP, DP, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
     "mlp_destroy": (None, [P]),
     "qp_warm_start_mlp": (C.c_int, [P, P, DP, C.c_double, C.c_double]),
+    "gpusls_kkt_noalloc": (C.c_int, [qp_dims] + [DP] * 18 + [P]),
 }
 
 _lock = threading.Lock()
