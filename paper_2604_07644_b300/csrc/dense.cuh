@@ -128,109 +128,148 @@ __device__ void cta_zero(int m, int n, T* Y, int ldy) {
 
 // Gauss-Jordan inversion of the n x n matrix held in shared memory S (leading
 // dimension lds), written to Wout (leading dimension ldw; shared or global).
-// S is destroyed.  pivot = true: partial pivoting over the not-yet-used rows
-// (the pivot row is recorded instead of swapped, and the result gathered
-// through the permutation at the end); failure if a pivot is below
-// tiny_pivot.  pivot = false: pivots taken on the diagonal, failure if one is
-// not positive (the test that the matrix is symmetric positive definite).
-// Returns 0 on success, 1 on failure.
-// Thread map: warp w owns rows i = w (mod 8); lane l owns columns l, l+32, l+64.
-// One step = [read pivot row and column into registers] barrier [update,
-// and the owners of column k+1 propose its pivot candidates] barrier.
-// buf: shared scratch of 2*TILE elements (candidate values and rows);
-// perm: shared int[2*TILE]; flag: shared int[2].
+// pivot = true: partial pivoting over the not-yet-used rows (largest |value|,
+// ties to the lower row; the pivot row is recorded instead of swapped and the
+// result gathered through the permutation at the end); failure if a pivot is
+// not above tiny_pivot.  pivot = false: pivots on the diagonal, failure if one
+// is not positive (the test that the matrix is symmetric positive definite).
+// Returns 0 on success, 1 on failure; S is left unchanged.
+//
+// The matrix lives in registers: thread (ty, tx) of the 16 x 16 thread grid
+// owns rows ty + 16 a and columns tx + 16 b (a, b < 5).  Elimination step k
+// with pivot row p is the rank-one update M' = M0 - c r^T, where M0 is M with
+// column k replaced by the unit vector e_p, c = column k of M with c_p
+// replaced by (pivot - 1), and r = row p of M / pivot with r_k = 1 / pivot:
+// one FMA per element, no branches on the element's position.
+// Per step: [every warp finds the pivot row from the published column k;
+// owners of row p publish it] barrier [update in registers; owners of column
+// k+1 publish it into the other column buffer] barrier.
+// buf: shared scratch of 3*TILE elements; perm: shared int[2*TILE];
+// flag: shared int (flag[0] = failure).
 template <typename T>
 __device__ __noinline__ int cta_inverse(T* S, int lds, int n, bool pivot, T* Wout, int ldw, T* buf, int* perm,
                                         int* flag) {
-  const int t = threadIdx.x, w = t >> 5, l = t & 31;
-  int* used = perm + TILE;       // used[i]: physical row i already a pivot row
-  T* cval = buf;                 // per-warp candidate |value|
-  int* cand_row = reinterpret_cast<int*>(buf + TILE);
-  if (t == 0) flag[0] = 0;
-  for (int i = t; i < n; i += NT) used[i] = 0;
-  __syncthreads();
-  // candidates for column 0
-  if (pivot && l == 0) {
-    T best = T(-1);
-    int bi = -1;
-    for (int i = w; i < n; i += 8) {
-      const T v = fabs(S[i * lds]);
-      if (v > best) { best = v; bi = i; }
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15, lane = t & 31;
+  T* rowp = buf;                           // pivot row of the current step
+  T* colbuf[2] = {buf + TILE, buf + 2 * TILE};   // column k, double-buffered
+  T m[5][5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      m[a][b] = (i < n && j < n) ? S[i * lds + j] : T(0);
     }
-    cval[w] = best;
-    cand_row[w] = bi;
-  }
+  // column 0 from S itself
+  for (int i = t; i < n; i += NT) colbuf[0][i] = S[i * lds];
+  if (t == 0) flag[0] = 0;
+  unsigned used = 0;                       // bit q: row lane + 32 q already a pivot row
+  int bad = 0;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
+    const T* colk = colbuf[k & 1];
     int p = k;
     if (pivot) {
+      // warp-redundant argmax of |column k| over the unused rows
       T best = T(-1);
-      for (int q = 0; q < 8; ++q) {
-        const int r = cand_row[q];
-        const T v = cval[q];
-        if (r >= 0 && (v > best || (v == best && r < p))) { best = v; p = r; }
+      int bi = -1;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int i = lane + 32 * q;
+        if (i < n && !((used >> q) & 1u)) {
+          const T av = fabs(colk[i]);
+          if (bi < 0 || av > best) { best = av; bi = i; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
+      }
+      p = bi;
+      if ((p & 31) == lane) used |= 1u << (p >> 5);
+    }
+    if (t == 0) perm[k] = p;
+    // owners publish row p (values divided later, by every reader)
+    if ((p & 15) == ty) {
+      const int pa = p >> 4;
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        T v = m[0][b];
+#pragma unroll
+        for (int a = 1; a < 5; ++a) v = (a == pa) ? m[a][b] : v;   // constant indices only
+        const int j = tx + 16 * b;
+        if (j < n) rowp[j] = v;
       }
     }
-    T piv = S[p * lds + k];
-    const bool bad = pivot ? !(fabs(piv) > tiny_pivot<T>()) : !(piv > T(0));
-    if (bad) piv = T(1);
-    const T ip = T(1) / piv;
-    // registers: pivot row entries of own columns, column-k entries of own rows
-    T rowp[3], colk[10];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int j = l + 32 * c;
-      rowp[c] = (j < n) ? S[p * lds + j] : T(0);
-    }
-#pragma unroll
-    for (int a = 0; a < 10; ++a) {
-      const int i = w + 8 * a;
-      colk[a] = (i < n) ? S[i * lds + k] : T(0);
-    }
-    if (t == 0) {
-      perm[k] = p;
-      used[p] = 1;
-      if (bad) flag[0] = 1;
-    }
     __syncthreads();
-    T best = T(-1);
-    int bi = -1;
+    T piv = colk[p];
+    const bool badk = pivot ? !(fabs(piv) > tiny_pivot<T>()) : !(piv > T(0));
+    if (badk) {
+      bad = 1;
+      piv = T(1);
+    }
+    const T ip = T(1) / piv;
+    T r[5], c[5];
 #pragma unroll
-    for (int a = 0; a < 10; ++a) {
-      const int i = w + 8 * a;
-      if (i < n) {
+    for (int b = 0; b < 5; ++b) {
+      const int j = tx + 16 * b;
+      r[b] = (j == k) ? ip : ((j < n) ? rowp[j] * ip : T(0));
+    }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const int j = l + 32 * c;
-          if (j < n) {
-            T v;
-            if (i == p) v = (j == k) ? ip : rowp[c] * ip;
-            else if (j == k) v = -colk[a] * ip;
-            else v = S[i * lds + j] - colk[a] * rowp[c] * ip;
-            S[i * lds + j] = v;
-            if (pivot && j == k + 1 && !used[i]) {
-              const T av = fabs(v);
-              if (av > best) { best = av; bi = i; }
-            }
+    for (int a = 0; a < 5; ++a) {
+      const int i = ty + 16 * a;
+      c[a] = (i == p) ? piv - T(1) : ((i < n) ? colk[i] : T(0));
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      if (16 * a < n) {                    // uniform over the CTA
+        const T e = (ty + 16 * a == p) ? T(1) : T(0);
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          if (16 * b < n) {
+            const T m0 = (tx + 16 * b == k) ? e : m[a][b];
+            m[a][b] = fma(-c[a], r[b], m0);
           }
         }
       }
     }
-    if (pivot && k + 1 < n && l == ((k + 1) & 31)) {
-      cval[w] = best;
-      cand_row[w] = bi;
+    // owners of column k+1 publish it for the next step
+    const int k1 = k + 1;
+    if (k1 < n && (k1 & 15) == tx) {
+      T* dst = colbuf[k1 & 1];
+      const int kb = k1 >> 4;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        T v = m[a][0];
+#pragma unroll
+        for (int b = 1; b < 5; ++b) v = (b == kb) ? m[a][b] : v;   // constant indices only
+        const int i = ty + 16 * a;
+        if (i < n) dst[i] = v;
+      }
     }
     __syncthreads();
   }
-  // gather: W[a][b] = S[perm[a]][iperm[b]], iperm[perm[c]] = c (identity without pivoting)
-  int* iperm = used;
-  if (pivot) {
-    for (int c = t; c < n; c += NT) iperm[perm[c]] = c;
-  }
+  if (t == 0 && bad) flag[0] = 1;
+  // gather: W[a][b] = M'[perm[a]][iperm[b]] (iperm[perm[c]] = c): the owner of
+  // M'[i][j] writes W[iperm[i]][perm[j]]
+  int* iperm = perm + TILE;
+  if (pivot)
+    for (int q = t; q < n; q += NT) iperm[perm[q]] = q;
   __syncthreads();
-  for (int a = w; a < n; a += 8) {
-    const int ra = pivot ? perm[a] : a;
-    for (int b = l; b < n; b += 32) Wout[a * ldw + b] = S[ra * lds + (pivot ? iperm[b] : b)];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    const int i = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const int j = tx + 16 * b;
+      if (i < n && j < n) {
+        const int wa = pivot ? iperm[i] : i;
+        const int wb = pivot ? perm[j] : j;
+        Wout[wa * ldw + wb] = m[a][b];
+      }
+    }
   }
   __syncthreads();
   const int f = flag[0];

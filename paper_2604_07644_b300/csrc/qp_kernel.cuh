@@ -108,7 +108,7 @@ __host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf
   SmemLayout s;
   int off = 0;
   const int ring_b = depth * slot * esz;
-  const int dense_b = (2 * KT * TILE + TILE * GJ_LD + 2 * TILE) * esz;
+  const int dense_b = (2 * KT * TILE + TILE * GJ_LD + 3 * TILE) * esz;
   const int uni = ring_b > dense_b ? ring_b : dense_b;
   s.ring = 0;
   s.gemm = 0;
