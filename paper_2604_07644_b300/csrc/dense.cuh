@@ -377,4 +377,218 @@ __device__ void smem_mv(const T* M, int ld, int rows, int cols, const T* x, cons
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Bulk (TMA) copies global -> shared with mbarrier completion.
+// ---------------------------------------------------------------------------
+__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses.
+__device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// One thread: expect `bytes` on `bar` and start the bulk copy (16-byte aligned
+// addresses, bytes a multiple of 16).
+__device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Wait for the phase with the given parity to complete; gives up after
+// `limit` polls and returns false.
+__device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity, int limit) {
+  const unsigned a = smem_addr(bar);
+  for (int k = 0; k < limit; ++k) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// One-round split sweep: y = [A | B]^T x with A (rows x na, leading dim lda)
+// at the start of a shared block and B (rows x nb, leading dim ldb) at element
+// offset offB.  Outputs are grouped in 16-byte vectors (VW elements); the
+// rows are split into G contiguous groups, every (vector, group) pair is one
+// thread, and the G partial vectors are summed by the output's owner thread
+// (t < na + nb) after one barrier.  The role of each thread is computed once
+// (sweep_plan) and reused for every block of a stream.
+// ---------------------------------------------------------------------------
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
+
+constexpr int SWEEP_MAXG = 16;
+// shared scratch of a sweep: NT vectors of 16 bytes
+constexpr int SWEEP_SMEM_BYTES = NT * 16;
+
+struct SweepPlan {
+  int nr;        // rows of this thread's group (0: no partial role)
+  int moff;      // element offset of its first (row, vector) in the block
+  int ld;        // leading dimension of its matrix
+  int r0;        // first row
+  int slot;      // vector slot of its partial
+  int G;         // row groups
+  int red_off;   // element offset of its output in a partial row (red_off < 0: no output)
+  int pstride;   // elements per partial row (nq * VW)
+};
+
+template <typename T>
+__device__ inline SweepPlan sweep_plan(int rows, int na, int lda, int nb, int ldb, int offB) {
+  constexpr int VW = Vec16<T>::W;
+  const int t = threadIdx.x;
+  const int nqa = (na + VW - 1) / VW, nqb = (nb + VW - 1) / VW, nq = nqa + nqb;
+  SweepPlan p;
+  int G = NT / nq;
+  G = G < 1 ? 1 : (G > SWEEP_MAXG ? SWEEP_MAXG : G);
+  const int Rg = (rows + G - 1) / G;
+  const int q = t % nq, g = t / nq;
+  p.G = G;
+  p.pstride = nq * VW;
+  p.slot = g * nq + q;
+  p.nr = 0;
+  p.moff = 0;
+  p.ld = lda;
+  p.r0 = 0;
+  if (g < G) {
+    const bool isa = q < nqa;
+    const int r0 = min(rows, g * Rg);
+    p.r0 = r0;
+    p.nr = min(rows, r0 + Rg) - r0;
+    p.ld = isa ? lda : ldb;
+    p.moff = (isa ? 0 : offB) + r0 * p.ld + (isa ? q : q - nqa) * VW;
+  }
+  p.red_off = t < na ? t : (t < na + nb ? nqa * VW + (t - na) : -1);
+  return p;
+}
+
+template <typename T>
+__device__ inline void vload16(const T* p, T* v);
+template <> __device__ inline void vload16<float>(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+template <> __device__ inline void vload16<double>(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  v[0] = a.x; v[1] = a.y;
+}
+
+// Batched plan: nmat matrices of rows x ncols (leading dim ld, element stride
+// `stride` between matrices) times the same x; output o = mat * ncols + col.
+// Needs nmat * ceil(ncols / VW) <= NT and nmat * ncols <= NT.
+template <typename T>
+__device__ inline SweepPlan sweep_plan_batched(int rows, int ncols, int ld, int nmat, int stride) {
+  constexpr int VW = Vec16<T>::W;
+  const int t = threadIdx.x;
+  const int nqc = (ncols + VW - 1) / VW, nq = nmat * nqc;
+  SweepPlan p;
+  int G = NT / nq;
+  G = G < 1 ? 1 : (G > SWEEP_MAXG ? SWEEP_MAXG : G);
+  const int Rg = (rows + G - 1) / G;
+  const int q = t % nq, g = t / nq;
+  p.G = G;
+  p.pstride = nq * VW;
+  p.slot = g * nq + q;
+  p.nr = 0;
+  p.moff = 0;
+  p.ld = ld;
+  p.r0 = 0;
+  if (g < G) {
+    const int mat = q / nqc, vq = q - mat * nqc;
+    const int r0 = min(rows, g * Rg);
+    p.r0 = r0;
+    p.nr = min(rows, r0 + Rg) - r0;
+    p.moff = mat * stride + r0 * ld + vq * VW;
+  }
+  if (t < nmat * ncols) {
+    const int mat = t / ncols, col = t - mat * ncols;
+    p.red_off = mat * nqc * VW + col;
+  } else {
+    p.red_off = -1;
+  }
+  return p;
+}
+
+// Partial sums of this thread's (vector, row group) on block `blk` with
+// vector x (both shared), added into acc[VW].  No barrier.
+template <typename T>
+__device__ inline void sweep_partial(const SweepPlan& p, const T* blk, const T* x, T* acc) {
+  constexpr int VW = Vec16<T>::W;
+  if (p.nr <= 0) return;
+  T b[VW], m0[VW], m1[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) b[e] = T(0);
+  const T* mp = blk + p.moff;
+  const T* xp = x + p.r0;
+  const int ld2 = 2 * p.ld;
+  int k = 0;
+  for (; k + 1 < p.nr; k += 2) {
+    vload16<T>(mp, m0);
+    vload16<T>(mp + p.ld, m1);
+    const T x0 = xp[k], x1 = xp[k + 1];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      acc[e] = fma(m0[e], x0, acc[e]);
+      b[e] = fma(m1[e], x1, b[e]);
+    }
+    mp += ld2;
+  }
+  if (k < p.nr) {
+    vload16<T>(mp, m0);
+    const T x0 = xp[k];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) acc[e] = fma(m0[e], x0, acc[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < VW; ++e) acc[e] += b[e];
+}
+
+// Publishes the partial vectors (zero for threads of a row group without
+// rows), one barrier, and returns the total for the owner of an output
+// (red_off >= 0), else 0.  The caller must barrier before `swp` is reused.
+template <typename T>
+__device__ inline T sweep_reduce(const SweepPlan& p, const T* acc, T* swp) {
+  constexpr int VW = Vec16<T>::W;
+  using V = typename Vec16<T>::type;
+  if (p.slot < p.G * (p.pstride / VW)) {
+    V o;
+    T* op = reinterpret_cast<T*>(&o);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) op[e] = acc[e];
+    reinterpret_cast<V*>(swp)[p.slot] = o;
+  }
+  __syncthreads();
+  T sum = T(0);
+  if (p.red_off >= 0) {
+    const T* ps = swp + p.red_off;
+#pragma unroll 4
+    for (int g = 0; g < p.G; ++g) sum += ps[g * p.pstride];
+  }
+  return sum;
+}
+
+// One block: partial sums, one barrier, reduction.
+template <typename T>
+__device__ inline T sweep_run(const SweepPlan& p, const T* blk, const T* x, T* swp) {
+  constexpr int VW = Vec16<T>::W;
+  T acc[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) acc[e] = T(0);
+  sweep_partial<T>(p, blk, x, acc);
+  return sweep_reduce<T>(p, acc, swp);
+}
+
 }  // namespace gsls

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   __syncthreads();
   QPDesc& d = dsh;
 
-  const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
+  const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.nch, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
                                      (int)sizeof(T));
   Ctx<T> c;
   c.d = &d;
@@ -72,10 +72,21 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   c.part = reinterpret_cast<double*>(smem + lay.part);
   c.perm = reinterpret_cast<int*>(smem + lay.perm);
   c.flag = reinterpret_cast<int*>(smem + lay.flag);
+  c.bar = reinterpret_cast<unsigned long long*>(smem + lay.bar);
+  c.swp = reinterpret_cast<T*>(smem + lay.swp);
+  c.gath = reinterpret_cast<T*>(smem + lay.gath);
+  c.ws = c.wp = 0;
+  c.inflight = c.ipar = 0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < d.depth; ++k) mbar_init(&c.bar[k], 1);
+    mbar_init_fence();
+    c.flag[RING_FLAG] = 0;
+  }
+  __syncthreads();
   c.msz = d.nx * d.ldx;
   c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
   const int t = threadIdx.x;
-  c.prof = (args.prof && qi == 0 && rank == 0 && t == 0) ? args.prof : nullptr;
+  c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
   c.t_last = clock64();
 
   if (args.mode == MODE_KKT) {
@@ -139,11 +150,15 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
       Partials pl;
       admm_iteration<T>(c, cl, rho, check, pl);
       if (!check) continue;
-      double v[4] = {pl.rp, pl.rd, pl.vm, pl.zm};
-      cluster_max(c, cl, v, 4);
+      double v[5] = {pl.rp, pl.rd, pl.vm, pl.zm, c.flag[RING_FLAG] ? 1.0 : 0.0};
+      cluster_max(c, cl, v, 5);
       prof_mark(c, PH_CHECK);
       rp = v[0];
       rd = v[1];
+      if (v[4] > 0.0) {
+        status = GPUSLS_ERR_TIMEOUT;
+        break;
+      }
       if (!(isfinite(rp) && isfinite(rd))) {
         status = GPUSLS_ERR_NAN;
         break;
@@ -245,6 +260,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     d.flags[1] = 0;
     d.flags[2] = fell_back;
   }
+  ring_drain<T>(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -314,11 +330,13 @@ static int auto_cluster(int N) {
 template <typename T>
 static int launch_qp(qp_handle* h, const SolveArgs& a) {
   auto kern = qp_kernel<T>;
-  CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem));
+  int smem = h->smem;
+  if (const char* e = getenv("GPUSLS_SMEM_MIN")) smem = std::max(smem, std::min(atoi(e), 227 * 1024));
+  CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(h->batch * h->cs, 1, 1);
   cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = h->smem;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = h->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -332,28 +350,34 @@ static int launch_qp(qp_handle* h, const SolveArgs& a) {
   return GPUSLS_OK;
 }
 
-// Debug aid: GPUSLS_PROFILE=1 accumulates per-phase cycle counts of rank 0 of
-// QP 0 and prints them to stderr after each launch.
+// Debug aid: GPUSLS_PROFILE=1 accumulates per-phase cycle counts of every CTA
+// of QP 0 and prints them to stderr after each launch.
 static int launch(qp_handle* h, const SolveArgs& a0) {
   SolveArgs a = a0;
   static const bool prof_on = getenv("GPUSLS_PROFILE") != nullptr;
   unsigned long long* dprof = nullptr;
+  const int nprof = MAXCS * PH_COUNT;
   if (prof_on) {
-    CU(cudaMalloc(&dprof, PH_COUNT * sizeof(unsigned long long)));
-    CU(cudaMemsetAsync(dprof, 0, PH_COUNT * sizeof(unsigned long long), h->stream));
+    CU(cudaMalloc(&dprof, nprof * sizeof(unsigned long long)));
+    CU(cudaMemsetAsync(dprof, 0, nprof * sizeof(unsigned long long), h->stream));
     a.prof = dprof;
   }
   const int st = h->esz == 8 ? launch_qp<double>(h, a) : launch_qp<float>(h, a);
   if (prof_on) {
-    unsigned long long hp[PH_COUNT];
+    unsigned long long hp[MAXCS * PH_COUNT];
     CU(cudaMemcpyAsync(hp, dprof, sizeof(hp), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     cudaFree(dprof);
     static const char* names[PH_COUNT] = {"P1", "bwd", "sync1", "P3", "fwd", "sync2", "P5", "check", "rho",
-                                          "R1", "R2", "R3", "R4", "R5", "R6", "kkt"};
-    fprintf(stderr, "[gpusls prof cycles]");
-    for (int k = 0; k < PH_COUNT; ++k) fprintf(stderr, " %s=%llu", names[k], hp[k]);
-    fprintf(stderr, "\n");
+                                          "R1", "R2", "R3", "R4", "R5", "R6", "kkt", "ringwait(incl)"};
+    for (int r = 0; r < MAXCS; ++r) {
+      unsigned long long tot = 0;
+      for (int k = 0; k < PH_COUNT; ++k) tot += hp[r * PH_COUNT + k];
+      if (!tot) continue;
+      fprintf(stderr, "[gpusls prof cycles rank %d]", r);
+      for (int k = 0; k < PH_COUNT; ++k) fprintf(stderr, " %s=%llu", names[k], hp[r * PH_COUNT + k]);
+      fprintf(stderr, "\n");
+    }
   }
   return st;
 }
@@ -485,9 +509,9 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     D_.slot = std::max(std::max(std::max(bws, fws), (int)msz),
                        std::max(std::max(d.nx * (int)ldu, d.nx * (int)ldc), cds));
     D_.depth = 3;
-    if (smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, (int)ldx, (int)ldu, ldv, ldf, 3, D_.slot, esz).total > 227 * 1024)
+    if (smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, D_.nch, (int)ldx, (int)ldu, ldv, ldf, 3, D_.slot, esz).total > 227 * 1024)
       D_.depth = 2;
-    const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, (int)ldx, (int)ldu, ldv, ldf, D_.depth,
+    const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, D_.nch, (int)ldx, (int)ldu, ldv, ldf, D_.depth,
                                        D_.slot, esz);
     smem = std::max(smem, lay.total);
   }

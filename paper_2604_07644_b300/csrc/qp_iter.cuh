@@ -26,45 +26,83 @@ __device__ inline int own_rows(Ctx<T>& c) {
 }
 
 // ---------------------------------------------------------------------------
-// cp.async ring over the union region: slot k holds block k % depth.
+// Bulk-copy ring over the union region.  Blocks go round the `depth` slots in
+// order; the k-th use of a slot completes phase k of its mbarrier, so a
+// consumer waits on parity k & 1.  One thread issues the copies; every thread
+// waits on the slot's mbarrier itself (no barrier between arrival and use).
+// The ring position (slot, parity) is carried across streams in Ctx, so no
+// division is needed per block.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ inline T* ring_slot(Ctx<T>& c, int k) {
-  return c.ring + (size_t)(k % c.d->depth) * c.d->slot;
-}
-
 template <typename T>
 struct Blk {
   const T* ptr;
   int bytes;
 };
 
-// Stream nblk blocks (src(b) -> Blk) through the ring, depth-1 blocks ahead
-// of the compute f(b, slot).  Every block must fit a slot.
+__device__ inline void ring_advance(unsigned& slot, unsigned& par, unsigned depth) {
+  if (++slot == depth) {
+    slot = 0;
+    par ^= 1u;
+  }
+}
+
+// Stream nblk blocks (src(b) -> Blk) through the ring, depth-1 blocks ahead of
+// the compute f(b, slot).  Every block must fit a slot; addresses 16-byte
+// aligned, sizes multiples of 16 bytes.  A wait that gives up sets
+// flag[RING_FLAG]; from then on the CTA issues and waits for nothing more (the
+// iteration runs to its end on stale data and the solve reports
+// GPUSLS_ERR_TIMEOUT).
 template <typename T, typename Src, typename Fn>
 __device__ void stream_blocks(Ctx<T>& c, int nblk, Src src, Fn f) {
-  const int depth = c.d->depth;
-  for (int b = 0; b < depth - 1; ++b) {
-    if (b < nblk) {
-      const Blk<T> k = src(b);
-      cta_stage(ring_slot(c, b), k.ptr, k.bytes);
-    }
-    cp_async_commit();
-  }
-  for (int b = 0; b < nblk; ++b) {
-    if (b + depth - 1 < nblk) {
-      const Blk<T> k = src(b + depth - 1);
-      cta_stage(ring_slot(c, b + depth - 1), k.ptr, k.bytes);
-    }
-    cp_async_commit();
-    if (depth >= 3) cp_async_wait<2>();
-    else cp_async_wait<1>();
-    __syncthreads();
-    f(b, (const T*)ring_slot(c, b));
-    __syncthreads();
-  }
-  cp_async_wait<0>();
+  const unsigned depth = (unsigned)c.d->depth;
+  const size_t slot_el = (size_t)c.d->slot;
+  T* const ring = c.ring;
+  unsigned long long* const bar = c.bar;
+  int* const flag = c.flag;
+  unsigned long long* const prof = c.prof;
+  const bool issuer = threadIdx.x == 0;
+  fence_proxy_async();     // earlier generic accesses of the ring region come first
   __syncthreads();
+  bool dead = flag[RING_FLAG] != 0;
+  unsigned ws = c.ws, wp = c.wp;          // next slot to consume, its parity
+  unsigned is = ws, ip = wp;              // next slot to fill (issuer)
+  unsigned inflight = c.inflight, ipar = c.ipar;
+  auto issue = [&](int b) {
+    const Blk<T> k = src(b);
+    bulk_g2s(ring + is * slot_el, k.ptr, (unsigned)k.bytes, &bar[is]);
+    inflight |= 1u << is;
+    ipar = (ipar & ~(1u << is)) | (ip << is);
+    ring_advance(is, ip, depth);
+  };
+  if (issuer && !dead)
+    for (int b = 0; b < nblk && b < (int)depth - 1; ++b) issue(b);
+  for (int b = 0; b < nblk; ++b) {
+    if (!dead) {
+      if (issuer && b + (int)depth - 1 < nblk) issue(b + (int)depth - 1);
+      const long long tw = prof ? clock64() : 0;
+      if (mbar_wait(&bar[ws], wp, RING_WAIT_LIMIT)) inflight &= ~(1u << ws);
+      else flag[RING_FLAG] = 1;
+      if (prof) prof[PH_RINGWAIT] += (unsigned long long)(clock64() - tw);
+    }
+    f(b, (const T*)(ring + ws * slot_el));
+    __syncthreads();
+    dead = flag[RING_FLAG] != 0;
+    ring_advance(ws, wp, depth);
+  }
+  c.ws = ws;
+  c.wp = wp;
+  c.inflight = inflight;
+  c.ipar = ipar;
+}
+
+// Before the CTA exits: if a ring wait gave up, the issuing thread waits
+// (bounded) for every copy it started that was not seen to complete, so that
+// none lands after the CTA's shared memory is gone.
+template <typename T>
+__device__ void ring_drain(Ctx<T>& c) {
+  if (threadIdx.x != 0 || c.flag[RING_FLAG] == 0) return;
+  for (unsigned sl = 0; sl < (unsigned)c.d->depth; ++sl)
+    if ((c.inflight >> sl) & 1u) mbar_wait(&c.bar[sl], (c.ipar >> sl) & 1u, RING_WAIT_LIMIT);
 }
 
 struct Partials {
@@ -115,23 +153,24 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
     }
     __syncthreads();
     prof_mark(c, PH_P1);
-    // P2: backward chain over the BW bundles: threads j < nx sweep [Abar; CK]
-    // for l_i, threads 128 + a sweep [F | J]^T for k~_i.
+    // P2: backward chain over the BW bundles: one split sweep of
+    // [Abar; CK | (F | J)^T] per stage gives l_i (t < nx) and k~_i.
     const int R = nx + nc;
-    stream_blocks<T>(
-        c, L, [&](int st) { return Blk<T>{BW + (size_t)(c.e - 1 - st) * bws, bws * (int)sizeof(T)}; },
-        [&](int st, const T* S) {
-          const int li = L - 1 - st;
-          const T* xin = c.lS + (size_t)(li + 1) * ldv;
-          const T* fjt = S + (size_t)R * ldx;
-          const T* c0b = fjt + (size_t)R * ldu;
-          if (t < nx) {
-            c.lS[(size_t)li * ldv + t] = c0b[t] + col_dot(S, ldx, R, t, xin);
-          } else if (t >= 128 && t < 128 + nu) {
-            const int a = t - 128;
-            c.ktS[li * ldu + a] = c0b[ldx + a] + col_dot(fjt, ldu, R, a, xin);
-          }
-        });
+    {
+      const SweepPlan sp = sweep_plan<T>(R, nx, ldx, nu, ldu, R * ldx);
+      T* const lS = c.lS;
+      T* const ktS = c.ktS;
+      T* const swp = c.swp;
+      const int c0o = t < nx ? R * ldx + R * ldu + t : R * ldx + R * ldu + ldx + (t - nx);
+      stream_blocks<T>(
+          c, L, [&](int st) { return Blk<T>{BW + (size_t)(c.e - 1 - st) * bws, bws * (int)sizeof(T)}; },
+          [&](int st, const T* S) {
+            const int li = L - 1 - st;
+            const T y = sweep_run<T>(sp, S, lS + (size_t)(li + 1) * ldv, swp);
+            if (t < nx) lS[(size_t)li * ldv + t] = S[c0o] + y;
+            else if (t < nx + nu) ktS[li * ldu + t - nx] = S[c0o] + y;
+          });
+    }
     for (int j = t; j < nx; j += NT) c.slotL[j] = c.lS[j];
     prof_mark(c, PH_BWD);
   }
@@ -140,20 +179,41 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
   // P3: boundary p_e from the later chunks, then k_i = k~_i + FPi_i p_e.
   if (c.active) {
     if (!c.last) {
-      const T* rem = cl.map_shared_rank(c.slotL, c.rank + 1);
-      for (int j = t; j < nx; j += NT) c.pe[j] = rem[j];
+      // the later chunks' local results l_m (m = rank+1 .. nch-1), gathered
+      // in one round of distributed shared memory reads
+      const int nlat = d.nch - 1 - c.rank;
+      T* const gath = c.gath;
+      for (int e2 = t; e2 < nlat * nx; e2 += NT) {
+        const int m = e2 / nx;
+        gath[e2] = cl.map_shared_rank(c.slotL, c.rank + 1 + m)[e2 - m * nx];
+      }
+      __syncthreads();
+      // p_e = l_{rank+1} + sum_m Theta_{rank,m} l_m over m = rank+2 .., one
+      // split sweep accumulated across the streamed Theta blocks
+      constexpr int VW = Vec16<T>::W;
       const int m0 = c.rank + 2, nb = d.nch - m0;
+      const SweepPlan sp = sweep_plan<T>(nx, nx, ldx, 0, ldx, 0);
+      T acc[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) acc[e] = T(0);
       stream_blocks<T>(
           c, nb, [&](int b) { return Blk<T>{Theta + (size_t)(c.rank * MAXCS + m0 + b) * msz, msz * (int)sizeof(T)}; },
-          [&](int b, const T* S) {
-            const T* rm = cl.map_shared_rank(c.slotL, m0 + b);
-            for (int j = t; j < nx; j += NT) c.tmp1[j] = rm[j];
-            __syncthreads();
-            if (t < nx) c.pe[t] += col_dot(S, ldx, nx, t, c.tmp1);
-          });
+          [&](int b, const T* S) { sweep_partial<T>(sp, S, gath + (size_t)(b + 1) * nx, acc); });
+      {
+        const T y = sweep_reduce<T>(sp, acc, c.swp);
+        if (t < nx) c.pe[t] = gath[t] + y;
+        __syncthreads();
+      }
+      // k_i = k~_i + FPi_i p_e for own stages, Gs stages per streamed block
       const int per = nx * ldu;   // FPi_i^T
-      const int Gs = max(1, d.slot / per);
+      const int Gs = min(max(1, d.slot / per), NT / nu);
       const int nbk = (L + Gs - 1) / Gs;
+      const SweepPlan fp = sweep_plan_batched<T>(nx, nu, ldu, Gs, per);
+      T* const xS = c.xS;
+      const T* const ktS = c.ktS;
+      const T* const pe = c.pe;
+      T* const swp = c.swp;
+      const int ls_t = t / nu, a_t = t - ls_t * nu;
       stream_blocks<T>(
           c, nbk,
           [&](int b) {
@@ -161,11 +221,9 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
             return Blk<T>{FPi + (size_t)(s + b * Gs) * per, n_st * per * (int)sizeof(T)};
           },
           [&](int b, const T* S) {
-            const int n_st = min(Gs, L - b * Gs);
-            for (int pr = t; pr < n_st * nu; pr += NT) {
-              const int ls = pr / nu, a = pr - ls * nu, li = b * Gs + ls;
-              c.xS[(size_t)li * ldf + nx + a] = c.ktS[li * ldu + a] + col_dot(S + (size_t)ls * per, ldu, nx, a, c.pe);
-            }
+            const T y = sweep_run<T>(fp, S, pe, swp);
+            const int li = b * Gs + ls_t;
+            if (t < Gs * nu && li < L) xS[(size_t)li * ldf + nx + a_t] = ktS[li * ldu + a_t] + y;
           });
     } else {
       for (int e2 = t; e2 < L * nu; e2 += NT) {
@@ -179,17 +237,20 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
     // P4: forward chain over the FW^T bundles: thread r < nx + nc sweeps
     // column r of FW^T for lx_{i+1} (r < nx) or v~_i (r >= nx).
     const int R = nx + nc, Cn = nx + nu;
-    stream_blocks<T>(
-        c, L, [&](int st) { return Blk<T>{FW + (size_t)(s + st) * fws, fws * (int)sizeof(T)}; },
-        [&](int st, const T* S) {
-          const T* xin = c.xS + (size_t)st * ldf;
-          const T* bvec = S + (size_t)Cn * ldv;
-          for (int r = t; r < R; r += NT) {
-            const T v = col_dot(S, ldv, Cn, r, xin);
-            if (r < nx) c.xS[(size_t)(st + 1) * ldf + r] = v + bvec[r];
-            else c.vS[st * nc + r - nx] = v;
-          }
-        });
+    {
+      const SweepPlan sp = sweep_plan<T>(Cn, R, ldv, 0, ldv, 0);
+      T* const xS = c.xS;
+      T* const vS = c.vS;
+      T* const swp = c.swp;
+      const int bo = Cn * ldv + t;
+      stream_blocks<T>(
+          c, L, [&](int st) { return Blk<T>{FW + (size_t)(s + st) * fws, fws * (int)sizeof(T)}; },
+          [&](int st, const T* S) {
+            const T y = sweep_run<T>(sp, S, xS + (size_t)st * ldf, swp);
+            if (t < nx) xS[(size_t)(st + 1) * ldf + t] = y + S[bo];
+            else if (t < R) vS[st * nc + t - nx] = y;
+          });
+    }
     for (int j = t; j < nx; j += NT) c.slotX[j] = c.xS[(size_t)L * ldf + j];
     prof_mark(c, PH_FWD);
   }
@@ -199,22 +260,41 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
   // projection and scaled dual update.
   if (c.active) {
     if (!c.first) {
-      const T* rem = cl.map_shared_rank(c.slotX, c.rank - 1);
-      for (int j = t; j < nx; j += NT) c.xs[j] = rem[j];
-      const int nb = c.rank - 1;   // m = rank-2 .. 0
+      // the earlier chunks' end states lx_m (m = rank-1 .. 0), gathered in one
+      // round of distributed shared memory reads: gath row j = chunk rank-1-j
+      const int near = c.rank;
+      T* const gath = c.gath;
+      for (int e2 = t; e2 < near * nx; e2 += NT) {
+        const int j = e2 / nx;
+        gath[e2] = cl.map_shared_rank(c.slotX, c.rank - 1 - j)[e2 - j * nx];
+      }
+      __syncthreads();
+      // x_s = lx_{rank-1} + sum_m Xi_{rank,m} lx_m over m = rank-2 .. 0
+      constexpr int VW = Vec16<T>::W;
+      const int nb = c.rank - 1;
+      const SweepPlan sp = sweep_plan<T>(nx, nx, ldx, 0, ldx, 0);
+      T acc[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) acc[e] = T(0);
       stream_blocks<T>(
           c, nb, [&](int b) { return Blk<T>{Xi + (size_t)(c.rank * MAXCS + (c.rank - 2 - b)) * msz, msz * (int)sizeof(T)}; },
-          [&](int b, const T* S) {
-            const T* rm = cl.map_shared_rank(c.slotX, c.rank - 2 - b);
-            for (int j = t; j < nx; j += NT) c.tmp1[j] = rm[j];
-            __syncthreads();
-            if (t < nx) c.xs[t] += col_dot(S, ldx, nx, t, c.tmp1);
-          });
+          [&](int b, const T* S) { sweep_partial<T>(sp, S, gath + (size_t)(b + 1) * nx, acc); });
+      {
+        const T y = sweep_reduce<T>(sp, acc, c.swp);
+        if (t < nx) c.xs[t] = gath[t] + y;
+        __syncthreads();
+      }
+      // v_i += CKSig_i x_s for own stages, Gs stages per streamed block
       const int ldc = d.ldc;
       const int per = nx * ldc;   // CKSig_i^T
       if (nc > 0) {
-        const int Gs = max(1, d.slot / per);
+        const int Gs = min(max(1, d.slot / per), NT / nc);
         const int nbk = (L + Gs - 1) / Gs;
+        const SweepPlan cp = sweep_plan_batched<T>(nx, nc, ldc, Gs, per);
+        T* const vS = c.vS;
+        const T* const xs = c.xs;
+        T* const swp = c.swp;
+        const int ls_t = t / nc, r_t = t - ls_t * nc;
         stream_blocks<T>(
             c, nbk,
             [&](int b) {
@@ -222,11 +302,9 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
               return Blk<T>{CKSig + (size_t)(s + b * Gs) * per, n_st * per * (int)sizeof(T)};
             },
             [&](int b, const T* S) {
-              const int n_st = min(Gs, L - b * Gs);
-              for (int pr = t; pr < n_st * nc; pr += NT) {
-                const int ls = pr / nc, rr = pr - ls * nc, li = b * Gs + ls;
-                c.vS[li * nc + rr] += col_dot(S + (size_t)ls * per, ldc, nx, rr, c.xs);
-              }
+              const T y = sweep_run<T>(cp, S, xs, swp);
+              const int li = b * Gs + ls_t;
+              if (t < Gs * nc && li < L) vS[li * nc + r_t] += y;
             });
       }
     }

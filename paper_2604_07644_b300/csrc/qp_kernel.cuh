@@ -64,7 +64,7 @@ struct QPDesc {
 enum Mode { MODE_SOLVE = 0, MODE_RICCATI = 1, MODE_KKT = 2 };
 
 struct SolveArgs {
-  unsigned long long* prof;   // optional per-phase cycle counters (rank 0 of QP 0), else null
+  unsigned long long* prof;   // optional per-phase cycle counters [cs][phases] of QP 0, else null
   int mode;
   int max_iter;
   int fixed_iters;
@@ -97,14 +97,18 @@ constexpr int MAXCS_SMEM = 8;
 struct SmemLayout {
   int ring, gemm, gj, gjbuf;                 // union region
   int z, y, w, l, x, kt, v, d, u, pe, xs, slotL, slotX, tmp1, tmp2, tmp3, red;
-  int part, perm, flag;
+  int part, perm, flag, bar, swp, gath;
   int total;
 };
 
+constexpr int MAX_RING = 8;   // ring slots (mbarriers) at most
+constexpr int RING_FLAG = 8;  // index in the shared flag[] array: a ring wait gave up
+constexpr int RING_WAIT_LIMIT = 1 << 22;   // polls of one bulk-copy completion before giving up
+
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf, int Lc, int ldx, int ldu, int ldv,
-                                                  int ldf, int depth, int slot, int esz) {
+__host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf, int Lc, int nch, int ldx, int ldu,
+                                                  int ldv, int ldf, int depth, int slot, int esz) {
   SmemLayout s;
   int off = 0;
   const int ring_b = depth * slot * esz;
@@ -136,6 +140,23 @@ __host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf
   s.part = off; off = al16(off + (16 + MAXCS_SMEM * 8) * 8);
   s.perm = off; off = al16(off + 2 * TILE * 4);
   s.flag = off; off = al16(off + 16 * 4);
+  s.bar = off; off = al16(off + MAX_RING * 8);
+  // sweep partials and the gathered chunk-boundary vectors go in the union
+  // region's slack after the ring when the dense scratch is the larger part
+  // of it, else in regions of their own
+  int slack = al16(ring_b);
+  const int uend = al16(uni);
+  const int gath_b = (nch > 1 ? nch - 1 : 1) * ldx * esz;
+  if (slack + SWEEP_SMEM_BYTES <= uend) {
+    s.swp = slack; slack = al16(slack + SWEEP_SMEM_BYTES);
+  } else {
+    s.swp = off; off = al16(off + SWEEP_SMEM_BYTES);
+  }
+  if (slack + gath_b <= uend) {
+    s.gath = slack; slack = al16(slack + gath_b);
+  } else {
+    s.gath = off; off = al16(off + gath_b);
+  }
   s.total = off;
   return s;
 }
@@ -150,15 +171,20 @@ struct Ctx {
   T *zS, *yS, *wS, *lS, *xS, *ktS, *vS, *dS, *uS, *pe, *xs, *slotL, *slotX, *tmp1, *tmp2, *tmp3, *red;
   double* part;
   int *perm, *flag;
+  unsigned long long* bar;   // ring mbarriers, one per slot
+  T* swp;                    // sweep partials
+  T* gath;                   // chunk-boundary vectors gathered from the other CTAs
+  unsigned ws, wp;           // ring: next slot to consume and its phase parity (same in every thread)
+  unsigned inflight, ipar;   // issuing thread: slots with a copy not yet seen complete, their parities
   T* scr;   // per-CTA global scratch: 6 matrices nx x ldx
   int msz;  // nx * ldx
-  unsigned long long* prof;  // non-null only in thread 0 of rank 0 of QP 0 when profiling
+  unsigned long long* prof;  // non-null only in thread 0 of each CTA of QP 0 when profiling
   long long t_last;
 };
 
 // Phase timers (debug aid; compiled in, inactive unless SolveArgs.prof is set).
 enum Phase { PH_P1 = 0, PH_BWD, PH_SYNC1, PH_P3, PH_FWD, PH_SYNC2, PH_P5, PH_CHECK, PH_RHO, PH_R1, PH_R2, PH_R3,
-             PH_R4, PH_R5, PH_R6, PH_KKT, PH_COUNT };
+             PH_R4, PH_R5, PH_R6, PH_KKT, PH_RINGWAIT, PH_COUNT };
 template <typename T>
 __device__ inline void prof_mark(Ctx<T>& c, int ph) {
   if (c.prof) {
