@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--fallback", type=int, default=2000)
+    p.add_argument("--no-autotune", action="store_true", help="keep --cluster instead of tuning the launch shape")
+    p.add_argument("--eager", action="store_true", help="time the step as separate calls instead of the graph")
     p.add_argument("--model", default=os.path.join(ROOT, "paper_2604_07644_b300", "warmstart_quadruped61.npz"))
     return p.parse_args()
 
@@ -216,17 +218,29 @@ def main():
     settings = native.default_settings(precision=prec, cluster=args.cluster, max_refine=3,
                                        fallback_iters=args.fallback, max_iter=6000,
                                        eps_floor=1e-5 if prec == native.GPUSLS_FP32 else 1e-7)
+    tuned = None
+    if not args.no_autotune:
+        from paper_2604_07644_b300 import autotune
+        cache = autotune.Cache(os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else None)
+        settings, tuned = autotune.choose(qps, settings, expected_iters=250, cache=cache)
     with torch.cuda.stream(stream):
         hb = QPBatch(qps, settings, stream=stream, device=dev)
         mlp = learned.load(args.model, max_batch=args.batch, stream=stream)
         feats = torch.from_numpy(learned.features(qps)).to(dev)
+        g_learned = None if args.eager else hb.graph(mlp, feats)
+        g_cold = None if args.eager else hb.graph()
 
     def step_learned():
+        if g_learned is not None:
+            return g_learned.launch(stream)
         hb.reset()
         mlp.warm_start(hb, feats)
         return hb.solve(fetch=False)
 
     def step_cold():
+        if g_cold is not None:
+            return g_cold.launch(stream)
         hb.reset()
         return hb.solve(fetch=False)
 
@@ -254,6 +268,12 @@ def main():
     value = t_ms / (args.steps * args.batch * ws)
 
     def read_info(warm: bool):
+        g = g_learned if warm else g_cold
+        if g is not None:
+            g.launch(stream)
+            stream.synchronize()
+            from types import SimpleNamespace
+            return [SimpleNamespace(**d) for d in g.info()]
         info = (native.qp_info * args.batch)()
         hb.reset()
         if warm:
@@ -344,7 +364,10 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": "quadruped-shaped LTV-QP family (nx=61 nu=12 N=100 nc=20 nf=8), held-out "
                                        "instances; learned warm start + batched persistent solve",
-                           "batch": args.batch, "precision": args.precision, "cluster": args.cluster,
+                           "batch": args.batch, "precision": args.precision,
+                           "cluster": int(settings.cluster), "occupancy": int(settings.occupancy),
+                           "launch_shape": ("autotuned" if tuned is not None else "fixed"),
+                           "step": "eager calls" if args.eager else "one CUDA graph per step",
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (FP64 pools 2.2 GB per 256 QPs)",
                            "model": os.path.basename(args.model)},

@@ -69,7 +69,8 @@ typedef struct qp_settings {
                              (qp_set_warm_start / qp_warm_start_mlp) and has not
                              converged after this many iterations restarts cold
                              (z = y = 0, setup rho) within the same solve        */
-  int32_t pad;
+  int32_t occupancy; /* 0: as many CTAs per SM as fit; 1: one CTA per SM (the
+                         shared-memory request is raised to force it)        */
   double eps_floor;   /* the KKT gate divides eps by 10 on failure, not below this;
                          at the floor a failing KKT check triggers a refinement:
                          r <- r + (FP64 u-stationarity residual)                   */
@@ -254,6 +255,33 @@ void mlp_destroy(mlp_handle* h);
  * rho_max), y = Y[m:2m] / rho (Y[m:2m] predicts the unscaled multiplier).
  * Runs on the network's stream; give both handles the same stream. */
 int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max);
+
+/* ------------------------------------------------------------------------ */
+/* Serving graph: one batched serving step captured as a CUDA graph         */
+/* ------------------------------------------------------------------------ */
+/* qp_graph_create captures one serving step of the batch held by q into a
+ * CUDA graph (on a private stream; nothing runs at creation):
+ *   qp_reset -> learned warm start from features [batch][n_in] (only when
+ *   m != NULL; same rules as qp_warm_start_mlp) -> x0 taken from the device
+ *   pool x0 (qp_solve layout) -> the persistent solve kernel (settings of q)
+ *   -> per-QP results copied to the device arrays info_i [batch][8] (status,
+ *   iters, refactors, refines, fallback, 0, 0, 0) and info_d [batch][4] (rho,
+ *   r_prim, r_dual, kkt); either may be NULL.
+ * dx, du, lam: device outputs in the qp_solve layouts.  Every pointer given
+ * here is baked into the graph: the buffers must stay valid, and be refilled
+ * in place, while the graph exists.  Problem data may change between
+ * launches through qp_update (same dims).  While a graph exists, calls that
+ * rewrite the output pointers of q (qp_solve, qp_riccati) must not run
+ * between launches.
+ * qp_graph_launch replays the step on `stream` (no host synchronization, no
+ * host copies).  Errors: GPUSLS_ERR_INVALID for null handles or pointers,
+ * GPUSLS_ERR_CUDA if capture, instantiation or launch fails. */
+typedef struct qp_graph qp_graph;
+int qp_graph_create(qp_graph** g, qp_handle* q, mlp_handle* m, const float* features, const double* x0,
+                    double* dx, double* du, double* lam, int32_t* info_i, double* info_d,
+                    double rho_min, double rho_max);
+int qp_graph_launch(qp_graph* g, void* stream);
+void qp_graph_destroy(qp_graph* g);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free KKT residual (the paper has no counterpart)              */

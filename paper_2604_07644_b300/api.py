@@ -82,6 +82,7 @@ class QPBatch:
         self.out_u = torch.zeros(max(1, sum(self.sizes["u"])), dtype=torch.float64, device=device)
         self.out_l = torch.zeros(max(1, sum(self.sizes["m"])), dtype=torch.float64, device=device)
         self.x0 = pool([qp.x0 for qp in self.qps], device)
+        self._graphs = []
 
     # -- helpers ---------------------------------------------------------
     def _split(self, t: torch.Tensor, key: str, shapes):
@@ -162,10 +163,60 @@ class QPBatch:
     def reset(self):
         native.check(self.lib.qp_reset(self.h), "qp_reset")
 
+    def graph(self, mlp: "MLP | None" = None, features: torch.Tensor | None = None, rho_min=1e-3,
+              rho_max=1e3) -> "ServeGraph":
+        """Capture one serving step (reset, optional learned warm start, solve)
+        as a CUDA graph (qp_graph_create).  x0, the outputs and `features` are
+        baked in: refill them in place (e.g. self.x0.copy_(...))."""
+        g = ServeGraph(self, mlp, features, rho_min, rho_max)
+        self._graphs.append(g)
+        return g
+
     def close(self):
+        for g in getattr(self, "_graphs", []):
+            g.close()
         if getattr(self, "h", None) is not None:
             self.lib.qp_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ServeGraph:
+    """A QPBatch serving step captured as a CUDA graph: launch() replays reset,
+    the learned warm start (when an MLP was given) and the persistent solve on
+    a stream, with no host synchronization; info() reads the per-QP results."""
+
+    def __init__(self, qb: QPBatch, mlp=None, features=None, rho_min=1e-3, rho_max=1e3):
+        self.lib = qb.lib
+        self.qb = qb
+        self.features = features
+        self.info_i = torch.zeros(qb.B * 8, dtype=torch.int32, device=qb.device)
+        self.info_d = torch.zeros(qb.B * 4, dtype=torch.float64, device=qb.device)
+        g = C.c_void_p()
+        st = self.lib.qp_graph_create(C.byref(g), qb.h, mlp.h if mlp is not None else None, _dptr(features),
+                                      _dptr(qb.x0), _dptr(qb.out_x), _dptr(qb.out_u), _dptr(qb.out_l),
+                                      _dptr(self.info_i), _dptr(self.info_d), float(rho_min), float(rho_max))
+        native.check(st, "qp_graph_create")
+        self.g = g
+
+    def launch(self, stream: torch.cuda.Stream | None = None):
+        native.check(self.lib.qp_graph_launch(self.g, _stream_ptr(stream or self.qb.stream)), "qp_graph_launch")
+
+    def info(self) -> list[dict]:
+        ii = self.info_i.view(self.qb.B, 8).cpu().numpy()
+        dd = self.info_d.view(self.qb.B, 4).cpu().numpy()
+        return [dict(status=int(a[0]), iters=int(a[1]), refactors=int(a[2]), refines=int(a[3]), fallback=int(a[4]),
+                     rho=float(b[0]), r_prim=float(b[1]), r_dual=float(b[2]), kkt=float(b[3])) for a, b in zip(ii, dd)]
+
+    def close(self):
+        if getattr(self, "g", None) is not None:
+            self.lib.qp_graph_destroy(self.g)
+            self.g = None
 
     def __del__(self):
         try:

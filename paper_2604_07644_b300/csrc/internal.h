@@ -46,6 +46,10 @@ struct qp_handle {
 
 namespace gsls {
 int set_error(int code, const std::string& msg);
+// Learned warm start of every QP of q, enqueued on `stream` without host
+// synchronization (graph-capturable).
+int mlp_enqueue_warm_start(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max,
+                           cudaStream_t stream);
 // Factorization only (MODE_RICCATI) without copying results out.
 int qp_refactor_internal(qp_handle* h);
 }  // namespace gsls

@@ -456,7 +456,10 @@ __global__ void warm_assemble_kernel(const QPDesc* __restrict__ descs, const flo
 }
 }  // namespace gsls
 
-extern "C" int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max) {
+// Enqueues the learned warm start of every QP of q on `stream` (no host
+// synchronization and no host copies, so it can be captured into a graph).
+int gsls::mlp_enqueue_warm_start(qp_handle* q, mlp_handle* h, const float* features, double rho_min,
+                                 double rho_max, cudaStream_t stream) {
   if (!q || !h || !features) return set_error(GPUSLS_ERR_INVALID, "qp_warm_start_mlp: null argument");
   if (q->batch > h->maxb) return set_error(GPUSLS_ERR_INVALID, "qp_warm_start_mlp: batch exceeds the network's max batch");
   for (int b = 0; b < q->batch; ++b) {
@@ -464,18 +467,28 @@ extern "C" int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* featu
     if (2 * m + 1 != h->n_out)
       return set_error(GPUSLS_ERR_INVALID, "qp_warm_start_mlp: network output size must be 2 m + 1 for every QP");
   }
-  affine_rows_kernel<<<blocks((size_t)q->batch * h->n_in), 256, 0, h->stream>>>(features, h->Xn, h->xm, h->xs,
-                                                                                  q->batch, h->n_in, 0);
+  const cudaStream_t saved = h->stream;
+  h->stream = stream;
+  affine_rows_kernel<<<blocks((size_t)q->batch * h->n_in), 256, 0, stream>>>(features, h->Xn, h->xm, h->xs,
+                                                                              q->batch, h->n_in, 0);
   int st = forward(h, h->Xn, q->batch);
+  h->stream = saved;
   if (st) return st;
   float* Yd = h->dY;   // denormalized outputs
-  affine_rows_kernel<<<blocks((size_t)q->batch * h->n_out), 256, 0, h->stream>>>(h->Y, Yd, h->ym, h->ys, q->batch,
-                                                                                   h->n_out, 1);
+  affine_rows_kernel<<<blocks((size_t)q->batch * h->n_out), 256, 0, stream>>>(h->Y, Yd, h->ym, h->ys, q->batch,
+                                                                               h->n_out, 1);
   if (q->esz == 8)
-    warm_assemble_kernel<double><<<q->batch, 256, 0, h->stream>>>(q->ddesc, Yd, h->n_out, rho_min, rho_max);
+    warm_assemble_kernel<double><<<q->batch, 256, 0, stream>>>(q->ddesc, Yd, h->n_out, rho_min, rho_max);
   else
-    warm_assemble_kernel<float><<<q->batch, 256, 0, h->stream>>>(q->ddesc, Yd, h->n_out, rho_min, rho_max);
+    warm_assemble_kernel<float><<<q->batch, 256, 0, stream>>>(q->ddesc, Yd, h->n_out, rho_min, rho_max);
   CUM(cudaGetLastError());
+  return GPUSLS_OK;
+}
+
+extern "C" int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max) {
+  if (!h) return set_error(GPUSLS_ERR_INVALID, "qp_warm_start_mlp: null argument");
+  const int st = gsls::mlp_enqueue_warm_start(q, h, features, rho_min, rho_max, h->stream);
+  if (st) return st;
   CUM(cudaStreamSynchronize(h->stream));
   return GPUSLS_OK;
 }

@@ -331,7 +331,9 @@ template <typename T>
 static int launch_qp(qp_handle* h, const SolveArgs& a) {
   auto kern = qp_kernel<T>;
   int smem = h->smem;
-  if (const char* e = getenv("GPUSLS_SMEM_MIN")) smem = std::max(smem, std::min(atoi(e), 227 * 1024));
+  // occupancy 1: ask for more than half of the SM's shared memory, so that
+  // exactly one CTA of this kernel fits an SM
+  if (h->set.occupancy == 1) smem = std::max(smem, 116 * 1024);
   CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(h->batch * h->cs, 1, 1);
@@ -354,7 +356,9 @@ static int launch_qp(qp_handle* h, const SolveArgs& a) {
 // of QP 0 and prints them to stderr after each launch.
 static int launch(qp_handle* h, const SolveArgs& a0) {
   SolveArgs a = a0;
-  static const bool prof_on = getenv("GPUSLS_PROFILE") != nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(h->stream, &cap));
+  const bool prof_on = getenv("GPUSLS_PROFILE") != nullptr && cap == cudaStreamCaptureStatusNone;
   unsigned long long* dprof = nullptr;
   const int nprof = MAXCS * PH_COUNT;
   if (prof_on) {
@@ -689,13 +693,7 @@ static int collect(qp_handle* h, qp_info* info) {
   return worst;
 }
 
-extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double tol, double* dx, double* du,
-                        double* lam, qp_info* info) {
-  if (!h || !x0 || !dx || !du || !lam) return fail(GPUSLS_ERR_INVALID, "qp_solve: null argument");
-  int st = set_x0(h, x0);
-  if (st) return st;
-  st = set_outputs(h, dx, du, lam, 0, 0, false);
-  if (st) return st;
+static SolveArgs solve_args(const qp_handle* h, int32_t iters, double tol) {
   SolveArgs a = {};
   a.mode = MODE_SOLVE;
   a.max_iter = iters > 0 ? iters : h->set.max_iter;
@@ -710,9 +708,120 @@ extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double to
   a.eps_floor = h->set.eps_floor;
   a.max_refine = h->set.max_refine;
   a.fallback_iters = h->set.fallback_iters;
-  st = launch(h, a);
+  return a;
+}
+
+extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double tol, double* dx, double* du,
+                        double* lam, qp_info* info) {
+  if (!h || !x0 || !dx || !du || !lam) return fail(GPUSLS_ERR_INVALID, "qp_solve: null argument");
+  int st = set_x0(h, x0);
+  if (st) return st;
+  st = set_outputs(h, dx, du, lam, 0, 0, false);
+  if (st) return st;
+  st = launch(h, solve_args(h, iters, tol));
   if (st) return st;
   return collect(h, info);
+}
+
+// ---------------------------------------------------------------------------
+// serving graph
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void reset_kernel(const QPDesc* __restrict__ descs, const double* __restrict__ rho0);
+
+struct qp_graph {
+  qp_handle* q = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  PackJob* djobs = nullptr;   // x0 pack jobs (uploaded once)
+  int njobs = 0;
+};
+
+extern "C" void qp_graph_destroy(qp_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->djobs) cudaFree(g->djobs);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  delete g;
+}
+
+extern "C" int qp_graph_create(qp_graph** out, qp_handle* h, mlp_handle* m, const float* features, const double* x0,
+                               double* dx, double* du, double* lam, int32_t* info_i, double* info_d,
+                               double rho_min, double rho_max) {
+  if (!out || !h || !x0 || !dx || !du || !lam || (m && !features))
+    return fail(GPUSLS_ERR_INVALID, "qp_graph_create: null argument");
+  *out = nullptr;
+  qp_graph* g = new qp_graph();
+  g->q = h;
+  auto bail = [&](int code, const std::string& msg) {
+    qp_graph_destroy(g);
+    return fail(code, msg);
+  };
+  // outputs and x0 pack jobs are fixed for the graph's life: set them now
+  int st = set_outputs(h, dx, du, lam, 0, 0, false);
+  if (st) return bail(st, gpusls_last_error());
+  std::vector<PackJob> jobs;
+  size_t tot = 0;
+  for (int b = 0; b < h->batch; ++b) {
+    jobs.push_back({x0 + h->off[b].x0, h->tx0[b], 1, 1, h->dims[b].nx, h->hdesc[b].ldx});
+    tot += h->dims[b].nx;
+  }
+  g->njobs = (int)jobs.size();
+  if (cudaMalloc(&g->djobs, jobs.size() * sizeof(PackJob)) != cudaSuccess)
+    return bail(GPUSLS_ERR_CUDA, "qp_graph_create: cudaMalloc failed");
+  if (cudaMemcpy(g->djobs, jobs.data(), jobs.size() * sizeof(PackJob), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return bail(GPUSLS_ERR_CUDA, "qp_graph_create: upload failed");
+  if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(GPUSLS_ERR_CUDA, "qp_graph_create: cudaStreamCreate failed");
+  // the kernel attributes are set before capture
+  {
+    const int smem = h->set.occupancy == 1 ? std::max(h->smem, 116 * 1024) : h->smem;
+    const cudaError_t e = h->esz == 8
+        ? cudaFuncSetAttribute(qp_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+        : cudaFuncSetAttribute(qp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return bail(GPUSLS_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+  }
+  const cudaStream_t saved = h->stream;
+  h->stream = g->cap;
+  if (cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    h->stream = saved;
+    return bail(GPUSLS_ERR_CUDA, "qp_graph_create: cudaStreamBeginCapture failed");
+  }
+  int est = GPUSLS_OK;
+  if (h->esz == 8) reset_kernel<double><<<h->batch, 256, 0, g->cap>>>(h->ddesc, h->rho0_dev);
+  else reset_kernel<float><<<h->batch, 256, 0, g->cap>>>(h->ddesc, h->rho0_dev);
+  if (m) est = gsls::mlp_enqueue_warm_start(h, m, features, rho_min, rho_max, g->cap);
+  if (!est && cudaMemcpyAsync(h->hdesc[0].x064, x0, tot * sizeof(double), cudaMemcpyDeviceToDevice, g->cap))
+    est = GPUSLS_ERR_CUDA;
+  if (!est) {
+    dim3 grid(32, g->njobs);
+    if (h->esz == 8) pack_kernel<double><<<grid, 256, 0, g->cap>>>(g->djobs);
+    else pack_kernel<float><<<grid, 256, 0, g->cap>>>(g->djobs);
+    est = launch(h, solve_args(h, 0, 0.0));
+  }
+  if (!est && info_i &&
+      cudaMemcpyAsync(info_i, h->info_i, (size_t)h->batch * 8 * sizeof(int), cudaMemcpyDeviceToDevice, g->cap))
+    est = GPUSLS_ERR_CUDA;
+  if (!est && info_d &&
+      cudaMemcpyAsync(info_d, h->info_d, (size_t)h->batch * 4 * sizeof(double), cudaMemcpyDeviceToDevice, g->cap))
+    est = GPUSLS_ERR_CUDA;
+  const cudaError_t ee = cudaStreamEndCapture(g->cap, &g->graph);
+  h->stream = saved;
+  if (est) return bail(est, std::string("qp_graph_create: capture failed: ") + gpusls_last_error());
+  if (ee != cudaSuccess) return bail(GPUSLS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ee));
+  const cudaError_t ei = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (ei != cudaSuccess) return bail(GPUSLS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+  *out = g;
+  return GPUSLS_OK;
+}
+
+extern "C" int qp_graph_launch(qp_graph* g, void* stream) {
+  if (!g || !g->exec) return fail(GPUSLS_ERR_INVALID, "qp_graph_launch: null graph");
+  CU(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+  return GPUSLS_OK;
 }
 
 extern "C" int qp_riccati(qp_handle* h, double* P, double* K) {

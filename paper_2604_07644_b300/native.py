@@ -37,7 +37,7 @@ class qp_settings(C.Structure):
                 ("rho_max", C.c_double), ("sigma", C.c_int32), ("check_every", C.c_int32),
                 ("max_iter", C.c_int32), ("precision", C.c_int32), ("cluster", C.c_int32),
                 ("fixed_iters", C.c_int32), ("max_refine", C.c_int32), ("fallback_iters", C.c_int32),
-                ("pad", C.c_int32), ("eps_floor", C.c_double)]
+                ("occupancy", C.c_int32), ("eps_floor", C.c_double)]
 
 
 class qp_info(C.Structure):
@@ -79,6 +79,9 @@ SIGNATURES = {
     "mlp_train_step": (C.c_int, [P, DP, DP, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
     "mlp_destroy": (None, [P]),
     "qp_warm_start_mlp": (C.c_int, [P, P, DP, C.c_double, C.c_double]),
+    "qp_graph_create": (C.c_int, [C.POINTER(P), P, P, DP, DP, DP, DP, DP, DP, DP, C.c_double, C.c_double]),
+    "qp_graph_launch": (C.c_int, [P, P]),
+    "qp_graph_destroy": (None, [P]),
     "gpusls_kkt_noalloc": (C.c_int, [qp_dims] + [DP] * 18 + [P]),
 }
 

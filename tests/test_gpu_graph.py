@@ -1,0 +1,107 @@
+"""Serving graph (qp_graph_create / qp_graph_launch): one captured step of
+reset, learned warm start and persistent solve gives, bit for bit, the results
+of the same calls made one by one, and stays valid across replays and
+problem updates."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2604_07644_b300 import learned, native
+from paper_2604_07644_b300 import workloads as W
+from paper_2604_07644_b300.api import QPBatch
+
+pytestmark = pytest.mark.gpu
+
+MODEL = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2604_07644_b300", "warmstart_quadruped61.npz")
+
+
+def _snapshot(qb):
+    return qb.out_x.clone(), qb.out_u.clone(), qb.out_l.clone()
+
+
+def _eager(qb, mlp=None, feats=None):
+    qb.reset()
+    if mlp is not None:
+        mlp.warm_start(qb, feats)
+    r = qb.solve(fetch=True)
+    return _snapshot(qb), r.info
+
+
+def _same(a, b):
+    return all(torch.equal(x, y) for x, y in zip(a, b))
+
+
+def test_graph_cold_batch_matches_eager(lib):
+    qps = [W.plain_4d(0), W.random_general(3, 7, 3, 23, 5, 2), W.quadrotor_12d(1, N=20)]
+    st = native.default_settings(precision=native.GPUSLS_FP64, cluster=4)
+    qb = QPBatch(qps, st)
+    ref, info_e = _eager(qb)
+    g = qb.graph()
+    for _ in range(2):                       # replays are independent steps
+        qb.out_x.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        assert _same(_snapshot(qb), ref)
+    info_g = g.info()
+    for a, b in zip(info_g, info_e):
+        assert a["iters"] == b["iters"] and a["status"] == b["status"] and a["kkt"] == b["kkt"]
+    qb.close()
+
+
+def test_graph_learned_warm_start_matches_eager(lib):
+    fam = W.family(0)
+    qps = [fam.instance(100000 + i) for i in range(6)]
+    st = native.default_settings(precision=native.GPUSLS_FP32, cluster=8, max_refine=3, fallback_iters=2000,
+                                 max_iter=6000, eps_floor=1e-5)
+    qb = QPBatch(qps, st)
+    mlp = learned.load(MODEL, max_batch=len(qps))
+    feats = torch.from_numpy(learned.features(qps)).cuda()
+    ref, info_e = _eager(qb, mlp, feats)
+    g = qb.graph(mlp, feats)
+    g.launch()
+    torch.cuda.synchronize()
+    assert _same(_snapshot(qb), ref)
+    assert [i["iters"] for i in g.info()] == [i["iters"] for i in info_e]
+    assert all(i["status"] == native.GPUSLS_OK for i in g.info())
+    mlp.close()
+    qb.close()
+
+
+def test_graph_sees_problem_updates_and_new_x0(lib):
+    """Problem data changed by qp_update and x0 refilled in place between
+    replays: the graph solves the new problem (equal to an eager solve)."""
+    qps = [W.random_general(5, 6, 2, 17, 4, 2), W.random_general(6, 6, 2, 17, 4, 2)]
+    st = native.default_settings(precision=native.GPUSLS_FP64, cluster=2)
+    qb = QPBatch(qps, st)
+    g = qb.graph()
+    g.launch()
+    torch.cuda.synchronize()
+    gen = np.random.default_rng(7)
+    new_q = [qp.q + 0.3 * gen.standard_normal(qp.q.shape) for qp in qps]
+    new_x0 = [qp.x0 + 0.1 * gen.standard_normal(qp.x0.shape) for qp in qps]
+    qb.update(q=new_q)
+    qb.x0.copy_(torch.from_numpy(np.concatenate(new_x0)).to(qb.x0.device))
+    g.launch()
+    torch.cuda.synchronize()
+    got = _snapshot(qb)
+    # eager reference on a fresh handle with the updated problem
+    for qp, q, x0 in zip(qps, new_q, new_x0):
+        qp.q = q
+        qp.x0 = x0
+    qe = QPBatch(qps, st)
+    ref, _ = _eager(qe)
+    assert _same(got, ref)
+    qe.close()
+    qb.close()
+
+
+def test_graph_rejects_null_arguments(lib):
+    qb = QPBatch([W.tiny(0)])
+    import ctypes as C
+    g = C.c_void_p()
+    st = lib.qp_graph_create(C.byref(g), qb.h, None, None, None, None, None, None, None, None, 1e-3, 1e3)
+    assert st == native.GPUSLS_ERR_INVALID
+    assert lib.qp_graph_launch(None, None) == native.GPUSLS_ERR_INVALID
+    qb.close()
