@@ -35,6 +35,7 @@ import numpy as np  # noqa: E402
 METRIC = "ms/QP solve to 1e-4 KKT residual (61D, N=100): learned+batched vs plain ADMM"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
+TRAFFIC_PER_QP_ITER = 6.66e6   # bytes, ncu dram__bytes_read+write per QP-iteration (61D, N=100, FP32)
 
 
 def parse():
@@ -52,6 +53,8 @@ def parse():
     p.add_argument("--fallback", type=int, default=2000)
     p.add_argument("--no-autotune", action="store_true", help="keep --cluster instead of tuning the launch shape")
     p.add_argument("--eager", action="store_true", help="time the step as separate calls instead of the graph")
+    p.add_argument("--case", default="", choices=["", "iter", "refactor", "mlp", "sls"],
+                   help="small fixed case for profiler captures (prints no bench line)")
     p.add_argument("--model", default=os.path.join(ROOT, "paper_2604_07644_b300", "warmstart_quadruped61.npz"))
     return p.parse_args()
 
@@ -189,11 +192,69 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """Small fixed workloads for ncu captures (inputs larger than L2, a few
+    hundred MB on the device):
+      iter      32 quadruped-shaped QPs (FP32), factorized by a first launch;
+                launches 2 and 3 run 100 cached ADMM iterations each (no
+                refactor), so a capture of launch 2 is the iteration alone;
+      refactor  the same batch, three launches that each refactor and run one
+                iteration;
+      mlp       the learned warm start of 256 QPs (BF16 tensor-core GEMMs);
+      sls       SLS synthesis at nx=75, nu=21, N=40 with per-j tau."""
+    import torch
+
+    from paper_2604_07644_b300 import build as B_
+    from paper_2604_07644_b300 import learned, native
+    from paper_2604_07644_b300 import workloads as W
+    from paper_2604_07644_b300.api import SLS, QPBatch
+    B_.build()
+    native.load()
+    fam = W.family(0)
+    if args.case in ("iter", "refactor"):
+        qps = [fam.instance(100000 + i) for i in range(32)]
+        s = native.default_settings(precision=native.GPUSLS_FP32, cluster=8, sigma=0, fixed_iters=1)
+        if args.case == "iter":
+            s.fixed_iters = 100
+        qb = QPBatch(qps, s)
+        qb.reset()
+        qb.solve(fetch=False)                         # launch 1: factorization + iterations
+        for _ in range(2):                            # launches 2, 3
+            if args.case == "refactor":
+                qb.reset()                            # refactor again
+            qb.solve(fetch=False)                     # iter: cached factorization, 100 iterations
+        torch.cuda.synchronize()
+        qb.close()
+    elif args.case == "mlp":
+        qps = [fam.instance(100000 + i) for i in range(256)]
+        qb = QPBatch(qps, native.default_settings(precision=native.GPUSLS_FP32))
+        mlp = learned.load(args.model, max_batch=256)
+        feats = torch.from_numpy(learned.features(qps)).cuda()
+        for _ in range(3):
+            mlp.warm_start(qb, feats)
+        torch.cuda.synchronize()
+        mlp.close()
+        qb.close()
+    elif args.case == "sls":
+        p = W.sls_problem(0, tau_mode="uniform")
+        N, nx = p.A.shape[0], p.A.shape[1]
+        nu, nc, nf = p.B.shape[2], p.C.shape[1], p.CN.shape[0]
+        sls = SLS(nx, nu, N, nc, nf, per_j_tau=True, precision=native.GPUSLS_FP32)
+        for _ in range(2):
+            sls.solve(p, fetch=False)
+        torch.cuda.synchronize()
+        sls.close()
+    print(f"case {args.case} done", flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.case:
+        profile_case(args)
         return
     import torch
 
@@ -221,9 +282,8 @@ def main():
     tuned = None
     if not args.no_autotune:
         from paper_2604_07644_b300 import autotune
-        cache = autotune.Cache(os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else None)
-        settings, tuned = autotune.choose(qps, settings, expected_iters=250, cache=cache)
+        cache = autotune.Cache()
+        settings, tuned = autotune.choose(qps, settings, expected_iters=250, tail_iters=2000, cache=cache)
     with torch.cuda.stream(stream):
         hb = QPBatch(qps, settings, stream=stream, device=dev)
         mlp = learned.load(args.model, max_batch=args.batch, stream=stream)
@@ -346,8 +406,12 @@ def main():
     pk, pk_kind = peaks()
     algo = algorithmic_bytes_per_iter(nx, nu, N, nc, esz) * float(np.sum(iters))
     achieved = algo / (ms_per_step * 1e-3) / 1e9
+    # DRAM bytes per QP-iteration of qp_kernel<float> from the ncu capture of the
+    # iteration-only case (profiles/qp_kernel_iter_quadruped61_b32.md), scaled
+    # by this launch's QP-iterations; must be re-measured when the kernel changes
+    traffic = TRAFFIC_PER_QP_ITER * float(np.sum(iters)) if esz == 4 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "kernel": "qp_kernel (persistent cluster solve)", "peak_kind": pk_kind,
             "algorithmic_bytes_per_launch": algo}
 

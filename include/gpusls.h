@@ -4,7 +4,7 @@
  * Operations follow "Safe Large-Scale Robust Nonlinear MPC in Milliseconds via
  * Reachability-Constrained System Level Synthesis on the GPU":
  *   qp_*   the ADMM solver for the LTV-QP of Sec. III-B (eq. sqp_qp), Sec. IV-A
- *   sls_*  the SLS controller / reachability solve of Sec. III-C and IV-B
+ *   sls_*  the SLS controller / reachability solve of Sec. III-D and IV-B
  *   mlp_*  the learned warm start (no counterpart in the paper)
  *
  * Conventions (all calls):
@@ -181,7 +181,7 @@ int qp_riccati(qp_handle* h, double* P, double* K);
 void qp_destroy(qp_handle* h);
 
 /* ------------------------------------------------------------------------ */
-/* SLS controller synthesis and reachability margins (Sec. III-C, IV-B)     */
+/* SLS controller synthesis and reachability margins (Sec. III-D, IV-B)     */
 /* ------------------------------------------------------------------------ */
 typedef struct sls_handle sls_handle;
 
@@ -194,7 +194,7 @@ int sls_setup(sls_handle** h, qp_dims d, int32_t precision, int32_t per_j_tau, v
 
 /* sls_solve: the SLS controller QP (eq. fastsls_qp) by per-j reverse scans
  * (eq. robust_combin, eq. backward_prop) and forward propagation
- * (eq. forward_prop), plus the margins of Sec. III-C.
+ * (eq. forward_prop), plus the margins of Sec. III-D.
  *   A [N][nx][nx]  B [N][nx][nu]  E [N][nx][nx] (disturbance scaling E_j)
  *   Qbar [nx][nx]  Rbar [nu][nu]  QbarN [nx][nx]   (SPD)
  *   C [N][nc][nx]  D [N][nc][nu]  CN [nf][nx]

@@ -1,4 +1,4 @@
-"""SLS controller synthesis and reachability margins (Sec. III-C, Sec. IV-B,
+"""SLS controller synthesis and reachability margins (Sec. III-D, Sec. IV-B,
 App. B).
 
 Test infrastructure only (see oracle/__init__.py).
@@ -59,7 +59,8 @@ def riccati_j(sp, j: int):
 def solve(sp):
     """Phi_x [N*nx, N*nx] (block row k-1 holds Phi_x_{k,.} for k = 1..N, block
     column j), Phi_u [N*nu, N*nx] (block row k for k = 0..N-1), margins
-    h [N, nc], hf [nf] and the gains {(k, j): K}."""
+    h [N, nc], hf [nf] (the stacked constraint tightenings of Sec. III-D) and
+    the gains {(k, j): K}."""
     N, nx, nu = sp.N, sp.nx, sp.nu
     Phix = np.zeros((N * nx, N * nx))
     Phiu = np.zeros((N * nu, N * nx))
@@ -90,7 +91,7 @@ def block_u(sp, Phiu, k, j):
 
 
 def margins(sp, Phix, Phiu):
-    """Constraint tightenings (Sec. III-C):
+    """Constraint tightenings (Sec. III-D):
     h_k = sum_{j<k} || C_k Phi_x_{k,j} + D_k Phi_u_{k,j} ||_{2,row},
     h^f = sum_{j<N} || C_N Phi_x_{N,j} ||_{2,row}."""
     N = sp.N

@@ -45,7 +45,8 @@ class Result:
 class QPBatch:
     """A handle over one or more LTV-QPs (qp_batch_setup)."""
 
-    def __init__(self, qps, settings: native.qp_settings | None = None, rho=None, stream=None, device="cuda"):
+    def __init__(self, qps, settings: native.qp_settings | None = None, rho=None, stream=None, device="cuda",
+                 pools: dict | None = None):
         self.lib = native.load()
         self.qps = list(qps)
         self.B = len(self.qps)
@@ -56,9 +57,12 @@ class QPBatch:
         for i, qp in enumerate(self.qps):
             dims[i].nx, dims[i].nu, dims[i].N, dims[i].nc, dims[i].nf = qp.dims()
         self.dims = dims
-        self.pools = {f: pool([getattr(qp, f) for qp in self.qps], device) for f in QP_FIELDS}
-        self.pools["lo"] = pool([qp.lo for qp in self.qps], device)
-        self.pools["hi"] = pool([qp.hi for qp in self.qps], device)
+        if pools is not None:          # device pools of another handle over the same QPs (copied at setup)
+            self.pools = pools
+        else:
+            self.pools = {f: pool([getattr(qp, f) for qp in self.qps], device) for f in QP_FIELDS}
+            self.pools["lo"] = pool([qp.lo for qp in self.qps], device)
+            self.pools["hi"] = pool([qp.hi for qp in self.qps], device)
         rho_arr = None
         if rho is not None:
             rho_arr = (C.c_double * self.B)(*([float(rho)] * self.B if np.isscalar(rho) else [float(v) for v in rho]))

@@ -11,11 +11,17 @@ candidates on the caller's own problems and caches the winner per bucket:
     nx buckets 16 / 32 / 64 / 80, N buckets 32 / 64 / 128 / 256 / 1024,
     batch buckets 1 / 8 / 64 / 256 / 4096.
 
-A candidate is scored by the modeled time of a whole solve per QP,
-(t(k2) - t(k1)) / (k2 - k1) * expected_iters + t(k1) - k1 * slope, from two
-fixed-iteration solves of the sample batch (k1 < k2 iterations), so both the
-factorization and the per-iteration cost are weighed.  All timing is done with
-CUDA events on the handle's stream; the tuner itself does no arithmetic of the
+A candidate is scored by the modeled time of one batched solve, per QP:
+
+    max( T_batch(expected_iters),  T_one(tail_iters) ) / batch,
+
+where T(k) = t(k1) + (k - k1) (t(k2) - t(k1)) / (k2 - k1) is the straight line
+through two fixed-iteration timings (k1 < k2 iterations, so the factorization
+and the per-iteration cost are both weighed), T_batch is timed on the whole
+sample batch (throughput: every QP at the mean iteration count) and T_one on
+its first QP alone (latency: the slowest QP of a batch, at tail_iters, bounds
+the batch's makespan however well the rest is packed).  All timing is done
+with CUDA events on the handle's stream; the tuner does no arithmetic of the
 method.
 """
 from __future__ import annotations
@@ -56,6 +62,15 @@ def score(t1: float, t2: float, k1: int, k2: int, expected_iters: float) -> floa
     return (t1 - k1 * slope) + expected_iters * slope
 
 
+def makespan(batch_t: tuple[float, float], one_t: tuple[float, float], k1: int, k2: int, expected_iters: float,
+             tail_iters: float) -> float:
+    """Modeled time of one batched solve: throughput of the batch at the mean
+    iteration count, or the latency of one QP at the tail count, whichever is
+    longer."""
+    return max(score(batch_t[0], batch_t[1], k1, k2, expected_iters),
+               score(one_t[0], one_t[1], k1, k2, tail_iters))
+
+
 @dataclass
 class Choice:
     cluster: int
@@ -93,38 +108,52 @@ class Cache:
             pass
 
 
-def _time_solve(qps, settings, iters: int, reps: int = 2) -> float:
+def _timer(qps, settings, pools=None):
+    """A handle over qps that runs exactly k iterations per solve (no stop
+    test, fixed rho), and a function timing one reset + solve of k iterations
+    (best of two, after one warm-up)."""
     import torch
 
-    from .api import QPBatch
+    from .api import QPBatch, _dptr
     s = copy.copy(settings)
-    s.fixed_iters = iters
+    s.fixed_iters = 0
     s.sigma = 0
+    s.eps = 0.0
+    s.eps_kkt = 0.0
     stream = torch.cuda.Stream()
-    qb = QPBatch(qps, s, stream=stream)
-    try:
-        with torch.cuda.stream(stream):
+    qb = QPBatch(qps, s, stream=stream, pools=pools)
+
+    def run(k: int) -> float:
+        from . import native
+        info = (native.qp_info * qb.B)()
+
+        def once():
             qb.reset()
-            qb.solve(fetch=False)                 # warm-up (module load, caches)
+            qb.lib.qp_solve(qb.h, _dptr(qb.x0), int(k), 0.0, _dptr(qb.out_x), _dptr(qb.out_u), _dptr(qb.out_l),
+                            info)
+
+        with torch.cuda.stream(stream):
+            once()
             best = float("inf")
-            for _ in range(reps):
-                qb.reset()
+            for _ in range(2):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                qb.solve(fetch=False)
+                once()
                 e1.record(stream)
                 e1.synchronize()
                 best = min(best, e0.elapsed_time(e1))
         return best
-    finally:
-        qb.close()
+
+    return qb, run
 
 
-def tune(qps, settings, expected_iters: float = 250.0, k1: int = 10, k2: int = 40, cache: Cache | None = None,
-         sample: int = 0) -> Choice:
+def tune(qps, settings, expected_iters: float = 250.0, tail_iters: float | None = None, k1: int = 10, k2: int = 40,
+         cache: Cache | None = None, sample: int = 0) -> Choice:
     """Measure every candidate launch shape on `qps` (or the first `sample` of
-    them) and return (and cache) the fastest for their bucket."""
+    them) and return (and cache) the fastest for their bucket.  tail_iters
+    (default 8 x expected_iters) is the iteration count of the slowest QP."""
+    tail = 8.0 * expected_iters if tail_iters is None else float(tail_iters)
     import torch
 
     qps = list(qps)
@@ -135,17 +164,24 @@ def tune(qps, settings, expected_iters: float = 250.0, k1: int = 10, k2: int = 4
     dev = torch.cuda.get_device_name()
     k = key(dev, settings.precision, nx, N, len(qps))
     best = None
+    pools = None
     for c, o in candidates(N):
         s = copy.copy(settings)
         s.cluster = c
         s.occupancy = o
         try:
-            t1 = _time_solve(qps, s, k1)
-            t2 = _time_solve(qps, s, k2)
+            qb, run = _timer(qps, s, pools)
+            pools = qb.pools
+            bt = (run(k1), run(k2))
+            qb.close()
+            q1, run1 = _timer(qps[:1], s)
+            ot = (run1(k1), run1(k2))
+            q1.close()
         except RuntimeError:
             continue                               # shape does not fit (shared memory)
-        ms = score(t1, t2, k1, k2, expected_iters) / len(qps)
-        if best is None or ms < best.ms_per_qp:
+        ms = makespan(bt, ot, k1, k2, expected_iters, tail) / len(qps)
+        # ties (within 2 %) go to the larger cluster: lower latency per QP
+        if best is None or ms < 0.98 * best.ms_per_qp or (ms <= 1.02 * best.ms_per_qp and c > best.cluster):
             best = Choice(c, o, ms)
     if best is None:
         raise RuntimeError("autotune: no candidate launch shape fits these problems")
@@ -154,7 +190,8 @@ def tune(qps, settings, expected_iters: float = 250.0, k1: int = 10, k2: int = 4
     return best
 
 
-def choose(qps, settings, expected_iters: float = 250.0, cache: Cache | None = None, sample: int = 0):
+def choose(qps, settings, expected_iters: float = 250.0, tail_iters: float | None = None, cache: Cache | None = None,
+           sample: int = 0):
     """Settings with the tuned cluster size and occupancy for `qps`, from the
     cache when the bucket was tuned before, else by measuring."""
     import torch
@@ -166,7 +203,7 @@ def choose(qps, settings, expected_iters: float = 250.0, cache: Cache | None = N
     k = key(torch.cuda.get_device_name(), settings.precision, nx, N, len(qps))
     c = cache.get(k)
     if c is None:
-        c = tune(qps, settings, expected_iters=expected_iters, cache=cache, sample=sample)
+        c = tune(qps, settings, expected_iters=expected_iters, tail_iters=tail_iters, cache=cache, sample=sample)
     s = copy.copy(settings)
     s.cluster = c.cluster
     s.occupancy = c.occupancy

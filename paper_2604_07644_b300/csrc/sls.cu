@@ -1,4 +1,4 @@
-// SLS controller synthesis and reachability margins (Sec. III-C, Sec. IV-B)
+// SLS controller synthesis and reachability margins (Sec. III-D, Sec. IV-B)
 // on top of the batched tree-scan factorization of qp.cu.
 //
 //   1. sls_build_kernel forms, for every disturbance index j, the LQR data of
@@ -15,7 +15,7 @@
 //      (A_k + B_k K_k^(j)) Phi_x_{k,j} from Phi_x_{j+1,j} = E_j and
 //      Phi_u_{k,j} = K_k^(j) Phi_x_{k,j} (eq. forward_prop), and the row norms
 //      of C_k Phi_x_{k,j} + D_k Phi_u_{k,j}; sls_margin_kernel sums them over j
-//      in a fixed order into h_k and h^f (the tightenings of Sec. III-C).
+//      in a fixed order into h_k and h^f (the tightenings of Sec. III-D).
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -1,6 +1,6 @@
 """Train the warm-start network for the quadruped-shaped QP family on the GPU.
 
-    python -m paper_2604_07644_b300.train_warmstart [--n 10000] [--epochs 60] [--out PATH]
+    python -m paper_2604_07644_b300.train_warmstart [--n 10000] [--epochs 120] [--out PATH]
 
 Generates n family instances (indices 0..n-1), solves them cold with the plain
 batched solver, trains the 2x256 MLP with the library's kernels and saves the

@@ -50,3 +50,11 @@ def test_settings_copy_is_independent():
     t.cluster = 3
     t.occupancy = 1
     assert s.cluster != 3 and s.occupancy == 0
+
+
+def test_makespan_takes_the_slower_of_throughput_and_tail():
+    # batch: 10 + 0.5 k for the whole batch; one QP: 2 + 0.2 k
+    bt = (10 + 0.5 * 10, 10 + 0.5 * 40)
+    ot = (2 + 0.2 * 10, 2 + 0.2 * 40)
+    assert AT.makespan(bt, ot, 10, 40, 100, 200) == pytest.approx(10 + 50)        # throughput-bound
+    assert AT.makespan(bt, ot, 10, 40, 100, 1000) == pytest.approx(2 + 200)       # tail-bound

@@ -1,4 +1,4 @@
-"""Pins of the oracle's SLS solve and margins (Sec. III-C, IV-B)."""
+"""Pins of the oracle's SLS solve and margins (Sec. III-D, IV-B)."""
 import numpy as np
 import pytest
 
@@ -83,7 +83,7 @@ def _closed_loop_deviation(sp, Phiu, w):
 def test_margins_bound_monte_carlo_and_are_attained():
     """h_k bounds the constraint deviation for every unit-ball disturbance
     sequence and is attained by the adversarial one w_j = v_j / ||v_j||
-    (Sec. II-A: w_k in the unit ball)."""
+    (Sec. III-A: w_k in the unit ball)."""
     sp = W.sls_small(3)
     Phix, Phiu, h, hf, _ = sls.solve(sp)
     g = np.random.default_rng(0)
