@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--fallback", type=int, default=2000)
     p.add_argument("--no-autotune", action="store_true", help="keep --cluster instead of tuning the launch shape")
     p.add_argument("--eager", action="store_true", help="time the step as separate calls instead of the graph")
+    p.add_argument("--index-order", action="store_true",
+                   help="launch QPs in index order instead of longest-expected-first")
     p.add_argument("--case", default="", choices=["", "iter", "refactor", "mlp", "sls"],
                    help="small fixed case for profiler captures (prints no bench line)")
     p.add_argument("--model", default=os.path.join(ROOT, "paper_2604_07644_b300", "warmstart_quadruped61.npz"))
@@ -278,7 +280,8 @@ def main():
     nx, nu, N, nc, nf = qps[0].dims()
     settings = native.default_settings(precision=prec, cluster=args.cluster, max_refine=3,
                                        fallback_iters=args.fallback, max_iter=6000,
-                                       eps_floor=1e-5 if prec == native.GPUSLS_FP32 else 1e-7)
+                                       eps_floor=1e-5 if prec == native.GPUSLS_FP32 else 1e-7,
+                                       schedule=0 if args.index_order else 1)
     tuned = None
     if not args.no_autotune:
         from paper_2604_07644_b300 import autotune
@@ -432,6 +435,8 @@ def main():
                            "cluster": int(settings.cluster), "occupancy": int(settings.occupancy),
                            "launch_shape": ("autotuned" if tuned is not None else "fixed"),
                            "step": "eager calls" if args.eager else "one CUDA graph per step",
+                           "launch_order": ("index" if args.index_order else
+                                            "longest expected first (each QP's previous solve)"),
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (FP64 pools 2.2 GB per 256 QPs)",
                            "model": os.path.basename(args.model)},
@@ -441,7 +446,7 @@ def main():
                 "refactors_mean": float(np.mean(refs)),
                 "refactors_mean_cold": float(np.mean([i.refactors for i in inf_c])),
                 "kkt_max": float(np.max(kkts)), "all_converged": all(s_ == 0 for s_ in stats),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 11 * args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (11 if args.index_order else 12) * args.steps,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     hb.close()

@@ -71,9 +71,16 @@ typedef struct qp_settings {
                              (z = y = 0, setup rho) within the same solve        */
   int32_t occupancy; /* 0: as many CTAs per SM as fit; 1: one CTA per SM (the
                          shared-memory request is raised to force it)        */
-  double eps_floor;   /* the KKT gate divides eps by 10 on failure, not below this;
+  double eps_floor;   /* the KKT gate divides eps by 10 on failure, not below this
+                         (0, the default: 1e-7 for GPUSLS_FP64, 1e-5 for GPUSLS_FP32);
                          at the floor a failing KKT check triggers a refinement:
                          r <- r + (FP64 u-stationarity residual)                   */
+  int32_t schedule;   /* launch order of the QPs of a batch: 0 (default) in index
+                         order; 1 longest expected first, the expectation being
+                         each QP's own previous solve on this handle (iterations +
+                         180 per factorization); the first solve runs in index
+                         order.  Only the order changes, never the result.     */
+  int32_t pad2;
 } qp_settings;
 
 /* Per-QP result summary (host memory). */
@@ -93,7 +100,8 @@ typedef struct qp_handle qp_handle;
 
 /* Fills s with the defaults: rho0 0.1, eps 1e-4, eps_kkt 1e-4, rho range
  * [1e-6, 1e6], sigma 25, check_every 5, max_iter 4000, FP64, cluster 0,
- * eps_floor 1e-7 (FP32 solves reach a KKT floor near 1e-4 on 61D problems: use 1e-5). */
+ * eps_floor 0 = automatic (1e-7 in FP64; 1e-5 in FP32, whose operators put a KKT
+ * floor near 1e-4 on 61D problems that the refinement at the floor removes). */
 void qp_default_settings(qp_settings* s);
 
 /* Message of the last failing call on this thread ("" if none). */

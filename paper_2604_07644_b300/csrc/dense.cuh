@@ -16,6 +16,32 @@ constexpr int GJ_LD = TILE + 1;
 __host__ __device__ inline int rup4(int x) { return (x + 3) & ~3; }
 __host__ __device__ inline int rup16(int x) { return (x + 15) & ~15; }
 
+// ---------------------------------------------------------------------------
+// cp.async staging (16-byte chunks, L2 -> shared), used to prefetch the
+// per-stage matrices of the dependent scan chains.
+// ---------------------------------------------------------------------------
+__device__ inline void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Issue the copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global to shared by the whole CTA.
+__device__ inline void cta_stage(void* dst, const void* src, int bytes) {
+  const int n16 = bytes >> 4;
+  const char* s = (const char*)src;
+  char* d = (char*)dst;
+  for (int i = threadIdx.x; i < n16; i += NT) cp_async16(d + 16 * i, s + 16 * i);
+}
+
+// 16-byte vector of T (VW elements)
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
+
 template <typename T> __device__ inline T tiny_pivot();
 template <> __device__ inline double tiny_pivot<double>() { return 1e-280; }
 template <> __device__ inline float tiny_pivot<float>() { return 1e-30f; }
@@ -24,10 +50,42 @@ template <> __device__ inline float tiny_pivot<float>() { return 1e-30f; }
 // op(B) k-slabs stored k-major).
 template <typename T> constexpr int gemm_smem_elems() { return 2 * KT * TILE; }
 
+// One element global -> shared without a register round trip (4 or 8
+// bytes), so a thread's staging loads are all in flight at once.
+template <typename T>
+__device__ inline void cp_async_elem(T* dst_smem, const T* src_global) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src_global) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src_global) : "memory");
+}
+
+// dst[e] = f(e) for e < total by the whole CTA, eight elements per thread per
+// round with all eight (independent) loads issued before the stores, so that
+// global-memory latency is paid once per round rather than once per element.
+template <typename T, typename F>
+__device__ inline void cta_fill(T* dst, int total, F f) {
+  for (int base = threadIdx.x; base < total; base += 8 * NT) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * NT;
+      v[u] = e < total ? f(e) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * NT;
+      if (e < total) dst[e] = v[u];
+    }
+  }
+}
+
 // C = alpha * op(A) * op(B) + beta * C0 (+ I if addI), with op(A) m x k and
 // op(B) k x n.  tA: A is stored k x m (op(A) = A^T); tB likewise.  C may alias
 // C0 but not A or B.  C0 may be null.  Operands may live in global or shared
-// memory.  Any m, n (tiled by TILE), any k.
+// memory.  Any m, n (tiled by TILE), any k.  5 x 5 register tiles per thread
+// on a 16 x 16 thread grid; operands staged k-major in shared memory.
 template <typename T>
 __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
                          const T* A, int lda, bool tA,
@@ -38,6 +96,7 @@ __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
   T* Bs = sm + KT * TILE;   // Bs[kk * TILE + j] = op(B)[kk][j]
   const int t = threadIdx.x;
   const int ty = t >> 4, tx = t & 15;
+  const bool gA = __isGlobal(A) != 0, gB = __isGlobal(B) != 0;
   for (int i0 = 0; i0 < m; i0 += TILE) {
     for (int j0 = 0; j0 < n; j0 += TILE) {
       const int mt = min(TILE, m - i0), nt = min(TILE, n - j0);
@@ -49,21 +108,42 @@ __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
       for (int k0 = 0; k0 < k; k0 += KT) {
         const int kt = min(KT, k - k0);
         __syncthreads();
-        // one burst of independent loads per operand, 16 x 16 thread grid,
-        // coalesced along the contiguous index of each operand
+        // 16 x 16 thread grid, coalesced along the contiguous index of each
+        // operand; global operands go by cp.async (every load of a thread in
+        // flight at once), shared ones by plain copies
         if (!tA) {
           for (int i = ty; i < mt; i += 16)
-            for (int kk = tx; kk < kt; kk += 16) As[kk * TILE + i] = A[(size_t)(i0 + i) * lda + k0 + kk];
+            for (int kk = tx; kk < kt; kk += 16) {
+              const T* src = A + (size_t)(i0 + i) * lda + k0 + kk;
+              if (gA) cp_async_elem(As + kk * TILE + i, src);
+              else As[kk * TILE + i] = *src;
+            }
         } else {
           for (int kk = ty; kk < kt; kk += 16)
-            for (int i = tx; i < mt; i += 16) As[kk * TILE + i] = A[(size_t)(k0 + kk) * lda + i0 + i];
+            for (int i = tx; i < mt; i += 16) {
+              const T* src = A + (size_t)(k0 + kk) * lda + i0 + i;
+              if (gA) cp_async_elem(As + kk * TILE + i, src);
+              else As[kk * TILE + i] = *src;
+            }
         }
         if (!tB) {
           for (int kk = ty; kk < kt; kk += 16)
-            for (int j = tx; j < nt; j += 16) Bs[kk * TILE + j] = B[(size_t)(k0 + kk) * ldb + j0 + j];
+            for (int j = tx; j < nt; j += 16) {
+              const T* src = B + (size_t)(k0 + kk) * ldb + j0 + j;
+              if (gB) cp_async_elem(Bs + kk * TILE + j, src);
+              else Bs[kk * TILE + j] = *src;
+            }
         } else {
           for (int j = ty; j < nt; j += 16)
-            for (int kk = tx; kk < kt; kk += 16) Bs[kk * TILE + j] = B[(size_t)(j0 + j) * ldb + k0 + kk];
+            for (int kk = tx; kk < kt; kk += 16) {
+              const T* src = B + (size_t)(j0 + j) * ldb + k0 + kk;
+              if (gB) cp_async_elem(Bs + kk * TILE + j, src);
+              else Bs[kk * TILE + j] = *src;
+            }
+        }
+        if (gA || gB) {
+          cp_async_commit();
+          cp_async_wait<0>();
         }
         __syncthreads();
         for (int kk = 0; kk < kt; ++kk) {
@@ -99,10 +179,27 @@ __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
 // Y = X (copy an m x n block), optional transpose (Y = X^T, Y is n x m).
 template <typename T>
 __device__ void cta_copy(int m, int n, const T* X, int ldxs, bool trans, T* Y, int ldy) {
-  for (int e = threadIdx.x; e < m * n; e += NT) {
-    const int i = e / n, j = e - i * n;
-    if (!trans) Y[(size_t)i * ldy + j] = X[(size_t)i * ldxs + j];
-    else Y[(size_t)j * ldy + i] = X[(size_t)i * ldxs + j];
+  // eight independent loads per thread before their stores
+  const int total = m * n;
+  for (int base = threadIdx.x; base < total; base += 8 * NT) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * NT;
+      if (e < total) {
+        const int i = trans ? e % m : e / n, j = trans ? e / m : e % n;
+        v[u] = X[(size_t)i * ldxs + j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * NT;
+      if (e < total) {
+        const int i = trans ? e % m : e / n, j = trans ? e / m : e % n;
+        if (!trans) Y[(size_t)i * ldy + j] = v[u];
+        else Y[(size_t)j * ldy + i] = v[u];
+      }
+    }
   }
   __syncthreads();
 }
@@ -128,148 +225,206 @@ __device__ void cta_zero(int m, int n, T* Y, int ldy) {
 
 // Gauss-Jordan inversion of the n x n matrix held in shared memory S (leading
 // dimension lds), written to Wout (leading dimension ldw; shared or global).
-// pivot = true: partial pivoting over the not-yet-used rows (largest |value|,
-// ties to the lower row; the pivot row is recorded instead of swapped and the
-// result gathered through the permutation at the end); failure if a pivot is
-// not above tiny_pivot.  pivot = false: pivots on the diagonal, failure if one
+// pivot = true: partial pivoting over the not-yet-used rows (largest |value|
+// up to a relative 2^-16 in FP32, 2^-13 in FP64, ties to the lower row; the
+// pivot row is recorded instead of swapped and the result gathered through the
+// permutation at the end); failure if a pivot is not above tiny_pivot.  pivot = false: pivots on the diagonal, failure if one
 // is not positive (the test that the matrix is symmetric positive definite).
-// Returns 0 on success, 1 on failure; S is left unchanged.
+// Returns 0 on success, 1 on failure.  S is overwritten.
 //
-// The matrix lives in registers: thread (ty, tx) of the 16 x 16 thread grid
-// owns rows ty + 16 a and columns tx + 16 b (a, b < 5).  Elimination step k
-// with pivot row p is the rank-one update M' = M0 - c r^T, where M0 is M with
-// column k replaced by the unit vector e_p, c = column k of M with c_p
-// replaced by (pivot - 1), and r = row p of M / pivot with r_k = 1 / pivot:
-// one FMA per element, no branches on the element's position.
-// Per step: [every warp finds the pivot row from the published column k;
-// owners of row p publish it] barrier [update in registers; owners of column
-// k+1 publish it into the other column buffer] barrier.
-// buf: shared scratch of 3*TILE elements; perm: shared int[2*TILE];
+// One elimination step with pivot (p, k) replaces column k by e_p and then
+// left-multiplies by L = I + g e_p^T, g = -(c - e_p) / c_p, c = column k.
+// The steps are blocked by INV_PANEL columns:
+//   * warp 0 runs the steps of a panel on the panel's columns only, held in
+//     registers (lane l owns rows l, l+32, l+64); after the panel, column k_j
+//     holds L_b ... L_1 e_{p_j};
+//   * every other column x then needs x <- L_b ... L_1 x.  Since e_{p_j} is
+//     untouched by the steps before j, L_b ... L_1 x = x + sum_j (PC_j -
+//     e_{p_j}) x_{p_j} with PC_j the final panel column j, i.e.
+//     x_i <- [i not a pivot row of the panel] x_i + sum_j PC[i][j] x_{p_j},
+//     a rank-b update done by the whole CTA from a copy of the pivot rows.
+// scratch: shared, >= INV_SCRATCH elements; perm: shared int[2*TILE];
 // flag: shared int (flag[0] = failure).
+constexpr int INV_PANEL = 16;
+constexpr int INV_SCRATCH = INV_PANEL * TILE + INV_PANEL;
+
+__device__ inline unsigned abs_hi32(float v) { return __float_as_uint(fabsf(v)); }
+__device__ inline unsigned abs_hi32(double v) { return (unsigned)((unsigned long long)__double_as_longlong(fabs(v)) >> 32); }
+
 template <typename T>
-__device__ __noinline__ int cta_inverse(T* S, int lds, int n, bool pivot, T* Wout, int ldw, T* buf, int* perm,
+__device__ __noinline__ int cta_inverse(T* S, int lds, int n, bool pivot, T* Wout, int ldw, T* scratch, int* perm,
                                         int* flag) {
-  const int t = threadIdx.x, ty = t >> 4, tx = t & 15, lane = t & 31;
-  T* rowp = buf;                           // pivot row of the current step
-  T* colbuf[2] = {buf + TILE, buf + 2 * TILE};   // column k, double-buffered
-  T m[5][5];
-#pragma unroll
-  for (int a = 0; a < 5; ++a)
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      const int i = ty + 16 * a, j = tx + 16 * b;
-      m[a][b] = (i < n && j < n) ? S[i * lds + j] : T(0);
-    }
-  // column 0 from S itself
-  for (int i = t; i < n; i += NT) colbuf[0][i] = S[i * lds];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int* panel_of = perm + TILE;   // panel index in which row i became a pivot row (-1: not yet)
+  T* XP = scratch;               // pivot rows of the current panel, [INV_PANEL][TILE]
+  T* rowbuf = scratch + INV_PANEL * TILE;   // warp 0: pivot row of the panel, [INV_PANEL]
+  for (int i = t; i < n; i += NT) panel_of[i] = -1;
   if (t == 0) flag[0] = 0;
-  unsigned used = 0;                       // bit q: row lane + 32 q already a pivot row
-  int bad = 0;
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    const T* colk = colbuf[k & 1];
-    int p = k;
-    if (pivot) {
-      // warp-redundant argmax of |column k| over the unused rows
-      T best = T(-1);
-      int bi = -1;
+  unsigned used = 0;             // warp 0: bit q = row lane + 32 q is a pivot row
+  int bad = 0;
+  const int npan = (n + INV_PANEL - 1) / INV_PANEL;
+  for (int pn = 0; pn < npan; ++pn) {
+    const int k0 = pn * INV_PANEL;
+    const int bw = min(INV_PANEL, n - k0);
+    if (w == 0) {
+      // Panel columns in registers, rotated so that the current step's
+      // column is always slot 0: after a step every slot moves down by one
+      // and the finished column goes to the last slot.  The step is then
+      // the same code for every j (a rolled loop: the panel code stays small
+      // enough for the instruction cache).  After bw steps slot m holds panel
+      // column (m + bw) mod INV_PANEL.
+      T pv[3][INV_PANEL];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int i = lane + 32 * q;
-        if (i < n && !((used >> q) & 1u)) {
-          const T av = fabs(colk[i]);
-          if (bi < 0 || av > best) { best = av; bi = i; }
+#pragma unroll
+        for (int l = 0; l < INV_PANEL; ++l) pv[q][l] = (i < n && l < bw) ? S[i * lds + k0 + l] : T(0);
+      }
+#pragma unroll 1
+      for (int j = 0; j < bw; ++j) {
+        const int k = k0 + j;
+        int p = k;
+        if (pivot) {
+          // argmax |column| over unused rows in one warp max: the key is the
+          // top 32 bits of |value| (non-negative floats order like unsigned
+          // integers) with the low 7 bits replaced by 127 - row, so the
+          // winner is a largest |value| up to a relative 2^-16 (FP32) or
+          // 2^-13 (FP64) -- as good a partial pivot -- ties to the lower row
+          unsigned key = 0u;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const int i = lane + 32 * q;
+            if (i < n && !((used >> q) & 1u)) {
+              const unsigned kq = (abs_hi32(pv[q][0]) & ~127u) | (unsigned)(127 - i);
+              key = kq > key ? kq : key;
+            }
+          }
+          const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+          p = 127 - (int)(kmax & 127u);
+          p = (p >= 0 && p < n) ? p : n - 1;   // always in range: an unused row exists while k < n
+        }
+        const int pl = p & 31, pq = p >> 5;
+        // pivot row of the panel, broadcast through shared memory by its owner
+        using V16 = typename Vec16<T>::type;
+        constexpr int VW = Vec16<T>::W;
+        if (lane == pl) {
+#pragma unroll
+          for (int l0 = 0; l0 < INV_PANEL; l0 += VW) {
+            V16 v;
+            T* vp = reinterpret_cast<T*>(&v);
+#pragma unroll
+            for (int e = 0; e < VW; ++e)
+              vp[e] = pq == 0 ? pv[0][l0 + e] : (pq == 1 ? pv[1][l0 + e] : pv[2][l0 + e]);
+            reinterpret_cast<V16*>(rowbuf)[l0 / VW] = v;
+          }
+        }
+        __syncwarp();
+        T rowp[INV_PANEL];
+#pragma unroll
+        for (int l0 = 0; l0 < INV_PANEL; l0 += VW) {
+          const V16 v = reinterpret_cast<const V16*>(rowbuf)[l0 / VW];
+          const T* vp = reinterpret_cast<const T*>(&v);
+#pragma unroll
+          for (int e = 0; e < VW; ++e) rowp[l0 + e] = vp[e];
+        }
+        __syncwarp();
+        T piv = rowp[0];
+        const bool badk = pivot ? !(fabs(piv) > tiny_pivot<T>()) : !(piv > T(0));
+        if (badk) {
+          bad = 1;
+          piv = T(1);
+        }
+        const T ip = T(1) / piv;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const bool isp = (lane + 32 * q) == p;
+          const T g = -(pv[q][0] - (isp ? T(1) : T(0))) * ip;
+          // slots 1.. get the step's update and move down; slot 0 (this
+          // step's column, replaced by e_p + g) goes to the last slot
+#pragma unroll
+          for (int l = 1; l < INV_PANEL; ++l) pv[q][l - 1] = fma(g, rowp[l], pv[q][l]);
+          pv[q][INV_PANEL - 1] = (isp ? T(1) : T(0)) + g;
+        }
+        if (lane == pl) used |= 1u << pq;
+        if (lane == 0) {
+          perm[k] = p;
+          panel_of[p] = pn;
         }
       }
+      // undo the rotation: slot m holds panel column (m + bw) mod INV_PANEL
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi >= 0 && (bi < 0 || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
-      }
-      p = bi;
-      if ((p & 31) == lane) used |= 1u << (p >> 5);
-    }
-    if (t == 0) perm[k] = p;
-    // owners publish row p (values divided later, by every reader)
-    if ((p & 15) == ty) {
-      const int pa = p >> 4;
+      for (int q = 0; q < 3; ++q) {
+        const int i = lane + 32 * q;
 #pragma unroll
-      for (int b = 0; b < 5; ++b) {
-        T v = m[0][b];
-#pragma unroll
-        for (int a = 1; a < 5; ++a) v = (a == pa) ? m[a][b] : v;   // constant indices only
-        const int j = tx + 16 * b;
-        if (j < n) rowp[j] = v;
+        for (int m = 0; m < INV_PANEL; ++m) {
+          const int l = (m + bw) & (INV_PANEL - 1);
+          if (i < n && l < bw) S[i * lds + k0 + l] = pv[q][m];
+        }
       }
     }
     __syncthreads();
-    T piv = colk[p];
-    const bool badk = pivot ? !(fabs(piv) > tiny_pivot<T>()) : !(piv > T(0));
-    if (badk) {
-      bad = 1;
-      piv = T(1);
+    // pivot rows of this panel, before the rank-b update
+    for (int e = t; e < bw * n; e += NT) {
+      const int j = e / n, col = e - j * n;
+      XP[j * TILE + col] = S[perm[k0 + j] * lds + col];
     }
-    const T ip = T(1) / piv;
-    T r[5], c[5];
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      const int j = tx + 16 * b;
-      r[b] = (j == k) ? ip : ((j < n) ? rowp[j] * ip : T(0));
-    }
-#pragma unroll
-    for (int a = 0; a < 5; ++a) {
-      const int i = ty + 16 * a;
-      c[a] = (i == p) ? piv - T(1) : ((i < n) ? colk[i] : T(0));
-    }
-#pragma unroll
-    for (int a = 0; a < 5; ++a) {
-      if (16 * a < n) {                    // uniform over the CTA
-        const T e = (ty + 16 * a == p) ? T(1) : T(0);
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          if (16 * b < n) {
-            const T m0 = (tx + 16 * b == k) ? e : m[a][b];
-            m[a][b] = fma(-c[a], r[b], m0);
-          }
-        }
-      }
-    }
-    // owners of column k+1 publish it for the next step
-    const int k1 = k + 1;
-    if (k1 < n && (k1 & 15) == tx) {
-      T* dst = colbuf[k1 & 1];
-      const int kb = k1 >> 4;
+    __syncthreads();
+    // x_i <- [i not a pivot row of this panel] x_i + sum_j PC[i][j] XP[j] for
+    // every column outside the panel: 16 x 16 thread grid, 5 x 5 elements each
+    // (rows ty + 16 a, columns tx + 16 b).  No other thread reads what a
+    // thread writes: it owns its (row, column) elements, and the panel
+    // columns it reads are not written in this phase.
+    {
+      const int ty = t >> 4, tx = t & 15;
+      T acc[5][5];
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
-        T v = m[a][0];
-#pragma unroll
-        for (int b = 1; b < 5; ++b) v = (b == kb) ? m[a][b] : v;   // constant indices only
         const int i = ty + 16 * a;
-        if (i < n) dst[i] = v;
+        const bool keep = i < n && panel_of[i] != pn;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          const int col = tx + 16 * b;
+          acc[a][b] = (keep && col < n) ? S[i * lds + col] : T(0);
+        }
+      }
+      for (int j = 0; j < bw; ++j) {
+        T xr[5], pc[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          const int col = tx + 16 * b;
+          xr[b] = col < n ? XP[j * TILE + col] : T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+          const int i = ty + 16 * a;
+          pc[a] = i < n ? S[i * lds + k0 + j] : T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) acc[a][b] = fma(pc[a], xr[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        const int i = ty + 16 * a;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          const int col = tx + 16 * b;
+          if (i < n && col < n && (col < k0 || col >= k0 + bw)) S[i * lds + col] = acc[a][b];
+        }
       }
     }
     __syncthreads();
   }
   if (t == 0 && bad) flag[0] = 1;
-  // gather: W[a][b] = M'[perm[a]][iperm[b]] (iperm[perm[c]] = c): the owner of
-  // M'[i][j] writes W[iperm[i]][perm[j]]
+  // gather: W[a][b] = M[perm[a]][iperm[b]] (iperm[perm[c]] = c)
   int* iperm = perm + TILE;
-  if (pivot)
-    for (int q = t; q < n; q += NT) iperm[perm[q]] = q;
+  for (int q = t; q < n; q += NT) iperm[perm[q]] = q;
   __syncthreads();
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    const int i = ty + 16 * a;
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      const int j = tx + 16 * b;
-      if (i < n && j < n) {
-        const int wa = pivot ? iperm[i] : i;
-        const int wb = pivot ? perm[j] : j;
-        Wout[wa * ldw + wb] = m[a][b];
-      }
-    }
+  for (int e = t; e < n * n; e += NT) {
+    const int a = e / n, b = e - a * n;
+    Wout[a * ldw + b] = S[perm[a] * lds + iperm[b]];
   }
   __syncthreads();
   const int f = flag[0];
@@ -318,27 +473,6 @@ __device__ inline T warp_dot(const T* a, const T* x, int n) {
   T s = T(0);
   for (int j = l; j < n; j += 32) s += a[j] * x[j];
   return warp_sum(s);
-}
-
-// ---------------------------------------------------------------------------
-// cp.async staging (16-byte chunks, L2 -> shared), used to prefetch the
-// per-stage matrices of the dependent scan chains.
-// ---------------------------------------------------------------------------
-__device__ inline void cp_async16(void* smem_dst, const void* gsrc) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Issue the copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
-// from global to shared by the whole CTA.
-__device__ inline void cta_stage(void* dst, const void* src, int bytes) {
-  const int n16 = bytes >> 4;
-  const char* s = (const char*)src;
-  char* d = (char*)dst;
-  for (int i = threadIdx.x; i < n16; i += NT) cp_async16(d + 16 * i, s + 16 * i);
 }
 
 // y = M^T x + c  (M: rows x cols in shared memory, leading dim ld; x: rows;
@@ -427,9 +561,6 @@ __device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity, int l
 // (t < na + nb) after one barrier.  The role of each thread is computed once
 // (sweep_plan) and reused for every block of a stream.
 // ---------------------------------------------------------------------------
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
-template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
 
 constexpr int SWEEP_MAXG = 16;
 // shared scratch of a sweep: NT vectors of 16 bytes

@@ -42,6 +42,7 @@ struct qp_handle {
   size_t njobs_cap = 0;
   std::vector<void*> tx0;       // per-QP x0 (solve precision)
   double* rho0_dev = nullptr;   // [batch] setup penalties (qp_reset)
+  int* order_dev = nullptr;     // [batch] launch order (settings.schedule == 1)
 };
 
 namespace gsls {

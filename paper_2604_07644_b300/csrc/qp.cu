@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   __shared__ QPDesc dsh;
   const int cs = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  const int qi = blockIdx.x / cs;
+  const int qi = args.order ? args.order[blockIdx.x / cs] : (int)(blockIdx.x / cs);
   if (threadIdx.x == 0) dsh = descs[qi];
   __syncthreads();
   QPDesc& d = dsh;
@@ -264,6 +264,35 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
 }
 
 // ---------------------------------------------------------------------------
+// launch order for the next solve: longest expected first
+// ---------------------------------------------------------------------------
+// Expected work of QP b = its last solve's iterations + 180 per factorization
+// (a 61D factorization costs about as much as 180 iterations); order[r] = b
+// for the rank r of b in decreasing work (ties by index), by counting.
+__global__ void order_kernel(const int* __restrict__ info_i, int batch, int* __restrict__ order) {
+  __shared__ int work[1024];
+  for (int b0 = 0; b0 < batch; b0 += blockDim.x) {            // same trip count in every thread
+    const int b = b0 + threadIdx.x;
+    const bool valid = b < batch;
+    const int wb = valid ? info_i[8 * b + 1] + 180 * info_i[8 * b + 2] : 0;
+    int rank = 0;
+    for (int j0 = 0; j0 < batch; j0 += 1024) {
+      const int nj = min(1024, batch - j0);
+      __syncthreads();
+      for (int j = threadIdx.x; j < nj; j += blockDim.x)
+        work[j] = info_i[8 * (j0 + j) + 1] + 180 * info_i[8 * (j0 + j) + 2];
+      __syncthreads();
+      if (valid)
+        for (int j = 0; j < nj; ++j) {
+          const int wj = work[j];
+          rank += (wj > wb || (wj == wb && j0 + j < b)) ? 1 : 0;
+        }
+    }
+    if (valid) order[rank] = b;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // packing FP64 caller arrays into padded solve-precision layouts
 // ---------------------------------------------------------------------------
 
@@ -317,7 +346,10 @@ extern "C" void qp_default_settings(qp_settings* s) {
   s->fixed_iters = 0;
   s->max_refine = 3;
   s->fallback_iters = 0;
-  s->eps_floor = 1e-7;
+  s->eps_floor = 0.0;   // auto: 1e-7 for FP64 solves, 1e-5 for FP32 solves
+  s->occupancy = 0;
+  s->schedule = 0;
+  s->pad2 = 0;
 }
 
 extern "C" const char* gpusls_last_error(void) { return g_err.c_str(); }
@@ -420,6 +452,8 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: unknown precision");
   if (s->cluster < 0 || s->cluster > MAXCS) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: cluster must be 0..8");
+  if (s->occupancy < 0 || s->occupancy > 1 || s->schedule < 0 || s->schedule > 1)
+    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: occupancy and schedule must be 0 or 1");
   if (s->check_every < 1 || s->max_iter < 1 || s->sigma < 0)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: check_every, max_iter >= 1 and sigma >= 0 required");
   int needC = 0, needCN = 0;
@@ -614,6 +648,14 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   }
   CU(cudaMemcpyAsync(h->rho0_dev, r0.data(), batch * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   for (int b = 0; b < batch; ++b) h->hdesc[b].rho0 = h->rho0_dev + b;
+  // launch order: index order until a solve has run (schedule 1)
+  std::vector<int> ord(batch);
+  for (int b = 0; b < batch; ++b) ord[b] = b;
+  if (cudaMalloc(&h->order_dev, batch * sizeof(int)) != cudaSuccess) {
+    qp_destroy(h);
+    return fail(GPUSLS_ERR_CUDA, "qp_batch_setup: cudaMalloc failed");
+  }
+  CU(cudaMemcpy(h->order_dev, ord.data(), batch * sizeof(int), cudaMemcpyHostToDevice));
   for (int b = 0; b < batch; ++b) {
     int fl[4] = {0, 0, 0, 0};
     CU(cudaMemcpyAsync(h->hdesc[b].rho, &r0[b], sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -705,10 +747,22 @@ static SolveArgs solve_args(const qp_handle* h, int32_t iters, double tol) {
   a.eps_kkt = h->set.eps_kkt > 0 ? (tol > 0 ? tol : h->set.eps_kkt) : -1.0;
   a.rho_min = h->set.rho_min;
   a.rho_max = h->set.rho_max;
-  a.eps_floor = h->set.eps_floor;
+  a.eps_floor = h->set.eps_floor > 0.0 ? h->set.eps_floor : (h->esz == 4 ? 1e-5 : 1e-7);
   a.max_refine = h->set.max_refine;
   a.fallback_iters = h->set.fallback_iters;
+  a.order = h->set.schedule == 1 ? h->order_dev : nullptr;
   return a;
+}
+
+// The solve launch, followed (schedule 1) by the launch order of the next solve.
+static int launch_solve(qp_handle* h, const SolveArgs& a) {
+  int st = launch(h, a);
+  if (st) return st;
+  if (h->set.schedule == 1) {
+    order_kernel<<<1, 256, 0, h->stream>>>(h->info_i, h->batch, h->order_dev);
+    CU(cudaGetLastError());
+  }
+  return GPUSLS_OK;
 }
 
 extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double tol, double* dx, double* du,
@@ -718,7 +772,7 @@ extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double to
   if (st) return st;
   st = set_outputs(h, dx, du, lam, 0, 0, false);
   if (st) return st;
-  st = launch(h, solve_args(h, iters, tol));
+  st = launch_solve(h, solve_args(h, iters, tol));
   if (st) return st;
   return collect(h, info);
 }
@@ -800,7 +854,7 @@ extern "C" int qp_graph_create(qp_graph** out, qp_handle* h, mlp_handle* m, cons
     dim3 grid(32, g->njobs);
     if (h->esz == 8) pack_kernel<double><<<grid, 256, 0, g->cap>>>(g->djobs);
     else pack_kernel<float><<<grid, 256, 0, g->cap>>>(g->djobs);
-    est = launch(h, solve_args(h, 0, 0.0));
+    est = launch_solve(h, solve_args(h, 0, 0.0));
   }
   if (!est && info_i &&
       cudaMemcpyAsync(info_i, h->info_i, (size_t)h->batch * 8 * sizeof(int), cudaMemcpyDeviceToDevice, g->cap))
@@ -1019,5 +1073,6 @@ extern "C" void qp_destroy(qp_handle* h) {
   if (h->info_d) cudaFree(h->info_d);
   if (h->djobs) cudaFree(h->djobs);
   if (h->rho0_dev) cudaFree(h->rho0_dev);
+  if (h->order_dev) cudaFree(h->order_dev);
   delete h;
 }

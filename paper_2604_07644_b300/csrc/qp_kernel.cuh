@@ -74,6 +74,7 @@ struct SolveArgs {
   double eps, eps_kkt, rho_min, rho_max, eps_floor;
   int max_refine;
   int fallback_iters;   // > 0: a warm-started QP not converged after this many iterations restarts cold
+  const int* order;     // launch order: cluster b solves QP order[b] (null: QP b)
 };
 
 // Per-stage operator bundles of the cached iteration (elements).  Every
@@ -247,7 +248,7 @@ __device__ __noinline__ int combine_full(Ctx<T>& c, const T* lP, const T* lA, co
   T* U = c.scr + 3 * c.msz;
   T* Wm = c.scr + 4 * c.msz;
   cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm);
-  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, Wm, ld, c.gjbuf, c.perm, c.flag);
+  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, Wm, ld, c.gemm, c.perm, c.flag);
   cta_gemm<T>(n, n, n, T(1), Wm, ld, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), rA, ld, false, Wm, ld, false, T(0), nullptr, 0, false, Psi, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm);
@@ -266,7 +267,7 @@ __device__ __noinline__ int combine_complete(Ctx<T>& c, const T* lP, const T* lA
   T* V = c.scr + 2 * c.msz;
   T* Wm = c.scr + 4 * c.msz;
   cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm);
-  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, Wm, ld, c.gjbuf, c.perm, c.flag);
+  const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, Wm, ld, c.gemm, c.perm, c.flag);
   cta_gemm<T>(n, n, n, T(1), Wm, ld, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm);
   cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm);
@@ -324,7 +325,7 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       cta_gemm<T>(nx, nx, nc, rho, Ci, ldx, true, Ci, ldx, false, T(1), Q + (size_t)i * msz, ldx, false, Pl, ldx, c.gemm);
       cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm);
       cta_gemm<T>(nu, nx, nc, rho, Di, ldu, true, Ci, ldx, false, T(1), S + (size_t)i * nu * ldx, ldx, false, Shi, ldx, c.gemm);
-      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Rhii, ldu, c.gjbuf, c.perm, c.flag);
+      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Rhii, ldu, c.gemm, c.perm, c.flag);
       // s0 = R^-1 S^ ; P~ = Q^ - S^^T s0 ; A~ = A - B s0 ; s1 = B R^-1 ; C~ = s1 B^T
       cta_gemm<T>(nu, nx, nu, T(1), Rhii, ldu, false, Shi, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm);
       cta_gemm<T>(nx, nx, nu, T(-1), Shi, ldx, true, s0, ldx, false, T(1), Pl, ldx, false, Pl, ldx, c.gemm);
@@ -411,7 +412,7 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       // Gamma^-1 = R^ + s0 B  (R^ rebuilt)
       cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm);
       cta_gemm<T>(nu, nu, nx, T(1), s0, ldx, false, Bi, ldu, false, T(1), c.gj, GJ_LD, false, c.gj, GJ_LD, c.gemm);
-      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Gi, ldu, c.gjbuf, c.perm, c.flag);
+      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Gi, ldu, c.gemm, c.perm, c.flag);
       // s1 = S^ + s0 A ; K = -Gamma s1
       cta_gemm<T>(nu, nx, nx, T(1), s0, ldx, false, Ai, ldx, false, T(1), Sh + (size_t)i * nu * ldx, ldx, false, s1, ldx, c.gemm);
       cta_gemm<T>(nu, nx, nu, T(-1), Gi, ldu, false, s1, ldx, false, T(0), nullptr, 0, false, Ki, ldx, c.gemm);
@@ -446,31 +447,34 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       const T* CKi = CK + (size_t)i * nc * ldx;
       const T* Fi = F + (size_t)i * nu * ldx;
       const T* Ji = J + (size_t)i * nu * ldc;
-      for (int e2 = threadIdx.x; e2 < R * ldx; e2 += NT) {
+      // (cta_fill: eight independent loads per thread before the stores)
+      cta_fill<T>(bw, R * ldx, [&](int e2) {
         const int rr = e2 / ldx, j = e2 - rr * ldx;
-        bw[e2] = (j >= nx) ? T(0) : (rr < nx ? Abi[(size_t)rr * ldx + j] : CKi[(size_t)(rr - nx) * ldx + j]);
-      }
+        return (j >= nx) ? T(0) : (rr < nx ? Abi[(size_t)rr * ldx + j] : CKi[(size_t)(rr - nx) * ldx + j]);
+      });
       T* fjt = bw + (size_t)R * ldx;           // [F | J]^T : row r, column a
-      for (int e2 = threadIdx.x; e2 < R * ldu; e2 += NT) {
+      cta_fill<T>(fjt, R * ldu, [&](int e2) {
         const int rr = e2 / ldu, a = e2 - rr * ldu;
-        fjt[e2] = a >= nu ? T(0) : (rr < nx ? Fi[(size_t)a * ldx + rr] : Ji[(size_t)a * ldc + rr - nx]);
-      }
+        return a >= nu ? T(0) : (rr < nx ? Fi[(size_t)a * ldx + rr] : Ji[(size_t)a * ldc + rr - nx]);
+      });
       T* c0b = fjt + (size_t)R * ldu;
-      for (int j = threadIdx.x; j < ldx; j += NT) c0b[j] = j < nx ? c0[(size_t)i * ldx + j] : T(0);
-      for (int a = threadIdx.x; a < ldu; a += NT) c0b[ldx + a] = a < nu ? k0[(size_t)i * ldu + a] : T(0);
+      cta_fill<T>(c0b, ldx + ldu, [&](int j) {
+        return j < ldx ? (j < nx ? c0[(size_t)i * ldx + j] : T(0))
+                       : (j - ldx < nu ? k0[(size_t)i * ldu + j - ldx] : T(0));
+      });
       // FW^T: row cc < nx+nu (input index), column r < nx+nc (output index)
-      for (int e2 = threadIdx.x; e2 < (nx + nu) * ldv; e2 += NT) {
+      cta_fill<T>(fw, (nx + nu) * ldv, [&](int e2) {
         const int cc = e2 / ldv, r2 = e2 - cc * ldv;
         T v = T(0);
         if (r2 < nx) v = cc < nx ? Abi[(size_t)r2 * ldx + cc] : Bi[(size_t)r2 * ldu + cc - nx];
         else if (r2 < R) v = cc < nx ? CKi[(size_t)(r2 - nx) * ldx + cc] : Di[(size_t)(r2 - nx) * ldu + cc - nx];
-        fw[e2] = v;
-      }
-      for (int j = threadIdx.x; j < ldx; j += NT) fw[(size_t)(nx + nu) * ldv + j] = j < nx ? bb[(size_t)i * ldx + j] : T(0);
-      for (int e2 = threadIdx.x; e2 < nc * ldf; e2 += NT) {
+        return v;
+      });
+      cta_fill<T>(fw + (size_t)(nx + nu) * ldv, ldx, [&](int j) { return j < nx ? bb[(size_t)i * ldx + j] : T(0); });
+      cta_fill<T>(cd, nc * ldf, [&](int e2) {
         const int rr = e2 / ldf, j = e2 - rr * ldf;
-        cd[e2] = j < nx ? Ci[(size_t)rr * ldx + j] : (j < nx + nu ? Di[(size_t)rr * ldu + j - nx] : T(0));
-      }
+        return j < nx ? Ci[(size_t)rr * ldx + j] : (j < nx + nu ? Di[(size_t)rr * ldu + j - nx] : T(0));
+      });
       __syncthreads();
     }
   }

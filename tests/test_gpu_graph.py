@@ -105,3 +105,27 @@ def test_graph_rejects_null_arguments(lib):
     assert st == native.GPUSLS_ERR_INVALID
     assert lib.qp_graph_launch(None, None) == native.GPUSLS_ERR_INVALID
     qb.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_longest_first_schedule_changes_only_the_order(lib, graph):
+    """schedule = 1 launches the QPs longest-expected-first (from their own
+    previous solve): every result, iteration count and status is the same as
+    in index order, on every solve."""
+    qps = [W.random_general(10 + i, 5 + i % 4, 2, 12 + 5 * i, 3, 1) for i in range(7)]
+    s0 = native.default_settings(precision=native.GPUSLS_FP64, cluster=2)
+    s1 = native.default_settings(precision=native.GPUSLS_FP64, cluster=2, schedule=1)
+    q0, q1 = QPBatch(qps, s0), QPBatch(qps, s1)
+    g1 = q1.graph() if graph else None
+    for _ in range(3):
+        ref, info0 = _eager(q0)
+        if graph:
+            g1.launch()
+            torch.cuda.synchronize()
+            got, info1 = _snapshot(q1), g1.info()
+        else:
+            got, info1 = _eager(q1)
+        assert _same(got, ref)
+        assert [i["iters"] for i in info1] == [i["iters"] for i in info0]
+    q0.close()
+    q1.close()

@@ -32,6 +32,15 @@ def test_default_settings_without_gpu(libpath):
     assert s.rho0 == 0.1 and s.sigma == 25 and s.check_every == 5 and s.eps == 1e-4
 
 
+def test_default_settings_fill_every_field(libpath):
+    """qp_default_settings writes every field, whatever the struct held."""
+    s = native.qp_settings()
+    ctypes.memset(ctypes.byref(s), 0xA5, ctypes.sizeof(s))
+    native.load().qp_default_settings(ctypes.byref(s))
+    assert s.occupancy == 0 and s.schedule == 0 and s.pad2 == 0 and s.eps_floor == 0.0
+    assert s.cluster == 0 and s.fixed_iters == 0 and s.fallback_iters == 0
+
+
 def test_invalid_arguments_are_rejected_without_gpu(libpath):
     lib = native.load()
     h = ctypes.c_void_p()
