@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--fallback", type=int, default=2000)
     p.add_argument("--no-autotune", action="store_true", help="keep --cluster instead of tuning the launch shape")
     p.add_argument("--eager", action="store_true", help="time the step as separate calls instead of the graph")
+    p.add_argument("--no-extras", action="store_true", help="skip the serving-mix / humanoid / SLS measurements")
     p.add_argument("--index-order", action="store_true",
                    help="launch QPs in index order instead of longest-expected-first")
     p.add_argument("--case", default="", choices=["", "iter", "refactor", "mlp", "sls"],
@@ -153,14 +154,17 @@ def algorithmic_bytes_per_iter(nx, nu, N, nc, esz):
     return N * (2 * nx * nx + 3 * nu * nx + nu * nc + 2 * nc * (nx + nu)) * esz
 
 
-def cpu_oracle_ms_per_qp(qps, eps=1e-4):
-    """The FP64 oracle as it stands on this host (single thread)."""
+def cpu_oracle_ms_per_qp(qps, eps=1e-4, results=None):
+    """The FP64 oracle as it stands on this host (single thread); the solutions
+    are appended to `results` when given."""
     from oracle import admm
     t0 = time.perf_counter()
     iters = []
     for qp in qps:
         r = admm.admm(qp, admm.Settings(eps=eps, eps_kkt=eps))
         iters.append(r.iters)
+        if results is not None:
+            results.append(r)
     dt = time.perf_counter() - t0
     return dt * 1e3 / len(qps), iters
 
@@ -192,6 +196,107 @@ def run_reference(args, ws, rank):
                              "sample": f"{args.steps} QPs, one per step, single thread; iters {iters}"},
             "e2e": {"value": ms, "unit": "ms/QP", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _time_graph(g, stream, steps):
+    import torch
+    g.launch(stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def extra_workloads(args, qps, hb, stream, dev, oracle_sols):
+    """Timed on the same device after the headline: the batched serving mix
+    (256 ragged QPs, nx in {12, 61, 75}, N in 16..128, cold FP32), 64
+    humanoid-shaped QPs (75D, N=40, cold FP32), the humanoid SLS solve (75D,
+    N=40) with per-j tau and with tau = 0, and checks of the headline's
+    solutions: the largest bound violation and the largest difference from
+    the FP64 oracle on the CPU-baseline sample."""
+    import torch
+
+    from paper_2604_07644_b300 import native
+    from paper_2604_07644_b300 import workloads as W
+    from paper_2604_07644_b300.api import SLS, QPBatch
+    out = {}
+    steps = max(1, args.steps)
+    base = dict(precision=native.GPUSLS_FP32, cluster=8, max_refine=3, max_iter=6000, schedule=1)
+
+    def batch_run(name, qps_, cluster):
+        s = native.default_settings(**dict(base, cluster=cluster))
+        with torch.cuda.stream(stream):
+            qb = QPBatch(qps_, s, stream=stream, device=dev)
+            g = qb.graph()
+            ms = _time_graph(g, stream, steps)
+            info = g.info()
+        out[name] = {"ms_per_qp": ms / len(qps_), "batch": len(qps_),
+                     "iters_mean": float(np.mean([i["iters"] for i in info])),
+                     "kkt_max": float(np.max([i["kkt"] for i in info])),
+                     "all_converged": all(i["status"] == 0 for i in info)}
+        qb.close()
+
+    batch_run("serving_mix_cold", W.serving_mix(0, 256), 8)
+    batch_run("humanoid75_cold", [W.humanoid_75d(s) for s in range(64)], 4)
+
+    # SLS: model flops from the per-j scans (2 (N - j) combines of ~16.7 nx^3
+    # each) and the forward products (2 nx^2 (nx + nu) per block)
+    for mode in ("uniform", "zero"):
+        sp = W.sls_problem(0, tau_mode=mode)
+        N, nx = sp.A.shape[0], sp.A.shape[1]
+        nu, nc, nf = sp.B.shape[2], sp.C.shape[1], sp.CN.shape[0]
+        t = {k: (None if getattr(sp, k) is None else
+                 torch.from_numpy(np.ascontiguousarray(getattr(sp, k), dtype=np.float64)).to(dev))
+             for k in ("A", "B", "E", "Qbar", "Rbar", "QbarN", "C", "D", "CN", "tau")}
+        from types import SimpleNamespace
+        spd = SimpleNamespace(**t)
+        sls = SLS(nx, nu, N, nc, nf, per_j_tau=(mode == "uniform"), precision=native.GPUSLS_FP32, stream=stream)
+        with torch.cuda.stream(stream):
+            sls.solve(spd, fetch=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                sls.solve(spd, fetch=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        scans = (sum(2 * (N - j) for j in range(N)) if mode == "uniform" else 2 * N) * 16.7 * nx ** 3
+        fwd = (N * (N + 1) / 2) * 2 * nx * nx * (nx + nu)
+        out[f"sls75_tau_{mode}"] = {"ms_per_solve": ms, "model_gflop": (scans + fwd) / 1e9,
+                                   "model_gflops_per_s": (scans + fwd) / (ms * 1e-3) / 1e9}
+        sls.close()
+
+    # checks on the headline's solutions (already in hb's output buffers)
+    x = hb.out_x.cpu().numpy()
+    u = hb.out_u.cpu().numpy()
+    viol, ox, ou = 0.0, 0, 0
+    xs, us = [], []
+    for qp in qps:
+        X = x[ox:ox + (qp.N + 1) * qp.nx].reshape(qp.N + 1, qp.nx)
+        U = u[ou:ou + qp.N * qp.nu].reshape(qp.N, qp.nu)
+        ox += (qp.N + 1) * qp.nx
+        ou += qp.N * qp.nu
+        xs.append(X)
+        us.append(U)
+        v = np.concatenate([np.einsum("kcx,kx->kc", qp.C, X[:-1]).ravel() + np.einsum("kcu,ku->kc", qp.D, U).ravel(),
+                            qp.CN @ X[-1]])
+        viol = max(viol, float(np.max(np.maximum(np.maximum(v - qp.hi, qp.lo - v), 0.0))))
+    out["bound_violation_max"] = viol
+    if oracle_sols:
+        d = 0.0
+        for i, r in enumerate(oracle_sols):
+            scale = max(1.0, float(np.max(np.abs(r.x))))
+            d = max(d, float(np.max(np.abs(xs[i] - r.x))) / scale, float(np.max(np.abs(us[i] - r.u))) / scale)
+        out["max_rel_diff_vs_oracle"] = {"value": d, "sample": f"first {args.cpu_sample} QPs; both solved to a "
+                                                                 "1e-4 KKT residual, so they agree to about that"}
+    return out
 
 
 def profile_case(args):
@@ -406,6 +511,18 @@ def main():
         e2e = {"value": te / (args.steps * args.batch * ws), "unit": "ms/QP", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    # ---- further workloads of the same library (rank 0): the serving mix, the
+    # humanoid-shaped QP, the humanoid SLS solve; solution checks ----
+    cpu = None
+    oracle_sols = []
+    if rank == 0 and args.cpu_sample > 0:
+        ms_cpu, it_cpu = cpu_oracle_ms_per_qp(qps[:args.cpu_sample], results=oracle_sols)
+        cpu = {"value": ms_cpu, "unit": "ms/QP", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} QPs of this batch, FP64 oracle ADMM, single thread; iters {it_cpu}"}
+    extra = {}
+    if rank == 0 and not args.no_extras:
+        extra = extra_workloads(args, qps, hb, stream, dev, oracle_sols)
+
     pk, pk_kind = peaks()
     algo = algorithmic_bytes_per_iter(nx, nu, N, nc, esz) * float(np.sum(iters))
     achieved = algo / (ms_per_step * 1e-3) / 1e9
@@ -418,11 +535,6 @@ def main():
             "kernel": "qp_kernel (persistent cluster solve)", "peak_kind": pk_kind,
             "algorithmic_bytes_per_launch": algo}
 
-    cpu = None
-    if rank == 0 and args.cpu_sample > 0:
-        ms_cpu, it_cpu = cpu_oracle_ms_per_qp(qps[:args.cpu_sample])
-        cpu = {"value": ms_cpu, "unit": "ms/QP", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_sample} QPs of this batch, FP64 oracle ADMM, single thread; iters {it_cpu}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "ms/QP", "n_gpus": ws, "steps": args.steps,
@@ -448,6 +560,7 @@ def main():
                 "kkt_max": float(np.max(kkts)), "all_converged": all(s_ == 0 for s_ in stats),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (11 if args.index_order else 12) * args.steps,
                 "clocks": clk.summary()}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     hb.close()
     if ws > 1:

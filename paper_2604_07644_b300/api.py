@@ -244,8 +244,17 @@ class SLS:
         self.h = h
 
     def solve(self, sp, fetch=True):
+        """sp: an SLSProblem whose arrays are numpy arrays or device tensors
+        (float64, in the sls_solve layouts; device tensors are used in place)."""
         nx, nu, N, nc, nf = self.dims
-        f = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(self.device)
+
+        def f(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                return a
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(self.device)
+
         t = dict(A=f(sp.A), B=f(sp.B), E=f(sp.E), Qbar=f(sp.Qbar), Rbar=f(sp.Rbar), QbarN=f(sp.QbarN),
                  C=f(sp.C), D=f(sp.D), CN=f(sp.CN), tau=f(sp.tau))
         Phix = torch.empty(N * nx, N * nx, dtype=torch.float64, device=self.device)
