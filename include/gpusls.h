@@ -43,6 +43,10 @@ extern "C" {
 /* arithmetic of the solve kernels */
 #define GPUSLS_FP64 0   /* all arithmetic in float64                                  */
 #define GPUSLS_FP32 1   /* all arithmetic in float32 (KKT check stays float64)        */
+#define GPUSLS_TF32 2   /* as GPUSLS_FP32, but the factorization's block products run
+                           on the tensor cores in TF32 (one pass, FP32 accumulation):
+                           faster products, ~1e-3 relative product error that the
+                           FP64 KKT gate and the refinement at the eps floor absorb */
 
 /* Dimensions of one LTV-QP (eq. sqp_qp): state nx, input nu, horizon N, stage
  * constraint rows nc (rows of C_k, D_k), terminal rows nf (rows of C_N). */

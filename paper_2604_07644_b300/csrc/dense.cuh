@@ -50,6 +50,22 @@ template <> __device__ inline float tiny_pivot<float>() { return 1e-30f; }
 // op(B) k-slabs stored k-major).
 template <typename T> constexpr int gemm_smem_elems() { return 2 * KT * TILE; }
 
+// TF32 tensor-core pieces (the GPUSLS_TF32 precision mode): operands rounded
+// to TF32, mma.sync m16n8k8 with FP32 accumulation.
+__device__ inline unsigned tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ inline void mma_tf32(float* c, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+constexpr int GEMM_NB = 4;   // n8 tiles per warp strip (16 x 32 outputs) of the TF32 path
+
 // One element global -> shared without a register round trip (4 or 8
 // bytes), so a thread's staging loads are all in flight at once.
 template <typename T>
@@ -84,29 +100,43 @@ __device__ inline void cta_fill(T* dst, int total, F f) {
 // C = alpha * op(A) * op(B) + beta * C0 (+ I if addI), with op(A) m x k and
 // op(B) k x n.  tA: A is stored k x m (op(A) = A^T); tB likewise.  C may alias
 // C0 but not A or B.  C0 may be null.  Operands may live in global or shared
-// memory.  Any m, n (tiled by TILE), any k.  5 x 5 register tiles per thread
-// on a 16 x 16 thread grid; operands staged k-major in shared memory.
+// memory.  Any m, n (tiled by TILE), any k.  Operands are staged k-major in
+// shared memory.  tc = false (or FP64): 5 x 5 register tiles per thread on a
+// 16 x 16 thread grid.  tc = true (FP32 only): TF32 tensor-core MMAs, one
+// 16 x 32 strip per warp.
 template <typename T>
 __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
                          const T* A, int lda, bool tA,
                          const T* B, int ldb, bool tB,
                          T beta, const T* C0, int ldc0, bool addI,
-                         T* C, int ldc, T* sm) {
+                         T* C, int ldc, T* sm, bool tc = false) {
   T* As = sm;               // As[kk * TILE + i] = op(A)[i][kk]
   T* Bs = sm + KT * TILE;   // Bs[kk * TILE + j] = op(B)[kk][j]
   const int t = threadIdx.x;
   const int ty = t >> 4, tx = t & 15;
   const bool gA = __isGlobal(A) != 0, gB = __isGlobal(B) != 0;
+  const bool TC = tc && sizeof(T) == 4;
+  const int lane = t & 31, w = t >> 5, gid = lane >> 2, tig = lane & 3;
   for (int i0 = 0; i0 < m; i0 += TILE) {
     for (int j0 = 0; j0 < n; j0 += TILE) {
       const int mt = min(TILE, m - i0), nt = min(TILE, n - j0);
       T acc[5][5];
+      float fr[2][GEMM_NB][4];
+      const int mt16 = (mt + 15) >> 4, nt8 = (nt + 7) >> 3;
+      const int nstrip_n = (nt8 + GEMM_NB - 1) / GEMM_NB, nstrips = mt16 * nstrip_n;
 #pragma unroll
       for (int a = 0; a < 5; ++a)
 #pragma unroll
         for (int b = 0; b < 5; ++b) acc[a][b] = T(0);
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+        for (int q = 0; q < GEMM_NB; ++q)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) fr[s2][q][e] = 0.f;
       for (int k0 = 0; k0 < k; k0 += KT) {
         const int kt = min(KT, k - k0);
+        const int kt8 = (kt + 7) & ~7;
         __syncthreads();
         // 16 x 16 thread grid, coalesced along the contiguous index of each
         // operand; global operands go by cp.async (every load of a thread in
@@ -141,22 +171,82 @@ __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
               else Bs[kk * TILE + j] = *src;
             }
         }
+        if (TC) {
+          // zero the k-padding up to a multiple of 8 and the row / column
+          // padding of the 16 x 8 fragments (stale values could be Inf / NaN)
+          for (int e = t; e < (kt8 - kt) * TILE; e += NT) {
+            As[kt * TILE + e] = T(0);
+            Bs[kt * TILE + e] = T(0);
+          }
+          for (int e = t; e < kt8 * 16; e += NT) {
+            const int kk = e >> 4, r = e & 15;
+            if (mt + r < TILE && mt + r < 16 * mt16) As[kk * TILE + mt + r] = T(0);
+            if (nt + r < TILE && nt + r < 8 * nt8) Bs[kk * TILE + nt + r] = T(0);
+          }
+        }
         if (gA || gB) {
           cp_async_commit();
           cp_async_wait<0>();
         }
         __syncthreads();
-        for (int kk = 0; kk < kt; ++kk) {
-          T av[5], bv[5];
+        if (TC) {
+          // fragments (m16n8k8, tf32): A row gid / gid+8, col tig / tig+4;
+          // B row tig / tig+4, col gid; C rows gid / gid+8, cols 2 tig, 2 tig+1
+          for (int s2 = 0; s2 < 2; ++s2) {
+            const int st = w + 8 * s2;
+            if (st < nstrips) {
+              const int r0 = (st / nstrip_n) * 16, c0 = (st % nstrip_n) * (8 * GEMM_NB);
+              for (int k8 = 0; k8 < kt8; k8 += 8) {
+                const float* a_lo = reinterpret_cast<const float*>(As) + (k8 + tig) * TILE + r0 + gid;
+                const float* a_hi = a_lo + 4 * TILE;
+                const unsigned af[4] = {tf32_rna(a_lo[0]), tf32_rna(a_lo[8]), tf32_rna(a_hi[0]), tf32_rna(a_hi[8])};
 #pragma unroll
-          for (int a = 0; a < 5; ++a) av[a] = As[kk * TILE + ty + 16 * a];
+                for (int q = 0; q < GEMM_NB; ++q) {
+                  const int cb = c0 + 8 * q;
+                  if (cb < 8 * nt8) {
+                    const float* b_lo = reinterpret_cast<const float*>(Bs) + (k8 + tig) * TILE + cb + gid;
+                    const unsigned bf[2] = {tf32_rna(b_lo[0]), tf32_rna(b_lo[4 * TILE])};
+                    mma_tf32(fr[s2][q], af, bf);
+                  }
+                }
+              }
+            }
+          }
+        } else {
+          for (int kk = 0; kk < kt; ++kk) {
+            T av[5], bv[5];
 #pragma unroll
-          for (int b = 0; b < 5; ++b) bv[b] = Bs[kk * TILE + tx + 16 * b];
+            for (int a = 0; a < 5; ++a) av[a] = As[kk * TILE + ty + 16 * a];
 #pragma unroll
-          for (int a = 0; a < 5; ++a)
+            for (int b = 0; b < 5; ++b) bv[b] = Bs[kk * TILE + tx + 16 * b];
 #pragma unroll
-            for (int b = 0; b < 5; ++b) acc[a][b] += av[a] * bv[b];
+            for (int a = 0; a < 5; ++a)
+#pragma unroll
+              for (int b = 0; b < 5; ++b) acc[a][b] += av[a] * bv[b];
+          }
         }
+      }
+      if (TC) {
+        for (int s2 = 0; s2 < 2; ++s2) {
+          const int st = w + 8 * s2;
+          if (st < nstrips) {
+            const int r0 = (st / nstrip_n) * 16, c0 = (st % nstrip_n) * (8 * GEMM_NB);
+#pragma unroll
+            for (int q = 0; q < GEMM_NB; ++q) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int i = r0 + gid + (e >> 1) * 8, j = c0 + 8 * q + 2 * tig + (e & 1);
+                if (i < mt && j < nt) {
+                  T v = alpha * (T)fr[s2][q][e];
+                  if (C0) v += beta * C0[(size_t)(i0 + i) * ldc0 + j0 + j];
+                  if (addI && (i0 + i) == (j0 + j)) v += T(1);
+                  C[(size_t)(i0 + i) * ldc + j0 + j] = v;
+                }
+              }
+            }
+          }
+        }
+        continue;
       }
 #pragma unroll
       for (int a = 0; a < 5; ++a) {

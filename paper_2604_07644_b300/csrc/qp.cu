@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   const int t = threadIdx.x;
   c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
   c.t_last = clock64();
+  c.tc = args.tc != 0;
 
   if (args.mode == MODE_KKT) {
     const double kkt = kkt_eval<T>(c, cl);
@@ -388,6 +389,7 @@ static int launch_qp(qp_handle* h, const SolveArgs& a) {
 // of QP 0 and prints them to stderr after each launch.
 static int launch(qp_handle* h, const SolveArgs& a0) {
   SolveArgs a = a0;
+  a.tc = h->set.precision == GPUSLS_TF32 ? 1 : 0;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(h->stream, &cap));
   const bool prof_on = getenv("GPUSLS_PROFILE") != nullptr && cap == cudaStreamCaptureStatusNone;
@@ -449,7 +451,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
                               const double* hi, const double* rho, const qp_settings* s, void* stream) {
   if (!out || batch < 1 || !dims || !A || !B || !c || !Q || !R || !q || !r || !lo || !hi || !s)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: null argument or batch < 1");
-  if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32)
+  if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32 && s->precision != GPUSLS_TF32)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: unknown precision");
   if (s->cluster < 0 || s->cluster > MAXCS) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: cluster must be 0..8");
   if (s->occupancy < 0 || s->occupancy > 1 || s->schedule < 0 || s->schedule > 1)

@@ -75,6 +75,7 @@ struct SolveArgs {
   int max_refine;
   int fallback_iters;   // > 0: a warm-started QP not converged after this many iterations restarts cold
   const int* order;     // launch order: cluster b solves QP order[b] (null: QP b)
+  int tc;               // 1: factorization block products on the tensor cores in TF32
 };
 
 // Per-stage operator bundles of the cached iteration (elements).  Every
@@ -180,6 +181,7 @@ struct Ctx {
   T* scr;   // per-CTA global scratch: 6 matrices nx x ldx
   int msz;  // nx * ldx
   unsigned long long* prof;  // non-null only in thread 0 of each CTA of QP 0 when profiling
+  bool tc;                   // factorization products in TF32 on the tensor cores
   long long t_last;
 };
 
@@ -247,15 +249,15 @@ __device__ __noinline__ int combine_full(Ctx<T>& c, const T* lP, const T* lA, co
   T* V = c.scr + 2 * c.msz;
   T* U = c.scr + 3 * c.msz;
   T* Wm = c.scr + 4 * c.msz;
-  cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm, c.tc);
   const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, Wm, ld, c.gemm, c.perm, c.flag);
-  cta_gemm<T>(n, n, n, T(1), Wm, ld, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), rA, ld, false, Wm, ld, false, T(0), nullptr, 0, false, Psi, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), Psi, ld, false, lA, ld, false, T(0), nullptr, 0, false, oA, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), Psi, ld, false, lC, ld, false, T(0), nullptr, 0, false, U, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), U, ld, false, rA, ld, true, T(1), rC, ld, false, oC, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), Wm, ld, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm, c.tc);
+  cta_gemm<T>(n, n, n, T(1), rA, ld, false, Wm, ld, false, T(0), nullptr, 0, false, Psi, ld, c.gemm, c.tc);
+  cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm, c.tc);
+  cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm, c.tc);
+  cta_gemm<T>(n, n, n, T(1), Psi, ld, false, lA, ld, false, T(0), nullptr, 0, false, oA, ld, c.gemm, c.tc);
+  cta_gemm<T>(n, n, n, T(1), Psi, ld, false, lC, ld, false, T(0), nullptr, 0, false, U, ld, c.gemm, c.tc);
+  cta_gemm<T>(n, n, n, T(1), U, ld, false, rA, ld, true, T(1), rC, ld, false, oC, ld, c.gemm, c.tc);
   return bad;
 }
 
@@ -266,11 +268,11 @@ __device__ __noinline__ int combine_complete(Ctx<T>& c, const T* lP, const T* lA
   T* X = c.scr;
   T* V = c.scr + 2 * c.msz;
   T* Wm = c.scr + 4 * c.msz;
-  cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), lC, ld, false, rP, ld, false, T(0), nullptr, 0, true, c.gj, GJ_LD, c.gemm, c.tc);
   const int bad = cta_inverse<T>(c.gj, GJ_LD, n, true, Wm, ld, c.gemm, c.perm, c.flag);
-  cta_gemm<T>(n, n, n, T(1), Wm, ld, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm);
-  cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm);
+  cta_gemm<T>(n, n, n, T(1), Wm, ld, false, lA, ld, false, T(0), nullptr, 0, false, X, ld, c.gemm, c.tc);
+  cta_gemm<T>(n, n, n, T(1), rP, ld, false, lA, ld, false, T(0), nullptr, 0, false, V, ld, c.gemm, c.tc);
+  cta_gemm<T>(n, n, n, T(1), V, ld, true, X, ld, false, T(1), lP, ld, false, oP, ld, c.gemm, c.tc);
   return bad;
 }
 
@@ -322,20 +324,20 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       T* Shi = Sh + (size_t)i * nu * ldx;
       T* Rhii = Rhi + (size_t)i * nu * ldu;
       // Q^ = Q + rho C^T C,  R^ = R + rho D^T D,  S^ = S + rho D^T C
-      cta_gemm<T>(nx, nx, nc, rho, Ci, ldx, true, Ci, ldx, false, T(1), Q + (size_t)i * msz, ldx, false, Pl, ldx, c.gemm);
-      cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm);
-      cta_gemm<T>(nu, nx, nc, rho, Di, ldu, true, Ci, ldx, false, T(1), S + (size_t)i * nu * ldx, ldx, false, Shi, ldx, c.gemm);
+      cta_gemm<T>(nx, nx, nc, rho, Ci, ldx, true, Ci, ldx, false, T(1), Q + (size_t)i * msz, ldx, false, Pl, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm, c.tc);
+      cta_gemm<T>(nu, nx, nc, rho, Di, ldu, true, Ci, ldx, false, T(1), S + (size_t)i * nu * ldx, ldx, false, Shi, ldx, c.gemm, c.tc);
       bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Rhii, ldu, c.gemm, c.perm, c.flag);
       // s0 = R^-1 S^ ; P~ = Q^ - S^^T s0 ; A~ = A - B s0 ; s1 = B R^-1 ; C~ = s1 B^T
-      cta_gemm<T>(nu, nx, nu, T(1), Rhii, ldu, false, Shi, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm);
-      cta_gemm<T>(nx, nx, nu, T(-1), Shi, ldx, true, s0, ldx, false, T(1), Pl, ldx, false, Pl, ldx, c.gemm);
-      cta_gemm<T>(nx, nx, nu, T(-1), Bi, ldu, false, s0, ldx, false, T(1), Ai, ldx, false, Al, ldx, c.gemm);
-      cta_gemm<T>(nx, nu, nu, T(1), Bi, ldu, false, Rhii, ldu, false, T(0), nullptr, 0, false, s1, ldu, c.gemm);
-      cta_gemm<T>(nx, nx, nu, T(1), s1, ldu, false, Bi, ldu, true, T(0), nullptr, 0, false, Cl, ldx, c.gemm);
+      cta_gemm<T>(nu, nx, nu, T(1), Rhii, ldu, false, Shi, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nx, nx, nu, T(-1), Shi, ldx, true, s0, ldx, false, T(1), Pl, ldx, false, Pl, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nx, nx, nu, T(-1), Bi, ldu, false, s0, ldx, false, T(1), Ai, ldx, false, Al, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nx, nu, nu, T(1), Bi, ldu, false, Rhii, ldu, false, T(0), nullptr, 0, false, s1, ldu, c.gemm, c.tc);
+      cta_gemm<T>(nx, nx, nu, T(1), s1, ldu, false, Bi, ldu, true, T(0), nullptr, 0, false, Cl, ldx, c.gemm, c.tc);
     }
     if (c.last) {
       T* Pl = VP + (size_t)N * msz;
-      cta_gemm<T>(nx, nx, nf, rho, CN, ldx, true, CN, ldx, false, T(1), Q + (size_t)N * msz, ldx, false, Pl, ldx, c.gemm);
+      cta_gemm<T>(nx, nx, nf, rho, CN, ldx, true, CN, ldx, false, T(1), Q + (size_t)N * msz, ldx, false, Pl, ldx, c.gemm, c.tc);
       cta_zero<T>(nx, nx, VA + (size_t)N * msz, ldx);
       cta_zero<T>(nx, nx, VC + (size_t)N * msz, ldx);
     }
@@ -408,19 +410,19 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       T* Ki = K + (size_t)i * nu * ldx;
       T* Abi = Abar + (size_t)i * msz;
       // s0 = B^T P_{i+1} (nu x nx)
-      cta_gemm<T>(nu, nx, nx, T(1), Bi, ldu, true, Pn, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm);
+      cta_gemm<T>(nu, nx, nx, T(1), Bi, ldu, true, Pn, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm, c.tc);
       // Gamma^-1 = R^ + s0 B  (R^ rebuilt)
-      cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm);
-      cta_gemm<T>(nu, nu, nx, T(1), s0, ldx, false, Bi, ldu, false, T(1), c.gj, GJ_LD, false, c.gj, GJ_LD, c.gemm);
+      cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm, c.tc);
+      cta_gemm<T>(nu, nu, nx, T(1), s0, ldx, false, Bi, ldu, false, T(1), c.gj, GJ_LD, false, c.gj, GJ_LD, c.gemm, c.tc);
       bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Gi, ldu, c.gemm, c.perm, c.flag);
       // s1 = S^ + s0 A ; K = -Gamma s1
-      cta_gemm<T>(nu, nx, nx, T(1), s0, ldx, false, Ai, ldx, false, T(1), Sh + (size_t)i * nu * ldx, ldx, false, s1, ldx, c.gemm);
-      cta_gemm<T>(nu, nx, nu, T(-1), Gi, ldu, false, s1, ldx, false, T(0), nullptr, 0, false, Ki, ldx, c.gemm);
+      cta_gemm<T>(nu, nx, nx, T(1), s0, ldx, false, Ai, ldx, false, T(1), Sh + (size_t)i * nu * ldx, ldx, false, s1, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nu, nx, nu, T(-1), Gi, ldu, false, s1, ldx, false, T(0), nullptr, 0, false, Ki, ldx, c.gemm, c.tc);
       // Abar = A + B K ; CK = C + D K ; F = -Gamma B^T ; J = -Gamma D^T
-      cta_gemm<T>(nx, nx, nu, T(1), Bi, ldu, false, Ki, ldx, false, T(1), Ai, ldx, false, Abi, ldx, c.gemm);
-      cta_gemm<T>(nc, nx, nu, T(1), Di, ldu, false, Ki, ldx, false, T(1), Ci, ldx, false, CK + (size_t)i * nc * ldx, ldx, c.gemm);
-      cta_gemm<T>(nu, nx, nu, T(-1), Gi, ldu, false, Bi, ldu, true, T(0), nullptr, 0, false, F + (size_t)i * nu * ldx, ldx, c.gemm);
-      cta_gemm<T>(nu, nc, nu, T(-1), Gi, ldu, false, Di, ldu, true, T(0), nullptr, 0, false, J + (size_t)i * nu * ldc, ldc, c.gemm);
+      cta_gemm<T>(nx, nx, nu, T(1), Bi, ldu, false, Ki, ldx, false, T(1), Ai, ldx, false, Abi, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nc, nx, nu, T(1), Di, ldu, false, Ki, ldx, false, T(1), Ci, ldx, false, CK + (size_t)i * nc * ldx, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nu, nx, nu, T(-1), Gi, ldu, false, Bi, ldu, true, T(0), nullptr, 0, false, F + (size_t)i * nu * ldx, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nu, nc, nu, T(-1), Gi, ldu, false, Di, ldu, true, T(0), nullptr, 0, false, J + (size_t)i * nu * ldc, ldc, c.gemm, c.tc);
       // vectors: k0 = -Gamma (s0 b + r) ; c0 = Abar^T (P b) + q + K^T r
       const T* bi = bb + (size_t)i * ldx;
       for (int e2 = threadIdx.x; e2 < nx; e2 += NT) c.tmp3[e2] = bi[e2];
@@ -495,9 +497,9 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       cta_copy<T>(nx, nx, Abar + (size_t)i1 * msz, ldx, true, Pc, ldx);
       for (int i = c.e - 2; i >= c.s; --i) {
         cta_gemm<T>(nx, nu, nx, T(1), Pc, ldx, true, F + (size_t)i * nu * ldx, ldx, true, T(0), nullptr, 0, false,
-                    FPi + (size_t)i * nx * ldu, ldu, c.gemm);
+                    FPi + (size_t)i * nx * ldu, ldu, c.gemm, c.tc);
         cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)i * msz, ldx, true, Pc, ldx, false, T(0), nullptr, 0, false, Pn2,
-                    ldx, c.gemm);
+                    ldx, c.gemm, c.tc);
         T* t_ = Pc; Pc = Pn2; Pn2 = t_;
       }
       cta_copy<T>(nx, nx, Pc, ldx, false, Tch + (size_t)c.rank * msz, ldx);
@@ -510,18 +512,18 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       for (int i = c.s + 1; i < c.e; ++i) {
         T* Si = Sig + (size_t)i * msz;
         cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)(i - 1) * msz, ldx, false, Sig + (size_t)(i - 1) * msz, ldx, false,
-                    T(0), nullptr, 0, false, Si, ldx, c.gemm);
+                    T(0), nullptr, 0, false, Si, ldx, c.gemm, c.tc);
         cta_gemm<T>(nu, nx, nx, T(1), K + (size_t)i * nu * ldx, ldx, false, Si, ldx, false, T(0), nullptr, 0, false,
-                    KSig + (size_t)i * nu * ldx, ldx, c.gemm);
+                    KSig + (size_t)i * nu * ldx, ldx, c.gemm, c.tc);
         cta_gemm<T>(nx, nc, nx, T(1), Si, ldx, true, CK + (size_t)i * nc * ldx, ldx, true, T(0), nullptr, 0, false,
-                    CKSig + (size_t)i * nx * ldc, ldc, c.gemm);
+                    CKSig + (size_t)i * nx * ldc, ldc, c.gemm, c.tc);
       }
       T* Ur = Uch + (size_t)c.rank * msz;
       cta_gemm<T>(nx, nx, nx, T(1), Abar + (size_t)(c.e - 1) * msz, ldx, false, Sig + (size_t)(c.e - 1) * msz, ldx,
-                  false, T(0), nullptr, 0, false, Ur, ldx, c.gemm);
+                  false, T(0), nullptr, 0, false, Ur, ldx, c.gemm, c.tc);
       if (c.last) {
         cta_copy<T>(nx, nx, Ur, ldx, false, SigN, ldx);
-        cta_gemm<T>(nf, nx, nx, T(1), CN, ldx, false, SigN, ldx, false, T(0), nullptr, 0, false, CNSig, ldx, c.gemm);
+        cta_gemm<T>(nf, nx, nx, T(1), CN, ldx, false, SigN, ldx, false, T(0), nullptr, 0, false, CNSig, ldx, c.gemm, c.tc);
       }
     }
   }
@@ -536,13 +538,13 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       T* Th = Theta + (size_t)(r0 * MAXCS + m) * msz;
       if (m == r0 + 2) cta_copy<T>(nx, nx, Tch + (size_t)(r0 + 1) * msz, ldx, true, Th, ldx);
       else cta_gemm<T>(nx, nx, nx, T(1), Tch + (size_t)(m - 1) * msz, ldx, true,
-                       Theta + (size_t)(r0 * MAXCS + m - 1) * msz, ldx, false, T(0), nullptr, 0, false, Th, ldx, c.gemm);
+                       Theta + (size_t)(r0 * MAXCS + m - 1) * msz, ldx, false, T(0), nullptr, 0, false, Th, ldx, c.gemm, c.tc);
     }
     for (int m = r0 - 2; m >= 0; --m) {
       T* X = Xi + (size_t)(r0 * MAXCS + m) * msz;
       if (m == r0 - 2) cta_copy<T>(nx, nx, Uch + (size_t)(r0 - 1) * msz, ldx, true, X, ldx);
       else cta_gemm<T>(nx, nx, nx, T(1), Uch + (size_t)(m + 1) * msz, ldx, true,
-                       Xi + (size_t)(r0 * MAXCS + m + 1) * msz, ldx, false, T(0), nullptr, 0, false, X, ldx, c.gemm);
+                       Xi + (size_t)(r0 * MAXCS + m + 1) * msz, ldx, false, T(0), nullptr, 0, false, X, ldx, c.gemm, c.tc);
     }
   }
   const int res = cluster_or<T>(c, cl, bad);

@@ -217,3 +217,29 @@ def test_fp32_refinement_reaches_kkt_on_stalling_instance(lib):
     r2 = b.solve()
     assert r2.info[0]["iters"] == r.info[0]["iters"]   # reset undoes the corrections
     b.close()
+
+
+@pytest.mark.parametrize("name,make", [("plain4d", lambda: W.plain_4d(1)), ("quad12d", lambda: W.quadrotor_12d(2)),
+                                       ("quadruped61", lambda: W.quadruped_61d(0))])
+def test_tf32_products_accuracy_level(lib, name, make):
+    """GPUSLS_TF32 (factorization block products in TF32 on the tensor cores,
+    one pass): the Riccati terms carry the TF32 product error (a few 1e-3,
+    checked against the oracle), and the FP64 KKT gate certifies what that
+    operator allows: a 3e-3 KKT tolerance is reached with every bound
+    satisfied to it.  (1e-4 is not reachable in this mode: the refinement of
+    the linear term cannot undo a 1e-3 operator error.)"""
+    qp = make()
+    b = batch([qp], precision=native.GPUSLS_TF32, rho=0.5)
+    Ps, Ks = b.riccati()
+    Qh, Rh, Sh = lq.augmented(qp, 0.5)
+    P, p, K, kff, G = lq.riccati(qp.A, qp.B, qp.c, Qh, Rh, Sh, np.zeros_like(qp.q), np.zeros_like(qp.r))
+    assert 1e-5 < rel(Ps[0], P) < 1e-2          # TF32-sized error, not FP32-sized
+    assert rel(Ks[0], K) < 1e-2
+    b.close()
+    b = batch([qp], precision=native.GPUSLS_TF32, max_refine=8, max_iter=8000)
+    r = b.solve(tol=3e-3)
+    assert r.info[0]["status"] == native.GPUSLS_OK, r.info
+    assert kkt.kkt_residual(qp, r.dx[0], r.du[0], r.lam[0]) <= 3.0001e-3
+    v = lq.G_apply(qp, r.dx[0], r.du[0])
+    assert np.all(v <= qp.hi + 3e-3) and np.all(v >= qp.lo - 3e-3)
+    b.close()
