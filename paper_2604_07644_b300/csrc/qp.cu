@@ -407,7 +407,8 @@ static int launch(qp_handle* h, const SolveArgs& a0) {
     CU(cudaStreamSynchronize(h->stream));
     cudaFree(dprof);
     static const char* names[PH_COUNT] = {"P1", "bwd", "sync1", "P3", "fwd", "sync2", "P5", "check", "rho",
-                                          "R1", "R2", "R3", "R4", "R5", "R6", "kkt", "ringwait(incl)"};
+                                          "R1", "R2", "R3", "R4", "R5", "R6", "kkt", "ringwait(incl)", "kkt:stages(incl)",
+                                          "kkt:sync(incl)", "kkt:costate(incl)"};
     for (int r = 0; r < MAXCS; ++r) {
       unsigned long long tot = 0;
       for (int k = 0; k < PH_COUNT; ++k) tot += hp[r * PH_COUNT + k];

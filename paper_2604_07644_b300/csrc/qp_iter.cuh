@@ -517,6 +517,7 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
   double* mu = lv + 96;
   double* mu2 = mu + 96;
   double dyn = 0.0, viol = 0.0, comp = 0.0, stat = 0.0;
+  long long kt0 = c.prof ? clock64() : 0;
   cl.sync();   // outputs of every chunk visible
   if (c.active) {
     const int iend = c.e + (c.last ? 1 : 0);
@@ -581,31 +582,61 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
       for (int j = t; j < nx; j += NT) dyn = fmax(dyn, fabs(d.ox[j] - d.x064[j]));
     }
   }
+  long long kt1 = c.prof ? clock64() : 0;
   cl.sync();
+  long long kt2 = c.prof ? clock64() : 0;
   if (c.rank == 0) {
+    // costate recursion mu_i = g_i + A_i^T mu_{i+1}, with the u-residual
+    // B_i^T mu_{i+1} + h_i at each stage.  Every stage is one split-row sweep
+    // over the nx + nu outputs: thread (o, g) sums rows k of group g of
+    // A_i(k, o) (o < nx) or B_i(k, o - nx) times mu(k) straight from global
+    // memory (independent scalar loads: the caller's arrays are unpadded),
+    // and the owners of the outputs add the G partial sums.
+    const int no = nx + nu;
+    int G = NT / no;
+    G = G < 1 ? 1 : (G > SWEEP_MAXG ? SWEEP_MAXG : G);
+    const int Rg = (nx + G - 1) / G;
+    const int o = t % no, g = t / no;
+    const int r0 = min(nx, g * Rg), r1 = min(nx, r0 + Rg);
+    double* part = reinterpret_cast<double*>(c.swp);   // [G][no] partial sums
     for (int j = t; j < nx; j += NT) mu[j] = d.kg[(size_t)N * nx + j];
     __syncthreads();
     for (int i = N - 1; i >= 0; --i) {
-      for (int a = w; a < nu; a += NT / 32) {
+      if (g < G) {
+        const bool isA = o < nx;
+        const double* M = isA ? d.A64 + (size_t)i * nx * nx + o : d.B64 + (size_t)i * nx * nu + (o - nx);
+        const int ld = isA ? nx : nu;
+        double a0 = 0.0, a1 = 0.0;
+        int k = r0;
+        for (; k + 1 < r1; k += 2) {
+          a0 = fma(M[(size_t)k * ld], mu[k], a0);
+          a1 = fma(M[(size_t)(k + 1) * ld], mu[k + 1], a1);
+        }
+        if (k < r1) a0 = fma(M[(size_t)k * ld], mu[k], a0);
+        part[g * no + o] = a0 + a1;
+      }
+      __syncthreads();
+      if (t < no) {
         double s2 = 0.0;
-        for (int j = lane; j < nx; j += 32) s2 += d.B64[(size_t)i * nx * nu + (size_t)j * nu + a] * mu[j];
-        s2 = warp_sum(s2);
-        if (lane == 0) {
+        for (int gg = 0; gg < G; ++gg) s2 += part[gg * no + t];
+        if (t < nx) {
+          mu2[t] = s2 + d.kg[(size_t)i * nx + t];
+        } else {
+          const int a = t - nx;
           const double ru = s2 + d.kh[(size_t)i * nu + a];
           stat = fmax(stat, fabs(ru));
           d.kh[(size_t)i * nu + a] = ru;   // u-stationarity residual, read by refine_linear_term
         }
       }
-      for (int j = t; j < nx; j += NT) {
-        double s2 = d.kg[(size_t)i * nx + j];
-        const double* Ai = d.A64 + (size_t)i * nx * nx;
-        for (int k = 0; k < nx; ++k) s2 += Ai[(size_t)k * nx + j] * mu[k];
-        mu2[j] = s2;
-      }
       __syncthreads();
       for (int j = t; j < nx; j += NT) mu[j] = mu2[j];
       __syncthreads();
     }
+  }
+  if (c.prof) {
+    c.prof[PH_KKT_STAGES] += (unsigned long long)(kt1 - kt0);
+    c.prof[PH_KKT_SYNC] += (unsigned long long)(kt2 - kt1);
+    c.prof[PH_KKT_COSTATE] += (unsigned long long)(clock64() - kt2);
   }
   double v4[4] = {dyn, viol, stat, comp};
   // block-level max of each (reuse red as double scratch)

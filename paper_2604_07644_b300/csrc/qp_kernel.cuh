@@ -187,7 +187,7 @@ struct Ctx {
 
 // Phase timers (debug aid; compiled in, inactive unless SolveArgs.prof is set).
 enum Phase { PH_P1 = 0, PH_BWD, PH_SYNC1, PH_P3, PH_FWD, PH_SYNC2, PH_P5, PH_CHECK, PH_RHO, PH_R1, PH_R2, PH_R3,
-             PH_R4, PH_R5, PH_R6, PH_KKT, PH_RINGWAIT, PH_COUNT };
+             PH_R4, PH_R5, PH_R6, PH_KKT, PH_RINGWAIT, PH_KKT_STAGES, PH_KKT_SYNC, PH_KKT_COSTATE, PH_COUNT };
 template <typename T>
 __device__ inline void prof_mark(Ctx<T>& c, int ph) {
   if (c.prof) {

@@ -63,8 +63,11 @@ def generate(fam, indices, chunk: int = 512, precision=native.GPUSLS_FP32, log=p
 
 
 def train(mlp: MLP, X: np.ndarray, T: np.ndarray, epochs: int = 60, batch: int = 256, lr: float = 1e-3,
-          seed: int = 0, log=print):
-    """Minibatch Adam on (X, T) with a fixed random order (rotated each epoch)."""
+          seed: int = 0, log=print, lr_final: float | None = None, reshuffle: bool = False):
+    """Minibatch Adam on (X, T).  Order: a fixed random permutation (rotated
+    each epoch), or a fresh seeded permutation every epoch (reshuffle).  The
+    step size decays from lr to lr_final on a cosine when lr_final is given."""
+    import math
     g = np.random.Generator(np.random.Philox(seed))
     perm = g.permutation(len(X))
     Xd = torch.from_numpy(np.ascontiguousarray(X[perm])).cuda()
@@ -73,15 +76,20 @@ def train(mlp: MLP, X: np.ndarray, T: np.ndarray, epochs: int = 60, batch: int =
     n = (len(X) // batch) * batch
     losses = []
     for ep in range(epochs):
-        off = (ep * 97) % batch
+        lr_e = lr if lr_final is None else lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * ep / epochs))
+        if reshuffle and ep > 0:
+            idx = torch.from_numpy(g.permutation(len(X))).cuda()
+            Xe, Te, off = Xd[idx], Td[idx], 0
+        else:
+            Xe, Te, off = Xd, Td, (ep * 97) % batch
         tot = 0.0
         steps = 0
         for s in range(off, n - batch + 1, batch):
-            tot += mlp.train_step(Xd[s:s + batch], Td[s:s + batch], lr)
+            tot += mlp.train_step(Xe[s:s + batch], Te[s:s + batch], lr_e)
             steps += 1
         losses.append(tot / max(1, steps))
         if log and (ep % 10 == 0 or ep == epochs - 1):
-            log(f"  epoch {ep}: loss {losses[-1]:.4f}")
+            log(f"  epoch {ep}: loss {losses[-1]:.4f} (lr {lr_e:.2e})")
     return losses
 
 
