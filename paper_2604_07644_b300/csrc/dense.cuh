@@ -355,6 +355,158 @@ constexpr int INV_SCRATCH = INV_PANEL * TILE + INV_PANEL;
 __device__ inline unsigned abs_hi32(float v) { return __float_as_uint(fabsf(v)); }
 __device__ inline unsigned abs_hi32(double v) { return (unsigned)((unsigned long long)__double_as_longlong(fabs(v)) >> 32); }
 
+// Rank-b update of the columns outside panel [k0, k0 + bw) (see cta_inverse),
+// with an R x R register tile per thread of the 16 x 16 grid.
+template <typename T, int R>
+__device__ __forceinline__ void inv_trailing(T* S, int lds, int n, int k0, int bw, int pn, const int* panel_of,
+                                             const T* XP) {
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+  T acc[R][R];
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    const int i = ty + 16 * a;
+    const bool keep = i < n && panel_of[i] != pn;
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const int col = tx + 16 * b;
+      acc[a][b] = (keep && col < n) ? S[i * lds + col] : T(0);
+    }
+  }
+  for (int j = 0; j < bw; ++j) {
+    T xr[R], pc[R];
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const int col = tx + 16 * b;
+      xr[b] = col < n ? XP[j * TILE + col] : T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      const int i = ty + 16 * a;
+      pc[a] = i < n ? S[i * lds + k0 + j] : T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) acc[a][b] = fma(pc[a], xr[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    const int i = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const int col = tx + 16 * b;
+      if (i < n && col < n && (col < k0 || col >= k0 + bw)) S[i * lds + col] = acc[a][b];
+    }
+  }
+}
+
+// Gauss-Jordan steps of one panel [k0, k0 + bw) by warp 0 (see cta_inverse):
+// lane l holds rows l + 32 q, q < QR (QR = 2 covers n <= 64, 3 covers 96).
+template <typename T, int QR>
+__device__ __forceinline__ void inv_panel(T* S, int lds, int n, int k0, int bw, int pn, bool pivot, unsigned& used,
+                                          int& bad, int* perm, int* panel_of, T* rowbuf) {
+  const int lane = threadIdx.x & 31;
+  // Panel columns in registers, rotated so that the current step's
+  // column is always slot 0: after a step every slot moves down by one
+  // and the finished column goes to the last slot.  The step is then
+  // the same code for every j (a rolled loop: the panel code stays small
+  // enough for the instruction cache).  After bw steps slot m holds panel
+  // column (m + bw) mod INV_PANEL.
+  T pv[QR][INV_PANEL];
+#pragma unroll
+  for (int q = 0; q < QR; ++q) {
+    const int i = lane + 32 * q;
+#pragma unroll
+    for (int l = 0; l < INV_PANEL; ++l) pv[q][l] = (i < n && l < bw) ? S[i * lds + k0 + l] : T(0);
+  }
+#pragma unroll 1
+  for (int j = 0; j < bw; ++j) {
+    const int k = k0 + j;
+    int p = k;
+    if (pivot) {
+      // argmax |column| over unused rows in one warp max: the key is the
+      // top 32 bits of |value| (non-negative floats order like unsigned
+      // integers) with the low 7 bits replaced by 127 - row, so the
+      // winner is a largest |value| up to a relative 2^-16 (FP32) or
+      // 2^-13 (FP64) -- as good a partial pivot -- ties to the lower row
+      unsigned key = 0u;
+#pragma unroll
+      for (int q = 0; q < QR; ++q) {
+        const int i = lane + 32 * q;
+        if (i < n && !((used >> q) & 1u)) {
+          const unsigned kq = (abs_hi32(pv[q][0]) & ~127u) | (unsigned)(127 - i);
+          key = kq > key ? kq : key;
+        }
+      }
+      const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+      p = 127 - (int)(kmax & 127u);
+      p = (p >= 0 && p < n) ? p : n - 1;   // always in range: an unused row exists while k < n
+    }
+    const int pl = p & 31, pq = p >> 5;
+    // pivot row of the panel, broadcast through shared memory by its owner
+    using V16 = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::W;
+    if (lane == pl) {
+#pragma unroll
+      for (int l0 = 0; l0 < INV_PANEL; l0 += VW) {
+        V16 v;
+        T* vp = reinterpret_cast<T*>(&v);
+#pragma unroll
+        for (int e = 0; e < VW; ++e)
+        {
+          T sel = pv[0][l0 + e];
+#pragma unroll
+          for (int q = 1; q < QR; ++q) sel = pq == q ? pv[q][l0 + e] : sel;   // constant indices only
+          vp[e] = sel;
+        }
+        reinterpret_cast<V16*>(rowbuf)[l0 / VW] = v;
+      }
+    }
+    __syncwarp();
+    T rowp[INV_PANEL];
+#pragma unroll
+    for (int l0 = 0; l0 < INV_PANEL; l0 += VW) {
+      const V16 v = reinterpret_cast<const V16*>(rowbuf)[l0 / VW];
+      const T* vp = reinterpret_cast<const T*>(&v);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) rowp[l0 + e] = vp[e];
+    }
+    __syncwarp();
+    T piv = rowp[0];
+    const bool badk = pivot ? !(fabs(piv) > tiny_pivot<T>()) : !(piv > T(0));
+    if (badk) {
+      bad = 1;
+      piv = T(1);
+    }
+    const T ip = T(1) / piv;
+#pragma unroll
+    for (int q = 0; q < QR; ++q) {
+      const bool isp = (lane + 32 * q) == p;
+      const T g = -(pv[q][0] - (isp ? T(1) : T(0))) * ip;
+      // slots 1.. get the step's update and move down; slot 0 (this
+      // step's column, replaced by e_p + g) goes to the last slot
+#pragma unroll
+      for (int l = 1; l < INV_PANEL; ++l) pv[q][l - 1] = fma(g, rowp[l], pv[q][l]);
+      pv[q][INV_PANEL - 1] = (isp ? T(1) : T(0)) + g;
+    }
+    if (lane == pl) used |= 1u << pq;
+    if (lane == 0) {
+      perm[k] = p;
+      panel_of[p] = pn;
+    }
+  }
+  // undo the rotation: slot m holds panel column (m + bw) mod INV_PANEL
+#pragma unroll
+  for (int q = 0; q < QR; ++q) {
+    const int i = lane + 32 * q;
+#pragma unroll
+    for (int m = 0; m < INV_PANEL; ++m) {
+      const int l = (m + bw) & (INV_PANEL - 1);
+      if (i < n && l < bw) S[i * lds + k0 + l] = pv[q][m];
+    }
+  }
+}
+
 template <typename T>
 __device__ __noinline__ int cta_inverse(T* S, int lds, int n, bool pivot, T* Wout, int ldw, T* scratch, int* perm,
                                         int* flag) {
@@ -372,100 +524,8 @@ __device__ __noinline__ int cta_inverse(T* S, int lds, int n, bool pivot, T* Wou
     const int k0 = pn * INV_PANEL;
     const int bw = min(INV_PANEL, n - k0);
     if (w == 0) {
-      // Panel columns in registers, rotated so that the current step's
-      // column is always slot 0: after a step every slot moves down by one
-      // and the finished column goes to the last slot.  The step is then
-      // the same code for every j (a rolled loop: the panel code stays small
-      // enough for the instruction cache).  After bw steps slot m holds panel
-      // column (m + bw) mod INV_PANEL.
-      T pv[3][INV_PANEL];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int i = lane + 32 * q;
-#pragma unroll
-        for (int l = 0; l < INV_PANEL; ++l) pv[q][l] = (i < n && l < bw) ? S[i * lds + k0 + l] : T(0);
-      }
-#pragma unroll 1
-      for (int j = 0; j < bw; ++j) {
-        const int k = k0 + j;
-        int p = k;
-        if (pivot) {
-          // argmax |column| over unused rows in one warp max: the key is the
-          // top 32 bits of |value| (non-negative floats order like unsigned
-          // integers) with the low 7 bits replaced by 127 - row, so the
-          // winner is a largest |value| up to a relative 2^-16 (FP32) or
-          // 2^-13 (FP64) -- as good a partial pivot -- ties to the lower row
-          unsigned key = 0u;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const int i = lane + 32 * q;
-            if (i < n && !((used >> q) & 1u)) {
-              const unsigned kq = (abs_hi32(pv[q][0]) & ~127u) | (unsigned)(127 - i);
-              key = kq > key ? kq : key;
-            }
-          }
-          const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-          p = 127 - (int)(kmax & 127u);
-          p = (p >= 0 && p < n) ? p : n - 1;   // always in range: an unused row exists while k < n
-        }
-        const int pl = p & 31, pq = p >> 5;
-        // pivot row of the panel, broadcast through shared memory by its owner
-        using V16 = typename Vec16<T>::type;
-        constexpr int VW = Vec16<T>::W;
-        if (lane == pl) {
-#pragma unroll
-          for (int l0 = 0; l0 < INV_PANEL; l0 += VW) {
-            V16 v;
-            T* vp = reinterpret_cast<T*>(&v);
-#pragma unroll
-            for (int e = 0; e < VW; ++e)
-              vp[e] = pq == 0 ? pv[0][l0 + e] : (pq == 1 ? pv[1][l0 + e] : pv[2][l0 + e]);
-            reinterpret_cast<V16*>(rowbuf)[l0 / VW] = v;
-          }
-        }
-        __syncwarp();
-        T rowp[INV_PANEL];
-#pragma unroll
-        for (int l0 = 0; l0 < INV_PANEL; l0 += VW) {
-          const V16 v = reinterpret_cast<const V16*>(rowbuf)[l0 / VW];
-          const T* vp = reinterpret_cast<const T*>(&v);
-#pragma unroll
-          for (int e = 0; e < VW; ++e) rowp[l0 + e] = vp[e];
-        }
-        __syncwarp();
-        T piv = rowp[0];
-        const bool badk = pivot ? !(fabs(piv) > tiny_pivot<T>()) : !(piv > T(0));
-        if (badk) {
-          bad = 1;
-          piv = T(1);
-        }
-        const T ip = T(1) / piv;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const bool isp = (lane + 32 * q) == p;
-          const T g = -(pv[q][0] - (isp ? T(1) : T(0))) * ip;
-          // slots 1.. get the step's update and move down; slot 0 (this
-          // step's column, replaced by e_p + g) goes to the last slot
-#pragma unroll
-          for (int l = 1; l < INV_PANEL; ++l) pv[q][l - 1] = fma(g, rowp[l], pv[q][l]);
-          pv[q][INV_PANEL - 1] = (isp ? T(1) : T(0)) + g;
-        }
-        if (lane == pl) used |= 1u << pq;
-        if (lane == 0) {
-          perm[k] = p;
-          panel_of[p] = pn;
-        }
-      }
-      // undo the rotation: slot m holds panel column (m + bw) mod INV_PANEL
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int i = lane + 32 * q;
-#pragma unroll
-        for (int m = 0; m < INV_PANEL; ++m) {
-          const int l = (m + bw) & (INV_PANEL - 1);
-          if (i < n && l < bw) S[i * lds + k0 + l] = pv[q][m];
-        }
-      }
+      if (n <= 64) inv_panel<T, 2>(S, lds, n, k0, bw, pn, pivot, used, bad, perm, panel_of, rowbuf);
+      else inv_panel<T, 3>(S, lds, n, k0, bw, pn, pivot, used, bad, perm, panel_of, rowbuf);
     }
     __syncthreads();
     // pivot rows of this panel, before the rank-b update
@@ -475,50 +535,12 @@ __device__ __noinline__ int cta_inverse(T* S, int lds, int n, bool pivot, T* Wou
     }
     __syncthreads();
     // x_i <- [i not a pivot row of this panel] x_i + sum_j PC[i][j] XP[j] for
-    // every column outside the panel: 16 x 16 thread grid, 5 x 5 elements each
-    // (rows ty + 16 a, columns tx + 16 b).  No other thread reads what a
-    // thread writes: it owns its (row, column) elements, and the panel
-    // columns it reads are not written in this phase.
-    {
-      const int ty = t >> 4, tx = t & 15;
-      T acc[5][5];
-#pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        const int i = ty + 16 * a;
-        const bool keep = i < n && panel_of[i] != pn;
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          const int col = tx + 16 * b;
-          acc[a][b] = (keep && col < n) ? S[i * lds + col] : T(0);
-        }
-      }
-      for (int j = 0; j < bw; ++j) {
-        T xr[5], pc[5];
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          const int col = tx + 16 * b;
-          xr[b] = col < n ? XP[j * TILE + col] : T(0);
-        }
-#pragma unroll
-        for (int a = 0; a < 5; ++a) {
-          const int i = ty + 16 * a;
-          pc[a] = i < n ? S[i * lds + k0 + j] : T(0);
-        }
-#pragma unroll
-        for (int a = 0; a < 5; ++a)
-#pragma unroll
-          for (int b = 0; b < 5; ++b) acc[a][b] = fma(pc[a], xr[b], acc[a][b]);
-      }
-#pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        const int i = ty + 16 * a;
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          const int col = tx + 16 * b;
-          if (i < n && col < n && (col < k0 || col >= k0 + bw)) S[i * lds + col] = acc[a][b];
-        }
-      }
-    }
+    // every column outside the panel: 16 x 16 thread grid, rows ty + 16 a and
+    // columns tx + 16 b (4 x 4 per thread when n <= 64, else 5 x 5).  No
+    // other thread reads what a thread writes: it owns its (row, column)
+    // elements, and the panel columns it reads are not written in this phase.
+    if (n <= 64) inv_trailing<T, 4>(S, lds, n, k0, bw, pn, panel_of, XP);
+    else inv_trailing<T, 5>(S, lds, n, k0, bw, pn, panel_of, XP);
     __syncthreads();
   }
   if (t == 0 && bad) flag[0] = 1;
