@@ -97,6 +97,46 @@ __device__ inline void cta_fill(T* dst, int total, F f) {
   }
 }
 
+// acc[a][b] += sum_kk As[kk][ty + 16 a] Bs[kk][tx + 16 b] for a < RA, b < RB.
+template <typename T, int RA, int RB>
+__device__ __forceinline__ void gemm_mac(const T* As, const T* Bs, int kt, int ty, int tx, T (&acc)[5][5]) {
+  for (int kk = 0; kk < kt; ++kk) {
+    T av[RA], bv[RB];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) av[a] = As[kk * TILE + ty + 16 * a];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) bv[b] = Bs[kk * TILE + tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int b = 0; b < RB; ++b) acc[a][b] += av[a] * bv[b];
+  }
+}
+
+template <typename T, int RA>
+__device__ __forceinline__ void gemm_mac_rb(int rb, const T* As, const T* Bs, int kt, int ty, int tx,
+                                            T (&acc)[5][5]) {
+  switch (rb) {
+    case 1: gemm_mac<T, RA, 1>(As, Bs, kt, ty, tx, acc); break;
+    case 2: gemm_mac<T, RA, 2>(As, Bs, kt, ty, tx, acc); break;
+    case 3: gemm_mac<T, RA, 3>(As, Bs, kt, ty, tx, acc); break;
+    case 4: gemm_mac<T, RA, 4>(As, Bs, kt, ty, tx, acc); break;
+    default: gemm_mac<T, RA, 5>(As, Bs, kt, ty, tx, acc); break;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void gemm_mac_dispatch(int ra, int rb, const T* As, const T* Bs, int kt, int ty, int tx,
+                                                  T (&acc)[5][5]) {
+  switch (ra) {
+    case 1: gemm_mac_rb<T, 1>(rb, As, Bs, kt, ty, tx, acc); break;
+    case 2: gemm_mac_rb<T, 2>(rb, As, Bs, kt, ty, tx, acc); break;
+    case 3: gemm_mac_rb<T, 3>(rb, As, Bs, kt, ty, tx, acc); break;
+    case 4: gemm_mac_rb<T, 4>(rb, As, Bs, kt, ty, tx, acc); break;
+    default: gemm_mac_rb<T, 5>(rb, As, Bs, kt, ty, tx, acc); break;
+  }
+}
+
 // C = alpha * op(A) * op(B) + beta * C0 (+ I if addI), with op(A) m x k and
 // op(B) k x n.  tA: A is stored k x m (op(A) = A^T); tB likewise.  C may alias
 // C0 but not A or B.  C0 may be null.  Operands may live in global or shared
@@ -212,32 +252,11 @@ __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
               }
             }
           }
-        } else if (mt <= 64 && nt <= 64) {
-          // 4 x 4 register tile (rows / columns 64..79 of the 5 x 5 tile are
-          // empty): 8 loads and 16 FMAs per k step instead of 10 and 25
-          for (int kk = 0; kk < kt; ++kk) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk * TILE + ty + 16 * a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk * TILE + tx + 16 * b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-              for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-          }
         } else {
-          for (int kk = 0; kk < kt; ++kk) {
-            T av[5], bv[5];
-#pragma unroll
-            for (int a = 0; a < 5; ++a) av[a] = As[kk * TILE + ty + 16 * a];
-#pragma unroll
-            for (int b = 0; b < 5; ++b) bv[b] = Bs[kk * TILE + tx + 16 * b];
-#pragma unroll
-            for (int a = 0; a < 5; ++a)
-#pragma unroll
-              for (int b = 0; b < 5; ++b) acc[a][b] += av[a] * bv[b];
-          }
+          // register tile sized to the block: rows ty + 16 a for a < RA =
+          // ceil(mt / 16), columns tx + 16 b for b < RB = ceil(nt / 16), so no
+          // arithmetic is spent on padding rows or columns
+          gemm_mac_dispatch<T>((mt + 15) >> 4, (nt + 15) >> 4, As, Bs, kt, ty, tx, acc);
         }
       }
       if (TC) {
