@@ -84,7 +84,19 @@ typedef struct qp_settings {
                          each QP's own previous solve on this handle (iterations +
                          180 per factorization); the first solve runs in index
                          order.  Only the order changes, never the result.     */
-  int32_t pad2;
+  int32_t factorization; /* schedule of the rho-dependent reverse scan:
+                         0 (default) blocked: each CTA folds its chunk of stage
+                         leaves (eq. assoc_init) into one element with combines
+                         whose left operand is a leaf, the chunk elements are
+                         combined across the cluster, and each chunk's Riccati
+                         terms and gains follow from its right neighbour's
+                         suffix; a leaf's C~ = B R^-1 B^T has rank nu, so these
+                         combines invert nu x nu blocks only (Woodbury).  Falls
+                         back to the tree when nu > 32 or its shared-memory
+                         buffers do not fit.
+                         1 tree: up-sweep and down-sweep of general combines
+                         (eq. combination_rules, App. A).  Both give the same
+                         P_i and K_i up to rounding.                             */
 } qp_settings;
 
 /* Per-QP result summary (host memory). */

@@ -299,6 +299,396 @@ __device__ __noinline__ void cta_gemm(int m, int n, int k, T alpha,
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Register-tile GEMM on operands already in place (normally shared memory):
+// no staging copies.  16 x 16 thread grid; thread (ty, tx) owns output rows
+// ty + 16 a (a < ceil(m / 16)) and columns tx + 16 b (b < ceil(n / 16)).
+// Every output is computed into registers before any is stored, with a CTA
+// barrier in between, so the output may alias A, B or C0.
+// ---------------------------------------------------------------------------
+// One product term op(A) B with op(A) m x k (tA: A stored k x m) and B k x n.
+template <typename T>
+struct MTerm {
+  const T* A;
+  int lda;
+  bool tA;
+  const T* B;
+  int ldb;
+  int k;   // 0: no term
+};
+
+// acc[a][b] += sum_kk op(A)[ty + 16 a][kk] B[kk][tx + 16 b].  Row and column
+// indices past m / n are clamped to m - 1 / n - 1 (their sums are discarded),
+// so no read leaves the operands.
+template <typename T, int RA, int RB, bool TA>
+__device__ __forceinline__ void rt_mac(int m, int n, int k, const T* A, int lda, const T* B, int ldb,
+                                       T (&acc)[5][5]) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const T* pa[RA];
+  const T* pb[RB];
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int i = min(ty + 16 * a, m - 1);
+    pa[a] = TA ? A + i : A + (size_t)i * lda;
+  }
+#pragma unroll
+  for (int b = 0; b < RB; ++b) pb[b] = B + min(tx + 16 * b, n - 1);
+  const int sa = TA ? lda : 1;
+#pragma unroll 2
+  for (int kk = 0; kk < k; ++kk) {
+    T av[RA], bv[RB];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) av[a] = pa[a][kk * sa];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) bv[b] = pb[b][kk * ldb];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int b = 0; b < RB; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+}
+
+template <typename T, int RA, bool TA>
+__device__ __forceinline__ void rt_mac_rb(int rb, int m, int n, const MTerm<T>& p, T (&acc)[5][5]) {
+  switch (rb) {
+    case 1: rt_mac<T, RA, 1, TA>(m, n, p.k, p.A, p.lda, p.B, p.ldb, acc); break;
+    case 2: rt_mac<T, RA, 2, TA>(m, n, p.k, p.A, p.lda, p.B, p.ldb, acc); break;
+    case 3: rt_mac<T, RA, 3, TA>(m, n, p.k, p.A, p.lda, p.B, p.ldb, acc); break;
+    case 4: rt_mac<T, RA, 4, TA>(m, n, p.k, p.A, p.lda, p.B, p.ldb, acc); break;
+    default: rt_mac<T, RA, 5, TA>(m, n, p.k, p.A, p.lda, p.B, p.ldb, acc); break;
+  }
+}
+
+template <typename T, bool TA>
+__device__ __forceinline__ void rt_mac_dispatch(int m, int n, const MTerm<T>& p, T (&acc)[5][5]) {
+  const int ra = (m + 15) >> 4, rb = (n + 15) >> 4;
+  switch (ra) {
+    case 1: rt_mac_rb<T, 1, TA>(rb, m, n, p, acc); break;
+    case 2: rt_mac_rb<T, 2, TA>(rb, m, n, p, acc); break;
+    case 3: rt_mac_rb<T, 3, TA>(rb, m, n, p, acc); break;
+    case 4: rt_mac_rb<T, 4, TA>(rb, m, n, p, acc); break;
+    default: rt_mac_rb<T, 5, TA>(rb, m, n, p, acc); break;
+  }
+}
+
+// Vectorized register-tile body.  Thread t -> (ty, tx) = (t / GX, t % GX) of
+// a GY x GX grid (GY = NT / GX); it owns rows ty + GY a (a < RA) and the
+// 4-column groups starting at 4 tx + 4 GX bb (bb < RB).  B is read as 16-byte
+// vectors along the columns; A (not transposed) as vectors along k, four
+// k-steps per load, with a scalar tail for k % 4; a transposed A by scalars.
+// Groups and rows past n / m are clamped onto the last valid ones for the
+// reads and skipped by the stores.  Requires 16-byte aligned A, B and leading
+// dims that are multiples of 4 elements (checked by the caller).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T* v) {
+  using V16 = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::W;
+#pragma unroll
+  for (int h = 0; h < 4; h += VW) *reinterpret_cast<V16*>(v + h) = *reinterpret_cast<const V16*>(p + h);
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T* v) {
+  using V16 = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::W;
+#pragma unroll
+  for (int h = 0; h < 4; h += VW) *reinterpret_cast<V16*>(p + h) = *reinterpret_cast<const V16*>(v + h);
+}
+
+template <typename T, int GX, int RA, int RB, bool TA>
+__device__ __forceinline__ void mk_mac(int m, int n, const MTerm<T>& p, T (&acc)[RA][RB][4]) {
+  constexpr int GY = NT / GX;
+  const int ty = threadIdx.x / GX, tx = threadIdx.x % GX;
+  const int k = p.k, lda = p.lda, ldb = p.ldb;
+  const int lastg = (n - 1) & ~3;
+  const T* pa[RA];
+  const T* pb[RB];
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int i = min(ty + GY * a, m - 1);
+    pa[a] = TA ? p.A + i : p.A + (size_t)i * lda;
+  }
+#pragma unroll
+  for (int bb = 0; bb < RB; ++bb) pb[bb] = p.B + min(4 * tx + 4 * GX * bb, lastg);
+  if (!TA) {
+    const int k4 = k & ~3;
+#pragma unroll 1
+    for (int kk = 0; kk < k4; kk += 4) {
+      T av[RA][4];
+#pragma unroll
+      for (int a = 0; a < RA; ++a) ld4<T>(pa[a] + kk, av[a]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T bv[RB][4];
+#pragma unroll
+        for (int bb = 0; bb < RB; ++bb) ld4<T>(pb[bb] + (size_t)(kk + q) * ldb, bv[bb]);
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+          for (int bb = 0; bb < RB; ++bb)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][bb][c] = fma(av[a][q], bv[bb][c], acc[a][bb][c]);
+      }
+    }
+    for (int kk = k4; kk < k; ++kk) {
+      T bv[RB][4];
+#pragma unroll
+      for (int bb = 0; bb < RB; ++bb) ld4<T>(pb[bb] + (size_t)kk * ldb, bv[bb]);
+#pragma unroll
+      for (int a = 0; a < RA; ++a) {
+        const T av = pa[a][kk];
+#pragma unroll
+        for (int bb = 0; bb < RB; ++bb)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][bb][c] = fma(av, bv[bb][c], acc[a][bb][c]);
+      }
+    }
+  } else {
+#pragma unroll 2
+    for (int kk = 0; kk < k; ++kk) {
+      T av[RA], bv[RB][4];
+#pragma unroll
+      for (int a = 0; a < RA; ++a) av[a] = pa[a][(size_t)kk * lda];
+#pragma unroll
+      for (int bb = 0; bb < RB; ++bb) ld4<T>(pb[bb] + (size_t)kk * ldb, bv[bb]);
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int bb = 0; bb < RB; ++bb)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][bb][c] = fma(av[a], bv[bb][c], acc[a][bb][c]);
+    }
+  }
+}
+
+template <typename T, int GX, int RA, int RB>
+__device__ __forceinline__ void sgemm_vec(int m, int n, T alpha, const MTerm<T>& p1, const MTerm<T>& p2, T beta,
+                                          const T* C0, int ldc0, bool addI, T* C, int ldc, bool tC) {
+  constexpr int GY = NT / GX;
+  constexpr bool PRE = RA * RB <= 4;   // C0 prefetched into registers when they allow
+  const int ty = threadIdx.x / GX, tx = threadIdx.x % GX;
+  T acc[RA][RB][4];
+  T c0v[PRE ? RA : 1][PRE ? RB : 1][4];
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int bb = 0; bb < RB; ++bb)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        acc[a][bb][c] = T(0);
+        if (PRE) {
+          const int i = ty + GY * a, j = 4 * tx + 4 * GX * bb + c;
+          c0v[PRE ? a : 0][PRE ? bb : 0][c] = (C0 && i < m && j < n) ? C0[(size_t)i * ldc0 + j] : T(0);
+        }
+      }
+  if (p1.k > 0) {
+    if (p1.tA) mk_mac<T, GX, RA, RB, true>(m, n, p1, acc);
+    else mk_mac<T, GX, RA, RB, false>(m, n, p1, acc);
+  }
+  if (p2.k > 0) {
+    if (p2.tA) mk_mac<T, GX, RA, RB, true>(m, n, p2, acc);
+    else mk_mac<T, GX, RA, RB, false>(m, n, p2, acc);
+  }
+  __syncthreads();   // every operand read before any output is written
+  const bool vst = !tC && ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc & 3) == 0;
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int i = ty + GY * a;
+    if (i >= m) continue;
+#pragma unroll
+    for (int bb = 0; bb < RB; ++bb) {
+      const int j0 = 4 * tx + 4 * GX * bb;
+      if (j0 >= n) continue;
+      T v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = j0 + c;
+        T c0 = T(0);
+        if (PRE) c0 = c0v[PRE ? a : 0][PRE ? bb : 0][c];
+        else if (C0 && j < n) c0 = C0[(size_t)i * ldc0 + j];
+        v[c] = alpha * acc[a][bb][c] + beta * c0;
+        if (addI && i == j) v[c] += T(1);
+      }
+      if (vst && j0 + 3 < n) {
+        st4<T>(C + (size_t)i * ldc + j0, v);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = j0 + c;
+          if (j < n) {
+            if (tC) C[(size_t)j * ldc + i] = v[c];
+            else C[(size_t)i * ldc + j] = v[c];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ inline bool mterm_vec_ok(const MTerm<T>& p) {
+  return p.k == 0 || ((((reinterpret_cast<uintptr_t>(p.A) | reinterpret_cast<uintptr_t>(p.B)) & 15) == 0) &&
+                      ((p.lda | p.ldb) & 3) == 0);
+}
+
+// C = alpha (op(A1) B1 + op(A2) B2) + beta C0 (+ I if addI), m, n <= 80; the
+// second term is skipped when p2.k == 0.  tC: C is written transposed
+// (C[j][i]).  C0 (shared or global) is read before the products when the
+// registers allow, so its global-memory latency overlaps them.  Ends with a
+// CTA barrier.  Operands that are not 16-byte aligned take a scalar path.
+template <typename T>
+__device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> p2, T beta, const T* C0, int ldc0,
+                                   bool addI, T* C, int ldc, bool tC) {
+  if (m <= 0 || n <= 0) {
+    __syncthreads();
+    return;
+  }
+  if (mterm_vec_ok(p1) && mterm_vec_ok(p2)) {
+    if (n <= 16) {
+      // narrow outputs: 64 x 4 grid, one column group per thread
+      if (m <= 64) sgemm_vec<T, 4, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+      else sgemm_vec<T, 4, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+    } else {
+      const int ra = (m + 15) >> 4;
+      if (n <= 64) {
+        switch (ra) {
+          case 1: sgemm_vec<T, 16, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 2: sgemm_vec<T, 16, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 3: sgemm_vec<T, 16, 3, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 4: sgemm_vec<T, 16, 4, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          default: sgemm_vec<T, 16, 5, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+        }
+      } else {
+        switch (ra) {
+          case 1: sgemm_vec<T, 16, 1, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 2: sgemm_vec<T, 16, 2, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 3: sgemm_vec<T, 16, 3, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 4: sgemm_vec<T, 16, 4, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          default: sgemm_vec<T, 16, 5, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+        }
+      }
+    }
+    return;
+  }
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  T acc[5][5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) acc[a][b] = T(0);
+  if (p1.k > 0) {
+    if (p1.tA) rt_mac_dispatch<T, true>(m, n, p1, acc);
+    else rt_mac_dispatch<T, false>(m, n, p1, acc);
+  }
+  if (p2.k > 0) {
+    if (p2.tA) rt_mac_dispatch<T, true>(m, n, p2, acc);
+    else rt_mac_dispatch<T, false>(m, n, p2, acc);
+  }
+  __syncthreads();   // every operand read before any output is written
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      if (i < m && j < n) {
+        T v = alpha * acc[a][b] + (C0 ? beta * C0[(size_t)i * ldc0 + j] : T(0));
+        if (addI && i == j) v += T(1);
+        if (tC) C[(size_t)j * ldc + i] = v;
+        else C[(size_t)i * ldc + j] = v;
+      }
+    }
+  __syncthreads();
+}
+
+// One-term convenience form.
+template <typename T>
+__device__ inline void sgemm1(int m, int n, int k, T alpha, const T* A, int lda, bool tA, const T* B, int ldb,
+                              T beta, const T* C0, int ldc0, T* C, int ldc, bool tC = false) {
+  sgemm<T>(m, n, alpha, MTerm<T>{A, lda, tA, B, ldb, k}, MTerm<T>{nullptr, 0, false, nullptr, 0, 0}, beta, C0, ldc0,
+           false, C, ldc, tC);
+}
+
+// Y = X for an m x n block by 16-byte vectors: X, Y 16-byte aligned, leading
+// dims multiples of 4 elements.  Columns n .. rup4(n) - 1 of Y are zeroed.
+template <typename T>
+__device__ void cta_copy_vec(int m, int n, const T* X, int ldxs, T* Y, int ldy) {
+  const int c4 = (n + 3) >> 2, tot = m * c4;
+  for (int e = threadIdx.x; e < tot; e += NT) {
+    const int r = e / c4, cc = (e - r * c4) * 4;
+    T v[4];
+    ld4<T>(X + (size_t)r * ldxs + cc, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (cc + q >= n) v[q] = T(0);
+    st4<T>(Y + (size_t)r * ldy + cc, v);
+  }
+  __syncthreads();
+}
+
+// Inverse of a symmetric positive definite n x n matrix, n <= CAP <= 32, by
+// warp 0: Gauss-Jordan on [G | I] without pivoting (the diagonal pivots of an
+// SPD matrix are positive), lane i holding row i in registers and the pivot
+// row broadcast by shuffles.  G and Gi: shared or global, may not alias.
+// Returns 1 in every thread (after the closing barrier) if a pivot was not
+// positive.  flag: shared int.
+template <typename T, int CAP>
+__device__ int warp_spd_inverse(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag) {
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    T a[CAP], b[CAP];
+#pragma unroll
+    for (int j = 0; j < CAP; ++j) {
+      a[j] = (l < n && j < n) ? G[l * ldg + j] : (l == j ? T(1) : T(0));
+      b[j] = l == j ? T(1) : T(0);
+    }
+    int bad = 0;
+#pragma unroll
+    for (int k = 0; k < CAP; ++k) {
+      if (k < n) {
+        T piv = __shfl_sync(0xffffffffu, a[k], k);
+        if (!(piv > T(0))) {
+          bad = 1;
+          piv = T(1);
+        }
+        const T ip = T(1) / piv;
+        const T f = l == k ? T(0) : a[k] * ip;
+        // columns < k of a are finished (e_j); only j >= k change
+#pragma unroll
+        for (int j = k; j < CAP; ++j) {
+          const T rk = __shfl_sync(0xffffffffu, a[j], k);
+          a[j] = l == k ? rk * ip : fma(-f, rk, a[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < CAP; ++j) {
+          const T rk = __shfl_sync(0xffffffffu, b[j], k);
+          b[j] = l == k ? rk * ip : fma(-f, rk, b[j]);
+        }
+      }
+    }
+    if (l < n) {
+#pragma unroll
+      for (int j = 0; j < CAP; ++j)
+        if (j < n) Gi[l * ldgi + j] = b[j];
+    }
+    if (l == 0) flag[0] = bad;
+  }
+  __syncthreads();
+  const int f = flag[0];
+  __syncthreads();
+  return f;
+}
+
+// Issue (without waiting) the cp.async copy of an m-row block whose rows are
+// `rowb` bytes (a multiple of 16) from global (row pitch gpitch bytes) to
+// shared (row pitch spitch bytes); all addresses 16-byte aligned.
+__device__ inline void cta_stage_rows(void* dst, int spitch, const void* src, int gpitch, int m, int rowb) {
+  const int c16 = rowb >> 4, tot = m * c16;
+  for (int e = threadIdx.x; e < tot; e += NT) {
+    const int r = e / c16, cc = e - r * c16;
+    cp_async16((char*)dst + (size_t)r * spitch + 16 * cc, (const char*)src + (size_t)r * gpitch + 16 * cc);
+  }
+}
+
 // Y = X (copy an m x n block), optional transpose (Y = X^T, Y is n x m).
 template <typename T>
 __device__ void cta_copy(int m, int n, const T* X, int ldxs, bool trans, T* Y, int ldy) {

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   QPDesc& d = dsh;
 
   const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.nch, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
-                                     (int)sizeof(T));
+                                     (int)sizeof(T), d.fact);
   Ctx<T> c;
   c.d = &d;
   c.rank = rank;
@@ -350,7 +350,7 @@ extern "C" void qp_default_settings(qp_settings* s) {
   s->eps_floor = 0.0;   // auto: 1e-7 for FP64 solves, 1e-5 for FP32 solves
   s->occupancy = 0;
   s->schedule = 0;
-  s->pad2 = 0;
+  s->factorization = 0;
 }
 
 extern "C" const char* gpusls_last_error(void) { return g_err.c_str(); }
@@ -408,7 +408,8 @@ static int launch(qp_handle* h, const SolveArgs& a0) {
     cudaFree(dprof);
     static const char* names[PH_COUNT] = {"P1", "bwd", "sync1", "P3", "fwd", "sync2", "P5", "check", "rho",
                                           "R1", "R2", "R3", "R4", "R5", "R6", "kkt", "ringwait(incl)", "kkt:stages(incl)",
-                                          "kkt:sync(incl)", "kkt:costate(incl)"};
+                                          "kkt:sync(incl)", "kkt:costate(incl)", "fA:gamma", "fA:xhc", "fA:ap",
+                                          "fC:gamma", "fC:xk", "fC:p", "fC:out", "fC:bundles"};
     for (int r = 0; r < MAXCS; ++r) {
       unsigned long long tot = 0;
       for (int k = 0; k < PH_COUNT; ++k) tot += hp[r * PH_COUNT + k];
@@ -455,8 +456,9 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32 && s->precision != GPUSLS_TF32)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: unknown precision");
   if (s->cluster < 0 || s->cluster > MAXCS) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: cluster must be 0..8");
-  if (s->occupancy < 0 || s->occupancy > 1 || s->schedule < 0 || s->schedule > 1)
-    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: occupancy and schedule must be 0 or 1");
+  if (s->occupancy < 0 || s->occupancy > 1 || s->schedule < 0 || s->schedule > 1 || s->factorization < 0 ||
+      s->factorization > 1)
+    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: occupancy, schedule and factorization must be 0 or 1");
   if (s->check_every < 1 || s->max_iter < 1 || s->sigma < 0)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: check_every, max_iter >= 1 and sigma >= 0 required");
   int needC = 0, needCN = 0;
@@ -502,7 +504,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   int smem = 0;
   h->hdesc.resize(batch);
   struct Sizes {
-    size_t A, B, b, Q, R, S, q, r, C, D, CN, lo, hi, x0, Rhi, Sh, V, scr, Abar, CK, F, FPi, J, K, KSig, CKSig, Sig,
+    size_t A, B, b, Q, R, S, q, r, C, D, CN, lo, hi, x0, Rhi, Sh, Rh, S0, V, scr, Abar, CK, F, FPi, J, K, KSig, CKSig, Sig,
         c0, k0, CNSig, SigN, Tch, Uch, Theta, Xi, Gam, z, y, BW, FW, CD;
   };
   std::vector<Sizes> sz(batch);
@@ -521,6 +523,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     z.R = al64(N * nu * ldu); z.S = al64(N * nu * ldx); z.q = al64((N + 1) * ldx); z.r = al64(N * ldu);
     z.C = al64(N * nc * ldx + 1); z.D = al64(N * nc * ldu + 1); z.CN = al64(nf * ldx + 1); z.lo = al64(m + 1);
     z.hi = al64(m + 1); z.x0 = al64(ldx); z.Rhi = al64(N * nu * ldu); z.Sh = al64(N * nu * ldx);
+    z.Rh = al64(N * nu * ldu); z.S0 = al64(N * nu * ldx);
     z.V = al64(nodes * msz); z.scr = al64((size_t)MAXCS * 6 * msz); z.Abar = al64(N * msz);
     z.CK = al64(N * nc * ldx + 1); z.F = al64(N * nu * ldx); z.FPi = al64(N * nx * ldu); z.J = al64(N * nu * ldc);
     z.K = al64(N * nu * ldx); z.KSig = al64(N * nu * ldx); z.CKSig = al64(N * nx * ldc + 1); z.Sig = al64(N * msz);
@@ -533,7 +536,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     z.BW = al64(N * (size_t)bws); z.FW = al64(N * (size_t)fws); z.CD = al64(N * (size_t)cds + 1);
     toff[b] = tsz;
     tsz += z.A + z.B + z.b + z.Q + z.R + z.S + z.q + z.r + z.C + z.D + z.CN + z.lo + z.hi + z.x0 + z.Rhi + z.Sh +
-           4 * z.V + z.scr + z.Abar + z.CK + z.F + z.FPi + z.J + z.K + z.KSig + z.CKSig + z.Sig + z.c0 + z.k0 +
+           z.Rh + z.S0 + 4 * z.V + z.scr + z.Abar + z.CK + z.F + z.FPi + z.J + z.K + z.KSig + z.CKSig + z.Sig + z.c0 + z.k0 +
            z.CNSig + z.SigN + z.Tch + z.Uch + z.Theta + z.Xi + z.Gam + z.z + z.y + z.BW + z.FW + z.CD;
     doff[b] = dsz;
     dsz += al64((N + 1) * nx) + al64(N * nu) + 64;   // kg, kh, rho/flags slot
@@ -549,11 +552,16 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     D_.ldf = ldf;
     D_.slot = std::max(std::max(std::max(bws, fws), (int)msz),
                        std::max(std::max(d.nx * (int)ldu, d.nx * (int)ldc), cds));
-    D_.depth = 3;
-    if (smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, D_.nch, (int)ldx, (int)ldu, ldv, ldf, 3, D_.slot, esz).total > 227 * 1024)
-      D_.depth = 2;
+    // blocked factorization unless asked for the tree or it does not fit
+    auto lay_total = [&](int depth, int fact) {
+      return smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, D_.nch, (int)ldx, (int)ldu, ldv, ldf, depth, D_.slot, esz,
+                         fact).total;
+    };
+    D_.fact = (s->factorization == 1 || s->precision == GPUSLS_TF32 || d.nu > FACT_MAX_NU) ? 1 : 0;
+    if (D_.fact == 0 && lay_total(1, 0) > 227 * 1024) D_.fact = 1;
+    D_.depth = lay_total(3, D_.fact) > 227 * 1024 ? 2 : 3;
     const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, D_.nch, (int)ldx, (int)ldu, ldv, ldf, D_.depth,
-                                       D_.slot, esz);
+                                       D_.slot, esz, D_.fact);
     smem = std::max(smem, lay.total);
   }
   h->smem = smem;
@@ -600,7 +608,8 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     auto take = [&](size_t n) { void* r_ = p; p += n * esz; return r_; };
     D_.A = take(z.A); D_.B = take(z.B); D_.b = take(z.b); D_.Q = take(z.Q); D_.R = take(z.R); D_.S = take(z.S);
     D_.q = take(z.q); D_.r = take(z.r); D_.C = take(z.C); D_.D = take(z.D); D_.CN = take(z.CN); D_.lo = take(z.lo);
-    D_.hi = take(z.hi); D_.x0 = take(z.x0); D_.Rhi = take(z.Rhi); D_.Sh = take(z.Sh); D_.VP = take(z.V);
+    D_.hi = take(z.hi); D_.x0 = take(z.x0); D_.Rhi = take(z.Rhi); D_.Sh = take(z.Sh); D_.Rh = take(z.Rh);
+    D_.S0 = take(z.S0); D_.VP = take(z.V);
     D_.VA = take(z.V); D_.VC = take(z.V); D_.IP = take(z.V); D_.scr = take(z.scr); D_.Abar = take(z.Abar);
     D_.CK = take(z.CK); D_.F = take(z.F); D_.FPi = take(z.FPi); D_.J = take(z.J); D_.K = take(z.K);
     D_.KSig = take(z.KSig); D_.CKSig = take(z.CKSig); D_.Sig = take(z.Sig); D_.c0 = take(z.c0); D_.k0 = take(z.k0);

@@ -37,11 +37,12 @@ struct QPDesc {
   int nlev;         // tree levels above the leaves
   int ldv, ldf;     // row strides of the stacked vectors [l; omega] and [x; k]
   int depth, slot;  // cp.async ring depth and slot size (elements)
-  int pad0;
+  int fact;         // factorization schedule: 0 blocked (leaf-structured combines), 1 tree
   // problem (T)
   void *A, *B, *b, *Q, *R, *S, *q, *r, *C, *D, *CN, *lo, *hi, *x0;
   // factorization workspace (T)
   void *Rhi, *Sh, *VP, *VA, *VC, *IP, *scr;
+  void *Rh, *S0;    // R^_i and R^_i^-1 S^_i per stage (blocked schedule)
   // cached iteration operators (T)
   void *Abar, *CK, *F, *FPi, *J, *K, *KSig, *CKSig, *Sig, *c0, *k0, *CNSig, *SigN, *Tch, *Uch,
       *Theta, *Xi, *Gam;
@@ -109,13 +110,54 @@ constexpr int RING_WAIT_LIMIT = 1 << 22;   // polls of one bulk-copy completion 
 
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
+// Shared-memory buffers of the blocked factorization, element offsets into
+// the union region (which the iteration's ring and the tree's GEMM staging
+// use at other times).  Every buffer starts on a multiple of 4 elements
+// (16 bytes in FP32, 32 in FP64).
+struct FactLayout {
+  int lds;   // row pitch of the nx-column buffers (ldx, or ldx + 4 when ldx is a multiple of 32: no bank conflicts
+             // between the two rows a warp reads)
+  int P, Aa, Xb, Bb[2], Rb[2], Db[2], S1, S2, S3, Gm, Gi, vec;
+  int vlen;  // length of each of the 8 vectors at vec
+  int total;
+};
+
+__host__ __device__ inline FactLayout fact_layout(int nx, int nu, int nc, int ldx, int ldu) {
+  FactLayout f;
+  f.lds = (ldx % 32 == 0) ? ldx + 4 : ldx;
+  f.vlen = rup4(nx > nu ? nx : nu);
+  int off = 0;
+  const int big = rup4(nx * f.lds), bsz = rup4(nx * ldu), rsz = rup4(nu * ldu), dsz = rup4(nc * ldu),
+            ssz = rup4(nu * f.lds);
+  f.P = off; off += big;
+  f.Aa = off; off += big;
+  f.Xb = off; off += big;
+  for (int k = 0; k < 2; ++k) { f.Bb[k] = off; off += bsz; }
+  for (int k = 0; k < 2; ++k) { f.Rb[k] = off; off += rsz; }
+  for (int k = 0; k < 2; ++k) { f.Db[k] = off; off += dsz; }
+  f.S1 = off; off += ssz;
+  f.S2 = off; off += ssz;
+  f.S3 = off; off += ssz;
+  f.Gm = off; off += rsz;
+  f.Gi = off; off += rsz;
+  f.vec = off; off += 8 * f.vlen;
+  f.total = off;
+  return f;
+}
+
+// The blocked schedule runs when its buffers fit and nu is small enough for
+// the one-warp inverse of the nu x nu blocks.
+constexpr int FACT_MAX_NU = 32;
+
 __host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf, int Lc, int nch, int ldx, int ldu,
-                                                  int ldv, int ldf, int depth, int slot, int esz) {
+                                                  int ldv, int ldf, int depth, int slot, int esz, int fact) {
   SmemLayout s;
   int off = 0;
   const int ring_b = depth * slot * esz;
   const int dense_b = (2 * KT * TILE + TILE * GJ_LD + 3 * TILE) * esz;
-  const int uni = ring_b > dense_b ? ring_b : dense_b;
+  const int fact_b = fact == 0 ? fact_layout(nx, nu, nc, ldx, ldu).total * esz : 0;
+  int uni = ring_b > dense_b ? ring_b : dense_b;
+  uni = uni > fact_b ? uni : fact_b;
   s.ring = 0;
   s.gemm = 0;
   s.gj = 2 * KT * TILE * esz;
@@ -187,7 +229,8 @@ struct Ctx {
 
 // Phase timers (debug aid; compiled in, inactive unless SolveArgs.prof is set).
 enum Phase { PH_P1 = 0, PH_BWD, PH_SYNC1, PH_P3, PH_FWD, PH_SYNC2, PH_P5, PH_CHECK, PH_RHO, PH_R1, PH_R2, PH_R3,
-             PH_R4, PH_R5, PH_R6, PH_KKT, PH_RINGWAIT, PH_KKT_STAGES, PH_KKT_SYNC, PH_KKT_COSTATE, PH_COUNT };
+             PH_R4, PH_R5, PH_R6, PH_KKT, PH_RINGWAIT, PH_KKT_STAGES, PH_KKT_SYNC, PH_KKT_COSTATE,
+             PH_FA1, PH_FA2, PH_FA3, PH_FC1, PH_FC2, PH_FC3, PH_FC4, PH_FC5, PH_COUNT };
 template <typename T>
 __device__ inline void prof_mark(Ctx<T>& c, int ph) {
   if (c.prof) {
@@ -290,61 +333,24 @@ __device__ int cluster_or(Ctx<T>& c, cg::cluster_group& cl, int v) {
   return r;
 }
 
-// ---------------------------------------------------------------------------
-// rho-dependent factorization (the "refactor")
-// ---------------------------------------------------------------------------
+// Tree schedule of the reverse scan (eq. combination_rules, App. A): up-sweep
+// of full combines and down-sweep of complete-suffix combines level by level,
+// then the gains (eq. controller_cache) and the iteration operators per stage.
 template <typename T>
-__device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
+__device__ __noinline__ int tree_scan(Ctx<T>& c, cg::cluster_group& cl, T rho) {
   QPDesc& d = *c.d;
-  const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, N = d.N;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, N = d.N;
   const int ldx = d.ldx, ldu = d.ldu, ldc = d.ldc;
   const int msz = c.msz;
-  const T *A = TP<T>(d.A), *B = TP<T>(d.B), *bb = TP<T>(d.b), *Q = TP<T>(d.Q), *R = TP<T>(d.R), *S = TP<T>(d.S);
-  const T *q = TP<T>(d.q), *r = TP<T>(d.r), *C = TP<T>(d.C), *D = TP<T>(d.D), *CN = TP<T>(d.CN);
-  T *Rhi = TP<T>(d.Rhi), *Sh = TP<T>(d.Sh), *VP = TP<T>(d.VP), *VA = TP<T>(d.VA), *VC = TP<T>(d.VC), *IP = TP<T>(d.IP);
-  T *Abar = TP<T>(d.Abar), *CK = TP<T>(d.CK), *F = TP<T>(d.F), *FPi = TP<T>(d.FPi), *J = TP<T>(d.J), *K = TP<T>(d.K);
-  T *KSig = TP<T>(d.KSig), *CKSig = TP<T>(d.CKSig), *Sig = TP<T>(d.Sig), *c0 = TP<T>(d.c0), *k0 = TP<T>(d.k0);
-  T *CNSig = TP<T>(d.CNSig), *SigN = TP<T>(d.SigN), *Tch = TP<T>(d.Tch), *Uch = TP<T>(d.Uch);
-  T *Theta = TP<T>(d.Theta), *Xi = TP<T>(d.Xi), *Gam = TP<T>(d.Gam);
+  const T *A = TP<T>(d.A), *B = TP<T>(d.B), *bb = TP<T>(d.b), *R = TP<T>(d.R);
+  const T *q = TP<T>(d.q), *r = TP<T>(d.r), *C = TP<T>(d.C), *D = TP<T>(d.D);
+  T *Sh = TP<T>(d.Sh), *VP = TP<T>(d.VP), *VA = TP<T>(d.VA), *VC = TP<T>(d.VC), *IP = TP<T>(d.IP);
+  T *Abar = TP<T>(d.Abar), *CK = TP<T>(d.CK), *F = TP<T>(d.F), *J = TP<T>(d.J), *K = TP<T>(d.K);
+  T *c0 = TP<T>(d.c0), *k0 = TP<T>(d.k0), *Gam = TP<T>(d.Gam);
   T* s0 = c.scr + 4 * msz;   // small temporaries (nu x nx etc.)
   T* s1 = c.scr + 5 * msz;
   int bad = 0;
   const int n = N + 1;
-
-  // R1: leaves (eq. assoc_init) for own stages, terminal by the last chunk.
-  if (c.active) {
-    for (int i = c.s; i < c.e; ++i) {
-      const T* Ai = A + (size_t)i * msz;
-      const T* Bi = B + (size_t)i * nx * ldu;
-      const T* Ci = C + (size_t)i * nc * ldx;
-      const T* Di = D + (size_t)i * nc * ldu;
-      T* Pl = VP + (size_t)i * msz;
-      T* Al = VA + (size_t)i * msz;
-      T* Cl = VC + (size_t)i * msz;
-      T* Shi = Sh + (size_t)i * nu * ldx;
-      T* Rhii = Rhi + (size_t)i * nu * ldu;
-      // Q^ = Q + rho C^T C,  R^ = R + rho D^T D,  S^ = S + rho D^T C
-      cta_gemm<T>(nx, nx, nc, rho, Ci, ldx, true, Ci, ldx, false, T(1), Q + (size_t)i * msz, ldx, false, Pl, ldx, c.gemm, c.tc);
-      cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm, c.tc);
-      cta_gemm<T>(nu, nx, nc, rho, Di, ldu, true, Ci, ldx, false, T(1), S + (size_t)i * nu * ldx, ldx, false, Shi, ldx, c.gemm, c.tc);
-      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Rhii, ldu, c.gemm, c.perm, c.flag);
-      // s0 = R^-1 S^ ; P~ = Q^ - S^^T s0 ; A~ = A - B s0 ; s1 = B R^-1 ; C~ = s1 B^T
-      cta_gemm<T>(nu, nx, nu, T(1), Rhii, ldu, false, Shi, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm, c.tc);
-      cta_gemm<T>(nx, nx, nu, T(-1), Shi, ldx, true, s0, ldx, false, T(1), Pl, ldx, false, Pl, ldx, c.gemm, c.tc);
-      cta_gemm<T>(nx, nx, nu, T(-1), Bi, ldu, false, s0, ldx, false, T(1), Ai, ldx, false, Al, ldx, c.gemm, c.tc);
-      cta_gemm<T>(nx, nu, nu, T(1), Bi, ldu, false, Rhii, ldu, false, T(0), nullptr, 0, false, s1, ldu, c.gemm, c.tc);
-      cta_gemm<T>(nx, nx, nu, T(1), s1, ldu, false, Bi, ldu, true, T(0), nullptr, 0, false, Cl, ldx, c.gemm, c.tc);
-    }
-    if (c.last) {
-      T* Pl = VP + (size_t)N * msz;
-      cta_gemm<T>(nx, nx, nf, rho, CN, ldx, true, CN, ldx, false, T(1), Q + (size_t)N * msz, ldx, false, Pl, ldx, c.gemm, c.tc);
-      cta_zero<T>(nx, nx, VA + (size_t)N * msz, ldx);
-      cta_zero<T>(nx, nx, VC + (size_t)N * msz, ldx);
-    }
-  }
-  cl.sync();
-  prof_mark(c, PH_R1);
-
   // R2: up-sweep.  Block (d, m) covers leaves [m 2^d, min((m+1) 2^d, n)); the
   // last block of every level contains the terminal leaf and is complete.
   for (int lv = 0; lv < d.nlev; ++lv) {
@@ -480,6 +486,360 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
       __syncthreads();
     }
   }
+  return bad;
+}
+
+// ---------------------------------------------------------------------------
+// Blocked schedule of the reverse scan.
+//
+// The combine of eq. combination_rules with a stage leaf of eq. assoc_init as
+// its left operand, e_ik = (P~_i, A~_i, C~_i = B_i R^_i^-1 B_i^T), and any
+// right operand e_kj = (P_r, A_r, C_r): C~_i has rank nu, so with
+//   Y^T = B_i^T P_r,  G = R^_i + Y^T B_i,  Gamma = G^-1,  H = Gamma Y^T A~_i,
+// the Woodbury identity (I + C~_i P_r)^-1 = I - B_i Gamma Y^T gives
+//   X = (I + C~_i P_r)^-1 A~_i = A~_i - B_i H,
+//   P~_ij = P~_i + A~_i^T P_r X = P~_i + X^T P_r X + H^T R^_i H,
+//   A~_ij = A_r X,
+//   C~_ij = C_r + A_r (I + C~_i P_r)^-1 C~_i A_r^T = C_r + E Gamma E^T,  E = A_r B_i,
+// inverting only the nu x nu block G.  With a complete right operand
+// (P_r = P_{i+1}, A_r = C_r = 0) it is one Riccati step: X = Abar_i and
+// K_i = -(R^_i^-1 S^_i + H) (eq. controller_cache).
+//
+// Schedule over the cluster's chunks [s_r, e_r):
+//   A  chunks 1 .. nch-2 fold their leaves right to left into one element
+//      T_r = e_{s_r} (x) ... (x) e_{e_r - 1}, while the last chunk, whose
+//      suffix is complete from the terminal leaf on, runs its Riccati steps;
+//   B  P_{s_r} = T_r (x) P_{s_{r+1}} for r = nch-2 .. 1, a general combine
+//      with a complete right operand, one CTA after the other;
+//   C  chunks 0 .. nch-2 run their Riccati steps from P_{e_r}.
+// A Riccati step also forms its stage's gains and iteration operators.  The
+// operands live in shared memory (the union region); only the stage inputs
+// are fetched, by cp.async issued at the start of the step.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FactBufs {
+  T *P, *Aa, *Xb, *Bb[2], *Rb[2], *Db[2], *S1, *S2, *S3, *Gm, *Gi, *v;
+  int lds, vlen;
+};
+
+template <typename T>
+__device__ inline FactBufs<T> fact_bufs(Ctx<T>& c) {
+  const QPDesc& d = *c.d;
+  const FactLayout f = fact_layout(d.nx, d.nu, d.nc, d.ldx, d.ldu);
+  T* b = c.ring;
+  FactBufs<T> fb;
+  fb.P = b + f.P;
+  fb.Aa = b + f.Aa;
+  fb.Xb = b + f.Xb;
+  for (int k = 0; k < 2; ++k) {
+    fb.Bb[k] = b + f.Bb[k];
+    fb.Rb[k] = b + f.Rb[k];
+    fb.Db[k] = b + f.Db[k];
+  }
+  fb.S1 = b + f.S1;
+  fb.S2 = b + f.S2;
+  fb.S3 = b + f.S3;
+  fb.Gm = b + f.Gm;
+  fb.Gi = b + f.Gi;
+  fb.v = b + f.vec;
+  fb.lds = f.lds;
+  fb.vlen = f.vlen;
+  return fb;
+}
+
+// cp.async (no wait) of stage i's B_i, R^_i and, for a Riccati step, D_i
+// into buffer set k.
+template <typename T>
+__device__ inline void fact_prefetch(Ctx<T>& c, const FactBufs<T>& fb, int i, int k, bool withD) {
+  const QPDesc& d = *c.d;
+  const int esz = (int)sizeof(T);
+  cta_stage(fb.Bb[k], TP<T>(d.B) + (size_t)i * d.nx * d.ldu, d.nx * d.ldu * esz);
+  cta_stage(fb.Rb[k], TP<T>(d.Rh) + (size_t)i * d.nu * d.ldu, d.nu * d.ldu * esz);
+  if (withD && d.nc > 0) cta_stage(fb.Db[k], TP<T>(d.D) + (size_t)i * d.nc * d.ldu, d.nc * d.ldu * esz);
+}
+
+// n x n (n <= FACT_MAX_NU) SPD inverse by one warp.
+template <typename T>
+__device__ inline int small_spd_inverse(Ctx<T>& c, const T* G, int ldg, int n, T* Gi, int ldgi) {
+  if (n <= 16) return warp_spd_inverse<T, 16>(G, ldg, n, Gi, ldgi, c.flag + 1);
+  return warp_spd_inverse<T, FACT_MAX_NU>(G, ldg, n, Gi, ldgi, c.flag + 1);
+}
+
+// Phase A step: (P, Aa, Cacc) <- e_i (x) (P, Aa, Cacc).  Cacc stays in global
+// memory (it is only ever updated, never a product operand).
+template <typename T>
+__device__ int fact_step_full(Ctx<T>& c, const FactBufs<T>& fb, int i, int k, T* Cacc) {
+  const QPDesc& d = *c.d;
+  const int nx = d.nx, nu = d.nu, ldx = d.ldx, ldu = d.ldu, lds = fb.lds;
+  const int esz = (int)sizeof(T);
+  T *Bb = fb.Bb[k], *Rb = fb.Rb[k];
+  cta_stage_rows(fb.Xb, lds * esz, TP<T>(d.VA) + (size_t)i * c.msz, ldx * esz, nx, ldx * esz);   // A~_i
+  if (i - 1 >= c.s) fact_prefetch<T>(c, fb, i - 1, k ^ 1, false);
+  cp_async_commit();
+  sgemm1<T>(nx, nu, nx, T(1), fb.P, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S1, lds, true);    // Y^T
+  sgemm1<T>(nx, nu, nx, T(1), fb.Aa, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S3, lds, true);   // E^T
+  sgemm1<T>(nu, nu, nx, T(1), fb.S1, lds, false, Bb, ldu, T(1), Rb, ldu, fb.Gm, ldu);             // G
+  const int bad = small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
+  cp_async_wait<0>();
+  __syncthreads();
+  prof_mark(c, PH_FA1);
+  sgemm1<T>(nu, nx, nx, T(1), fb.S1, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.S2, lds);       // Y^T A~_i
+  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S2, lds);       // H
+  sgemm1<T>(nx, nx, nu, T(-1), Bb, ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds);         // X
+  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S3, lds, T(0), nullptr, 0, fb.S1, lds);       // Gamma E^T
+  sgemm1<T>(nx, nx, nu, T(1), fb.S3, lds, true, fb.S1, lds, T(1), Cacc, ldx, Cacc, ldx);          // C~_ij
+  prof_mark(c, PH_FA2);
+  sgemm1<T>(nx, nx, nx, T(1), fb.Aa, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.Aa, lds);       // A~_ij
+  sgemm1<T>(nx, nx, nx, T(1), fb.P, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.P, lds);         // P_r X
+  sgemm1<T>(nu, nx, nu, T(1), Rb, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S1, lds);          // R^ H
+  sgemm<T>(nx, nx, T(1), MTerm<T>{fb.Xb, lds, true, fb.P, lds, nx}, MTerm<T>{fb.S2, lds, true, fb.S1, lds, nu},
+           T(1), TP<T>(d.VP) + (size_t)i * c.msz, ldx, false, fb.P, lds, false);                 // P~_ij
+  prof_mark(c, PH_FA3);
+  return bad;
+}
+
+// Iteration operators of stage i (layouts: see bundle_sizes) from the
+// shared copies of Abar_i (Xb), B_i, D_i, c0_i, k0_i and b_i.
+template <typename T>
+__device__ void fact_bundles(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
+  const QPDesc& d = *c.d;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, ldx = d.ldx, ldu = d.ldu, ldc = d.ldc, ldv = d.ldv, ldf = d.ldf;
+  const int lds = fb.lds, R = nx + nc;
+  int bws, fws, cds;
+  bundle_sizes(nx, nu, nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
+  T* bw = TP<T>(d.BW) + (size_t)i * bws;
+  T* fw = TP<T>(d.FW) + (size_t)i * fws;
+  T* cd = TP<T>(d.CD) + (size_t)i * cds;
+  const T* Ab = fb.Xb;
+  const T* Bb = fb.Bb[k];
+  const T* Db = fb.Db[k];
+  const T* CKi = TP<T>(d.CK) + (size_t)i * nc * ldx;
+  const T* Fi = TP<T>(d.F) + (size_t)i * nu * ldx;
+  const T* Ji = TP<T>(d.J) + (size_t)i * nu * ldc;
+  const T* Ci = TP<T>(d.C) + (size_t)i * nc * ldx;
+  const T* bv = fb.v;
+  const T* c0v = fb.v + 5 * fb.vlen;
+  const T* k0v = fb.v + 6 * fb.vlen;
+  cta_fill<T>(bw, R * ldx, [&](int e2) {
+    const int rr = e2 / ldx, j = e2 - rr * ldx;
+    return (j >= nx) ? T(0) : (rr < nx ? Ab[rr * lds + j] : CKi[(size_t)(rr - nx) * ldx + j]);
+  });
+  T* fjt = bw + (size_t)R * ldx;   // [F | J]^T : row r, column a
+  cta_fill<T>(fjt, R * ldu, [&](int e2) {
+    const int rr = e2 / ldu, a = e2 - rr * ldu;
+    return a >= nu ? T(0) : (rr < nx ? Fi[(size_t)a * ldx + rr] : Ji[(size_t)a * ldc + rr - nx]);
+  });
+  T* c0b = fjt + (size_t)R * ldu;
+  cta_fill<T>(c0b, ldx + ldu, [&](int j) {
+    return j < ldx ? (j < nx ? c0v[j] : T(0)) : (j - ldx < nu ? k0v[j - ldx] : T(0));
+  });
+  // FW^T: row cc < nx+nu (input index), column r < nx+nc (output index)
+  cta_fill<T>(fw, (nx + nu) * ldv, [&](int e2) {
+    const int cc = e2 / ldv, r2 = e2 - cc * ldv;
+    T v = T(0);
+    if (r2 < nx) v = cc < nx ? Ab[r2 * lds + cc] : Bb[r2 * ldu + cc - nx];
+    else if (r2 < R) v = cc < nx ? CKi[(size_t)(r2 - nx) * ldx + cc] : Db[(r2 - nx) * ldu + cc - nx];
+    return v;
+  });
+  cta_fill<T>(fw + (size_t)(nx + nu) * ldv, ldx, [&](int j) { return j < nx ? bv[j] : T(0); });
+  cta_fill<T>(cd, nc * ldf, [&](int e2) {
+    const int rr = e2 / ldf, j = e2 - rr * ldf;
+    return j < nx ? Ci[(size_t)rr * ldx + j] : (j < nx + nu ? Db[rr * ldu + j - nx] : T(0));
+  });
+  __syncthreads();
+}
+
+// Riccati step of stage i from P_{i+1} (in P) to P_i, with the gains and
+// the iteration operators of the stage (eq. controller_cache):
+//   Gamma_i, K_i, Abar_i = X, CK_i = C_i + D_i K_i, F_i = -Gamma_i B_i^T,
+//   J_i = -Gamma_i D_i^T, k0_i = -Gamma_i (B_i^T P_{i+1} b_i + r_i),
+//   c0_i = Abar_i^T P_{i+1} b_i + q_i + K_i^T r_i.
+template <typename T>
+__device__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
+  const QPDesc& d = *c.d;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, ldx = d.ldx, ldu = d.ldu, ldc = d.ldc, lds = fb.lds, msz = c.msz;
+  const int esz = (int)sizeof(T), t = threadIdx.x;
+  T *Bb = fb.Bb[k], *Rb = fb.Rb[k], *Db = fb.Db[k];
+  T *bv = fb.v, *pb = fb.v + fb.vlen, *rv = fb.v + 2 * fb.vlen, *qv = fb.v + 3 * fb.vlen, *tv = fb.v + 4 * fb.vlen;
+  T *c0v = fb.v + 5 * fb.vlen, *k0v = fb.v + 6 * fb.vlen;
+  cta_stage_rows(fb.Xb, lds * esz, TP<T>(d.VA) + (size_t)i * msz, ldx * esz, nx, ldx * esz);    // A~_i
+  cta_stage_rows(fb.S3, lds * esz, TP<T>(d.S0) + (size_t)i * nu * ldx, ldx * esz, nu, ldx * esz);  // R^-1 S^
+  if (i - 1 >= c.s) fact_prefetch<T>(c, fb, i - 1, k ^ 1, true);
+  cp_async_commit();
+  for (int e = t; e < nx; e += NT) {
+    bv[e] = TP<T>(d.b)[(size_t)i * ldx + e];
+    qv[e] = TP<T>(d.q)[(size_t)i * ldx + e];
+  }
+  for (int e = t; e < nu; e += NT) rv[e] = TP<T>(d.r)[(size_t)i * ldu + e];
+  __syncthreads();
+  smem_mvT<T>(fb.P, lds, nx, nx, bv, nullptr, pb, c.red);                                         // P_{i+1} b_i (P symmetric)
+  sgemm1<T>(nx, nu, nx, T(1), fb.P, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S1, lds, true);    // Y^T
+  sgemm1<T>(nu, nu, nx, T(1), fb.S1, lds, false, Bb, ldu, T(1), Rb, ldu, fb.Gm, ldu);             // Gamma^-1
+  const int bad = small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
+  cp_async_wait<0>();
+  __syncthreads();
+  prof_mark(c, PH_FC1);
+  sgemm1<T>(nu, nx, nx, T(1), fb.S1, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.S2, lds);       // Y^T A~_i
+  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S2, lds);       // H
+  sgemm1<T>(nx, nx, nu, T(-1), Bb, ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds);         // Abar_i
+  T* Kg = TP<T>(d.K) + (size_t)i * nu * ldx;
+  for (int e = t; e < nu * nx; e += NT) {
+    const int a = e / nx, j = e - a * nx;
+    const T v = -(fb.S3[a * lds + j] + fb.S2[a * lds + j]);
+    fb.S1[a * lds + j] = v;
+    Kg[(size_t)a * ldx + j] = v;
+  }
+  __syncthreads();
+  smem_mvT<T>(Bb, ldu, nx, nu, pb, rv, tv, c.red);       // B^T P b + r
+  smem_mvT<T>(fb.Xb, lds, nx, nx, pb, qv, c0v, c.red);   // Abar^T P b + q
+  smem_mvT<T>(fb.S1, lds, nu, nx, rv, c0v, c0v, c.red);  // ... + K^T r
+  smem_mv<T>(fb.Gi, ldu, nu, nu, tv, nullptr, k0v);
+  if (t < nu) k0v[t] = -k0v[t];
+  __syncthreads();
+  prof_mark(c, PH_FC2);
+  // P_i = P~_i + X^T (P_{i+1} X) + H^T (R^ H)
+  sgemm1<T>(nx, nx, nx, T(1), fb.P, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.P, lds);
+  sgemm1<T>(nu, nx, nu, T(1), Rb, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S3, lds);
+  sgemm<T>(nx, nx, T(1), MTerm<T>{fb.Xb, lds, true, fb.P, lds, nx}, MTerm<T>{fb.S2, lds, true, fb.S3, lds, nu},
+           T(1), TP<T>(d.VP) + (size_t)i * msz, ldx, false, fb.P, lds, false);
+  prof_mark(c, PH_FC3);
+  // stage outputs
+  cta_copy_vec<T>(nx, nx, fb.P, lds, TP<T>(d.IP) + (size_t)i * msz, ldx);
+  cta_copy_vec<T>(nx, nx, fb.Xb, lds, TP<T>(d.Abar) + (size_t)i * msz, ldx);
+  cta_copy_vec<T>(nu, nu, fb.Gi, ldu, TP<T>(d.Gam) + (size_t)i * nu * ldu, ldu);
+  for (int e = t; e < nx; e += NT) TP<T>(d.c0)[(size_t)i * ldx + e] = c0v[e];
+  for (int e = t; e < nu; e += NT) TP<T>(d.k0)[(size_t)i * ldu + e] = k0v[e];
+  sgemm1<T>(nc, nx, nu, T(1), Db, ldu, false, fb.S1, lds, T(1), TP<T>(d.C) + (size_t)i * nc * ldx, ldx,
+            TP<T>(d.CK) + (size_t)i * nc * ldx, ldx);                                             // CK
+  sgemm1<T>(nx, nu, nu, T(-1), Bb, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, TP<T>(d.F) + (size_t)i * nu * ldx, ldx,
+            true);                                                                                // F = -(B Gamma)^T
+  sgemm1<T>(nc, nu, nu, T(-1), Db, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, TP<T>(d.J) + (size_t)i * nu * ldc, ldc,
+            true);                                                                                // J = -(D Gamma)^T
+  prof_mark(c, PH_FC4);
+  fact_bundles<T>(c, fb, i, k);
+  prof_mark(c, PH_FC5);
+  return bad;
+}
+
+template <typename T>
+__device__ __noinline__ int blocked_scan(Ctx<T>& c, cg::cluster_group& cl) {
+  QPDesc& d = *c.d;
+  const int nx = d.nx, ldx = d.ldx, msz = c.msz, N = d.N, nch = d.nch;
+  const int esz = (int)sizeof(T);
+  T *VP = TP<T>(d.VP), *VA = TP<T>(d.VA), *VC = TP<T>(d.VC), *IP = TP<T>(d.IP);
+  const FactBufs<T> fb = fact_bufs<T>(c);
+  const int lds = fb.lds;
+  const int n = N + 1;   // leaves; chunk elements T_r are kept at tree nodes n + r
+  int bad = 0;
+  if (c.active && c.last) {
+    // A (last chunk): Riccati steps from the terminal leaf, P_N = Q^_N
+    cta_stage_rows(fb.P, lds * esz, VP + (size_t)N * msz, ldx * esz, nx, ldx * esz);
+    fact_prefetch<T>(c, fb, c.e - 1, 0, true);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    cta_copy_vec<T>(nx, nx, fb.P, lds, IP + (size_t)N * msz, ldx);
+    int k = 0;
+    for (int i = c.e - 1; i >= c.s; --i, k ^= 1) bad |= fact_step_riccati<T>(c, fb, i, k);
+  } else if (c.active && c.rank >= 1) {
+    // A: T_r, starting from the chunk's last leaf
+    const int i0 = c.e - 1;
+    T* Cacc = VC + (size_t)(n + c.rank) * msz;
+    cta_stage_rows(fb.P, lds * esz, VP + (size_t)i0 * msz, ldx * esz, nx, ldx * esz);
+    cta_stage_rows(fb.Aa, lds * esz, VA + (size_t)i0 * msz, ldx * esz, nx, ldx * esz);
+    if (i0 - 1 >= c.s) fact_prefetch<T>(c, fb, i0 - 1, 0, false);
+    cp_async_commit();
+    cta_copy_vec<T>(nx, nx, VC + (size_t)i0 * msz, ldx, Cacc, ldx);
+    cp_async_wait<0>();
+    __syncthreads();
+    int k = 0;
+    for (int i = i0 - 1; i >= c.s; --i, k ^= 1) bad |= fact_step_full<T>(c, fb, i, k, Cacc);
+    cta_copy_vec<T>(nx, nx, fb.P, lds, VP + (size_t)(n + c.rank) * msz, ldx);
+    cta_copy_vec<T>(nx, nx, fb.Aa, lds, VA + (size_t)(n + c.rank) * msz, ldx);
+  }
+  cl.sync();
+  prof_mark(c, PH_R2);
+  // B: P_{s_r} = T_r (x) P_{e_r}, r = nch-2 .. 1
+  for (int r = nch - 2; r >= 1; --r) {
+    if (c.rank == r) {
+      const size_t ti = (size_t)(n + r) * msz;
+      bad |= combine_complete<T>(c, VP + ti, VA + ti, VC + ti, IP + (size_t)c.e * msz, IP + (size_t)c.s * msz);
+    }
+    cl.sync();
+  }
+  prof_mark(c, PH_R3);
+  // C: Riccati steps of chunks 0 .. nch-2 from P_{e_r}
+  if (c.active && !c.last) {
+    cta_stage_rows(fb.P, lds * esz, IP + (size_t)c.e * msz, ldx * esz, nx, ldx * esz);
+    fact_prefetch<T>(c, fb, c.e - 1, 0, true);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    int k = 0;
+    for (int i = c.e - 1; i >= c.s; --i, k ^= 1) bad |= fact_step_riccati<T>(c, fb, i, k);
+  }
+  return bad;
+}
+
+// ---------------------------------------------------------------------------
+// rho-dependent factorization (the "refactor")
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
+  QPDesc& d = *c.d;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, N = d.N;
+  const int ldx = d.ldx, ldu = d.ldu, ldc = d.ldc;
+  const int msz = c.msz;
+  const T *A = TP<T>(d.A), *B = TP<T>(d.B), *bb = TP<T>(d.b), *Q = TP<T>(d.Q), *R = TP<T>(d.R), *S = TP<T>(d.S);
+  const T *q = TP<T>(d.q), *r = TP<T>(d.r), *C = TP<T>(d.C), *D = TP<T>(d.D), *CN = TP<T>(d.CN);
+  T *Rhi = TP<T>(d.Rhi), *Sh = TP<T>(d.Sh), *VP = TP<T>(d.VP), *VA = TP<T>(d.VA), *VC = TP<T>(d.VC), *IP = TP<T>(d.IP);
+  T *Abar = TP<T>(d.Abar), *CK = TP<T>(d.CK), *F = TP<T>(d.F), *FPi = TP<T>(d.FPi), *J = TP<T>(d.J), *K = TP<T>(d.K);
+  T *KSig = TP<T>(d.KSig), *CKSig = TP<T>(d.CKSig), *Sig = TP<T>(d.Sig), *c0 = TP<T>(d.c0), *k0 = TP<T>(d.k0);
+  T *CNSig = TP<T>(d.CNSig), *SigN = TP<T>(d.SigN), *Tch = TP<T>(d.Tch), *Uch = TP<T>(d.Uch);
+  T *Theta = TP<T>(d.Theta), *Xi = TP<T>(d.Xi), *Gam = TP<T>(d.Gam);
+  T* s1 = c.scr + 5 * msz;   // small temporary (nx x nu)
+  T *Rh = TP<T>(d.Rh), *S0 = TP<T>(d.S0);
+  int bad = 0;
+
+  // R1: leaves (eq. assoc_init) for own stages, terminal by the last chunk.
+  if (c.active) {
+    for (int i = c.s; i < c.e; ++i) {
+      const T* Ai = A + (size_t)i * msz;
+      const T* Bi = B + (size_t)i * nx * ldu;
+      const T* Ci = C + (size_t)i * nc * ldx;
+      const T* Di = D + (size_t)i * nc * ldu;
+      T* Pl = VP + (size_t)i * msz;
+      T* Al = VA + (size_t)i * msz;
+      T* Cl = VC + (size_t)i * msz;
+      T* Shi = Sh + (size_t)i * nu * ldx;
+      T* Rhii = Rhi + (size_t)i * nu * ldu;
+      // Q^ = Q + rho C^T C,  R^ = R + rho D^T D,  S^ = S + rho D^T C
+      cta_gemm<T>(nx, nx, nc, rho, Ci, ldx, true, Ci, ldx, false, T(1), Q + (size_t)i * msz, ldx, false, Pl, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nu, nu, nc, rho, Di, ldu, true, Di, ldu, false, T(1), R + (size_t)i * nu * ldu, ldu, false, c.gj, GJ_LD, c.gemm, c.tc);
+      cta_copy<T>(nu, nu, c.gj, GJ_LD, false, Rh + (size_t)i * nu * ldu, ldu);   // R^ kept for the blocked scan
+      cta_gemm<T>(nu, nx, nc, rho, Di, ldu, true, Ci, ldx, false, T(1), S + (size_t)i * nu * ldx, ldx, false, Shi, ldx, c.gemm, c.tc);
+      bad |= cta_inverse<T>(c.gj, GJ_LD, nu, false, Rhii, ldu, c.gemm, c.perm, c.flag);
+      // s0 = R^-1 S^ (kept: K_i = -(s0 + H_i) in the blocked scan) ; P~ = Q^ - S^^T s0 ;
+      // A~ = A - B s0 ; s1 = B R^-1 ; C~ = s1 B^T
+      T* s0 = S0 + (size_t)i * nu * ldx;
+      cta_gemm<T>(nu, nx, nu, T(1), Rhii, ldu, false, Shi, ldx, false, T(0), nullptr, 0, false, s0, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nx, nx, nu, T(-1), Shi, ldx, true, s0, ldx, false, T(1), Pl, ldx, false, Pl, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nx, nx, nu, T(-1), Bi, ldu, false, s0, ldx, false, T(1), Ai, ldx, false, Al, ldx, c.gemm, c.tc);
+      cta_gemm<T>(nx, nu, nu, T(1), Bi, ldu, false, Rhii, ldu, false, T(0), nullptr, 0, false, s1, ldu, c.gemm, c.tc);
+      cta_gemm<T>(nx, nx, nu, T(1), s1, ldu, false, Bi, ldu, true, T(0), nullptr, 0, false, Cl, ldx, c.gemm, c.tc);
+    }
+    if (c.last) {
+      T* Pl = VP + (size_t)N * msz;
+      cta_gemm<T>(nx, nx, nf, rho, CN, ldx, true, CN, ldx, false, T(1), Q + (size_t)N * msz, ldx, false, Pl, ldx, c.gemm, c.tc);
+      cta_zero<T>(nx, nx, VA + (size_t)N * msz, ldx);
+      cta_zero<T>(nx, nx, VC + (size_t)N * msz, ldx);
+    }
+  }
+  cl.sync();
+  prof_mark(c, PH_R1);
+
+  if (d.fact == 0) bad |= blocked_scan<T>(c, cl);
+  else bad |= tree_scan<T>(c, cl, rho);
   cl.sync();
   prof_mark(c, PH_R4);
   // R5: chunk products.  Backward (not needed in the last chunk):

@@ -39,7 +39,7 @@ class qp_settings(C.Structure):
                 ("max_iter", C.c_int32), ("precision", C.c_int32), ("cluster", C.c_int32),
                 ("fixed_iters", C.c_int32), ("max_refine", C.c_int32), ("fallback_iters", C.c_int32),
                 ("occupancy", C.c_int32), ("eps_floor", C.c_double), ("schedule", C.c_int32),
-                ("pad2", C.c_int32)]
+                ("factorization", C.c_int32)]
 
 
 class qp_info(C.Structure):

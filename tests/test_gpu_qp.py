@@ -35,15 +35,18 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("fact", [0, 1])
 @pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32])
 @pytest.mark.parametrize("cluster", [1, 3, 8])
 @pytest.mark.parametrize("name,make", CASES)
-def test_riccati_matches_oracle(lib, name, make, cluster, prec):
-    """The tree-scan refactor (eq. assoc_init, eq. combination_rules,
-    eq. controller_cache) gives the sequential Riccati P_i and K_i."""
+def test_riccati_matches_oracle(lib, name, make, cluster, prec, fact):
+    """The refactor (eq. assoc_init, eq. combination_rules, eq.
+    controller_cache) gives the sequential Riccati P_i and K_i, with the
+    blocked schedule (fact 0: leaf-structured combines, chunk elements
+    combined across the cluster) and with the tree (fact 1)."""
     qp = make()
     rho = 0.7
-    b = batch([qp], precision=prec, cluster=cluster, rho=rho)
+    b = batch([qp], precision=prec, cluster=cluster, rho=rho, factorization=fact)
     Ps, Ks = b.riccati()
     Qh, Rh, Sh = lq.augmented(qp, rho)
     P, p, K, kff, G = lq.riccati(qp.A, qp.B, qp.c, Qh, Rh, Sh, np.zeros_like(qp.q), np.zeros_like(qp.r))

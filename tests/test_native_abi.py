@@ -37,7 +37,7 @@ def test_default_settings_fill_every_field(libpath):
     s = native.qp_settings()
     ctypes.memset(ctypes.byref(s), 0xA5, ctypes.sizeof(s))
     native.load().qp_default_settings(ctypes.byref(s))
-    assert s.occupancy == 0 and s.schedule == 0 and s.pad2 == 0 and s.eps_floor == 0.0
+    assert s.occupancy == 0 and s.schedule == 0 and s.factorization == 0 and s.eps_floor == 0.0
     assert s.cluster == 0 and s.fixed_iters == 0 and s.fallback_iters == 0
 
 
