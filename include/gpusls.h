@@ -78,7 +78,10 @@ typedef struct qp_settings {
   double eps_floor;   /* the KKT gate divides eps by 10 on failure, not below this
                          (0, the default: 1e-7 for GPUSLS_FP64, 1e-5 for GPUSLS_FP32);
                          at the floor a failing KKT check triggers a refinement:
-                         r <- r + (FP64 u-stationarity residual)                   */
+                         r <- r + (FP64 u-stationarity residual).  FP32 solves
+                         also run the check after 250 iterations at the floor
+                         whose residuals stay above it (FP32 rounding can hold
+                         them there)                                              */
   int32_t schedule;   /* launch order of the QPs of a batch: 0 (default) in index
                          order; 1 longest expected first, the expectation being
                          each QP's own previous solve on this handle (iterations +

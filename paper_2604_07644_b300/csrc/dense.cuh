@@ -460,9 +460,11 @@ __device__ __forceinline__ void mk_mac(int m, int n, const MTerm<T>& p, T (&acc)
   }
 }
 
+// Each shape is its own (non-inlined) function so that its registers are
+// allocated for it alone.
 template <typename T, int GX, int RA, int RB>
-__device__ __forceinline__ void sgemm_vec(int m, int n, T alpha, const MTerm<T>& p1, const MTerm<T>& p2, T beta,
-                                          const T* C0, int ldc0, bool addI, T* C, int ldc, bool tC) {
+__device__ __noinline__ void sgemm_vec(int m, int n, T alpha, const MTerm<T>& p1, const MTerm<T>& p2, T beta,
+                                       const T* C0, int ldc0, bool addI, T* C, int ldc, bool tC) {
   constexpr int GY = NT / GX;
   constexpr bool PRE = RA * RB <= 4;   // C0 prefetched into registers when they allow
   const int ty = threadIdx.x / GX, tx = threadIdx.x % GX;
@@ -525,51 +527,10 @@ __device__ __forceinline__ void sgemm_vec(int m, int n, T alpha, const MTerm<T>&
   __syncthreads();
 }
 
+// Scalar register-tile path for operands that are not 16-byte aligned.
 template <typename T>
-__device__ inline bool mterm_vec_ok(const MTerm<T>& p) {
-  return p.k == 0 || ((((reinterpret_cast<uintptr_t>(p.A) | reinterpret_cast<uintptr_t>(p.B)) & 15) == 0) &&
-                      ((p.lda | p.ldb) & 3) == 0);
-}
-
-// C = alpha (op(A1) B1 + op(A2) B2) + beta C0 (+ I if addI), m, n <= 80; the
-// second term is skipped when p2.k == 0.  tC: C is written transposed
-// (C[j][i]).  C0 (shared or global) is read before the products when the
-// registers allow, so its global-memory latency overlaps them.  Ends with a
-// CTA barrier.  Operands that are not 16-byte aligned take a scalar path.
-template <typename T>
-__device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> p2, T beta, const T* C0, int ldc0,
-                                   bool addI, T* C, int ldc, bool tC) {
-  if (m <= 0 || n <= 0) {
-    __syncthreads();
-    return;
-  }
-  if (mterm_vec_ok(p1) && mterm_vec_ok(p2)) {
-    if (n <= 16) {
-      // narrow outputs: 64 x 4 grid, one column group per thread
-      if (m <= 64) sgemm_vec<T, 4, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
-      else sgemm_vec<T, 4, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
-    } else {
-      const int ra = (m + 15) >> 4;
-      if (n <= 64) {
-        switch (ra) {
-          case 1: sgemm_vec<T, 16, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          case 2: sgemm_vec<T, 16, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          case 3: sgemm_vec<T, 16, 3, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          case 4: sgemm_vec<T, 16, 4, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          default: sgemm_vec<T, 16, 5, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-        }
-      } else {
-        switch (ra) {
-          case 1: sgemm_vec<T, 16, 1, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          case 2: sgemm_vec<T, 16, 2, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          case 3: sgemm_vec<T, 16, 3, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          case 4: sgemm_vec<T, 16, 4, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          default: sgemm_vec<T, 16, 5, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-        }
-      }
-    }
-    return;
-  }
+__device__ __noinline__ void sgemm_scalar(int m, int n, T alpha, const MTerm<T>& p1, const MTerm<T>& p2, T beta,
+                                          const T* C0, int ldc0, bool addI, T* C, int ldc, bool tC) {
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   T acc[5][5];
 #pragma unroll
@@ -598,6 +559,58 @@ __device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> 
       }
     }
   __syncthreads();
+}
+
+template <typename T>
+__device__ inline bool mterm_vec_ok(const MTerm<T>& p) {
+  return p.k == 0 || ((((reinterpret_cast<uintptr_t>(p.A) | reinterpret_cast<uintptr_t>(p.B)) & 15) == 0) &&
+                      ((p.lda | p.ldb) & 3) == 0);
+}
+
+// C = alpha (op(A1) B1 + op(A2) B2) + beta C0 (+ I if addI), m, n <= 80; the
+// second term is skipped when p2.k == 0.  tC: C is written transposed
+// (C[j][i]).  C0 (shared or global) is read before the products when the
+// registers allow, so its global-memory latency overlaps them.  Ends with a
+// CTA barrier.  Operands that are not 16-byte aligned take a scalar path.
+template <typename T>
+__device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> p2, T beta, const T* C0, int ldc0,
+                                   bool addI, T* C, int ldc, bool tC) {
+  if (m <= 0 || n <= 0) {
+    __syncthreads();
+    return;
+  }
+  // FP64 products run at the FP64 FMA rate whatever the loads, so FP64 keeps
+  // the scalar path (and the vector shapes are instantiated for FP32 only)
+  if constexpr (sizeof(T) == 4) {
+    if (mterm_vec_ok(p1) && mterm_vec_ok(p2)) {
+      if (n <= 16) {
+        // narrow outputs: 64 x 4 grid, one column group per thread
+        if (m <= 64) sgemm_vec<T, 4, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+        else sgemm_vec<T, 4, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+      } else {
+        const int ra = (m + 15) >> 4;
+        if (n <= 64) {
+          switch (ra) {
+            case 1: sgemm_vec<T, 16, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+            case 2: sgemm_vec<T, 16, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+            case 3: sgemm_vec<T, 16, 3, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+            case 4: sgemm_vec<T, 16, 4, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+            default: sgemm_vec<T, 16, 5, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          }
+        } else {
+          switch (ra) {
+            case 1: sgemm_vec<T, 16, 1, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+            case 2: sgemm_vec<T, 16, 2, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+            case 3: sgemm_vec<T, 16, 3, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+            case 4: sgemm_vec<T, 16, 4, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+            default: sgemm_vec<T, 16, 5, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          }
+        }
+      }
+      return;
+    }
+  }
+  sgemm_scalar<T>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
 }
 
 // One-term convenience form.
@@ -632,7 +645,7 @@ __device__ void cta_copy_vec(int m, int n, const T* X, int ldxs, T* Y, int ldy) 
 // Returns 1 in every thread (after the closing barrier) if a pivot was not
 // positive.  flag: shared int.
 template <typename T, int CAP>
-__device__ int warp_spd_inverse(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag) {
+__device__ __noinline__ int warp_spd_inverse(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag) {
   if (threadIdx.x < 32) {
     const int l = threadIdx.x;
     T a[CAP], b[CAP];

@@ -17,252 +17,12 @@
 
 namespace gsls {
 
-// ---------------------------------------------------------------------------
-// the solve kernel
-// ---------------------------------------------------------------------------
-// FP32 solves fit two CTAs per SM (<= 128 registers, ~100 KB shared), which
-// lets one cluster's barrier and latency stalls overlap another's work.
-template <typename T> struct KernelOcc { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
-
+// The solve kernel lives in qp_kernel_f32.cu / qp_kernel_f64.cu.
 template <typename T>
-__global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDesc* __restrict__ descs, SolveArgs args) {
-  cg::cluster_group cl = cg::this_cluster();
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ QPDesc dsh;
-  const int cs = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
-  const int qi = args.order ? args.order[blockIdx.x / cs] : (int)(blockIdx.x / cs);
-  if (threadIdx.x == 0) dsh = descs[qi];
-  __syncthreads();
-  QPDesc& d = dsh;
-
-  const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.nch, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
-                                     (int)sizeof(T), d.fact);
-  Ctx<T> c;
-  c.d = &d;
-  c.rank = rank;
-  c.cs = cs;
-  c.s = min(rank * d.Lc, d.N);
-  c.e = min((rank + 1) * d.Lc, d.N);
-  c.L = c.e - c.s;
-  c.active = rank < d.nch;
-  c.first = rank == 0;
-  c.last = rank == d.nch - 1;
-  c.gemm = reinterpret_cast<T*>(smem + lay.gemm);
-  c.gj = reinterpret_cast<T*>(smem + lay.gj);
-  c.gjbuf = reinterpret_cast<T*>(smem + lay.gjbuf);
-  c.ring = reinterpret_cast<T*>(smem + lay.ring);
-  c.zS = reinterpret_cast<T*>(smem + lay.z);
-  c.yS = reinterpret_cast<T*>(smem + lay.y);
-  c.wS = reinterpret_cast<T*>(smem + lay.w);
-  c.lS = reinterpret_cast<T*>(smem + lay.l);
-  c.xS = reinterpret_cast<T*>(smem + lay.x);
-  c.ktS = reinterpret_cast<T*>(smem + lay.kt);
-  c.vS = reinterpret_cast<T*>(smem + lay.v);
-  c.dS = reinterpret_cast<T*>(smem + lay.d);
-  c.uS = reinterpret_cast<T*>(smem + lay.u);
-  c.pe = reinterpret_cast<T*>(smem + lay.pe);
-  c.xs = reinterpret_cast<T*>(smem + lay.xs);
-  c.slotL = reinterpret_cast<T*>(smem + lay.slotL);
-  c.slotX = reinterpret_cast<T*>(smem + lay.slotX);
-  c.tmp1 = reinterpret_cast<T*>(smem + lay.tmp1);
-  c.tmp2 = reinterpret_cast<T*>(smem + lay.tmp2);
-  c.tmp3 = reinterpret_cast<T*>(smem + lay.tmp3);
-  c.red = reinterpret_cast<T*>(smem + lay.red);
-  c.part = reinterpret_cast<double*>(smem + lay.part);
-  c.perm = reinterpret_cast<int*>(smem + lay.perm);
-  c.flag = reinterpret_cast<int*>(smem + lay.flag);
-  c.bar = reinterpret_cast<unsigned long long*>(smem + lay.bar);
-  c.swp = reinterpret_cast<T*>(smem + lay.swp);
-  c.gath = reinterpret_cast<T*>(smem + lay.gath);
-  c.ws = c.wp = 0;
-  c.inflight = c.ipar = 0;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < d.depth; ++k) mbar_init(&c.bar[k], 1);
-    mbar_init_fence();
-    c.flag[RING_FLAG] = 0;
-  }
-  __syncthreads();
-  c.msz = d.nx * d.ldx;
-  c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
-  const int t = threadIdx.x;
-  c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
-  c.t_last = clock64();
-  c.tc = args.tc != 0;
-
-  if (args.mode == MODE_KKT) {
-    const double kkt = kkt_eval<T>(c, cl);
-    if (rank == 0 && t == 0) d.info_d[3] = kkt;
-    return;
-  }
-
-  T rho = (T)d.rho[0];
-  int refactors = 0;
-  int status = GPUSLS_MAX_ITER;
-  if (args.mode == MODE_RICCATI || d.flags[0] == 0) {
-    const int bad = refactor<T>(c, cl, rho);
-    ++refactors;
-    if (bad) status = GPUSLS_ERR_NOT_SPD;
-  }
-  if (args.mode == MODE_RICCATI) {
-    // P_i = level-0 inclusive suffixes, K_i gains, as FP64 dense blocks.
-    const int nx = d.nx, nu = d.nu, ldx = d.ldx, msz = c.msz;
-    if (c.active && d.ox && d.ou) {
-      const int iend = c.e + (c.last ? 1 : 0);
-      for (int i = c.s; i < iend; ++i)
-        for (int e2 = t; e2 < nx * nx; e2 += NT)
-          d.ox[(size_t)i * nx * nx + e2] = (double)TP<T>(d.IP)[(size_t)i * msz + (e2 / nx) * ldx + e2 % nx];
-      for (int i = c.s; i < c.e; ++i)
-        for (int e2 = t; e2 < nu * nx; e2 += NT)
-          d.ou[(size_t)i * nu * nx + e2] = (double)TP<T>(d.K)[(size_t)i * nu * ldx + (e2 / nx) * ldx + e2 % nx];
-    }
-    if (rank == 0 && t == 0) {
-      d.info_i[0] = status == GPUSLS_ERR_NOT_SPD ? status : GPUSLS_OK;
-      d.info_i[2] = refactors;
-      d.flags[0] = status == GPUSLS_ERR_NOT_SPD ? 0 : 1;
-    }
-    return;
-  }
-
-  // load the ADMM state of own rows
-  const int nrows = own_rows(c);
-  const T* zg = TP<T>(d.z);
-  const T* yg = TP<T>(d.y);
-  for (int e2 = t; e2 < nrows; e2 += NT) {
-    c.zS[e2] = zg[(size_t)c.s * d.nc + e2];
-    c.yS[e2] = yg[(size_t)c.s * d.nc + e2];
-  }
-  __syncthreads();
-
-  double eps = args.eps;
-  const bool fixed = args.fixed_iters > 0;
-  const int max_it = fixed ? args.fixed_iters : args.max_iter;
-  double rp = INFINITY, rd = INFINITY, kkt = -1.0;
-  int it = 0;
-  int refines = 0;
-  bool warm = d.flags[1] != 0;
-  const int it_warm0 = 0;
-  int fell_back = 0;
-  if (status != GPUSLS_ERR_NOT_SPD) {
-    for (it = 1; it <= max_it; ++it) {
-      const bool stop_iter = !fixed && (it % args.check_every == 0);
-      const bool rho_iter = !fixed && args.sigma > 0 && (it % args.sigma == 0);
-      const bool check = stop_iter || rho_iter || (it == max_it);
-      Partials pl;
-      admm_iteration<T>(c, cl, rho, check, pl);
-      if (!check) continue;
-      double v[5] = {pl.rp, pl.rd, pl.vm, pl.zm, c.flag[RING_FLAG] ? 1.0 : 0.0};
-      cluster_max(c, cl, v, 5);
-      prof_mark(c, PH_CHECK);
-      rp = v[0];
-      rd = v[1];
-      if (v[4] > 0.0) {
-        status = GPUSLS_ERR_TIMEOUT;
-        break;
-      }
-      if (!(isfinite(rp) && isfinite(rd))) {
-        status = GPUSLS_ERR_NAN;
-        break;
-      }
-      if (stop_iter && rp <= eps && rd <= eps) {
-        if (args.eps_kkt <= 0.0) {
-          status = GPUSLS_OK;
-          break;
-        }
-        full_xu<T>(c);
-        write_outputs<T>(c, rho);
-        kkt = kkt_eval<T>(c, cl);
-        prof_mark(c, PH_KKT);
-        if (kkt <= args.eps_kkt) {
-          status = GPUSLS_OK;
-          break;
-        }
-        if (eps > args.eps_floor) {
-          eps = fmax(eps * 0.1, args.eps_floor);
-        } else if (refines < args.max_refine) {
-          refine_linear_term<T>(c);
-          ++refines;
-        }
-      }
-      if (warm && args.fallback_iters > 0 && it - it_warm0 >= args.fallback_iters) {
-        // cold-start fallback of a warm start that did not converge in time
-        for (int e2 = t; e2 < nrows; e2 += NT) {
-          c.zS[e2] = T(0);
-          c.yS[e2] = T(0);
-        }
-        warm = false;
-        fell_back = 1;
-        eps = args.eps;
-        const T rho_c = (T)d.rho0[0];
-        __syncthreads();
-        if (rho_c != rho) {
-          rho = rho_c;
-          const int bad = refactor<T>(c, cl, rho);
-          ++refactors;
-          if (bad) {
-            status = GPUSLS_ERR_NOT_SPD;
-            break;
-          }
-        }
-        continue;
-      }
-      if (rho_iter) {
-        full_xu<T>(c);
-        double hm, gm, qm;
-        rho_rule_partials<T>(c, rho, hm, gm, qm);
-        double u[3] = {hm, gm, qm};
-        cluster_max(c, cl, u, 3);
-        prof_mark(c, PH_RHO);
-        const double prim_scale = fmax(v[2], v[3]);
-        const double dual_scale = fmax(fmax(u[0], u[1]), u[2]);
-        double rho_new = (double)rho;
-        if (rp > 0.0 && rd > 0.0 && prim_scale > 0.0 && dual_scale > 0.0) {
-          const double ratio = (rp / prim_scale) / (rd / dual_scale);
-          rho_new = fmin(fmax((double)rho * sqrt(ratio), args.rho_min), args.rho_max);
-        }
-        if (rho_new > 5.0 * (double)rho || rho_new < (double)rho / 5.0) {
-          const T scale = (T)((double)rho / rho_new);
-          for (int e2 = t; e2 < nrows; e2 += NT) c.yS[e2] *= scale;
-          rho = (T)rho_new;
-          __syncthreads();
-          const int bad = refactor<T>(c, cl, rho);
-          ++refactors;
-          if (bad) {
-            status = GPUSLS_ERR_NOT_SPD;
-            break;
-          }
-        }
-      }
-    }
-    if (it > max_it) it = max_it;
-    full_xu<T>(c);
-    write_outputs<T>(c, rho);
-    if (status == GPUSLS_OK && args.eps_kkt <= 0.0) kkt = -1.0;
-  }
-  // store state
-  T* zw = TP<T>(d.z);
-  T* yw = TP<T>(d.y);
-  for (int e2 = t; e2 < nrows; e2 += NT) {
-    zw[(size_t)c.s * d.nc + e2] = c.zS[e2];
-    yw[(size_t)c.s * d.nc + e2] = c.yS[e2];
-  }
-  if (rank == 0 && t == 0) {
-    d.info_i[0] = status;
-    d.info_i[1] = it;
-    d.info_i[2] = refactors;
-    d.info_i[3] = refines;
-    d.info_i[4] = fell_back;
-    d.info_d[0] = (double)rho;
-    d.info_d[1] = rp;
-    d.info_d[2] = rd;
-    d.info_d[3] = kkt;
-    d.rho[0] = (double)rho;
-    d.flags[0] = (status == GPUSLS_ERR_NOT_SPD) ? 0 : 1;
-    d.flags[1] = 0;
-    d.flags[2] = fell_back;
-  }
-  ring_drain<T>(c);
-}
+const void* qp_kernel_entry();
+template <> const void* qp_kernel_entry<float>();
+template <> const void* qp_kernel_entry<double>();
+using QPKernelFn = void (*)(const QPDesc*, SolveArgs);
 
 // ---------------------------------------------------------------------------
 // launch order for the next solve: longest expected first
@@ -362,7 +122,7 @@ static int auto_cluster(int N) {
 
 template <typename T>
 static int launch_qp(qp_handle* h, const SolveArgs& a) {
-  auto kern = qp_kernel<T>;
+  const QPKernelFn kern = reinterpret_cast<QPKernelFn>(const_cast<void*>(qp_kernel_entry<T>()));
   int smem = h->smem;
   // occupancy 1: ask for more than half of the SM's shared memory, so that
   // exactly one CTA of this kernel fits an SM
@@ -846,8 +606,8 @@ extern "C" int qp_graph_create(qp_graph** out, qp_handle* h, mlp_handle* m, cons
   {
     const int smem = h->set.occupancy == 1 ? std::max(h->smem, 116 * 1024) : h->smem;
     const cudaError_t e = h->esz == 8
-        ? cudaFuncSetAttribute(qp_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-        : cudaFuncSetAttribute(qp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        ? cudaFuncSetAttribute(qp_kernel_entry<double>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+        : cudaFuncSetAttribute(qp_kernel_entry<float>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return bail(GPUSLS_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
   }
   const cudaStream_t saved = h->stream;

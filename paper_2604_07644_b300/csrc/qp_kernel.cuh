@@ -117,18 +117,18 @@ __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 struct FactLayout {
   int lds;   // row pitch of the nx-column buffers (ldx, or ldx + 4 when ldx is a multiple of 32: no bank conflicts
              // between the two rows a warp reads)
-  int P, Aa, Xb, Bb[2], Rb[2], Db[2], S1, S2, S3, Gm, Gi, vec;
+  int P, Aa, Xb, Bb[2], Rb[2], Db[2], S1, S2, S3, Gm, Gi, BG, CKb[2], JT, vec;
   int vlen;  // length of each of the 8 vectors at vec
   int total;
 };
 
-__host__ __device__ inline FactLayout fact_layout(int nx, int nu, int nc, int ldx, int ldu) {
+__host__ __device__ inline FactLayout fact_layout(int nx, int nu, int nc, int nf, int ldx, int ldu) {
   FactLayout f;
   f.lds = (ldx % 32 == 0) ? ldx + 4 : ldx;
   f.vlen = rup4(nx > nu ? nx : nu);
   int off = 0;
   const int big = rup4(nx * f.lds), bsz = rup4(nx * ldu), rsz = rup4(nu * ldu), dsz = rup4(nc * ldu),
-            ssz = rup4(nu * f.lds);
+            ssz = rup4(nu * f.lds), csz = rup4((nc > nf ? nc : nf) * f.lds);
   f.P = off; off += big;
   f.Aa = off; off += big;
   f.Xb = off; off += big;
@@ -140,6 +140,9 @@ __host__ __device__ inline FactLayout fact_layout(int nx, int nu, int nc, int ld
   f.S3 = off; off += ssz;
   f.Gm = off; off += rsz;
   f.Gi = off; off += rsz;
+  f.BG = off; off += bsz;
+  for (int k = 0; k < 2; ++k) { f.CKb[k] = off; off += csz; }
+  f.JT = off; off += dsz;
   f.vec = off; off += 8 * f.vlen;
   f.total = off;
   return f;
@@ -155,7 +158,7 @@ __host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf
   int off = 0;
   const int ring_b = depth * slot * esz;
   const int dense_b = (2 * KT * TILE + TILE * GJ_LD + 3 * TILE) * esz;
-  const int fact_b = fact == 0 ? fact_layout(nx, nu, nc, ldx, ldu).total * esz : 0;
+  const int fact_b = fact == 0 ? fact_layout(nx, nu, nc, nf, ldx, ldu).total * esz : 0;
   int uni = ring_b > dense_b ? ring_b : dense_b;
   uni = uni > fact_b ? uni : fact_b;
   s.ring = 0;
@@ -518,14 +521,14 @@ __device__ __noinline__ int tree_scan(Ctx<T>& c, cg::cluster_group& cl, T rho) {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct FactBufs {
-  T *P, *Aa, *Xb, *Bb[2], *Rb[2], *Db[2], *S1, *S2, *S3, *Gm, *Gi, *v;
+  T *P, *Aa, *Xb, *Bb[2], *Rb[2], *Db[2], *S1, *S2, *S3, *Gm, *Gi, *BG, *CKb[2], *JT, *v;
   int lds, vlen;
 };
 
 template <typename T>
 __device__ inline FactBufs<T> fact_bufs(Ctx<T>& c) {
   const QPDesc& d = *c.d;
-  const FactLayout f = fact_layout(d.nx, d.nu, d.nc, d.ldx, d.ldu);
+  const FactLayout f = fact_layout(d.nx, d.nu, d.nc, d.nf, d.ldx, d.ldu);
   T* b = c.ring;
   FactBufs<T> fb;
   fb.P = b + f.P;
@@ -541,6 +544,10 @@ __device__ inline FactBufs<T> fact_bufs(Ctx<T>& c) {
   fb.S3 = b + f.S3;
   fb.Gm = b + f.Gm;
   fb.Gi = b + f.Gi;
+  fb.BG = b + f.BG;
+  fb.CKb[0] = b + f.CKb[0];
+  fb.CKb[1] = b + f.CKb[1];
+  fb.JT = b + f.JT;
   fb.v = b + f.vec;
   fb.lds = f.lds;
   fb.vlen = f.vlen;
@@ -568,7 +575,7 @@ __device__ inline int small_spd_inverse(Ctx<T>& c, const T* G, int ldg, int n, T
 // Phase A step: (P, Aa, Cacc) <- e_i (x) (P, Aa, Cacc).  Cacc stays in global
 // memory (it is only ever updated, never a product operand).
 template <typename T>
-__device__ int fact_step_full(Ctx<T>& c, const FactBufs<T>& fb, int i, int k, T* Cacc) {
+__device__ __noinline__ int fact_step_full(Ctx<T>& c, const FactBufs<T>& fb, int i, int k, T* Cacc) {
   const QPDesc& d = *c.d;
   const int nx = d.nx, nu = d.nu, ldx = d.ldx, ldu = d.ldu, lds = fb.lds;
   const int esz = (int)sizeof(T);
@@ -599,11 +606,12 @@ __device__ int fact_step_full(Ctx<T>& c, const FactBufs<T>& fb, int i, int k, T*
 }
 
 // Iteration operators of stage i (layouts: see bundle_sizes) from the
-// shared copies of Abar_i (Xb), B_i, D_i, c0_i, k0_i and b_i.
+// shared copies of Abar_i (Xb), B_i, D_i, CK_i, -B_i Gamma_i (= F_i^T),
+// -D_i Gamma_i (= J_i^T), c0_i, k0_i and b_i; C_i from global memory.
 template <typename T>
-__device__ void fact_bundles(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
+__device__ __noinline__ void fact_bundles(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
   const QPDesc& d = *c.d;
-  const int nx = d.nx, nu = d.nu, nc = d.nc, ldx = d.ldx, ldu = d.ldu, ldc = d.ldc, ldv = d.ldv, ldf = d.ldf;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, ldx = d.ldx, ldu = d.ldu, ldv = d.ldv, ldf = d.ldf;
   const int lds = fb.lds, R = nx + nc;
   int bws, fws, cds;
   bundle_sizes(nx, nu, nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
@@ -613,21 +621,21 @@ __device__ void fact_bundles(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
   const T* Ab = fb.Xb;
   const T* Bb = fb.Bb[k];
   const T* Db = fb.Db[k];
-  const T* CKi = TP<T>(d.CK) + (size_t)i * nc * ldx;
-  const T* Fi = TP<T>(d.F) + (size_t)i * nu * ldx;
-  const T* Ji = TP<T>(d.J) + (size_t)i * nu * ldc;
+  const T* CKs = fb.CKb[0];
+  const T* BG = fb.BG;
+  const T* JT = fb.JT;
   const T* Ci = TP<T>(d.C) + (size_t)i * nc * ldx;
   const T* bv = fb.v;
   const T* c0v = fb.v + 5 * fb.vlen;
   const T* k0v = fb.v + 6 * fb.vlen;
   cta_fill<T>(bw, R * ldx, [&](int e2) {
     const int rr = e2 / ldx, j = e2 - rr * ldx;
-    return (j >= nx) ? T(0) : (rr < nx ? Ab[rr * lds + j] : CKi[(size_t)(rr - nx) * ldx + j]);
+    return (j >= nx) ? T(0) : (rr < nx ? Ab[rr * lds + j] : CKs[(rr - nx) * lds + j]);
   });
   T* fjt = bw + (size_t)R * ldx;   // [F | J]^T : row r, column a
   cta_fill<T>(fjt, R * ldu, [&](int e2) {
     const int rr = e2 / ldu, a = e2 - rr * ldu;
-    return a >= nu ? T(0) : (rr < nx ? Fi[(size_t)a * ldx + rr] : Ji[(size_t)a * ldc + rr - nx]);
+    return a >= nu ? T(0) : (rr < nx ? BG[rr * ldu + a] : JT[(rr - nx) * ldu + a]);
   });
   T* c0b = fjt + (size_t)R * ldu;
   cta_fill<T>(c0b, ldx + ldu, [&](int j) {
@@ -638,7 +646,7 @@ __device__ void fact_bundles(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
     const int cc = e2 / ldv, r2 = e2 - cc * ldv;
     T v = T(0);
     if (r2 < nx) v = cc < nx ? Ab[r2 * lds + cc] : Bb[r2 * ldu + cc - nx];
-    else if (r2 < R) v = cc < nx ? CKi[(size_t)(r2 - nx) * ldx + cc] : Db[(r2 - nx) * ldu + cc - nx];
+    else if (r2 < R) v = cc < nx ? CKs[(r2 - nx) * lds + cc] : Db[(r2 - nx) * ldu + cc - nx];
     return v;
   });
   cta_fill<T>(fw + (size_t)(nx + nu) * ldv, ldx, [&](int j) { return j < nx ? bv[j] : T(0); });
@@ -653,9 +661,11 @@ __device__ void fact_bundles(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
 // the iteration operators of the stage (eq. controller_cache):
 //   Gamma_i, K_i, Abar_i = X, CK_i = C_i + D_i K_i, F_i = -Gamma_i B_i^T,
 //   J_i = -Gamma_i D_i^T, k0_i = -Gamma_i (B_i^T P_{i+1} b_i + r_i),
-//   c0_i = Abar_i^T P_{i+1} b_i + q_i + K_i^T r_i.
+//   c0_i = Abar_i^T P_{i+1} b_i + q_i + K_i^T r_i,
+// and, outside the last chunk, the backward chunk products with
+// Pi_{i+1} (in Aa, Pi_e = I): FPi_i = F_i Pi_{i+1}, Pi_i = Abar_i^T Pi_{i+1}.
 template <typename T>
-__device__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
+__device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
   const QPDesc& d = *c.d;
   const int nx = d.nx, nu = d.nu, nc = d.nc, ldx = d.ldx, ldu = d.ldu, ldc = d.ldc, lds = fb.lds, msz = c.msz;
   const int esz = (int)sizeof(T), t = threadIdx.x;
@@ -703,18 +713,22 @@ __device__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, int i, int k)
   sgemm<T>(nx, nx, T(1), MTerm<T>{fb.Xb, lds, true, fb.P, lds, nx}, MTerm<T>{fb.S2, lds, true, fb.S3, lds, nu},
            T(1), TP<T>(d.VP) + (size_t)i * msz, ldx, false, fb.P, lds, false);
   prof_mark(c, PH_FC3);
-  // stage outputs
+  // stage outputs: -B Gamma (= F_i^T), -D Gamma (= J_i^T), CK_i = C_i + D_i K_i
+  sgemm1<T>(nx, nu, nu, T(-1), Bb, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.BG, ldu);
+  sgemm1<T>(nc, nu, nu, T(-1), Db, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.JT, ldu);
+  sgemm1<T>(nc, nx, nu, T(1), Db, ldu, false, fb.S1, lds, T(1), TP<T>(d.C) + (size_t)i * nc * ldx, ldx, fb.CKb[0], lds);
   cta_copy_vec<T>(nx, nx, fb.P, lds, TP<T>(d.IP) + (size_t)i * msz, ldx);
   cta_copy_vec<T>(nx, nx, fb.Xb, lds, TP<T>(d.Abar) + (size_t)i * msz, ldx);
   cta_copy_vec<T>(nu, nu, fb.Gi, ldu, TP<T>(d.Gam) + (size_t)i * nu * ldu, ldu);
+  cta_copy_vec<T>(nc, nx, fb.CKb[0], lds, TP<T>(d.CK) + (size_t)i * nc * ldx, ldx);
   for (int e = t; e < nx; e += NT) TP<T>(d.c0)[(size_t)i * ldx + e] = c0v[e];
   for (int e = t; e < nu; e += NT) TP<T>(d.k0)[(size_t)i * ldu + e] = k0v[e];
-  sgemm1<T>(nc, nx, nu, T(1), Db, ldu, false, fb.S1, lds, T(1), TP<T>(d.C) + (size_t)i * nc * ldx, ldx,
-            TP<T>(d.CK) + (size_t)i * nc * ldx, ldx);                                             // CK
-  sgemm1<T>(nx, nu, nu, T(-1), Bb, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, TP<T>(d.F) + (size_t)i * nu * ldx, ldx,
-            true);                                                                                // F = -(B Gamma)^T
-  sgemm1<T>(nc, nu, nu, T(-1), Db, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, TP<T>(d.J) + (size_t)i * nu * ldc, ldc,
-            true);                                                                                // J = -(D Gamma)^T
+  if (!c.last) {
+    // backward chunk products (Pi in Aa): FPi_i^T = Pi_{i+1}^T F_i^T, Pi_i = Abar_i^T Pi_{i+1}
+    sgemm1<T>(nx, nu, nx, T(1), fb.Aa, lds, true, fb.BG, ldu, T(0), nullptr, 0,
+              TP<T>(d.FPi) + (size_t)i * nx * ldu, ldu);
+    sgemm1<T>(nx, nx, nx, T(1), fb.Xb, lds, true, fb.Aa, lds, T(0), nullptr, 0, fb.Aa, lds);
+  }
   prof_mark(c, PH_FC4);
   fact_bundles<T>(c, fb, i, k);
   prof_mark(c, PH_FC5);
@@ -773,12 +787,126 @@ __device__ __noinline__ int blocked_scan(Ctx<T>& c, cg::cluster_group& cl) {
     cta_stage_rows(fb.P, lds * esz, IP + (size_t)c.e * msz, ldx * esz, nx, ldx * esz);
     fact_prefetch<T>(c, fb, c.e - 1, 0, true);
     cp_async_commit();
+    cta_eye<T>(nx, fb.Aa, lds);   // Pi_e
     cp_async_wait<0>();
     __syncthreads();
     int k = 0;
     for (int i = c.e - 1; i >= c.s; --i, k ^= 1) bad |= fact_step_riccati<T>(c, fb, i, k);
+    cta_copy_vec<T>(nx, nx, fb.Aa, lds, TP<T>(d.Tch) + (size_t)c.rank * msz, ldx);   // T_r = Pi_s
   }
   return bad;
+}
+
+// R1 of the blocked schedule: the stage leaves of eq. assoc_init with
+// shared-memory GEMMs,
+//   Q^ = Q + rho C^T C,  R^ = R + rho D^T D,  S^ = S + rho D^T C,
+//   s0 = R^^-1 S^,  P~ = Q^ - S^^T s0,  A~ = A - B s0,
+// kept in global memory (P~, A~, R^, s0) for the phases of blocked_scan; C~ =
+// B R^^-1 B^T only for the last leaf of chunks 1 .. nch-2 (the start of their
+// fold); the last chunk also forms the terminal leaf P~_N = Q_N + rho C_N^T C_N.
+template <typename T>
+__device__ __noinline__ int leaves_blocked(Ctx<T>& c, T rho) {
+  QPDesc& d = *c.d;
+  if (!c.active) return 0;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, N = d.N, ldx = d.ldx, ldu = d.ldu, msz = c.msz;
+  const int esz = (int)sizeof(T);
+  const FactBufs<T> fb = fact_bufs<T>(c);
+  const int lds = fb.lds;
+  int bad = 0;
+  const bool need_ct = c.rank >= 1 && !c.last;
+  for (int i = c.s; i < c.e; ++i) {
+    cta_stage_rows(fb.P, lds * esz, TP<T>(d.Q) + (size_t)i * msz, ldx * esz, nx, ldx * esz);
+    cta_stage_rows(fb.Xb, lds * esz, TP<T>(d.A) + (size_t)i * msz, ldx * esz, nx, ldx * esz);
+    cta_stage_rows(fb.S3, lds * esz, TP<T>(d.S) + (size_t)i * nu * ldx, ldx * esz, nu, ldx * esz);
+    if (nc > 0) {
+      cta_stage_rows(fb.CKb[0], lds * esz, TP<T>(d.C) + (size_t)i * nc * ldx, ldx * esz, nc, ldx * esz);
+      cta_stage(fb.Db[0], TP<T>(d.D) + (size_t)i * nc * ldu, nc * ldu * esz);
+    }
+    cta_stage(fb.Bb[0], TP<T>(d.B) + (size_t)i * nx * ldu, nx * ldu * esz);
+    cta_stage(fb.Rb[0], TP<T>(d.R) + (size_t)i * nu * ldu, nu * ldu * esz);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    sgemm1<T>(nx, nx, nc, rho, fb.CKb[0], lds, true, fb.CKb[0], lds, T(1), fb.P, lds, fb.P, lds);      // Q^
+    sgemm1<T>(nu, nu, nc, rho, fb.Db[0], ldu, true, fb.Db[0], ldu, T(1), fb.Rb[0], ldu, fb.Gm, ldu);   // R^
+    sgemm1<T>(nu, nx, nc, rho, fb.Db[0], ldu, true, fb.CKb[0], lds, T(1), fb.S3, lds, fb.S1, lds);     // S^
+    cta_copy_vec<T>(nu, nu, fb.Gm, ldu, TP<T>(d.Rh) + (size_t)i * nu * ldu, ldu);
+    bad |= small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
+    sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S1, lds, T(0), nullptr, 0, fb.S2, lds);          // s0
+    sgemm1<T>(nx, nx, nu, T(-1), fb.S1, lds, true, fb.S2, lds, T(1), fb.P, lds, fb.P, lds);            // P~
+    sgemm1<T>(nx, nx, nu, T(-1), fb.Bb[0], ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds);      // A~
+    cta_copy_vec<T>(nu, nx, fb.S2, lds, TP<T>(d.S0) + (size_t)i * nu * ldx, ldx);
+    cta_copy_vec<T>(nx, nx, fb.P, lds, TP<T>(d.VP) + (size_t)i * msz, ldx);
+    cta_copy_vec<T>(nx, nx, fb.Xb, lds, TP<T>(d.VA) + (size_t)i * msz, ldx);
+    if (need_ct && i == c.e - 1) {
+      // C~ = B (B R^^-1)^T
+      sgemm1<T>(nx, nu, nu, T(1), fb.Bb[0], ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.S3, lds, true);
+      sgemm1<T>(nx, nx, nu, T(1), fb.Bb[0], ldu, false, fb.S3, lds, T(0), nullptr, 0,
+                TP<T>(d.VC) + (size_t)i * msz, ldx);
+    }
+  }
+  if (c.last) {
+    cta_stage_rows(fb.P, lds * esz, TP<T>(d.Q) + (size_t)N * msz, ldx * esz, nx, ldx * esz);
+    if (nf > 0) cta_stage_rows(fb.CKb[0], lds * esz, TP<T>(d.CN), ldx * esz, nf, ldx * esz);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    sgemm1<T>(nx, nx, nf, rho, fb.CKb[0], lds, true, fb.CKb[0], lds, T(1), fb.P, lds, fb.P, lds);
+    cta_copy_vec<T>(nx, nx, fb.P, lds, TP<T>(d.VP) + (size_t)N * msz, ldx);
+  }
+  return bad;
+}
+
+// Forward chunk products of the blocked schedule (not needed in the first
+// chunk): Sig_s = I, Sig_{i+1} = Abar_i Sig_i, KSig_i = K_i Sig_i,
+// CKSig_i = (CK_i Sig_i)^T (stored transposed), U_r = Sig_e; the last chunk
+// also Sig_N and C_N Sig_N.  Sig stays in shared memory; the next stage's
+// Abar, K and CK are fetched while the current one is used.
+template <typename T>
+__device__ __noinline__ void forward_products(Ctx<T>& c) {
+  QPDesc& d = *c.d;
+  if (!c.active || c.first) return;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, ldx = d.ldx, ldc = d.ldc, msz = c.msz;
+  const int esz = (int)sizeof(T);
+  const FactBufs<T> fb = fact_bufs<T>(c);
+  const int lds = fb.lds;
+  T* Sg = fb.P;
+  T* const Ab[2] = {fb.Xb, fb.Aa};
+  T* const Kb[2] = {fb.S1, fb.S2};
+  auto issue = [&](int i, int k) {
+    cta_stage_rows(Ab[k], lds * esz, TP<T>(d.Abar) + (size_t)i * msz, ldx * esz, nx, ldx * esz);
+    cta_stage_rows(Kb[k], lds * esz, TP<T>(d.K) + (size_t)i * nu * ldx, ldx * esz, nu, ldx * esz);
+    if (nc > 0) cta_stage_rows(fb.CKb[k], lds * esz, TP<T>(d.CK) + (size_t)i * nc * ldx, ldx * esz, nc, ldx * esz);
+    cp_async_commit();
+  };
+  issue(c.s, 0);
+  cta_eye<T>(nx, Sg, lds);
+  int k = 0;
+  for (int i = c.s; i < c.e; ++i, k ^= 1) {
+    if (i + 1 < c.e) {
+      issue(i + 1, k ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    cta_copy_vec<T>(nx, nx, Sg, lds, TP<T>(d.Sig) + (size_t)i * msz, ldx);
+    sgemm1<T>(nu, nx, nx, T(1), Kb[k], lds, false, Sg, lds, T(0), nullptr, 0, TP<T>(d.KSig) + (size_t)i * nu * ldx, ldx);
+    sgemm1<T>(nc, nx, nx, T(1), fb.CKb[k], lds, false, Sg, lds, T(0), nullptr, 0,
+              TP<T>(d.CKSig) + (size_t)i * nx * ldc, ldc, true);
+    sgemm1<T>(nx, nx, nx, T(1), Ab[k], lds, false, Sg, lds, T(0), nullptr, 0, Sg, lds);
+  }
+  cta_copy_vec<T>(nx, nx, Sg, lds, TP<T>(d.Uch) + (size_t)c.rank * msz, ldx);
+  if (c.last) {
+    cta_copy_vec<T>(nx, nx, Sg, lds, TP<T>(d.SigN), ldx);
+    if (nf > 0) {
+      cta_stage_rows(fb.CKb[0], lds * esz, TP<T>(d.CN), ldx * esz, nf, ldx * esz);
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+      sgemm1<T>(nf, nx, nx, T(1), fb.CKb[0], lds, false, Sg, lds, T(0), nullptr, 0, TP<T>(d.CNSig), ldx);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -802,7 +930,8 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
   int bad = 0;
 
   // R1: leaves (eq. assoc_init) for own stages, terminal by the last chunk.
-  if (c.active) {
+  if (d.fact == 0) bad |= leaves_blocked<T>(c, rho);
+  else if (c.active) {
     for (int i = c.s; i < c.e; ++i) {
       const T* Ai = A + (size_t)i * msz;
       const T* Bi = B + (size_t)i * nx * ldu;
@@ -847,7 +976,8 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
   // Forward (not needed in the first chunk):
   //   Sig_s = I, Sig_{i+1} = Abar_i Sig_i, KSig_i = K_i Sig_i,
   //   CKSig_i = CK_i Sig_i, U_r = Sig_e; the last chunk also C_N Sig_N.
-  if (c.active) {
+  if (d.fact == 0) forward_products<T>(c);   // backward products came with the Riccati steps
+  else if (c.active) {
     if (!c.last) {
       T* Pc = c.scr;
       T* Pn2 = c.scr + c.msz;
