@@ -505,6 +505,64 @@ __device__ void write_outputs(Ctx<T>& c, T rho) {
 // FP64 KKT residual of (ox, ou, olam) -- see include/gpusls.h for the
 // definition.  Every CTA evaluates the stage-local parts of its chunk; CTA 0
 // then runs the costate recursion mu_k = g_k + A_k^T mu_{k+1} sequentially.
+// FP64 products of the KKT check on the caller's unpadded arrays (global
+// memory), by the whole CTA; each ends with a barrier.
+// Column sweep: y[o] (+)= sum_{k<m} M[k ld + o] x[k], o < n.  Thread (o, g)
+// sums the rows of group g with independent loads (coalesced across o);
+// part: shared, >= NT doubles.
+__device__ inline void kkt_colsweep(const double* M, int ld, int m, int n, const double* x, double* y, bool acc,
+                                    double* part) {
+  const int t = threadIdx.x;
+  if (n > 0) {
+    const int G = NT / n;
+    const int Rg = (m + G - 1) / G;
+    const int o = t % n, g = t / n;
+    if (g < G) {
+      const int r0 = min(m, g * Rg), r1 = min(m, r0 + Rg);
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int k = r0;
+      for (; k + 3 < r1; k += 4) {
+        a0 = fma(M[(size_t)k * ld + o], x[k], a0);
+        a1 = fma(M[(size_t)(k + 1) * ld + o], x[k + 1], a1);
+        a2 = fma(M[(size_t)(k + 2) * ld + o], x[k + 2], a2);
+        a3 = fma(M[(size_t)(k + 3) * ld + o], x[k + 3], a3);
+      }
+      for (; k < r1; ++k) a0 = fma(M[(size_t)k * ld + o], x[k], a0);
+      part[g * n + o] = (a0 + a1) + (a2 + a3);
+    }
+    __syncthreads();
+    if (t < n) {
+      double s2 = acc ? y[t] : 0.0;
+      for (int gg = 0; gg < G; ++gg) s2 += part[gg * n + t];
+      y[t] = s2;
+    }
+  }
+  __syncthreads();
+}
+
+// Row dots: y[j] (+)= sum_{k<n} M[j ld + k] x[k], j < rows; a warp takes four
+// rows at a time (lanes along k), so four rows' loads are in flight together.
+__device__ inline void kkt_rowdots(const double* M, int ld, int rows, int n, const double* x, double* y, bool acc) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int j0 = 4 * w; j0 < rows; j0 += 4 * (NT / 32)) {
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = l; k < n; k += 32) {
+      const double xk = x[k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j0 + q < rows) s4[q] = fma(M[(size_t)(j0 + q) * ld + k], xk, s4[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s4[q] = warp_sum(s4[q]);
+    const double mine = l == 0 ? s4[0] : (l == 1 ? s4[1] : (l == 2 ? s4[2] : s4[3]));
+    if (l < 4 && j0 + l < rows) y[j0 + l] = (acc ? y[j0 + l] : 0.0) + mine;
+  }
+  __syncthreads();
+}
+
+// FP64 KKT residual of the outputs written by write_outputs (see the
+// library's residual definition): dynamics, bound violation, u-stationarity
+// after costate recovery and complementarity, max over the cluster.
 template <typename T>
 __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
   QPDesc& d = *c.d;
@@ -516,6 +574,14 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
   double* lv = uv + 96;
   double* mu = lv + 96;
   double* mu2 = mu + 96;
+  double* gv = mu2 + 96;
+  double* ax = gv + 96;
+  double* hv = ax + 96;
+  double* vv = hv + 96;
+  // partial sums (NT doubles) after the vectors: everything the check uses
+  // lies in the first 9.7 KB of the union region (>= 67 KB), clear of the
+  // sweep and gather buffers that may follow a small ring there
+  double* part = vv + 96;
   double dyn = 0.0, viol = 0.0, comp = 0.0, stat = 0.0;
   long long kt0 = c.prof ? clock64() : 0;
   cl.sync();   // outputs of every chunk visible
@@ -533,48 +599,37 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
       __syncthreads();
       const double* Qi = d.Q64 + (size_t)i * nx * nx;
       const double* Ci = term ? d.CN64 : d.C64 + (size_t)i * nc * nx;
-      const double* Di = term ? nullptr : d.D64 + (size_t)i * nc * nu;
-      // dynamics row j: x_{i+1} - A x - B u - b ;  g_i = Q x + S^T u + q + C^T lam
-      for (int j = w; j < nx; j += NT / 32) {
-        double gsum = warp_dot(Qi + (size_t)j * nx, xv, nx);
-        if (!term) {
-          const double* Ai = d.A64 + (size_t)i * nx * nx + (size_t)j * nx;
-          const double* Bi = d.B64 + (size_t)i * nx * nu + (size_t)j * nu;
-          const double ax = warp_dot(Ai, xv, nx) + warp_dot(Bi, uv, nu);
-          if (lane == 0) dyn = fmax(dyn, fabs(xn[j] - ax - d.b64[(size_t)i * nx + j]));
-          double st = 0.0;
-          for (int a = lane; a < nu; a += 32) st += d.S64[(size_t)i * nu * nx + (size_t)a * nx + j] * uv[a];
-          gsum += warp_sum(st);
-        }
-        double ct = 0.0;
-        for (int k = lane; k < nr; k += 32) ct += Ci[(size_t)k * nx + j] * lv[k];
-        gsum += warp_sum(ct);
-        if (lane == 0) d.kg[(size_t)i * nx + j] = gsum + d.q64[(size_t)i * nx + j];
-      }
+      // g_i = Q x + S^T u + C^T lam + q
+      kkt_rowdots(Qi, nx, nx, nx, xv, gv, false);
+      kkt_colsweep(Ci, nx, nr, nx, lv, gv, true, part);
       if (!term) {
-        // h_i = R u + S x + r + D^T lam
-        for (int a = w; a < nu; a += NT / 32) {
-          double hs = warp_dot(d.R64 + (size_t)i * nu * nu + (size_t)a * nu, uv, nu) +
-                      warp_dot(d.S64 + (size_t)i * nu * nx + (size_t)a * nx, xv, nx);
-          double dt = 0.0;
-          for (int k = lane; k < nc; k += 32) dt += Di[(size_t)k * nu + a] * lv[k];
-          hs += warp_sum(dt);
-          if (lane == 0) d.kh[(size_t)i * nu + a] = hs + d.r64[(size_t)i * nu + a];
-        }
+        const double* Ai = d.A64 + (size_t)i * nx * nx;
+        const double* Bi = d.B64 + (size_t)i * nx * nu;
+        const double* Si = d.S64 + (size_t)i * nu * nx;
+        const double* Di = d.D64 + (size_t)i * nc * nu;
+        kkt_colsweep(Si, nx, nu, nx, uv, gv, true, part);
+        // dynamics A x + B u ; h_i = R u + S x + D^T lam + r ; rows C x + D u
+        kkt_rowdots(Ai, nx, nx, nx, xv, ax, false);
+        kkt_rowdots(Bi, nu, nx, nu, uv, ax, true);
+        kkt_rowdots(d.R64 + (size_t)i * nu * nu, nu, nu, nu, uv, hv, false);
+        kkt_colsweep(Di, nu, nc, nu, lv, hv, true, part);
+        kkt_rowdots(Si, nx, nu, nx, xv, hv, true);
+        kkt_rowdots(Di, nu, nc, nu, uv, vv, false);
+        kkt_rowdots(Ci, nx, nc, nx, xv, vv, true);
+        for (int j = t; j < nx; j += NT) dyn = fmax(dyn, fabs(xn[j] - ax[j] - d.b64[(size_t)i * nx + j]));
+        for (int a = t; a < nu; a += NT) d.kh[(size_t)i * nu + a] = hv[a] + d.r64[(size_t)i * nu + a];
+      } else {
+        kkt_rowdots(Ci, nx, nr, nx, xv, vv, false);
       }
-      // rows: v = C x + D u ; violation and complementarity
-      for (int k = w; k < nr; k += NT / 32) {
-        double v = warp_dot(Ci + (size_t)k * nx, xv, nx);
-        if (!term) v += warp_dot(Di + (size_t)k * nu, uv, nu);
-        if (lane == 0) {
-          const size_t gi = (size_t)i * nc + k;
-          const double lo = d.lo64[gi], hi = d.hi64[gi], l = lv[k];
-          viol = fmax(viol, fmax(fmax(v - hi, lo - v), 0.0));
-          double cp = 0.0;
-          if (l > 0) cp = isfinite(hi) ? l * fabs(hi - v) : fabs(l);
-          else if (l < 0) cp = isfinite(lo) ? -l * fabs(v - lo) : fabs(l);
-          comp = fmax(comp, cp);
-        }
+      for (int j = t; j < nx; j += NT) d.kg[(size_t)i * nx + j] = gv[j] + d.q64[(size_t)i * nx + j];
+      for (int k = t; k < nr; k += NT) {
+        const size_t gi = (size_t)i * nc + k;
+        const double v = vv[k], lo = d.lo64[gi], hi = d.hi64[gi], l = lv[k];
+        viol = fmax(viol, fmax(fmax(v - hi, lo - v), 0.0));
+        double cp = 0.0;
+        if (l > 0) cp = isfinite(hi) ? l * fabs(hi - v) : fabs(l);
+        else if (l < 0) cp = isfinite(lo) ? -l * fabs(v - lo) : fabs(l);
+        comp = fmax(comp, cp);
       }
       __syncthreads();
     }
@@ -589,22 +644,48 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
     // costate recursion mu_i = g_i + A_i^T mu_{i+1}, with the u-residual
     // B_i^T mu_{i+1} + h_i at each stage.  Every stage is one split-row sweep
     // over the nx + nu outputs: thread (o, g) sums rows k of group g of
-    // A_i(k, o) (o < nx) or B_i(k, o - nx) times mu(k) straight from global
-    // memory (independent scalar loads: the caller's arrays are unpadded),
-    // and the owners of the outputs add the G partial sums.
+    // A_i(k, o) (o < nx) or B_i(k, o - nx) times mu(k), and the owners of the
+    // outputs add the G partial sums.  When two stages' A_i, B_i fit the
+    // union region after the vectors, the next stage's are copied into shared
+    // memory (cp.async, 8-byte elements: the caller's arrays are unpadded)
+    // while the current one is swept; otherwise they are read from global
+    // memory in the sweep.
     const int no = nx + nu;
     int G = NT / no;
     G = G < 1 ? 1 : (G > SWEEP_MAXG ? SWEEP_MAXG : G);
     const int Rg = (nx + G - 1) / G;
     const int o = t % no, g = t / no;
     const int r0 = min(nx, g * Rg), r1 = min(nx, r0 + Rg);
-    double* part = reinterpret_cast<double*>(c.swp);   // [G][no] partial sums
+    const int per = nx * nx + nx * nu;   // doubles of A_i then B_i
+    double* pbuf = part + NT;
+    const bool pre = (int)((pbuf - xv) + 2 * per) * 8 <= c.uni;
+    auto issue = [&](int i, int k) {
+      double* dst = pbuf + (size_t)k * per;
+      const double* Ai = d.A64 + (size_t)i * nx * nx;
+      const double* Bi = d.B64 + (size_t)i * nx * nu;
+      for (int e2 = t; e2 < nx * nx; e2 += NT) cp_async_elem<double>(dst + e2, Ai + e2);
+      for (int e2 = t; e2 < nx * nu; e2 += NT) cp_async_elem<double>(dst + nx * nx + e2, Bi + e2);
+      cp_async_commit();
+    };
     for (int j = t; j < nx; j += NT) mu[j] = d.kg[(size_t)N * nx + j];
+    if (pre) issue(N - 1, 0);
     __syncthreads();
-    for (int i = N - 1; i >= 0; --i) {
+    int kb = 0;
+    for (int i = N - 1; i >= 0; --i, kb ^= 1) {
+      if (pre) {
+        if (i > 0) {
+          issue(i - 1, kb ^ 1);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+        __syncthreads();
+      }
       if (g < G) {
         const bool isA = o < nx;
-        const double* M = isA ? d.A64 + (size_t)i * nx * nx + o : d.B64 + (size_t)i * nx * nu + (o - nx);
+        const double* base = pre ? pbuf + (size_t)kb * per
+                                 : (isA ? d.A64 + (size_t)i * nx * nx : d.B64 + (size_t)i * nx * nu);
+        const double* M = isA ? base + o : (pre ? base + nx * nx : base) + (o - nx);
         const int ld = isA ? nx : nu;
         double a0 = 0.0, a1 = 0.0;
         int k = r0;

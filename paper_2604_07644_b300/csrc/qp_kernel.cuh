@@ -101,6 +101,7 @@ struct SmemLayout {
   int ring, gemm, gj, gjbuf;                 // union region
   int z, y, w, l, x, kt, v, d, u, pe, xs, slotL, slotX, tmp1, tmp2, tmp3, red;
   int part, perm, flag, bar, swp, gath;
+  int uni;     // bytes of the union region (ring / dense scratch / factorization buffers)
   int total;
 };
 
@@ -204,6 +205,7 @@ __host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf
   } else {
     s.gath = off; off = al16(off + gath_b);
   }
+  s.uni = uend;
   s.total = off;
   return s;
 }
@@ -225,6 +227,7 @@ struct Ctx {
   unsigned inflight, ipar;   // issuing thread: slots with a copy not yet seen complete, their parities
   T* scr;   // per-CTA global scratch: 6 matrices nx x ldx
   int msz;  // nx * ldx
+  int uni;  // bytes of the union region at ring
   unsigned long long* prof;  // non-null only in thread 0 of each CTA of QP 0 when profiling
   bool tc;                   // factorization products in TF32 on the tensor cores
   long long t_last;

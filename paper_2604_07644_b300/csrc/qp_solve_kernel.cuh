@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   }
   __syncthreads();
   c.msz = d.nx * d.ldx;
+  c.uni = lay.uni;
   c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
   const int t = threadIdx.x;
   c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
