@@ -230,12 +230,16 @@ def extra_workloads(args, qps, hb, stream, dev, oracle_sols):
 
     def batch_run(name, qps_, cluster):
         s = native.default_settings(**dict(base, cluster=cluster))
+        if not args.no_autotune:
+            from paper_2604_07644_b300 import autotune
+            s, _ = autotune.choose(qps_, s, expected_iters=300, tail_iters=1500, cache=autotune.Cache())
         with torch.cuda.stream(stream):
             qb = QPBatch(qps_, s, stream=stream, device=dev)
             g = qb.graph()
             ms = _time_graph(g, stream, steps)
             info = g.info()
-        out[name] = {"ms_per_qp": ms / len(qps_), "batch": len(qps_),
+        out[name] = {"ms_per_qp": ms / len(qps_), "batch": len(qps_), "cluster": int(s.cluster),
+                     "occupancy": int(s.occupancy),
                      "iters_mean": float(np.mean([i["iters"] for i in info])),
                      "kkt_max": float(np.max([i["kkt"] for i in info])),
                      "all_converged": all(i["status"] == 0 for i in info)}

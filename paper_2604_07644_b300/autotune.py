@@ -34,7 +34,10 @@ from dataclasses import dataclass
 NX_BUCKETS = (16, 32, 64, 80)
 N_BUCKETS = (32, 64, 128, 256, 1024)
 B_BUCKETS = (1, 8, 64, 256, 4096)
-CLUSTERS = (1, 2, 4, 8)
+# Every cluster size: a GPC holds two CTAs per SM, and the sizes that tile
+# its slots best (6 on B300: four 8-CTA clusters leave slots idle) can beat
+# the longer chains they imply.
+CLUSTERS = (1, 2, 3, 4, 5, 6, 7, 8)
 OCCUPANCIES = (0, 1)
 
 

@@ -335,41 +335,57 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
       pl.rp = (double)block_max(c, rp);
       pl.vm = (double)block_max(c, vm);
       pl.zm = (double)block_max(c, zm);
-      // dual residual partial: rho * ||G^T (z+ - z)||_inf = rho * max |[C D]^T dz|
-      T rd = T(0);
-      const int Cn = nx + nu;
-      if (cds > 0) {
-        const int Gs = max(1, d.slot / cds);
-        const int nbk = (L + Gs - 1) / Gs;
-        stream_blocks<T>(
-            c, nbk,
-            [&](int b) {
-              const int n_st = min(Gs, L - b * Gs);
-              return Blk<T>{CD + (size_t)(s + b * Gs) * cds, n_st * cds * (int)sizeof(T)};
-            },
-            [&](int b, const T* S) {
-              const int n_st = min(Gs, L - b * Gs);
-              for (int e2 = t; e2 < n_st * Cn; e2 += NT) {
-                const int ls = e2 / Cn, col = e2 - ls * Cn, li = b * Gs + ls;
-                const T* Sb = S + (size_t)ls * cds;
-                T a = T(0);
-                for (int rr = 0; rr < nc; ++rr) a += Sb[rr * ldf + col] * c.wS[li * nc + rr];
-                rd = fmax(rd, fabs(a));
-              }
-            });
-      }
-      if (c.last) {
-        for (int j = t; j < nx; j += NT) {
-          T a = T(0);
-          for (int rr = 0; rr < nf; ++rr) a += CN[rr * ldx + j] * c.wS[L * nc + rr];
-          rd = fmax(rd, fabs(a));
-        }
-      }
-      pl.rd = (double)rho * (double)block_max(c, rd);
+      pl.rd = 0.0;   // formed by dual_residual_partial when the solve loop needs it
     }
   } else {
     pl.rp = pl.rd = pl.vm = pl.zm = 0.0;
   }
+}
+
+// Dual-residual partial of own rows, rho * ||G^T (z+ - z)||_inf = rho * max
+// |[C D]^T dz| over own stages (dz = wS, left by the projection of the last
+// iteration), block-level max.  Only the solve loop's checks that need it
+// call it (the primal test passed, a rho update, the last iteration).
+template <typename T>
+__device__ double dual_residual_partial(Ctx<T>& c, T rho) {
+  QPDesc& d = *c.d;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, ldx = d.ldx, ldu = d.ldu, ldv = d.ldv, ldf = d.ldf;
+  const int L = c.L, s = c.s, t = threadIdx.x;
+  const T *CD = TP<T>(d.CD), *CN = TP<T>(d.CN);
+  int bws, fws, cds;
+  bundle_sizes(nx, nu, nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
+  T rd = T(0);
+  if (c.active) {
+    const int Cn = nx + nu;
+    if (cds > 0) {
+      const int Gs = max(1, d.slot / cds);
+      const int nbk = (L + Gs - 1) / Gs;
+      stream_blocks<T>(
+          c, nbk,
+          [&](int b) {
+            const int n_st = min(Gs, L - b * Gs);
+            return Blk<T>{CD + (size_t)(s + b * Gs) * cds, n_st * cds * (int)sizeof(T)};
+          },
+          [&](int b, const T* S) {
+            const int n_st = min(Gs, L - b * Gs);
+            for (int e2 = t; e2 < n_st * Cn; e2 += NT) {
+              const int ls = e2 / Cn, col = e2 - ls * Cn, li = b * Gs + ls;
+              const T* Sb = S + (size_t)ls * cds;
+              T a = T(0);
+              for (int rr = 0; rr < nc; ++rr) a += Sb[rr * ldf + col] * c.wS[li * nc + rr];
+              rd = fmax(rd, fabs(a));
+            }
+          });
+    }
+    if (c.last) {
+      for (int j = t; j < nx; j += NT) {
+        T a = T(0);
+        for (int rr = 0; rr < nf; ++rr) a += CN[rr * ldx + j] * c.wS[L * nc + rr];
+        rd = fmax(rd, fabs(a));
+      }
+    }
+  }
+  return (double)rho * (double)block_max(c, rd);
 }
 
 // Full state and input of own stages: x_i = lx_i + Sig_i x_s (into dS rows

@@ -146,16 +146,24 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
       Partials pl;
       admm_iteration<T>(c, cl, rho, check, pl);
       if (!check) continue;
-      double v[5] = {pl.rp, pl.rd, pl.vm, pl.zm, c.flag[RING_FLAG] ? 1.0 : 0.0};
+      double v[5] = {pl.rp, 0.0, pl.vm, pl.zm, c.flag[RING_FLAG] ? 1.0 : 0.0};
       cluster_max(c, cl, v, 5);
-      prof_mark(c, PH_CHECK);
       rp = v[0];
-      rd = v[1];
+      // the dual residual only where a decision reads it: the primal test
+      // passed, a rho update, the last iteration (all uniform in the cluster)
+      const bool need_rd = rho_iter || it == max_it || (stop_iter && rp <= eps);
+      if (need_rd && v[4] == 0.0 && isfinite(rp)) {
+        double u2[2] = {dual_residual_partial<T>(c, rho), c.flag[RING_FLAG] ? 1.0 : 0.0};
+        cluster_max(c, cl, u2, 2);
+        rd = u2[0];
+        v[4] = fmax(v[4], u2[1]);
+      }
+      prof_mark(c, PH_CHECK);
       if (v[4] > 0.0) {
         status = GPUSLS_ERR_TIMEOUT;
         break;
       }
-      if (!(isfinite(rp) && isfinite(rd))) {
+      if (!isfinite(rp) || (need_rd && !isfinite(rd))) {
         status = GPUSLS_ERR_NAN;
         break;
       }

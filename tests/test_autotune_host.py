@@ -25,7 +25,7 @@ def test_key_separates_precision_and_buckets():
 
 
 def test_candidates_respect_horizon():
-    assert set(AT.candidates(3)) == {(1, 0), (1, 1), (2, 0), (2, 1)}
+    assert set(AT.candidates(3)) == {(1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1)}
     assert (8, 1) in AT.candidates(100)
 
 
