@@ -202,6 +202,32 @@ static int run_pack(qp_handle* h, const std::vector<PackJob>& jobs) {
   return GPUSLS_OK;
 }
 
+// Per-QP launch-shape plan for cluster size cs: chunk length and count, ring
+// slot, factorization schedule (blocked unless asked for the tree, in TF32,
+// or its buffers do not fit), ring depth, and the shared memory per CTA.
+struct ShapePlan {
+  int Lc, nch, slot, fact, depth, smem;
+};
+static ShapePlan plan_shape(const qp_dims& d, int cs, int esz, const qp_settings* s) {
+  ShapePlan p;
+  const int ldx = rup4(d.nx), ldu = rup4(d.nu), ldc = rup4(std::max(1, d.nc));
+  const int ldv = rup4(d.nx + d.nc), ldf = rup4(d.nx + d.nu);
+  const int msz = d.nx * ldx;
+  int bws, fws, cds;
+  bundle_sizes(d.nx, d.nu, d.nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
+  p.Lc = (d.N + cs - 1) / cs;
+  p.nch = (d.N + p.Lc - 1) / p.Lc;
+  p.slot = std::max(std::max(std::max(bws, fws), msz), std::max(std::max(d.nx * ldu, d.nx * ldc), cds));
+  auto lay_total = [&](int depth, int fact) {
+    return smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, ldx, ldu, ldv, ldf, depth, p.slot, esz, fact).total;
+  };
+  p.fact = (s->factorization == 1 || s->precision == GPUSLS_TF32 || d.nu > FACT_MAX_NU) ? 1 : 0;
+  if (p.fact == 0 && lay_total(1, 0) > 227 * 1024) p.fact = 1;
+  p.depth = lay_total(3, p.fact) > 227 * 1024 ? 2 : 3;
+  p.smem = lay_total(p.depth, p.fact);
+  return p;
+}
+
 static bool dims_ok(const qp_dims& d) {
   return d.nx >= 1 && d.nx <= TILE && d.nu >= 1 && d.nu <= 32 && d.nc >= 0 && d.nc <= 64 && d.nf >= 0 &&
          d.nf <= 64 && d.N >= 1 && d.N <= 1024;
@@ -305,24 +331,16 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     memset(&D_, 0, sizeof(D_));
     D_.nx = d.nx; D_.nu = d.nu; D_.N = d.N; D_.nc = d.nc; D_.nf = d.nf; D_.m = (int)m;
     D_.ldx = (int)ldx; D_.ldu = (int)ldu; D_.ldc = (int)ldc;
-    D_.Lc = (d.N + cs - 1) / cs;
-    D_.nch = (d.N + D_.Lc - 1) / D_.Lc;
+    const ShapePlan sp = plan_shape(d, cs, esz, s);
+    D_.Lc = sp.Lc;
+    D_.nch = sp.nch;
     D_.nlev = nlev;
     D_.ldv = ldv;
     D_.ldf = ldf;
-    D_.slot = std::max(std::max(std::max(bws, fws), (int)msz),
-                       std::max(std::max(d.nx * (int)ldu, d.nx * (int)ldc), cds));
-    // blocked factorization unless asked for the tree or it does not fit
-    auto lay_total = [&](int depth, int fact) {
-      return smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, D_.nch, (int)ldx, (int)ldu, ldv, ldf, depth, D_.slot, esz,
-                         fact).total;
-    };
-    D_.fact = (s->factorization == 1 || s->precision == GPUSLS_TF32 || d.nu > FACT_MAX_NU) ? 1 : 0;
-    if (D_.fact == 0 && lay_total(1, 0) > 227 * 1024) D_.fact = 1;
-    D_.depth = lay_total(3, D_.fact) > 227 * 1024 ? 2 : 3;
-    const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, D_.Lc, D_.nch, (int)ldx, (int)ldu, ldv, ldf, D_.depth,
-                                       D_.slot, esz, D_.fact);
-    smem = std::max(smem, lay.total);
+    D_.slot = sp.slot;
+    D_.fact = sp.fact;
+    D_.depth = sp.depth;
+    smem = std::max(smem, sp.smem);
   }
   h->smem = smem;
   if (smem > 227 * 1024) {
