@@ -197,6 +197,57 @@ def test_quadruped_61d_full_size(lib):
     b.close()
 
 
+@pytest.mark.parametrize("cluster", [6, 8])
+def test_riccati_schedules_agree_full_size(lib, cluster):
+    """Full-size 61D / N=100 factorization at the tuned launch shapes: the
+    blocked schedule (leaf-structured combines) and the tree give the same
+    P_i and K_i in FP64, and the FP32 blocked terms match the FP64 oracle's
+    sequential Riccati recursion."""
+    qp = W.quadruped_61d(0)
+    rho = 0.3
+    out = {}
+    for fact in (0, 1):
+        b = batch([qp], precision=native.GPUSLS_FP64, cluster=cluster, rho=rho, factorization=fact)
+        out[fact] = b.riccati()
+        b.close()
+    assert rel(out[0][0][0], out[1][0][0]) < 1e-12
+    assert rel(out[0][1][0], out[1][1][0]) < 1e-12
+    Qh, Rh, Sh = lq.augmented(qp, rho)
+    P, p, K, kff, G = lq.riccati(qp.A, qp.B, qp.c, Qh, Rh, Sh, np.zeros_like(qp.q), np.zeros_like(qp.r))
+    assert rel(out[0][0][0], P) < 1e-8 and rel(out[0][1][0], K) < 1e-8
+    b = batch([qp], precision=native.GPUSLS_FP32, cluster=cluster, rho=rho)
+    Ps, Ks = b.riccati()
+    b.close()
+    assert rel(Ps[0], P) < 1e-4 and rel(Ks[0], K) < 1e-4
+
+
+def test_fp32_stall_rule_converges(lib):
+    """A 75D QP of the serving mix whose FP32 dual residual stays just above
+    the 1e-5 eps floor: the stall rule runs the FP64 KKT gate (and refines)
+    instead of iterating to max_iter."""
+    qp = W.serving_mix(0, 256)[11]
+    b = batch([qp], precision=native.GPUSLS_FP32, cluster=8, max_refine=3, max_iter=6000)
+    r = b.solve()
+    assert r.info[0]["status"] == native.GPUSLS_OK, r.info[0]
+    assert r.info[0]["iters"] < 6000 and r.info[0]["kkt"] <= 1e-4
+    assert kkt.kkt_residual(qp, r.dx[0], r.du[0], r.lam[0]) <= 1.5e-4
+    b.close()
+
+
+def test_cluster_sizes_give_the_same_fp64_iterates(lib):
+    """The cluster sizes the autotuner can pick at this size run the same
+    ADMM: 6 fixed FP64 iterations on the 61D problem agree to 1e-9."""
+    qp = W.quadruped_61d(0)
+    ref = None
+    for cs in (4, 5, 6, 7, 8):   # shared memory per CTA limits FP64 at N = 100 to the larger clusters
+        b = batch([qp], precision=native.GPUSLS_FP64, cluster=cs, sigma=0, fixed_iters=6, rho=0.1)
+        r = b.solve()
+        if ref is None:
+            ref = r.dx[0].copy()
+        assert rel(r.dx[0], ref) < 1e-9, cs
+        b.close()
+
+
 def test_invalid_dims_rejected(lib):
     qp = W.random_general(0, 3, 2, 5, 2, 1)
     qp.A = np.zeros((5, 81, 81))
