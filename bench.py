@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 METRIC = "ms/QP solve to 1e-4 KKT residual (61D, N=100): learned+batched vs plain ADMM"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
-TRAFFIC_PER_QP_ITER = 6.71e6   # bytes, ncu dram__bytes_read+write per QP-iteration (61D, N=100, FP32)
+TRAFFIC_PER_QP_ITER = 6.17e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6)
 
 
 def parse():
@@ -306,7 +306,7 @@ def extra_workloads(args, qps, hb, stream, dev, oracle_sols):
 def profile_case(args):
     """Small fixed workloads for ncu captures (inputs larger than L2, a few
     hundred MB on the device):
-      iter      32 quadruped-shaped QPs (FP32), factorized by a first launch;
+      iter      32 quadruped-shaped QPs (FP32, cluster 6), factorized by a first launch;
                 launches 2 and 3 run 100 cached ADMM iterations each (no
                 refactor), so a capture of launch 2 is the iteration alone;
       refactor  the same batch, three launches that each refactor and run one
@@ -324,7 +324,8 @@ def profile_case(args):
     fam = W.family(0)
     if args.case in ("iter", "refactor"):
         qps = [fam.instance(100000 + i) for i in range(32)]
-        s = native.default_settings(precision=native.GPUSLS_FP32, cluster=8, sigma=0, fixed_iters=1)
+        # the launch shape the autotuner picks for the bench's batch (cluster 6)
+        s = native.default_settings(precision=native.GPUSLS_FP32, cluster=6, sigma=0, fixed_iters=1)
         if args.case == "iter":
             s.fixed_iters = 100
         qb = QPBatch(qps, s)
