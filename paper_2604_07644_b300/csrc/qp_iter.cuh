@@ -395,23 +395,38 @@ __device__ void full_xu(Ctx<T>& c) {
   QPDesc& d = *c.d;
   const int nx = d.nx, nu = d.nu, ldx = d.ldx, ldu = d.ldu, ldf = d.ldf, msz = c.msz, L = c.L, s = c.s;
   const T *K = TP<T>(d.K), *KSig = TP<T>(d.KSig), *Sig = TP<T>(d.Sig), *SigN = TP<T>(d.SigN);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!c.active) return;
+  // one thread per output, each walking its own row: a warp keeps 32 rows'
+  // loads in flight (a warp per row keeps one)
+  const int t = threadIdx.x;
   const int nxr = (L + (c.last ? 1 : 0)) * nx;
-  for (int pr = w; pr < nxr; pr += NT / 32) {
+  for (int pr = t; pr < nxr; pr += NT) {
     const int li = pr / nx, j = pr - li * nx;
     T v = T(0);
     if (!c.first) {
       const T* Sr = (li < L) ? Sig + (size_t)(s + li) * msz + j * ldx : SigN + j * ldx;
-      v = warp_dot(Sr, c.xs, nx);
+      T a0 = T(0), a1 = T(0);
+      int k = 0;
+      for (; k + 1 < nx; k += 2) {
+        a0 = fma(Sr[k], c.xs[k], a0);
+        a1 = fma(Sr[k + 1], c.xs[k + 1], a1);
+      }
+      if (k < nx) a0 = fma(Sr[k], c.xs[k], a0);
+      v = a0 + a1;
     }
-    if (lane == 0) c.dS[(size_t)li * ldx + j] = c.xS[(size_t)li * ldf + j] + v;
+    c.dS[(size_t)li * ldx + j] = c.xS[(size_t)li * ldf + j] + v;
   }
-  for (int pr = w; pr < L * nu; pr += NT / 32) {
+  for (int pr = t; pr < L * nu; pr += NT) {
     const int li = pr / nu, a = pr - li * nu, i = s + li;
-    T v = warp_dot(K + (size_t)i * nu * ldx + a * ldx, c.xS + (size_t)li * ldf, nx);
-    if (!c.first) v += warp_dot(KSig + (size_t)i * nu * ldx + a * ldx, c.xs, nx);
-    if (lane == 0) c.uS[li * ldu + a] = v + c.xS[(size_t)li * ldf + nx + a];
+    const T* Kr = K + (size_t)i * nu * ldx + a * ldx;
+    const T* KSr = KSig + (size_t)i * nu * ldx + a * ldx;
+    const T* lx = c.xS + (size_t)li * ldf;
+    T a0 = T(0), a1 = T(0);
+    for (int k = 0; k < nx; ++k) {
+      a0 = fma(Kr[k], lx[k], a0);
+      if (!c.first) a1 = fma(KSr[k], c.xs[k], a1);
+    }
+    c.uS[li * ldu + a] = a0 + a1 + c.xS[(size_t)li * ldf + nx + a];
   }
   __syncthreads();
 }
