@@ -309,10 +309,17 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
       }
     }
     if (c.last) {
-      for (int rr = w; rr < nf; rr += NT / 32) {
-        T v = warp_dot(CN + rr * ldx, c.xS + (size_t)L * ldf, nx);
-        if (!c.first) v += warp_dot(CNSig + rr * ldx, c.xs, nx);
-        if (lane == 0) c.vS[L * nc + rr] = v;
+      // terminal rows, one thread each (loads of all rows in flight at once)
+      for (int rr = t; rr < nf; rr += NT) {
+        const T* Cr = CN + rr * ldx;
+        const T* Sr = CNSig + rr * ldx;
+        const T* xN = c.xS + (size_t)L * ldf;
+        T a0 = T(0), a1 = T(0);
+        for (int k = 0; k < nx; ++k) {
+          a0 = fma(Cr[k], xN[k], a0);
+          if (!c.first) a1 = fma(Sr[k], c.xs[k], a1);
+        }
+        c.vS[L * nc + rr] = a0 + a1;
       }
     }
     __syncthreads();
@@ -536,61 +543,6 @@ __device__ void write_outputs(Ctx<T>& c, T rho) {
 // FP64 KKT residual of (ox, ou, olam) -- see include/gpusls.h for the
 // definition.  Every CTA evaluates the stage-local parts of its chunk; CTA 0
 // then runs the costate recursion mu_k = g_k + A_k^T mu_{k+1} sequentially.
-// FP64 products of the KKT check on the caller's unpadded arrays (global
-// memory), by the whole CTA; each ends with a barrier.
-// Column sweep: y[o] (+)= sum_{k<m} M[k ld + o] x[k], o < n.  Thread (o, g)
-// sums the rows of group g with independent loads (coalesced across o);
-// part: shared, >= NT doubles.
-__device__ inline void kkt_colsweep(const double* M, int ld, int m, int n, const double* x, double* y, bool acc,
-                                    double* part) {
-  const int t = threadIdx.x;
-  if (n > 0) {
-    const int G = NT / n;
-    const int Rg = (m + G - 1) / G;
-    const int o = t % n, g = t / n;
-    if (g < G) {
-      const int r0 = min(m, g * Rg), r1 = min(m, r0 + Rg);
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int k = r0;
-      for (; k + 3 < r1; k += 4) {
-        a0 = fma(M[(size_t)k * ld + o], x[k], a0);
-        a1 = fma(M[(size_t)(k + 1) * ld + o], x[k + 1], a1);
-        a2 = fma(M[(size_t)(k + 2) * ld + o], x[k + 2], a2);
-        a3 = fma(M[(size_t)(k + 3) * ld + o], x[k + 3], a3);
-      }
-      for (; k < r1; ++k) a0 = fma(M[(size_t)k * ld + o], x[k], a0);
-      part[g * n + o] = (a0 + a1) + (a2 + a3);
-    }
-    __syncthreads();
-    if (t < n) {
-      double s2 = acc ? y[t] : 0.0;
-      for (int gg = 0; gg < G; ++gg) s2 += part[gg * n + t];
-      y[t] = s2;
-    }
-  }
-  __syncthreads();
-}
-
-// Row dots: y[j] (+)= sum_{k<n} M[j ld + k] x[k], j < rows; a warp takes four
-// rows at a time (lanes along k), so four rows' loads are in flight together.
-__device__ inline void kkt_rowdots(const double* M, int ld, int rows, int n, const double* x, double* y, bool acc) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  for (int j0 = 4 * w; j0 < rows; j0 += 4 * (NT / 32)) {
-    double s4[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int k = l; k < n; k += 32) {
-      const double xk = x[k];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (j0 + q < rows) s4[q] = fma(M[(size_t)(j0 + q) * ld + k], xk, s4[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) s4[q] = warp_sum(s4[q]);
-    const double mine = l == 0 ? s4[0] : (l == 1 ? s4[1] : (l == 2 ? s4[2] : s4[3]));
-    if (l < 4 && j0 + l < rows) y[j0 + l] = (acc ? y[j0 + l] : 0.0) + mine;
-  }
-  __syncthreads();
-}
-
 // FP64 KKT residual of the outputs written by write_outputs (see the
 // library's residual definition): dynamics, bound violation, u-stationarity
 // after costate recovery and complementarity, max over the cluster.
@@ -603,16 +555,15 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
   double* xn = xv + 96;
   double* uv = xn + 96;
   double* lv = uv + 96;
-  double* mu = lv + 96;
-  double* mu2 = mu + 96;
-  double* gv = mu2 + 96;
-  double* ax = gv + 96;
-  double* hv = ax + 96;
-  double* vv = hv + 96;
-  // partial sums (NT doubles) after the vectors: everything the check uses
-  // lies in the first 9.7 KB of the union region (>= 67 KB), clear of the
-  // sweep and gather buffers that may follow a small ring there
-  double* part = vv + 96;
+  double* qx = lv + 96;   // Q x
+  double* ax = qx + 96;   // A x
+  double* bu = ax + 96;   // B u
+  double* sx = bu + 96;   // S x
+  double* ru = sx + 96;   // R u
+  double* cx = ru + 96;   // C x
+  double* du = cx + 96;   // D u
+  double* gt = du + 96;   // C^T lam + S^T u
+  double* ht = gt + 96;   // D^T lam
   double dyn = 0.0, viol = 0.0, comp = 0.0, stat = 0.0;
   long long kt0 = c.prof ? clock64() : 0;
   cl.sync();   // outputs of every chunk visible
@@ -630,32 +581,60 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
       __syncthreads();
       const double* Qi = d.Q64 + (size_t)i * nx * nx;
       const double* Ci = term ? d.CN64 : d.C64 + (size_t)i * nc * nx;
-      // g_i = Q x + S^T u + C^T lam + q
-      kkt_rowdots(Qi, nx, nx, nx, xv, gv, false);
-      kkt_colsweep(Ci, nx, nr, nx, lv, gv, true, part);
-      if (!term) {
-        const double* Ai = d.A64 + (size_t)i * nx * nx;
-        const double* Bi = d.B64 + (size_t)i * nx * nu;
-        const double* Si = d.S64 + (size_t)i * nu * nx;
-        const double* Di = d.D64 + (size_t)i * nc * nu;
-        kkt_colsweep(Si, nx, nu, nx, uv, gv, true, part);
-        // dynamics A x + B u ; h_i = R u + S x + D^T lam + r ; rows C x + D u
-        kkt_rowdots(Ai, nx, nx, nx, xv, ax, false);
-        kkt_rowdots(Bi, nu, nx, nu, uv, ax, true);
-        kkt_rowdots(d.R64 + (size_t)i * nu * nu, nu, nu, nu, uv, hv, false);
-        kkt_colsweep(Di, nu, nc, nu, lv, hv, true, part);
-        kkt_rowdots(Si, nx, nu, nx, xv, hv, true);
-        kkt_rowdots(Di, nu, nc, nu, uv, vv, false);
-        kkt_rowdots(Ci, nx, nc, nx, xv, vv, true);
-        for (int j = t; j < nx; j += NT) dyn = fmax(dyn, fabs(xn[j] - ax[j] - d.b64[(size_t)i * nx + j]));
-        for (int a = t; a < nu; a += NT) d.kh[(size_t)i * nu + a] = hv[a] + d.r64[(size_t)i * nu + a];
-      } else {
-        kkt_rowdots(Ci, nx, nr, nx, xv, vv, false);
+      const double* Ai = d.A64 + (size_t)i * nx * nx;
+      const double* Bi = d.B64 + (size_t)i * nx * nu;
+      const double* Si = d.S64 + (size_t)i * nu * nx;
+      const double* Ri = d.R64 + (size_t)i * nu * nu;
+      const double* Di = d.D64 + (size_t)i * nc * nu;
+      // Every dot product of the stage is one work item walked by one thread
+      // (rows: Q x, A x, B u, S x, R u, C x, D u; columns: C^T lam + S^T u,
+      // D^T lam), so all their loads are in flight in one pass.
+      const int nrow = term ? nx + nr : 3 * nx + 2 * nu + nr + nc;
+      const int ncol = term ? nx : nx + nu;
+      for (int it = t; it < nrow + ncol; it += NT) {
+        const double* M;
+        const double* x;
+        int len, stride;
+        double* out;
+        if (it < nrow) {
+          int r = it;
+          stride = 1;
+          if (r < nx) { M = Qi + (size_t)r * nx; x = xv; len = nx; out = qx + r; }
+          else if (term) { r -= nx; M = Ci + (size_t)r * nx; x = xv; len = nx; out = cx + r; }
+          else if ((r -= nx) < nx) { M = Ai + (size_t)r * nx; x = xv; len = nx; out = ax + r; }
+          else if ((r -= nx) < nx) { M = Bi + (size_t)r * nu; x = uv; len = nu; out = bu + r; }
+          else if ((r -= nx) < nu) { M = Si + (size_t)r * nx; x = xv; len = nx; out = sx + r; }
+          else if ((r -= nu) < nu) { M = Ri + (size_t)r * nu; x = uv; len = nu; out = ru + r; }
+          else if ((r -= nu) < nr) { M = Ci + (size_t)r * nx; x = xv; len = nx; out = cx + r; }
+          else { r -= nr; M = Di + (size_t)r * nu; x = uv; len = nu; out = du + r; }
+        } else {
+          const int col = it - nrow;
+          if (col < nx) { M = Ci + col; stride = nx; x = lv; len = nr; out = gt + col; }
+          else { M = Di + (col - nx); stride = nu; x = lv; len = nc; out = ht + (col - nx); }
+        }
+        double a0 = 0.0, a1 = 0.0;
+        int k = 0;
+        for (; k + 1 < len; k += 2) {
+          a0 = fma(M[(size_t)k * stride], x[k], a0);
+          a1 = fma(M[(size_t)(k + 1) * stride], x[k + 1], a1);
+        }
+        if (k < len) a0 = fma(M[(size_t)k * stride], x[k], a0);
+        if (it >= nrow && it - nrow < nx && !term) {
+          // S^T u joins the column sum of C^T lam
+          const int col = it - nrow;
+          for (int q2 = 0; q2 < nu; ++q2) a1 = fma(Si[(size_t)q2 * nx + col], uv[q2], a1);
+        }
+        *out = a0 + a1;
       }
-      for (int j = t; j < nx; j += NT) d.kg[(size_t)i * nx + j] = gv[j] + d.q64[(size_t)i * nx + j];
+      __syncthreads();
+      for (int j = t; j < nx; j += NT) d.kg[(size_t)i * nx + j] = qx[j] + gt[j] + d.q64[(size_t)i * nx + j];
+      if (!term) {
+        for (int j = t; j < nx; j += NT) dyn = fmax(dyn, fabs(xn[j] - ax[j] - bu[j] - d.b64[(size_t)i * nx + j]));
+        for (int a = t; a < nu; a += NT) d.kh[(size_t)i * nu + a] = ru[a] + sx[a] + ht[a] + d.r64[(size_t)i * nu + a];
+      }
       for (int k = t; k < nr; k += NT) {
         const size_t gi = (size_t)i * nc + k;
-        const double v = vv[k], lo = d.lo64[gi], hi = d.hi64[gi], l = lv[k];
+        const double v = cx[k] + (term ? 0.0 : du[k]), lo = d.lo64[gi], hi = d.hi64[gi], l = lv[k];
         viol = fmax(viol, fmax(fmax(v - hi, lo - v), 0.0));
         double cp = 0.0;
         if (l > 0) cp = isfinite(hi) ? l * fabs(hi - v) : fabs(l);
@@ -688,6 +667,10 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
     const int o = t % no, g = t / no;
     const int r0 = min(nx, g * Rg), r1 = min(nx, r0 + Rg);
     const int per = nx * nx + nx * nu;   // doubles of A_i then B_i
+    // the stage scratch is dead here: the recursion reuses the region
+    double* mu = xv;
+    double* mu2 = xv + 96;
+    double* part = xv + 192;              // [G][no] partial sums
     double* pbuf = part + NT;
     const bool pre = (int)((pbuf - xv) + 2 * per) * 8 <= c.uni;
     auto issue = [&](int i, int k) {
