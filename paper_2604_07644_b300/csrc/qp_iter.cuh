@@ -53,13 +53,13 @@ __device__ inline void ring_advance(unsigned& slot, unsigned& par, unsigned dept
 // iteration runs to its end on stale data and the solve reports
 // GPUSLS_ERR_TIMEOUT).
 template <typename T, typename Src, typename Fn>
-__device__ void stream_blocks(Ctx<T>& c, int nblk, Src src, Fn f) {
+__device__ __forceinline__ void stream_blocks(Ctx<T>& c, int nblk, Src src, Fn f) {
   const unsigned depth = (unsigned)c.d->depth;
   const size_t slot_el = (size_t)c.d->slot;
   T* const ring = c.ring;
   unsigned long long* const bar = c.bar;
   int* const flag = c.flag;
-  unsigned long long* const prof = c.prof;
+  unsigned long long* const prof = threadIdx.x == 0 ? c.prof : nullptr;
   const bool issuer = threadIdx.x == 0;
   fence_proxy_async();     // earlier generic accesses of the ring region come first
   __syncthreads();
@@ -89,10 +89,12 @@ __device__ void stream_blocks(Ctx<T>& c, int nblk, Src src, Fn f) {
     dead = flag[RING_FLAG] != 0;
     ring_advance(ws, wp, depth);
   }
-  c.ws = ws;
-  c.wp = wp;
-  c.inflight = inflight;
-  c.ipar = ipar;
+  if (issuer) {   // every thread holds the same ws, wp; inflight, ipar are the issuer's
+    c.ws = ws;
+    c.wp = wp;
+    c.inflight = inflight;
+    c.ipar = ipar;
+  }
 }
 
 // Before the CTA exits: if a ring wait gave up, the issuing thread waits
@@ -103,6 +105,53 @@ __device__ void ring_drain(Ctx<T>& c) {
   if (threadIdx.x != 0 || c.flag[RING_FLAG] == 0) return;
   for (unsigned sl = 0; sl < (unsigned)c.d->depth; ++sl)
     if ((c.inflight >> sl) & 1u) mbar_wait(&c.bar[sl], (c.ipar >> sl) & 1u, RING_WAIT_LIMIT);
+  if (c.bulk_inflight) mbar_wait(&c.bar[BULK_BAR], c.bpar, RING_WAIT_LIMIT);
+}
+
+// ---------------------------------------------------------------------------
+// Whole-region copies.  The chunk-boundary corrections stream runs of
+// contiguous blocks with little arithmetic per block, which the ring serves one
+// slot at a time; here as many blocks as the ring region holds come in one
+// bulk copy on a barrier of their own, so a run costs one copy latency (the
+// first one issued before the cluster barrier that precedes its use).  The
+// ring must be idle: no ring copy in flight.  Both calls are made by every
+// thread of the CTA and contain a CTA barrier.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline int bulk_capacity(const Ctx<T>& c) {   // elements
+  return c.d->depth * c.d->slot;
+}
+
+// Orders every thread's earlier accesses of the ring region before the copy of
+// n_el elements from src (16-byte aligned, n_el * sizeof(T) a multiple of 16,
+// n_el <= bulk_capacity) into it; thread 0 issues the copy.
+template <typename T>
+__device__ void bulk_issue(Ctx<T>& c, const T* src, int n_el) {
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0 && c.flag[RING_FLAG] == 0) {
+    bulk_g2s(c.ring, src, (unsigned)(n_el * (int)sizeof(T)), &c.bar[BULK_BAR]);
+    c.bulk_inflight = 1;
+  }
+}
+
+// Waits (bounded) for the copy of the last bulk_issue.  A wait that gives up
+// sets flag[RING_FLAG], as in the ring.  Returns after a CTA barrier.
+template <typename T>
+__device__ void bulk_wait(Ctx<T>& c) {
+  const bool issued = c.flag[RING_FLAG] == 0;   // the flag is only set by waits, none since the issue
+  bool ok = true;
+  if (issued) {
+    const long long tw = (threadIdx.x == 0 && c.prof) ? clock64() : 0;
+    ok = mbar_wait(&c.bar[BULK_BAR], c.bpar, RING_WAIT_LIMIT);
+    if (!ok) c.flag[RING_FLAG] = 1;
+    if (threadIdx.x == 0 && c.prof) c.prof[PH_RINGWAIT] += (unsigned long long)(clock64() - tw);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && issued && ok) {
+    c.bpar ^= 1u;
+    c.bulk_inflight = 0;
+  }
 }
 
 struct Partials {
@@ -133,6 +182,34 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
   int bws, fws, cds;
   bundle_sizes(nx, nu, nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
   const int nrows = own_rows(c);
+  // The chunk-boundary corrections in whole-region rounds (bulk_issue):
+  // P3: nr_th rounds of Theta blocks (cap_bk per round), then nr_fp rounds of
+  //     FPi stages (gs_fp per round);
+  // P5: nr_xi rounds of Xi blocks, then nr_ck rounds of CKSig stages.
+  const int cap_el = bulk_capacity(c);
+  const int cap_bk = cap_el / msz;   // >= 1: a ring slot holds a Theta or Xi block
+  const int m0 = c.rank + 2, nb_th = max(0, d.nch - m0), nr_th = (nb_th + cap_bk - 1) / cap_bk;
+  const int per_fp = nx * ldu, gs_fp = min(min(cap_el / per_fp, NT / nu), max(L, 1));
+  const int nr_fp = (L + gs_fp - 1) / gs_fp;
+  const int nb_xi = max(0, c.rank - 1), nr_xi = (nb_xi + cap_bk - 1) / cap_bk;
+  const int ldc = d.ldc, per_ck = nx * ldc;
+  const int gs_ck = nc > 0 ? min(min(cap_el / per_ck, NT / nc), max(L, 1)) : 1;
+  const int nr_ck = nc > 0 ? (L + gs_ck - 1) / gs_ck : 0;
+  T lo_a = T(0), hi_a = T(0), lo_b = T(0), hi_b = T(0);   // bounds of the first two own rows (P5)
+  auto p3_src = [&](int r) -> const T* {
+    return r < nr_th ? Theta + (size_t)(c.rank * MAXCS + m0 + r * cap_bk) * msz
+                     : FPi + (size_t)(s + (r - nr_th) * gs_fp) * per_fp;
+  };
+  auto p3_len = [&](int r) -> int {
+    return r < nr_th ? min(cap_bk, nb_th - r * cap_bk) * msz : min(gs_fp, L - (r - nr_th) * gs_fp) * per_fp;
+  };
+  auto p5_src = [&](int r) -> const T* {
+    return r < nr_xi ? Xi + (size_t)(c.rank * MAXCS + r * cap_bk) * msz
+                     : CKSig + (size_t)(s + (r - nr_xi) * gs_ck) * per_ck;
+  };
+  auto p5_len = [&](int r) -> int {
+    return r < nr_xi ? min(cap_bk, nb_xi - r * cap_bk) * msz : min(gs_ck, L - (r - nr_xi) * gs_ck) * per_ck;
+  };
 
   // P1: omega = rho (y - z) into the stacked rows; boundary of the backward
   // chain (p_N = q^_N = q_N + C_N^T omega_N for the last chunk, 0 otherwise).
@@ -172,6 +249,8 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
           });
     }
     for (int j = t; j < nx; j += NT) c.slotL[j] = c.lS[j];
+    // the ring is idle: start the first copy of P3 before the cluster barrier
+    if (!c.last) bulk_issue<T>(c, p3_src(0), p3_len(0));
     prof_mark(c, PH_BWD);
   }
   cl.sync();
@@ -187,44 +266,42 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
         const int m = e2 / nx;
         gath[e2] = cl.map_shared_rank(c.slotL, c.rank + 1 + m)[e2 - m * nx];
       }
-      __syncthreads();
-      // p_e = l_{rank+1} + sum_m Theta_{rank,m} l_m over m = rank+2 .., one
-      // split sweep accumulated across the streamed Theta blocks
+      // p_e = l_{rank+1} + sum_m Theta_{rank,m} l_m over m = rank+2 ..: the
+      // Theta blocks of a row are contiguous, so a round of k of them is one
+      // tall (k nx) x nx block swept against the stacked l_m
       constexpr int VW = Vec16<T>::W;
-      const int m0 = c.rank + 2, nb = d.nch - m0;
-      const SweepPlan sp = sweep_plan<T>(nx, nx, ldx, 0, ldx, 0);
       T acc[VW];
 #pragma unroll
       for (int e = 0; e < VW; ++e) acc[e] = T(0);
-      stream_blocks<T>(
-          c, nb, [&](int b) { return Blk<T>{Theta + (size_t)(c.rank * MAXCS + m0 + b) * msz, msz * (int)sizeof(T)}; },
-          [&](int b, const T* S) { sweep_partial<T>(sp, S, gath + (size_t)(b + 1) * nx, acc); });
+      for (int r = 0; r < nr_th; ++r) {
+        if (r > 0) bulk_issue<T>(c, p3_src(r), p3_len(r));
+        bulk_wait<T>(c);   // also orders the gather before the sweep
+        const int b0 = r * cap_bk, k = min(cap_bk, nb_th - b0);
+        const SweepPlan sp = sweep_plan<T>(k * nx, nx, ldx, 0, ldx, 0);
+        sweep_partial<T>(sp, c.ring, gath + (size_t)(b0 + 1) * nx, acc);
+      }
+      // the first FPi round's copy overlaps the reduction (it was the
+      // prefetched round when there are no Theta rounds)
+      if (nr_th > 0) bulk_issue<T>(c, p3_src(nr_th), p3_len(nr_th));
       {
+        const SweepPlan sp = sweep_plan<T>(nx, nx, ldx, 0, ldx, 0);
         const T y = sweep_reduce<T>(sp, acc, c.swp);
         if (t < nx) c.pe[t] = gath[t] + y;
-        __syncthreads();
       }
-      // k_i = k~_i + FPi_i p_e for own stages, Gs stages per streamed block
+      // k_i = k~_i + FPi_i p_e for own stages, gs_fp stages per round
       const int per = nx * ldu;   // FPi_i^T
-      const int Gs = min(max(1, d.slot / per), NT / nu);
-      const int nbk = (L + Gs - 1) / Gs;
-      const SweepPlan fp = sweep_plan_batched<T>(nx, nu, ldu, Gs, per);
       T* const xS = c.xS;
       const T* const ktS = c.ktS;
-      const T* const pe = c.pe;
-      T* const swp = c.swp;
       const int ls_t = t / nu, a_t = t - ls_t * nu;
-      stream_blocks<T>(
-          c, nbk,
-          [&](int b) {
-            const int n_st = min(Gs, L - b * Gs);
-            return Blk<T>{FPi + (size_t)(s + b * Gs) * per, n_st * per * (int)sizeof(T)};
-          },
-          [&](int b, const T* S) {
-            const T y = sweep_run<T>(fp, S, pe, swp);
-            const int li = b * Gs + ls_t;
-            if (t < Gs * nu && li < L) xS[(size_t)li * ldf + nx + a_t] = ktS[li * ldu + a_t] + y;
-          });
+      for (int r = 0; r < nr_fp; ++r) {
+        if (r > 0) bulk_issue<T>(c, p3_src(nr_th + r), p3_len(nr_th + r));
+        bulk_wait<T>(c);   // also orders p_e before the sweep
+        const int n_st = min(gs_fp, L - r * gs_fp);
+        const SweepPlan fp = sweep_plan_batched<T>(nx, nu, ldu, n_st, per);
+        const T y = sweep_run<T>(fp, c.ring, c.pe, c.swp);
+        const int li = r * gs_fp + ls_t;
+        if (t < n_st * nu) xS[(size_t)li * ldf + nx + a_t] = ktS[li * ldu + a_t] + y;
+      }
     } else {
       for (int e2 = t; e2 < L * nu; e2 += NT) {
         const int li = e2 / nu, a = e2 - li * nu;
@@ -252,6 +329,17 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
           });
     }
     for (int j = t; j < nx; j += NT) c.slotX[j] = c.xS[(size_t)L * ldf + j];
+    // the ring is idle: start the first copy of P5 before the cluster barrier
+    if (!c.first && nr_xi + nr_ck > 0) bulk_issue<T>(c, p5_src(0), p5_len(0));
+    // the bounds of this thread's first two rows, loaded ahead of the projection
+    if (t < nrows) {
+      lo_a = lo[s * nc + t];
+      hi_a = hi[s * nc + t];
+    }
+    if (t + NT < nrows) {
+      lo_b = lo[s * nc + t + NT];
+      hi_b = hi[s * nc + t + NT];
+    }
     prof_mark(c, PH_FWD);
   }
   cl.sync();
@@ -260,75 +348,70 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
   // projection and scaled dual update.
   if (c.active) {
     if (!c.first) {
-      // the earlier chunks' end states lx_m (m = rank-1 .. 0), gathered in one
-      // round of distributed shared memory reads: gath row j = chunk rank-1-j
-      const int near = c.rank;
+      // the earlier chunks' end states lx_m (m = 0 .. rank-1), gathered in one
+      // round of distributed shared memory reads: gath row m = chunk m
       T* const gath = c.gath;
-      for (int e2 = t; e2 < near * nx; e2 += NT) {
-        const int j = e2 / nx;
-        gath[e2] = cl.map_shared_rank(c.slotX, c.rank - 1 - j)[e2 - j * nx];
+      for (int e2 = t; e2 < c.rank * nx; e2 += NT) {
+        const int m = e2 / nx;
+        gath[e2] = cl.map_shared_rank(c.slotX, m)[e2 - m * nx];
       }
-      __syncthreads();
-      // x_s = lx_{rank-1} + sum_m Xi_{rank,m} lx_m over m = rank-2 .. 0
+      // x_s = lx_{rank-1} + sum_m Xi_{rank,m} lx_m over m = 0 .. rank-2, in
+      // tall rounds of contiguous Xi blocks as in P3
       constexpr int VW = Vec16<T>::W;
-      const int nb = c.rank - 1;
-      const SweepPlan sp = sweep_plan<T>(nx, nx, ldx, 0, ldx, 0);
       T acc[VW];
 #pragma unroll
       for (int e = 0; e < VW; ++e) acc[e] = T(0);
-      stream_blocks<T>(
-          c, nb, [&](int b) { return Blk<T>{Xi + (size_t)(c.rank * MAXCS + (c.rank - 2 - b)) * msz, msz * (int)sizeof(T)}; },
-          [&](int b, const T* S) { sweep_partial<T>(sp, S, gath + (size_t)(b + 1) * nx, acc); });
+      for (int r = 0; r < nr_xi; ++r) {
+        if (r > 0) bulk_issue<T>(c, p5_src(r), p5_len(r));
+        bulk_wait<T>(c);   // also orders the gather before the sweep
+        const int b0 = r * cap_bk, k = min(cap_bk, nb_xi - b0);
+        const SweepPlan sp = sweep_plan<T>(k * nx, nx, ldx, 0, ldx, 0);
+        sweep_partial<T>(sp, c.ring, gath + (size_t)b0 * nx, acc);
+      }
+      if (nr_xi > 0 && nr_ck > 0) bulk_issue<T>(c, p5_src(nr_xi), p5_len(nr_xi));
       {
+        const SweepPlan sp = sweep_plan<T>(nx, nx, ldx, 0, ldx, 0);
         const T y = sweep_reduce<T>(sp, acc, c.swp);
-        if (t < nx) c.xs[t] = gath[t] + y;
-        __syncthreads();
+        if (t < nx) c.xs[t] = gath[(size_t)(c.rank - 1) * nx + t] + y;
       }
-      // v_i += CKSig_i x_s for own stages, Gs stages per streamed block
-      const int ldc = d.ldc;
-      const int per = nx * ldc;   // CKSig_i^T
-      if (nc > 0) {
-        const int Gs = min(max(1, d.slot / per), NT / nc);
-        const int nbk = (L + Gs - 1) / Gs;
-        const SweepPlan cp = sweep_plan_batched<T>(nx, nc, ldc, Gs, per);
-        T* const vS = c.vS;
-        const T* const xs = c.xs;
-        T* const swp = c.swp;
-        const int ls_t = t / nc, r_t = t - ls_t * nc;
-        stream_blocks<T>(
-            c, nbk,
-            [&](int b) {
-              const int n_st = min(Gs, L - b * Gs);
-              return Blk<T>{CKSig + (size_t)(s + b * Gs) * per, n_st * per * (int)sizeof(T)};
-            },
-            [&](int b, const T* S) {
-              const T y = sweep_run<T>(cp, S, xs, swp);
-              const int li = b * Gs + ls_t;
-              if (t < Gs * nc && li < L) vS[li * nc + r_t] += y;
-            });
+      // v_i += CKSig_i x_s for own stages, gs_ck stages per round
+      T* const vS = c.vS;
+      const int ls_t = nc > 0 ? t / nc : 0, r_t = t - ls_t * nc;
+      for (int r = 0; r < nr_ck; ++r) {
+        if (r > 0) bulk_issue<T>(c, p5_src(nr_xi + r), p5_len(nr_xi + r));
+        bulk_wait<T>(c);   // also orders x_s before the sweep
+        const int n_st = min(gs_ck, L - r * gs_ck);
+        const SweepPlan cp = sweep_plan_batched<T>(nx, nc, ldc, n_st, per_ck);
+        const T y = sweep_run<T>(cp, c.ring, c.xs, c.swp);
+        const int li = r * gs_ck + ls_t;
+        if (t < n_st * nc) vS[li * nc + r_t] += y;
       }
+      if (nr_ck == 0) __syncthreads();   // x_s before the terminal rows
     }
     if (c.last) {
-      // terminal rows, one thread each (loads of all rows in flight at once)
-      for (int rr = t; rr < nf; rr += NT) {
+      // terminal rows, one warp each
+      const T* xN = c.xS + (size_t)L * ldf;
+      for (int rr = w; rr < nf; rr += NT / 32) {
         const T* Cr = CN + rr * ldx;
         const T* Sr = CNSig + rr * ldx;
-        const T* xN = c.xS + (size_t)L * ldf;
-        T a0 = T(0), a1 = T(0);
-        for (int k = 0; k < nx; ++k) {
-          a0 = fma(Cr[k], xN[k], a0);
-          if (!c.first) a1 = fma(Sr[k], c.xs[k], a1);
+        T a = T(0);
+        for (int k = lane; k < nx; k += 32) {
+          a = fma(Cr[k], xN[k], a);
+          if (!c.first) a = fma(Sr[k], c.xs[k], a);
         }
-        c.vS[L * nc + rr] = a0 + a1;
+        a = warp_sum(a);
+        if (lane == 0) c.vS[L * nc + rr] = a;
       }
     }
     __syncthreads();
     T rp = T(0), vm = T(0), zm = T(0);
-    for (int lr = t; lr < nrows; lr += NT) {
+    for (int lr = t, k2 = 0; lr < nrows; lr += NT, ++k2) {
       const int gi = s * nc + lr;
       const T v = c.vS[lr];
       const T zo = c.zS[lr], yo = c.yS[lr];
-      const T zn = fmin(fmax(v + yo, lo[gi]), hi[gi]);
+      const T lo_r = k2 == 0 ? lo_a : (k2 == 1 ? lo_b : lo[gi]);
+      const T hi_r = k2 == 0 ? hi_a : (k2 == 1 ? hi_b : hi[gi]);
+      const T zn = fmin(fmax(v + yo, lo_r), hi_r);
       c.yS[lr] = yo + v - zn;
       c.zS[lr] = zn;
       c.wS[lr] = zn - zo;
@@ -728,7 +811,7 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
       __syncthreads();
     }
   }
-  if (c.prof) {
+  if (threadIdx.x == 0 && c.prof) {
     c.prof[PH_KKT_STAGES] += (unsigned long long)(kt1 - kt0);
     c.prof[PH_KKT_SYNC] += (unsigned long long)(kt2 - kt1);
     c.prof[PH_KKT_COSTATE] += (unsigned long long)(clock64() - kt2);

@@ -106,6 +106,7 @@ struct SmemLayout {
 };
 
 constexpr int MAX_RING = 8;   // ring slots (mbarriers) at most
+constexpr int BULK_BAR = MAX_RING - 1;   // mbarrier of the whole-region copies (ring depth < BULK_BAR)
 constexpr int RING_FLAG = 8;  // index in the shared flag[] array: a ring wait gave up
 constexpr int RING_WAIT_LIMIT = 1 << 22;   // polls of one bulk-copy completion before giving up
 
@@ -223,12 +224,14 @@ struct Ctx {
   unsigned long long* bar;   // ring mbarriers, one per slot
   T* swp;                    // sweep partials
   T* gath;                   // chunk-boundary vectors gathered from the other CTAs
-  unsigned ws, wp;           // ring: next slot to consume and its phase parity (same in every thread)
+  unsigned ws, wp;           // ring: next slot to consume and its phase parity
   unsigned inflight, ipar;   // issuing thread: slots with a copy not yet seen complete, their parities
+  unsigned bpar;             // whole-region copies: parity of the next completion of bar[BULK_BAR]
+  int bulk_inflight;         // a whole-region copy was issued and not yet seen complete
   T* scr;   // per-CTA global scratch: 6 matrices nx x ldx
   int msz;  // nx * ldx
   int uni;  // bytes of the union region at ring
-  unsigned long long* prof;  // non-null only in thread 0 of each CTA of QP 0 when profiling
+  unsigned long long* prof;  // non-null in each CTA of QP 0 when profiling (thread 0 records)
   bool tc;                   // factorization products in TF32 on the tensor cores
   long long t_last;
 };
@@ -239,7 +242,7 @@ enum Phase { PH_P1 = 0, PH_BWD, PH_SYNC1, PH_P3, PH_FWD, PH_SYNC2, PH_P5, PH_CHE
              PH_FA1, PH_FA2, PH_FA3, PH_FC1, PH_FC2, PH_FC3, PH_FC4, PH_FC5, PH_COUNT };
 template <typename T>
 __device__ inline void prof_mark(Ctx<T>& c, int ph) {
-  if (c.prof) {
+  if (threadIdx.x == 0 && c.prof) {
     const long long now = clock64();
     c.prof[ph] += (unsigned long long)(now - c.t_last);
     c.t_last = now;

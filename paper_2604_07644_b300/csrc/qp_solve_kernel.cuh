@@ -31,58 +31,65 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
 
   const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.nch, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
                                      (int)sizeof(T), d.fact);
-  Ctx<T> c;
-  c.d = &d;
-  c.rank = rank;
-  c.cs = cs;
-  c.s = min(rank * d.Lc, d.N);
-  c.e = min((rank + 1) * d.Lc, d.N);
-  c.L = c.e - c.s;
-  c.active = rank < d.nch;
-  c.first = rank == 0;
-  c.last = rank == d.nch - 1;
-  c.gemm = reinterpret_cast<T*>(smem + lay.gemm);
-  c.gj = reinterpret_cast<T*>(smem + lay.gj);
-  c.gjbuf = reinterpret_cast<T*>(smem + lay.gjbuf);
-  c.ring = reinterpret_cast<T*>(smem + lay.ring);
-  c.zS = reinterpret_cast<T*>(smem + lay.z);
-  c.yS = reinterpret_cast<T*>(smem + lay.y);
-  c.wS = reinterpret_cast<T*>(smem + lay.w);
-  c.lS = reinterpret_cast<T*>(smem + lay.l);
-  c.xS = reinterpret_cast<T*>(smem + lay.x);
-  c.ktS = reinterpret_cast<T*>(smem + lay.kt);
-  c.vS = reinterpret_cast<T*>(smem + lay.v);
-  c.dS = reinterpret_cast<T*>(smem + lay.d);
-  c.uS = reinterpret_cast<T*>(smem + lay.u);
-  c.pe = reinterpret_cast<T*>(smem + lay.pe);
-  c.xs = reinterpret_cast<T*>(smem + lay.xs);
-  c.slotL = reinterpret_cast<T*>(smem + lay.slotL);
-  c.slotX = reinterpret_cast<T*>(smem + lay.slotX);
-  c.tmp1 = reinterpret_cast<T*>(smem + lay.tmp1);
-  c.tmp2 = reinterpret_cast<T*>(smem + lay.tmp2);
-  c.tmp3 = reinterpret_cast<T*>(smem + lay.tmp3);
-  c.red = reinterpret_cast<T*>(smem + lay.red);
-  c.part = reinterpret_cast<double*>(smem + lay.part);
-  c.perm = reinterpret_cast<int*>(smem + lay.perm);
-  c.flag = reinterpret_cast<int*>(smem + lay.flag);
-  c.bar = reinterpret_cast<unsigned long long*>(smem + lay.bar);
-  c.swp = reinterpret_cast<T*>(smem + lay.swp);
-  c.gath = reinterpret_cast<T*>(smem + lay.gath);
-  c.ws = c.wp = 0;
-  c.inflight = c.ipar = 0;
-  if (threadIdx.x == 0) {
+  // One context per CTA in shared memory, filled by thread 0: every thread
+  // reads the same fields, and a per-thread copy would sit in local memory
+  // that the L1 left beside two CTAs' shared memory cannot hold.
+  __shared__ Ctx<T> csh;
+  Ctx<T>& c = csh;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    c.d = &d;
+    c.rank = rank;
+    c.cs = cs;
+    c.s = min(rank * d.Lc, d.N);
+    c.e = min((rank + 1) * d.Lc, d.N);
+    c.L = c.e - c.s;
+    c.active = rank < d.nch;
+    c.first = rank == 0;
+    c.last = rank == d.nch - 1;
+    c.gemm = reinterpret_cast<T*>(smem + lay.gemm);
+    c.gj = reinterpret_cast<T*>(smem + lay.gj);
+    c.gjbuf = reinterpret_cast<T*>(smem + lay.gjbuf);
+    c.ring = reinterpret_cast<T*>(smem + lay.ring);
+    c.zS = reinterpret_cast<T*>(smem + lay.z);
+    c.yS = reinterpret_cast<T*>(smem + lay.y);
+    c.wS = reinterpret_cast<T*>(smem + lay.w);
+    c.lS = reinterpret_cast<T*>(smem + lay.l);
+    c.xS = reinterpret_cast<T*>(smem + lay.x);
+    c.ktS = reinterpret_cast<T*>(smem + lay.kt);
+    c.vS = reinterpret_cast<T*>(smem + lay.v);
+    c.dS = reinterpret_cast<T*>(smem + lay.d);
+    c.uS = reinterpret_cast<T*>(smem + lay.u);
+    c.pe = reinterpret_cast<T*>(smem + lay.pe);
+    c.xs = reinterpret_cast<T*>(smem + lay.xs);
+    c.slotL = reinterpret_cast<T*>(smem + lay.slotL);
+    c.slotX = reinterpret_cast<T*>(smem + lay.slotX);
+    c.tmp1 = reinterpret_cast<T*>(smem + lay.tmp1);
+    c.tmp2 = reinterpret_cast<T*>(smem + lay.tmp2);
+    c.tmp3 = reinterpret_cast<T*>(smem + lay.tmp3);
+    c.red = reinterpret_cast<T*>(smem + lay.red);
+    c.part = reinterpret_cast<double*>(smem + lay.part);
+    c.perm = reinterpret_cast<int*>(smem + lay.perm);
+    c.flag = reinterpret_cast<int*>(smem + lay.flag);
+    c.bar = reinterpret_cast<unsigned long long*>(smem + lay.bar);
+    c.swp = reinterpret_cast<T*>(smem + lay.swp);
+    c.gath = reinterpret_cast<T*>(smem + lay.gath);
+    c.ws = c.wp = 0;
+    c.inflight = c.ipar = 0;
+    c.bpar = 0;
+    c.bulk_inflight = 0;
     for (int k = 0; k < d.depth; ++k) mbar_init(&c.bar[k], 1);
+    mbar_init(&c.bar[BULK_BAR], 1);
     mbar_init_fence();
     c.flag[RING_FLAG] = 0;
+    c.msz = d.nx * d.ldx;
+    c.uni = lay.uni;
+    c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
+    c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
+    c.t_last = clock64();
+    c.tc = args.tc != 0;
   }
   __syncthreads();
-  c.msz = d.nx * d.ldx;
-  c.uni = lay.uni;
-  c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
-  const int t = threadIdx.x;
-  c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
-  c.t_last = clock64();
-  c.tc = args.tc != 0;
 
   if (args.mode == MODE_KKT) {
     const double kkt = kkt_eval<T>(c, cl);
