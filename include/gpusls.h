@@ -129,6 +129,7 @@ const char* gpusls_last_error(void);
 /* qp_setup: one LTV-QP (eq. sqp_qp), Sec. IV-A.
  *   A [N][nx][nx]  B [N][nx][nu]  c [N][nx]   (c_k is the paper's b_k)
  *   Q [N+1][nx][nx] (Q[N] = Q_N)  R [N][nu][nu]  S [N][nu][nx] or NULL (zero)
+ *   (Q_k and R_k symmetric, as in the cost of eq. sqp_qp)
  *   q [N+1][nx]  r [N][nu]
  *   C [N][nc][nx]  D [N][nc][nu]  CN [nf][nx]
  *   lo, hi [N*nc + nf]: lo <= G(dx, du) <= hi, +-INFINITY allowed (the paper's

@@ -486,25 +486,54 @@ __device__ void full_xu(Ctx<T>& c) {
   const int nx = d.nx, nu = d.nu, ldx = d.ldx, ldu = d.ldu, ldf = d.ldf, msz = c.msz, L = c.L, s = c.s;
   const T *K = TP<T>(d.K), *KSig = TP<T>(d.KSig), *Sig = TP<T>(d.Sig), *SigN = TP<T>(d.SigN);
   if (!c.active) return;
-  // one thread per output, each walking its own row: a warp keeps 32 rows'
-  // loads in flight (a warp per row keeps one)
   const int t = threadIdx.x;
-  const int nxr = (L + (c.last ? 1 : 0)) * nx;
-  for (int pr = t; pr < nxr; pr += NT) {
-    const int li = pr / nx, j = pr - li * nx;
-    T v = T(0);
-    if (!c.first) {
-      const T* Sr = (li < L) ? Sig + (size_t)(s + li) * msz + j * ldx : SigN + j * ldx;
-      T a0 = T(0), a1 = T(0);
-      int k = 0;
-      for (; k + 1 < nx; k += 2) {
-        a0 = fma(Sr[k], c.xs[k], a0);
-        a1 = fma(Sr[k + 1], c.xs[k + 1], a1);
-      }
-      if (k < nx) a0 = fma(Sr[k], c.xs[k], a0);
-      v = a0 + a1;
+  if (c.first) {
+    const int nxr = (L + (c.last ? 1 : 0)) * nx;
+    for (int pr = t; pr < nxr; pr += NT) {
+      const int li = pr / nx, j = pr - li * nx;
+      c.dS[(size_t)li * ldx + j] = c.xS[(size_t)li * ldf + j];
     }
-    c.dS[(size_t)li * ldx + j] = c.xS[(size_t)li * ldf + j] + v;
+  } else {
+    // Sig_i of own stages are contiguous: whole-region rounds of cap stages
+    // (the ring is idle between iterations), one thread per output row dot
+    // product from shared memory.  Lane l starts its row at column l mod nx
+    // and wraps, so a warp's reads of 32 rows fall in 32 different banks.
+    const int cap = bulk_capacity(c) / msz;
+    const int k0 = (t & 31) % nx;
+    const T* const xs = c.xs;
+    for (int st0 = 0; st0 < L; st0 += cap) {
+      const int n_st = min(cap, L - st0);
+      bulk_issue<T>(c, Sig + (size_t)(s + st0) * msz, n_st * msz);
+      bulk_wait<T>(c);
+      for (int pr = t; pr < n_st * nx; pr += NT) {
+        const int lr = pr / nx, j = pr - lr * nx, li = st0 + lr;
+        const T* Sr = c.ring + (size_t)lr * msz + j * ldx;
+        T a0 = T(0), a1 = T(0);
+        int k = k0;
+        int it = 0;
+        for (; it + 1 < nx; it += 2) {
+          a0 = fma(Sr[k], xs[k], a0);
+          k = (k + 1 == nx) ? 0 : k + 1;
+          a1 = fma(Sr[k], xs[k], a1);
+          k = (k + 1 == nx) ? 0 : k + 1;
+        }
+        if (it < nx) a0 = fma(Sr[k], xs[k], a0);
+        c.dS[(size_t)li * ldx + j] = c.xS[(size_t)li * ldf + j] + a0 + a1;
+      }
+    }
+    if (c.last) {   // x_N = lx_N + Sig_N x_s, from global memory
+      for (int j = t; j < nx; j += NT) {
+        const T* Sr = SigN + j * ldx;
+        T a0 = T(0), a1 = T(0);
+        int k = 0;
+        for (; k + 1 < nx; k += 2) {
+          a0 = fma(Sr[k], xs[k], a0);
+          a1 = fma(Sr[k + 1], xs[k + 1], a1);
+        }
+        if (k < nx) a0 = fma(Sr[k], xs[k], a0);
+        c.dS[(size_t)L * ldx + j] = c.xS[(size_t)L * ldf + j] + a0 + a1;
+      }
+    }
   }
   for (int pr = t; pr < L * nu; pr += NT) {
     const int li = pr / nu, a = pr - li * nu, i = s + li;
@@ -532,13 +561,22 @@ __device__ void rho_rule_partials(Ctx<T>& c, T rho, double& hm, double& gm, doub
   const int t = threadIdx.x;
   T h = T(0), g = T(0), qq = T(0);
   if (c.active) {
+    // Q_i and R_i are symmetric: row j is read as column j, so the threads of
+    // a warp (consecutive j) read consecutive addresses
     for (int e2 = t; e2 < L * nx; e2 += NT) {
       const int li = e2 / nx, j = e2 - li * nx, i = s + li;
-      const T* Qi = Q + (size_t)i * msz + j * ldx;
-      T a = T(0);
-      for (int k = 0; k < nx; ++k) a += Qi[k] * c.dS[li * ldx + k];
+      const T* Qi = Q + (size_t)i * msz + j;
+      const T* xi = c.dS + li * ldx;
+      T a = T(0), a1 = T(0);
+      int k = 0;
+      for (; k + 1 < nx; k += 2) {
+        a = fma(Qi[(size_t)k * ldx], xi[k], a);
+        a1 = fma(Qi[(size_t)(k + 1) * ldx], xi[k + 1], a1);
+      }
+      if (k < nx) a = fma(Qi[(size_t)k * ldx], xi[k], a);
       const T* Si = S + (size_t)i * nu * ldx;
-      for (int k = 0; k < nu; ++k) a += Si[k * ldx + j] * c.uS[li * ldu + k];
+      for (int k2 = 0; k2 < nu; ++k2) a1 = fma(Si[k2 * ldx + j], c.uS[li * ldu + k2], a1);
+      a += a1;
       h = fmax(h, fabs(a));
       const T* Ci = C + (size_t)i * nc * ldx;
       T b2 = T(0);
@@ -548,11 +586,18 @@ __device__ void rho_rule_partials(Ctx<T>& c, T rho, double& hm, double& gm, doub
     }
     for (int e2 = t; e2 < L * nu; e2 += NT) {
       const int li = e2 / nu, a2 = e2 - li * nu, i = s + li;
-      const T* Ri = R + (size_t)i * nu * ldu + a2 * ldu;
-      T a = T(0);
-      for (int k = 0; k < nu; ++k) a += Ri[k] * c.uS[li * ldu + k];
+      const T* Ri = R + (size_t)i * nu * ldu + a2;
+      T a = T(0), a1 = T(0);
+      for (int k = 0; k < nu; ++k) a = fma(Ri[k * ldu], c.uS[li * ldu + k], a);
       const T* Si = S + (size_t)i * nu * ldx + a2 * ldx;
-      for (int k = 0; k < nx; ++k) a += Si[k] * c.dS[li * ldx + k];
+      const T* xi = c.dS + li * ldx;
+      int k = 0;
+      for (; k + 1 < nx; k += 2) {
+        a = fma(Si[k], xi[k], a);
+        a1 = fma(Si[k + 1], xi[k + 1], a1);
+      }
+      if (k < nx) a = fma(Si[k], xi[k], a);
+      a += a1;
       h = fmax(h, fabs(a));
       const T* Di = D + (size_t)i * nc * ldu;
       T b2 = T(0);
@@ -562,9 +607,9 @@ __device__ void rho_rule_partials(Ctx<T>& c, T rho, double& hm, double& gm, doub
     }
     if (c.last) {
       for (int j = t; j < nx; j += NT) {
-        const T* Qi = Q + (size_t)N * msz + j * ldx;
+        const T* Qi = Q + (size_t)N * msz + j;   // column j = row j (symmetric)
         T a = T(0);
-        for (int k = 0; k < nx; ++k) a += Qi[k] * c.dS[L * ldx + k];
+        for (int k = 0; k < nx; ++k) a = fma(Qi[(size_t)k * ldx], c.dS[L * ldx + k], a);
         h = fmax(h, fabs(a));
         T b2 = T(0);
         for (int rr = 0; rr < d.nf; ++rr) b2 += CN[rr * ldx + j] * c.yS[L * nc + rr];
@@ -578,28 +623,39 @@ __device__ void rho_rule_partials(Ctx<T>& c, T rho, double& hm, double& gm, doub
   qm = (double)block_max(c, qq);
 }
 
-// Cluster-wide max of up to 8 doubles through the part[] slots: every remote
-// value is read by its own thread, then combined from shared memory.
-template <typename T>
-__device__ void cluster_max(Ctx<T>& c, cg::cluster_group& cl, double* v, int n) {
-  if (threadIdx.x < n) c.part[threadIdx.x] = v[threadIdx.x];
-  cl.sync();
-  double* gath = c.part + 16;   // [cs * n]
+// Cluster-wide max (NaN-propagating) of N <= 7 doubles per CTA.  Thread 0
+// publishes them in one of two slots of part[] that alternate between calls,
+// every remote value is read by its own thread, and the values are combined
+// from shared memory.  One cluster barrier per call: a CTA writes a slot again
+// only two calls later, after every CTA has passed the barrier of the call in
+// between (so after its reads of that slot).  part[15] belongs to cluster_or.
+template <typename T, int N>
+__device__ void cluster_max(Ctx<T>& c, cg::cluster_group& cl, double (&v)[N]) {
+  static_assert(N <= 7, "cluster_max: at most 7 values");
   const int t = threadIdx.x;
-  if (t < c.cs * n) {
-    const double* p = cl.map_shared_rank(c.part, t / n);
-    gath[t] = p[t % n];
+  const int par = c.cm_par;
+  double* const slot = c.part + 8 * par;
+  if (t == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) slot[k] = v[k];
   }
+  cl.sync();
+  double* const gath = c.part + 16;   // [cs * N]
+  if (t < c.cs * N) {
+    const int rk = t / N;
+    gath[t] = cl.map_shared_rank(slot, rk)[t - rk * N];
+  }
+  if (t == 0) c.cm_par = par ^ 1;   // every thread read par before the cluster barrier
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
     double r = 0.0;
     for (int rk = 0; rk < c.cs; ++rk) {
-      const double a = gath[rk * n + k];
+      const double a = gath[rk * N + k];
       r = (a != a || r != r) ? a + r : fmax(r, a);
     }
     v[k] = r;
   }
-  cl.sync();
 }
 
 // Write full x, u and lambda = rho y of own stages to the FP64 outputs.
@@ -831,7 +887,7 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
     v4[k] = r2;
     __syncthreads();
   }
-  cluster_max(c, cl, v4, 4);
+  cluster_max(c, cl, v4);
   return fmax(fmax(v4[0], v4[1]), fmax(v4[2], v4[3]));
 }
 

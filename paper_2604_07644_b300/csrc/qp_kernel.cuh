@@ -228,6 +228,7 @@ struct Ctx {
   unsigned inflight, ipar;   // issuing thread: slots with a copy not yet seen complete, their parities
   unsigned bpar;             // whole-region copies: parity of the next completion of bar[BULK_BAR]
   int bulk_inflight;         // a whole-region copy was issued and not yet seen complete
+  int cm_par;                // cluster_max: slot of part[] of the next call
   T* scr;   // per-CTA global scratch: 6 matrices nx x ldx
   int msz;  // nx * ldx
   int uni;  // bytes of the union region at ring

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     c.inflight = c.ipar = 0;
     c.bpar = 0;
     c.bulk_inflight = 0;
+    c.cm_par = 0;
     for (int k = 0; k < d.depth; ++k) mbar_init(&c.bar[k], 1);
     mbar_init(&c.bar[BULK_BAR], 1);
     mbar_init_fence();
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   if (args.mode == MODE_KKT) {
     const double kkt = kkt_eval<T>(c, cl);
     if (rank == 0 && t == 0) d.info_d[3] = kkt;
+    cl.sync();   // no CTA leaves while another may still read its shared memory
     return;
   }
 
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
       d.info_i[2] = refactors;
       d.flags[0] = status == GPUSLS_ERR_NOT_SPD ? 0 : 1;
     }
+    cl.sync();
     return;
   }
 
@@ -154,14 +157,14 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
       admm_iteration<T>(c, cl, rho, check, pl);
       if (!check) continue;
       double v[5] = {pl.rp, 0.0, pl.vm, pl.zm, c.flag[RING_FLAG] ? 1.0 : 0.0};
-      cluster_max(c, cl, v, 5);
+      cluster_max(c, cl, v);
       rp = v[0];
       // the dual residual only where a decision reads it: the primal test
       // passed, a rho update, the last iteration (all uniform in the cluster)
       const bool need_rd = rho_iter || it == max_it || (stop_iter && rp <= eps);
       if (need_rd && v[4] == 0.0 && isfinite(rp)) {
         double u2[2] = {dual_residual_partial<T>(c, rho), c.flag[RING_FLAG] ? 1.0 : 0.0};
-        cluster_max(c, cl, u2, 2);
+        cluster_max(c, cl, u2);
         rd = u2[0];
         v[4] = fmax(v[4], u2[1]);
       }
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
         double hm, gm, qm;
         rho_rule_partials<T>(c, rho, hm, gm, qm);
         double u[3] = {hm, gm, qm};
-        cluster_max(c, cl, u, 3);
+        cluster_max(c, cl, u);
         prof_mark(c, PH_RHO);
         const double prim_scale = fmax(v[2], v[3]);
         const double dual_scale = fmax(fmax(u[0], u[1]), u[2]);
@@ -282,6 +285,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     d.flags[2] = fell_back;
   }
   ring_drain<T>(c);
+  cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 }  // namespace gsls
