@@ -18,6 +18,31 @@ __device__ T block_max(Ctx<T>& c, T v) {
   return r;
 }
 
+// Block-level max of three values in one round (one barrier pair).
+template <typename T>
+__device__ void block_max3(Ctx<T>& c, T& a, T& b, T& d) {
+  a = warp_max(a);
+  b = warp_max(b);
+  d = warp_max(d);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  constexpr int NW = NT / 32;
+  __syncthreads();
+  if (l == 0) {
+    c.red[w] = a;
+    c.red[NW + w] = b;
+    c.red[2 * NW + w] = d;
+  }
+  __syncthreads();
+  a = b = d = T(0);
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    a = fmax(a, c.red[k]);
+    b = fmax(b, c.red[NW + k]);
+    d = fmax(d, c.red[2 * NW + k]);
+  }
+  __syncthreads();
+}
+
 // Number of constraint rows owned by this CTA (stage rows, plus terminal rows
 // for the last chunk).  Owned row `lr` has global index s*nc + lr.
 template <typename T>
@@ -214,17 +239,18 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
   // P1: omega = rho (y - z) into the stacked rows; boundary of the backward
   // chain (p_N = q^_N = q_N + C_N^T omega_N for the last chunk, 0 otherwise).
   if (c.active) {
-    for (int e2 = t; e2 < nrows; e2 += NT) c.wS[e2] = rho * (c.yS[e2] - c.zS[e2]);
-    __syncthreads();
+    // omega straight into the stacked rows (wS keeps the last dz for the dual
+    // residual); the terminal omega_N is formed where it is used
     for (int e2 = t; e2 < L * nc; e2 += NT) {
       const int li = e2 / nc, rr = e2 - li * nc;
-      c.lS[(size_t)(li + 1) * ldv + nx + rr] = c.wS[e2];
+      c.lS[(size_t)(li + 1) * ldv + nx + rr] = rho * (c.yS[e2] - c.zS[e2]);
     }
     for (int j = t; j < nx; j += NT) {
       T a = T(0);
       if (c.last) {
         a = q[(size_t)N * ldx + j];
-        for (int rr = 0; rr < nf; ++rr) a += CN[rr * ldx + j] * c.wS[L * nc + rr];
+        for (int rr = 0; rr < nf; ++rr)
+          a += CN[rr * ldx + j] * (rho * (c.yS[L * nc + rr] - c.zS[L * nc + rr]));
       }
       c.lS[(size_t)L * ldv + j] = a;
     }
@@ -422,9 +448,10 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
     __syncthreads();
     prof_mark(c, PH_P5);
     if (check) {
-      pl.rp = (double)block_max(c, rp);
-      pl.vm = (double)block_max(c, vm);
-      pl.zm = (double)block_max(c, zm);
+      block_max3(c, rp, vm, zm);
+      pl.rp = (double)rp;
+      pl.vm = (double)vm;
+      pl.zm = (double)zm;
       pl.rd = 0.0;   // formed by dual_residual_partial when the solve loop needs it
     }
   } else {
