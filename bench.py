@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 METRIC = "ms/QP solve to 1e-4 KKT residual (61D, N=100): learned+batched vs plain ADMM"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
-TRAFFIC_PER_QP_ITER = 5.81e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6)
+TRAFFIC_PER_QP_ITER = 5.82e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6)
 
 
 def parse():
