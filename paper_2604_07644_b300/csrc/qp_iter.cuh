@@ -18,7 +18,7 @@ __device__ T block_max(Ctx<T>& c, T v) {
   return r;
 }
 
-// Block-level max of three values in one round (one barrier pair).
+// Block-level max of three values in one round (three CTA barriers, not nine).
 template <typename T>
 __device__ void block_max3(Ctx<T>& c, T& a, T& b, T& d) {
   a = warp_max(a);
@@ -475,24 +475,21 @@ __device__ double dual_residual_partial(Ctx<T>& c, T rho) {
   if (c.active) {
     const int Cn = nx + nu;
     if (cds > 0) {
-      const int Gs = max(1, d.slot / cds);
-      const int nbk = (L + Gs - 1) / Gs;
-      stream_blocks<T>(
-          c, nbk,
-          [&](int b) {
-            const int n_st = min(Gs, L - b * Gs);
-            return Blk<T>{CD + (size_t)(s + b * Gs) * cds, n_st * cds * (int)sizeof(T)};
-          },
-          [&](int b, const T* S) {
-            const int n_st = min(Gs, L - b * Gs);
-            for (int e2 = t; e2 < n_st * Cn; e2 += NT) {
-              const int ls = e2 / Cn, col = e2 - ls * Cn, li = b * Gs + ls;
-              const T* Sb = S + (size_t)ls * cds;
-              T a = T(0);
-              for (int rr = 0; rr < nc; ++rr) a += Sb[rr * ldf + col] * c.wS[li * nc + rr];
-              rd = fmax(rd, fabs(a));
-            }
-          });
+      // the [C D] blocks of own stages are contiguous: whole-region rounds
+      // (the ring is idle between iterations)
+      const int cap = max(1, bulk_capacity(c) / cds);
+      for (int st0 = 0; st0 < L; st0 += cap) {
+        const int n_st = min(cap, L - st0);
+        bulk_issue<T>(c, CD + (size_t)(s + st0) * cds, n_st * cds);
+        bulk_wait<T>(c);
+        for (int e2 = t; e2 < n_st * Cn; e2 += NT) {
+          const int ls = e2 / Cn, col = e2 - ls * Cn, li = st0 + ls;
+          const T* Sb = c.ring + (size_t)ls * cds;
+          T a = T(0);
+          for (int rr = 0; rr < nc; ++rr) a += Sb[rr * ldf + col] * c.wS[li * nc + rr];
+          rd = fmax(rd, fabs(a));
+        }
+      }
     }
     if (c.last) {
       for (int j = t; j < nx; j += NT) {
@@ -645,9 +642,10 @@ __device__ void rho_rule_partials(Ctx<T>& c, T rho, double& hm, double& gm, doub
       }
     }
   }
-  hm = (double)block_max(c, h);
-  gm = (double)block_max(c, g);
-  qm = (double)block_max(c, qq);
+  block_max3(c, h, g, qq);
+  hm = (double)h;
+  gm = (double)g;
+  qm = (double)qq;
 }
 
 // Cluster-wide max (NaN-propagating) of N <= 7 doubles per CTA.  Thread 0
