@@ -585,32 +585,45 @@ __device__ void rho_rule_partials(Ctx<T>& c, T rho, double& hm, double& gm, doub
   const int t = threadIdx.x;
   T h = T(0), g = T(0), qq = T(0);
   if (c.active) {
-    // Q_i and R_i are symmetric: row j is read as column j, so the threads of
-    // a warp (consecutive j) read consecutive addresses
-    for (int e2 = t; e2 < L * nx; e2 += NT) {
-      const int li = e2 / nx, j = e2 - li * nx, i = s + li;
-      const T* Qi = Q + (size_t)i * msz + j;
-      const T* xi = c.dS + li * ldx;
-      T a = T(0), a1 = T(0);
-      int k = 0;
-      for (; k + 1 < nx; k += 2) {
-        a = fma(Qi[(size_t)k * ldx], xi[k], a);
-        a1 = fma(Qi[(size_t)(k + 1) * ldx], xi[k + 1], a1);
+    // Q_i x_i from whole-region rounds of the Q_i of own stages (contiguous;
+    // the ring is idle between iterations), one thread per row dot product,
+    // lane l starting at column l mod nx so that a warp's 32 rows fall in 32
+    // banks; S_i^T u_i and C_i^T y_i by columns from global memory (the
+    // threads of a warp, consecutive j, read consecutive addresses)
+    const int capq = max(1, bulk_capacity(c) / msz);
+    const int k0 = (t & 31) % nx;
+    for (int st0 = 0; st0 < L; st0 += capq) {
+      const int n_st = min(capq, L - st0);
+      bulk_issue<T>(c, Q + (size_t)(s + st0) * msz, n_st * msz);
+      bulk_wait<T>(c);
+      for (int e2 = t; e2 < n_st * nx; e2 += NT) {
+        const int lr = e2 / nx, j = e2 - lr * nx, li = st0 + lr, i = s + li;
+        const T* Qr = c.ring + (size_t)lr * msz + j * ldx;
+        const T* xi = c.dS + li * ldx;
+        T a = T(0), a1 = T(0);
+        int k = k0;
+        int it = 0;
+        for (; it + 1 < nx; it += 2) {
+          a = fma(Qr[k], xi[k], a);
+          k = (k + 1 == nx) ? 0 : k + 1;
+          a1 = fma(Qr[k], xi[k], a1);
+          k = (k + 1 == nx) ? 0 : k + 1;
+        }
+        if (it < nx) a = fma(Qr[k], xi[k], a);
+        const T* Si = S + (size_t)i * nu * ldx;
+        for (int k2 = 0; k2 < nu; ++k2) a1 = fma(Si[k2 * ldx + j], c.uS[li * ldu + k2], a1);
+        a += a1;
+        h = fmax(h, fabs(a));
+        const T* Ci = C + (size_t)i * nc * ldx;
+        T b2 = T(0);
+        for (int rr = 0; rr < nc; ++rr) b2 += Ci[rr * ldx + j] * c.yS[li * nc + rr];
+        g = fmax(g, fabs(rho * b2));
+        qq = fmax(qq, fabs(q[(size_t)i * ldx + j]));
       }
-      if (k < nx) a = fma(Qi[(size_t)k * ldx], xi[k], a);
-      const T* Si = S + (size_t)i * nu * ldx;
-      for (int k2 = 0; k2 < nu; ++k2) a1 = fma(Si[k2 * ldx + j], c.uS[li * ldu + k2], a1);
-      a += a1;
-      h = fmax(h, fabs(a));
-      const T* Ci = C + (size_t)i * nc * ldx;
-      T b2 = T(0);
-      for (int rr = 0; rr < nc; ++rr) b2 += Ci[rr * ldx + j] * c.yS[li * nc + rr];
-      g = fmax(g, fabs(rho * b2));
-      qq = fmax(qq, fabs(q[(size_t)i * ldx + j]));
     }
     for (int e2 = t; e2 < L * nu; e2 += NT) {
       const int li = e2 / nu, a2 = e2 - li * nu, i = s + li;
-      const T* Ri = R + (size_t)i * nu * ldu + a2;
+      const T* Ri = R + (size_t)i * nu * ldu + a2;   // column a2 = row a2 (R_i symmetric)
       T a = T(0), a1 = T(0);
       for (int k = 0; k < nu; ++k) a = fma(Ri[k * ldu], c.uS[li * ldu + k], a);
       const T* Si = S + (size_t)i * nu * ldx + a2 * ldx;
