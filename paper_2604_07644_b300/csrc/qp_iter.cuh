@@ -183,6 +183,28 @@ struct Partials {
   double rp, rd, vm, zm;
 };
 
+// The iteration's per-launch constants, computed once by thread 0 (the
+// divisions would otherwise run in every iteration): bundle sizes, and the
+// whole-region rounds of the chunk-boundary corrections.  A ring slot holds a
+// Theta or Xi block, so cap_bk >= 1; a batched fix-up sweep takes at most
+// NT / nu (NT / nc) stages.
+template <typename T>
+__device__ void iter_plan(Ctx<T>& c) {
+  const QPDesc& d = *c.d;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, L = c.L;
+  bundle_sizes(nx, nu, nc, d.ldx, d.ldu, d.ldv, d.ldf, &c.bws, &c.fws, &c.cds);
+  const int cap_el = d.depth * d.slot;
+  c.cap_bk = cap_el / c.msz;
+  c.nb_th = max(0, d.nch - (c.rank + 2));
+  c.nr_th = (c.nb_th + c.cap_bk - 1) / c.cap_bk;
+  c.gs_fp = min(min(cap_el / (nx * d.ldu), NT / nu), max(L, 1));
+  c.nr_fp = (L + c.gs_fp - 1) / c.gs_fp;
+  c.nb_xi = max(0, c.rank - 1);
+  c.nr_xi = (c.nb_xi + c.cap_bk - 1) / c.cap_bk;
+  c.gs_ck = nc > 0 ? min(min(cap_el / (nx * d.ldc), NT / nc), max(L, 1)) : 1;
+  c.nr_ck = nc > 0 ? (L + c.gs_ck - 1) / c.gs_ck : 0;
+}
+
 // One ADMM iteration (eq. augmented_linear, the LQ solve of eq. primal_update
 // with the cached factorization, the z-projection and the scaled dual update).
 //
@@ -204,22 +226,17 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
   const T *FPi = TP<T>(d.FPi), *CKSig = TP<T>(d.CKSig), *CNSig = TP<T>(d.CNSig);
   const T *Theta = TP<T>(d.Theta), *Xi = TP<T>(d.Xi);
   const T *BW = TP<T>(d.BW), *FW = TP<T>(d.FW), *CD = TP<T>(d.CD);
-  int bws, fws, cds;
-  bundle_sizes(nx, nu, nc, ldx, ldu, ldv, ldf, &bws, &fws, &cds);
+  const int bws = c.bws, fws = c.fws;
   const int nrows = own_rows(c);
-  // The chunk-boundary corrections in whole-region rounds (bulk_issue):
+  // The chunk-boundary corrections in whole-region rounds (bulk_issue), as
+  // planned by iter_plan:
   // P3: nr_th rounds of Theta blocks (cap_bk per round), then nr_fp rounds of
   //     FPi stages (gs_fp per round);
   // P5: nr_xi rounds of Xi blocks, then nr_ck rounds of CKSig stages.
-  const int cap_el = bulk_capacity(c);
-  const int cap_bk = cap_el / msz;   // >= 1: a ring slot holds a Theta or Xi block
-  const int m0 = c.rank + 2, nb_th = max(0, d.nch - m0), nr_th = (nb_th + cap_bk - 1) / cap_bk;
-  const int per_fp = nx * ldu, gs_fp = min(min(cap_el / per_fp, NT / nu), max(L, 1));
-  const int nr_fp = (L + gs_fp - 1) / gs_fp;
-  const int nb_xi = max(0, c.rank - 1), nr_xi = (nb_xi + cap_bk - 1) / cap_bk;
-  const int ldc = d.ldc, per_ck = nx * ldc;
-  const int gs_ck = nc > 0 ? min(min(cap_el / per_ck, NT / nc), max(L, 1)) : 1;
-  const int nr_ck = nc > 0 ? (L + gs_ck - 1) / gs_ck : 0;
+  const int cap_bk = c.cap_bk, m0 = c.rank + 2, nb_th = c.nb_th, nr_th = c.nr_th;
+  const int per_fp = nx * ldu, gs_fp = c.gs_fp, nr_fp = c.nr_fp;
+  const int nb_xi = c.nb_xi, nr_xi = c.nr_xi;
+  const int ldc = d.ldc, per_ck = nx * ldc, gs_ck = c.gs_ck, nr_ck = c.nr_ck;
   T lo_a = T(0), hi_a = T(0), lo_b = T(0), hi_b = T(0);   // bounds of the first two own rows (P5)
   auto p3_src = [&](int r) -> const T* {
     return r < nr_th ? Theta + (size_t)(c.rank * MAXCS + m0 + r * cap_bk) * msz

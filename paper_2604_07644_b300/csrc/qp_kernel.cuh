@@ -229,6 +229,11 @@ struct Ctx {
   unsigned bpar;             // whole-region copies: parity of the next completion of bar[BULK_BAR]
   int bulk_inflight;         // a whole-region copy was issued and not yet seen complete
   int cm_par;                // cluster_max: slot of part[] of the next call
+  // per-launch iteration plan (iter_plan): bundle sizes, and the whole-region
+  // rounds of the chunk-boundary corrections (P3: Theta blocks, then FPi
+  // stages; P5: Xi blocks, then CKSig stages)
+  int bws, fws, cds;
+  int cap_bk, nb_th, nr_th, gs_fp, nr_fp, nb_xi, nr_xi, gs_ck, nr_ck;
   T* scr;   // per-CTA global scratch: 6 matrices nx x ldx
   int msz;  // nx * ldx
   int uni;  // bytes of the union region at ring

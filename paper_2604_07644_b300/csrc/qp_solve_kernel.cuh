@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
     c.t_last = clock64();
     c.tc = args.tc != 0;
+    iter_plan<T>(c);
   }
   __syncthreads();
 
