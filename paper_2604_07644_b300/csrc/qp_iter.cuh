@@ -222,7 +222,7 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
   const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, N = d.N, ldx = d.ldx, ldu = d.ldu;
   const int ldv = d.ldv, ldf = d.ldf, msz = c.msz, L = c.L, s = c.s;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const T *q = TP<T>(d.q), *CN = TP<T>(d.CN), *lo = TP<T>(d.lo), *hi = TP<T>(d.hi), *x0 = TP<T>(d.x0);
+  const T *q = TP<T>(d.q), *CN = TP<T>(d.CN), *lo = TP<T>(d.lo), *hi = TP<T>(d.hi);
   const T *FPi = TP<T>(d.FPi), *CKSig = TP<T>(d.CKSig), *CNSig = TP<T>(d.CNSig);
   const T *Theta = TP<T>(d.Theta), *Xi = TP<T>(d.Xi);
   const T *BW = TP<T>(d.BW), *FW = TP<T>(d.FW), *CD = TP<T>(d.CD);
@@ -351,8 +351,7 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
         c.xS[(size_t)li * ldf + nx + a] = c.ktS[li * ldu + a];
       }
     }
-    for (int j = t; j < nx; j += NT) c.xS[j] = c.first ? x0[j] : T(0);
-    __syncthreads();
+    __syncthreads();   // (xS row 0 = x0 or 0 is set once per launch)
     prof_mark(c, PH_P3);
     // P4: forward chain over the FW^T bundles: thread r < nx + nc sweeps
     // column r of FW^T for lx_{i+1} (r < nx) or v~_i (r >= nx).

@@ -137,6 +137,9 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     c.zS[e2] = zg[(size_t)c.s * d.nc + e2];
     c.yS[e2] = yg[(size_t)c.s * d.nc + e2];
   }
+  // the forward chain's start lx_s (x0 for the first chunk, 0 for the others);
+  // no phase writes row 0 of xS below column nx
+  for (int j = t; j < d.nx; j += NT) c.xS[j] = c.first ? TP<T>(d.x0)[j] : T(0);
   __syncthreads();
 
   double eps = args.eps;
