@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--cluster", type=int, default=8)
     p.add_argument("--plain-qps", type=int, default=2)
-    p.add_argument("--cpu-sample", type=int, default=2)
+    p.add_argument("--cpu-sample", type=int, default=32)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--fallback", type=int, default=2000)
     p.add_argument("--no-autotune", action="store_true", help="keep --cluster instead of tuning the launch shape")
@@ -154,6 +154,51 @@ def algorithmic_bytes_per_iter(nx, nu, N, nc, esz):
     return N * (2 * nx * nx + 3 * nu * nx + nu * nc + 2 * nc * (nx + nu)) * esz
 
 
+def _oracle_worker_init():
+    """Pool worker start-up: the oracle's imports, outside the timed region."""
+    sys.path.insert(0, ROOT)
+    import oracle.admm  # noqa: F401
+    from paper_2604_07644_b300 import workloads  # noqa: F401
+
+
+def _oracle_worker(idx):
+    """One family instance solved by the FP64 oracle ADMM to the 1e-4 KKT
+    tolerance (the instance is regenerated here from its index)."""
+    from oracle import admm
+    from paper_2604_07644_b300 import workloads as W
+    qp = W.family(0).instance(idx)
+    r = admm.admm(qp, admm.Settings(eps=1e-4, eps_kkt=1e-4))
+    return idx, r.iters, r.x, r.u
+
+
+def cpu_oracle_pool(indices):
+    """The FP64 oracle as it stands over the host's cores: one QP per worker
+    process (spawned, so it is safe after CUDA initialisation), as many
+    workers as cores or QPs.  Returns (ms per QP of wall time, workers,
+    results [(index, iters, x, u)])."""
+    import multiprocessing as mp
+    procs = max(1, min(len(os.sched_getaffinity(0)), len(indices)))
+    with mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init) as pool:
+        pool.map(abs, range(procs))                      # workers up before the clock starts
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, indices, chunksize=1)
+        dt = time.perf_counter() - t0
+    return dt * 1e3 / len(indices), procs, res
+
+
+def host_cpu():
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "usable": len(os.sched_getaffinity(0)), "model": model}
+
+
 def cpu_oracle_ms_per_qp(qps, eps=1e-4, results=None):
     """The FP64 oracle as it stands on this host (single thread); the solutions
     are appended to `results` when given."""
@@ -212,7 +257,7 @@ def _time_graph(g, stream, steps):
     return e0.elapsed_time(e1) / steps
 
 
-def extra_workloads(args, qps, hb, stream, dev, oracle_sols):
+def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
     """Timed on the same device after the headline: the batched serving mix
     (256 ragged QPs, nx in {12, 61, 75}, N in 16..128, cold FP32), 64
     humanoid-shaped QPs (75D, N=40, cold FP32), the humanoid SLS solve (75D,
@@ -277,9 +322,8 @@ def extra_workloads(args, qps, hb, stream, dev, oracle_sols):
                                    "model_gflops_per_s": (scans + fwd) / (ms * 1e-3) / 1e9}
         sls.close()
 
-    # checks on the headline's solutions (already in hb's output buffers)
-    x = hb.out_x.cpu().numpy()
-    u = hb.out_u.cpu().numpy()
+    # checks on the headline's solutions (snapshot of the learned step's outputs)
+    x, u = sol
     viol, ox, ou = 0.0, 0, 0
     xs, us = [], []
     for qp in qps:
@@ -293,13 +337,34 @@ def extra_workloads(args, qps, hb, stream, dev, oracle_sols):
                             qp.CN @ X[-1]])
         viol = max(viol, float(np.max(np.maximum(np.maximum(v - qp.hi, qp.lo - v), 0.0))))
     out["bound_violation_max"] = viol
-    if oracle_sols:
-        d = 0.0
-        for i, r in enumerate(oracle_sols):
-            scale = max(1.0, float(np.max(np.abs(r.x))))
-            d = max(d, float(np.max(np.abs(xs[i] - r.x))) / scale, float(np.max(np.abs(us[i] - r.u))) / scale)
-        out["max_rel_diff_vs_oracle"] = {"value": d, "sample": f"first {args.cpu_sample} QPs; both solved to a "
-                                                                 "1e-4 KKT residual, so they agree to about that"}
+    # distance to the exact optimum of eq. sqp_qp that the FP64 oracle stored
+    # for sampled instances of this batch (tests/golden/exact_quadruped61.npz),
+    # next to the oracle's own ADMM solves at the same 1e-4 KKT tolerance
+    gold_path = os.path.join(ROOT, "tests", "golden", "exact_quadruped61.npz")
+    if os.path.exists(gold_path):
+        gold = np.load(gold_path)
+        base = 100000
+        d_gpu, d_or, n_or = 0.0, 0.0, 0
+        ids = []
+        by_idx = {r[0]: r for r in (oracle_sols or [])}
+        for j, i in enumerate(gold["ids"]):
+            i = int(i)
+            if i >= len(qps):
+                continue
+            ids.append(i)
+            scale = max(1.0, float(np.max(np.abs(gold["x"][j]))))
+            d_gpu = max(d_gpu, float(np.max(np.abs(xs[i] - gold["x"][j]))) / scale,
+                        float(np.max(np.abs(us[i] - gold["u"][j]))) / scale)
+            r = by_idx.get(base + i)
+            if r is not None:
+                n_or += 1
+                d_or = max(d_or, float(np.max(np.abs(r[2] - gold["x"][j]))) / scale,
+                           float(np.max(np.abs(r[3] - gold["u"][j]))) / scale)
+        out["max_rel_diff_vs_exact"] = {
+            "value": d_gpu, "qps": ids,
+            "oracle_admm_same_tolerance": d_or if n_or else None, "oracle_qps": n_or,
+            "note": "relative to max(1, max|x*|); x* = the exact optimum (oracle ADMM to 1e-11 + dense-KKT "
+                    "active-set solve); a 1e-4 KKT residual bounds the distance only through the curvature"}
     return out
 
 
@@ -455,6 +520,7 @@ def main():
         return [info[i] for i in range(args.batch)]
 
     inf_w = read_info(True)
+    sol_w = (hb.out_x.cpu().numpy(), hb.out_u.cpu().numpy())
     iters = [i.iters for i in inf_w]
     refs = [i.refactors for i in inf_w]
     kkts = [i.kkt for i in inf_w]
@@ -560,13 +626,17 @@ def main():
     # humanoid-shaped QP, the humanoid SLS solve; solution checks ----
     cpu = None
     oracle_sols = []
-    if rank == 0 and args.cpu_sample > 0:
-        ms_cpu, it_cpu = cpu_oracle_ms_per_qp(qps[:args.cpu_sample], results=oracle_sols)
-        cpu = {"value": ms_cpu, "unit": "ms/QP", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_sample} QPs of this batch, FP64 oracle ADMM, single thread; iters {it_cpu}"}
+    if rank == 0 and ws == 1 and args.cpu_sample > 0:
+        n_s = min(args.cpu_sample, args.batch)
+        ms_cpu, procs, oracle_sols = cpu_oracle_pool([base + i for i in range(n_s)])
+        it_cpu = [r[1] for r in oracle_sols]
+        cpu = {"value": ms_cpu, "unit": "ms/QP", "cores": procs, "kind": "oracle", "host": host_cpu(),
+               "sample": f"the first {n_s} QPs of this batch, FP64 oracle ADMM to the 1e-4 KKT tolerance, one QP "
+                         f"per worker process over {procs} cores; value = wall time / QPs; "
+                         f"mean iters {np.mean(it_cpu):.0f}"}
     extra = {}
     if rank == 0 and not args.no_extras:
-        extra = extra_workloads(args, qps, hb, stream, dev, oracle_sols)
+        extra = extra_workloads(args, qps, sol_w, stream, dev, oracle_sols)
 
     pk, pk_kind = peaks()
     algo = algorithmic_bytes_per_iter(nx, nu, N, nc, esz) * float(np.sum(iters))
@@ -603,7 +673,8 @@ def main():
                 "refactors_mean": float(np.mean(refs)),
                 "refactors_mean_cold": float(np.mean([i.refactors for i in inf_c])),
                 "kkt_max": float(np.max(kkts)), "all_converged": all(s_ == 0 for s_ in stats),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (11 if args.index_order else 12) * args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": None if g_learned is None else g_learned.kernel_count() * args.steps,
                 "clocks": clk.summary()}
         line.update(extra)
         print(json.dumps(line), flush=True)

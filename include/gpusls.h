@@ -309,6 +309,9 @@ int qp_graph_create(qp_graph** g, qp_handle* q, mlp_handle* m, const float* feat
                     double* dx, double* du, double* lam, int32_t* info_i, double* info_d,
                     double rho_min, double rho_max);
 int qp_graph_launch(qp_graph* g, void* stream);
+/* qp_graph_kernel_count: number of kernel launches one replay of the graph
+ * performs (the kernel nodes of the captured graph), into *n (HOST). */
+int qp_graph_kernel_count(qp_graph* g, int32_t* n);
 void qp_graph_destroy(qp_graph* g);
 
 /* ------------------------------------------------------------------------ */
@@ -323,17 +326,22 @@ void qp_graph_destroy(qp_graph* g);
  * loop where cudaMalloc may block or synchronize the device, a context that
  * forbids allocation, or a host runtime that owns all device buffers).  It
  * needs no handle and calls no allocator.
+ *   Sizes accepted: 1 <= nx <= 80, 1 <= nu <= 64, 0 <= nc <= 64, 0 <= nf <= 64,
+ *   N >= 1 and (N+1)*nx + N*nu <= GPUSLS_NOALLOC_MAX_SCRATCH (the residual
+ *   needs no blocked buffers, so nu may exceed the solver's limit of 32).
  *   Inputs are device float64 arrays in the qp_setup layouts (S may be NULL)
  *   plus the candidate point x0 [nx], dx [N+1][nx], du [N][nu], lam [N*nc+nf];
  *   out: device float64 [5] receiving (kkt, dynamics, bound violation,
  *   u-stationarity, complementarity).  Runs asynchronously on `stream`.
  * Scratch: a fixed device array of GPUSLS_NOALLOC_MAX_SCRATCH doubles, held by
- * every GPU that loads the library until the process exits.  Problems needing
- * more return GPUSLS_ERR_INVALID with the sizes in gpusls_last_error().  The
- * array's device address is looked up on the first call on each device, so
- * make that first call before any stream capture.  Every call uses the same
- * array (it is fully rewritten before it is read): calls whose executions
- * overlap on a device -- e.g. on two streams at once -- race on it. */
+ * every GPU that loads the library until the process exits.  Sizes outside the
+ * ranges above return GPUSLS_ERR_INVALID (with the sizes in
+ * gpusls_last_error()).  Every call looks up the array's device address on the
+ * current device (allocation-free); the first call on a device also loads the
+ * library's device code there, so make that first call before any stream
+ * capture.  Every call uses the same array (it is fully rewritten before it is
+ * read): calls whose executions overlap on a device -- e.g. on two streams at
+ * once -- race on it. */
 int gpusls_kkt_noalloc(qp_dims d, const double* A, const double* B, const double* c,
                        const double* Q, const double* R, const double* S,
                        const double* q, const double* r,

@@ -26,6 +26,17 @@ Readings (the paper is silent or garbled here):
     ru_k (oracle.kkt.u_residuals) is added to the linear term r_k used by the
     iteration (and by the rho rule's ||(q, r)||), while the KKT check keeps the
     original data.
+  * stall rule (option stall_iters > 0, used to mirror FP32 solves): once the
+    in-loop tolerance has sat at eps_floor for stall_iters iterations without
+    the in-loop test passing, the next stop-test iteration runs the KKT check
+    anyway (and refines on failure), as if the test had passed.  Rounding in a
+    reduced-precision LQ solve can hold r_prim or r_dual just above the floor;
+    in exact arithmetic both go to zero and the rule never fires.
+
+The KKT gate, the tightening of eps, the refinement and the stall rule are
+this project's stopping rule: the paper stops ADMM on its residual tolerance
+alone and prints no such control.  With eps_kkt = None (the default) the
+oracle runs the paper's ADMM and stops on r_prim, r_dual <= eps.
 """
 from __future__ import annotations
 
@@ -46,6 +57,7 @@ class Settings:
     eps_kkt: float | None = None   # None: stop on the in-loop test alone
     eps_floor: float = 1e-7        # lowest in-loop tolerance the KKT gate tightens to
     max_refine: int = 3            # refinement rounds allowed at the floor
+    stall_iters: int = 0           # > 0: stall rule (module docstring); 0 off
     sigma: int = 25                # 0: fixed rho
     check_every: int = 5
     max_iter: int = 4000
@@ -68,6 +80,15 @@ class Result:
     refactors: int
     rho_hist: list = field(default_factory=list)
     kkt: float | None = None
+
+
+def residuals(qp, v, z_new, z, rho):
+    """Primal and dual residuals of one iteration (Sec. IV-A):
+    r_prim = ||v - z+||_inf, r_dual = ||rho G^T (z+ - z)||_inf."""
+    r_prim = float(np.max(np.abs(v - z_new))) if qp.m else 0.0
+    gx, gu = GT_apply(qp, rho * (z_new - z))
+    r_dual = float(max(np.max(np.abs(gx)), np.max(np.abs(gu)) if gu.size else 0.0))
+    return r_prim, r_dual
 
 
 def rho_rule(qp, x, u, v, z_new, y_new, rho, r_prim, r_dual, s: Settings) -> float:
@@ -103,6 +124,7 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
     r_prim = r_dual = np.inf
     x = u = None
     kkt = None
+    floor_it = -1                  # first stop-test iteration at the eps floor (stall rule)
     t = 0
     for t in range(1, max_iter + 1):
         qh, rh = augmented_linear(qp, rho, y, z)
@@ -110,13 +132,20 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
         v = G_apply(qp, x, u)
         z_new = np.clip(v + y, qp.lo, qp.hi)
         y = y + v - z_new
-        r_prim = float(np.max(np.abs(v - z_new))) if m else 0.0
-        gx, gu = GT_apply(qp, rho * (z_new - z))
-        r_dual = float(max(np.max(np.abs(gx)), np.max(np.abs(gu)) if gu.size else 0.0))
+        r_prim, r_dual = residuals(qp, v, z_new, z, rho)
         z = z_new
         if iters is not None:
             continue
-        if t % s.check_every == 0 and r_prim <= eps and r_dual <= eps:
+        # eps counts as at the floor within a relative 1e-9: repeated
+        # multiplication by 0.1 does not land on the floor exactly in binary
+        at_floor = eps <= s.eps_floor * (1.0 + 1e-9)
+        stalled = False
+        if s.stall_iters > 0 and t % s.check_every == 0 and at_floor:
+            if floor_it < 0:
+                floor_it = t
+            stalled = t - floor_it >= s.stall_iters
+        if t % s.check_every == 0 and ((r_prim <= eps and r_dual <= eps) or stalled):
+            floor_it = -1
             if s.eps_kkt is None:
                 converged = True
                 break
@@ -124,7 +153,7 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
             if kkt <= s.eps_kkt:
                 converged = True
                 break
-            if eps > s.eps_floor:
+            if not at_floor:
                 eps = max(eps * 0.1, s.eps_floor)
             elif refines < s.max_refine:
                 qp = dataclasses.replace(qp, r=qp.r + u_residuals(qp0, x, u, rho * y))

@@ -211,6 +211,12 @@ class ServeGraph:
     def launch(self, stream: torch.cuda.Stream | None = None):
         native.check(self.lib.qp_graph_launch(self.g, _stream_ptr(stream or self.qb.stream)), "qp_graph_launch")
 
+    def kernel_count(self) -> int:
+        """Kernel launches per replay, counted from the captured graph."""
+        n = C.c_int32()
+        native.check(self.lib.qp_graph_kernel_count(self.g, C.byref(n)), "qp_graph_kernel_count")
+        return int(n.value)
+
     def info(self) -> list[dict]:
         ii = self.info_i.view(self.qb.B, 8).cpu().numpy()
         dd = self.info_d.view(self.qb.B, 4).cpu().numpy()

@@ -11,7 +11,6 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
-#include <mutex>
 #include <string>
 
 #include "../../include/gpusls.h"
@@ -142,24 +141,16 @@ __global__ void __launch_bounds__(NT) kkt_noalloc_kernel(NoAllocArgs a) {
   }
 }
 
-// Device address of the scratch array, looked up once per device.
-std::mutex g_mu;
-double* g_ptr[128] = {nullptr};
-
+// Device address of the scratch array on the current device.  It is looked up
+// on every call (the lookup allocates nothing): a cached address would dangle
+// after cudaDeviceReset or any other re-creation of the primary context, which
+// reloads the module and with it the array.
 int scratch_for_current_device(double** ptr) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_error(GPUSLS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= 128) return set_error(GPUSLS_ERR_INVALID, "gpusls_kkt_noalloc: device index out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_kkt_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return set_error(GPUSLS_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-    g_ptr[dev] = static_cast<double*>(p);
-  }
-  *ptr = g_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_kkt_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(GPUSLS_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+  *ptr = static_cast<double*>(p);
   return GPUSLS_OK;
 }
 

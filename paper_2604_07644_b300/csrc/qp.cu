@@ -668,6 +668,22 @@ extern "C" int qp_graph_launch(qp_graph* g, void* stream) {
   return GPUSLS_OK;
 }
 
+extern "C" int qp_graph_kernel_count(qp_graph* g, int32_t* n) {
+  if (!g || !g->graph || !n) return fail(GPUSLS_ERR_INVALID, "qp_graph_kernel_count: null argument");
+  size_t count = 0;
+  CU(cudaGraphGetNodes(g->graph, nullptr, &count));
+  std::vector<cudaGraphNode_t> nodes(count);
+  if (count) CU(cudaGraphGetNodes(g->graph, nodes.data(), &count));
+  int k = 0;
+  for (size_t i = 0; i < count; ++i) {
+    cudaGraphNodeType ty;
+    CU(cudaGraphNodeGetType(nodes[i], &ty));
+    if (ty == cudaGraphNodeTypeKernel) ++k;
+  }
+  *n = k;
+  return GPUSLS_OK;
+}
+
 extern "C" int qp_riccati(qp_handle* h, double* P, double* K) {
   if (!h || !P || !K) return fail(GPUSLS_ERR_INVALID, "qp_riccati: null argument");
   int st = set_outputs(h, P, K, nullptr, 0, 0, true);

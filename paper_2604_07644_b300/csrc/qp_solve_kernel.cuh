@@ -185,8 +185,11 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
       // r_dual just above the eps floor, where the gate below would never
       // run; after FP32_STALL_ITERS iterations at the floor it runs anyway
       // (and refines the linear term if the FP64 KKT check fails).
+      // eps counts as at the floor within a relative 1e-9: repeated
+      // multiplication by 0.1 does not land on the floor exactly in binary
+      const bool at_floor = eps <= args.eps_floor * (1.0 + 1e-9);
       bool stalled = false;
-      if (sizeof(T) == 4 && eps <= args.eps_floor) {
+      if (sizeof(T) == 4 && at_floor) {
         if (floor_it < 0) floor_it = it;
         stalled = it - floor_it >= FP32_STALL_ITERS;
       }
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
           status = GPUSLS_OK;
           break;
         }
-        if (eps > args.eps_floor) {
+        if (!at_floor) {
           eps = fmax(eps * 0.1, args.eps_floor);
         } else if (refines < args.max_refine) {
           refine_linear_term<T>(c);

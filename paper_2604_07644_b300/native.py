@@ -84,6 +84,7 @@ SIGNATURES = {
     "qp_graph_create": (C.c_int, [C.POINTER(P), P, P, DP, DP, DP, DP, DP, DP, DP, C.c_double, C.c_double]),
     "qp_graph_launch": (C.c_int, [P, P]),
     "qp_graph_destroy": (None, [P]),
+    "qp_graph_kernel_count": (C.c_int, [P, C.POINTER(C.c_int32)]),
     "gpusls_kkt_noalloc": (C.c_int, [qp_dims] + [DP] * 18 + [P]),
 }
 

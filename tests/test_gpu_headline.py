@@ -1,0 +1,142 @@
+"""Solution-level parity of the headline configuration: the learned warm
+start, the batched persistent FP32 solve and the FP64 KKT gate, launched as
+the benchmark launches them (256 held-out quadruped-shaped QPs, nx=61, nu=12,
+N=100, one CUDA graph per step, cluster 6, longest expected first), compared
+QP by QP with the exact optimum of eq. sqp_qp that the FP64 oracle stored in
+tests/golden/exact_quadruped61.npz (make_exact.py), and the plain FP64 solve
+compared with the same optima.
+
+Tolerances.  The benchmark solves to a 1e-4 FP64 KKT residual, which bounds
+the distance to the optimum only through the problem's curvature: the
+oracle's own FP64 ADMM stopped at a 1e-4 KKT residual lies 1.1e-4 (relative to
+max(1, max|x*|)) from the optimum on instance 100000.  So the 1e-4 solves are
+held to their KKT residual (measured by the oracle) and to a distance of 1e-3;
+the 1e-4 relative agreement on the solution is checked on the same path
+solved to a 1e-5 KKT residual, and 1e-6 relative for the plain FP64 solve at a
+1e-8 KKT residual.  Measured on B300: 7.3e-4 at 1e-4 (the oracle's own ADMM at
+1e-4: 2.5e-4), 7.3e-5 at 1e-5, 1.6e-7 for FP64 at 1e-8."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import kkt, lq
+from paper_2604_07644_b300 import native
+from paper_2604_07644_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLD = os.path.join(ROOT, "tests", "golden", "exact_quadruped61.npz")
+MODEL = os.path.join(ROOT, "paper_2604_07644_b300", "warmstart_quadruped61.npz")
+BATCH = 256
+BASE = 100000
+
+
+def rel(a, b, scale):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b)))) / scale
+
+
+@pytest.fixture(scope="module")
+def exact():
+    return np.load(GOLD)
+
+
+@pytest.fixture(scope="module")
+def batch_qps():
+    fam = W.family(0)
+    return [fam.instance(BASE + i) for i in range(BATCH)]
+
+
+def headline_solve(qps, eps_kkt, max_refine=3):
+    """The benchmark's launch: tuned shape (cluster 6, two CTAs per SM),
+    longest-expected-first order, learned warm start, one graph per step;
+    the second replay is read (its order comes from the first)."""
+    from paper_2604_07644_b300 import learned
+    from paper_2604_07644_b300.api import QPBatch
+    s = native.default_settings(precision=native.GPUSLS_FP32, cluster=6, occupancy=0, max_refine=max_refine,
+                                fallback_iters=2000, max_iter=6000, eps_kkt=eps_kkt,
+                                eps_floor=min(1e-5, 0.1 * eps_kkt), schedule=1)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        qb = QPBatch(qps, s, stream=stream)
+        mlp = learned.load(MODEL, max_batch=len(qps), stream=stream)
+        feats = torch.from_numpy(learned.features(qps)).cuda()
+        g = qb.graph(mlp, feats)
+        for _ in range(2):
+            g.launch(stream)
+        stream.synchronize()
+        info = g.info()
+        x = qb.out_x.cpu().numpy()
+        u = qb.out_u.cpu().numpy()
+        lam = qb.out_l.cpu().numpy()
+    out = []
+    ox = ou = ol = 0
+    for qp in qps:
+        nxs, nus = (qp.N + 1) * qp.nx, qp.N * qp.nu
+        out.append((x[ox:ox + nxs].reshape(qp.N + 1, qp.nx), u[ou:ou + nus].reshape(qp.N, qp.nu),
+                    lam[ol:ol + qp.m]))
+        ox, ou, ol = ox + nxs, ou + nus, ol + qp.m
+    g.close()
+    mlp.close()
+    qb.close()
+    return out, info
+
+
+def check_against_exact(qps, sols, info, exact, kkt_tol, dist_tol):
+    worst = 0.0
+    for j, i in enumerate(exact["ids"]):
+        qp = qps[int(i)]
+        dx, du, lam = sols[int(i)]
+        assert info[int(i)]["status"] == native.GPUSLS_OK, (i, info[int(i)])
+        k = kkt.kkt_residual(qp, dx, du, lam)
+        assert k <= kkt_tol * 1.0001, (i, k)
+        v = lq.G_apply(qp, dx, du)
+        assert np.all(v <= qp.hi + kkt_tol) and np.all(v >= qp.lo - kkt_tol), i
+        scale = max(1.0, float(np.max(np.abs(exact["x"][j]))))
+        d = max(rel(dx, exact["x"][j], scale), rel(du, exact["u"][j], scale))
+        worst = max(worst, d)
+        assert d <= dist_tol, (i, d)
+    return worst
+
+
+def test_headline_path_at_1e4_kkt(lib, batch_qps, exact):
+    """The benchmark's step: every QP converged; the sampled QPs (the first
+    four, the two slowest and two more) pass the oracle's KKT check at 1e-4
+    with every bound met, and lie within 1e-3 of the exact optimum."""
+    sols, info = headline_solve(batch_qps, 1e-4)
+    assert all(i["status"] == native.GPUSLS_OK for i in info)
+    assert max(i["kkt"] for i in info) <= 1e-4
+    worst = check_against_exact(batch_qps, sols, info, exact, 1e-4, 1e-3)
+    print(f"headline 1e-4: max distance to the exact optimum {worst:.2e}")
+
+
+def test_headline_path_solution_matches_exact_at_1e4_relative(lib, batch_qps, exact):
+    """The same path solved to a 1e-5 KKT residual (eps floor 1e-6, up to 8
+    refinement rounds: with 3, two of the 256 QPs stop at max_iter with a KKT
+    residual of 4e-5 to 6e-5) matches the exact optimum to 1e-4 relative, the
+    reduced-precision solution tolerance."""
+    sols, info = headline_solve(batch_qps, 1e-5, max_refine=8)
+    assert all(i["status"] == native.GPUSLS_OK for i in info)
+    worst = check_against_exact(batch_qps, sols, info, exact, 1e-5, 1e-4)
+    print(f"headline 1e-5: max distance to the exact optimum {worst:.2e}")
+
+
+@pytest.mark.parametrize("j", [0, 4])
+def test_plain_fp64_solution_matches_exact_at_1e6_relative(lib, batch_qps, exact, j):
+    """The plain FP64 solve (cold, one QP per launch) to a 1e-8 KKT residual
+    matches the exact optimum to 1e-6 relative."""
+    from paper_2604_07644_b300.api import QPBatch
+    i = int(exact["ids"][j])
+    qp = batch_qps[i]
+    qb = QPBatch([qp], native.default_settings(precision=native.GPUSLS_FP64, eps_kkt=1e-8, eps_floor=1e-10,
+                                               max_iter=40000))
+    r = qb.solve()
+    qb.close()
+    assert r.info[0]["status"] == native.GPUSLS_OK, r.info[0]
+    assert kkt.kkt_residual(qp, r.dx[0], r.du[0], r.lam[0]) <= 1.0001e-8
+    scale = max(1.0, float(np.max(np.abs(exact["x"][j]))))
+    d = max(rel(r.dx[0], exact["x"][j], scale), rel(r.du[0], exact["u"][j], scale))
+    print(f"plain FP64 QP {i}: {r.info[0]['iters']} iterations, distance {d:.2e}")
+    assert d <= 1e-6, d

@@ -136,3 +136,159 @@ def test_refinement_recovers_a_planted_operator_error(monkeypatch):
     k1 = kkt.kkt_residual(qp, r1.x, r1.u, r1.lam)
     assert not r0.converged and k0 > 1e-6
     assert r1.converged and k1 <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# The rho rule (Sec. IV-A.2: an OSQP-style update, read as OSQP Sec. 5.2),
+# pinned against values worked out by hand on a scalar QP (nx = nu = nc = nf = 1,
+# N = 1): Q_0 = 2, Q_1 = 3, R_0 = 0.5, S_0 = 0.25, C_0 = 1, D_0 = 2, C_N = 1,
+# rho = 0.5, r_prim = 0.5, r_dual = 0.1.  With xi = (x_0, x_1, u_0):
+#   v = (C_0 x_0 + D_0 u_0, C_N x_1),  H xi = (Q_0 x_0 + S_0 u_0, Q_1 x_1, R_0 u_0 + S_0 x_0),
+#   G^T lam = (C_0 lam_0, C_N lam_1, D_0 lam_0) with lam = rho y,
+#   rho_new = rho sqrt((r_prim / max(|v|, |z|)) / (r_dual / max(|H xi|, |G^T lam|, |(q, r)|))).
+# Each case makes a different scale term the maximum, so dropping any one of
+# them, or inverting the ratio, changes a pinned value.
+# ---------------------------------------------------------------------------
+def _scalar_qp(q, r):
+    f = lambda v: np.array(v, dtype=float)  # noqa: E731
+    return W.QP(A=f([[[1.0]]]), B=f([[[1.0]]]), c=f([[0.0]]), Q=f([[[2.0]], [[3.0]]]), R=f([[[0.5]]]),
+                S=f([[[0.25]]]), q=f(q), r=f(r), C=f([[[1.0]]]), D=f([[[2.0]]]), CN=f([[1.0]]),
+                lo=f([-10.0, -10.0]), hi=f([10.0, 10.0]), x0=f([1.0]))
+
+
+RHO_CASES = [
+    # (x_0, x_1), u_0, z, y, (q_0, q_1), r_0, rho_new worked out by hand
+    # A: |v| = 2 and |H xi| = Q_1 x_1 = 6 dominate: ratio (0.5/2)/(0.1/6) = 15
+    ((1.0, 2.0), -1.0, (-0.5, 1.5), (0.2, -0.4), (0.1, -0.2), 0.3, 0.5 * np.sqrt(15.0)),
+    # B: |z| = 3 and |G^T lam| = D_0 lam_0 = 4 dominate: ratio (0.5/3)/(0.1/4) = 20/3
+    ((1.0, 0.5), -1.0, (-0.5, 3.0), (4.0, -0.4), (0.1, -0.2), 0.3, 0.5 * np.sqrt(20.0 / 3.0)),
+    # C: |z| = 1.5 and |(q, r)| = 5 dominate: ratio (0.5/1.5)/(0.1/5) = 50/3
+    ((1.0, 0.5), -1.0, (-0.5, 1.5), (0.2, -0.4), (5.0, -0.2), 0.3, 0.5 * np.sqrt(50.0 / 3.0)),
+]
+
+
+def _rho_case(case):
+    (x0, x1), u0, z, y, q, r0, want = case
+    qp = _scalar_qp([[q[0]], [q[1]]], [[r0]])
+    x = np.array([[x0], [x1]])
+    u = np.array([[u0]])
+    v = lq.G_apply(qp, x, u)
+    return qp, x, u, v, np.array(z), np.array(y), want
+
+
+@pytest.mark.parametrize("case", range(len(RHO_CASES)))
+def test_rho_rule_matches_hand_computed_values(case):
+    qp, x, u, v, z, y, want = _rho_case(RHO_CASES[case])
+    s = admm.Settings()
+    got = admm.rho_rule(qp, x, u, v, z, y, 0.5, 0.5, 0.1, s)
+    assert abs(got - want) < 1e-14 * want, (got, want)
+
+
+def test_rho_rule_clamps_and_skips_degenerate_ratios():
+    qp, x, u, v, z, y, want = _rho_case(RHO_CASES[0])
+    s = admm.Settings(rho_max=1.0)
+    assert admm.rho_rule(qp, x, u, v, z, y, 0.5, 0.5, 0.1, s) == 1.0
+    s = admm.Settings(rho_min=5.0)
+    assert admm.rho_rule(qp, x, u, v, z, y, 0.5, 0.5, 0.1, s) == 5.0
+    # a zero residual leaves rho unchanged (no division by zero)
+    assert admm.rho_rule(qp, x, u, v, z, y, 0.5, 0.0, 0.1, admm.Settings()) == 0.5
+    assert admm.rho_rule(qp, x, u, v, z, y, 0.5, 0.5, 0.0, admm.Settings()) == 0.5
+
+
+def _planted_rules():
+    """Plausible mistakes in the rho rule, planted in copies of the oracle's
+    function on the CPU: inverted ratio, each scale term dropped, a missing
+    square root."""
+    from oracle.lq import GT_apply, H_apply
+
+    def make(invert=False, drop=None, no_sqrt=False):
+        def rule(qp, x, u, v, z_new, y_new, rho, r_prim, r_dual, s):
+            prim = [np.max(np.abs(v)), np.max(np.abs(z_new))]
+            if drop == "v":
+                prim = prim[1:]
+            if drop == "z":
+                prim = prim[:1]
+            hx, hu = H_apply(qp, x, u)
+            gx, gu = GT_apply(qp, rho * y_new)
+            terms = {"H": max(np.max(np.abs(hx)), np.max(np.abs(hu))),
+                     "G": max(np.max(np.abs(gx)), np.max(np.abs(gu))),
+                     "qr": max(np.max(np.abs(qp.q)), np.max(np.abs(qp.r)))}
+            if drop in terms:
+                del terms[drop]
+            ratio = (r_prim / max(prim)) / (r_dual / max(terms.values()))
+            if invert:
+                ratio = 1.0 / ratio
+            f = ratio if no_sqrt else np.sqrt(ratio)
+            return float(min(max(rho * f, s.rho_min), s.rho_max))
+        return rule
+
+    return {"inverted": make(invert=True), "no_sqrt": make(no_sqrt=True),
+            **{f"drop_{k}": make(drop=k) for k in ("v", "z", "H", "G", "qr")}}
+
+
+@pytest.mark.parametrize("mistake", ["inverted", "no_sqrt", "drop_v", "drop_z", "drop_H", "drop_G", "drop_qr"])
+def test_rho_rule_pin_catches_planted_mistakes(mistake):
+    """Every planted mistake fails at least one hand-computed case, and the
+    same planted function without the mistake would pass them all (the oracle
+    itself, checked above)."""
+    rule = _planted_rules()[mistake]
+    s = admm.Settings()
+    missed = 0
+    for case in RHO_CASES:
+        qp, x, u, v, z, y, want = _rho_case(case)
+        if abs(rule(qp, x, u, v, z, y, 0.5, 0.5, 0.1, s) - want) < 1e-14 * want:
+            missed += 1
+    assert missed < len(RHO_CASES), mistake
+
+
+# ---------------------------------------------------------------------------
+# The stall rule (the oracle's option mirroring FP32 solves; not in the paper)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(3))
+def test_stall_rule_never_fires_when_residuals_reach_the_floor(seed):
+    """With exact FP64 iterates the residuals reach every floor, so turning
+    the stall rule on changes nothing: same iterations, same point."""
+    qp = W.plain_4d(seed)
+    base = dict(eps=1e-4, eps_kkt=1e-9, eps_floor=1e-9, max_iter=6000)
+    r0 = admm.admm(qp, admm.Settings(**base))
+    r1 = admm.admm(qp, admm.Settings(**base, stall_iters=250))
+    assert r0.converged and r1.converged
+    assert r0.iters == r1.iters and np.array_equal(r0.x, r1.x) and np.array_equal(r0.lam, r1.lam)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_stall_rule_runs_the_gate_when_residuals_are_held_above_the_floor(seed, monkeypatch):
+    """A dual residual held at 2e-7, above a 1e-7 floor (standing in for FP32
+    rounding), keeps the in-loop test from ever passing at the floor: without
+    the rule the solve runs to max_iter; with it the FP64 KKT check runs after
+    250 iterations at the floor, passes, and the point agrees with the
+    unplanted solve to the KKT tolerance (the rule changes when the check
+    runs, not the point the iteration converges to)."""
+    qp = W.plain_4d(seed)
+    s = dict(eps=1e-4, eps_kkt=1e-7, eps_floor=1e-7, max_iter=4000)
+    ref = admm.admm(qp, admm.Settings(**s))
+    orig = admm.residuals
+
+    def held(qp_, v, z_new, z, rho):
+        rp, rd = orig(qp_, v, z_new, z, rho)
+        return rp, max(rd, 2e-7)
+
+    monkeypatch.setattr(admm, "residuals", held)
+    r0 = admm.admm(qp, admm.Settings(**s))
+    r1 = admm.admm(qp, admm.Settings(**s, stall_iters=250))
+    assert ref.converged and not r0.converged and r0.iters == 4000
+    assert r1.converged and r1.iters < 1000
+    assert kkt.kkt_residual(qp, r1.x, r1.u, r1.lam) <= 1e-7
+    assert np.max(np.abs(r1.x - ref.x)) < 1e-6 and np.max(np.abs(r1.u - ref.u)) < 1e-6
+
+
+def test_residuals_definition():
+    """r_prim = ||v - z+||_inf and r_dual = ||rho G^T (z+ - z)||_inf, checked
+    on the scalar QP of the rho-rule pins: G^T w = (C_0 w_0, C_N w_1, D_0 w_0)."""
+    qp = _scalar_qp([[0.1], [-0.2]], [[0.3]])
+    v = np.array([-1.0, 2.0])
+    z_new = np.array([-0.5, 1.5])
+    z = np.array([-0.75, 1.0])
+    rp, rd = admm.residuals(qp, v, z_new, z, 0.5)
+    assert rp == 0.5                                  # max(|-1 + 0.5|, |2 - 1.5|)
+    assert rd == 0.5 * max(0.25, 0.5, 2.0 * 0.25)     # rho * max(|C_0 dz_0|, |C_N dz_1|, |D_0 dz_0|)
