@@ -322,6 +322,34 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
                                    "model_gflops_per_s": (scans + fwd) / (ms * 1e-3) / 1e9}
         sls.close()
 
+    # one RTI step of the FastSLS alternation at the humanoid size (nx=75,
+    # nu=21, N=40; Sec. III-D / IV-C): SLS solve from the previous step's
+    # duals, tightening, warm-started tightened QP solve, new duals
+    from paper_2604_07644_b300.api import FastSLS
+    qp75, sp75 = W.fastsls_problem(0, 75, 21, 40, w_range=(0.001, 0.01), tag=4)
+    f = FastSLS(qp75, sp75, native.default_settings(precision=native.GPUSLS_FP32, eps_floor=1e-5, max_iter=6000),
+                sls_precision=native.GPUSLS_FP32, stream=stream)
+    with torch.cuda.stream(stream):
+        f.step(1, fetch=False)
+        tau_prev = f.tau.clone()
+        for _ in range(2):
+            f.step(1, tau_in=tau_prev, fetch=False)
+            tau_prev.copy_(f.tau)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            f.step(1, tau_in=tau_prev, fetch=False)
+            tau_prev.copy_(f.tau)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    r = f.step(1, tau_in=tau_prev)
+    out["fastsls75_rti_step"] = {"ms_per_step": e0.elapsed_time(e1) / steps, "qp_iters_last": r["info"]["iters"],
+                                 "qp_kkt_last": r["info"]["kkt"], "h_max": float(np.max(r["h"])),
+                                 "step": "sls_solve (per-j tau) + tighten + warm tightened QP solve (FP32) + sls_tau"}
+    f.close()
+
     # checks on the headline's solutions (snapshot of the learned step's outputs)
     x, u = sol
     viol, ox, ou = 0.0, 0, 0

@@ -240,7 +240,54 @@ int sls_solve(sls_handle* h, const double* A, const double* B, const double* E,
               const double* C, const double* D, const double* CN, const double* tau,
               double* Phi_x, double* Phi_u, double* hk, double* hf);
 
+/* sls_tau: the FastSLS duals of App. B from the last sls_solve on h and the
+ * unscaled QP multipliers lam [N*nc + nf] (device float64, the qp_solve
+ * layout) of the tightened nominal QP:
+ *   beta_{k,j}[c] = || row c of C_k Phi_x_{k,j} + D_k Phi_u_{k,j} ||^2  (k < N)
+ *   beta_{N,j}[c] = || row c of C_N Phi_x_{N,j} ||^2
+ *   tau_{k,j}[c]  = |lam_{k,c}| / sqrt(beta_{k,j}[c] + eps)  for j < k <= N,
+ * zero for k <= j (where Phi_{k,j} = 0) and beyond a stage's rows.  The row
+ * norms are the ones the margins of that sls_solve were summed from (solve
+ * precision).  |lam|: a two-sided row lo <= g <= hi is the paper's pair of
+ * one-sided rows with one row norm and at most one of them active.
+ *   tau: device float64 [N+1][N][max(nc, nf)] (the sls_solve tau layout).
+ * Errors: GPUSLS_ERR_INVALID before any sls_solve on h, for eps <= 0 or null
+ * pointers. */
+int sls_tau(sls_handle* h, const double* lam, double eps, double* tau);
+
 void sls_destroy(sls_handle* h);
+
+/* fastsls_solve: `iters` steps of the FastSLS alternation between the robust
+ * controller and the tightened nominal trajectory (Sec. III-D, eq.
+ * nmpc_problem_tightened, eq. fastsls_qp, App. B; the RTI order of Sec. IV-C):
+ * each step
+ *   1. sls_solve with the duals of the previous step (tau_in on the first
+ *      step, NULL = zero) -> Phi_x, Phi_u, margins h_k, h^f;
+ *   2. tightens the bounds: stage-k rows lo + h_k <= g <= hi - h_k, terminal
+ *      rows by h^f (infinite bounds stay infinite; h_0 = 0);
+ *   3. qp_update(q, bounds only: the cached factorization stays valid) and
+ *      qp_solve(q) from q's current ADMM state (the previous step's solution
+ *      after the first);
+ *   4. sls_tau from the new multipliers and the Phi of step 1.
+ * q: a qp_handle holding ONE QP whose data (A, B, C, D, CN) are the nominal
+ *   linearization; s: a per-j-tau sls_handle of the same dims.
+ * A, B, E, Qbar, Rbar, QbarN, C, D, CN: the sls_solve inputs (the same A, B,
+ *   C, D, CN as q's data); lo, hi [N*nc+nf]: the untightened bounds; x0 [nx].
+ * Outputs (device float64): tau_out (NULL: not copied) the duals of the last
+ *   step, ready as the next call's tau_in; dx, du, lam the last tightened QP
+ *   solution (qp_solve layouts); Phi_x, Phi_u (may be NULL), hk [N][nc],
+ *   hf [nf] (NULL if nf == 0) of the last step -- the returned trajectory is
+ *   feasible for the tightening of the same step.  info: HOST qp_info of the
+ *   last QP solve (or NULL).
+ * Returns the worst qp_solve status over the steps (GPUSLS_OK, GPUSLS_MAX_ITER)
+ * or the first error. */
+int fastsls_solve(qp_handle* q, sls_handle* s, const double* A, const double* B, const double* E,
+                  const double* Qbar, const double* Rbar, const double* QbarN,
+                  const double* C, const double* D, const double* CN,
+                  const double* lo, const double* hi, const double* x0,
+                  int32_t iters, double eps_tau, const double* tau_in, double* tau_out,
+                  double* dx, double* du, double* lam,
+                  double* Phi_x, double* Phi_u, double* hk, double* hf, qp_info* info);
 
 /* ------------------------------------------------------------------------ */
 /* Learned warm start (no counterpart in the paper)                         */

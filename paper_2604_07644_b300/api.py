@@ -275,6 +275,15 @@ class SLS:
         return (Phix.cpu().numpy(), Phiu.cpu().numpy(), h.cpu().numpy()[:N * nc].reshape(N, nc),
                 hf.cpu().numpy()[:nf])
 
+    def tau(self, lam, eps: float = 1e-8) -> np.ndarray:
+        """sls_tau: App. B duals from the last solve and multipliers lam."""
+        nx, nu, N, nc, nf = self.dims
+        w = max(nc, nf, 1)
+        tl = _dev64(lam, self.device)
+        out = torch.empty((N + 1) * N * w, dtype=torch.float64, device=self.device)
+        native.check(self.lib.sls_tau(self.h, _dptr(tl), float(eps), _dptr(out)), "sls_tau")
+        return out.cpu().numpy().reshape(N + 1, N, w)
+
     def close(self):
         if getattr(self, "h", None) is not None:
             self.lib.sls_destroy(self.h)
@@ -285,6 +294,70 @@ class SLS:
             self.close()
         except Exception:
             pass
+
+
+def _dev64(a, device):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        return a
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+
+
+class FastSLS:
+    """The FastSLS alternation (fastsls_solve): one nominal QP handle and one
+    per-j-tau SLS handle over the same dynamics and constraints.  step()
+    runs `iters` alternation steps and returns the last step's outputs; the
+    duals it returns are the next call's tau_in (the RTI chaining)."""
+
+    def __init__(self, qp, sp, settings: native.qp_settings | None = None, sls_precision=native.GPUSLS_FP64,
+                 stream=None, device="cuda", eps_tau: float = 1e-8):
+        self.lib = native.load()
+        self.device = device
+        self.qb = QPBatch([qp], settings, stream=stream, device=device)
+        self.sls = SLS(qp.nx, qp.nu, qp.N, qp.nc, qp.nf, per_j_tau=True, precision=sls_precision, stream=stream,
+                       device=device)
+        self.eps_tau = float(eps_tau)
+        self.dims = qp.dims()
+        nx, nu, N, nc, nf = self.dims
+        self.w = max(nc, nf, 1)
+        self.data = {k: _dev64(getattr(sp, k), device) for k in ("A", "B", "E", "Qbar", "Rbar", "QbarN", "C", "D",
+                                                                 "CN")}
+        self.lo = _dev64(qp.lo, device)
+        self.hi = _dev64(qp.hi, device)
+        self.x0 = _dev64(qp.x0, device)
+        self.tau = torch.zeros((N + 1) * N * self.w, dtype=torch.float64, device=device)
+        self.Phix = torch.empty(N * nx, N * nx, dtype=torch.float64, device=device)
+        self.Phiu = torch.empty(N * nu, N * nx, dtype=torch.float64, device=device)
+        self.hk = torch.zeros(max(1, N * nc), dtype=torch.float64, device=device)
+        self.hf = torch.zeros(max(1, nf), dtype=torch.float64, device=device)
+
+    def step(self, iters: int = 1, tau_in: torch.Tensor | None = None, fetch: bool = True, phi: bool = True):
+        info = (native.qp_info * 1)()
+        d = self.data
+        qb = self.qb
+        st = self.lib.fastsls_solve(qb.h, self.sls.h, *[_dptr(d[k]) for k in ("A", "B", "E", "Qbar", "Rbar", "QbarN",
+                                                                                "C", "D", "CN")],
+                                    _dptr(self.lo), _dptr(self.hi), _dptr(self.x0), int(iters), self.eps_tau,
+                                    _dptr(tau_in), _dptr(self.tau), _dptr(qb.out_x), _dptr(qb.out_u),
+                                    _dptr(qb.out_l), _dptr(self.Phix) if phi else None,
+                                    _dptr(self.Phiu) if phi else None, _dptr(self.hk),
+                                    _dptr(self.hf) if self.dims[4] else None, info)
+        native.check(st, "fastsls_solve")
+        if not fetch:
+            return st
+        nx, nu, N, nc, nf = self.dims
+        return dict(x=qb.out_x.cpu().numpy()[:(N + 1) * nx].reshape(N + 1, nx),
+                    u=qb.out_u.cpu().numpy()[:N * nu].reshape(N, nu), lam=qb.out_l.cpu().numpy()[:N * nc + nf],
+                    tau=self.tau.cpu().numpy().reshape(N + 1, N, self.w),
+                    Phix=self.Phix.cpu().numpy() if phi else None, Phiu=self.Phiu.cpu().numpy() if phi else None,
+                    h=self.hk.cpu().numpy()[:N * nc].reshape(N, nc), hf=self.hf.cpu().numpy()[:nf],
+                    info=dict(status=info[0].status, iters=info[0].iters, refactors=info[0].refactors,
+                              kkt=info[0].kkt), status=st)
+
+    def close(self):
+        self.qb.close()
+        self.sls.close()
 
 
 class MLP:

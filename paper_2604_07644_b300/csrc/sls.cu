@@ -50,6 +50,10 @@ struct sls_handle {
   void *ET = nullptr, *CT = nullptr, *DT = nullptr, *CNT = nullptr, *scr = nullptr;
   double *rn = nullptr, *rnf = nullptr;   // row norms [N][N][nc], [N][nf]
   int ldx = 0, ldu = 0;
+  int solved = 0;                         // rn / rnf hold the last sls_solve
+  // FastSLS alternation (per-j handles): working tau [N+1][N][max(nc, nf)],
+  // tightened bounds [N nc + nf]
+  double *tau = nullptr, *lo_t = nullptr, *hi_t = nullptr;
 };
 
 namespace gsls {
@@ -238,6 +242,46 @@ __global__ void sls_margin_kernel(const double* __restrict__ rn, const double* _
   }
 }
 
+// FastSLS duals (App. B): tau_{k,j}[c] = |lam_{k,c}| / sqrt(beta_{k,j}[c] + eps)
+// with beta the squared row norms of C_k Phi_x_{k,j} + D_k Phi_u_{k,j} (stage
+// k < N) or C_N Phi_x_{N,j} (k = N) that the last solve left in rn / rnf;
+// zero for k <= j (Phi_{k,j} = 0 there) and beyond a stage's rows.  |lam|:
+// a two-sided row is two one-sided rows of the same norm, at most one active.
+__global__ void sls_tau_kernel(const double* __restrict__ rn, const double* __restrict__ rnf,
+                               const double* __restrict__ lam, double eps, double* __restrict__ tau, int N, int nc,
+                               int nf, int w) {
+  const size_t total = (size_t)(N + 1) * N * w;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / ((size_t)N * w));
+    const int rem = (int)(e - (size_t)k * N * w);
+    const int j = rem / w, c = rem - j * w;
+    double v = 0.0;
+    if (j < k) {
+      if (k < N && c < nc) {
+        const double r = rn[((size_t)k * N + j) * nc + c];
+        v = fabs(lam[(size_t)k * nc + c]) / sqrt(r * r + eps);
+      } else if (k == N && c < nf) {
+        const double r = rnf[(size_t)j * nf + c];
+        v = fabs(lam[(size_t)N * nc + c]) / sqrt(r * r + eps);
+      }
+    }
+    tau[e] = v;
+  }
+}
+
+// Tightened bounds of eq. nmpc_problem_tightened: the rows of stage k move
+// inwards by h_k (lo + h, hi - h), the terminal rows by h^f; infinite bounds
+// stay infinite.
+__global__ void fastsls_tighten_kernel(const double* __restrict__ lo, const double* __restrict__ hi,
+                                       const double* __restrict__ hk, const double* __restrict__ hf,
+                                       double* __restrict__ lo_t, double* __restrict__ hi_t, int N, int nc, int nf) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * nc + nf) return;
+  const double m = e < N * nc ? hk[e] : hf[e - N * nc];
+  lo_t[e] = lo[e] + m;
+  hi_t[e] = hi[e] - m;
+}
+
 }  // namespace gsls
 
 extern "C" int sls_setup(sls_handle** out, qp_dims d, int32_t precision, int32_t per_j_tau, void* stream) {
@@ -282,6 +326,11 @@ extern "C" int sls_setup(sls_handle** out, qp_dims d, int32_t precision, int32_t
                                                    esz + 256));
   e = (cudaError_t)(e | alloc(&h->rn, (size_t)N * N * std::max(nc, 1)));
   e = (cudaError_t)(e | alloc(&h->rnf, (size_t)N * std::max(nf, 1)));
+  if (h->per_j) {
+    e = (cudaError_t)(e | alloc(&h->tau, (size_t)(N + 1) * N * std::max(std::max(nc, nf), 1)));
+    e = (cudaError_t)(e | alloc(&h->lo_t, (size_t)N * nc + nf));
+    e = (cudaError_t)(e | alloc(&h->hi_t, (size_t)N * nc + nf));
+  }
   if (e != cudaSuccess) {
     sls_destroy(h);
     return set_error(GPUSLS_ERR_CUDA, "sls_setup: cudaMalloc failed");
@@ -368,13 +417,76 @@ extern "C" int sls_solve(sls_handle* h, const double* A, const double* B, const 
     CUS(cudaGetLastError());
   }
   CUS(cudaStreamSynchronize(st));
+  h->solved = 1;
   return GPUSLS_OK;
+}
+
+extern "C" int sls_tau(sls_handle* h, const double* lam, double eps, double* tau) {
+  if (!h || !lam || !tau) return set_error(GPUSLS_ERR_INVALID, "sls_tau: null argument");
+  if (!h->solved) return set_error(GPUSLS_ERR_INVALID, "sls_tau: no sls_solve has run on this handle");
+  if (!(eps > 0.0)) return set_error(GPUSLS_ERR_INVALID, "sls_tau: eps must be positive");
+  const qp_dims d = h->d;
+  const int w = std::max(std::max(d.nc, d.nf), 1);
+  const size_t total = (size_t)(d.N + 1) * d.N * w;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  sls_tau_kernel<<<blocks, 256, 0, h->stream>>>(h->rn, h->rnf, lam, eps, tau, d.N, d.nc, d.nf, w);
+  CUS(cudaGetLastError());
+  CUS(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+extern "C" int fastsls_solve(qp_handle* q, sls_handle* s, const double* A, const double* B, const double* E,
+                             const double* Qbar, const double* Rbar, const double* QbarN, const double* C,
+                             const double* D, const double* CN, const double* lo, const double* hi, const double* x0,
+                             int32_t iters, double eps_tau, const double* tau_in, double* tau_out, double* dx,
+                             double* du, double* lam, double* Phi_x, double* Phi_u, double* hk, double* hf,
+                             qp_info* info) {
+  if (!q || !s || !lo || !hi || !x0 || !dx || !du || !lam || !hk || (s->d.nf > 0 && !hf))
+    return set_error(GPUSLS_ERR_INVALID, "fastsls_solve: null argument");
+  if (!s->per_j || !s->tau) return set_error(GPUSLS_ERR_INVALID, "fastsls_solve: the SLS handle needs per-j tau");
+  if (q->batch != 1) return set_error(GPUSLS_ERR_INVALID, "fastsls_solve: the QP handle must hold one QP");
+  const qp_dims d = s->d, dq = q->dims[0];
+  if (dq.nx != d.nx || dq.nu != d.nu || dq.N != d.N || dq.nc != d.nc || dq.nf != d.nf)
+    return set_error(GPUSLS_ERR_INVALID, "fastsls_solve: QP and SLS dims differ");
+  if (iters < 1) return set_error(GPUSLS_ERR_INVALID, "fastsls_solve: iters must be >= 1");
+  if (!(eps_tau > 0.0)) return set_error(GPUSLS_ERR_INVALID, "fastsls_solve: eps_tau must be positive");
+  const int rows = d.N * d.nc + d.nf;
+  const int w = std::max(std::max(d.nc, d.nf), 1);
+  const size_t ntau = (size_t)(d.N + 1) * d.N * w;
+  int worst = GPUSLS_OK;
+  for (int it = 0; it < iters; ++it) {
+    // controller update from the previous duals (zero on the first step without tau_in)
+    const double* tau_cur = it == 0 ? tau_in : s->tau;
+    int st = sls_solve(s, A, B, E, Qbar, Rbar, QbarN, C, D, CN, tau_cur, Phi_x, Phi_u, hk, hf);
+    if (st) return st;
+    // tightened nominal QP
+    if (rows > 0) {
+      fastsls_tighten_kernel<<<(rows + 255) / 256, 256, 0, s->stream>>>(lo, hi, hk, d.nf > 0 ? hf : hk, s->lo_t,
+                                                                         s->hi_t, d.N, d.nc, d.nf);
+      CUS(cudaGetLastError());
+      CUS(cudaStreamSynchronize(s->stream));
+    }
+    st = qp_update(q, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                   nullptr, s->lo_t, s->hi_t);
+    if (st) return st;
+    st = qp_solve(q, x0, 0, 0.0, dx, du, lam, info);
+    if (st < 0) return st;
+    if (st > worst) worst = st;
+    // duals for the next controller update
+    st = sls_tau(s, lam, eps_tau, s->tau);
+    if (st) return st;
+  }
+  if (tau_out) {
+    CUS(cudaMemcpyAsync(tau_out, s->tau, ntau * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    CUS(cudaStreamSynchronize(s->stream));
+  }
+  return worst;
 }
 
 extern "C" void sls_destroy(sls_handle* h) {
   if (!h) return;
   if (h->qh) qp_destroy(h->qh);
-  for (double* p : {h->pA, h->pB, h->pQ, h->pR, h->pS, h->dummy, h->rn, h->rnf})
+  for (double* p : {h->pA, h->pB, h->pQ, h->pR, h->pS, h->dummy, h->rn, h->rnf, h->tau, h->lo_t, h->hi_t})
     if (p) cudaFree(p);
   for (void* p : {h->ET, h->CT, h->DT, h->CNT, h->scr})
     if (p) cudaFree(p);

@@ -70,6 +70,8 @@ SIGNATURES = {
     "sls_setup": (C.c_int, [C.POINTER(P), qp_dims, C.c_int32, C.c_int32, P]),
     "sls_solve": (C.c_int, [P, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP]),
     "sls_destroy": (None, [P]),
+    "sls_tau": (C.c_int, [P, DP, C.c_double, DP]),
+    "fastsls_solve": (C.c_int, [P, P] + [DP] * 12 + [C.c_int32, C.c_double] + [DP] * 9 + [C.POINTER(qp_info)]),
     "mlp_create": (C.c_int, [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32, C.c_int32, P]),
     "mlp_set_params": (C.c_int, [P, DP, DP, DP, DP, DP, DP]),
     "mlp_get_params": (C.c_int, [P, DP, DP, DP, DP, DP, DP]),

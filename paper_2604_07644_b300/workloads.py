@@ -477,6 +477,23 @@ def sls_problem(seed: int = 0, nx: int = 75, nu: int = 21, N: int = 40, n_obs: i
                       C=qp.C, D=qp.D, CN=qp.CN, tau=tau, name=f"sls{nx}d-N{N}-{tau_mode}-s{seed}")
 
 
+def fastsls_problem(seed: int = 0, nx: int = 12, nu: int = 4, N: int = 17, n_obs: int = 8,
+                    w_range: tuple = (0.002, 0.01), tag: int = 12) -> tuple[QP, SLSProblem]:
+    """Nominal LTV-QP and SLS controller data of the FastSLS alternation
+    (Sec. III-D) sharing A_k, B_k, C_k, D_k, C_N: the legged recipe (|u| <= 1
+    box rows and obstacle half-spaces that the goal pulls the trajectory
+    into), E = diag(w) with w ~ U[w_range] per state (time-invariant),
+    Qbar = I, Rbar = I, QbarN = I.  tag 4 with (75, 21, 40) and w in
+    [0.001, 0.01] is the humanoid-shaped problem of sls_problem."""
+    qp = legged(seed, nx, nu, N, n_obs, tag=tag)
+    g = rng(13, seed, nx, N)
+    w = g.uniform(w_range[0], w_range[1], nx)
+    E = np.repeat(np.diag(w)[None], N, axis=0)
+    sp = SLSProblem(A=qp.A, B=qp.B, E=E, Qbar=np.eye(nx), Rbar=np.eye(nu), QbarN=np.eye(nx), C=qp.C, D=qp.D,
+                    CN=qp.CN, tau=None, name=f"fastsls{nx}d-N{N}-s{seed}")
+    return qp, sp
+
+
 def sls_small(seed: int = 0, nx: int = 3, nu: int = 2, N: int = 5, nc: int = 3, nf: int = 2,
               tau_mode: str = "uniform") -> SLSProblem:
     """Small random SLS problem for pins and parity (every term present)."""
