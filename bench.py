@@ -291,6 +291,21 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
         qb.close()
 
     batch_run("serving_mix_cold", W.serving_mix(0, 256), 8)
+
+    # long horizon (the horizon study of Sec. V-A): torque-limited
+    # pendulum-shaped QP, nx=30, nu=15, N=3000 (1.35e5 decision variables),
+    # cold FP32 solve to the 1e-4 KKT tolerance, one QP per launch, cluster 8
+    qpl = W.long_horizon(0)
+    sl = native.default_settings(precision=native.GPUSLS_FP32, cluster=8, eps_floor=1e-5, max_iter=20000)
+    with torch.cuda.stream(stream):
+        ql = QPBatch([qpl], sl, stream=stream, device=dev)
+        gl = ql.graph()
+        ms = _time_graph(gl, stream, steps)
+        il = gl.info()[0]
+    out["long_horizon_N3000"] = {"ms_per_qp": ms, "iters": il["iters"], "kkt": il["kkt"], "status": il["status"],
+                                 "variables": (qpl.N + 1) * qpl.nx + qpl.N * qpl.nu,
+                                 "workload": "pendulum-shaped LTV-QP nx=30 nu=15 N=3000, |u| <= 1, cold FP32"}
+    ql.close()
     batch_run("humanoid75_cold", [W.humanoid_75d(s) for s in range(64)], 4)
 
     # SLS: model flops from the per-j scans (2 (N - j) combines of ~16.7 nx^3

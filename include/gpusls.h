@@ -19,7 +19,10 @@
  *   - Every call returns an int status (GPUSLS_*).  On failure
  *     gpusls_last_error() returns a message for the calling thread.
  *   - Sizes: 1 <= nx <= 80, 1 <= nu <= 32, 0 <= nc <= 64, 0 <= nf <= 64,
- *     1 <= N <= 1024.  Larger values return GPUSLS_ERR_INVALID.
+ *     1 <= N <= GPUSLS_MAX_N (4096) for the qp_* calls, N <= 512 for sls_*.
+ *     Larger values return GPUSLS_ERR_INVALID.  Horizons whose per-chunk
+ *     vectors do not fit a CTA's shared memory (thousands of stages) keep
+ *     them in a per-CTA region of the handle's device memory instead.
  */
 #ifndef GPUSLS_H
 #define GPUSLS_H
@@ -29,6 +32,9 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+/* longest horizon the qp_* calls accept */
+#define GPUSLS_MAX_N 4096
 
 /* status codes */
 #define GPUSLS_OK             0   /* solved (converged to the tolerance)            */

@@ -8,7 +8,7 @@ dimension, the horizon and the batch size, so the tuner measures the
 candidates on the caller's own problems and caches the winner per bucket:
 
     key = (device name, precision, nx bucket, N bucket, batch bucket)
-    nx buckets 16 / 32 / 64 / 80, N buckets 32 / 64 / 128 / 256 / 1024,
+    nx buckets 16 / 32 / 64 / 80, N buckets 32 / 64 / 128 / 256 / 1024 / 4096,
     batch buckets 1 / 8 / 64 / 256 / 4096.
 
 A candidate is scored by the modeled time of one batched solve, per QP:
@@ -32,7 +32,7 @@ import os
 from dataclasses import dataclass
 
 NX_BUCKETS = (16, 32, 64, 80)
-N_BUCKETS = (32, 64, 128, 256, 1024)
+N_BUCKETS = (32, 64, 128, 256, 1024, 4096)
 B_BUCKETS = (1, 8, 64, 256, 4096)
 # Every cluster size: a GPC holds two CTAs per SM, and the sizes that tile
 # its slots best (6 on B300: four 8-CTA clusters leave slots idle) can beat

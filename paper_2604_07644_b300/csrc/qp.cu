@@ -206,7 +206,7 @@ static int run_pack(qp_handle* h, const std::vector<PackJob>& jobs) {
 // slot, factorization schedule (blocked unless asked for the tree, in TF32,
 // or its buffers do not fit), ring depth, and the shared memory per CTA.
 struct ShapePlan {
-  int Lc, nch, slot, fact, depth, smem;
+  int Lc, nch, slot, fact, depth, smem, vg, vbytes;
 };
 static ShapePlan plan_shape(const qp_dims& d, int cs, int esz, const qp_settings* s) {
   ShapePlan p;
@@ -218,19 +218,25 @@ static ShapePlan plan_shape(const qp_dims& d, int cs, int esz, const qp_settings
   p.Lc = (d.N + cs - 1) / cs;
   p.nch = (d.N + p.Lc - 1) / p.Lc;
   p.slot = std::max(std::max(std::max(bws, fws), msz), std::max(std::max(d.nx * ldu, d.nx * ldc), cds));
+  p.vg = 0;
   auto lay_total = [&](int depth, int fact) {
-    return smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, ldx, ldu, ldv, ldf, depth, p.slot, esz, fact).total;
+    return smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, ldx, ldu, ldv, ldf, depth, p.slot, esz, fact, p.vg).total;
   };
+  // long horizons: when even the smallest layout (tree, ring depth 2) cannot
+  // hold the per-chunk vectors, they move to a per-CTA global region
+  if (lay_total(2, 1) > 227 * 1024) p.vg = 1;
   p.fact = (s->factorization == 1 || s->precision == GPUSLS_TF32 || d.nu > FACT_MAX_NU) ? 1 : 0;
   if (p.fact == 0 && lay_total(1, 0) > 227 * 1024) p.fact = 1;
   p.depth = lay_total(3, p.fact) > 227 * 1024 ? 2 : 3;
   p.smem = lay_total(p.depth, p.fact);
+  p.vbytes = smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, ldx, ldu, ldv, ldf, p.depth, p.slot, esz, p.fact, p.vg)
+                 .vbytes;
   return p;
 }
 
 static bool dims_ok(const qp_dims& d) {
   return d.nx >= 1 && d.nx <= TILE && d.nu >= 1 && d.nu <= 32 && d.nc >= 0 && d.nc <= 64 && d.nf >= 0 &&
-         d.nf <= 64 && d.N >= 1 && d.N <= 1024;
+         d.nf <= 64 && d.N >= 1 && d.N <= GPUSLS_MAX_N;
 }
 
 extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dims, const double* A, const double* B,
@@ -291,8 +297,9 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   h->hdesc.resize(batch);
   struct Sizes {
     size_t A, B, b, Q, R, S, q, r, C, D, CN, lo, hi, x0, Rhi, Sh, Rh, S0, V, scr, Abar, CK, F, FPi, J, K, KSig, CKSig, Sig,
-        c0, k0, CNSig, SigN, Tch, Uch, Theta, Xi, Gam, z, y, BW, FW, CD;
+        c0, k0, CNSig, SigN, Tch, Uch, Theta, Xi, Gam, z, y, BW, FW, CD, vec;
   };
+  std::vector<ShapePlan> plans(batch);
   std::vector<Sizes> sz(batch);
   for (int b = 0; b < batch; ++b) {
     const qp_dims& d = dims[b];
@@ -320,10 +327,12 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     int bws, fws, cds;
     bundle_sizes(d.nx, d.nu, d.nc, (int)ldx, (int)ldu, ldv, ldf, &bws, &fws, &cds);
     z.BW = al64(N * (size_t)bws); z.FW = al64(N * (size_t)fws); z.CD = al64(N * (size_t)cds + 1);
+    plans[b] = plan_shape(d, cs, esz, s);
+    z.vec = plans[b].vg ? al64((size_t)cs * plans[b].vbytes / esz) : 0;
     toff[b] = tsz;
     tsz += z.A + z.B + z.b + z.Q + z.R + z.S + z.q + z.r + z.C + z.D + z.CN + z.lo + z.hi + z.x0 + z.Rhi + z.Sh +
            z.Rh + z.S0 + 4 * z.V + z.scr + z.Abar + z.CK + z.F + z.FPi + z.J + z.K + z.KSig + z.CKSig + z.Sig + z.c0 + z.k0 +
-           z.CNSig + z.SigN + z.Tch + z.Uch + z.Theta + z.Xi + z.Gam + z.z + z.y + z.BW + z.FW + z.CD;
+           z.CNSig + z.SigN + z.Tch + z.Uch + z.Theta + z.Xi + z.Gam + z.z + z.y + z.BW + z.FW + z.CD + z.vec;
     doff[b] = dsz;
     dsz += al64((N + 1) * nx) + al64(N * nu) + 64;   // kg, kh, rho/flags slot
     // per-QP descriptor (pointers filled after allocation)
@@ -331,7 +340,9 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     memset(&D_, 0, sizeof(D_));
     D_.nx = d.nx; D_.nu = d.nu; D_.N = d.N; D_.nc = d.nc; D_.nf = d.nf; D_.m = (int)m;
     D_.ldx = (int)ldx; D_.ldu = (int)ldu; D_.ldc = (int)ldc;
-    const ShapePlan sp = plan_shape(d, cs, esz, s);
+    const ShapePlan& sp = plans[b];
+    D_.vg = sp.vg;
+    D_.vstride = sp.vbytes;
     D_.Lc = sp.Lc;
     D_.nch = sp.nch;
     D_.nlev = nlev;
@@ -394,6 +405,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     D_.CNSig = take(z.CNSig); D_.SigN = take(z.SigN); D_.Tch = take(z.Tch); D_.Uch = take(z.Uch);
     D_.Theta = take(z.Theta); D_.Xi = take(z.Xi); D_.Gam = take(z.Gam); D_.z = take(z.z); D_.y = take(z.y);
     D_.BW = take(z.BW); D_.FW = take(z.FW); D_.CD = take(z.CD);
+    D_.vec = z.vec ? take(z.vec) : nullptr;
     h->tx0[b] = D_.x0;
     D_.A64 = A64 + po.A; D_.B64 = B64 + po.B; D_.b64 = b64 + po.c; D_.Q64 = Q64 + po.Q; D_.R64 = R64 + po.R;
     D_.S64 = S64 + po.S; D_.q64 = q64 + po.q; D_.r64 = r64 + po.r; D_.C64 = C64 + po.C; D_.D64 = D64 + po.D;

@@ -38,6 +38,8 @@ struct QPDesc {
   int ldv, ldf;     // row strides of the stacked vectors [l; omega] and [x; k]
   int depth, slot;  // cp.async ring depth and slot size (elements)
   int fact;         // factorization schedule: 0 blocked (leaf-structured combines), 1 tree
+  int vg;           // 1: per-chunk vectors in the global region vec (long horizons), 0: shared memory
+  int vstride;      // bytes of one CTA's part of vec
   // problem (T)
   void *A, *B, *b, *Q, *R, *S, *q, *r, *C, *D, *CN, *lo, *hi, *x0;
   // factorization workspace (T)
@@ -50,6 +52,7 @@ struct QPDesc {
   void *BW, *FW, *CD;
   // ADMM state (T)
   void *z, *y;
+  void* vec;        // vg: per-CTA vector regions [cluster][vstride bytes]
   // FP64 copies (dense, caller layout) and scratch
   double *A64, *B64, *b64, *Q64, *R64, *S64, *q64, *r64, *C64, *D64, *CN64, *lo64, *hi64, *x064;
   double *kg, *kh;
@@ -103,6 +106,7 @@ struct SmemLayout {
   int part, perm, flag, bar, swp, gath;
   int uni;     // bytes of the union region (ring / dense scratch / factorization buffers)
   int total;
+  int vbytes;  // vg: bytes of the per-CTA global region holding z, y, w, l, x, kt, v, d, u
 };
 
 constexpr int MAX_RING = 8;   // ring slots (mbarriers) at most
@@ -154,8 +158,13 @@ __host__ __device__ inline FactLayout fact_layout(int nx, int nu, int nc, int nf
 // the one-warp inverse of the nu x nu blocks.
 constexpr int FACT_MAX_NU = 32;
 
+// vg = 1 (long horizons): the per-chunk vectors z, y, w, l, x, kt, v, d, u,
+// whose size grows with the chunk length, live in a per-CTA region of global
+// memory (offsets relative to its base, vbytes long) instead of shared
+// memory; the kernel reaches them through the same generic pointers.
 __host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf, int Lc, int nch, int ldx, int ldu,
-                                                  int ldv, int ldf, int depth, int slot, int esz, int fact) {
+                                                  int ldv, int ldf, int depth, int slot, int esz, int fact,
+                                                  int vg = 0) {
   SmemLayout s;
   int off = 0;
   const int ring_b = depth * slot * esz;
@@ -169,15 +178,18 @@ __host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf
   s.gjbuf = s.gj + TILE * GJ_LD * esz;
   off = al16(uni);
   const int rows = Lc * nc + nf;
-  s.z = off; off = al16(off + rows * esz);
-  s.y = off; off = al16(off + rows * esz);
-  s.w = off; off = al16(off + rows * esz);
-  s.l = off; off = al16(off + (Lc + 1) * ldv * esz);
-  s.x = off; off = al16(off + (Lc + 1) * ldf * esz);
-  s.kt = off; off = al16(off + Lc * ldu * esz);
-  s.v = off; off = al16(off + rows * esz);
-  s.d = off; off = al16(off + (Lc + 1) * ldx * esz);
-  s.u = off; off = al16(off + Lc * ldu * esz);
+  int voff = 0;
+  int& vo = vg ? voff : off;
+  s.z = vo; vo = al16(vo + rows * esz);
+  s.y = vo; vo = al16(vo + rows * esz);
+  s.w = vo; vo = al16(vo + rows * esz);
+  s.l = vo; vo = al16(vo + (Lc + 1) * ldv * esz);
+  s.x = vo; vo = al16(vo + (Lc + 1) * ldf * esz);
+  s.kt = vo; vo = al16(vo + Lc * ldu * esz);
+  s.v = vo; vo = al16(vo + rows * esz);
+  s.d = vo; vo = al16(vo + (Lc + 1) * ldx * esz);
+  s.u = vo; vo = al16(vo + Lc * ldu * esz);
+  s.vbytes = vg ? (voff + 255) & ~255 : 0;
   s.pe = off; off = al16(off + TILE * esz);
   s.xs = off; off = al16(off + TILE * esz);
   s.slotL = off; off = al16(off + TILE * esz);

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   QPDesc& d = dsh;
 
   const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.nch, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
-                                     (int)sizeof(T), d.fact);
+                                     (int)sizeof(T), d.fact, d.vg);
   // One context per CTA in shared memory, filled by thread 0: every thread
   // reads the same fields, and a per-thread copy would sit in local memory
   // that the L1 left beside two CTAs' shared memory cannot hold.
@@ -51,15 +51,17 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     c.gj = reinterpret_cast<T*>(smem + lay.gj);
     c.gjbuf = reinterpret_cast<T*>(smem + lay.gjbuf);
     c.ring = reinterpret_cast<T*>(smem + lay.ring);
-    c.zS = reinterpret_cast<T*>(smem + lay.z);
-    c.yS = reinterpret_cast<T*>(smem + lay.y);
-    c.wS = reinterpret_cast<T*>(smem + lay.w);
-    c.lS = reinterpret_cast<T*>(smem + lay.l);
-    c.xS = reinterpret_cast<T*>(smem + lay.x);
-    c.ktS = reinterpret_cast<T*>(smem + lay.kt);
-    c.vS = reinterpret_cast<T*>(smem + lay.v);
-    c.dS = reinterpret_cast<T*>(smem + lay.d);
-    c.uS = reinterpret_cast<T*>(smem + lay.u);
+    // the per-chunk vectors: shared memory, or this CTA's global region (vg)
+    unsigned char* vb = d.vg ? static_cast<unsigned char*>(d.vec) + (size_t)rank * d.vstride : smem;
+    c.zS = reinterpret_cast<T*>(vb + lay.z);
+    c.yS = reinterpret_cast<T*>(vb + lay.y);
+    c.wS = reinterpret_cast<T*>(vb + lay.w);
+    c.lS = reinterpret_cast<T*>(vb + lay.l);
+    c.xS = reinterpret_cast<T*>(vb + lay.x);
+    c.ktS = reinterpret_cast<T*>(vb + lay.kt);
+    c.vS = reinterpret_cast<T*>(vb + lay.v);
+    c.dS = reinterpret_cast<T*>(vb + lay.d);
+    c.uS = reinterpret_cast<T*>(vb + lay.u);
     c.pe = reinterpret_cast<T*>(smem + lay.pe);
     c.xs = reinterpret_cast<T*>(smem + lay.xs);
     c.slotL = reinterpret_cast<T*>(smem + lay.slotL);

@@ -289,6 +289,53 @@ def humanoid_75d(seed: int = 0, N: int = 40) -> QP:
     return legged(seed, 75, 21, N, tag=4)
 
 
+def long_horizon(seed: int = 0, links: int = 15, N: int = 3000, dt: float = 0.01) -> QP:
+    """Long-horizon workload shaped like a torque-limited n-link pendulum
+    linearized along a trajectory (Sec. V-A's horizon study: more than 1.35e5
+    decision variables at N = 3000, i.e. nx + nu = 45 per stage): state
+    (angles, rates), nx = 2 links, nu = links,
+        A_k = [[I, dt I], [-dt K_k, I - dt Dmp]],  B_k = [[0], [dt M^-1]],
+    with a chain stiffness K_k = diag(s) + 0.5 L (L the path Laplacian,
+    s ~ U[0.5, 1.5]) plus a symmetric per-stage perturbation 0.05 sym(G_k),
+    damping Dmp = 0.1 I, M^-1 = I + 0.05 sym(G); Q = diag(U[1, 5] on angles,
+    U[0.05, 0.2] on rates), Q_N = Q, R = diag U[0.01, 0.1]; torque limits
+    |u| <= 1 (nc = nu two-sided rows), no terminal rows; angle targets of
+    +-1 rad (q_k = -Q x_ref) that the torque limits make active;
+    x0 = (U[-0.5, 0.5] angles, zero rates)."""
+    g = rng(14, seed, links, N)
+    n = links
+    nx, nu = 2 * n, n
+    lap = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    lap[0, 0] = lap[-1, -1] = 1.0
+    Kc = np.diag(g.uniform(0.5, 1.5, n)) + 0.5 * lap
+    Gm = g.standard_normal((n, n))
+    Minv = np.eye(n) + 0.05 * (Gm + Gm.T) / 2.0
+    A = np.zeros((N, nx, nx))
+    B = np.zeros((N, nx, nu))
+    Gk = g.standard_normal((N, n, n))
+    for k in range(N):
+        Kk = Kc + 0.05 * (Gk[k] + Gk[k].T) / 2.0
+        A[k, :n, :n] = np.eye(n)
+        A[k, :n, n:] = dt * np.eye(n)
+        A[k, n:, :n] = -dt * Kk
+        A[k, n:, n:] = (1.0 - 0.1 * dt) * np.eye(n)
+        B[k, n:, :] = dt * Minv
+    qd = np.concatenate([g.uniform(1.0, 5.0, n), g.uniform(0.05, 0.2, n)])
+    rd = g.uniform(0.01, 0.1, nu)
+    Q = np.repeat(np.diag(qd)[None], N + 1, axis=0)
+    R = np.repeat(np.diag(rd)[None], N, axis=0)
+    C = np.zeros((N, nu, nx))
+    D = np.repeat(np.eye(nu)[None], N, axis=0)
+    hi = np.ones(N * nu)
+    lo = -hi.copy()
+    xref = np.concatenate([np.where(np.arange(n) % 2 == 0, 1.0, -1.0), np.zeros(n)])
+    q = np.repeat(-(np.diag(qd) @ xref)[None], N + 1, axis=0)
+    x0 = np.concatenate([g.uniform(-0.5, 0.5, n), np.zeros(n)])
+    e = _empty(nx, nu, N)
+    return QP(A=A, B=B, c=e["c"], Q=Q, R=R, S=e["S"], q=q, r=e["r"], C=C, D=D, CN=np.zeros((0, nx)), lo=lo, hi=hi,
+              x0=x0, name=f"pendulum{n}-N{N}-s{seed}")
+
+
 def tiny(seed: int = 0, nx: int = 2, nu: int = 1, N: int = 3, box_u: float = 0.3,
          n_half: int = 1, S_nonzero: bool = True, b_nonzero: bool = True) -> QP:
     """Tiny random QP for brute-force pins: dense random A, B, SPD Q, R, random
