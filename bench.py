@@ -365,6 +365,57 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
                                  "step": "sls_solve (per-j tau) + tighten + warm tightened QP solve (FP32) + sls_tau"}
     f.close()
 
+    # RTI control steps (Sec. IV-C) on the paper's analytic models: the planar
+    # quadrotor (App. D, N=25) robust (linearization + SLS update from the
+    # previous duals + tightened QP + duals) and classical, and a batch of
+    # 256 disturbed Dubins-car closed loops (App. C, N=30) per classical step
+    from paper_2604_07644_b300.api import SQP
+    s_rti = native.default_settings(precision=native.GPUSLS_FP64, max_iter=20000)
+    mq = W.quad2d(0, N=25)
+    for robust in (True, False):
+        sq = SQP(mq, 1, s_rti, robust=robust, stream=stream)
+        X0, U0 = mq.initial_guess()
+        sq.set_nominal(X0[None], U0[None])
+        sq.set_state(mq.x0[None])
+        sq.solve(6)
+        Wd = torch.from_numpy(W.disturbances(3, steps + 2, 1, mq.nx)).to(dev)
+        with torch.cuda.stream(stream):
+            for t in range(2):
+                sq.rti_step(Wd[t])
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for t in range(steps):
+                info = sq.rti_step(Wd[2 + t])
+            e1.record(stream)
+            torch.cuda.synchronize()
+        out["quad2d_rti_" + ("robust" if robust else "classical")] = {
+            "ms_per_step": e0.elapsed_time(e1) / steps, "qp_iters_last": info[0]["iters"],
+            "step": "linearize + " + ("SLS(tau_prev) + tighten + " if robust else "") + "QP (FP64) + simulate + shift"}
+        sq.close()
+    md = W.dubins(0)
+    Bd = 256
+    sq = SQP(md, Bd, s_rti, stream=stream)
+    X0, U0 = md.initial_guess()
+    sq.set_nominal(np.repeat(X0[None], Bd, 0), np.repeat(U0[None], Bd, 0))
+    sq.set_state(np.repeat(md.x0[None], Bd, 0))
+    sq.solve(6)
+    Wd = torch.from_numpy(W.disturbances(4, steps + 1, Bd, md.nx)).to(dev)
+    with torch.cuda.stream(stream):
+        sq.rti_step(Wd[0])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(steps):
+            sq.rti_step(Wd[1 + t])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    out["dubins_rti_batch256"] = {"ms_per_step": e0.elapsed_time(e1) / steps, "rollouts": Bd,
+                                  "ms_per_rollout_step": e0.elapsed_time(e1) / steps / Bd}
+    sq.close()
+
     # checks on the headline's solutions (snapshot of the learned step's outputs)
     x, u = sol
     viol, ox, ou = 0.0, 0, 0

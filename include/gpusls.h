@@ -368,6 +368,91 @@ int qp_graph_kernel_count(qp_graph* g, int32_t* n);
 void qp_graph_destroy(qp_graph* g);
 
 /* ------------------------------------------------------------------------ */
+/* Analytic models and the SQP / RTI outer loop (Sec. III-B, Sec. IV-C,      */
+/* App. C, App. D)                                                          */
+/* ------------------------------------------------------------------------ */
+#define GPUSLS_MODEL_DUBINS 0   /* App. C: x = (p_x, p_y, theta), u = omega, speed v */
+#define GPUSLS_MODEL_QUAD2D 1   /* App. D: x = (p_x, p_y, phi, v_x, v_y, phidot), u = thrusts;
+                                   explicit Euler step of the continuous dynamics */
+#define GPUSLS_MODEL_MAX_OBS 16
+
+/* One model instance.  Cost: 1/2 |x - xref|^2_diag(Qd) + 1/2 |u - uref|^2_diag(Rd)
+ * per stage, 1/2 |x_N - xref|^2_diag(QNd) terminal.  Constraints: u_lo <= u <=
+ * u_hi (two-sided rows) and per obstacle (c_x, c_y, r) in obs[3 o .. 3 o + 2]:
+ * r^2 - (p_x - c_x)^2 - (p_y - c_y)^2 <= 0 on every stage and on x_N
+ * (eq. obstacle_constraints).  E: disturbance scaling [nx][nx] row-major.
+ * Only the first nx (nu) entries of the per-state (per-input) arrays are read. */
+typedef struct model_spec {
+  int32_t kind, N, n_obs, pad;
+  double dt, v, mass, grav, arm, inertia;
+  double u_lo[2], u_hi[2];
+  double xref[6], uref[2], Qd[6], Rd[2], QNd[6];
+  double E[36];
+  double obs[3 * GPUSLS_MODEL_MAX_OBS];
+} model_spec;
+
+/* model_dims: the LTV-QP dims of a model: nx, nu, N, nc = nu + n_obs, nf = n_obs. */
+int model_dims(const model_spec* m, qp_dims* d);
+
+/* model_linearize: the LTV-QP eq. sqp_qp around nominal trajectories, every
+ * stage of every trajectory in parallel (the parallel linearization of
+ * Fig. fig:schematic).  X [batch][N+1][nx], U [batch][N][nu], x0bar
+ * [batch][nx] (device).  Outputs are pools in the qp_setup layouts
+ * (batch QPs of identical dims): A_k, B_k the analytic Jacobians;
+ * c_k = f(x_k, u_k) - x_{k+1} (the paper's b_k); Gauss-Newton Q_k =
+ * diag(Qd), R_k = diag(Rd), S_k = 0, Q_N = diag(QNd); q_k, r_k, q_N the cost
+ * gradients at the nominal; stage rows [input box; obstacles] with C =
+ * (0; grad g_o), D = (I; 0), bounds (u_lo - u_k, u_hi - u_k) and
+ * (-inf, -g_o(x_k)); terminal obstacle rows likewise; dx0 = x0bar - x_0.
+ * Synchronous on `stream`. */
+int model_linearize(const model_spec* m, int32_t batch, const double* X, const double* U, const double* x0bar,
+                    double* A, double* B, double* c, double* Q, double* R, double* S, double* q, double* r,
+                    double* C, double* D, double* CN, double* lo, double* hi, double* dx0, void* stream);
+
+/* model_merit: l1 merit phi = J(X + a dX, U + a dU) + w (sum_k |f(x_k, u_k) -
+ * x_{k+1}|_1 + |x_0 - x0bar|_1 + input-box and obstacle violations) per
+ * trajectory, a = alpha[b] (device [batch]; NULL, or dX = dU = NULL: a = 0);
+ * out: device [batch].  The step-size search of sqp_solve uses it. */
+int model_merit(const model_spec* m, int32_t batch, const double* X, const double* U, const double* dX,
+                const double* dU, const double* alpha, const double* x0bar, double w, double* out, void* stream);
+
+/* sqp_setup: a batch of `batch` trajectories of one model, with the QP
+ * settings s for the inner LTV-QP solves.  robust != 0 (batch 1, N <= 512)
+ * adds the SLS controller and tightening of each RTI step (fastsls_solve with
+ * E_j = E, Qbar = Rbar = QbarN = I).  Allocates all device memory. */
+typedef struct sqp_handle sqp_handle;
+int sqp_setup(sqp_handle** h, const model_spec* m, int32_t batch, const qp_settings* s, int32_t robust,
+              void* stream);
+
+/* sqp_solve: `iters` SQP iterations (Sec. III-B) in place on the device
+ * trajectories X, U from the initial states x0bar: linearize, solve the
+ * LTV-QPs (warm-started from the previous iteration's ADMM state), and step
+ * x <- x + alpha dx, u <- u + alpha du with alpha in {1, 1/2, ..., 1/128}
+ * chosen per trajectory as the first that lowers the l1 merit (weight
+ * merit_w; line_search == 0: alpha = 1).  alpha_out: HOST [iters][batch]
+ * or NULL; info: HOST qp_info [batch] of the last QP solve, or NULL.
+ * Returns the worst QP status (GPUSLS_OK / GPUSLS_MAX_ITER) or an error. */
+int sqp_solve(sqp_handle* h, double* X, double* U, const double* x0bar, int32_t iters, double merit_w,
+              int32_t line_search, double* alpha_out, qp_info* info);
+
+/* rti_step: one real-time iteration (Sec. IV-C) for every trajectory: one
+ * linearization at the nominal (X, U) and the measured state x, one QP solve
+ * (robust handles: the controller update from the previous step's duals,
+ * the tightened QP and new duals, as fastsls_solve with one step), the full
+ * step, the first input applied to the disturbed plant x <- f(x, u_0) + E w
+ * (W [batch][nx], device, or NULL for no disturbance), and the nominal
+ * shifted one stage (the last stage kept).  u_applied [batch][nu] (device or
+ * NULL) receives u_0; hk [N][nc], hf [nf] (robust only, device or NULL)
+ * receive the step's margins. */
+int rti_step(sqp_handle* h, double* X, double* U, double* x, const double* W, double* u_applied,
+             double* hk, double* hf, qp_info* info);
+
+/* sqp_reset_duals: cold ADMM state and zero controller duals (next rti_step
+ * starts the alternation from tau = 0). */
+int sqp_reset_duals(sqp_handle* h);
+void sqp_destroy(sqp_handle* h);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free KKT residual (the paper has no counterpart)              */
 /* ------------------------------------------------------------------------ */
 /* Largest scratch (in doubles) gpusls_kkt_noalloc can use: it needs

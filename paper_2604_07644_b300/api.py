@@ -360,6 +360,126 @@ class FastSLS:
         self.sls.close()
 
 
+def model_spec(ms) -> native.model_spec:
+    """The C struct of a workloads.ModelSpec (field by field)."""
+    m = native.model_spec()
+    m.kind = native.GPUSLS_MODEL_DUBINS if ms.kind == "dubins" else native.GPUSLS_MODEL_QUAD2D
+    m.N, m.n_obs = int(ms.N), int(ms.n_obs)
+    if m.n_obs > native.GPUSLS_MODEL_MAX_OBS:
+        raise ValueError("too many obstacles")
+    m.dt, m.v, m.mass, m.grav, m.arm, m.inertia = (float(ms.dt), float(ms.v), float(ms.mass), float(ms.grav),
+                                                   float(ms.arm), float(ms.inertia))
+    for name in ("u_lo", "u_hi", "xref", "uref", "Qd", "Rd", "QNd"):
+        arr = getattr(m, name)
+        for i, v in enumerate(np.asarray(getattr(ms, name), dtype=float).ravel()):
+            arr[i] = float(v)
+    for i, v in enumerate(np.asarray(ms.E, dtype=float).ravel()):
+        m.E[i] = float(v)
+    for i, v in enumerate(np.asarray(ms.obstacles, dtype=float).ravel()):
+        m.obs[i] = float(v)
+    return m
+
+
+def linearize(ms, X, U, x0bar, device="cuda"):
+    """model_linearize on a batch of nominal trajectories (numpy [batch, ...]);
+    returns one dict of numpy arrays per trajectory (the LTV-QP arrays and
+    the initial deviation dx0)."""
+    lib = native.load()
+    m = model_spec(ms)
+    d = native.qp_dims()
+    native.check(lib.model_dims(C.byref(m), C.byref(d)), "model_dims")
+    X = np.asarray(X, dtype=np.float64)
+    Bn = X.shape[0]
+    nx, nu, N, nc, nf = d.nx, d.nu, d.N, d.nc, d.nf
+    shapes = dict(A=(N, nx, nx), B=(N, nx, nu), c=(N, nx), Q=(N + 1, nx, nx), R=(N, nu, nu), S=(N, nu, nx),
+                  q=(N + 1, nx), r=(N, nu), C=(N, nc, nx), D=(N, nc, nu), CN=(nf, nx), lo=(N * nc + nf,),
+                  hi=(N * nc + nf,), dx0=(nx,))
+    out = {k: torch.empty(max(1, Bn * int(np.prod(v))), dtype=torch.float64, device=device)
+           for k, v in shapes.items()}
+    tX, tU, tx = _dev64(X, device), _dev64(U, device), _dev64(x0bar, device)
+    keys = ("A", "B", "c", "Q", "R", "S", "q", "r", "C", "D", "CN", "lo", "hi", "dx0")
+    native.check(lib.model_linearize(C.byref(m), Bn, _dptr(tX), _dptr(tU), _dptr(tx), *[_dptr(out[k]) for k in keys],
+                                     _stream_ptr(None)), "model_linearize")
+    res = []
+    for b in range(Bn):
+        res.append({k: out[k].cpu().numpy()[b * int(np.prod(v)):(b + 1) * int(np.prod(v))].reshape(v)
+                    for k, v in shapes.items()})
+    return res
+
+
+class SQP:
+    """sqp_setup / sqp_solve / rti_step over a batch of trajectories of one
+    model (workloads.ModelSpec).  X [batch, N+1, nx], U [batch, N, nu] and
+    the states x [batch, nx] live on the device (torch tensors) and are
+    updated in place by the library."""
+
+    def __init__(self, ms, batch: int, settings: native.qp_settings | None = None, robust: bool = False,
+                 stream=None, device="cuda"):
+        self.lib = native.load()
+        self.ms = ms
+        self.spec = model_spec(ms)
+        self.batch = batch
+        self.device = device
+        self.settings = settings or native.default_settings()
+        d = native.qp_dims()
+        native.check(self.lib.model_dims(C.byref(self.spec), C.byref(d)), "model_dims")
+        self.dims = (d.nx, d.nu, d.N, d.nc, d.nf)
+        h = C.c_void_p()
+        native.check(self.lib.sqp_setup(C.byref(h), C.byref(self.spec), batch, C.byref(self.settings), int(robust),
+                                        _stream_ptr(stream)), "sqp_setup")
+        self.h = h
+        nx, nu, N, nc, nf = self.dims
+        self.X = torch.zeros(batch, N + 1, nx, dtype=torch.float64, device=device)
+        self.U = torch.zeros(batch, N, nu, dtype=torch.float64, device=device)
+        self.x = torch.zeros(batch, nx, dtype=torch.float64, device=device)
+        self.u0 = torch.zeros(batch, nu, dtype=torch.float64, device=device)
+        self.hk = torch.zeros(max(1, N * nc), dtype=torch.float64, device=device)
+        self.hf = torch.zeros(max(1, nf), dtype=torch.float64, device=device)
+
+    def set_nominal(self, X, U):
+        self.X.copy_(torch.as_tensor(np.asarray(X, dtype=np.float64).reshape(self.X.shape)))
+        self.U.copy_(torch.as_tensor(np.asarray(U, dtype=np.float64).reshape(self.U.shape)))
+
+    def set_state(self, x):
+        self.x.copy_(torch.as_tensor(np.asarray(x, dtype=np.float64).reshape(self.x.shape)))
+
+    def solve(self, iters: int, merit_w: float = 100.0, line_search: bool = True):
+        """sqp_solve from the current nominal and states; returns the step
+        sizes [iters, batch] and the last QP infos."""
+        a = (C.c_double * (iters * self.batch))()
+        info = (native.qp_info * self.batch)()
+        st = self.lib.sqp_solve(self.h, _dptr(self.X), _dptr(self.U), _dptr(self.x), int(iters), float(merit_w),
+                                int(bool(line_search)), a, info)
+        native.check(st, "sqp_solve")
+        return np.array(a[:]).reshape(iters, self.batch), [dict(status=i.status, iters=i.iters, kkt=i.kkt)
+                                                            for i in info]
+
+    def rti_step(self, W=None):
+        """rti_step with the disturbances W [batch, nx] (numpy or device
+        tensor; None: no disturbance); returns the QP infos."""
+        tW = None if W is None else _dev64(np.asarray(W, dtype=np.float64) if not isinstance(W, torch.Tensor) else W,
+                                           self.device)
+        info = (native.qp_info * self.batch)()
+        st = self.lib.rti_step(self.h, _dptr(self.X), _dptr(self.U), _dptr(self.x), _dptr(tW), _dptr(self.u0),
+                               _dptr(self.hk), _dptr(self.hf), info)
+        native.check(st, "rti_step")
+        return [dict(status=i.status, iters=i.iters, kkt=i.kkt) for i in info]
+
+    def reset_duals(self):
+        native.check(self.lib.sqp_reset_duals(self.h), "sqp_reset_duals")
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.lib.sqp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class MLP:
     """The warm-start network (mlp_* in include/gpusls.h); FP32 device tensors."""
 

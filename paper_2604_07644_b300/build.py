@@ -13,7 +13,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgpusls.so")
-SOURCES = ["qp.cu", "qp_kernel_f32.cu", "qp_kernel_f64.cu", "sls.cu", "mlp.cu", "noalloc.cu"]
+SOURCES = ["qp.cu", "qp_kernel_f32.cu", "qp_kernel_f64.cu", "sls.cu", "mlp.cu", "models.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -48,6 +48,19 @@ class qp_info(C.Structure):
                 ("rho", C.c_double), ("r_prim", C.c_double), ("r_dual", C.c_double), ("kkt", C.c_double)]
 
 
+GPUSLS_MODEL_DUBINS = 0
+GPUSLS_MODEL_QUAD2D = 1
+GPUSLS_MODEL_MAX_OBS = 16
+
+
+class model_spec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("N", C.c_int32), ("n_obs", C.c_int32), ("pad", C.c_int32),
+                ("dt", C.c_double), ("v", C.c_double), ("mass", C.c_double), ("grav", C.c_double),
+                ("arm", C.c_double), ("inertia", C.c_double), ("u_lo", C.c_double * 2), ("u_hi", C.c_double * 2),
+                ("xref", C.c_double * 6), ("uref", C.c_double * 2), ("Qd", C.c_double * 6), ("Rd", C.c_double * 2),
+                ("QNd", C.c_double * 6), ("E", C.c_double * 36), ("obs", C.c_double * (3 * GPUSLS_MODEL_MAX_OBS))]
+
+
 P = C.c_void_p
 DP = C.c_void_p   # device pointer to double
 
@@ -87,6 +100,15 @@ SIGNATURES = {
     "qp_graph_launch": (C.c_int, [P, P]),
     "qp_graph_destroy": (None, [P]),
     "qp_graph_kernel_count": (C.c_int, [P, C.POINTER(C.c_int32)]),
+    "model_dims": (C.c_int, [C.POINTER(model_spec), C.POINTER(qp_dims)]),
+    "model_linearize": (C.c_int, [C.POINTER(model_spec), C.c_int32] + [DP] * 17 + [P]),
+    "model_merit": (C.c_int, [C.POINTER(model_spec), C.c_int32] + [DP] * 6 + [C.c_double, DP, P]),
+    "sqp_setup": (C.c_int, [C.POINTER(P), C.POINTER(model_spec), C.c_int32, C.POINTER(qp_settings), C.c_int32, P]),
+    "sqp_solve": (C.c_int, [P, DP, DP, DP, C.c_int32, C.c_double, C.c_int32, C.POINTER(C.c_double),
+                            C.POINTER(qp_info)]),
+    "rti_step": (C.c_int, [P] + [DP] * 7 + [C.POINTER(qp_info)]),
+    "sqp_reset_duals": (C.c_int, [P]),
+    "sqp_destroy": (None, [P]),
     "gpusls_kkt_noalloc": (C.c_int, [qp_dims] + [DP] * 18 + [P]),
 }
 

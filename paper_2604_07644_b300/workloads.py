@@ -563,6 +563,125 @@ def sls_small(seed: int = 0, nx: int = 3, nu: int = 2, N: int = 5, nc: int = 3, 
 
 
 # ----------------------------------------------------------------------------
+# analytic models of App. C (Dubins car) and App. D (planar quadrotor) for
+# the SQP / RTI outer loop: parameters, references, weights, obstacles and
+# disturbance draws (data only; the dynamics live in the oracle and the
+# library)
+# ----------------------------------------------------------------------------
+
+MODEL_DUBINS, MODEL_QUAD2D = 0, 1
+MODEL_MAX_OBS = 16
+
+
+@dataclass
+class ModelSpec:
+    """One model instance: kind ("dubins" / "quad2d"), horizon N, time step,
+    obstacles [n_obs, 3] (c_x, c_y, r), input box, tracking reference and
+    diagonal weights (stage Qd, Rd; terminal QNd), disturbance scaling E and
+    the physical parameters (Dubins speed v; quadrotor m, g, L, J of App. D)."""
+    kind: str
+    N: int
+    dt: float
+    obstacles: np.ndarray
+    u_lo: np.ndarray
+    u_hi: np.ndarray
+    xref: np.ndarray
+    uref: np.ndarray
+    Qd: np.ndarray
+    Rd: np.ndarray
+    QNd: np.ndarray
+    E: np.ndarray
+    x0: np.ndarray
+    v: float = 1.0
+    mass: float = 2.0576
+    grav: float = 9.81
+    arm: float = 0.25
+    inertia: float = 0.01
+
+    @property
+    def nx(self) -> int:
+        return 3 if self.kind == "dubins" else 6
+
+    @property
+    def nu(self) -> int:
+        return 1 if self.kind == "dubins" else 2
+
+    @property
+    def n_obs(self) -> int:
+        return self.obstacles.shape[0]
+
+    def dims(self) -> tuple[int, int, int, int, int]:
+        return (self.nx, self.nu, self.N, self.nu + self.n_obs, self.n_obs)
+
+    def initial_guess(self) -> tuple[np.ndarray, np.ndarray]:
+        """Nominal to start SQP from: the state held at x0, inputs at u_ref;
+        for the Dubins car the states after x0 follow the chord from x0 to
+        the reference position at speed v, heading along it."""
+        X = np.repeat(self.x0[None], self.N + 1, axis=0)
+        if self.kind == "dubins":
+            d = self.xref[:2] - self.x0[:2]
+            th = float(np.arctan2(d[1], d[0]))
+            t = np.arange(1, self.N + 1) * self.dt * self.v
+            X[1:, 0] = self.x0[0] + t * np.cos(th)
+            X[1:, 1] = self.x0[1] + t * np.sin(th)
+            X[1:, 2] = th
+        U = np.repeat(self.uref[None], self.N, axis=0)
+        return X, U
+
+
+def dubins(seed: int = 0, N: int = 30, n_obs: int = 2) -> ModelSpec:
+    """Dubins car of App. C: v = 1 m/s, dt = 0.1 s, |omega| <= 2, from the
+    origin heading +x towards a goal at (2.6, 1.2) (the chord to it is
+    shorter than the N dt v = 3 m path, so the car must turn) past obstacles
+    of radius U[0.3, 0.45] whose edges sit 0.05 to 0.15 m from the chord, on
+    alternating sides; E = 2.5e-2 I_3."""
+    g = rng(20, seed, N)
+    goal = np.array([2.6, 1.2])
+    d = goal / np.linalg.norm(goal)
+    nrm = np.array([-d[1], d[0]])
+    obs = np.zeros((n_obs, 3))
+    for i in range(n_obs):
+        r = g.uniform(0.3, 0.45)
+        side = 1.0 if i % 2 == 0 else -1.0
+        s_ = (0.35 + 0.4 * i / max(1, n_obs - 1) + g.uniform(-0.05, 0.05)) * np.linalg.norm(goal)
+        cxy = s_ * d + side * (r + g.uniform(0.05, 0.15)) * nrm
+        obs[i] = [cxy[0], cxy[1], r]
+    return ModelSpec(kind="dubins", N=N, dt=0.1, obstacles=obs, u_lo=np.array([-2.0]), u_hi=np.array([2.0]),
+                     xref=np.array([goal[0], goal[1], 0.0]), uref=np.zeros(1), Qd=np.array([1.0, 1.0, 0.1]),
+                     Rd=np.array([0.1]), QNd=np.array([10.0, 10.0, 1.0]), E=2.5e-2 * np.eye(3),
+                     x0=np.zeros(3), v=1.0)
+
+
+def quad2d(seed: int = 0, N: int = 40, n_obs: int = 1) -> ModelSpec:
+    """Planar quadrotor of App. D (m = 2.0576, g = 9.81, L = 0.25, J = 0.01),
+    dt = 0.05 s, thrusts 0 <= u_i <= 20, from hover at the origin to a goal
+    at (2, 0) past obstacles of radius U[0.3, 0.4] whose edges sit 0.05 to
+    0.15 m from the straight path; E = 5e-2 diag(0, 0, 0, 1, 1, 0)."""
+    g = rng(21, seed, N)
+    mass, grav = 2.0576, 9.81
+    uh = mass * grav / 2.0
+    obs = np.zeros((n_obs, 3))
+    for i in range(n_obs):
+        r = g.uniform(0.3, 0.4)
+        side = 1.0 if i % 2 == 0 else -1.0
+        obs[i] = [1.0 + g.uniform(-0.2, 0.2) + 0.6 * i, side * (r + g.uniform(0.05, 0.15)), r]
+    Qd = np.array([5.0, 5.0, 1.0, 1.0, 1.0, 0.1])
+    return ModelSpec(kind="quad2d", N=N, dt=0.05, obstacles=obs, u_lo=np.zeros(2), u_hi=np.array([20.0, 20.0]),
+                     xref=np.array([2.0, 0.0, 0.0, 0.0, 0.0, 0.0]), uref=np.array([uh, uh]), Qd=Qd,
+                     Rd=np.array([0.1, 0.1]), QNd=10.0 * Qd, E=5e-2 * np.diag([0.0, 0, 0, 1, 1, 0]),
+                     x0=np.zeros(6), mass=mass, grav=grav)
+
+
+def disturbances(seed: int, steps: int, batch: int, nx: int) -> np.ndarray:
+    """Disturbance draws w [steps, batch, nx] in the unit ball (|w|_2 <= 1,
+    direction uniform, radius U[0, 1]^(1/nx))."""
+    g = rng(22, seed, steps, batch, nx)
+    w = g.standard_normal((steps, batch, nx))
+    w /= np.linalg.norm(w, axis=2, keepdims=True)
+    return w * g.uniform(0.0, 1.0, (steps, batch, 1)) ** (1.0 / nx)
+
+
+# ----------------------------------------------------------------------------
 # MLP initial weights (input to both the GPU trainer and the oracle)
 # ----------------------------------------------------------------------------
 
