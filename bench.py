@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpusls", choices=["gpusls", "reference"])
     p.add_argument("--batch", type=int, default=256)
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     p.add_argument("--cluster", type=int, default=8)
     p.add_argument("--plain-qps", type=int, default=2)
     p.add_argument("--cpu-sample", type=int, default=32)
@@ -484,7 +484,8 @@ def profile_case(args):
     if args.case in ("iter", "refactor"):
         qps = [fam.instance(100000 + i) for i in range(32)]
         # the launch shape the autotuner picks for the bench's batch (cluster 6)
-        s = native.default_settings(precision=native.GPUSLS_FP32, cluster=6, sigma=0, fixed_iters=1)
+        prec = {"fp32": native.GPUSLS_FP32, "fp64": native.GPUSLS_FP64, "mixed": native.GPUSLS_MIXED}[args.precision]
+        s = native.default_settings(precision=prec, cluster=6, sigma=0, fixed_iters=1)
         if args.case == "iter":
             s.fixed_iters = 100
         qb = QPBatch(qps, s)
@@ -541,15 +542,15 @@ def main():
     native.load()
     dev = f"cuda:{local}"
     stream = torch.cuda.Stream(device=dev)
-    prec = native.GPUSLS_FP32 if args.precision == "fp32" else native.GPUSLS_FP64
-    esz = 4 if prec == native.GPUSLS_FP32 else 8
+    prec = {"fp32": native.GPUSLS_FP32, "fp64": native.GPUSLS_FP64, "mixed": native.GPUSLS_MIXED}[args.precision]
+    esz = 8 if prec == native.GPUSLS_FP64 else 4
     fam = W.family(0)
     base = 100000 + rank * args.batch
     qps = [fam.instance(base + i) for i in range(args.batch)]
     nx, nu, N, nc, nf = qps[0].dims()
     settings = native.default_settings(precision=prec, cluster=args.cluster, max_refine=3,
                                        fallback_iters=args.fallback, max_iter=6000,
-                                       eps_floor=1e-5 if prec == native.GPUSLS_FP32 else 1e-7,
+                                       eps_floor=1e-7 if prec == native.GPUSLS_FP64 else 1e-5,
                                        schedule=0 if args.index_order else 1)
     tuned = None
     if not args.no_autotune:
@@ -625,6 +626,29 @@ def main():
     t_cold = timed(step_cold, max(1, args.steps))
     cold_ms = t_cold / (max(1, args.steps) * args.batch * ws)
     inf_c = read_info(False)
+
+    # the same learned step with the factorization's block products on the
+    # tensor cores (GPUSLS_MIXED: three TF32 passes, FP64 per-stage solves)
+    mixed = None
+    if prec == native.GPUSLS_FP32:
+        sm = native.default_settings(precision=native.GPUSLS_MIXED, cluster=int(settings.cluster),
+                                     occupancy=int(settings.occupancy), max_refine=3, fallback_iters=args.fallback,
+                                     max_iter=6000, eps_floor=1e-5, schedule=0 if args.index_order else 1)
+        with torch.cuda.stream(stream):
+            hm = QPBatch(qps, sm, stream=stream, device=dev, pools=hb.pools)
+            gm = hm.graph(mlp, feats)
+            for _ in range(2):
+                gm.launch(stream)
+        tm = timed(lambda: gm.launch(stream), max(1, args.steps))
+        im = gm.info()
+        mixed = {"ms_per_qp": tm / (max(1, args.steps) * args.batch * ws),
+                 "iters_mean": float(np.mean([i["iters"] for i in im])),
+                 "kkt_max": float(np.max([i["kkt"] for i in im])),
+                 "all_converged": all(i["status"] == 0 for i in im),
+                 "mode": "GPUSLS_MIXED: blocked-factorization block products in three TF32 passes (mma.sync), "
+                         "FP64 per-stage solves, FP64 KKT gate"}
+        gm.close()
+        hm.close()
 
     # plain FP64 single-QP solves (cold, one QP per launch)
     plain = []
@@ -762,6 +786,7 @@ def main():
                            "l2": "inputs larger than L2 (FP64 pools 2.2 GB per 256 QPs)",
                            "model": os.path.basename(args.model)},
                 "batched_cold_ms_per_qp": cold_ms,
+                "mixed_precision": mixed,
                 "plain_fp64_ms_per_qp": plain_ms,
                 "iters_mean": float(np.mean(iters)), "iters_mean_cold": float(np.mean([i.iters for i in inf_c])),
                 "refactors_mean": float(np.mean(refs)),

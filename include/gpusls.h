@@ -53,6 +53,11 @@ extern "C" {
                            on the tensor cores in TF32 (one pass, FP32 accumulation):
                            faster products, ~1e-3 relative product error that the
                            FP64 KKT gate and the refinement at the eps floor absorb */
+#define GPUSLS_MIXED 3  /* FP32 storage and iterations; the blocked factorization's
+                           block products on the tensor cores in three TF32 passes
+                           (a = a_hi + a_lo, FP32 accumulation: FP32 accuracy), its
+                           per-stage nu x nu solves (Gamma_i, R^_i^-1) in FP64, the KKT
+                           check in FP64 (the mixed-precision mode of the target) */
 
 /* Dimensions of one LTV-QP (eq. sqp_qp): state nx, input nu, horizon N, stage
  * constraint rows nc (rows of C_k, D_k), terminal rows nf (rows of C_N). */
@@ -71,7 +76,7 @@ typedef struct qp_settings {
   int32_t sigma;      /* rho-update interval in iterations; 0 keeps rho fixed       */
   int32_t check_every;/* stop-test interval                                         */
   int32_t max_iter;
-  int32_t precision;  /* GPUSLS_FP64 or GPUSLS_FP32                                 */
+  int32_t precision;  /* GPUSLS_FP64, GPUSLS_FP32, GPUSLS_TF32 or GPUSLS_MIXED        */
   int32_t cluster;    /* CTAs (thread blocks) per QP, 1..8; 0 picks by N            */
   int32_t fixed_iters;/* > 0: run exactly this many iterations, no stop test        */
   int32_t max_refine; /* iterative-refinement rounds allowed at the eps floor (3)   */

@@ -561,6 +561,120 @@ __device__ __noinline__ void sgemm_scalar(int m, int n, T alpha, const MTerm<T>&
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM with three TF32 products (the GPUSLS_MIXED mode): every
+// operand is split a = a_hi + a_lo with a_hi = tf32(a), a_lo = tf32(a - a_hi),
+// and op(A) B is accumulated in FP32 as a_lo b_hi + a_hi b_lo + a_hi b_hi by
+// mma.sync m16n8k8 (the a_lo b_lo term is below FP32 rounding), which keeps
+// FP32 accuracy on the tensor pipe.  Same contract as sgemm_vec: operands in
+// place (shared or global memory, any alignment), m, n <= 80, output
+// computed before any store (it may alias an operand), optional transposed
+// A, transposed output, + I, two product terms.
+//   Fragments (PTX ISA, mma.m16n8k8 .tf32, g = lane / 4, q = lane % 4):
+//   A 16 x 8: (g, q) (g + 8, q) (g, q + 4) (g + 8, q + 4);  B 8 x 8: (q, g) (q + 4, g);
+//   C 16 x 8: (g, 2q) (g, 2q + 1) (g + 8, 2q) (g + 8, 2q + 1).
+// Warp w owns units u = w, w + 8 (a unit: one 16-row tile x four 8-column
+// tiles); rows, columns and k past the operands are clamped for the reads
+// and zeroed in k.
+// ---------------------------------------------------------------------------
+__device__ inline void split_tf32(float x, unsigned& hi, unsigned& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void tc3_mac(int m, int n, const MTerm<float>& p, int mt, int ng, float (&acc)[4][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int r0 = mt * 16 + g, r1 = r0 + 8;
+  const int ra = min(r0, m - 1), rb = min(r1, m - 1);
+  const int k = p.k;
+  for (int k0 = 0; k0 < k; k0 += 8) {
+    const int ka = k0 + q, kb = k0 + q + 4;
+    const bool va = ka < k, vb = kb < k;
+    const int kac = min(ka, k - 1), kbc = min(kb, k - 1);
+    float av[4];
+    if (p.tA) {
+      av[0] = p.A[(size_t)kac * p.lda + ra];
+      av[1] = p.A[(size_t)kac * p.lda + rb];
+      av[2] = p.A[(size_t)kbc * p.lda + ra];
+      av[3] = p.A[(size_t)kbc * p.lda + rb];
+    } else {
+      av[0] = p.A[(size_t)ra * p.lda + kac];
+      av[1] = p.A[(size_t)rb * p.lda + kac];
+      av[2] = p.A[(size_t)ra * p.lda + kbc];
+      av[3] = p.A[(size_t)rb * p.lda + kbc];
+    }
+    if (!va) av[0] = av[1] = 0.f;
+    if (!vb) av[2] = av[3] = 0.f;
+    unsigned ah[4], al[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) split_tf32(av[e], ah[e], al[e]);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int col = min((ng * 4 + t) * 8 + g, n - 1);
+      float b0 = p.B[(size_t)kac * p.ldb + col];
+      float b1 = p.B[(size_t)kbc * p.ldb + col];
+      if (!va) b0 = 0.f;
+      if (!vb) b1 = 0.f;
+      unsigned bh[2], bl[2];
+      split_tf32(b0, bh[0], bl[0]);
+      split_tf32(b1, bh[1], bl[1]);
+      // the three passes of this k-step into a fresh accumulator, added to the
+      // running sum by a rounded FP32 add: the tensor core's own accumulation
+      // then spans 24 products, not the whole k (measured: it otherwise leaves
+      // ~8x the FFMA path's error in the Riccati terms)
+      float tmp[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_tf32(tmp, al, bh);
+      mma_tf32(tmp, ah, bl);
+      mma_tf32(tmp, ah, bh);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[t][e] += tmp[e];
+    }
+  }
+}
+
+static __device__ __noinline__ void sgemm_tc3(int m, int n, float alpha, const MTerm<float>& p1, const MTerm<float>& p2,
+                                       float beta, const float* C0, int ldc0, bool addI, float* C, int ldc, bool tC) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int mtiles = (m + 15) >> 4, ngroups = (n + 31) >> 5, units = mtiles * ngroups;
+  float acc[2][4][4];
+#pragma unroll
+  for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[s2][t][e] = 0.f;
+#pragma unroll
+  for (int s2 = 0; s2 < 2; ++s2) {
+    const int u = w + 8 * s2;
+    if (u < units) {
+      const int mt = u / ngroups, ng = u - mt * ngroups;
+      if (p1.k > 0) tc3_mac(m, n, p1, mt, ng, acc[s2]);
+      if (p2.k > 0) tc3_mac(m, n, p2, mt, ng, acc[s2]);
+    }
+  }
+  __syncthreads();   // every operand read before any output is written
+#pragma unroll
+  for (int s2 = 0; s2 < 2; ++s2) {
+    const int u = w + 8 * s2;
+    if (u >= units) continue;
+    const int mt = u / ngroups, ng = u - mt * ngroups;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int j = (ng * 4 + t) * 8 + 2 * q + (e & 1);
+        if (i < m && j < n) {
+          float v = alpha * acc[s2][t][e] + (C0 ? beta * C0[(size_t)i * ldc0 + j] : 0.f);
+          if (addI && i == j) v += 1.f;
+          if (tC) C[(size_t)j * ldc + i] = v;
+          else C[(size_t)i * ldc + j] = v;
+        }
+      }
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ inline bool mterm_vec_ok(const MTerm<T>& p) {
   return p.k == 0 || ((((reinterpret_cast<uintptr_t>(p.A) | reinterpret_cast<uintptr_t>(p.B)) & 15) == 0) &&
@@ -572,12 +686,20 @@ __device__ inline bool mterm_vec_ok(const MTerm<T>& p) {
 // (C[j][i]).  C0 (shared or global) is read before the products when the
 // registers allow, so its global-memory latency overlaps them.  Ends with a
 // CTA barrier.  Operands that are not 16-byte aligned take a scalar path.
+// tc (FP32 only, the GPUSLS_MIXED mode): products with k >= 8 run on the
+// tensor cores in three TF32 passes (sgemm_tc3).
 template <typename T>
 __device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> p2, T beta, const T* C0, int ldc0,
-                                   bool addI, T* C, int ldc, bool tC) {
+                                   bool addI, T* C, int ldc, bool tC, bool tc = false) {
   if (m <= 0 || n <= 0) {
     __syncthreads();
     return;
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (tc && p1.k >= 8 && (p2.k == 0 || p2.k >= 8)) {
+      sgemm_tc3(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+      return;
+    }
   }
   // FP64 products run at the FP64 FMA rate whatever the loads, so FP64 keeps
   // the scalar path (and the vector shapes are instantiated for FP32 only)
@@ -616,9 +738,9 @@ __device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> 
 // One-term convenience form.
 template <typename T>
 __device__ inline void sgemm1(int m, int n, int k, T alpha, const T* A, int lda, bool tA, const T* B, int ldb,
-                              T beta, const T* C0, int ldc0, T* C, int ldc, bool tC = false) {
+                              T beta, const T* C0, int ldc0, T* C, int ldc, bool tC = false, bool tc = false) {
   sgemm<T>(m, n, alpha, MTerm<T>{A, lda, tA, B, ldb, k}, MTerm<T>{nullptr, 0, false, nullptr, 0, 0}, beta, C0, ldc0,
-           false, C, ldc, tC);
+           false, C, ldc, tC, tc);
 }
 
 // Y = X for an m x n block by 16-byte vectors: X, Y 16-byte aligned, leading
@@ -644,36 +766,38 @@ __device__ void cta_copy_vec(int m, int n, const T* X, int ldxs, T* Y, int ldy) 
 // row broadcast by shuffles.  G and Gi: shared or global, may not alias.
 // Returns 1 in every thread (after the closing barrier) if a pivot was not
 // positive.  flag: shared int.
-template <typename T, int CAP>
-__device__ __noinline__ int warp_spd_inverse(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag) {
+// Loads T, computes in A (GPUSLS_MIXED: FP32 operands, FP64 arithmetic),
+// stores T.
+template <typename T, typename A, int CAP>
+__device__ __noinline__ int warp_spd_inverse_as(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag) {
   if (threadIdx.x < 32) {
     const int l = threadIdx.x;
-    T a[CAP], b[CAP];
+    A a[CAP], b[CAP];
 #pragma unroll
     for (int j = 0; j < CAP; ++j) {
-      a[j] = (l < n && j < n) ? G[l * ldg + j] : (l == j ? T(1) : T(0));
-      b[j] = l == j ? T(1) : T(0);
+      a[j] = (l < n && j < n) ? (A)G[l * ldg + j] : (l == j ? A(1) : A(0));
+      b[j] = l == j ? A(1) : A(0);
     }
     int bad = 0;
 #pragma unroll
     for (int k = 0; k < CAP; ++k) {
       if (k < n) {
-        T piv = __shfl_sync(0xffffffffu, a[k], k);
-        if (!(piv > T(0))) {
+        A piv = __shfl_sync(0xffffffffu, a[k], k);
+        if (!(piv > A(0))) {
           bad = 1;
-          piv = T(1);
+          piv = A(1);
         }
-        const T ip = T(1) / piv;
-        const T f = l == k ? T(0) : a[k] * ip;
+        const A ip = A(1) / piv;
+        const A f = l == k ? A(0) : a[k] * ip;
         // columns < k of a are finished (e_j); only j >= k change
 #pragma unroll
         for (int j = k; j < CAP; ++j) {
-          const T rk = __shfl_sync(0xffffffffu, a[j], k);
+          const A rk = __shfl_sync(0xffffffffu, a[j], k);
           a[j] = l == k ? rk * ip : fma(-f, rk, a[j]);
         }
 #pragma unroll
         for (int j = 0; j < CAP; ++j) {
-          const T rk = __shfl_sync(0xffffffffu, b[j], k);
+          const A rk = __shfl_sync(0xffffffffu, b[j], k);
           b[j] = l == k ? rk * ip : fma(-f, rk, b[j]);
         }
       }
@@ -681,7 +805,7 @@ __device__ __noinline__ int warp_spd_inverse(const T* G, int ldg, int n, T* Gi, 
     if (l < n) {
 #pragma unroll
       for (int j = 0; j < CAP; ++j)
-        if (j < n) Gi[l * ldgi + j] = b[j];
+        if (j < n) Gi[l * ldgi + j] = (T)b[j];
     }
     if (l == 0) flag[0] = bad;
   }
@@ -689,6 +813,11 @@ __device__ __noinline__ int warp_spd_inverse(const T* G, int ldg, int n, T* Gi, 
   const int f = flag[0];
   __syncthreads();
   return f;
+}
+
+template <typename T, int CAP>
+__device__ __noinline__ int warp_spd_inverse(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag) {
+  return warp_spd_inverse_as<T, T, CAP>(G, ldg, n, Gi, ldgi, flag);
 }
 
 // Issue (without waiting) the cp.async copy of an m-row block whose rows are

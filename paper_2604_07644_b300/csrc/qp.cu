@@ -149,7 +149,7 @@ static int launch_qp(qp_handle* h, const SolveArgs& a) {
 // of QP 0 and prints them to stderr after each launch.
 static int launch(qp_handle* h, const SolveArgs& a0) {
   SolveArgs a = a0;
-  a.tc = h->set.precision == GPUSLS_TF32 ? 1 : 0;
+  a.tc = h->set.precision == GPUSLS_TF32 ? 1 : (h->set.precision == GPUSLS_MIXED ? 2 : 0);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(h->stream, &cap));
   const bool prof_on = getenv("GPUSLS_PROFILE") != nullptr && cap == cudaStreamCaptureStatusNone;
@@ -245,7 +245,8 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
                               const double* hi, const double* rho, const qp_settings* s, void* stream) {
   if (!out || batch < 1 || !dims || !A || !B || !c || !Q || !R || !q || !r || !lo || !hi || !s)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: null argument or batch < 1");
-  if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32 && s->precision != GPUSLS_TF32)
+  if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32 && s->precision != GPUSLS_TF32 &&
+      s->precision != GPUSLS_MIXED)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: unknown precision");
   if (s->cluster < 0 || s->cluster > MAXCS) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: cluster must be 0..8");
   if (s->occupancy < 0 || s->occupancy > 1 || s->schedule < 0 || s->schedule > 1 || s->factorization < 0 ||

@@ -79,7 +79,8 @@ struct SolveArgs {
   int max_refine;
   int fallback_iters;   // > 0: a warm-started QP not converged after this many iterations restarts cold
   const int* order;     // launch order: cluster b solves QP order[b] (null: QP b)
-  int tc;               // 1: factorization block products on the tensor cores in TF32
+  int tc;               // 1: factorization block products on the tensor cores in TF32 (GPUSLS_TF32);
+                        // 2: GPUSLS_MIXED (three TF32 passes, FP64 per-stage solves)
 };
 
 // Per-stage operator bundles of the cached iteration (elements).  Every
@@ -250,7 +251,9 @@ struct Ctx {
   int msz;  // nx * ldx
   int uni;  // bytes of the union region at ring
   unsigned long long* prof;  // non-null in each CTA of QP 0 when profiling (thread 0 records)
-  bool tc;                   // factorization products in TF32 on the tensor cores
+  bool tc;                   // factorization products in TF32 on the tensor cores (tree schedule)
+  bool mix;                  // GPUSLS_MIXED: blocked-schedule products in three TF32 passes on the
+                             // tensor cores, per-stage nu x nu solves in FP64
   long long t_last;
 };
 
@@ -590,8 +593,13 @@ __device__ inline void fact_prefetch(Ctx<T>& c, const FactBufs<T>& fb, int i, in
 }
 
 // n x n (n <= FACT_MAX_NU) SPD inverse by one warp.
+// GPUSLS_MIXED: the per-stage solve (Gamma_i, R^_i^-1) in FP64 arithmetic.
 template <typename T>
 __device__ inline int small_spd_inverse(Ctx<T>& c, const T* G, int ldg, int n, T* Gi, int ldgi) {
+  if (sizeof(T) == 4 && c.mix) {
+    if (n <= 16) return warp_spd_inverse_as<T, double, 16>(G, ldg, n, Gi, ldgi, c.flag + 1);
+    return warp_spd_inverse_as<T, double, FACT_MAX_NU>(G, ldg, n, Gi, ldgi, c.flag + 1);
+  }
   if (n <= 16) return warp_spd_inverse<T, 16>(G, ldg, n, Gi, ldgi, c.flag + 1);
   return warp_spd_inverse<T, FACT_MAX_NU>(G, ldg, n, Gi, ldgi, c.flag + 1);
 }
@@ -607,24 +615,24 @@ __device__ __noinline__ int fact_step_full(Ctx<T>& c, const FactBufs<T>& fb, int
   cta_stage_rows(fb.Xb, lds * esz, TP<T>(d.VA) + (size_t)i * c.msz, ldx * esz, nx, ldx * esz);   // A~_i
   if (i - 1 >= c.s) fact_prefetch<T>(c, fb, i - 1, k ^ 1, false);
   cp_async_commit();
-  sgemm1<T>(nx, nu, nx, T(1), fb.P, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S1, lds, true);    // Y^T
-  sgemm1<T>(nx, nu, nx, T(1), fb.Aa, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S3, lds, true);   // E^T
-  sgemm1<T>(nu, nu, nx, T(1), fb.S1, lds, false, Bb, ldu, T(1), Rb, ldu, fb.Gm, ldu);             // G
+  sgemm1<T>(nx, nu, nx, T(1), fb.P, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S1, lds, true, c.mix);    // Y^T
+  sgemm1<T>(nx, nu, nx, T(1), fb.Aa, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S3, lds, true, c.mix);   // E^T
+  sgemm1<T>(nu, nu, nx, T(1), fb.S1, lds, false, Bb, ldu, T(1), Rb, ldu, fb.Gm, ldu, false, c.mix);             // G
   const int bad = small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
   cp_async_wait<0>();
   __syncthreads();
   prof_mark(c, PH_FA1);
-  sgemm1<T>(nu, nx, nx, T(1), fb.S1, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.S2, lds);       // Y^T A~_i
-  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S2, lds);       // H
-  sgemm1<T>(nx, nx, nu, T(-1), Bb, ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds);         // X
-  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S3, lds, T(0), nullptr, 0, fb.S1, lds);       // Gamma E^T
-  sgemm1<T>(nx, nx, nu, T(1), fb.S3, lds, true, fb.S1, lds, T(1), Cacc, ldx, Cacc, ldx);          // C~_ij
+  sgemm1<T>(nu, nx, nx, T(1), fb.S1, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.S2, lds, false, c.mix);       // Y^T A~_i
+  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S2, lds, false, c.mix);       // H
+  sgemm1<T>(nx, nx, nu, T(-1), Bb, ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds, false, c.mix);         // X
+  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S3, lds, T(0), nullptr, 0, fb.S1, lds, false, c.mix);       // Gamma E^T
+  sgemm1<T>(nx, nx, nu, T(1), fb.S3, lds, true, fb.S1, lds, T(1), Cacc, ldx, Cacc, ldx, false, c.mix);          // C~_ij
   prof_mark(c, PH_FA2);
-  sgemm1<T>(nx, nx, nx, T(1), fb.Aa, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.Aa, lds);       // A~_ij
-  sgemm1<T>(nx, nx, nx, T(1), fb.P, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.P, lds);         // P_r X
-  sgemm1<T>(nu, nx, nu, T(1), Rb, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S1, lds);          // R^ H
+  sgemm1<T>(nx, nx, nx, T(1), fb.Aa, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.Aa, lds, false, c.mix);       // A~_ij
+  sgemm1<T>(nx, nx, nx, T(1), fb.P, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.P, lds, false, c.mix);         // P_r X
+  sgemm1<T>(nu, nx, nu, T(1), Rb, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S1, lds, false, c.mix);          // R^ H
   sgemm<T>(nx, nx, T(1), MTerm<T>{fb.Xb, lds, true, fb.P, lds, nx}, MTerm<T>{fb.S2, lds, true, fb.S1, lds, nu},
-           T(1), TP<T>(d.VP) + (size_t)i * c.msz, ldx, false, fb.P, lds, false);                 // P~_ij
+           T(1), TP<T>(d.VP) + (size_t)i * c.msz, ldx, false, fb.P, lds, false, c.mix);                 // P~_ij
   prof_mark(c, PH_FA3);
   return bad;
 }
@@ -707,15 +715,15 @@ __device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, 
   for (int e = t; e < nu; e += NT) rv[e] = TP<T>(d.r)[(size_t)i * ldu + e];
   __syncthreads();
   smem_mvT<T>(fb.P, lds, nx, nx, bv, nullptr, pb, c.red);                                         // P_{i+1} b_i (P symmetric)
-  sgemm1<T>(nx, nu, nx, T(1), fb.P, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S1, lds, true);    // Y^T
-  sgemm1<T>(nu, nu, nx, T(1), fb.S1, lds, false, Bb, ldu, T(1), Rb, ldu, fb.Gm, ldu);             // Gamma^-1
+  sgemm1<T>(nx, nu, nx, T(1), fb.P, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S1, lds, true, c.mix);    // Y^T
+  sgemm1<T>(nu, nu, nx, T(1), fb.S1, lds, false, Bb, ldu, T(1), Rb, ldu, fb.Gm, ldu, false, c.mix);             // Gamma^-1
   const int bad = small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
   cp_async_wait<0>();
   __syncthreads();
   prof_mark(c, PH_FC1);
-  sgemm1<T>(nu, nx, nx, T(1), fb.S1, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.S2, lds);       // Y^T A~_i
-  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S2, lds);       // H
-  sgemm1<T>(nx, nx, nu, T(-1), Bb, ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds);         // Abar_i
+  sgemm1<T>(nu, nx, nx, T(1), fb.S1, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.S2, lds, false, c.mix);       // Y^T A~_i
+  sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S2, lds, false, c.mix);       // H
+  sgemm1<T>(nx, nx, nu, T(-1), Bb, ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds, false, c.mix);         // Abar_i
   T* Kg = TP<T>(d.K) + (size_t)i * nu * ldx;
   for (int e = t; e < nu * nx; e += NT) {
     const int a = e / nx, j = e - a * nx;
@@ -732,15 +740,15 @@ __device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, 
   __syncthreads();
   prof_mark(c, PH_FC2);
   // P_i = P~_i + X^T (P_{i+1} X) + H^T (R^ H)
-  sgemm1<T>(nx, nx, nx, T(1), fb.P, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.P, lds);
-  sgemm1<T>(nu, nx, nu, T(1), Rb, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S3, lds);
+  sgemm1<T>(nx, nx, nx, T(1), fb.P, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.P, lds, false, c.mix);
+  sgemm1<T>(nu, nx, nu, T(1), Rb, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S3, lds, false, c.mix);
   sgemm<T>(nx, nx, T(1), MTerm<T>{fb.Xb, lds, true, fb.P, lds, nx}, MTerm<T>{fb.S2, lds, true, fb.S3, lds, nu},
-           T(1), TP<T>(d.VP) + (size_t)i * msz, ldx, false, fb.P, lds, false);
+           T(1), TP<T>(d.VP) + (size_t)i * msz, ldx, false, fb.P, lds, false, c.mix);
   prof_mark(c, PH_FC3);
   // stage outputs: -B Gamma (= F_i^T), -D Gamma (= J_i^T), CK_i = C_i + D_i K_i
-  sgemm1<T>(nx, nu, nu, T(-1), Bb, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.BG, ldu);
-  sgemm1<T>(nc, nu, nu, T(-1), Db, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.JT, ldu);
-  sgemm1<T>(nc, nx, nu, T(1), Db, ldu, false, fb.S1, lds, T(1), TP<T>(d.C) + (size_t)i * nc * ldx, ldx, fb.CKb[0], lds);
+  sgemm1<T>(nx, nu, nu, T(-1), Bb, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.BG, ldu, false, c.mix);
+  sgemm1<T>(nc, nu, nu, T(-1), Db, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.JT, ldu, false, c.mix);
+  sgemm1<T>(nc, nx, nu, T(1), Db, ldu, false, fb.S1, lds, T(1), TP<T>(d.C) + (size_t)i * nc * ldx, ldx, fb.CKb[0], lds, false, c.mix);
   cta_copy_vec<T>(nx, nx, fb.P, lds, TP<T>(d.IP) + (size_t)i * msz, ldx);
   cta_copy_vec<T>(nx, nx, fb.Xb, lds, TP<T>(d.Abar) + (size_t)i * msz, ldx);
   cta_copy_vec<T>(nu, nu, fb.Gi, ldu, TP<T>(d.Gam) + (size_t)i * nu * ldu, ldu);
@@ -750,8 +758,8 @@ __device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, 
   if (!c.last) {
     // backward chunk products (Pi in Aa): FPi_i^T = Pi_{i+1}^T F_i^T, Pi_i = Abar_i^T Pi_{i+1}
     sgemm1<T>(nx, nu, nx, T(1), fb.Aa, lds, true, fb.BG, ldu, T(0), nullptr, 0,
-              TP<T>(d.FPi) + (size_t)i * nx * ldu, ldu);
-    sgemm1<T>(nx, nx, nx, T(1), fb.Xb, lds, true, fb.Aa, lds, T(0), nullptr, 0, fb.Aa, lds);
+              TP<T>(d.FPi) + (size_t)i * nx * ldu, ldu, false, c.mix);
+    sgemm1<T>(nx, nx, nx, T(1), fb.Xb, lds, true, fb.Aa, lds, T(0), nullptr, 0, fb.Aa, lds, false, c.mix);
   }
   prof_mark(c, PH_FC4);
   fact_bundles<T>(c, fb, i, k);
@@ -851,22 +859,22 @@ __device__ __noinline__ int leaves_blocked(Ctx<T>& c, T rho) {
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    sgemm1<T>(nx, nx, nc, rho, fb.CKb[0], lds, true, fb.CKb[0], lds, T(1), fb.P, lds, fb.P, lds);      // Q^
-    sgemm1<T>(nu, nu, nc, rho, fb.Db[0], ldu, true, fb.Db[0], ldu, T(1), fb.Rb[0], ldu, fb.Gm, ldu);   // R^
-    sgemm1<T>(nu, nx, nc, rho, fb.Db[0], ldu, true, fb.CKb[0], lds, T(1), fb.S3, lds, fb.S1, lds);     // S^
+    sgemm1<T>(nx, nx, nc, rho, fb.CKb[0], lds, true, fb.CKb[0], lds, T(1), fb.P, lds, fb.P, lds, false, c.mix);      // Q^
+    sgemm1<T>(nu, nu, nc, rho, fb.Db[0], ldu, true, fb.Db[0], ldu, T(1), fb.Rb[0], ldu, fb.Gm, ldu, false, c.mix);   // R^
+    sgemm1<T>(nu, nx, nc, rho, fb.Db[0], ldu, true, fb.CKb[0], lds, T(1), fb.S3, lds, fb.S1, lds, false, c.mix);     // S^
     cta_copy_vec<T>(nu, nu, fb.Gm, ldu, TP<T>(d.Rh) + (size_t)i * nu * ldu, ldu);
     bad |= small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
-    sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S1, lds, T(0), nullptr, 0, fb.S2, lds);          // s0
-    sgemm1<T>(nx, nx, nu, T(-1), fb.S1, lds, true, fb.S2, lds, T(1), fb.P, lds, fb.P, lds);            // P~
-    sgemm1<T>(nx, nx, nu, T(-1), fb.Bb[0], ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds);      // A~
+    sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S1, lds, T(0), nullptr, 0, fb.S2, lds, false, c.mix);          // s0
+    sgemm1<T>(nx, nx, nu, T(-1), fb.S1, lds, true, fb.S2, lds, T(1), fb.P, lds, fb.P, lds, false, c.mix);            // P~
+    sgemm1<T>(nx, nx, nu, T(-1), fb.Bb[0], ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds, false, c.mix);      // A~
     cta_copy_vec<T>(nu, nx, fb.S2, lds, TP<T>(d.S0) + (size_t)i * nu * ldx, ldx);
     cta_copy_vec<T>(nx, nx, fb.P, lds, TP<T>(d.VP) + (size_t)i * msz, ldx);
     cta_copy_vec<T>(nx, nx, fb.Xb, lds, TP<T>(d.VA) + (size_t)i * msz, ldx);
     if (need_ct && i == c.e - 1) {
       // C~ = B (B R^^-1)^T
-      sgemm1<T>(nx, nu, nu, T(1), fb.Bb[0], ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.S3, lds, true);
+      sgemm1<T>(nx, nu, nu, T(1), fb.Bb[0], ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.S3, lds, true, c.mix);
       sgemm1<T>(nx, nx, nu, T(1), fb.Bb[0], ldu, false, fb.S3, lds, T(0), nullptr, 0,
-                TP<T>(d.VC) + (size_t)i * msz, ldx);
+                TP<T>(d.VC) + (size_t)i * msz, ldx, false, c.mix);
     }
   }
   if (c.last) {
@@ -875,7 +883,7 @@ __device__ __noinline__ int leaves_blocked(Ctx<T>& c, T rho) {
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    sgemm1<T>(nx, nx, nf, rho, fb.CKb[0], lds, true, fb.CKb[0], lds, T(1), fb.P, lds, fb.P, lds);
+    sgemm1<T>(nx, nx, nf, rho, fb.CKb[0], lds, true, fb.CKb[0], lds, T(1), fb.P, lds, fb.P, lds, false, c.mix);
     cta_copy_vec<T>(nx, nx, fb.P, lds, TP<T>(d.VP) + (size_t)N * msz, ldx);
   }
   return bad;
@@ -915,10 +923,10 @@ __device__ __noinline__ void forward_products(Ctx<T>& c) {
     }
     __syncthreads();
     cta_copy_vec<T>(nx, nx, Sg, lds, TP<T>(d.Sig) + (size_t)i * msz, ldx);
-    sgemm1<T>(nu, nx, nx, T(1), Kb[k], lds, false, Sg, lds, T(0), nullptr, 0, TP<T>(d.KSig) + (size_t)i * nu * ldx, ldx);
+    sgemm1<T>(nu, nx, nx, T(1), Kb[k], lds, false, Sg, lds, T(0), nullptr, 0, TP<T>(d.KSig) + (size_t)i * nu * ldx, ldx, false, c.mix);
     sgemm1<T>(nc, nx, nx, T(1), fb.CKb[k], lds, false, Sg, lds, T(0), nullptr, 0,
-              TP<T>(d.CKSig) + (size_t)i * nx * ldc, ldc, true);
-    sgemm1<T>(nx, nx, nx, T(1), Ab[k], lds, false, Sg, lds, T(0), nullptr, 0, Sg, lds);
+              TP<T>(d.CKSig) + (size_t)i * nx * ldc, ldc, true, c.mix);
+    sgemm1<T>(nx, nx, nx, T(1), Ab[k], lds, false, Sg, lds, T(0), nullptr, 0, Sg, lds, false, c.mix);
   }
   cta_copy_vec<T>(nx, nx, Sg, lds, TP<T>(d.Uch) + (size_t)c.rank * msz, ldx);
   if (c.last) {
@@ -928,7 +936,7 @@ __device__ __noinline__ void forward_products(Ctx<T>& c) {
       cp_async_commit();
       cp_async_wait<0>();
       __syncthreads();
-      sgemm1<T>(nf, nx, nx, T(1), fb.CKb[0], lds, false, Sg, lds, T(0), nullptr, 0, TP<T>(d.CNSig), ldx);
+      sgemm1<T>(nf, nx, nx, T(1), fb.CKb[0], lds, false, Sg, lds, T(0), nullptr, 0, TP<T>(d.CNSig), ldx, false, c.mix);
     }
   }
 }

@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
     c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
     c.t_last = clock64();
-    c.tc = args.tc != 0;
+    c.tc = args.tc == 1;
+    c.mix = args.tc == 2;
     iter_plan<T>(c);
   }
   __syncthreads();

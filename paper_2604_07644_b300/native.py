@@ -24,6 +24,7 @@ GPUSLS_ERR_TIMEOUT = -6
 GPUSLS_FP64 = 0
 GPUSLS_FP32 = 1
 GPUSLS_TF32 = 2
+GPUSLS_MIXED = 3
 
 STATUS_NAMES = {0: "ok", 1: "max_iter", -1: "invalid", -2: "not_spd", -3: "nan", -4: "infeasible",
                 -5: "cuda", -6: "timeout"}

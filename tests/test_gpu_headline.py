@@ -49,13 +49,13 @@ def batch_qps():
     return [fam.instance(BASE + i) for i in range(BATCH)]
 
 
-def headline_solve(qps, eps_kkt, max_refine=3):
+def headline_solve(qps, eps_kkt, max_refine=3, precision=native.GPUSLS_FP32):
     """The benchmark's launch: tuned shape (cluster 6, two CTAs per SM),
     longest-expected-first order, learned warm start, one graph per step;
     the second replay is read (its order comes from the first)."""
     from paper_2604_07644_b300 import learned
     from paper_2604_07644_b300.api import QPBatch
-    s = native.default_settings(precision=native.GPUSLS_FP32, cluster=6, occupancy=0, max_refine=max_refine,
+    s = native.default_settings(precision=precision, cluster=6, occupancy=0, max_refine=max_refine,
                                 fallback_iters=2000, max_iter=6000, eps_kkt=eps_kkt,
                                 eps_floor=min(1e-5, 0.1 * eps_kkt), schedule=1)
     stream = torch.cuda.Stream()
@@ -140,3 +140,19 @@ def test_plain_fp64_solution_matches_exact_at_1e6_relative(lib, batch_qps, exact
     d = max(rel(r.dx[0], exact["x"][j], scale), rel(r.du[0], exact["u"][j], scale))
     print(f"plain FP64 QP {i}: {r.info[0]['iters']} iterations, distance {d:.2e}")
     assert d <= 1e-6, d
+
+
+def test_mixed_precision_headline_path(lib, batch_qps, exact):
+    """The benchmark's launch in GPUSLS_MIXED (tensor-core factorization
+    products in three TF32 passes, FP64 per-stage solves): every QP
+    converges, the sampled QPs pass the oracle's KKT check at 1e-4 and lie as
+    close to the exact optimum as the FP32 path's, and the mean iteration
+    count is within 5 % of the FP32 path's."""
+    sols, info = headline_solve(batch_qps, 1e-4, precision=native.GPUSLS_MIXED)
+    assert all(i["status"] == native.GPUSLS_OK for i in info)
+    worst = check_against_exact(batch_qps, sols, info, exact, 1e-4, 1e-3)
+    _, info32 = headline_solve(batch_qps, 1e-4)
+    it_m = np.mean([i["iters"] for i in info])
+    it_32 = np.mean([i["iters"] for i in info32])
+    print(f"mixed: mean iterations {it_m:.1f} (FP32 {it_32:.1f}), distance {worst:.2e}")
+    assert abs(it_m - it_32) <= 0.05 * it_32

@@ -10,7 +10,7 @@ from paper_2604_07644_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {native.GPUSLS_FP64: 1e-6, native.GPUSLS_FP32: 1e-4}
+TOL = {native.GPUSLS_FP64: 1e-6, native.GPUSLS_FP32: 1e-4, native.GPUSLS_MIXED: 1e-4}
 
 
 def rel(a, b):
@@ -36,7 +36,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("fact", [0, 1])
-@pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32])
+@pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32, native.GPUSLS_MIXED])
 @pytest.mark.parametrize("cluster", [1, 3, 8])
 @pytest.mark.parametrize("name,make", CASES)
 def test_riccati_matches_oracle(lib, name, make, cluster, prec, fact):
@@ -50,7 +50,7 @@ def test_riccati_matches_oracle(lib, name, make, cluster, prec, fact):
     Ps, Ks = b.riccati()
     Qh, Rh, Sh = lq.augmented(qp, rho)
     P, p, K, kff, G = lq.riccati(qp.A, qp.B, qp.c, Qh, Rh, Sh, np.zeros_like(qp.q), np.zeros_like(qp.r))
-    tol = TOL[prec] * (10 if prec == native.GPUSLS_FP32 else 1e-2)
+    tol = TOL[prec] * (1e-2 if prec == native.GPUSLS_FP64 else 10)
     assert rel(Ps[0], P) < tol, rel(Ps[0], P)
     assert rel(Ks[0], K) < tol, rel(Ks[0], K)
     b.close()
@@ -71,10 +71,11 @@ def test_fixed_iterations_match_oracle_fp64(lib, name, make, cluster):
     b.close()
 
 
+@pytest.mark.parametrize("prec", [native.GPUSLS_FP32, native.GPUSLS_MIXED])
 @pytest.mark.parametrize("name,make", CASES)
-def test_fixed_iterations_match_oracle_fp32(lib, name, make):
+def test_fixed_iterations_match_oracle_fp32(lib, name, make, prec):
     qp = make()
-    b = batch([qp], precision=native.GPUSLS_FP32, sigma=0, fixed_iters=9, rho=0.3)
+    b = batch([qp], precision=prec, sigma=0, fixed_iters=9, rho=0.3)
     r = b.solve()
     o = admm.admm(qp, admm.Settings(rho0=0.3, sigma=0), iters=9)
     assert rel(r.dx[0], o.x) < 1e-4
@@ -316,3 +317,27 @@ def test_tf32_products_accuracy_level(lib, name, make):
     v = lq.G_apply(qp, r.dx[0], r.du[0])
     assert np.all(v <= qp.hi + 3e-3) and np.all(v >= qp.lo - 3e-3)
     b.close()
+
+
+@pytest.mark.parametrize("cluster", [6, 8])
+def test_mixed_precision_full_size(lib, cluster):
+    """GPUSLS_MIXED at 61D / N=100 (block products in three TF32 passes on the
+    tensor cores, FP64 per-stage solves): the Riccati terms carry FP32-sized
+    errors against the FP64 sequential recursion (1e-4 relative, like FP32,
+    where one TF32 pass leaves 2e-3 to 5e-3), and the adaptive solve meets the
+    1e-4 KKT tolerance by the oracle's own measure with every bound met."""
+    qp = W.quadruped_61d(0)
+    rho = 0.3
+    b = batch([qp], precision=native.GPUSLS_MIXED, cluster=cluster, rho=rho)
+    Ps, Ks = b.riccati()
+    b.close()
+    Qh, Rh, Sh = lq.augmented(qp, rho)
+    P, p, K, kff, G = lq.riccati(qp.A, qp.B, qp.c, Qh, Rh, Sh, np.zeros_like(qp.q), np.zeros_like(qp.r))
+    assert rel(Ps[0], P) < 1e-4 and rel(Ks[0], K) < 1e-4, (rel(Ps[0], P), rel(Ks[0], K))
+    b = batch([qp], precision=native.GPUSLS_MIXED, cluster=cluster)
+    r = b.solve()
+    b.close()
+    assert r.info[0]["status"] == native.GPUSLS_OK
+    assert kkt.kkt_residual(qp, r.dx[0], r.du[0], r.lam[0]) <= 1.0001e-4
+    v = lq.G_apply(qp, r.dx[0], r.du[0])
+    assert np.all(v <= qp.hi + 1e-4) and np.all(v >= qp.lo - 1e-4)
