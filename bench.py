@@ -292,6 +292,30 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
 
     batch_run("serving_mix_cold", W.serving_mix(0, 256), 8)
 
+    # the learned serving mix: 256 QPs of three shape families (12D/4, 61D/12,
+    # 75D/21) with N ~ U{16..128}, one warm-start head per family inside the
+    # graph, against the same batch cold
+    from paper_2604_07644_b300 import learned as L
+    mixl = W.serving_mix_learned(0, 256)
+    qpl_ = [q for q, _ in mixl]
+    s = native.default_settings(**dict(base, cluster=4))
+    if not args.no_autotune:
+        from paper_2604_07644_b300 import autotune
+        s, _ = autotune.choose(qpl_, s, expected_iters=200, tail_iters=1500, cache=autotune.Cache())
+    with torch.cuda.stream(stream):
+        qb = QPBatch(qpl_, s, stream=stream, device=dev)
+        heads_ = L.mix_heads(mixl, os.path.join(ROOT, "paper_2604_07644_b300"), stream=stream)
+        for name, g in (("serving_mix_learned", qb.graph(heads=heads_)), ("serving_mix_learned_cold", qb.graph())):
+            ms = _time_graph(g, stream, steps)
+            info = g.info()
+            out[name] = {"ms_per_qp": ms / len(qpl_), "batch": len(qpl_), "cluster": int(s.cluster),
+                         "occupancy": int(s.occupancy), "iters_mean": float(np.mean([i["iters"] for i in info])),
+                         "kkt_max": float(np.max([i["kkt"] for i in info])),
+                         "all_converged": all(i["status"] == 0 for i in info)}
+        for h_ in heads_:
+            h_[0].close()
+        qb.close()
+
     # long horizon (the horizon study of Sec. V-A): torque-limited
     # pendulum-shaped QP, nx=30, nu=15, N=3000 (1.35e5 decision variables),
     # cold FP32 solve to the 1e-4 KKT tolerance, one QP per launch, cluster 8
@@ -501,9 +525,9 @@ def profile_case(args):
         qps = [fam.instance(100000 + i) for i in range(256)]
         qb = QPBatch(qps, native.default_settings(precision=native.GPUSLS_FP32))
         mlp = learned.load(args.model, max_batch=256)
-        feats = torch.from_numpy(learned.features(qps)).cuda()
+        heads = [(mlp, list(range(len(qps))), qps[0].N)]
         for _ in range(3):
-            mlp.warm_start(qb, feats)
+            qb.warm_start_heads(heads)
         torch.cuda.synchronize()
         mlp.close()
         qb.close()
@@ -560,15 +584,15 @@ def main():
     with torch.cuda.stream(stream):
         hb = QPBatch(qps, settings, stream=stream, device=dev)
         mlp = learned.load(args.model, max_batch=args.batch, stream=stream)
-        feats = torch.from_numpy(learned.features(qps)).to(dev)
-        g_learned = None if args.eager else hb.graph(mlp, feats)
+        heads = [(mlp, list(range(args.batch)), N)]   # features computed from the data inside the step
+        g_learned = None if args.eager else hb.graph(heads=heads)
         g_cold = None if args.eager else hb.graph()
 
     def step_learned():
         if g_learned is not None:
             return g_learned.launch(stream)
         hb.reset()
-        mlp.warm_start(hb, feats)
+        hb.warm_start_heads(heads)
         return hb.solve(fetch=False)
 
     def step_cold():
@@ -610,7 +634,7 @@ def main():
         info = (native.qp_info * args.batch)()
         hb.reset()
         if warm:
-            mlp.warm_start(hb, feats)
+            hb.warm_start_heads(heads)
         hb.lib.qp_solve(hb.h, C_ptr(hb.x0), 0, 0.0, C_ptr(hb.out_x), C_ptr(hb.out_u), C_ptr(hb.out_l), info)
         return [info[i] for i in range(args.batch)]
 
@@ -636,7 +660,7 @@ def main():
                                      max_iter=6000, eps_floor=1e-5, schedule=0 if args.index_order else 1)
         with torch.cuda.stream(stream):
             hm = QPBatch(qps, sm, stream=stream, device=dev, pools=hb.pools)
-            gm = hm.graph(mlp, feats)
+            gm = hm.graph(heads=heads)
             for _ in range(2):
                 gm.launch(stream)
         tm = timed(lambda: gm.launch(stream), max(1, args.steps))
@@ -679,12 +703,10 @@ def main():
         keys = ("A", "B", "c", "Q", "R", "S", "q", "r", "C", "D", "CN", "lo", "hi")
         host = {k: hb.pools[k].cpu().pin_memory() for k in keys}
         host_x0 = hb.x0.cpu().pin_memory()
-        host_f = feats.cpu().pin_memory()
         bufs = [{k: torch.empty_like(hb.pools[k]) for k in keys} for _ in range(2)]
         x0b = [torch.empty_like(hb.x0) for _ in range(2)]
-        fb = [torch.empty_like(feats) for _ in range(2)]
         out_host = [torch.empty_like(t, device="cpu").pin_memory() for t in (hb.out_x, hb.out_u, hb.out_l)]
-        h2d = sum(t.numel() * 8 for t in host.values()) + host_x0.numel() * 8 + host_f.numel() * 4
+        h2d = sum(t.numel() * 8 for t in host.values()) + host_x0.numel() * 8
         d2h = sum(t.numel() * 8 for t in out_host)
         copy_stream = torch.cuda.Stream(device=dev)
 
@@ -699,7 +721,6 @@ def main():
                     for k in keys:
                         bufs[j][k].copy_(host[k], non_blocking=True)
                     x0b[j].copy_(host_x0, non_blocking=True)
-                    fb[j].copy_(host_f, non_blocking=True)
                     ev_h2d[j] = torch.cuda.Event()
                     ev_h2d[j].record(copy_stream)
 
@@ -711,7 +732,6 @@ def main():
                 with torch.cuda.stream(stream):
                     stream.wait_event(ev_h2d[j])
                     hb.x0.copy_(x0b[j])
-                    feats.copy_(fb[j])
                     hb.update_pools(bufs[j])
                     ev_free[j] = torch.cuda.Event()
                     ev_free[j].record(stream)

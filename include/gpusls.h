@@ -342,6 +342,35 @@ void mlp_destroy(mlp_handle* h);
  * Runs on the network's stream; give both handles the same stream. */
 int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max);
 
+/* Linearization features (no counterpart in the paper): what a warm-start
+ * network sees of a QP, computed from the data the caller gave the handle.
+ * Row of QP b: [x0 (nx), then GPUSLS_FEATURE_P values each of four fixed
+ * +-1 (Rademacher) projections, scaled by 1/sqrt(inputs), of
+ * mean_k (A_k - I), mean_k B_k, mean_{k<=N} q_k and the per-row mean over the
+ * stages of the finite upper bounds (clamped to +-10), then N / 128]:
+ * nx + 4 GPUSLS_FEATURE_P + 1 floats.  The signs come from a 32-bit hash of
+ * (projection, row, input index), so no matrix is stored. */
+#define GPUSLS_FEATURE_P 16
+
+/* qp_features: features of the QPs idx[0..count) (device int32 array, or
+ * NULL with count == batch for all QPs in order) for the initial states x0
+ * (device pool, qp_solve layout) into out: device float32 [count][ld],
+ * ld >= nx + 4 GPUSLS_FEATURE_P + 1. */
+int qp_features(qp_handle* q, const double* x0, const int32_t* idx, int32_t count, int32_t ld, float* out);
+
+/* qp_warm_start_heads: learned warm start with one network per shape family.
+ * Head hh serves the QPs idx[hh][0..counts[hh]) (device int32 arrays, no QP
+ * listed twice): its input is the QP's features (qp_features, so n_in = nx +
+ * 4 GPUSLS_FEATURE_P + 1), its output is laid out for a horizon n_stage[hh]
+ * >= every served QP's N: z of stage rows (n_stage nc), z of terminal rows
+ * (nf), lambda likewise, log rho -- n_out = 2 (n_stage nc + nf) + 1.  A QP of
+ * horizon N takes its first N nc stage rows and the terminal rows; z is
+ * clamped to the bounds, y = lambda / rho, rho clamped to [rho_min, rho_max].
+ * x0: device pool (qp_solve layout).  Runs on the QP handle's stream. */
+int qp_warm_start_heads(qp_handle* q, int32_t n_heads, mlp_handle* const* heads, const int32_t* const* idx,
+                        const int32_t* counts, const int32_t* n_stage, const double* x0,
+                        double rho_min, double rho_max);
+
 /* ------------------------------------------------------------------------ */
 /* Serving graph: one batched serving step captured as a CUDA graph         */
 /* ------------------------------------------------------------------------ */
@@ -367,6 +396,14 @@ int qp_graph_create(qp_graph** g, qp_handle* q, mlp_handle* m, const float* feat
                     double* dx, double* du, double* lam, int32_t* info_i, double* info_d,
                     double rho_min, double rho_max);
 int qp_graph_launch(qp_graph* g, void* stream);
+/* qp_graph_create_heads: as qp_graph_create, with the learned warm start
+ * of qp_warm_start_heads (features computed inside the graph from the
+ * handle's current data and x0) in place of the single network.  The index
+ * arrays, the networks and x0 must stay valid while the graph exists. */
+int qp_graph_create_heads(qp_graph** g, qp_handle* q, int32_t n_heads, mlp_handle* const* heads,
+                          const int32_t* const* idx, const int32_t* counts, const int32_t* n_stage,
+                          const double* x0, double* dx, double* du, double* lam, int32_t* info_i, double* info_d,
+                          double rho_min, double rho_max);
 /* qp_graph_kernel_count: number of kernel launches one replay of the graph
  * performs (the kernel nodes of the captured graph), into *n (HOST). */
 int qp_graph_kernel_count(qp_graph* g, int32_t* n);

@@ -167,12 +167,42 @@ class QPBatch:
     def reset(self):
         native.check(self.lib.qp_reset(self.h), "qp_reset")
 
+    def features(self, idx=None) -> torch.Tensor:
+        """qp_features of the QPs idx (default all) at the handle's x0:
+        float32 device tensor [count, max nx + 4 P + 1] (rows padded with 0)."""
+        ids = list(range(self.B)) if idx is None else [int(i) for i in idx]
+        ld = max(self.nx[i] for i in ids) + 4 * native.GPUSLS_FEATURE_P + 1
+        out = torch.zeros(len(ids), ld, dtype=torch.float32, device=self.device)
+        tidx = torch.tensor(ids, dtype=torch.int32, device=self.device)
+        native.check(self.lib.qp_features(self.h, _dptr(self.x0), _dptr(tidx), len(ids), ld, _dptr(out)),
+                     "qp_features")
+        return out
+
+    def _heads_args(self, heads):
+        """heads: list of (MLP, QP indices, n_stage) -> ctypes arrays (the
+        index tensors are kept alive on the handle)."""
+        n = len(heads)
+        hs = (C.c_void_p * n)(*[hh[0].h.value for hh in heads])
+        idx_t = [torch.tensor([int(i) for i in hh[1]], dtype=torch.int32, device=self.device) for hh in heads]
+        self._keep = getattr(self, "_keep", []) + idx_t
+        ids = (C.c_void_p * n)(*[t.data_ptr() for t in idx_t])
+        counts = (C.c_int32 * n)(*[len(hh[1]) for hh in heads])
+        ns = (C.c_int32 * n)(*[int(hh[2]) for hh in heads])
+        return n, hs, ids, counts, ns
+
+    def warm_start_heads(self, heads, rho_min=1e-3, rho_max=1e3):
+        """qp_warm_start_heads: one network per shape family (list of
+        (MLP, QP indices, n_stage)), features computed by the library."""
+        n, hs, ids, counts, ns = self._heads_args(heads)
+        native.check(self.lib.qp_warm_start_heads(self.h, n, hs, ids, counts, ns, _dptr(self.x0), float(rho_min),
+                                                  float(rho_max)), "qp_warm_start_heads")
+
     def graph(self, mlp: "MLP | None" = None, features: torch.Tensor | None = None, rho_min=1e-3,
-              rho_max=1e3) -> "ServeGraph":
+              rho_max=1e3, heads=None) -> "ServeGraph":
         """Capture one serving step (reset, optional learned warm start, solve)
         as a CUDA graph (qp_graph_create).  x0, the outputs and `features` are
         baked in: refill them in place (e.g. self.x0.copy_(...))."""
-        g = ServeGraph(self, mlp, features, rho_min, rho_max)
+        g = ServeGraph(self, mlp, features, rho_min, rho_max, heads=heads)
         self._graphs.append(g)
         return g
 
@@ -195,17 +225,25 @@ class ServeGraph:
     the learned warm start (when an MLP was given) and the persistent solve on
     a stream, with no host synchronization; info() reads the per-QP results."""
 
-    def __init__(self, qb: QPBatch, mlp=None, features=None, rho_min=1e-3, rho_max=1e3):
+    def __init__(self, qb: QPBatch, mlp=None, features=None, rho_min=1e-3, rho_max=1e3, heads=None):
         self.lib = qb.lib
         self.qb = qb
         self.features = features
         self.info_i = torch.zeros(qb.B * 8, dtype=torch.int32, device=qb.device)
         self.info_d = torch.zeros(qb.B * 4, dtype=torch.float64, device=qb.device)
         g = C.c_void_p()
-        st = self.lib.qp_graph_create(C.byref(g), qb.h, mlp.h if mlp is not None else None, _dptr(features),
-                                      _dptr(qb.x0), _dptr(qb.out_x), _dptr(qb.out_u), _dptr(qb.out_l),
-                                      _dptr(self.info_i), _dptr(self.info_d), float(rho_min), float(rho_max))
-        native.check(st, "qp_graph_create")
+        if heads:
+            n, hs, ids, counts, ns = qb._heads_args(heads)
+            st = self.lib.qp_graph_create_heads(C.byref(g), qb.h, n, hs, ids, counts, ns, _dptr(qb.x0),
+                                                _dptr(qb.out_x), _dptr(qb.out_u), _dptr(qb.out_l),
+                                                _dptr(self.info_i), _dptr(self.info_d), float(rho_min),
+                                                float(rho_max))
+            native.check(st, "qp_graph_create_heads")
+        else:
+            st = self.lib.qp_graph_create(C.byref(g), qb.h, mlp.h if mlp is not None else None, _dptr(features),
+                                          _dptr(qb.x0), _dptr(qb.out_x), _dptr(qb.out_u), _dptr(qb.out_l),
+                                          _dptr(self.info_i), _dptr(self.info_d), float(rho_min), float(rho_max))
+            native.check(st, "qp_graph_create")
         self.g = g
 
     def launch(self, stream: torch.cuda.Stream | None = None):

@@ -53,4 +53,13 @@ int mlp_enqueue_warm_start(qp_handle* q, mlp_handle* h, const float* features, d
                            cudaStream_t stream);
 // Factorization only (MODE_RICCATI) without copying results out.
 int qp_refactor_internal(qp_handle* h);
+// Linearization features and one warm-start head (features -> network ->
+// warm start of the QPs idx_dev[0..count)), enqueued on `stream` without host
+// synchronization; features_smem gives the features kernel's shared memory
+// for the listed QPs (host indices).
+int features_smem(const qp_handle* q, const int32_t* host_idx, int count);
+int enqueue_head(qp_handle* q, mlp_handle* h, const int32_t* idx_dev, int count, int smem, int n_stage,
+                 const double* x0, float* feat, double rho_min, double rho_max, cudaStream_t stream);
+int mlp_n_in(const mlp_handle* h);
+const void* qp_features_kernel_ptr();
 }  // namespace gsls

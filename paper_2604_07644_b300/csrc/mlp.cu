@@ -492,3 +492,248 @@ extern "C" int qp_warm_start_mlp(qp_handle* q, mlp_handle* h, const float* featu
   CUM(cudaStreamSynchronize(h->stream));
   return GPUSLS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Linearization features and per-family warm-start heads
+// ---------------------------------------------------------------------------
+namespace gsls {
+
+// +-1 from a 32-bit mix of (salt, row l, input index e) (the finalizer of
+// MurmurHash3): a fixed Rademacher projection that needs no stored matrix.
+__device__ inline float rad_sign(unsigned salt, unsigned l, unsigned e) {
+  unsigned h = salt * 0x9E3779B1u ^ (l + 0x7F4A7C15u) * 0x85EBCA77u ^ (e + 0x165667B1u) * 0xC2B2AE3Du;
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return (h & 1u) ? 1.f : -1.f;
+}
+
+// Block sum of one value per thread (blockDim.x == 256), result to all threads.
+__device__ inline float feat_block_sum(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int w = 0; w < 8; ++w) s += red[w];
+  return s;
+}
+
+// One CTA per listed QP: row i of out = [x0 (nx), p projections each of
+// mean_k (A_k - I), mean_k B_k, mean_k q_k (k = 0..N) and the mean of the
+// finite upper bounds of each stage row (clamped to +-10), N / 128].
+__global__ void __launch_bounds__(256) qp_features_kernel(const QPDesc* __restrict__ descs, const int* __restrict__ idx,
+                                                          const double* __restrict__ x064_base,
+                                                          const double* __restrict__ x0, int p, int ld,
+                                                          float* __restrict__ out) {
+  extern __shared__ float fsm[];
+  __shared__ float red[8];
+  const int b = idx ? idx[blockIdx.x] : (int)blockIdx.x;
+  const QPDesc& d = descs[b];
+  const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, t = threadIdx.x;
+  float* row = out + (size_t)blockIdx.x * ld;
+  const double* xb = x0 + (d.x064 - x064_base);
+  for (int i = t; i < nx; i += blockDim.x) row[i] = (float)xb[i];
+  float* mA = fsm;                      // [nx * nx]
+  float* mB = mA + nx * nx;             // [nx * nu]
+  float* mq = mB + nx * nu;             // [nx]
+  float* mh = mq + nx;                  // [nc]
+  const double invN = 1.0 / N;
+  for (int e = t; e < nx * nx; e += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += d.A64[(size_t)k * nx * nx + e];
+    mA[e] = (float)(s * invN - ((e % (nx + 1)) == 0 ? 1.0 : 0.0));
+  }
+  for (int e = t; e < nx * nu; e += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += d.B64[(size_t)k * nx * nu + e];
+    mB[e] = (float)(s * invN);
+  }
+  for (int e = t; e < nx; e += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k <= N; ++k) s += d.q64[(size_t)k * nx + e];
+    mq[e] = (float)(s / (N + 1));
+  }
+  for (int e = t; e < nc; e += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) {
+      const double h = d.hi64[(size_t)k * nc + e];
+      s += isfinite(h) ? fmin(fmax(h, -10.0), 10.0) : 0.0;
+    }
+    mh[e] = (float)(s * invN);
+  }
+  __syncthreads();
+  const float sA = rsqrtf((float)(nx * nx)), sB = rsqrtf((float)(nx * nu)), sq = rsqrtf((float)nx),
+              sh = nc > 0 ? rsqrtf((float)nc) : 0.f;
+  for (int l = 0; l < p; ++l) {
+    float a = 0.f, bb = 0.f, q = 0.f, h = 0.f;
+    for (int e = t; e < nx * nx; e += blockDim.x) a += rad_sign(1u, l, e) * mA[e];
+    for (int e = t; e < nx * nu; e += blockDim.x) bb += rad_sign(2u, l, e) * mB[e];
+    for (int e = t; e < nx; e += blockDim.x) q += rad_sign(3u, l, e) * mq[e];
+    for (int e = t; e < nc; e += blockDim.x) h += rad_sign(4u, l, e) * mh[e];
+    a = feat_block_sum(a, red);
+    bb = feat_block_sum(bb, red);
+    q = feat_block_sum(q, red);
+    h = feat_block_sum(h, red);
+    if (t == 0) {
+      row[nx + l] = a * sA;
+      row[nx + p + l] = bb * sB;
+      row[nx + 2 * p + l] = q * sq;
+      row[nx + 3 * p + l] = h * sh;
+    }
+  }
+  if (t == 0) row[nx + 4 * p] = (float)N / 128.f;
+}
+
+// Warm start of the listed QPs from a head's denormalized outputs Y [count]
+// [ldy] laid out for horizon n_stage (>= each QP's N): z stage rows, z
+// terminal rows, lambda stage rows, lambda terminal rows, log rho.
+template <typename T>
+__global__ void warm_assemble_heads_kernel(const QPDesc* __restrict__ descs, const int* __restrict__ idx,
+                                           const float* __restrict__ Y, int ldy, int n_stage, double rho_lo,
+                                           double rho_hi) {
+  const int b = idx ? idx[blockIdx.x] : (int)blockIdx.x;
+  const QPDesc d = descs[b];
+  const float* y = Y + (size_t)blockIdx.x * ldy;
+  const int m = d.m, ns = d.N * d.nc, mmax = n_stage * d.nc + d.nf;
+  double rho = exp((double)y[2 * mmax]);
+  rho = fmin(fmax(rho, rho_lo), rho_hi);
+  T* z = reinterpret_cast<T*>(d.z);
+  T* yy = reinterpret_cast<T*>(d.y);
+  const T* lo = reinterpret_cast<const T*>(d.lo);
+  const T* hi = reinterpret_cast<const T*>(d.hi);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int src = i < ns ? i : n_stage * d.nc + (i - ns);
+    const T zz = fmin(fmax((T)y[src], lo[i]), hi[i]);
+    z[i] = zz;
+    yy[i] = (T)((double)y[mmax + src] / rho);
+  }
+  if (threadIdx.x == 0) {
+    if (d.rho[0] != rho) d.flags[0] = 0;
+    d.rho[0] = rho;
+    d.flags[1] = 1;
+  }
+}
+
+int features_smem(const qp_handle* q, const int32_t* host_idx, int count) {
+  int mx = 0;
+  for (int i = 0; i < (host_idx ? count : q->batch); ++i) {
+    const qp_dims& d = q->dims[host_idx ? host_idx[i] : i];
+    mx = std::max(mx, (d.nx * d.nx + d.nx * d.nu + d.nx + d.nc) * (int)sizeof(float));
+  }
+  return mx;
+}
+
+// Features of the QPs idx[0..count) into out [count][ld] on `stream`.
+int enqueue_features(qp_handle* q, const int32_t* idx_dev, int count, int smem, const double* x0, int p, int ld,
+                     float* out, cudaStream_t stream) {
+  qp_features_kernel<<<count, 256, smem, stream>>>(q->ddesc, idx_dev, q->hdesc[0].x064, x0, p, ld, out);
+  CUM(cudaGetLastError());
+  return GPUSLS_OK;
+}
+
+// One head: features -> network -> warm start of its QPs, all on `stream`.
+int enqueue_head(qp_handle* q, mlp_handle* h, const int32_t* idx_dev, int count, int smem, int n_stage,
+                 const double* x0, float* feat, double rho_min, double rho_max, cudaStream_t stream) {
+  if (count > h->maxb) return set_error(GPUSLS_ERR_INVALID, "warm-start head: more QPs than the network's max batch");
+  int st = enqueue_features(q, idx_dev, count, smem, x0, GPUSLS_FEATURE_P, h->n_in, feat, stream);
+  if (st) return st;
+  const cudaStream_t saved = h->stream;
+  h->stream = stream;
+  affine_rows_kernel<<<blocks((size_t)count * h->n_in), 256, 0, stream>>>(feat, h->Xn, h->xm, h->xs, count, h->n_in,
+                                                                           0);
+  st = forward(h, h->Xn, count);
+  h->stream = saved;
+  if (st) return st;
+  float* Yd = h->dY;
+  affine_rows_kernel<<<blocks((size_t)count * h->n_out), 256, 0, stream>>>(h->Y, Yd, h->ym, h->ys, count, h->n_out, 1);
+  if (q->esz == 8)
+    warm_assemble_heads_kernel<double><<<count, 256, 0, stream>>>(q->ddesc, idx_dev, Yd, h->n_out, n_stage, rho_min,
+                                                                  rho_max);
+  else
+    warm_assemble_heads_kernel<float><<<count, 256, 0, stream>>>(q->ddesc, idx_dev, Yd, h->n_out, n_stage, rho_min,
+                                                                 rho_max);
+  CUM(cudaGetLastError());
+  return GPUSLS_OK;
+}
+
+int mlp_n_in(const mlp_handle* h) { return h->n_in; }
+const void* qp_features_kernel_ptr() { return reinterpret_cast<const void*>(qp_features_kernel); }
+
+}  // namespace gsls
+
+extern "C" int qp_features(qp_handle* q, const double* x0, const int32_t* idx, int32_t count, int32_t ld,
+                           float* out) {
+  if (!q || !x0 || !out || count < 1 || (!idx && count != q->batch))
+    return set_error(GPUSLS_ERR_INVALID, "qp_features: invalid argument");
+  std::vector<int32_t> hidx;
+  if (idx) {
+    hidx.resize(count);
+    CUM(cudaMemcpy(hidx.data(), idx, count * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  }
+  for (int i = 0; i < count; ++i) {
+    const int b = idx ? hidx[i] : i;
+    if (b < 0 || b >= q->batch) return set_error(GPUSLS_ERR_INVALID, "qp_features: index out of range");
+    if (q->dims[b].nx + 4 * GPUSLS_FEATURE_P + 1 > ld)
+      return set_error(GPUSLS_ERR_INVALID, "qp_features: ld < nx + 4 GPUSLS_FEATURE_P + 1");
+  }
+  const int smem = gsls::features_smem(q, idx ? hidx.data() : nullptr, count);
+  CUM(cudaFuncSetAttribute(gsls::qp_features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int st = gsls::enqueue_features(q, idx, count, smem, x0, GPUSLS_FEATURE_P, ld, out, q->stream);
+  if (st) return st;
+  CUM(cudaStreamSynchronize(q->stream));
+  return GPUSLS_OK;
+}
+
+namespace {
+// host-side checks of a head list; fills the shared-memory need per head
+int check_heads(qp_handle* q, int32_t n_heads, mlp_handle* const* heads, const int32_t* const* idx,
+                const int32_t* counts, const int32_t* n_stage, std::vector<int>& smem) {
+  if (!q || n_heads < 1 || !heads || !idx || !counts || !n_stage)
+    return set_error(GPUSLS_ERR_INVALID, "warm-start heads: null argument");
+  smem.assign(n_heads, 0);
+  std::vector<int> seen(q->batch, 0);
+  for (int hh = 0; hh < n_heads; ++hh) {
+    mlp_handle* h = heads[hh];
+    if (!h || !idx[hh] || counts[hh] < 1 || counts[hh] > h->maxb)
+      return set_error(GPUSLS_ERR_INVALID, "warm-start heads: bad head, index list or count");
+    std::vector<int32_t> hidx(counts[hh]);
+    CUM(cudaMemcpy(hidx.data(), idx[hh], counts[hh] * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < counts[hh]; ++i) {
+      const int b = hidx[i];
+      if (b < 0 || b >= q->batch || seen[b]++)
+        return set_error(GPUSLS_ERR_INVALID, "warm-start heads: QP index out of range or listed twice");
+      const qp_dims& d = q->dims[b];
+      if (d.N > n_stage[hh] || h->n_in != d.nx + 4 * GPUSLS_FEATURE_P + 1 ||
+          h->n_out != 2 * (n_stage[hh] * d.nc + d.nf) + 1)
+        return set_error(GPUSLS_ERR_INVALID, "warm-start heads: network sizes do not match QP " + std::to_string(b));
+    }
+    smem[hh] = gsls::features_smem(q, hidx.data(), counts[hh]);
+  }
+  CUM(cudaFuncSetAttribute(gsls::qp_features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           *std::max_element(smem.begin(), smem.end())));
+  return GPUSLS_OK;
+}
+}  // namespace
+
+extern "C" int qp_warm_start_heads(qp_handle* q, int32_t n_heads, mlp_handle* const* heads,
+                                   const int32_t* const* idx, const int32_t* counts, const int32_t* n_stage,
+                                   const double* x0, double rho_min, double rho_max) {
+  std::vector<int> smem;
+  int st = check_heads(q, n_heads, heads, idx, counts, n_stage, smem);
+  if (st) return st;
+  if (!x0) return set_error(GPUSLS_ERR_INVALID, "qp_warm_start_heads: null x0");
+  for (int hh = 0; hh < n_heads; ++hh) {
+    float* feat = nullptr;
+    CUM(cudaMalloc(&feat, (size_t)counts[hh] * heads[hh]->n_in * sizeof(float)));
+    st = gsls::enqueue_head(q, heads[hh], idx[hh], counts[hh], smem[hh], n_stage[hh], x0, feat, rho_min, rho_max,
+                            q->stream);
+    cudaError_t e = cudaStreamSynchronize(q->stream);
+    cudaFree(feat);
+    if (st) return st;
+    if (e != cudaSuccess) return set_error(GPUSLS_ERR_CUDA, std::string("qp_warm_start_heads: ") + cudaGetErrorString(e));
+  }
+  return GPUSLS_OK;
+}

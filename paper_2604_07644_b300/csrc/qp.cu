@@ -593,6 +593,7 @@ struct qp_graph {
   cudaGraphExec_t exec = nullptr;
   PackJob* djobs = nullptr;   // x0 pack jobs (uploaded once)
   int njobs = 0;
+  std::vector<float*> feat;   // per-head feature buffers (qp_graph_create_heads)
 };
 
 extern "C" void qp_graph_destroy(qp_graph* g) {
@@ -600,17 +601,16 @@ extern "C" void qp_graph_destroy(qp_graph* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->djobs) cudaFree(g->djobs);
+  for (float* f : g->feat) cudaFree(f);
   if (g->cap) cudaStreamDestroy(g->cap);
   delete g;
 }
 
-extern "C" int qp_graph_create(qp_graph** out, qp_handle* h, mlp_handle* m, const float* features, const double* x0,
-                               double* dx, double* du, double* lam, int32_t* info_i, double* info_d,
-                               double rho_min, double rho_max) {
-  if (!out || !h || !x0 || !dx || !du || !lam || (m && !features))
-    return fail(GPUSLS_ERR_INVALID, "qp_graph_create: null argument");
+// Captures reset -> warm(stream) -> x0 pack -> solve -> info copies.
+template <typename Warm>
+static int graph_create(qp_graph** out, qp_graph* g, qp_handle* h, Warm warm, const double* x0, double* dx,
+                        double* du, double* lam, int32_t* info_i, double* info_d) {
   *out = nullptr;
-  qp_graph* g = new qp_graph();
   g->q = h;
   auto bail = [&](int code, const std::string& msg) {
     qp_graph_destroy(g);
@@ -650,7 +650,7 @@ extern "C" int qp_graph_create(qp_graph** out, qp_handle* h, mlp_handle* m, cons
   int est = GPUSLS_OK;
   if (h->esz == 8) reset_kernel<double><<<h->batch, 256, 0, g->cap>>>(h->ddesc, h->rho0_dev);
   else reset_kernel<float><<<h->batch, 256, 0, g->cap>>>(h->ddesc, h->rho0_dev);
-  if (m) est = gsls::mlp_enqueue_warm_start(h, m, features, rho_min, rho_max, g->cap);
+  est = warm(g->cap);
   if (!est && cudaMemcpyAsync(h->hdesc[0].x064, x0, tot * sizeof(double), cudaMemcpyDeviceToDevice, g->cap))
     est = GPUSLS_ERR_CUDA;
   if (!est) {
@@ -673,6 +673,61 @@ extern "C" int qp_graph_create(qp_graph** out, qp_handle* h, mlp_handle* m, cons
   if (ei != cudaSuccess) return bail(GPUSLS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
   *out = g;
   return GPUSLS_OK;
+}
+
+extern "C" int qp_graph_create(qp_graph** out, qp_handle* h, mlp_handle* m, const float* features, const double* x0,
+                               double* dx, double* du, double* lam, int32_t* info_i, double* info_d,
+                               double rho_min, double rho_max) {
+  if (!out || !h || !x0 || !dx || !du || !lam || (m && !features))
+    return fail(GPUSLS_ERR_INVALID, "qp_graph_create: null argument");
+  qp_graph* g = new qp_graph();
+  auto warm = [&](cudaStream_t st) -> int {
+    return m ? gsls::mlp_enqueue_warm_start(h, m, features, rho_min, rho_max, st) : GPUSLS_OK;
+  };
+  return graph_create(out, g, h, warm, x0, dx, du, lam, info_i, info_d);
+}
+
+extern "C" int qp_graph_create_heads(qp_graph** out, qp_handle* h, int32_t n_heads, mlp_handle* const* heads,
+                                     const int32_t* const* idx, const int32_t* counts, const int32_t* n_stage,
+                                     const double* x0, double* dx, double* du, double* lam, int32_t* info_i,
+                                     double* info_d, double rho_min, double rho_max) {
+  if (!out || !h || !x0 || !dx || !du || !lam || n_heads < 1 || !heads || !idx || !counts || !n_stage)
+    return fail(GPUSLS_ERR_INVALID, "qp_graph_create_heads: null argument");
+  // the host-side checks of qp_warm_start_heads
+  std::vector<int> smem(n_heads);
+  for (int hh = 0; hh < n_heads; ++hh) {
+    if (!heads[hh] || !idx[hh] || counts[hh] < 1) return fail(GPUSLS_ERR_INVALID, "qp_graph_create_heads: bad head");
+    std::vector<int32_t> hidx(counts[hh]);
+    if (cudaMemcpy(hidx.data(), idx[hh], counts[hh] * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(GPUSLS_ERR_CUDA, "qp_graph_create_heads: index copy failed");
+    for (int i = 0; i < counts[hh]; ++i)
+      if (hidx[i] < 0 || hidx[i] >= h->batch || h->dims[hidx[i]].N > n_stage[hh])
+        return fail(GPUSLS_ERR_INVALID, "qp_graph_create_heads: QP index or horizon out of range");
+    smem[hh] = gsls::features_smem(h, hidx.data(), counts[hh]);
+  }
+  qp_graph* g = new qp_graph();
+  for (int hh = 0; hh < n_heads; ++hh) {
+    float* f = nullptr;
+    if (cudaMalloc(&f, (size_t)counts[hh] * gsls::mlp_n_in(heads[hh]) * sizeof(float)) != cudaSuccess) {
+      qp_graph_destroy(g);
+      return fail(GPUSLS_ERR_CUDA, "qp_graph_create_heads: cudaMalloc failed");
+    }
+    g->feat.push_back(f);
+  }
+  if (cudaFuncSetAttribute(gsls::qp_features_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           *std::max_element(smem.begin(), smem.end())) != cudaSuccess) {
+    qp_graph_destroy(g);
+    return fail(GPUSLS_ERR_CUDA, "qp_graph_create_heads: cudaFuncSetAttribute failed");
+  }
+  auto warm = [&](cudaStream_t st) -> int {
+    for (int hh = 0; hh < n_heads; ++hh) {
+      const int e = gsls::enqueue_head(h, heads[hh], idx[hh], counts[hh], smem[hh], n_stage[hh], x0, g->feat[hh],
+                                       rho_min, rho_max, st);
+      if (e) return e;
+    }
+    return GPUSLS_OK;
+  };
+  return graph_create(out, g, h, warm, x0, dx, du, lam, info_i, info_d);
 }
 
 extern "C" int qp_graph_launch(qp_graph* g, void* stream) {

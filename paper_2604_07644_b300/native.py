@@ -25,6 +25,7 @@ GPUSLS_FP64 = 0
 GPUSLS_FP32 = 1
 GPUSLS_TF32 = 2
 GPUSLS_MIXED = 3
+GPUSLS_FEATURE_P = 16
 
 STATUS_NAMES = {0: "ok", 1: "max_iter", -1: "invalid", -2: "not_spd", -3: "nan", -4: "infeasible",
                 -5: "cuda", -6: "timeout"}
@@ -101,6 +102,12 @@ SIGNATURES = {
     "qp_graph_launch": (C.c_int, [P, P]),
     "qp_graph_destroy": (None, [P]),
     "qp_graph_kernel_count": (C.c_int, [P, C.POINTER(C.c_int32)]),
+    "qp_features": (C.c_int, [P, DP, P, C.c_int32, C.c_int32, P]),
+    "qp_warm_start_heads": (C.c_int, [P, C.c_int32, C.POINTER(P), C.POINTER(P), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_int32), DP, C.c_double, C.c_double]),
+    "qp_graph_create_heads": (C.c_int, [C.POINTER(P), P, C.c_int32, C.POINTER(P), C.POINTER(P),
+                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32), DP, DP, DP, DP, P, DP,
+                                        C.c_double, C.c_double]),
     "model_dims": (C.c_int, [C.POINTER(model_spec), C.POINTER(qp_dims)]),
     "model_linearize": (C.c_int, [C.POINTER(model_spec), C.c_int32] + [DP] * 17 + [P]),
     "model_merit": (C.c_int, [C.POINTER(model_spec), C.c_int32] + [DP] * 6 + [C.c_double, DP, P]),

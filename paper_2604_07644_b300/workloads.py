@@ -465,10 +465,12 @@ class Family:
     M: np.ndarray = field(repr=False)        # [N_THETA, nx, nx] perturbation directions of A
     goal_dirs: np.ndarray = field(repr=False)  # [N_THETA, 2]
 
-    def instance(self, i: int) -> QP:
+    def instance(self, i: int, N: int | None = None) -> QP:
         """Instance i: x0 ~ U[-0.5, 0.5]^nx, theta ~ U[-1, 1]^8,
-        A_k(theta) = A_k + 0.002 sum_l theta_l M_l, goal angle set by theta."""
-        b = self.base
+        A_k(theta) = A_k + 0.002 sum_l theta_l M_l, goal angle set by theta.
+        N (<= the base horizon): the first N stages of the base problem with
+        its terminal cost and rows (the serving mix's ragged horizons)."""
+        b = self.base if N is None or N == self.base.N else _truncate(self.base, N)
         g = rng(77, i, b.nx)
         x0 = g.uniform(-0.5, 0.5, b.nx)
         th = g.uniform(-1.0, 1.0, N_THETA)
@@ -494,6 +496,57 @@ class Family:
         return QP(A=A, B=b.B, c=b.c, Q=b.Q, R=b.R, S=b.S, q=q, r=b.r, C=b.C, D=b.D,
                   CN=b.CN, lo=b.lo, hi=hi, x0=x0, name=f"{b.name}-inst{i}",
                   features=np.concatenate([x0, th]))
+
+
+def _truncate(qp: QP, N: int) -> QP:
+    """The first N stages of qp with its terminal cost and terminal rows."""
+    if not 1 <= N <= qp.N:
+        raise ValueError("horizon out of range")
+    nc = qp.nc
+    return QP(A=qp.A[:N], B=qp.B[:N], c=qp.c[:N], Q=np.concatenate([qp.Q[:N], qp.Q[-1:]]), R=qp.R[:N],
+              S=qp.S[:N], q=np.concatenate([qp.q[:N], qp.q[-1:]]), r=qp.r[:N], C=qp.C[:N], D=qp.D[:N], CN=qp.CN,
+              lo=np.concatenate([qp.lo[:N * nc], qp.lo[qp.N * nc:]]),
+              hi=np.concatenate([qp.hi[:N * nc], qp.hi[qp.N * nc:]]), x0=qp.x0, name=f"{qp.name}-N{N}")
+
+
+def family_from(base: QP, seed: int) -> Family:
+    """A warm-start family around any base problem (the perturbation
+    directions M_l and goal directions drawn from the seed)."""
+    nx = base.nx
+    g = rng(79, seed, nx)
+    M = g.standard_normal((N_THETA, nx, nx)) / math.sqrt(nx)
+    goal_dirs = g.standard_normal((N_THETA, 2))
+    return Family(base=base, M=M, goal_dirs=goal_dirs)
+
+
+# shape families of the serving mix (nx, nu): the quadrotor-shaped 12D/4 and
+# the legged 61D/12 and 75D/21 recipes, each built at the longest horizon
+# (128) and truncated per instance
+MIX_FAMILIES = ((12, 4), (61, 12), (75, 21))
+MIX_N_MAX = 128
+
+
+def mix_family(kind: int, seed: int = 0) -> Family:
+    """Family `kind` (0: 12D quadrotor-shaped, 1: 61D, 2: 75D legged) of
+    the learned serving mix, at horizon MIX_N_MAX."""
+    if kind == 0:
+        return family_from(quadrotor_12d(seed + 1000, MIX_N_MAX), seed)
+    nx, nu = MIX_FAMILIES[kind]
+    return family_from(legged(seed + 1000, nx, nu, MIX_N_MAX, tag=6 + kind), seed + kind)
+
+
+def serving_mix_learned(seed: int = 0, count: int = 256, first: int = 100000):
+    """256 QPs of the three mix families (uniform) with N ~ U{16..128}, as
+    (QP, family kind) pairs; instance indices from `first` (held out from
+    training, which uses indices below 100000)."""
+    g = rng(23, seed, count)
+    fams = [mix_family(k) for k in range(3)]
+    out = []
+    for i in range(count):
+        kind = int(g.integers(0, 3))
+        N = int(g.integers(16, MIX_N_MAX + 1))
+        out.append((fams[kind].instance(first + i, N), kind))
+    return out
 
 
 def family(seed: int = 0, nx: int = 61, nu: int = 12, N: int = 100) -> Family:

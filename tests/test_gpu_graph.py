@@ -57,7 +57,7 @@ def test_graph_learned_warm_start_matches_eager(lib):
                                  max_iter=6000, eps_floor=1e-5)
     qb = QPBatch(qps, st)
     mlp = learned.load(MODEL, max_batch=len(qps))
-    feats = torch.from_numpy(learned.features(qps)).cuda()
+    feats = qb.features()            # the library's linearization features, given explicitly
     ref, info_e = _eager(qb, mlp, feats)
     g = qb.graph(mlp, feats)
     g.launch()
@@ -65,6 +65,32 @@ def test_graph_learned_warm_start_matches_eager(lib):
     assert _same(_snapshot(qb), ref)
     assert [i["iters"] for i in g.info()] == [i["iters"] for i in info_e]
     assert all(i["status"] == native.GPUSLS_OK for i in g.info())
+    mlp.close()
+    qb.close()
+
+
+def test_graph_heads_match_eager_and_single_network(lib):
+    """The per-family heads graph (features computed inside the graph) gives
+    bit for bit the eager qp_warm_start_heads + solve, and the single-network
+    path fed the same features."""
+    fam = W.family(0)
+    qps = [fam.instance(100010 + i) for i in range(6)]
+    st = native.default_settings(precision=native.GPUSLS_FP32, cluster=8, max_refine=3, fallback_iters=2000,
+                                 max_iter=6000, eps_floor=1e-5)
+    qb = QPBatch(qps, st)
+    mlp = learned.load(MODEL, max_batch=len(qps))
+    heads = [(mlp, list(range(len(qps))), qps[0].N)]
+    qb.reset()
+    qb.warm_start_heads(heads)
+    r = qb.solve(fetch=True)
+    ref = _snapshot(qb)
+    g = qb.graph(heads=heads)
+    g.launch()
+    torch.cuda.synchronize()
+    assert _same(_snapshot(qb), ref)
+    assert [i["iters"] for i in g.info()] == [i["iters"] for i in r.info]
+    ref2, _ = _eager(qb, mlp, qb.features())
+    assert _same(ref2, ref)
     mlp.close()
     qb.close()
 

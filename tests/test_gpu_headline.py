@@ -62,8 +62,7 @@ def headline_solve(qps, eps_kkt, max_refine=3, precision=native.GPUSLS_FP32):
     with torch.cuda.stream(stream):
         qb = QPBatch(qps, s, stream=stream)
         mlp = learned.load(MODEL, max_batch=len(qps), stream=stream)
-        feats = torch.from_numpy(learned.features(qps)).cuda()
-        g = qb.graph(mlp, feats)
+        g = qb.graph(heads=[(mlp, list(range(len(qps))), qps[0].N)])
         for _ in range(2):
             g.launch(stream)
         stream.synchronize()
