@@ -51,8 +51,9 @@ int set_error(int code, const std::string& msg);
 // synchronization (graph-capturable).
 int mlp_enqueue_warm_start(qp_handle* q, mlp_handle* h, const float* features, double rho_min, double rho_max,
                            cudaStream_t stream);
-// Factorization only (MODE_RICCATI) without copying results out.
-int qp_refactor_internal(qp_handle* h);
+// Factorization only (MODE_RICCATI) without copying results out; gains_only
+// (MODE_GAINS) skips the iteration operators.
+int qp_refactor_internal(qp_handle* h, bool gains_only = false);
 // Linearization features and one warm-start head (features -> network ->
 // warm start of the QPs idx_dev[0..count)), enqueued on `stream` without host
 // synchronization; features_smem gives the features kernel's shared memory

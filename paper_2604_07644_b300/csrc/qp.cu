@@ -764,11 +764,11 @@ extern "C" int qp_riccati(qp_handle* h, double* P, double* K) {
   return collect(h, nullptr);
 }
 
-int gsls::qp_refactor_internal(qp_handle* h) {
+int gsls::qp_refactor_internal(qp_handle* h, bool gains_only) {
   int st = set_outputs(h, nullptr, nullptr, nullptr, 0, 0, true);
   if (st) return st;
   SolveArgs a = {};
-  a.mode = MODE_RICCATI;
+  a.mode = gains_only ? MODE_GAINS : MODE_RICCATI;
   a.cs = h->cs;
   st = launch(h, a);
   if (st) return st;

@@ -65,7 +65,11 @@ struct QPDesc {
   double* info_d;   // [4]: rho, r_prim, r_dual, kkt
 };
 
-enum Mode { MODE_SOLVE = 0, MODE_RICCATI = 1, MODE_KKT = 2 };
+// MODE_GAINS: the factorization for its gains alone (K_i, Abar_i, P_i,
+// Gamma_i), without the iteration operators (bundles, chunk products,
+// chunk-boundary operators): the SLS controller solves need no more, and
+// the handle's factorization is left marked invalid for iterations.
+enum Mode { MODE_SOLVE = 0, MODE_RICCATI = 1, MODE_KKT = 2, MODE_GAINS = 3 };
 
 struct SolveArgs {
   unsigned long long* prof;   // optional per-phase cycle counters [cs][phases] of QP 0, else null
@@ -252,6 +256,7 @@ struct Ctx {
   int uni;  // bytes of the union region at ring
   unsigned long long* prof;  // non-null in each CTA of QP 0 when profiling (thread 0 records)
   bool tc;                   // factorization products in TF32 on the tensor cores (tree schedule)
+  bool gains;                // MODE_GAINS: skip the iteration operators in the factorization
   bool mix;                  // GPUSLS_MIXED: blocked-schedule products in three TF32 passes on the
                              // tensor cores, per-stage nu x nu solves in FP64
   long long t_last;
@@ -755,6 +760,10 @@ __device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, 
   cta_copy_vec<T>(nc, nx, fb.CKb[0], lds, TP<T>(d.CK) + (size_t)i * nc * ldx, ldx);
   for (int e = t; e < nx; e += NT) TP<T>(d.c0)[(size_t)i * ldx + e] = c0v[e];
   for (int e = t; e < nu; e += NT) TP<T>(d.k0)[(size_t)i * ldu + e] = k0v[e];
+  if (c.gains) {
+    prof_mark(c, PH_FC4);
+    return bad;
+  }
   if (!c.last) {
     // backward chunk products (Pi in Aa): FPi_i^T = Pi_{i+1}^T F_i^T, Pi_i = Abar_i^T Pi_{i+1}
     sgemm1<T>(nx, nu, nx, T(1), fb.Aa, lds, true, fb.BG, ldu, T(0), nullptr, 0,
@@ -1003,6 +1012,11 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
   else bad |= tree_scan<T>(c, cl, rho);
   cl.sync();
   prof_mark(c, PH_R4);
+  if (c.gains) {
+    const int res = cluster_or<T>(c, cl, bad);
+    prof_mark(c, PH_R6);
+    return res;
+  }
   // R5: chunk products.  Backward (not needed in the last chunk):
   //   FPi_i = F_i Pi_{i+1},  Pi_i = Abar_i^T Pi_{i+1},  Pi_e = I,  T_r = Pi_s.
   // Forward (not needed in the first chunk):

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     c.scr = TP<T>(d.scr) + (size_t)rank * 6 * c.msz;
     c.prof = (args.prof && qi == 0 && t == 0) ? args.prof + (size_t)rank * PH_COUNT : nullptr;
     c.t_last = clock64();
+    c.gains = args.mode == MODE_GAINS;
     c.tc = args.tc == 1;
     c.mix = args.tc == 2;
     iter_plan<T>(c);
@@ -106,12 +107,12 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   T rho = (T)d.rho[0];
   int refactors = 0;
   int status = GPUSLS_MAX_ITER;
-  if (args.mode == MODE_RICCATI || d.flags[0] == 0) {
+  if (args.mode == MODE_RICCATI || args.mode == MODE_GAINS || d.flags[0] == 0) {
     const int bad = refactor<T>(c, cl, rho);
     ++refactors;
     if (bad) status = GPUSLS_ERR_NOT_SPD;
   }
-  if (args.mode == MODE_RICCATI) {
+  if (args.mode == MODE_RICCATI || args.mode == MODE_GAINS) {
     // P_i = level-0 inclusive suffixes, K_i gains, as FP64 dense blocks.
     const int nx = d.nx, nu = d.nu, ldx = d.ldx, msz = c.msz;
     if (c.active && d.ox && d.ou) {
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
     if (rank == 0 && t == 0) {
       d.info_i[0] = status == GPUSLS_ERR_NOT_SPD ? status : GPUSLS_OK;
       d.info_i[2] = refactors;
-      d.flags[0] = status == GPUSLS_ERR_NOT_SPD ? 0 : 1;
+      d.flags[0] = (status == GPUSLS_ERR_NOT_SPD || args.mode == MODE_GAINS) ? 0 : 1;
     }
     cl.sync();
     return;

@@ -65,7 +65,11 @@ struct SLSBuild {
 };
 
 // One CTA per (problem q, local stage i <= N_q): copies A_k, B_k and forms the
-// cost blocks of stage k = first(q) + i (i == N_q: terminal) in FP64.
+// cost blocks of stage k = first(q) + i (i == N_q: terminal), accumulating in
+// Acc (FP64 handles: double; FP32 handles: float, whose solves round the
+// blocks to FP32 anyway -- B300's FP64 rate made this kernel 7 % of a
+// 75D solve).
+template <typename Acc>
 __global__ void sls_build_kernel(SLSBuild a) {
   const int q = blockIdx.y, i = blockIdx.x;
   const int first = a.per_j ? q + 1 : 1;
@@ -97,32 +101,32 @@ __global__ void sls_build_kernel(SLSBuild a) {
     double* Sd = a.pS + (oR + i) * nu * nx;
     for (int e = t; e < nx * nx; e += blockDim.x) {
       const int r = e / nx, c = e - r * nx;
-      double v = a.Qbar[e];
+      Acc v = (Acc)a.Qbar[e];
       if (tau)
-        for (int l = 0; l < nc; ++l) v += Ck[l * nx + r] * tau[l] * Ck[l * nx + c];
+        for (int l = 0; l < nc; ++l) v += (Acc)Ck[l * nx + r] * (Acc)tau[l] * (Acc)Ck[l * nx + c];
       Qd[e] = v;
     }
     for (int e = t; e < nu * nu; e += blockDim.x) {
       const int r = e / nu, c = e - r * nu;
-      double v = a.Rbar[e];
+      Acc v = (Acc)a.Rbar[e];
       if (tau)
-        for (int l = 0; l < nc; ++l) v += Dk[l * nu + r] * tau[l] * Dk[l * nu + c];
+        for (int l = 0; l < nc; ++l) v += (Acc)Dk[l * nu + r] * (Acc)tau[l] * (Acc)Dk[l * nu + c];
       Rd[e] = v;
     }
     for (int e = t; e < nu * nx; e += blockDim.x) {
       const int r = e / nx, c = e - r * nx;
-      double v = 0.0;
+      Acc v = Acc(0);
       if (tau)
-        for (int l = 0; l < nc; ++l) v += Dk[l * nu + r] * tau[l] * Ck[l * nx + c];
+        for (int l = 0; l < nc; ++l) v += (Acc)Dk[l * nu + r] * (Acc)tau[l] * (Acc)Ck[l * nx + c];
       Sd[e] = v;
     }
   } else {
     double* Qd = a.pQ + (oQ + Nq) * nx * nx;
     for (int e = t; e < nx * nx; e += blockDim.x) {
       const int r = e / nx, c = e - r * nx;
-      double v = a.QbarN[e];
+      Acc v = (Acc)a.QbarN[e];
       if (tau)
-        for (int l = 0; l < nf; ++l) v += a.CN[l * nx + r] * tau[l] * a.CN[l * nx + c];
+        for (int l = 0; l < nf; ++l) v += (Acc)a.CN[l * nx + r] * (Acc)tau[l] * (Acc)a.CN[l * nx + c];
       Qd[e] = v;
     }
   }
@@ -376,13 +380,14 @@ extern "C" int sls_solve(sls_handle* h, const double* A, const double* B, const 
     SLSBuild a = {A, B, Qbar, Rbar, QbarN, C, D, CN, tau, h->pA, h->pB, h->pQ, h->pR, h->pS,
                   nx, nu, N, nc, nf, std::max(nc, nf), h->per_j, h->nq};
     dim3 grid(N, h->nq);
-    sls_build_kernel<<<grid, 256, 0, st>>>(a);
+    if (h->esz == 8) sls_build_kernel<double><<<grid, 256, 0, st>>>(a);
+    else sls_build_kernel<float><<<grid, 256, 0, st>>>(a);
     CUS(cudaGetLastError());
     int s2 = qp_update(h->qh, h->pA, h->pB, nullptr, h->pQ, h->pR, h->pS, nullptr, nullptr, nullptr, nullptr, nullptr,
                        nullptr, nullptr);
     if (s2) return s2;
     // 2. reverse scans over the horizon and gains for every problem
-    s2 = qp_refactor_internal(h->qh);
+    s2 = qp_refactor_internal(h->qh, true);   // gains K_k^(j) and Abar_k^(j) only
     if (s2) return s2;
   }
   // solve-precision copies of E, C, D, CN
