@@ -71,6 +71,7 @@ struct SLSBuild {
 // 75D solve).
 template <typename Acc>
 __global__ void sls_build_kernel(SLSBuild a) {
+  extern __shared__ __align__(16) unsigned char bsm[];
   const int q = blockIdx.y, i = blockIdx.x;
   const int first = a.per_j ? q + 1 : 1;
   const int Nq = a.N - first;
@@ -89,13 +90,32 @@ __global__ void sls_build_kernel(SLSBuild a) {
   const double* tau = nullptr;
   if (a.tau) tau = a.tau + ((size_t)k * a.N + j) * a.tw;
   const int t = threadIdx.x;
+  // the constraint rows in shared memory, once as loaded (Cs, Ds) and once
+  // scaled by tau (CT = diag(tau) C, DT = diag(tau) D): every block entry is
+  // then a short dot product over rows read from shared memory
+  const int rows = i < Nq ? nc : nf;
+  Acc* Cs = reinterpret_cast<Acc*>(bsm);
+  Acc* CT = Cs + rows * nx;
+  Acc* Ds = CT + rows * nx;
+  Acc* DT = Ds + rows * nu;
+  const double* Cg = i < Nq ? a.C + (size_t)k * nc * nx : a.CN;
+  if (tau) {
+    for (int e = t; e < rows * nx; e += blockDim.x) {
+      Cs[e] = (Acc)Cg[e];
+      CT[e] = (Acc)tau[e / nx] * Cs[e];
+    }
+    if (i < Nq)
+      for (int e = t; e < nc * nu; e += blockDim.x) {
+        Ds[e] = (Acc)a.D[(size_t)k * nc * nu + e];
+        DT[e] = (Acc)tau[e / nu] * Ds[e];
+      }
+  }
+  __syncthreads();
   if (i < Nq) {
     double* Ad = a.pA + (oA + i) * nx * nx;
     double* Bd = a.pB + (oA + i) * nx * nu;
     for (int e = t; e < nx * nx; e += blockDim.x) Ad[e] = a.A[(size_t)k * nx * nx + e];
     for (int e = t; e < nx * nu; e += blockDim.x) Bd[e] = a.B[(size_t)k * nx * nu + e];
-    const double* Ck = a.C + (size_t)k * nc * nx;
-    const double* Dk = a.D + (size_t)k * nc * nu;
     double* Qd = a.pQ + (oQ + i) * nx * nx;
     double* Rd = a.pR + (oR + i) * nu * nu;
     double* Sd = a.pS + (oR + i) * nu * nx;
@@ -103,21 +123,21 @@ __global__ void sls_build_kernel(SLSBuild a) {
       const int r = e / nx, c = e - r * nx;
       Acc v = (Acc)a.Qbar[e];
       if (tau)
-        for (int l = 0; l < nc; ++l) v += (Acc)Ck[l * nx + r] * (Acc)tau[l] * (Acc)Ck[l * nx + c];
+        for (int l = 0; l < nc; ++l) v += CT[l * nx + r] * Cs[l * nx + c];
       Qd[e] = v;
     }
     for (int e = t; e < nu * nu; e += blockDim.x) {
       const int r = e / nu, c = e - r * nu;
       Acc v = (Acc)a.Rbar[e];
       if (tau)
-        for (int l = 0; l < nc; ++l) v += (Acc)Dk[l * nu + r] * (Acc)tau[l] * (Acc)Dk[l * nu + c];
+        for (int l = 0; l < nc; ++l) v += DT[l * nu + r] * Ds[l * nu + c];
       Rd[e] = v;
     }
     for (int e = t; e < nu * nx; e += blockDim.x) {
       const int r = e / nx, c = e - r * nx;
       Acc v = Acc(0);
       if (tau)
-        for (int l = 0; l < nc; ++l) v += (Acc)Dk[l * nu + r] * (Acc)tau[l] * (Acc)Ck[l * nx + c];
+        for (int l = 0; l < nc; ++l) v += DT[l * nu + r] * Cs[l * nx + c];
       Sd[e] = v;
     }
   } else {
@@ -126,7 +146,7 @@ __global__ void sls_build_kernel(SLSBuild a) {
       const int r = e / nx, c = e - r * nx;
       Acc v = (Acc)a.QbarN[e];
       if (tau)
-        for (int l = 0; l < nf; ++l) v += (Acc)a.CN[l * nx + r] * (Acc)tau[l] * (Acc)a.CN[l * nx + c];
+        for (int l = 0; l < nf; ++l) v += CT[l * nx + r] * Cs[l * nx + c];
       Qd[e] = v;
     }
   }
@@ -380,8 +400,15 @@ extern "C" int sls_solve(sls_handle* h, const double* A, const double* B, const 
     SLSBuild a = {A, B, Qbar, Rbar, QbarN, C, D, CN, tau, h->pA, h->pB, h->pQ, h->pR, h->pS,
                   nx, nu, N, nc, nf, std::max(nc, nf), h->per_j, h->nq};
     dim3 grid(N, h->nq);
-    if (h->esz == 8) sls_build_kernel<double><<<grid, 256, 0, st>>>(a);
-    else sls_build_kernel<float><<<grid, 256, 0, st>>>(a);
+    const int brows = std::max(nc, nf);
+    const size_t bsm = (size_t)(2 * brows * nx + 2 * nc * nu) * h->esz;
+    if (h->esz == 8) {
+      CUS(cudaFuncSetAttribute(sls_build_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+      sls_build_kernel<double><<<grid, 256, bsm, st>>>(a);
+    } else {
+      CUS(cudaFuncSetAttribute(sls_build_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+      sls_build_kernel<float><<<grid, 256, bsm, st>>>(a);
+    }
     CUS(cudaGetLastError());
     int s2 = qp_update(h->qh, h->pA, h->pB, nullptr, h->pQ, h->pR, h->pS, nullptr, nullptr, nullptr, nullptr, nullptr,
                        nullptr, nullptr);
