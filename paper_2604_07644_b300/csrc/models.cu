@@ -29,7 +29,7 @@ using namespace gsls;
 #define CUM2(x)                                                                                     \
   do {                                                                                              \
     cudaError_t e_ = (x);                                                                           \
-    if (e_ != cudaSuccess) return set_error(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    if (e_ != cudaSuccess) return (void)cudaGetLastError(), set_error(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
 namespace {

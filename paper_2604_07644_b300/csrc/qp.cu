@@ -85,10 +85,15 @@ static int fail(int code, const std::string& msg) {
   return code;
 }
 int gsls::set_error(int code, const std::string& msg) { return fail(code, msg); }
+// On a failing runtime call the error is also cleared (cudaGetLastError), so
+// that it is not reported again by a later, unrelated call.
 #define CU(x)                                                                                \
   do {                                                                                       \
     cudaError_t e_ = (x);                                                                    \
-    if (e_ != cudaSuccess) return fail(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    if (e_ != cudaSuccess) {                                                                 \
+      (void)cudaGetLastError();                                                              \
+      return fail(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));         \
+    }                                                                                        \
   } while (0)
 
 static size_t al64(size_t x) { return (x + 63) & ~(size_t)63; }
@@ -202,13 +207,27 @@ static int run_pack(qp_handle* h, const std::vector<PackJob>& jobs) {
   return GPUSLS_OK;
 }
 
+// Dynamic shared memory a CTA of the solve kernel may request: the device's
+// opt-in maximum per block less the kernel's static shared memory.
+static int smem_limit(int esz) {
+  int dev = 0, optin = 227 * 1024;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa = {};
+  const cudaError_t e = esz == 8 ? cudaFuncGetAttributes(&fa, qp_kernel_entry<double>())
+                                 : cudaFuncGetAttributes(&fa, qp_kernel_entry<float>());
+  (void)cudaGetLastError();
+  const int stat = e == cudaSuccess ? (int)fa.sharedSizeBytes : 4096;
+  return std::min(optin, 227 * 1024) - stat;
+}
+
 // Per-QP launch-shape plan for cluster size cs: chunk length and count, ring
 // slot, factorization schedule (blocked unless asked for the tree, in TF32,
 // or its buffers do not fit), ring depth, and the shared memory per CTA.
 struct ShapePlan {
   int Lc, nch, slot, fact, depth, smem, vg, vbytes;
 };
-static ShapePlan plan_shape(const qp_dims& d, int cs, int esz, const qp_settings* s) {
+static ShapePlan plan_shape(const qp_dims& d, int cs, int esz, const qp_settings* s, int lim) {
   ShapePlan p;
   const int ldx = rup4(d.nx), ldu = rup4(d.nu), ldc = rup4(std::max(1, d.nc));
   const int ldv = rup4(d.nx + d.nc), ldf = rup4(d.nx + d.nu);
@@ -224,10 +243,10 @@ static ShapePlan plan_shape(const qp_dims& d, int cs, int esz, const qp_settings
   };
   // long horizons: when even the smallest layout (tree, ring depth 2) cannot
   // hold the per-chunk vectors, they move to a per-CTA global region
-  if (lay_total(2, 1) > 227 * 1024) p.vg = 1;
+  if (lay_total(2, 1) > lim) p.vg = 1;
   p.fact = (s->factorization == 1 || s->precision == GPUSLS_TF32 || d.nu > FACT_MAX_NU) ? 1 : 0;
-  if (p.fact == 0 && lay_total(1, 0) > 227 * 1024) p.fact = 1;
-  p.depth = lay_total(3, p.fact) > 227 * 1024 ? 2 : 3;
+  if (p.fact == 0 && lay_total(1, 0) > lim) p.fact = 1;
+  p.depth = lay_total(3, p.fact) > lim ? 2 : 3;
   p.smem = lay_total(p.depth, p.fact);
   p.vbytes = smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, ldx, ldu, ldv, ldf, p.depth, p.slot, esz, p.fact, p.vg)
                  .vbytes;
@@ -292,6 +311,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
 
   // workspace sizes
   const int esz = h->esz;
+  const int lim = smem_limit(esz);
   std::vector<size_t> toff(batch), doff(batch);
   size_t tsz = 0, dsz = 0;
   int smem = 0;
@@ -328,7 +348,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     int bws, fws, cds;
     bundle_sizes(d.nx, d.nu, d.nc, (int)ldx, (int)ldu, ldv, ldf, &bws, &fws, &cds);
     z.BW = al64(N * (size_t)bws); z.FW = al64(N * (size_t)fws); z.CD = al64(N * (size_t)cds + 1);
-    plans[b] = plan_shape(d, cs, esz, s);
+    plans[b] = plan_shape(d, cs, esz, s, lim);
     z.vec = plans[b].vg ? al64((size_t)cs * plans[b].vbytes / esz) : 0;
     toff[b] = tsz;
     tsz += z.A + z.B + z.b + z.Q + z.R + z.S + z.q + z.r + z.C + z.D + z.CN + z.lo + z.hi + z.x0 + z.Rhi + z.Sh +
@@ -355,9 +375,11 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     smem = std::max(smem, sp.smem);
   }
   h->smem = smem;
-  if (smem > 227 * 1024) {
+  if (smem > lim) {
     delete h;
-    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: shared memory per CTA exceeds 227 KB (raise cluster or lower N)");
+    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: shared memory per CTA (" + std::to_string(smem) +
+                                        " B) exceeds the device's " + std::to_string(lim) +
+                                        " B for this kernel (smaller nx, nc or nf)");
   }
   // FP64 copies of the caller's arrays live in dpool after the per-QP scratch
   const size_t d_copy = tot.A + tot.B + tot.c + tot.Q + tot.R + tot.S + tot.q + tot.r + tot.C + tot.D + tot.CN +

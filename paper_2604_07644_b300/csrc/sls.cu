@@ -32,7 +32,7 @@ using namespace gsls;
 #define CUS(x)                                                                                      \
   do {                                                                                              \
     cudaError_t e_ = (x);                                                                           \
-    if (e_ != cudaSuccess) return set_error(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    if (e_ != cudaSuccess) return (void)cudaGetLastError(), set_error(GPUSLS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
 struct sls_handle {
