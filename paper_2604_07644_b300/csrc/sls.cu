@@ -11,7 +11,7 @@
 //      case of eq. combination_rules) and the gains K_k^(j) (eq. backward_prop)
 //      run as one batched launch of the QP factorization kernel, one cluster
 //      per problem.
-//   3. sls_phi_kernel, one CTA per j, propagates Phi_x_{k+1,j} =
+//   3. sls_phi_kernel, one CTA per (j, column block), propagates Phi_x_{k+1,j} =
 //      (A_k + B_k K_k^(j)) Phi_x_{k,j} from Phi_x_{j+1,j} = E_j and
 //      Phi_u_{k,j} = K_k^(j) Phi_x_{k,j} (eq. forward_prop), and the row norms
 //      of C_k Phi_x_{k,j} + D_k Phi_u_{k,j}; sls_margin_kernel sums them over j
@@ -48,7 +48,8 @@ struct sls_handle {
   size_t nA = 0, nB = 0, nQ = 0, nR = 0, nS = 0;
   // solve-precision copies of E, C, D, CN (padded) and per-j scratch
   void *ET = nullptr, *CT = nullptr, *DT = nullptr, *CNT = nullptr, *scr = nullptr;
-  double *rn = nullptr, *rnf = nullptr;   // row norms [N][N][nc], [N][nf]
+  double *rn = nullptr, *rnf = nullptr;   // partial row sums of squares [N][N][nblk][nc], [N][nblk][nf]
+  int nblk = 1;                           // column blocks of Phi_{.,j} propagated by separate CTAs
   int ldx = 0, ldu = 0;
   int solved = 0;                         // rn / rnf hold the last sls_solve
   // FastSLS alternation (per-j handles): working tau [N+1][N][max(nc, nf)],
@@ -169,19 +170,28 @@ struct SLSPhi {
   const void *ET, *CT, *DT, *CNT;
   void* scr;
   double *Phix, *Phiu, *rn, *rnf;
-  int nx, nu, N, nc, nf, ldx, ldu, per_j;
+  int nx, nu, N, nc, nf, ldx, ldu, per_j, nblk;
 };
 
+// One CTA per (disturbance index j, column block cb): the columns
+// [c0, c1) of Phi_{.,j} evolve independently (Phi_x_{k+1,j} = Abar_k^(j)
+// Phi_x_{k,j} acts on each column), so a block propagates them alone and
+// leaves, per constraint row, its partial sum of squares of
+// C_k Phi_x_{k,j} + D_k Phi_u_{k,j} (the block's columns) for the margins
+// and duals to add up.
 template <typename T>
 __global__ void __launch_bounds__(NT, 1) sls_phi_kernel(SLSPhi a) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* gm = reinterpret_cast<T*>(smem);
-  const int j = blockIdx.x;
+  const int j = blockIdx.x, cb = blockIdx.y, nblk = a.nblk;
   const int nx = a.nx, nu = a.nu, N = a.N, nc = a.nc, nf = a.nf, ldx = a.ldx, ldu = a.ldu;
+  const int bw = (nx + nblk - 1) / nblk, c0 = cb * bw, w = min(nx, c0 + bw) - c0;
+  if (w <= 0) return;
   const int msz = nx * ldx;
   const int NX = N * nx;
-  const int t = threadIdx.x, w = t >> 5, l = t & 31;
-  T* X0 = reinterpret_cast<T*>(a.scr) + (size_t)j * (2 * msz + (nc > nf ? nc : nf) * ldx + nu * ldx + 16);
+  const int t = threadIdx.x, wp = t >> 5, l = t & 31;
+  T* X0 = reinterpret_cast<T*>(a.scr) +
+          ((size_t)j * nblk + cb) * (2 * msz + (nc > nf ? nc : nf) * ldx + nu * ldx + 16);
   T* X1 = X0 + msz;
   T* Xu = X1 + msz;
   T* M = Xu + nu * ldx;
@@ -189,29 +199,29 @@ __global__ void __launch_bounds__(NT, 1) sls_phi_kernel(SLSPhi a) {
   const T* CT = reinterpret_cast<const T*>(a.CT);
   const T* DT = reinterpret_cast<const T*>(a.DT);
   const T* CNT = reinterpret_cast<const T*>(a.CNT);
-  // Phi_x_{j+1,j} = E_j
-  cta_copy<T>(nx, nx, ET + (size_t)j * msz, ldx, false, X0, ldx);
+  // Phi_x_{j+1,j} = E_j (columns c0 .. c0 + w)
+  cta_copy<T>(nx, w, ET + (size_t)j * msz + c0, ldx, false, X0, ldx);
   const int q = a.per_j ? j : 0;
   const int first = a.per_j ? j + 1 : 1;
   const QPDesc* dq = (j + 1 < N || !a.per_j) ? &a.descs[q] : nullptr;
   T* cur = X0;
   T* nxt = X1;
   for (int k = j + 1; k <= N; ++k) {
-    // write Phi_x_{k,j} (block row k-1, block column j)
+    // write Phi_x_{k,j} (block row k-1, block column j, columns c0 ..)
     if (a.Phix)
-      for (int e = t; e < nx * nx; e += NT) {
-        const int r = e / nx, c = e - r * nx;
-        a.Phix[(size_t)((k - 1) * nx + r) * NX + (size_t)j * nx + c] = (double)cur[r * ldx + c];
+      for (int e = t; e < nx * w; e += NT) {
+        const int r = e / w, c = e - r * w;
+        a.Phix[(size_t)((k - 1) * nx + r) * NX + (size_t)j * nx + c0 + c] = (double)cur[r * ldx + c];
       }
     if (k == N) {
       // terminal margin rows: C_N Phi_x_{N,j}
       if (nf > 0) {
-        cta_gemm<T>(nf, nx, nx, T(1), CNT, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, M, ldx, gm);
-        for (int r = w; r < nf; r += NT / 32) {
+        cta_gemm<T>(nf, w, nx, T(1), CNT, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, M, ldx, gm);
+        for (int r = wp; r < nf; r += NT / 32) {
           T s2 = T(0);
-          for (int c = l; c < nx; c += 32) s2 += M[r * ldx + c] * M[r * ldx + c];
+          for (int c = l; c < w; c += 32) s2 += M[r * ldx + c] * M[r * ldx + c];
           s2 = warp_sum(s2);
-          if (l == 0) a.rnf[(size_t)j * nf + r] = sqrt((double)s2);
+          if (l == 0) a.rnf[((size_t)j * nblk + cb) * nf + r] = (double)s2;
         }
         __syncthreads();
       }
@@ -221,59 +231,70 @@ __global__ void __launch_bounds__(NT, 1) sls_phi_kernel(SLSPhi a) {
     const T* Kk = reinterpret_cast<const T*>(dq->K) + (size_t)i * nu * ldx;
     const T* Ab = reinterpret_cast<const T*>(dq->Abar) + (size_t)i * msz;
     // Phi_u_{k,j} = K_k^(j) Phi_x_{k,j}
-    cta_gemm<T>(nu, nx, nx, T(1), Kk, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, Xu, ldx, gm);
+    cta_gemm<T>(nu, w, nx, T(1), Kk, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, Xu, ldx, gm);
     if (a.Phiu)
-      for (int e = t; e < nu * nx; e += NT) {
-        const int r = e / nx, c = e - r * nx;
-        a.Phiu[(size_t)(k * nu + r) * NX + (size_t)j * nx + c] = (double)Xu[r * ldx + c];
+      for (int e = t; e < nu * w; e += NT) {
+        const int r = e / w, c = e - r * w;
+        a.Phiu[(size_t)(k * nu + r) * NX + (size_t)j * nx + c0 + c] = (double)Xu[r * ldx + c];
       }
     // margin rows: C_k Phi_x + D_k Phi_u
     if (nc > 0) {
-      cta_gemm<T>(nc, nx, nx, T(1), CT + (size_t)k * nc * ldx, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, M,
+      cta_gemm<T>(nc, w, nx, T(1), CT + (size_t)k * nc * ldx, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, M,
                   ldx, gm);
-      cta_gemm<T>(nc, nx, nu, T(1), DT + (size_t)k * nc * ldu, ldu, false, Xu, ldx, false, T(1), M, ldx, false, M, ldx,
+      cta_gemm<T>(nc, w, nu, T(1), DT + (size_t)k * nc * ldu, ldu, false, Xu, ldx, false, T(1), M, ldx, false, M, ldx,
                   gm);
-      for (int r = w; r < nc; r += NT / 32) {
+      for (int r = wp; r < nc; r += NT / 32) {
         T s2 = T(0);
-        for (int c = l; c < nx; c += 32) s2 += M[r * ldx + c] * M[r * ldx + c];
+        for (int c = l; c < w; c += 32) s2 += M[r * ldx + c] * M[r * ldx + c];
         s2 = warp_sum(s2);
-        if (l == 0) a.rn[((size_t)k * N + j) * nc + r] = sqrt((double)s2);
+        if (l == 0) a.rn[(((size_t)k * N + j) * nblk + cb) * nc + r] = (double)s2;
       }
       __syncthreads();
     }
     // Phi_x_{k+1,j} = (A_k + B_k K_k^(j)) Phi_x_{k,j}
-    cta_gemm<T>(nx, nx, nx, T(1), Ab, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, nxt, ldx, gm);
+    cta_gemm<T>(nx, w, nx, T(1), Ab, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, nxt, ldx, gm);
     T* tmp = cur;
     cur = nxt;
     nxt = tmp;
   }
 }
 
-// h_k[c] = sum_{j<k} rn[k][j][c] (j ascending), h^f[c] = sum_j rnf[j][c].
+// h_k[c] = sum_{j<k} sqrt(sum_cb rn[k][j][cb][c]) (j ascending),
+// h^f[c] = sum_j sqrt(sum_cb rnf[j][cb][c]): the row norms of the column
+// blocks' partial sums of squares, summed over j in a fixed order.
 __global__ void sls_margin_kernel(const double* __restrict__ rn, const double* __restrict__ rnf, double* h, double* hf,
-                                  int N, int nc, int nf) {
+                                  int N, int nc, int nf, int nblk) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < N * nc) {
     const int k = e / nc, c = e - k * nc;
     double s = 0.0;
-    for (int j = 0; j < k; ++j) s += rn[((size_t)k * N + j) * nc + c];
+    for (int j = 0; j < k; ++j) {
+      double q = 0.0;
+      for (int b = 0; b < nblk; ++b) q += rn[(((size_t)k * N + j) * nblk + b) * nc + c];
+      s += sqrt(q);
+    }
     if (h) h[e] = s;
   } else if (e < N * nc + nf) {
     const int c = e - N * nc;
     double s = 0.0;
-    for (int j = 0; j < N; ++j) s += rnf[(size_t)j * nf + c];
+    for (int j = 0; j < N; ++j) {
+      double q = 0.0;
+      for (int b = 0; b < nblk; ++b) q += rnf[((size_t)j * nblk + b) * nf + c];
+      s += sqrt(q);
+    }
     if (hf) hf[c] = s;
   }
 }
 
 // FastSLS duals (App. B): tau_{k,j}[c] = |lam_{k,c}| / sqrt(beta_{k,j}[c] + eps)
 // with beta the squared row norms of C_k Phi_x_{k,j} + D_k Phi_u_{k,j} (stage
-// k < N) or C_N Phi_x_{N,j} (k = N) that the last solve left in rn / rnf;
+// k < N) or C_N Phi_x_{N,j} (k = N): the sum of the column blocks' partial
+// sums of squares that the last solve left in rn / rnf;
 // zero for k <= j (Phi_{k,j} = 0 there) and beyond a stage's rows.  |lam|:
 // a two-sided row is two one-sided rows of the same norm, at most one active.
 __global__ void sls_tau_kernel(const double* __restrict__ rn, const double* __restrict__ rnf,
                                const double* __restrict__ lam, double eps, double* __restrict__ tau, int N, int nc,
-                               int nf, int w) {
+                               int nf, int w, int nblk) {
   const size_t total = (size_t)(N + 1) * N * w;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e / ((size_t)N * w));
@@ -282,11 +303,13 @@ __global__ void sls_tau_kernel(const double* __restrict__ rn, const double* __re
     double v = 0.0;
     if (j < k) {
       if (k < N && c < nc) {
-        const double r = rn[((size_t)k * N + j) * nc + c];
-        v = fabs(lam[(size_t)k * nc + c]) / sqrt(r * r + eps);
+        double beta = 0.0;
+        for (int b = 0; b < nblk; ++b) beta += rn[(((size_t)k * N + j) * nblk + b) * nc + c];
+        v = fabs(lam[(size_t)k * nc + c]) / sqrt(beta + eps);
       } else if (k == N && c < nf) {
-        const double r = rnf[(size_t)j * nf + c];
-        v = fabs(lam[(size_t)N * nc + c]) / sqrt(r * r + eps);
+        double beta = 0.0;
+        for (int b = 0; b < nblk; ++b) beta += rnf[((size_t)j * nblk + b) * nf + c];
+        v = fabs(lam[(size_t)N * nc + c]) / sqrt(beta + eps);
       }
     }
     tau[e] = v;
@@ -323,6 +346,9 @@ extern "C" int sls_setup(sls_handle** out, qp_dims d, int32_t precision, int32_t
   h->stream = (cudaStream_t)stream;
   h->ldx = rup4(d.nx);
   h->ldu = rup4(d.nu);
+  // column blocks of about 16 columns (at most 5): more CTAs per disturbance
+  // index and shorter products along each CTA's chain over k
+  h->nblk = std::max(1, std::min(5, (d.nx + 15) / 16));
   const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf;
   h->nq = N >= 2 ? (h->per_j ? N - 1 : 1) : 0;
   std::vector<qp_dims> dims;
@@ -346,10 +372,11 @@ extern "C" int sls_setup(sls_handle** out, qp_dims d, int32_t precision, int32_t
   e = (cudaError_t)(e | cudaMalloc(&h->CT, (size_t)N * std::max(nc, 1) * h->ldx * esz + 256));
   e = (cudaError_t)(e | cudaMalloc(&h->DT, (size_t)N * std::max(nc, 1) * h->ldu * esz + 256));
   e = (cudaError_t)(e | cudaMalloc(&h->CNT, (size_t)std::max(nf, 1) * h->ldx * esz + 256));
-  e = (cudaError_t)(e | cudaMalloc(&h->scr, (size_t)N * (2 * nx * h->ldx + std::max(nc, nf) * h->ldx + nu * h->ldx + 16) *
+  e = (cudaError_t)(e | cudaMalloc(&h->scr, (size_t)N * h->nblk *
+                                                   (2 * nx * h->ldx + std::max(nc, nf) * h->ldx + nu * h->ldx + 16) *
                                                    esz + 256));
-  e = (cudaError_t)(e | alloc(&h->rn, (size_t)N * N * std::max(nc, 1)));
-  e = (cudaError_t)(e | alloc(&h->rnf, (size_t)N * std::max(nf, 1)));
+  e = (cudaError_t)(e | alloc(&h->rn, (size_t)N * N * h->nblk * std::max(nc, 1)));
+  e = (cudaError_t)(e | alloc(&h->rnf, (size_t)N * h->nblk * std::max(nf, 1)));
   if (h->per_j) {
     e = (cudaError_t)(e | alloc(&h->tau, (size_t)(N + 1) * N * std::max(std::max(nc, nf), 1)));
     e = (cudaError_t)(e | alloc(&h->lo_t, (size_t)N * nc + nf));
@@ -433,19 +460,20 @@ extern "C" int sls_solve(sls_handle* h, const double* A, const double* B, const 
   CUS(cudaGetLastError());
   // 3. Phi and margin row norms, one CTA per disturbance index j
   SLSPhi p = {h->qh ? h->qh->ddesc : nullptr, h->ET, h->CT, h->DT, h->CNT, h->scr, Phi_x, Phi_u, h->rn, h->rnf,
-              nx, nu, N, nc, nf, ldx, ldu, h->per_j};
+              nx, nu, N, nc, nf, ldx, ldu, h->per_j, h->nblk};
+  const dim3 pgrid(N, h->nblk);
   const int smem = 2 * KT * TILE * h->esz;
   if (h->esz == 8) {
     CUS(cudaFuncSetAttribute(sls_phi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    sls_phi_kernel<double><<<N, NT, smem, st>>>(p);
+    sls_phi_kernel<double><<<pgrid, NT, smem, st>>>(p);
   } else {
     CUS(cudaFuncSetAttribute(sls_phi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    sls_phi_kernel<float><<<N, NT, smem, st>>>(p);
+    sls_phi_kernel<float><<<pgrid, NT, smem, st>>>(p);
   }
   CUS(cudaGetLastError());
   const int tot = N * nc + nf;
   if (tot > 0) {
-    sls_margin_kernel<<<(tot + 255) / 256, 256, 0, st>>>(h->rn, h->rnf, hk, hf, N, nc, nf);
+    sls_margin_kernel<<<(tot + 255) / 256, 256, 0, st>>>(h->rn, h->rnf, hk, hf, N, nc, nf, h->nblk);
     CUS(cudaGetLastError());
   }
   CUS(cudaStreamSynchronize(st));
@@ -461,7 +489,7 @@ extern "C" int sls_tau(sls_handle* h, const double* lam, double eps, double* tau
   const int w = std::max(std::max(d.nc, d.nf), 1);
   const size_t total = (size_t)(d.N + 1) * d.N * w;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
-  sls_tau_kernel<<<blocks, 256, 0, h->stream>>>(h->rn, h->rnf, lam, eps, tau, d.N, d.nc, d.nf, w);
+  sls_tau_kernel<<<blocks, 256, 0, h->stream>>>(h->rn, h->rnf, lam, eps, tau, d.N, d.nc, d.nf, w, h->nblk);
   CUS(cudaGetLastError());
   CUS(cudaStreamSynchronize(h->stream));
   return GPUSLS_OK;
