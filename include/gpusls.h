@@ -231,6 +231,12 @@ typedef struct sls_handle sls_handle;
  * precision: GPUSLS_FP64 or GPUSLS_FP32.  Allocates all device memory. */
 int sls_setup(sls_handle** h, qp_dims d, int32_t precision, int32_t per_j_tau, void* stream);
 
+/* sls_setup_ex: as sls_setup, with the launch shape of the controller
+ * problems' factorization taken from inner (cluster: CTAs per problem, 0 =
+ * by horizon; occupancy; factorization schedule); inner may be NULL. */
+int sls_setup_ex(sls_handle** h, qp_dims d, int32_t precision, int32_t per_j_tau, const qp_settings* inner,
+                 void* stream);
+
 /* sls_solve: the SLS controller QP (eq. fastsls_qp) by per-j reverse scans
  * (eq. robust_combin, eq. backward_prop) and forward propagation
  * (eq. forward_prop), plus the margins of Sec. III-D.

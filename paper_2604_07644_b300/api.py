@@ -277,14 +277,15 @@ class SLS:
     """SLS controller synthesis and reachability margins (sls_setup / sls_solve)."""
 
     def __init__(self, nx, nu, N, nc, nf, per_j_tau: bool, precision=native.GPUSLS_FP64, stream=None,
-                 device="cuda"):
+                 device="cuda", inner: native.qp_settings | None = None):
         self.lib = native.load()
         self.dims = (nx, nu, N, nc, nf)
         self.device = device
         d = native.qp_dims(nx, nu, N, nc, nf)
         h = C.c_void_p()
-        native.check(self.lib.sls_setup(C.byref(h), d, int(precision), int(bool(per_j_tau)), _stream_ptr(stream)),
-                     "sls_setup")
+        native.check(self.lib.sls_setup_ex(C.byref(h), d, int(precision), int(bool(per_j_tau)),
+                                           C.byref(inner) if inner is not None else None, _stream_ptr(stream)),
+                     "sls_setup_ex")
         self.h = h
 
     def solve(self, sp, fetch=True):

@@ -83,6 +83,7 @@ SIGNATURES = {
     "qp_riccati": (C.c_int, [P, DP, DP]),
     "qp_destroy": (None, [P]),
     "sls_setup": (C.c_int, [C.POINTER(P), qp_dims, C.c_int32, C.c_int32, P]),
+    "sls_setup_ex": (C.c_int, [C.POINTER(P), qp_dims, C.c_int32, C.c_int32, C.POINTER(qp_settings), P]),
     "sls_solve": (C.c_int, [P, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP, DP]),
     "sls_destroy": (None, [P]),
     "sls_tau": (C.c_int, [P, DP, C.c_double, DP]),
