@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 METRIC = "ms/QP solve to 1e-4 KKT residual (61D, N=100): learned+batched vs plain ADMM"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
-TRAFFIC_PER_QP_ITER = 5.82e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6)
+TRAFFIC_PER_QP_ITER = 5.51e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6, 49 QPs)
 
 
 def parse():
@@ -58,6 +58,7 @@ def parse():
                    help="launch QPs in index order instead of longest-expected-first")
     p.add_argument("--case", default="", choices=["", "iter", "refactor", "mlp", "sls"],
                    help="small fixed case for profiler captures (prints no bench line)")
+    p.add_argument("--case-batch", type=int, default=32, help="QPs of the iter / refactor profiling cases")
     p.add_argument("--model", default=os.path.join(ROOT, "paper_2604_07644_b300", "warmstart_quadruped61.npz"))
     return p.parse_args()
 
@@ -320,16 +321,19 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
     # pendulum-shaped QP, nx=30, nu=15, N=3000 (1.35e5 decision variables),
     # cold FP32 solve to the 1e-4 KKT tolerance, one QP per launch, cluster 8
     qpl = W.long_horizon(0)
-    sl = native.default_settings(precision=native.GPUSLS_FP32, cluster=8, eps_floor=1e-5, max_iter=20000)
-    with torch.cuda.stream(stream):
-        ql = QPBatch([qpl], sl, stream=stream, device=dev)
-        gl = ql.graph()
-        ms = _time_graph(gl, stream, steps)
-        il = gl.info()[0]
-    out["long_horizon_N3000"] = {"ms_per_qp": ms, "iters": il["iters"], "kkt": il["kkt"], "status": il["status"],
-                                 "variables": (qpl.N + 1) * qpl.nx + qpl.N * qpl.nu,
-                                 "workload": "pendulum-shaped LTV-QP nx=30 nu=15 N=3000, |u| <= 1, cold FP32"}
-    ql.close()
+    for tol, key in ((1e-4, "long_horizon_N3000"), (1e-2, "long_horizon_N3000_tol1e-2")):
+        # 1e-2: the residual tolerance of the paper's horizon study (Sec. V-A)
+        sl = native.default_settings(precision=native.GPUSLS_FP32, cluster=8, eps=tol, eps_kkt=tol,
+                                     eps_floor=min(1e-5, 0.1 * tol), max_iter=20000)
+        with torch.cuda.stream(stream):
+            ql = QPBatch([qpl], sl, stream=stream, device=dev)
+            gl = ql.graph()
+            ms = _time_graph(gl, stream, steps)
+            il = gl.info()[0]
+        out[key] = {"ms_per_qp": ms, "iters": il["iters"], "kkt": il["kkt"], "status": il["status"],
+                    "variables": (qpl.N + 1) * qpl.nx + qpl.N * qpl.nu, "kkt_tolerance": tol,
+                    "workload": "pendulum-shaped LTV-QP nx=30 nu=15 N=3000, |u| <= 1, cold FP32"}
+        ql.close()
     batch_run("humanoid75_cold", [W.humanoid_75d(s) for s in range(64)], 4)
 
     # SLS: model flops from the per-j scans (2 (N - j) combines of ~16.7 nx^3
@@ -489,7 +493,7 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
 def profile_case(args):
     """Small fixed workloads for ncu captures (inputs larger than L2, a few
     hundred MB on the device):
-      iter      32 quadruped-shaped QPs (FP32, cluster 6), factorized by a first launch;
+      iter      32 (--case-batch) quadruped-shaped QPs (FP32, cluster 6), factorized by a first launch;
                 launches 2 and 3 run 100 cached ADMM iterations each (no
                 refactor), so a capture of launch 2 is the iteration alone;
       refactor  the same batch, three launches that each refactor and run one
@@ -506,8 +510,9 @@ def profile_case(args):
     native.load()
     fam = W.family(0)
     if args.case in ("iter", "refactor"):
-        qps = [fam.instance(100000 + i) for i in range(32)]
-        # the launch shape the autotuner picks for the bench's batch (cluster 6)
+        qps = [fam.instance(100000 + i) for i in range(args.case_batch)]
+        # the launch shape the autotuner picks for the bench's batch (cluster 6);
+        # --case-batch 49 fills every SM's two CTA slots with 6-CTA clusters
         prec = {"fp32": native.GPUSLS_FP32, "fp64": native.GPUSLS_FP64, "mixed": native.GPUSLS_MIXED}[args.precision]
         s = native.default_settings(precision=prec, cluster=6, sigma=0, fixed_iters=1)
         if args.case == "iter":
@@ -524,6 +529,7 @@ def profile_case(args):
     elif args.case == "mlp":
         qps = [fam.instance(100000 + i) for i in range(256)]
         qb = QPBatch(qps, native.default_settings(precision=native.GPUSLS_FP32))
+        qb.set_x0([q.x0 for q in qps])
         mlp = learned.load(args.model, max_batch=256)
         heads = [(mlp, list(range(len(qps))), qps[0].N)]
         for _ in range(3):
@@ -780,7 +786,7 @@ def main():
     algo = algorithmic_bytes_per_iter(nx, nu, N, nc, esz) * float(np.sum(iters))
     achieved = algo / (ms_per_step * 1e-3) / 1e9
     # DRAM bytes per QP-iteration of qp_kernel<float> from the ncu capture of the
-    # iteration-only case (profiles/qp_kernel_iter_quadruped61_b32.md), scaled
+    # iteration-only case at full occupancy (profiles/qp_kernel_iter_quadruped61_b49.md), scaled
     # by this launch's QP-iterations; must be re-measured when the kernel changes
     traffic = TRAFFIC_PER_QP_ITER * float(np.sum(iters)) if esz == 4 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",

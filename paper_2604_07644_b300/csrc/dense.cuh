@@ -686,8 +686,10 @@ __device__ inline bool mterm_vec_ok(const MTerm<T>& p) {
 // (C[j][i]).  C0 (shared or global) is read before the products when the
 // registers allow, so its global-memory latency overlaps them.  Ends with a
 // CTA barrier.  Operands that are not 16-byte aligned take a scalar path.
-// tc (FP32 only, the GPUSLS_MIXED mode): products with k >= 8 run on the
-// tensor cores in three TF32 passes (sgemm_tc3).
+// tc (FP32 only, the GPUSLS_MIXED mode): products that give every warp a
+// unit (16 rows x 32 columns) and k >= 16 run on the tensor cores in three
+// TF32 passes (sgemm_tc3); narrower ones keep the FFMA path, where the
+// tensor path would leave warps waiting at the closing barrier.
 template <typename T>
 __device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> p2, T beta, const T* C0, int ldc0,
                                    bool addI, T* C, int ldc, bool tC, bool tc = false) {
@@ -696,7 +698,7 @@ __device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> 
     return;
   }
   if constexpr (sizeof(T) == 4) {
-    if (tc && p1.k >= 8 && (p2.k == 0 || p2.k >= 8)) {
+    if (tc && ((m + 15) >> 4) * ((n + 31) >> 5) >= NT / 32 && p1.k >= 16 && (p2.k == 0 || p2.k >= 16)) {
       sgemm_tc3(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
       return;
     }
