@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 METRIC = "ms/QP solve to 1e-4 KKT residual (61D, N=100): learned+batched vs plain ADMM"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
-TRAFFIC_PER_QP_ITER = 5.51e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6, 49 QPs)
+TRAFFIC_PER_QP_ITER = 5.99e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6, 45 QPs)
 
 
 def parse():
@@ -261,8 +261,10 @@ def _time_graph(g, stream, steps):
 def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
     """Timed on the same device after the headline: the batched serving mix
     (256 ragged QPs, nx in {12, 61, 75}, N in 16..128, cold FP32), 64
-    humanoid-shaped QPs (75D, N=40, cold FP32), the humanoid SLS solve (75D,
-    N=40) with per-j tau and with tau = 0, and checks of the headline's
+    humanoid-shaped QPs (75D, N=40, cold FP32), the plain 4D QP (FP64, 200
+    iterations) and 64 quadrotor-shaped QPs (12D, N=64; FP32 and FP64), the
+    humanoid SLS solve (75D, N=40) with per-j tau and with tau = 0, and
+    checks of the headline's
     solutions: the largest bound violation and the largest difference from
     the FP64 oracle on the CPU-baseline sample."""
     import torch
@@ -274,8 +276,8 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
     steps = max(1, args.steps)
     base = dict(precision=native.GPUSLS_FP32, cluster=8, max_refine=3, max_iter=6000, schedule=1)
 
-    def batch_run(name, qps_, cluster):
-        s = native.default_settings(**dict(base, cluster=cluster))
+    def batch_run(name, qps_, cluster, precision=native.GPUSLS_FP32):
+        s = native.default_settings(**dict(base, cluster=cluster, precision=precision))
         if not args.no_autotune:
             from paper_2604_07644_b300 import autotune
             s, _ = autotune.choose(qps_, s, expected_iters=300, tail_iters=1500, cache=autotune.Cache())
@@ -319,11 +321,12 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
 
     # long horizon (the horizon study of Sec. V-A): torque-limited
     # pendulum-shaped QP, nx=30, nu=15, N=3000 (1.35e5 decision variables),
-    # cold FP32 solve to the 1e-4 KKT tolerance, one QP per launch, cluster 8
+    # cold FP32 solve to the 1e-4 KKT tolerance, one QP per launch; the
+    # automatic launch shape (cluster = 0) takes 16-CTA clusters here
     qpl = W.long_horizon(0)
     for tol, key in ((1e-4, "long_horizon_N3000"), (1e-2, "long_horizon_N3000_tol1e-2")):
         # 1e-2: the residual tolerance of the paper's horizon study (Sec. V-A)
-        sl = native.default_settings(precision=native.GPUSLS_FP32, cluster=8, eps=tol, eps_kkt=tol,
+        sl = native.default_settings(precision=native.GPUSLS_FP32, cluster=0, eps=tol, eps_kkt=tol,
                                      eps_floor=min(1e-5, 0.1 * tol), max_iter=20000)
         with torch.cuda.stream(stream):
             ql = QPBatch([qpl], sl, stream=stream, device=dev)
@@ -332,9 +335,26 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
             il = gl.info()[0]
         out[key] = {"ms_per_qp": ms, "iters": il["iters"], "kkt": il["kkt"], "status": il["status"],
                     "variables": (qpl.N + 1) * qpl.nx + qpl.N * qpl.nu, "kkt_tolerance": tol,
+                    "cluster": "automatic (16 CTAs, non-portable cluster size)",
                     "workload": "pendulum-shaped LTV-QP nx=30 nu=15 N=3000, |u| <= 1, cold FP32"}
         ql.close()
     batch_run("humanoid75_cold", [W.humanoid_75d(s) for s in range(64)], 4)
+
+    # the two small configurations: the plain 4D QP (FP64, 200 iterations,
+    # one instance per launch) and 64 quadrotor-shaped QPs (12D, N=64) in
+    # FP32 and in FP64, cold, to the 1e-4 KKT tolerance
+    s4 = native.default_settings(precision=native.GPUSLS_FP64, fixed_iters=200)
+    with torch.cuda.stream(stream):
+        q4 = QPBatch([W.plain_4d(0)], s4, stream=stream, device=dev)
+        g4 = q4.graph()
+        ms = _time_graph(g4, stream, max(steps, 10))
+        i4 = g4.info()[0]
+    out["plain4d_fp64_200iter"] = {"ms_per_solve": ms, "iters": i4["iters"], "kkt": i4["kkt"],
+                                   "workload": "nx=4 nu=2 N=32, FP64, 200 ADMM iterations, one QP per launch"}
+    q4.close()
+    q12 = [W.quadrotor_12d(s) for s in range(64)]
+    batch_run("quadrotor12_b64", q12, 4)
+    batch_run("quadrotor12_b64_fp64", q12, 4, precision=native.GPUSLS_FP64)
 
     # SLS: model flops from the per-j scans (2 (N - j) combines of ~16.7 nx^3
     # each) and the forward products (2 nx^2 (nx + nu) per block)
@@ -512,7 +532,8 @@ def profile_case(args):
     if args.case in ("iter", "refactor"):
         qps = [fam.instance(100000 + i) for i in range(args.case_batch)]
         # the launch shape the autotuner picks for the bench's batch (cluster 6);
-        # --case-batch 49 fills every SM's two CTA slots with 6-CTA clusters
+        # --case-batch 45 is the most 6-CTA clusters the device holds at once
+        # (two CTAs on most SMs): one wave at the bench's occupancy
         prec = {"fp32": native.GPUSLS_FP32, "fp64": native.GPUSLS_FP64, "mixed": native.GPUSLS_MIXED}[args.precision]
         s = native.default_settings(precision=prec, cluster=6, sigma=0, fixed_iters=1)
         if args.case == "iter":
@@ -786,7 +807,7 @@ def main():
     algo = algorithmic_bytes_per_iter(nx, nu, N, nc, esz) * float(np.sum(iters))
     achieved = algo / (ms_per_step * 1e-3) / 1e9
     # DRAM bytes per QP-iteration of qp_kernel<float> from the ncu capture of the
-    # iteration-only case at full occupancy (profiles/qp_kernel_iter_quadruped61_b49.md), scaled
+    # iteration-only case at full occupancy (profiles/qp_kernel_iter_quadruped61_b45.md), scaled
     # by this launch's QP-iterations; must be re-measured when the kernel changes
     traffic = TRAFFIC_PER_QP_ITER * float(np.sum(iters)) if esz == 4 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",

@@ -77,7 +77,11 @@ typedef struct qp_settings {
   int32_t check_every;/* stop-test interval                                         */
   int32_t max_iter;
   int32_t precision;  /* GPUSLS_FP64, GPUSLS_FP32, GPUSLS_TF32 or GPUSLS_MIXED        */
-  int32_t cluster;    /* CTAs (thread blocks) per QP, 1..8; 0 picks by N            */
+  int32_t cluster;    /* CTAs (thread blocks) per QP, 1..16; 0 picks by N (at most
+                         8).  9..16 are non-portable cluster sizes: qp_setup /
+                         qp_batch_setup fail with GPUSLS_ERR_INVALID when the
+                         device cannot schedule one such cluster at the
+                         handle's shared memory per CTA                     */
   int32_t fixed_iters;/* > 0: run exactly this many iterations, no stop test        */
   int32_t max_refine; /* iterative-refinement rounds allowed at the eps floor (3)   */
   int32_t fallback_iters; /* > 0: a QP whose state came from a warm start

@@ -122,29 +122,57 @@ extern "C" const char* gpusls_last_error(void) { return g_err.c_str(); }
 
 static int auto_cluster(int N) {
   int cs = (N + 11) / 12;
-  return std::max(1, std::min(MAXCS, cs));
+  return std::max(1, std::min(MAXCS_PORTABLE, cs));
+}
+
+// Kernel attributes and launch configuration of a solve launch: one cluster
+// of h->cs CTAs per QP; cluster sizes above 8 need the non-portable attribute.
+template <typename T>
+static cudaError_t prepare_launch(qp_handle* h, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+  const void* kern = qp_kernel_entry<T>();
+  int smem = h->smem;
+  // occupancy 1: ask for more than half of the SM's shared memory, so that
+  // exactly one CTA of this kernel fits an SM
+  if (h->set.occupancy == 1) smem = std::max(smem, 116 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess && h->cs > MAXCS_PORTABLE)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  *cfg = {};
+  cfg->gridDim = dim3(h->batch * h->cs, 1, 1);
+  cfg->blockDim = dim3(NT, 1, 1);
+  cfg->dynamicSmemBytes = smem;
+  cfg->stream = h->stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = h->cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  return e;
+}
+
+// Clusters of this handle's launch shape the device can hold at once (0: the
+// shape cannot be scheduled, e.g. a non-portable cluster size the device does
+// not offer at this shared-memory size).
+template <typename T>
+static int max_active_clusters(qp_handle* h) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  int n = 0;
+  if (prepare_launch<T>(h, &cfg, attr) != cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&n, qp_kernel_entry<T>(), &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 template <typename T>
 static int launch_qp(qp_handle* h, const SolveArgs& a) {
   const QPKernelFn kern = reinterpret_cast<QPKernelFn>(const_cast<void*>(qp_kernel_entry<T>()));
-  int smem = h->smem;
-  // occupancy 1: ask for more than half of the SM's shared memory, so that
-  // exactly one CTA of this kernel fits an SM
-  if (h->set.occupancy == 1) smem = std::max(smem, 116 * 1024);
-  CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(h->batch * h->cs, 1, 1);
-  cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = h->stream;
+  cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = h->cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  CU(prepare_launch<T>(h, &cfg, attr));
   CU(cudaLaunchKernelEx(&cfg, kern, (const QPDesc*)h->ddesc, a));
   CU(cudaGetLastError());
   return GPUSLS_OK;
@@ -239,7 +267,8 @@ static ShapePlan plan_shape(const qp_dims& d, int cs, int esz, const qp_settings
   p.slot = std::max(std::max(std::max(bws, fws), msz), std::max(std::max(d.nx * ldu, d.nx * ldc), cds));
   p.vg = 0;
   auto lay_total = [&](int depth, int fact) {
-    return smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, ldx, ldu, ldv, ldf, depth, p.slot, esz, fact, p.vg).total;
+    return smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, cs, ldx, ldu, ldv, ldf, depth, p.slot, esz, fact, p.vg)
+        .total;
   };
   // long horizons: when even the smallest layout (tree, ring depth 2) cannot
   // hold the per-chunk vectors, they move to a per-CTA global region
@@ -248,8 +277,9 @@ static ShapePlan plan_shape(const qp_dims& d, int cs, int esz, const qp_settings
   if (p.fact == 0 && lay_total(1, 0) > lim) p.fact = 1;
   p.depth = lay_total(3, p.fact) > lim ? 2 : 3;
   p.smem = lay_total(p.depth, p.fact);
-  p.vbytes = smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, ldx, ldu, ldv, ldf, p.depth, p.slot, esz, p.fact, p.vg)
-                 .vbytes;
+  p.vbytes =
+      smem_layout(d.nx, d.nu, d.nc, d.nf, p.Lc, p.nch, cs, ldx, ldu, ldv, ldf, p.depth, p.slot, esz, p.fact, p.vg)
+          .vbytes;
   return p;
 }
 
@@ -267,7 +297,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32 && s->precision != GPUSLS_TF32 &&
       s->precision != GPUSLS_MIXED)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: unknown precision");
-  if (s->cluster < 0 || s->cluster > MAXCS) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: cluster must be 0..8");
+  if (s->cluster < 0 || s->cluster > MAXCS) return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: cluster must be 0..16");
   if (s->occupancy < 0 || s->occupancy > 1 || s->schedule < 0 || s->schedule > 1 || s->factorization < 0 ||
       s->factorization > 1)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: occupancy, schedule and factorization must be 0 or 1");
@@ -312,6 +342,23 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
   // workspace sizes
   const int esz = h->esz;
   const int lim = smem_limit(esz);
+  // automatic launch shape for long horizons: when the per-chunk vectors of
+  // 8-CTA clusters need the global-memory region, clusters of 16 CTAs (a
+  // non-portable size) halve the chunk chains, if the device schedules them
+  if (s->cluster == 0 && cs == MAXCS_PORTABLE) {
+    bool vg8 = false;
+    int smem16 = 0;
+    for (int b = 0; b < batch; ++b) {
+      vg8 = vg8 || plan_shape(dims[b], cs, esz, s, lim).vg != 0;
+      smem16 = std::max(smem16, plan_shape(dims[b], MAXCS, esz, s, lim).smem);
+    }
+    if (vg8 && smem16 <= lim) {
+      h->cs = MAXCS;
+      h->smem = smem16;
+      if ((esz == 8 ? max_active_clusters<double>(h) : max_active_clusters<float>(h)) >= 1) cs = MAXCS;
+      h->cs = cs;
+    }
+  }
   std::vector<size_t> toff(batch), doff(batch);
   size_t tsz = 0, dsz = 0;
   int smem = 0;
@@ -338,17 +385,18 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     z.C = al64(N * nc * ldx + 1); z.D = al64(N * nc * ldu + 1); z.CN = al64(nf * ldx + 1); z.lo = al64(m + 1);
     z.hi = al64(m + 1); z.x0 = al64(ldx); z.Rhi = al64(N * nu * ldu); z.Sh = al64(N * nu * ldx);
     z.Rh = al64(N * nu * ldu); z.S0 = al64(N * nu * ldx);
-    z.V = al64(nodes * msz); z.scr = al64((size_t)MAXCS * 6 * msz); z.Abar = al64(N * msz);
+    plans[b] = plan_shape(d, cs, esz, s, lim);
+    const size_t nch = plans[b].nch;
+    z.V = al64(nodes * msz); z.scr = al64((size_t)cs * 6 * msz); z.Abar = al64(N * msz);
     z.CK = al64(N * nc * ldx + 1); z.F = al64(N * nu * ldx); z.FPi = al64(N * nx * ldu); z.J = al64(N * nu * ldc);
     z.K = al64(N * nu * ldx); z.KSig = al64(N * nu * ldx); z.CKSig = al64(N * nx * ldc + 1); z.Sig = al64(N * msz);
     z.c0 = al64(N * ldx); z.k0 = al64(N * ldu); z.CNSig = al64(nf * ldx + 1); z.SigN = al64(msz);
-    z.Tch = al64(MAXCS * msz); z.Uch = al64(MAXCS * msz); z.Theta = al64(MAXCS * MAXCS * msz);
-    z.Xi = al64(MAXCS * MAXCS * msz); z.Gam = al64(N * nu * ldu); z.z = al64(m + 1); z.y = al64(m + 1);
+    z.Tch = al64(cs * msz); z.Uch = al64(cs * msz); z.Theta = al64(nch * nch * msz);
+    z.Xi = al64(nch * nch * msz); z.Gam = al64(N * nu * ldu); z.z = al64(m + 1); z.y = al64(m + 1);
     const int ldv = rup4(d.nx + d.nc), ldf = rup4(d.nx + d.nu);
     int bws, fws, cds;
     bundle_sizes(d.nx, d.nu, d.nc, (int)ldx, (int)ldu, ldv, ldf, &bws, &fws, &cds);
     z.BW = al64(N * (size_t)bws); z.FW = al64(N * (size_t)fws); z.CD = al64(N * (size_t)cds + 1);
-    plans[b] = plan_shape(d, cs, esz, s, lim);
     z.vec = plans[b].vg ? al64((size_t)cs * plans[b].vbytes / esz) : 0;
     toff[b] = tsz;
     tsz += z.A + z.B + z.b + z.Q + z.R + z.S + z.q + z.r + z.C + z.D + z.CN + z.lo + z.hi + z.x0 + z.Rhi + z.Sh +
@@ -380,6 +428,11 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: shared memory per CTA (" + std::to_string(smem) +
                                         " B) exceeds the device's " + std::to_string(lim) +
                                         " B for this kernel (smaller nx, nc or nf)");
+  }
+  if (cs > MAXCS_PORTABLE && (esz == 8 ? max_active_clusters<double>(h) : max_active_clusters<float>(h)) < 1) {
+    delete h;
+    return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: the device cannot schedule clusters of " + std::to_string(cs) +
+                                        " CTAs with " + std::to_string(smem) + " B of shared memory each");
   }
   // FP64 copies of the caller's arrays live in dpool after the per-QP scratch
   const size_t d_copy = tot.A + tot.B + tot.c + tot.Q + tot.R + tot.S + tot.q + tot.r + tot.C + tot.D + tot.CN +
@@ -657,10 +710,9 @@ static int graph_create(qp_graph** out, qp_graph* g, qp_handle* h, Warm warm, co
     return bail(GPUSLS_ERR_CUDA, "qp_graph_create: cudaStreamCreate failed");
   // the kernel attributes are set before capture
   {
-    const int smem = h->set.occupancy == 1 ? std::max(h->smem, 116 * 1024) : h->smem;
-    const cudaError_t e = h->esz == 8
-        ? cudaFuncSetAttribute(qp_kernel_entry<double>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-        : cudaFuncSetAttribute(qp_kernel_entry<float>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    const cudaError_t e = h->esz == 8 ? prepare_launch<double>(h, &cfg, attr) : prepare_launch<float>(h, &cfg, attr);
     if (e != cudaSuccess) return bail(GPUSLS_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
   }
   const cudaStream_t saved = h->stream;

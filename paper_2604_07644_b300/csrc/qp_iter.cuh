@@ -239,14 +239,14 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
   const int ldc = d.ldc, per_ck = nx * ldc, gs_ck = c.gs_ck, nr_ck = c.nr_ck;
   T lo_a = T(0), hi_a = T(0), lo_b = T(0), hi_b = T(0);   // bounds of the first two own rows (P5)
   auto p3_src = [&](int r) -> const T* {
-    return r < nr_th ? Theta + (size_t)(c.rank * MAXCS + m0 + r * cap_bk) * msz
+    return r < nr_th ? Theta + (size_t)(c.rank * d.nch + m0 + r * cap_bk) * msz
                      : FPi + (size_t)(s + (r - nr_th) * gs_fp) * per_fp;
   };
   auto p3_len = [&](int r) -> int {
     return r < nr_th ? min(cap_bk, nb_th - r * cap_bk) * msz : min(gs_fp, L - (r - nr_th) * gs_fp) * per_fp;
   };
   auto p5_src = [&](int r) -> const T* {
-    return r < nr_xi ? Xi + (size_t)(c.rank * MAXCS + r * cap_bk) * msz
+    return r < nr_xi ? Xi + (size_t)(c.rank * d.nch + r * cap_bk) * msz
                      : CKSig + (size_t)(s + (r - nr_xi) * gs_ck) * per_ck;
   };
   auto p5_len = [&](int r) -> int {

@@ -24,7 +24,11 @@ namespace cg = cooperative_groups;
 
 namespace gsls {
 
-constexpr int MAXCS = 8;
+// CTAs per QP: up to 8 is the portable cluster size; 9..16 are non-portable
+// cluster sizes (long horizons, whose per-chunk vectors then fit shared
+// memory), launched only where the device schedules them.
+constexpr int MAXCS = 16;
+constexpr int MAXCS_PORTABLE = 8;
 
 // Per-QP descriptor: dimensions and device pointers into the handle's pools.
 // Pointers typed void* are in the solve precision T (padded layouts, leading
@@ -102,8 +106,6 @@ __host__ __device__ inline void bundle_sizes(int nx, int nu, int nc, int ldx, in
   *cd = nc * ldf;
 }
 
-constexpr int MAXCS_SMEM = 8;
-
 // Shared-memory carve-up (byte offsets, 16-byte aligned).
 struct SmemLayout {
   int ring, gemm, gj, gjbuf;                 // union region
@@ -167,8 +169,8 @@ constexpr int FACT_MAX_NU = 32;
 // whose size grows with the chunk length, live in a per-CTA region of global
 // memory (offsets relative to its base, vbytes long) instead of shared
 // memory; the kernel reaches them through the same generic pointers.
-__host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf, int Lc, int nch, int ldx, int ldu,
-                                                  int ldv, int ldf, int depth, int slot, int esz, int fact,
+__host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf, int Lc, int nch, int cs, int ldx,
+                                                  int ldu, int ldv, int ldf, int depth, int slot, int esz, int fact,
                                                   int vg = 0) {
   SmemLayout s;
   int off = 0;
@@ -203,7 +205,7 @@ __host__ __device__ inline SmemLayout smem_layout(int nx, int nu, int nc, int nf
   s.tmp2 = off; off = al16(off + TILE * esz);
   s.tmp3 = off; off = al16(off + TILE * esz);
   s.red = off; off = al16(off + NT * esz);
-  s.part = off; off = al16(off + (16 + MAXCS_SMEM * 8) * 8);
+  s.part = off; off = al16(off + (16 + cs * 8) * 8);   // cluster_max slots and its [cs][8] gather
   s.perm = off; off = al16(off + 2 * TILE * 4);
   s.flag = off; off = al16(off + 16 * 4);
   s.bar = off; off = al16(off + MAX_RING * 8);
@@ -1071,16 +1073,16 @@ __device__ __noinline__ int refactor(Ctx<T>& c, cg::cluster_group& cl, T rho) {
     const int r0 = c.rank, nch = d.nch;
     // stored transposed: Theta_{r,m}^T = T_{m-1}^T Theta_{r,m-1}^T, Xi_{r,m-1}^T = U_m^T Xi_{r,m}^T
     for (int m = r0 + 2; m < nch; ++m) {
-      T* Th = Theta + (size_t)(r0 * MAXCS + m) * msz;
+      T* Th = Theta + (size_t)(r0 * nch + m) * msz;
       if (m == r0 + 2) cta_copy<T>(nx, nx, Tch + (size_t)(r0 + 1) * msz, ldx, true, Th, ldx);
       else cta_gemm<T>(nx, nx, nx, T(1), Tch + (size_t)(m - 1) * msz, ldx, true,
-                       Theta + (size_t)(r0 * MAXCS + m - 1) * msz, ldx, false, T(0), nullptr, 0, false, Th, ldx, c.gemm, c.tc);
+                       Theta + (size_t)(r0 * nch + m - 1) * msz, ldx, false, T(0), nullptr, 0, false, Th, ldx, c.gemm, c.tc);
     }
     for (int m = r0 - 2; m >= 0; --m) {
-      T* X = Xi + (size_t)(r0 * MAXCS + m) * msz;
+      T* X = Xi + (size_t)(r0 * nch + m) * msz;
       if (m == r0 - 2) cta_copy<T>(nx, nx, Uch + (size_t)(r0 - 1) * msz, ldx, true, X, ldx);
       else cta_gemm<T>(nx, nx, nx, T(1), Uch + (size_t)(m + 1) * msz, ldx, true,
-                       Xi + (size_t)(r0 * MAXCS + m + 1) * msz, ldx, false, T(0), nullptr, 0, false, X, ldx, c.gemm, c.tc);
+                       Xi + (size_t)(r0 * nch + m + 1) * msz, ldx, false, T(0), nullptr, 0, false, X, ldx, c.gemm, c.tc);
     }
   }
   const int res = cluster_or<T>(c, cl, bad);

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   __syncthreads();
   QPDesc& d = dsh;
 
-  const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.nch, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
+  const SmemLayout lay = smem_layout(d.nx, d.nu, d.nc, d.nf, d.Lc, d.nch, cs, d.ldx, d.ldu, d.ldv, d.ldf, d.depth, d.slot,
                                      (int)sizeof(T), d.fact, d.vg);
   // One context per CTA in shared memory, filled by thread 0: every thread
   // reads the same fields, and a per-thread copy would sit in local memory

@@ -1,5 +1,5 @@
 // SLS controller synthesis and reachability margins (Sec. III-D, Sec. IV-B)
-// on top of the batched tree-scan factorization of qp.cu.
+// on top of the batched factorization of qp.cu (blocked schedule by default).
 //
 //   1. sls_build_kernel forms, for every disturbance index j, the LQR data of
 //      the j-th controller problem (eq. fastsls_qp): stages k = j+1 .. N-1

@@ -1,7 +1,8 @@
 """Long horizons (Sec. V-A's horizon study, N up to 3000): the torque-limited
 pendulum-shaped workload (nx=30, nu=15, N=3000, 1.35e5 decision variables),
 whose per-chunk vectors no longer fit a CTA's shared memory and live in a
-per-CTA global region, against the FP64 oracle: the factorization against
+per-CTA global region at 8 CTAs per QP (at 16, a non-portable cluster size,
+they fit shared memory), against the FP64 oracle: the factorization against
 the sequential Riccati recursion, iterates against the step-by-step ADMM,
 and an adaptive FP32 solve against the oracle's KKT measure.  The global-
 region path is also compared with the shared-memory path on a horizon both
@@ -32,11 +33,12 @@ def pend():
     return W.long_horizon(0)
 
 
+@pytest.mark.parametrize("cluster", [8, 16])
 @pytest.mark.parametrize("prec,tol", [(native.GPUSLS_FP64, 1e-8), (native.GPUSLS_FP32, 1e-4)])
-def test_riccati_matches_sequential_recursion_N3000(lib, pend, prec, tol):
+def test_riccati_matches_sequential_recursion_N3000(lib, pend, prec, tol, cluster):
     qp = pend
     rho = 0.5
-    b = batch([qp], precision=prec, cluster=8, rho=rho)
+    b = batch([qp], precision=prec, cluster=cluster, rho=rho)
     Ps, Ks = b.riccati()
     b.close()
     Qh, Rh, Sh = lq.augmented(qp, rho)
@@ -45,20 +47,22 @@ def test_riccati_matches_sequential_recursion_N3000(lib, pend, prec, tol):
     assert rel(Ks[0], K) < tol, rel(Ks[0], K)
 
 
-def test_fixed_iterations_match_oracle_N3000(lib, pend):
+@pytest.mark.parametrize("cluster", [8, 16])
+def test_fixed_iterations_match_oracle_N3000(lib, pend, cluster):
     qp = pend
-    b = batch([qp], precision=native.GPUSLS_FP64, cluster=8, sigma=0, fixed_iters=5, rho=0.1)
+    b = batch([qp], precision=native.GPUSLS_FP64, cluster=cluster, sigma=0, fixed_iters=5, rho=0.1)
     r = b.solve()
     b.close()
     o = admm.admm(qp, admm.Settings(rho0=0.1, sigma=0), iters=5)
     assert rel(r.dx[0], o.x) < 1e-9 and rel(r.du[0], o.u) < 1e-9 and rel(r.lam[0], o.lam) < 1e-9
 
 
-def test_adaptive_fp32_solve_N3000(lib, pend):
+@pytest.mark.parametrize("cluster", [8, 16])
+def test_adaptive_fp32_solve_N3000(lib, pend, cluster):
     """The solve to the 1e-4 KKT tolerance: the returned point passes the
     oracle's KKT check and meets every torque limit."""
     qp = pend
-    b = batch([qp], precision=native.GPUSLS_FP32, cluster=8, eps_floor=1e-5, max_iter=20000)
+    b = batch([qp], precision=native.GPUSLS_FP32, cluster=cluster, eps_floor=1e-5, max_iter=20000)
     r = b.solve()
     b.close()
     assert r.info[0]["status"] == native.GPUSLS_OK, r.info[0]
@@ -87,3 +91,18 @@ def test_global_vectors_match_shared_vectors(lib, prec, tol):
         assert rel(r.dx[0], o.x) < tol and rel(r.lam[0], o.lam) < tol, (cs, rel(r.dx[0], o.x))
         out[cs] = r.dx[0]
     assert rel(out[1], out[8]) < (1e-12 if prec == native.GPUSLS_FP64 else 1e-5)
+
+
+def test_automatic_launch_shape_takes_16_cta_clusters_N3000(lib, pend):
+    """With cluster = 0 a horizon whose 8-CTA chunks would need the global
+    vector region runs in clusters of 16 CTAs (non-portable): its iterates
+    are bit-identical to an explicit cluster-16 solve and differ, by
+    rounding only, from the 8-CTA chunking."""
+    out = {}
+    for cs in (0, 16, 8):
+        b = batch([pend], precision=native.GPUSLS_FP32, cluster=cs, sigma=0, fixed_iters=20, rho=0.1)
+        out[cs] = b.solve().dx[0].copy()
+        b.close()
+    assert np.array_equal(out[0], out[16])
+    assert not np.array_equal(out[0], out[8])
+    assert rel(out[0], out[8]) < 1e-4

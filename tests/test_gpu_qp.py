@@ -37,7 +37,7 @@ CASES = [
 
 @pytest.mark.parametrize("fact", [0, 1])
 @pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32, native.GPUSLS_MIXED])
-@pytest.mark.parametrize("cluster", [1, 3, 8])
+@pytest.mark.parametrize("cluster", [1, 3, 8, 16])
 @pytest.mark.parametrize("name,make", CASES)
 def test_riccati_matches_oracle(lib, name, make, cluster, prec, fact):
     """The refactor (eq. assoc_init, eq. combination_rules, eq.
@@ -56,7 +56,7 @@ def test_riccati_matches_oracle(lib, name, make, cluster, prec, fact):
     b.close()
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 5, 8])
+@pytest.mark.parametrize("cluster", [1, 2, 5, 8, 16])
 @pytest.mark.parametrize("name,make", CASES)
 def test_fixed_iterations_match_oracle_fp64(lib, name, make, cluster):
     """Iterate parity: 9 ADMM iterations at fixed rho from a cold start."""
