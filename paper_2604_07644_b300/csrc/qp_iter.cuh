@@ -805,13 +805,23 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
           if (col < nx) { M = Ci + col; stride = nx; x = lv; len = nr; out = gt + col; }
           else { M = Di + (col - nx); stride = nu; x = lv; len = nc; out = ht + (col - nx); }
         }
-        double a0 = 0.0, a1 = 0.0;
+        // eight independent partial sums: eight loads of the row in flight
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0, a5 = 0.0, a6 = 0.0, a7 = 0.0;
         int k = 0;
-        for (; k + 1 < len; k += 2) {
-          a0 = fma(M[(size_t)k * stride], x[k], a0);
-          a1 = fma(M[(size_t)(k + 1) * stride], x[k + 1], a1);
+        for (; k + 7 < len; k += 8) {
+          const double* Mk = M + (size_t)k * stride;
+          a0 = fma(Mk[0], x[k], a0);
+          a1 = fma(Mk[(size_t)stride], x[k + 1], a1);
+          a2 = fma(Mk[(size_t)2 * stride], x[k + 2], a2);
+          a3 = fma(Mk[(size_t)3 * stride], x[k + 3], a3);
+          a4 = fma(Mk[(size_t)4 * stride], x[k + 4], a4);
+          a5 = fma(Mk[(size_t)5 * stride], x[k + 5], a5);
+          a6 = fma(Mk[(size_t)6 * stride], x[k + 6], a6);
+          a7 = fma(Mk[(size_t)7 * stride], x[k + 7], a7);
         }
-        if (k < len) a0 = fma(M[(size_t)k * stride], x[k], a0);
+        for (; k < len; ++k) a0 = fma(M[(size_t)k * stride], x[k], a0);
+        a0 = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+        a1 = 0.0;
         if (it >= nrow && it - nrow < nx && !term) {
           // S^T u joins the column sum of C^T lam
           const int col = it - nrow;
@@ -875,10 +885,15 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
       cp_async_commit();
     };
     for (int j = t; j < nx; j += NT) mu[j] = d.kg[(size_t)N * nx + j];
+    double* mcur = mu;    // mu_{i+1}, read by the sweep of stage i
+    double* mnext = mu2;  // mu_i, written by the owners (the two swap every stage)
     if (pre) issue(N - 1, 0);
     __syncthreads();
     int kb = 0;
     for (int i = N - 1; i >= 0; --i, kb ^= 1) {
+      // the owner's term of this stage, loaded ahead of the copy wait and the sweep
+      double own = 0.0;
+      if (t < no) own = t < nx ? d.kg[(size_t)i * nx + t] : d.kh[(size_t)i * nu + (t - nx)];
       if (pre) {
         if (i > 0) {
           issue(i - 1, kb ^ 1);
@@ -897,10 +912,10 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
         double a0 = 0.0, a1 = 0.0;
         int k = r0;
         for (; k + 1 < r1; k += 2) {
-          a0 = fma(M[(size_t)k * ld], mu[k], a0);
-          a1 = fma(M[(size_t)(k + 1) * ld], mu[k + 1], a1);
+          a0 = fma(M[(size_t)k * ld], mcur[k], a0);
+          a1 = fma(M[(size_t)(k + 1) * ld], mcur[k + 1], a1);
         }
-        if (k < r1) a0 = fma(M[(size_t)k * ld], mu[k], a0);
+        if (k < r1) a0 = fma(M[(size_t)k * ld], mcur[k], a0);
         part[g * no + o] = a0 + a1;
       }
       __syncthreads();
@@ -908,17 +923,18 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
         double s2 = 0.0;
         for (int gg = 0; gg < G; ++gg) s2 += part[gg * no + t];
         if (t < nx) {
-          mu2[t] = s2 + d.kg[(size_t)i * nx + t];
+          mnext[t] = s2 + own;
         } else {
           const int a = t - nx;
-          const double ru = s2 + d.kh[(size_t)i * nu + a];
+          const double ru = s2 + own;
           stat = fmax(stat, fabs(ru));
           d.kh[(size_t)i * nu + a] = ru;   // u-stationarity residual, read by refine_linear_term
         }
       }
-      __syncthreads();
-      for (int j = t; j < nx; j += NT) mu[j] = mu2[j];
-      __syncthreads();
+      __syncthreads();   // mu_i complete; part[] free again
+      double* const sw = mcur;
+      mcur = mnext;
+      mnext = sw;
     }
   }
   if (threadIdx.x == 0 && c.prof) {
