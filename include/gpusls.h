@@ -42,7 +42,9 @@ extern "C" {
 #define GPUSLS_ERR_INVALID   -1   /* invalid argument or dimensions                 */
 #define GPUSLS_ERR_NOT_SPD   -2   /* R^, Gamma^-1 or Qu not SPD, or I + C~P~ singular */
 #define GPUSLS_ERR_NAN       -3   /* NaN/Inf appeared in the iterates               */
-#define GPUSLS_ERR_INFEASIBLE -4  /* primal infeasibility detected                  */
+#define GPUSLS_ERR_INFEASIBLE -4  /* per-QP status (qp_info): the solve reached max_iter
+                                     and a primal infeasibility certificate holds (see
+                                     qp_solve); results are the last iterates       */
 #define GPUSLS_ERR_CUDA      -5   /* CUDA runtime error                             */
 #define GPUSLS_ERR_TIMEOUT   -6   /* a bounded device wait gave up                  */
 
@@ -119,7 +121,8 @@ typedef struct qp_settings {
 
 /* Per-QP result summary (host memory). */
 typedef struct qp_info {
-  int32_t status;     /* GPUSLS_OK, GPUSLS_MAX_ITER or a negative error            */
+  int32_t status;     /* GPUSLS_OK, GPUSLS_MAX_ITER, GPUSLS_ERR_INFEASIBLE or a
+                         negative error                                      */
   int32_t iters;      /* ADMM iterations run                                       */
   int32_t refactors;  /* rho-dependent factorizations (tree scans) performed       */
   int32_t refines;    /* iterative-refinement rounds applied                       */
@@ -179,8 +182,17 @@ int qp_batch_setup(qp_handle** h, int32_t batch, const qp_dims* dims,
  *   x0 [nx] (pool for batches)   outputs: dx [N+1][nx], du [N][nu],
  *   lam [N*nc+nf] (unscaled multipliers lambda = rho * y), all pools.
  *   info: HOST array [batch] or NULL.
- * Returns GPUSLS_OK if every QP converged, GPUSLS_MAX_ITER if some did not,
- * or the most severe negative per-QP status. */
+ * A QP that reaches the iteration limit is classified from the change w of
+ * its multipliers over the last check interval (Farkas: the constraints
+ * E xi = e of the dynamics and x_0, and lo <= G xi <= hi, admit no xi when
+ * E^T mu + G^T w = 0 and sigma(w) + e^T mu < 0, sigma the support function
+ * of the box; mu follows from the x-components, the u-components are the
+ * residual): with W = ||w||_inf, a residual and a push against infinite
+ * bounds of at most eps W and sigma(w) + e^T mu < -eps W, info[b].status is
+ * GPUSLS_ERR_INFEASIBLE, else GPUSLS_MAX_ITER.
+ * Returns GPUSLS_OK if every QP converged, GPUSLS_MAX_ITER if some did not
+ * (iteration limit or infeasible: see info), or the most severe other
+ * negative per-QP status. */
 int qp_solve(qp_handle* h, const double* x0, int32_t iters, double tol,
              double* dx, double* du, double* lam, qp_info* info);
 

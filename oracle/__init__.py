@@ -17,9 +17,14 @@ Modules
               (sequential fold and the App. A up/down-sweep schedule)
     admm      step-by-step ADMM (Sec. IV-A) with the OSQP-style rho rule
     kkt       FP64 KKT residual of the LTV-QP (eq. sqp_qp)
+    infeas    Farkas certificate of primal infeasibility from a multiplier
+              direction (the classification of solves at max_iter)
     activeset brute-force active-set solve of tiny LTV-QPs
     sls       N Riccati recursions, Phi_x / Phi_u, margins, beta / tau
     mlp       2-hidden-layer ReLU MLP forward / backward / Adam
+    fastsls   the FastSLS alternation (tightening, App. B duals, the loop)
+    models    Dubins car and planar quadrotor (App. C, App. D), the
+              linearized QP, merit, line search, SQP and RTI
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, dense linear algebra, brute force or invariants; the paper prints

@@ -33,8 +33,13 @@ Readings (the paper is silent or garbled here):
     reduced-precision LQ solve can hold r_prim or r_dual just above the floor;
     in exact arithmetic both go to zero and the rule never fires.
 
-The KKT gate, the tightening of eps, the refinement and the stall rule are
-this project's stopping rule: the paper stops ADMM on its residual tolerance
+  * a solve that reaches max_iter is classified by the primal infeasibility
+    certificate of oracle.infeas, taken from the change of lambda = rho y
+    over the last check interval (reference point saved at iteration
+    max_iter - check_every).
+
+The KKT gate, the tightening of eps, the refinement, the stall rule and the
+infeasibility classification are this project's stopping rule: the paper stops ADMM on its residual tolerance
 alone and prints no such control.  With eps_kkt = None (the default) the
 oracle runs the paper's ADMM and stops on r_prim, r_dual <= eps.
 """
@@ -46,6 +51,7 @@ import numpy as np
 
 import dataclasses
 
+from .infeas import certificate
 from .kkt import kkt_residual, u_residuals
 from .lq import G_apply, GT_apply, H_apply, augmented, augmented_linear, lq_solve
 
@@ -80,6 +86,7 @@ class Result:
     refactors: int
     rho_hist: list = field(default_factory=list)
     kkt: float | None = None
+    infeasible: bool = False       # reached max_iter with a primal infeasibility certificate
 
 
 def residuals(qp, v, z_new, z, rho):
@@ -125,6 +132,7 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
     x = u = None
     kkt = None
     floor_it = -1                  # first stop-test iteration at the eps floor (stall rule)
+    lam_ref = None                 # lambda one check interval before max_iter (certificate)
     t = 0
     for t in range(1, max_iter + 1):
         qh, rh = augmented_linear(qp, rho, y, z)
@@ -136,6 +144,8 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
         z = z_new
         if iters is not None:
             continue
+        if t == max_iter - s.check_every:
+            lam_ref = rho * y
         # eps counts as at the floor within a relative 1e-9: repeated
         # multiplication by 0.1 does not land on the floor exactly in binary
         at_floor = eps <= s.eps_floor * (1.0 + 1e-9)
@@ -166,8 +176,12 @@ def admm(qp, s: Settings | None = None, z0=None, y0=None, rho0=None, iters=None)
                 Qh, Rh, Sh = augmented(qp, rho)
                 refactors += 1
                 hist.append(rho)
+    infeasible = False
+    if iters is None and not converged and lam_ref is not None:
+        # the iteration limit: classify by the certificate of oracle.infeas
+        infeasible = certificate(qp0, rho * y - lam_ref, s.eps)["certified"]
     return Result(x=x, u=u, z=z, y=y, rho=rho, lam=rho * y, iters=t, r_prim=r_prim, r_dual=r_dual,
-                  converged=converged, refactors=refactors, rho_hist=hist, kkt=kkt)
+                  converged=converged, refactors=refactors, rho_hist=hist, kkt=kkt, infeasible=infeasible)
 
 
 def exact_solution(qp, tol: float = 1e-11, max_iter: int = 200000):

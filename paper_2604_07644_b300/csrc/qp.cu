@@ -607,8 +607,10 @@ static int collect(qp_handle* h, qp_info* info) {
       info[b].r_dual = dd[4 * b + 2];
       info[b].kkt = dd[4 * b + 3];
     }
-    if (st < 0 && (worst >= 0 || st < worst)) worst = st;
-    else if (st == GPUSLS_MAX_ITER && worst == GPUSLS_OK) worst = GPUSLS_MAX_ITER;
+    // an infeasible QP is a result (info[b].status), not a failed call: it
+    // counts as not converged
+    if (st < 0 && st != GPUSLS_ERR_INFEASIBLE && (worst >= 0 || st < worst)) worst = st;
+    else if ((st == GPUSLS_MAX_ITER || st == GPUSLS_ERR_INFEASIBLE) && worst == GPUSLS_OK) worst = GPUSLS_MAX_ITER;
   }
   return worst;
 }

@@ -1004,4 +1004,126 @@ __device__ void refine_linear_term(Ctx<T>& c) {
   }
 }
 
+// Multipliers lambda = rho y of own rows into the FP64 output buffer: the
+// reference point of the infeasibility certificate (infeas_eval), taken one
+// check interval before max_iter.  The final write_outputs overwrites it.
+template <typename T>
+__device__ void save_multipliers(Ctx<T>& c, T rho) {
+  QPDesc& d = *c.d;
+  if (!c.active) return;
+  const int nrows = own_rows(c);
+  for (int e2 = threadIdx.x; e2 < nrows; e2 += NT) d.olam[(size_t)c.s * d.nc + e2] = (double)rho * (double)c.yS[e2];
+}
+
+// Block reduction in FP64 (op 0: max, 1: sum) through `scr` (>= NT / 32
+// doubles of shared memory); the result is returned to every thread.
+__device__ inline double block_reduce_d(double v, int op, double* scr) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  v = op == 0 ? warp_max(v) : warp_sum(v);
+  __syncthreads();
+  if (l == 0) scr[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int k = 0; k < NT / 32; ++k) r = op == 0 ? fmax(r, scr[k]) : r + scr[k];
+  __syncthreads();
+  return r;
+}
+
+// Primal infeasibility certificate (Farkas) at a solve that reached max_iter.
+// The constraints of eq. sqp_qp are the dynamics and initial state, E xi = e
+// (rows x_0 = x0 and x_{k+1} - A_k x_k - B_k u_k = b_k), and the bounds
+// lo <= G xi <= hi.  No feasible xi exists if some (mu, w) has
+// E^T mu + G^T w = 0 and sigma(w) + e^T mu < 0, with the support function
+// sigma(w) = sum_i (w_i > 0 ? hi_i w_i : lo_i w_i) of the box.  For a given w
+// the x-components fix mu (nu_k the multiplier of stage k's dynamics row):
+//   nu_{N-1} = -C_N^T w_N,  nu_{k-1} = A_k^T nu_k - C_k^T w_k (k = N-1 .. 1),
+//   mu_0 = A_0^T nu_0 - C_0^T w_0,
+// and the u-components are left as the residual r_k = D_k^T w_k - B_k^T nu_k.
+// w is the change of the multipliers over the last check interval, lambda
+// now minus the saved lambda (olam), which on an infeasible problem tends to
+// a certificate direction.  Certified (returned in every thread of the
+// cluster) when, with W = ||w||_inf > 0: every w_i pushing against an
+// infinite bound is at most tol W, ||r||_inf <= tol W and
+// sigma(w) + e^T mu < -tol W.  Every CTA forms w of its own rows in olam;
+// CTA 0 runs the serial recursion over the stages in FP64.
+template <typename T>
+__device__ __noinline__ int infeas_eval(Ctx<T>& c, cg::cluster_group& cl, T rho, double tol) {
+  QPDesc& d = *c.d;
+  const int nx = d.nx, nu = d.nu, nc = d.nc, nf = d.nf, N = d.N, m = d.m;
+  const int t = threadIdx.x;
+  if (c.active) {
+    const int nrows = own_rows(c);
+    for (int e2 = t; e2 < nrows; e2 += NT) {
+      const size_t gi = (size_t)c.s * nc + e2;
+      d.olam[gi] = (double)rho * (double)c.yS[e2] - d.olam[gi];
+    }
+  }
+  cl.sync();   // every CTA's w in olam
+  int cert = 0;
+  if (c.rank == 0) {
+    double* nu_c = reinterpret_cast<double*>(c.ring);   // FP64 scratch in the union region
+    double* nu_n = nu_c + 96;
+    double* scr = nu_n + 96;
+    const double* w = d.olam;
+    // W, the push against infinite bounds, sigma(w)
+    double W = 0.0, pinf = 0.0, sig = 0.0;
+    for (int i = t; i < m; i += NT) {
+      const double wi = w[i];
+      W = fmax(W, fabs(wi));
+      if (wi > 0.0) {
+        const double h = d.hi64[i];
+        if (isfinite(h)) sig += h * wi;
+        else pinf = fmax(pinf, wi);
+      } else if (wi < 0.0) {
+        const double l = d.lo64[i];
+        if (isfinite(l)) sig += l * wi;
+        else pinf = fmax(pinf, -wi);
+      }
+    }
+    W = block_reduce_d(W, 0, scr);
+    pinf = block_reduce_d(pinf, 0, scr);
+    sig = block_reduce_d(sig, 1, scr);
+    // nu_{N-1} = -C_N^T w_N
+    for (int j = t; j < nx; j += NT) {
+      double a = 0.0;
+      for (int k = 0; k < nf; ++k) a += d.CN64[(size_t)k * nx + j] * w[(size_t)N * nc + k];
+      nu_c[j] = -a;
+    }
+    __syncthreads();
+    double rmax = 0.0, val = 0.0;   // val: this thread's share of e^T mu
+    for (int k = N - 1; k >= 0; --k) {
+      const double* Ak = d.A64 + (size_t)k * nx * nx;
+      const double* Bk = d.B64 + (size_t)k * nx * nu;
+      const double* Ck = d.C64 + (size_t)k * nc * nx;
+      const double* Dk = d.D64 + (size_t)k * nc * nu;
+      const double* wk = w + (size_t)k * nc;
+      if (t < nx) {
+        // nu_{k-1} (mu_0 at k = 0) = A_k^T nu_k - C_k^T w_k; e^T mu: b_k^T nu_k
+        double a = 0.0, b2 = 0.0;
+        for (int i = 0; i < nx; ++i) a = fma(Ak[(size_t)i * nx + t], nu_c[i], a);
+        for (int r = 0; r < nc; ++r) b2 = fma(Ck[(size_t)r * nx + t], wk[r], b2);
+        nu_n[t] = a - b2;
+        val = fma(d.b64[(size_t)k * nx + t], nu_c[t], val);
+      } else if (t < nx + nu) {
+        // r_k = D_k^T w_k - B_k^T nu_k
+        const int q = t - nx;
+        double a = 0.0, b2 = 0.0;
+        for (int r = 0; r < nc; ++r) a = fma(Dk[(size_t)r * nu + q], wk[r], a);
+        for (int i = 0; i < nx; ++i) b2 = fma(Bk[(size_t)i * nu + q], nu_c[i], b2);
+        rmax = fmax(rmax, fabs(a - b2));
+      }
+      __syncthreads();
+      double* sw = nu_c;
+      nu_c = nu_n;
+      nu_n = sw;
+    }
+    // nu_c = mu_0: e^T mu gains x0^T mu_0
+    if (t < nx) val = fma(d.x064[t], nu_c[t], val);
+    rmax = block_reduce_d(rmax, 0, scr);
+    val = block_reduce_d(val, 1, scr);
+    cert = (W > 0.0 && pinf <= tol * W && rmax <= tol * W && sig + val < -tol * W) ? 1 : 0;
+  }
+  return cluster_or<T>(c, cl, cert);
+}
+
 }  // namespace gsls

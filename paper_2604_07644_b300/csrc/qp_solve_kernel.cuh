@@ -163,6 +163,8 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
       const bool check = stop_iter || rho_iter || (it == max_it);
       Partials pl;
       admm_iteration<T>(c, cl, rho, check, pl);
+      // the reference multipliers of the infeasibility certificate
+      if (!fixed && it == max_it - args.check_every) save_multipliers<T>(c, rho);
       if (!check) continue;
       double v[5] = {pl.rp, 0.0, pl.vm, pl.zm, c.flag[RING_FLAG] ? 1.0 : 0.0};
       cluster_max(c, cl, v);
@@ -269,6 +271,11 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
       }
     }
     if (it > max_it) it = max_it;
+    // a solve that ran out of iterations: a primal infeasibility certificate
+    // from the multipliers' change over the last check interval
+    if (status == GPUSLS_MAX_ITER && !fixed && max_it > args.check_every &&
+        infeas_eval<T>(c, cl, rho, args.eps))
+      status = GPUSLS_ERR_INFEASIBLE;
     full_xu<T>(c);
     write_outputs<T>(c, rho);
     if (status == GPUSLS_OK && args.eps_kkt <= 0.0) kkt = -1.0;

@@ -18,6 +18,7 @@ Sec. III-B (eq. sqp_qp):
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass, field
 
@@ -287,6 +288,29 @@ def quadruped_61d(seed: int = 0, N: int = 100) -> QP:
 def humanoid_75d(seed: int = 0, N: int = 40) -> QP:
     """Humanoid-shaped QP: nx=75, nu=21, N=40, nc=29, nf=8."""
     return legged(seed, 75, 21, N, tag=4)
+
+
+def infeasible_x0(seed: int = 0) -> QP:
+    """The plain 4D QP with x0[0] = 9: x_0 = x0 is fixed and violates the
+    stage-0 state bound |x| <= 5, so no feasible point exists."""
+    qp = plain_4d(seed)
+    x0 = qp.x0.copy()
+    x0[0] = 9.0
+    return dataclasses.replace(qp, x0=x0, name=f"infeasible-x0-s{seed}")
+
+
+def infeasible_terminal(seed: int = 1, N: int = 12) -> QP:
+    """The plain 4D QP with |u| <= 1e-3 and the terminal row x_N[0] pinned to
+    4.9, which the nearly open-loop trajectory from x0 (kept inside |x| <= 4.5
+    by the plain 4D draw) cannot reach: no feasible point exists."""
+    qp = plain_4d(seed, N=N)
+    nx, nc = qp.nx, qp.nc
+    lo, hi = qp.lo.copy(), qp.hi.copy()
+    for k in range(N):
+        lo[k * nc + nx:(k + 1) * nc] = -1e-3   # rows [x; u]: the u rows
+        hi[k * nc + nx:(k + 1) * nc] = 1e-3
+    lo[N * nc], hi[N * nc] = 4.9, 4.9
+    return dataclasses.replace(qp, lo=lo, hi=hi, name=f"infeasible-terminal-s{seed}")
 
 
 def long_horizon(seed: int = 0, links: int = 15, N: int = 3000, dt: float = 0.01) -> QP:

@@ -2,8 +2,9 @@
 (a single stage, one state, one input, no constraint rows), the largest
 sizes a CTA's shared memory accepts, problems too large for it (rejected
 with GPUSLS_ERR_INVALID, after which the library keeps working), ragged
-batches mixing all of these, and a primal-infeasible QP (reported as
-GPUSLS_MAX_ITER with finite outputs)."""
+batches mixing all of these, and primal-infeasible QPs (classified
+GPUSLS_ERR_INFEASIBLE at max_iter as the oracle classifies them, with finite
+outputs)."""
 import numpy as np
 import pytest
 
@@ -80,11 +81,12 @@ def test_ragged_batch_with_degenerate_members(lib):
         assert rel(r.dx[i], o.x) < 1e-9 and rel(r.lam[i], o.lam) < 1e-9, i
 
 
-def test_infeasible_qp_reports_max_iter(lib):
+def test_infeasible_qp_is_classified_at_max_iter(lib):
     """x0 outside the state bound |x| <= 5 of stage 0 (x_0 = x0 is fixed):
-    no feasible point exists; the solve stops at max_iter with
-    GPUSLS_MAX_ITER, finite outputs and a primal residual that stays large,
-    and the other QP of the batch still converges."""
+    no feasible point exists; the solve stops at max_iter, its status is
+    GPUSLS_ERR_INFEASIBLE (the certificate holds), the call returns
+    GPUSLS_MAX_ITER, the outputs are finite with a primal residual that
+    stays large, and the other QP of the batch still converges."""
     from paper_2604_07644_b300.api import QPBatch
     bad = W.plain_4d(0)
     bad.x0 = bad.x0.copy()
@@ -94,6 +96,26 @@ def test_infeasible_qp_reports_max_iter(lib):
     r = b.solve()
     b.close()
     assert r.status == native.GPUSLS_MAX_ITER
-    assert r.info[0]["status"] == native.GPUSLS_MAX_ITER and r.info[0]["r_prim"] > 1.0
+    assert r.info[0]["status"] == native.GPUSLS_ERR_INFEASIBLE and r.info[0]["r_prim"] > 1.0
     assert all(np.isfinite(a).all() for a in (r.dx[0], r.du[0], r.lam[0]))
     assert r.info[1]["status"] == native.GPUSLS_OK
+
+
+@pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32])
+@pytest.mark.parametrize("case", ["x0_outside_the_box", "unreachable_terminal_box", "feasible_cut_short"])
+def test_max_iter_classification_matches_oracle(lib, case, prec):
+    """The certificate at max_iter (Farkas, from the multipliers' change
+    over the last check interval) classifies as the oracle's ADMM does:
+    infeasible by construction -> GPUSLS_ERR_INFEASIBLE, a feasible QP cut
+    short -> GPUSLS_MAX_ITER."""
+    from paper_2604_07644_b300.api import QPBatch
+    qp, it = {"x0_outside_the_box": (W.infeasible_x0(), 600),
+              "unreachable_terminal_box": (W.infeasible_terminal(), 600),
+              "feasible_cut_short": (W.plain_4d(0), 20)}[case]
+    o = admm.admm(qp, admm.Settings(max_iter=it))
+    b = QPBatch([qp], native.default_settings(precision=prec, max_iter=it, eps_kkt=0.0))
+    r = b.solve()
+    b.close()
+    want = native.GPUSLS_ERR_INFEASIBLE if o.infeasible else native.GPUSLS_MAX_ITER
+    assert r.info[0]["status"] == want, (r.info[0], o.infeasible)
+    assert (case != "feasible_cut_short") == o.infeasible
