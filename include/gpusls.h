@@ -46,7 +46,12 @@ extern "C" {
                                      and a primal infeasibility certificate holds (see
                                      qp_solve); results are the last iterates       */
 #define GPUSLS_ERR_CUDA      -5   /* CUDA runtime error                             */
-#define GPUSLS_ERR_TIMEOUT   -6   /* a bounded device wait gave up                  */
+#define GPUSLS_ERR_TIMEOUT   -6   /* a bounded device wait gave up.  Test hook: with
+                                     the environment variable GPUSLS_TEST_WAIT_TIMEOUT
+                                     set at launch, every solve first waits (bounded,
+                                     ~1 s at most) on a copy barrier that nothing
+                                     completes, gives up and returns this status; the
+                                     CUDA context stays usable                       */
 
 /* arithmetic of the solve kernels */
 #define GPUSLS_FP64 0   /* all arithmetic in float64                                  */
@@ -348,6 +353,14 @@ int mlp_fit_normalization(mlp_handle* h, const float* X, const float* T, int32_t
  * [n_in], [n_in], [n_out], [n_out]; NULL outputs skipped) */
 int mlp_set_normalization(mlp_handle* h, const float* xm, const float* xs, const float* ym, const float* ys);
 int mlp_get_normalization(mlp_handle* h, float* xm, float* xs, float* ym, float* ys);
+/* mlp_save / mlp_load: the network as a binary file (path: a HOST C string):
+ * the 8-byte tag "GSLSMLP1", int32 n_in, hidden, n_out (native byte order),
+ * then float32 W1, b1, W2, b2, W3, b3 (the mlp_set_params layouts) and xm,
+ * xs, ym, ys.  mlp_load fills a handle of the same sizes and restarts Adam;
+ * a missing, short, longer or foreign file, or other sizes, give
+ * GPUSLS_ERR_INVALID and leave the handle unchanged. */
+int mlp_save(mlp_handle* h, const char* path);
+int mlp_load(mlp_handle* h, const char* path);
 /* Y = denormalized network output for raw inputs X (B <= max_batch) */
 int mlp_forward(mlp_handle* h, const float* X, int32_t B, float* Y);
 /* gradients of the loss at ALREADY-normalized (Xn, Tn) into grads (device,

@@ -7,6 +7,8 @@ from __future__ import annotations
 import ctypes as C
 from dataclasses import dataclass
 
+import os
+
 import numpy as np
 import torch
 
@@ -551,6 +553,14 @@ class MLP:
     def set_normalization(self, xm, xs, ym, ys):
         ts = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(self.device) for a in (xm, xs, ym, ys)]
         native.check(self.lib.mlp_set_normalization(self.h, *[_dptr(t) for t in ts]), "mlp_set_normalization")
+
+    def save(self, path: str):
+        """The network (parameters and normalization) to a binary file (mlp_save)."""
+        native.check(self.lib.mlp_save(self.h, os.fsencode(path)), "mlp_save")
+
+    def load(self, path: str):
+        """Parameters and normalization from a file written by save (mlp_load)."""
+        native.check(self.lib.mlp_load(self.h, os.fsencode(path)), "mlp_load")
 
     def get_normalization(self):
         ts = [torch.empty(n, dtype=torch.float32, device=self.device)

@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <string>
@@ -379,6 +381,66 @@ extern "C" int mlp_get_normalization(mlp_handle* h, float* xm, float* xs, float*
   if (ym) CUM(cudaMemcpyAsync(ym, h->ym, h->n_out * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
   if (ys) CUM(cudaMemcpyAsync(ys, h->ys, h->n_out * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
   CUM(cudaStreamSynchronize(h->stream));
+  return GPUSLS_OK;
+}
+
+// Host image of a network in the file layout of mlp_save: parameters in the
+// mlp_set_params order, then the normalization.
+static std::vector<std::pair<float*, size_t>> file_fields(mlp_handle* h) {
+  return {{h->P + h->oW1, (size_t)h->hid * h->n_in}, {h->P + h->ob1, (size_t)h->hid},
+          {h->P + h->oW2, (size_t)h->hid * h->hid}, {h->P + h->ob2, (size_t)h->hid},
+          {h->P + h->oW3, (size_t)h->n_out * h->hid}, {h->P + h->ob3, (size_t)h->n_out},
+          {h->xm, (size_t)h->n_in}, {h->xs, (size_t)h->n_in}, {h->ym, (size_t)h->n_out}, {h->ys, (size_t)h->n_out}};
+}
+
+static const char MLP_FILE_TAG[8] = {'G', 'S', 'L', 'S', 'M', 'L', 'P', '1'};
+
+extern "C" int mlp_save(mlp_handle* h, const char* path) {
+  if (!h || !path) return set_error(GPUSLS_ERR_INVALID, "mlp_save: null argument");
+  std::vector<float> buf;
+  for (auto& f : file_fields(h)) {
+    const size_t o = buf.size();
+    buf.resize(o + f.second);
+    CUM(cudaMemcpyAsync(buf.data() + o, f.first, f.second * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUM(cudaStreamSynchronize(h->stream));
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return set_error(GPUSLS_ERR_INVALID, std::string("mlp_save: cannot open ") + path);
+  const int32_t dims[3] = {h->n_in, h->hid, h->n_out};
+  const bool ok = fwrite(MLP_FILE_TAG, 1, 8, fp) == 8 && fwrite(dims, sizeof(int32_t), 3, fp) == 3 &&
+                  fwrite(buf.data(), sizeof(float), buf.size(), fp) == buf.size();
+  if (fclose(fp) != 0 || !ok) return set_error(GPUSLS_ERR_INVALID, std::string("mlp_save: write failed: ") + path);
+  return GPUSLS_OK;
+}
+
+extern "C" int mlp_load(mlp_handle* h, const char* path) {
+  if (!h || !path) return set_error(GPUSLS_ERR_INVALID, "mlp_load: null argument");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return set_error(GPUSLS_ERR_INVALID, std::string("mlp_load: cannot open ") + path);
+  char tag[8] = {};
+  int32_t dims[3] = {};
+  const auto fields = file_fields(h);
+  size_t total = 0;
+  for (auto& f : fields) total += f.second;
+  std::vector<float> buf(total);
+  bool ok = fread(tag, 1, 8, fp) == 8 && memcmp(tag, MLP_FILE_TAG, 8) == 0 && fread(dims, sizeof(int32_t), 3, fp) == 3;
+  ok = ok && dims[0] == h->n_in && dims[1] == h->hid && dims[2] == h->n_out;
+  ok = ok && fread(buf.data(), sizeof(float), total, fp) == total;
+  char extra;
+  ok = ok && fread(&extra, 1, 1, fp) == 0;   // nothing after the last field
+  fclose(fp);
+  if (!ok)
+    return set_error(GPUSLS_ERR_INVALID, std::string("mlp_load: not a network of this handle's sizes: ") + path);
+  size_t o = 0;
+  for (auto& f : fields) {
+    CUM(cudaMemcpyAsync(f.first, buf.data() + o, f.second * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    o += f.second;
+  }
+  // new parameters restart the optimizer state
+  CUM(cudaMemsetAsync(h->Mm, 0, h->np * sizeof(float), h->stream));
+  CUM(cudaMemsetAsync(h->Vm, 0, h->np * sizeof(float), h->stream));
+  h->step = 0;
+  CUM(cudaStreamSynchronize(h->stream));   // buf is released on return
   return GPUSLS_OK;
 }
 

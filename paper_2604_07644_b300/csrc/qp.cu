@@ -183,6 +183,8 @@ static int launch_qp(qp_handle* h, const SolveArgs& a) {
 static int launch(qp_handle* h, const SolveArgs& a0) {
   SolveArgs a = a0;
   a.tc = h->set.precision == GPUSLS_TF32 ? 1 : (h->set.precision == GPUSLS_MIXED ? 2 : 0);
+  // test hook of the bounded device waits (see include/gpusls.h)
+  a.test_wait = getenv("GPUSLS_TEST_WAIT_TIMEOUT") != nullptr ? 1 : 0;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(h->stream, &cap));
   const bool prof_on = getenv("GPUSLS_PROFILE") != nullptr && cap == cudaStreamCaptureStatusNone;

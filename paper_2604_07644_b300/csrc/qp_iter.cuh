@@ -457,7 +457,9 @@ __device__ void admm_iteration(Ctx<T>& c, cg::cluster_group& cl, T rho, bool che
       c.yS[lr] = yo + v - zn;
       c.zS[lr] = zn;
       c.wS[lr] = zn - zo;
-      rp = fmax(rp, fabs(v - zn));
+      // a NaN or Inf in v (fmax would drop a NaN) makes r_prim infinite:
+      // the check reports GPUSLS_ERR_NAN
+      rp = isfinite(v) ? fmax(rp, fabs(v - zn)) : T(INFINITY);
       vm = fmax(vm, fabs(v));
       zm = fmax(zm, fabs(zn));
     }

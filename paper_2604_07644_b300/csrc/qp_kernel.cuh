@@ -89,6 +89,7 @@ struct SolveArgs {
   const int* order;     // launch order: cluster b solves QP order[b] (null: QP b)
   int tc;               // 1: factorization block products on the tensor cores in TF32 (GPUSLS_TF32);
                         // 2: GPUSLS_MIXED (three TF32 passes, FP64 per-stage solves)
+  int test_wait;        // test hook: one bounded wait on a copy barrier that nothing completes
 };
 
 // Per-stage operator bundles of the cached iteration (elements).  Every

@@ -157,6 +157,14 @@ __global__ void __launch_bounds__(NT, KernelOcc<T>::value) qp_kernel(const QPDes
   const int it_warm0 = 0;
   int fell_back = 0;
   if (status != GPUSLS_ERR_NOT_SPD) {
+    if (args.test_wait) {
+      // test hook: wait (bounded) for the next completion of the whole-region
+      // copy barrier, which no copy is issued to; the wait gives up, the
+      // flag stops every later copy and wait, and the first check reports
+      // GPUSLS_ERR_TIMEOUT
+      if (!mbar_wait(&c.bar[BULK_BAR], c.bpar, RING_WAIT_LIMIT)) c.flag[RING_FLAG] = 1;
+      __syncthreads();
+    }
     for (it = 1; it <= max_it; ++it) {
       const bool stop_iter = !fixed && (it % args.check_every == 0);
       const bool rho_iter = !fixed && args.sigma > 0 && (it % args.sigma == 0);

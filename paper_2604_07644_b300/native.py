@@ -95,6 +95,8 @@ SIGNATURES = {
     "mlp_forward": (C.c_int, [P, DP, C.c_int32, DP]),
     "mlp_set_normalization": (C.c_int, [P, DP, DP, DP, DP]),
     "mlp_get_normalization": (C.c_int, [P, DP, DP, DP, DP]),
+    "mlp_save": (C.c_int, [P, C.c_char_p]),
+    "mlp_load": (C.c_int, [P, C.c_char_p]),
     "mlp_gradients": (C.c_int, [P, DP, DP, C.c_int32, DP, C.POINTER(C.c_float)]),
     "mlp_train_step": (C.c_int, [P, DP, DP, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
     "mlp_destroy": (None, [P]),

@@ -119,3 +119,63 @@ def test_max_iter_classification_matches_oracle(lib, case, prec):
     want = native.GPUSLS_ERR_INFEASIBLE if o.infeasible else native.GPUSLS_MAX_ITER
     assert r.info[0]["status"] == want, (r.info[0], o.infeasible)
     assert (case != "feasible_cut_short") == o.infeasible
+
+
+@pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32])
+def test_nan_in_the_data_is_reported_and_the_library_keeps_working(lib, prec):
+    """A NaN injected on the host into q makes the iterates NaN: the first
+    check reports GPUSLS_ERR_NAN (a NaN primal residual is not dropped by
+    the max), and a clean QP solves afterwards."""
+    import dataclasses
+
+    from paper_2604_07644_b300.api import QPBatch
+    qp = W.plain_4d(0)
+    q = qp.q.copy()
+    q[3, 1] = np.nan
+    bad = dataclasses.replace(qp, q=q)
+    s = native.default_settings(precision=prec, max_iter=200)
+    b = QPBatch([bad], s)
+    with pytest.raises(RuntimeError, match="failed with nan"):
+        b.solve()
+    b.close()
+    b = QPBatch([qp], s)
+    r = b.solve()
+    b.close()
+    assert r.info[0]["status"] == native.GPUSLS_OK
+
+
+def test_indefinite_input_cost_is_reported_not_spd(lib):
+    """R = -I (host-side corrupt cost): R^ = R + rho D^T D is not positive
+    definite; the factorization reports GPUSLS_ERR_NOT_SPD."""
+    import dataclasses
+
+    from paper_2604_07644_b300.api import QPBatch
+    qp = W.plain_4d(0)
+    bad = dataclasses.replace(qp, R=-np.ones_like(qp.R) * np.eye(qp.nu))
+    b = QPBatch([bad], native.default_settings(precision=native.GPUSLS_FP64))
+    with pytest.raises(RuntimeError, match="failed with not_spd"):
+        b.solve()
+    b.close()
+
+
+def test_bounded_wait_gives_up_with_timeout_status(lib, monkeypatch):
+    """The test hook GPUSLS_TEST_WAIT_TIMEOUT makes every solve wait once
+    (bounded) on a copy barrier that nothing completes: the wait gives up,
+    the solve reports GPUSLS_ERR_TIMEOUT, and the context stays usable (a
+    later solve without the hook converges)."""
+    import torch
+
+    from paper_2604_07644_b300.api import QPBatch
+    qp = W.plain_4d(0)
+    s = native.default_settings(precision=native.GPUSLS_FP32, max_iter=200)
+    monkeypatch.setenv("GPUSLS_TEST_WAIT_TIMEOUT", "1")
+    b = QPBatch([qp], s)
+    with pytest.raises(RuntimeError, match="failed with timeout"):
+        b.solve()
+    b.close()
+    monkeypatch.delenv("GPUSLS_TEST_WAIT_TIMEOUT")
+    torch.cuda.synchronize()
+    b = QPBatch([qp], s)
+    r = b.solve()
+    b.close()
+    assert r.info[0]["status"] == native.GPUSLS_OK

@@ -93,3 +93,33 @@ def test_training_reduces_loss(lib):
         l = m.train_step(Xt, Tt, 1e-3)
     assert l < 0.1 * l0
     m.close()
+
+
+def test_save_and_load_round_trip(lib, tmp_path):
+    """mlp_save writes parameters and normalization; mlp_load into a fresh
+    handle of the same sizes reproduces the network bit for bit; a file of
+    other sizes, a truncated or a foreign file is rejected with
+    GPUSLS_ERR_INVALID and leaves the handle unchanged."""
+    from paper_2604_07644_b300.api import MLP
+    m, params, X, T = make(37, 96, 20, 16, 4)
+    Xt = torch.from_numpy(X.astype(np.float32)).cuda()
+    Tt = torch.from_numpy(T.astype(np.float32)).cuda()
+    m.fit_normalization(Xt, Tt)
+    y0 = m.forward(Xt).cpu().numpy()
+    path = str(tmp_path / "net.bin")
+    m.save(path)
+    m2 = MLP(37, 96, 20, max_batch=16)
+    m2.load(path)
+    assert np.array_equal(m2.forward(Xt).cpu().numpy(), y0)
+    other = MLP(37, 64, 20, max_batch=16)
+    with pytest.raises(RuntimeError, match="failed with invalid"):
+        other.load(path)
+    raw = open(path, "rb").read()
+    (tmp_path / "short.bin").write_bytes(raw[:-4])
+    (tmp_path / "foreign.bin").write_bytes(b"NOTANMLP" + raw[8:])
+    for bad in ("short.bin", "foreign.bin", "missing.bin"):
+        with pytest.raises(RuntimeError, match="failed with invalid"):
+            m2.load(str(tmp_path / bad))
+    assert np.array_equal(m2.forward(Xt).cpu().numpy(), y0)
+    for h in (m, m2, other):
+        h.close()
