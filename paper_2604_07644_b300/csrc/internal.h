@@ -2,6 +2,7 @@
 // of the public C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
@@ -19,6 +20,16 @@ struct PackJob {
 
 struct QPOffsets {
   size_t A, B, c, Q, R, S, q, r, C, D, CN, lohi, x0, dx, du, P, K;
+};
+
+// NVTX range over a host entry point ("gpusls/<call>"): visible to profilers
+// that record NVTX (e.g. `ncu --nvtx --nvtx-include "gpusls/qp_solve/"`),
+// free otherwise.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 }  // namespace gsls

@@ -466,6 +466,7 @@ extern "C" int mlp_gradients(mlp_handle* h, const float* Xn, const float* Tn, in
 }
 
 extern "C" int mlp_train_step(mlp_handle* h, const float* X, const float* T, int32_t B, float lr, float* loss) {
+  gsls::NvtxRange nvtx_("gpusls/mlp_train_step");
   if (!h || !X || !T || B < 1 || B > h->maxb) return set_error(GPUSLS_ERR_INVALID, "mlp_train_step: invalid argument");
   // normalized inputs and targets (targets into dH scratch region sized B * max(hid, n_out))
   affine_rows_kernel<<<blocks((size_t)B * h->n_in), 256, 0, h->stream>>>(X, h->Xn, h->xm, h->xs, B, h->n_in, 0);
@@ -783,6 +784,7 @@ int check_heads(qp_handle* q, int32_t n_heads, mlp_handle* const* heads, const i
 extern "C" int qp_warm_start_heads(qp_handle* q, int32_t n_heads, mlp_handle* const* heads,
                                    const int32_t* const* idx, const int32_t* counts, const int32_t* n_stage,
                                    const double* x0, double rho_min, double rho_max) {
+  gsls::NvtxRange nvtx_("gpusls/qp_warm_start_heads");
   std::vector<int> smem;
   int st = check_heads(q, n_heads, heads, idx, counts, n_stage, smem);
   if (st) return st;

@@ -398,6 +398,7 @@ int update_qp(sqp_handle* h) {
 
 extern "C" int sqp_solve(sqp_handle* h, double* X, double* U, const double* x0bar, int32_t iters, double merit_w,
                          int32_t line_search, double* alpha_out, qp_info* info) {
+  gsls::NvtxRange nvtx_("gpusls/sqp_solve");
   if (!h || !X || !U || !x0bar || iters < 1) return set_error(GPUSLS_ERR_INVALID, "sqp_solve: bad argument");
   const int B = h->batch, nx = h->d.nx, nu = h->d.nu, N = h->d.N;
   std::vector<double> a(B), phi0(B), phi(B);
@@ -447,6 +448,7 @@ extern "C" int sqp_solve(sqp_handle* h, double* X, double* U, const double* x0ba
 
 extern "C" int rti_step(sqp_handle* h, double* X, double* U, double* x, const double* W, double* u_applied,
                         double* hk, double* hf, qp_info* info) {
+  gsls::NvtxRange nvtx_("gpusls/rti_step");
   if (!h || !X || !U || !x) return set_error(GPUSLS_ERR_INVALID, "rti_step: null argument");
   const int B = h->batch, nx = h->d.nx, nu = h->d.nu, N = h->d.N;
   int st = launch_linearize(&h->m, B, X, U, x, h->lin, h->st);

@@ -294,6 +294,7 @@ extern "C" int qp_batch_setup(qp_handle** out, int32_t batch, const qp_dims* dim
                               const double* c, const double* Q, const double* R, const double* S, const double* q,
                               const double* r, const double* C, const double* D, const double* CN, const double* lo,
                               const double* hi, const double* rho, const qp_settings* s, void* stream) {
+  gsls::NvtxRange nvtx_("gpusls/qp_batch_setup");
   if (!out || batch < 1 || !dims || !A || !B || !c || !Q || !R || !q || !r || !lo || !hi || !s)
     return fail(GPUSLS_ERR_INVALID, "qp_batch_setup: null argument or batch < 1");
   if (s->precision != GPUSLS_FP64 && s->precision != GPUSLS_FP32 && s->precision != GPUSLS_TF32 &&
@@ -649,6 +650,7 @@ static int launch_solve(qp_handle* h, const SolveArgs& a) {
 
 extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double tol, double* dx, double* du,
                         double* lam, qp_info* info) {
+  gsls::NvtxRange nvtx_("gpusls/qp_solve");
   if (!h || !x0 || !dx || !du || !lam) return fail(GPUSLS_ERR_INVALID, "qp_solve: null argument");
   int st = set_x0(h, x0);
   if (st) return st;
@@ -809,6 +811,7 @@ extern "C" int qp_graph_create_heads(qp_graph** out, qp_handle* h, int32_t n_hea
 }
 
 extern "C" int qp_graph_launch(qp_graph* g, void* stream) {
+  gsls::NvtxRange nvtx_("gpusls/qp_graph_launch");
   if (!g || !g->exec) return fail(GPUSLS_ERR_INVALID, "qp_graph_launch: null graph");
   CU(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
   return GPUSLS_OK;
@@ -855,6 +858,7 @@ int gsls::qp_refactor_internal(qp_handle* h, bool gains_only) {
 
 extern "C" int qp_kkt(qp_handle* h, const double* x0, const double* dx, const double* du, const double* lam,
                       double* out) {
+  gsls::NvtxRange nvtx_("gpusls/qp_kkt");
   if (!h || !x0 || !dx || !du || !lam || !out) return fail(GPUSLS_ERR_INVALID, "qp_kkt: null argument");
   int st = set_x0(h, x0);
   if (st) return st;
@@ -943,6 +947,7 @@ extern "C" int qp_get_state(qp_handle* h, double* z, double* y, double* rho) {
 extern "C" int qp_update(qp_handle* h, const double* A, const double* B, const double* c, const double* Q,
                          const double* R, const double* S, const double* q, const double* r, const double* C,
                          const double* D, const double* CN, const double* lo, const double* hi) {
+  gsls::NvtxRange nvtx_("gpusls/qp_update");
   if (!h) return fail(GPUSLS_ERR_INVALID, "qp_update: null handle");
   std::vector<PackJob> jobs;
   const bool refac = A || B || c || Q || R || S || q || r || C || D || CN;

@@ -429,6 +429,7 @@ extern "C" int sls_setup_ex(sls_handle** out, qp_dims d, int32_t precision, int3
 extern "C" int sls_solve(sls_handle* h, const double* A, const double* B, const double* E, const double* Qbar,
                          const double* Rbar, const double* QbarN, const double* C, const double* D, const double* CN,
                          const double* tau, double* Phi_x, double* Phi_u, double* hk, double* hf) {
+  gsls::NvtxRange nvtx_("gpusls/sls_solve");
   if (!h || !A || !B || !E || !Qbar || !Rbar || !QbarN) return set_error(GPUSLS_ERR_INVALID, "sls_solve: null argument");
   const qp_dims d = h->d;
   const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf;
@@ -498,6 +499,7 @@ extern "C" int sls_solve(sls_handle* h, const double* A, const double* B, const 
 }
 
 extern "C" int sls_tau(sls_handle* h, const double* lam, double eps, double* tau) {
+  gsls::NvtxRange nvtx_("gpusls/sls_tau");
   if (!h || !lam || !tau) return set_error(GPUSLS_ERR_INVALID, "sls_tau: null argument");
   if (!h->solved) return set_error(GPUSLS_ERR_INVALID, "sls_tau: no sls_solve has run on this handle");
   if (!(eps > 0.0)) return set_error(GPUSLS_ERR_INVALID, "sls_tau: eps must be positive");
@@ -517,6 +519,7 @@ extern "C" int fastsls_solve(qp_handle* q, sls_handle* s, const double* A, const
                              int32_t iters, double eps_tau, const double* tau_in, double* tau_out, double* dx,
                              double* du, double* lam, double* Phi_x, double* Phi_u, double* hk, double* hf,
                              qp_info* info) {
+  gsls::NvtxRange nvtx_("gpusls/fastsls_solve");
   if (!q || !s || !lo || !hi || !x0 || !dx || !du || !lam || !hk || (s->d.nf > 0 && !hf))
     return set_error(GPUSLS_ERR_INVALID, "fastsls_solve: null argument");
   if (!s->per_j || !s->tau) return set_error(GPUSLS_ERR_INVALID, "fastsls_solve: the SLS handle needs per-j tau");
