@@ -817,6 +817,52 @@ __device__ __noinline__ int warp_spd_inverse_as(const T* G, int ldg, int n, T* G
   return f;
 }
 
+// Inverse of a symmetric positive definite n x n matrix by the whole CTA:
+// Gauss-Jordan in place in Gi without pivoting (the diagonal pivots of an SPD
+// matrix are positive).  Step k copies pivot row and column to prow / pcol
+// (shared, >= n elements each), then every thread updates its elements:
+//   g_kk <- 1/p,  g_kj <- g_kj / p,  g_ik <- -g_ik / p,  g_ij <- g_ij - g_ik g_kj / p.
+// Two CTA barriers per pivot; used for n > 16, where one warp's unrolled
+// chains of shuffles (warp_spd_inverse) grow with 32-wide registers rows.  G
+// and Gi shared, not aliased.  Returns 1 in every thread if a pivot was not
+// positive.  flag: shared int.
+template <typename T>
+__device__ __noinline__ int cta_spd_inverse(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag, T* prow,
+                                            T* pcol) {
+  const int t = threadIdx.x, nn = n * n;
+  for (int e = t; e < nn; e += NT) {
+    const int i = e / n, j = e - i * n;
+    Gi[i * ldgi + j] = G[i * ldg + j];
+  }
+  if (t == 0) flag[0] = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (t < n) {
+      prow[t] = Gi[k * ldgi + t];
+      pcol[t] = Gi[t * ldgi + k];
+    }
+    __syncthreads();
+    T p = prow[k];
+    if (!(p > T(0))) {
+      if (t == 0) flag[0] = 1;
+      p = T(1);
+    }
+    const T ip = T(1) / p;
+    for (int e = t; e < nn; e += NT) {
+      const int i = e / n, j = e - i * n;
+      T v;
+      if (i == k) v = j == k ? ip : prow[j] * ip;
+      else if (j == k) v = -pcol[i] * ip;
+      else v = fma(-(pcol[i] * ip), prow[j], Gi[i * ldgi + j]);
+      Gi[i * ldgi + j] = v;
+    }
+    __syncthreads();
+  }
+  const int f = flag[0];
+  __syncthreads();
+  return f;
+}
+
 template <typename T, int CAP>
 __device__ __noinline__ int warp_spd_inverse(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag) {
   return warp_spd_inverse_as<T, T, CAP>(G, ldg, n, Gi, ldgi, flag);

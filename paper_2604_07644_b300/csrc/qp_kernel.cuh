@@ -609,7 +609,7 @@ __device__ inline int small_spd_inverse(Ctx<T>& c, const T* G, int ldg, int n, T
     return warp_spd_inverse_as<T, double, FACT_MAX_NU>(G, ldg, n, Gi, ldgi, c.flag + 1);
   }
   if (n <= 16) return warp_spd_inverse<T, 16>(G, ldg, n, Gi, ldgi, c.flag + 1);
-  return warp_spd_inverse<T, FACT_MAX_NU>(G, ldg, n, Gi, ldgi, c.flag + 1);
+  return cta_spd_inverse<T>(G, ldg, n, Gi, ldgi, c.flag + 1, c.tmp1, c.tmp2);
 }
 
 // Phase A step: (P, Aa, Cacc) <- e_i (x) (P, Aa, Cacc).  Cacc stays in global
