@@ -33,6 +33,13 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "ms/QP solve to 1e-4 KKT residual (61D, N=100): learned+batched vs plain ADMM"
+EPS_KKT = 1e-4           # the certified FP64 KKT tolerance of the metric
+# In-loop residual tolerance of every 1e-4 solve here (GPU, plain FP64 GPU
+# and the CPU oracle alike): half the KKT tolerance.  At eps = 1e-4 the first
+# KKT gate usually fails and the tightening overshoots to 1e-5; chosen on
+# validation instances 300000..300255 (1e-4: 0.477, 5e-5: 0.455, 3e-5: 0.451,
+# 2e-5: 0.459 ms/QP) and the learned serving mix (0.556, 0.545, 0.552).
+EPS_IN = 0.5 * EPS_KKT
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
 TRAFFIC_PER_QP_ITER = 5.99e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6, 45 QPs)
@@ -168,7 +175,7 @@ def _oracle_worker(idx):
     from oracle import admm
     from paper_2604_07644_b300 import workloads as W
     qp = W.family(0).instance(idx)
-    r = admm.admm(qp, admm.Settings(eps=1e-4, eps_kkt=1e-4))
+    r = admm.admm(qp, admm.Settings(eps=EPS_IN, eps_kkt=EPS_KKT))
     return idx, r.iters, r.x, r.u
 
 
@@ -200,14 +207,14 @@ def host_cpu():
     return {"nproc": os.cpu_count(), "usable": len(os.sched_getaffinity(0)), "model": model}
 
 
-def cpu_oracle_ms_per_qp(qps, eps=1e-4, results=None):
+def cpu_oracle_ms_per_qp(qps, eps=EPS_KKT, results=None):
     """The FP64 oracle as it stands on this host (single thread); the solutions
     are appended to `results` when given."""
     from oracle import admm
     t0 = time.perf_counter()
     iters = []
     for qp in qps:
-        r = admm.admm(qp, admm.Settings(eps=eps, eps_kkt=eps))
+        r = admm.admm(qp, admm.Settings(eps=0.5 * eps, eps_kkt=eps))
         iters.append(r.iters)
         if results is not None:
             results.append(r)
@@ -274,7 +281,8 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
     from paper_2604_07644_b300.api import SLS, QPBatch
     out = {}
     steps = max(1, args.steps)
-    base = dict(precision=native.GPUSLS_FP32, cluster=8, max_refine=3, max_iter=6000, schedule=1)
+    base = dict(precision=native.GPUSLS_FP32, cluster=8, max_refine=3, max_iter=6000, schedule=1, eps=EPS_IN,
+                eps_kkt=EPS_KKT)
 
     def batch_run(name, qps_, cluster, precision=native.GPUSLS_FP32):
         s = native.default_settings(**dict(base, cluster=cluster, precision=precision))
@@ -600,7 +608,7 @@ def main():
     qps = [fam.instance(base + i) for i in range(args.batch)]
     nx, nu, N, nc, nf = qps[0].dims()
     settings = native.default_settings(precision=prec, cluster=args.cluster, max_refine=3,
-                                       fallback_iters=args.fallback, max_iter=6000,
+                                       fallback_iters=args.fallback, max_iter=6000, eps=EPS_IN, eps_kkt=EPS_KKT,
                                        eps_floor=1e-7 if prec == native.GPUSLS_FP64 else 1e-5,
                                        schedule=0 if args.index_order else 1)
     tuned = None
@@ -684,7 +692,8 @@ def main():
     if prec == native.GPUSLS_FP32:
         sm = native.default_settings(precision=native.GPUSLS_MIXED, cluster=int(settings.cluster),
                                      occupancy=int(settings.occupancy), max_refine=3, fallback_iters=args.fallback,
-                                     max_iter=6000, eps_floor=1e-5, schedule=0 if args.index_order else 1)
+                                     max_iter=6000, eps_floor=1e-5, eps=EPS_IN, eps_kkt=EPS_KKT,
+                                     schedule=0 if args.index_order else 1)
         with torch.cuda.stream(stream):
             hm = QPBatch(qps, sm, stream=stream, device=dev, pools=hb.pools)
             gm = hm.graph(heads=heads)
@@ -704,7 +713,8 @@ def main():
     # plain FP64 single-QP solves (cold, one QP per launch)
     plain = []
     for i in range(args.plain_qps):
-        hp = QPBatch([qps[i]], native.default_settings(precision=native.GPUSLS_FP64, cluster=args.cluster),
+        hp = QPBatch([qps[i]], native.default_settings(precision=native.GPUSLS_FP64, cluster=args.cluster,
+                                                       eps=EPS_IN, eps_kkt=EPS_KKT),
                      stream=stream, device=dev)
         with torch.cuda.stream(stream):
             hp.reset()
