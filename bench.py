@@ -810,7 +810,9 @@ def main():
                          f"per worker process over {procs} cores; value = wall time / QPs; "
                          f"mean iters {np.mean(it_cpu):.0f}"}
     extra = {}
-    if rank == 0 and not args.no_extras:
+    # the further workloads once, in the single-GPU run (a scaling run holds
+    # every GPU while rank 0 works)
+    if rank == 0 and ws == 1 and not args.no_extras:
         extra = extra_workloads(args, qps, sol_w, stream, dev, oracle_sols)
 
     pk, pk_kind = peaks()
