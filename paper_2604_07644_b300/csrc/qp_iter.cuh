@@ -735,12 +735,13 @@ __device__ void write_outputs(Ctx<T>& c, T rho) {
   __syncthreads();
 }
 
-// FP64 KKT residual of (ox, ou, olam) -- see include/gpusls.h for the
-// definition.  Every CTA evaluates the stage-local parts of its chunk; CTA 0
-// then runs the costate recursion mu_k = g_k + A_k^T mu_{k+1} sequentially.
-// FP64 KKT residual of the outputs written by write_outputs (see the
-// library's residual definition): dynamics, bound violation, u-stationarity
-// after costate recovery and complementarity, max over the cluster.
+// FP64 KKT residual of the outputs written by write_outputs (the definition
+// is the library's, see include/gpusls.h): dynamics, bound violation,
+// u-stationarity after costate recovery and complementarity, max over the
+// cluster.  Every CTA evaluates the stage-local parts of its chunk, with the
+// stage's Q_i, A_i and C_i copied into shared memory (coalesced, by
+// cp.async) when the union region holds them; CTA 0 then runs the costate
+// recursion mu_k = g_k + A_k^T mu_{k+1} sequentially.
 template <typename T>
 __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
   QPDesc& d = *c.d;
@@ -759,6 +760,11 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
   double* du = cx + 96;   // D u
   double* gt = du + 96;   // C^T lam + S^T u
   double* ht = gt + 96;   // D^T lam
+  // Q_i, A_i, C_i of the stage in shared memory after the vectors
+  double* Qs = ht + 96;
+  double* As = Qs + nx * nx;
+  double* Cs = As + nx * nx;
+  const bool stg = (13 * 96 + 2 * nx * nx + (nc > nf ? nc : nf) * nx) * 8 <= c.uni;
   double dyn = 0.0, viol = 0.0, comp = 0.0, stat = 0.0;
   long long kt0 = c.prof ? clock64() : 0;
   cl.sync();   // outputs of every chunk visible
@@ -767,16 +773,27 @@ __device__ __noinline__ double kkt_eval(Ctx<T>& c, cg::cluster_group& cl) {
     for (int i = c.s; i < iend; ++i) {
       const bool term = (i == N);
       const int nr = term ? nf : nc;
+      const double* Qg = d.Q64 + (size_t)i * nx * nx;
+      const double* Cg = term ? d.CN64 : d.C64 + (size_t)i * nc * nx;
+      const double* Ag = d.A64 + (size_t)i * nx * nx;
+      if (stg) {   // the caller's rows are unpadded: 8-byte copies
+        for (int e2 = t; e2 < nx * nx; e2 += NT) cp_async_elem<double>(Qs + e2, Qg + e2);
+        if (!term)
+          for (int e2 = t; e2 < nx * nx; e2 += NT) cp_async_elem<double>(As + e2, Ag + e2);
+        for (int e2 = t; e2 < nr * nx; e2 += NT) cp_async_elem<double>(Cs + e2, Cg + e2);
+        cp_async_commit();
+      }
       for (int j = t; j < nx; j += NT) {
         xv[j] = d.ox[(size_t)i * nx + j];
         if (!term) xn[j] = d.ox[(size_t)(i + 1) * nx + j];
       }
       for (int a = t; a < nu; a += NT) uv[a] = term ? 0.0 : d.ou[(size_t)i * nu + a];
       for (int k = t; k < nr; k += NT) lv[k] = d.olam[(size_t)i * nc + k];
+      if (stg) cp_async_wait<0>();
       __syncthreads();
-      const double* Qi = d.Q64 + (size_t)i * nx * nx;
-      const double* Ci = term ? d.CN64 : d.C64 + (size_t)i * nc * nx;
-      const double* Ai = d.A64 + (size_t)i * nx * nx;
+      const double* Qi = stg ? Qs : Qg;
+      const double* Ci = stg ? Cs : Cg;
+      const double* Ai = stg ? As : Ag;
       const double* Bi = d.B64 + (size_t)i * nx * nu;
       const double* Si = d.S64 + (size_t)i * nu * nx;
       const double* Ri = d.R64 + (size_t)i * nu * nu;
