@@ -52,13 +52,14 @@ def batch_qps():
 def headline_solve(qps, eps_kkt, max_refine=3, precision=native.GPUSLS_FP32):
     """The benchmark's launch: tuned shape (cluster 6, two CTAs per SM),
     longest-expected-first order, learned warm start, one graph per step,
-    in-loop tolerance half the KKT tolerance; the second replay is read (its
-    order comes from the first)."""
+    in-loop tolerance half the KKT tolerance, a stop test every 10
+    iterations; the second replay is read (its order comes from the
+    first)."""
     from paper_2604_07644_b300 import learned
     from paper_2604_07644_b300.api import QPBatch
     s = native.default_settings(precision=precision, cluster=6, occupancy=0, max_refine=max_refine,
                                 fallback_iters=2000, max_iter=6000, eps=0.5 * eps_kkt, eps_kkt=eps_kkt,
-                                eps_floor=min(1e-5, 0.1 * eps_kkt), schedule=1)
+                                eps_floor=min(1e-5, 0.1 * eps_kkt), schedule=1, check_every=10)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         qb = QPBatch(qps, s, stream=stream)
