@@ -45,6 +45,11 @@ EPS_IN = 0.5 * EPS_KKT
 # default 5, chosen on the same validation instances (5: 0.453, 10: 0.441,
 # 15: 0.438 ms/QP at the same iteration counts).
 CHECK_EVERY = 10
+# rho-update interval (every sigma iterations) of the same solves: 50 instead
+# of the library's default 25, chosen on the same validation instances
+# (learned 25: 0.443, 50: 0.428, 100: 0.421 ms/QP at the same iterations;
+# cold 25: 0.818 / 381 iterations, 50: 0.735 / 342, 100: 0.804 / 408).
+SIGMA = 50
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
 TRAFFIC_PER_QP_ITER = 5.99e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6, 45 QPs)
@@ -180,7 +185,7 @@ def _oracle_worker(idx):
     from oracle import admm
     from paper_2604_07644_b300 import workloads as W
     qp = W.family(0).instance(idx)
-    r = admm.admm(qp, admm.Settings(eps=EPS_IN, eps_kkt=EPS_KKT, check_every=CHECK_EVERY))
+    r = admm.admm(qp, admm.Settings(eps=EPS_IN, eps_kkt=EPS_KKT, check_every=CHECK_EVERY, sigma=SIGMA))
     return idx, r.iters, r.x, r.u
 
 
@@ -219,7 +224,7 @@ def cpu_oracle_ms_per_qp(qps, eps=EPS_KKT, results=None):
     t0 = time.perf_counter()
     iters = []
     for qp in qps:
-        r = admm.admm(qp, admm.Settings(eps=0.5 * eps, eps_kkt=eps, check_every=CHECK_EVERY))
+        r = admm.admm(qp, admm.Settings(eps=0.5 * eps, eps_kkt=eps, check_every=CHECK_EVERY, sigma=SIGMA))
         iters.append(r.iters)
         if results is not None:
             results.append(r)
@@ -287,7 +292,7 @@ def extra_workloads(args, qps, sol, stream, dev, oracle_sols):
     out = {}
     steps = max(1, args.steps)
     base = dict(precision=native.GPUSLS_FP32, cluster=8, max_refine=3, max_iter=6000, schedule=1, eps=EPS_IN,
-                eps_kkt=EPS_KKT, check_every=CHECK_EVERY)
+                eps_kkt=EPS_KKT, check_every=CHECK_EVERY, sigma=SIGMA)
 
     def batch_run(name, qps_, cluster, precision=native.GPUSLS_FP32):
         s = native.default_settings(**dict(base, cluster=cluster, precision=precision))
@@ -614,7 +619,7 @@ def main():
     nx, nu, N, nc, nf = qps[0].dims()
     settings = native.default_settings(precision=prec, cluster=args.cluster, max_refine=3,
                                        fallback_iters=args.fallback, max_iter=6000, eps=EPS_IN, eps_kkt=EPS_KKT,
-                                       check_every=CHECK_EVERY,
+                                       check_every=CHECK_EVERY, sigma=SIGMA,
                                        eps_floor=1e-7 if prec == native.GPUSLS_FP64 else 1e-5,
                                        schedule=0 if args.index_order else 1)
     tuned = None
@@ -699,7 +704,7 @@ def main():
         sm = native.default_settings(precision=native.GPUSLS_MIXED, cluster=int(settings.cluster),
                                      occupancy=int(settings.occupancy), max_refine=3, fallback_iters=args.fallback,
                                      max_iter=6000, eps_floor=1e-5, eps=EPS_IN, eps_kkt=EPS_KKT,
-                                     check_every=CHECK_EVERY,
+                                     check_every=CHECK_EVERY, sigma=SIGMA,
                                      schedule=0 if args.index_order else 1)
         with torch.cuda.stream(stream):
             hm = QPBatch(qps, sm, stream=stream, device=dev, pools=hb.pools)
@@ -721,7 +726,8 @@ def main():
     plain = []
     for i in range(args.plain_qps):
         hp = QPBatch([qps[i]], native.default_settings(precision=native.GPUSLS_FP64, cluster=args.cluster,
-                                                       eps=EPS_IN, eps_kkt=EPS_KKT, check_every=CHECK_EVERY),
+                                                       eps=EPS_IN, eps_kkt=EPS_KKT, check_every=CHECK_EVERY,
+                                                       sigma=SIGMA),
                      stream=stream, device=dev)
         with torch.cuda.stream(stream):
             hp.reset()
