@@ -664,6 +664,16 @@ extern "C" int qp_solve(qp_handle* h, const double* x0, int32_t iters, double to
 // ---------------------------------------------------------------------------
 // serving graph
 // ---------------------------------------------------------------------------
+// qp_update: mark every QP's factorization stale (flags[0]) and its state
+// as not warm-started (flags[1]).
+__global__ void flags_clear_kernel(const QPDesc* __restrict__ descs, int batch) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch) {
+    descs[b].flags[0] = 0;
+    descs[b].flags[1] = 0;
+  }
+}
+
 template <typename T>
 __global__ void reset_kernel(const QPDesc* __restrict__ descs, const double* __restrict__ rho0);
 
@@ -951,39 +961,44 @@ extern "C" int qp_update(qp_handle* h, const double* A, const double* B, const d
   if (!h) return fail(GPUSLS_ERR_INVALID, "qp_update: null handle");
   std::vector<PackJob> jobs;
   const bool refac = A || B || c || Q || R || S || q || r || C || D || CN;
+  // the FP64 copies mirror the caller's pool layout (per-QP blocks
+  // concatenated), so each array kind is one device-to-device copy for the
+  // whole batch; the padded solve-precision copies are pack jobs per QP
+  const double* srcs[13] = {A, B, c, Q, R, S, q, r, C, D, CN, lo, hi};
+  size_t n64[13] = {};
   for (int b = 0; b < h->batch; ++b) {
     const qp_dims& d = h->dims[b];
     const QPDesc& D_ = h->hdesc[b];
     const QPOffsets& po = h->off[b];
     const int nx = d.nx, nu = d.nu, N = d.N, nc = d.nc, nf = d.nf, m = N * nc + nf;
     const int ldx = D_.ldx, ldu = D_.ldu;
-    auto add = [&](const double* src, size_t o, void* dst, int count, int rows, int cols, int ld, double* d64,
-                   size_t n64) -> int {
-      if (!src || n64 == 0) return GPUSLS_OK;
-      jobs.push_back({src + o, dst, count, rows, cols, ld});
-      CU(cudaMemcpyAsync(d64, src + o, n64 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-      return GPUSLS_OK;
+    auto add = [&](int k, size_t o, void* dst, int count, int rows, int cols, int ld, size_t n) {
+      n64[k] += n;
+      if (srcs[k] && n > 0) jobs.push_back({srcs[k] + o, dst, count, rows, cols, ld});
     };
-    int st = GPUSLS_OK;
-    st |= add(A, po.A, D_.A, N, nx, nx, ldx, D_.A64, (size_t)N * nx * nx);
-    st |= add(B, po.B, D_.B, N, nx, nu, ldu, D_.B64, (size_t)N * nx * nu);
-    st |= add(c, po.c, D_.b, N, 1, nx, ldx, D_.b64, (size_t)N * nx);
-    st |= add(Q, po.Q, D_.Q, N + 1, nx, nx, ldx, D_.Q64, (size_t)(N + 1) * nx * nx);
-    st |= add(R, po.R, D_.R, N, nu, nu, ldu, D_.R64, (size_t)N * nu * nu);
-    st |= add(S, po.S, D_.S, N, nu, nx, ldx, D_.S64, (size_t)N * nu * nx);
-    st |= add(q, po.q, D_.q, N + 1, 1, nx, ldx, D_.q64, (size_t)(N + 1) * nx);
-    st |= add(r, po.r, D_.r, N, 1, nu, ldu, D_.r64, (size_t)N * nu);
-    st |= add(C, po.C, D_.C, N, nc, nx, ldx, D_.C64, (size_t)N * nc * nx);
-    st |= add(D, po.D, D_.D, N, nc, nu, ldu, D_.D64, (size_t)N * nc * nu);
-    st |= add(CN, po.CN, D_.CN, 1, nf, nx, ldx, D_.CN64, (size_t)nf * nx);
-    st |= add(lo, po.lohi, D_.lo, 1, 1, m, m, D_.lo64, (size_t)m);
-    st |= add(hi, po.lohi, D_.hi, 1, 1, m, m, D_.hi64, (size_t)m);
-    if (st) return GPUSLS_ERR_CUDA;
+    add(0, po.A, D_.A, N, nx, nx, ldx, (size_t)N * nx * nx);
+    add(1, po.B, D_.B, N, nx, nu, ldu, (size_t)N * nx * nu);
+    add(2, po.c, D_.b, N, 1, nx, ldx, (size_t)N * nx);
+    add(3, po.Q, D_.Q, N + 1, nx, nx, ldx, (size_t)(N + 1) * nx * nx);
+    add(4, po.R, D_.R, N, nu, nu, ldu, (size_t)N * nu * nu);
+    add(5, po.S, D_.S, N, nu, nx, ldx, (size_t)N * nu * nx);
+    add(6, po.q, D_.q, N + 1, 1, nx, ldx, (size_t)(N + 1) * nx);
+    add(7, po.r, D_.r, N, 1, nu, ldu, (size_t)N * nu);
+    add(8, po.C, D_.C, N, nc, nx, ldx, (size_t)N * nc * nx);
+    add(9, po.D, D_.D, N, nc, nu, ldu, (size_t)N * nc * nu);
+    add(10, po.CN, D_.CN, 1, nf, nx, ldx, (size_t)nf * nx);
+    add(11, po.lohi, D_.lo, 1, 1, m, m, (size_t)m);
+    add(12, po.lohi, D_.hi, 1, 1, m, m, (size_t)m);
   }
-  if (refac) {
-    std::vector<int> zero(2 * h->batch, 0);
-    for (int b = 0; b < h->batch; ++b)
-      CU(cudaMemcpyAsync(h->hdesc[b].flags, zero.data(), 2 * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  const QPDesc& D0 = h->hdesc[0];
+  double* dst64[13] = {D0.A64, D0.B64, D0.b64, D0.Q64, D0.R64, D0.S64, D0.q64, D0.r64, D0.C64, D0.D64,
+                       D0.CN64, D0.lo64, D0.hi64};
+  for (int k = 0; k < 13; ++k)
+    if (srcs[k] && n64[k] > 0)
+      CU(cudaMemcpyAsync(dst64[k], srcs[k], n64[k] * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (refac) {   // the factorization of every QP is stale
+    flags_clear_kernel<<<(h->batch + 255) / 256, 256, 0, h->stream>>>(h->ddesc, h->batch);
+    CU(cudaGetLastError());
   }
   int st = run_pack(h, jobs);
   if (st) return st;

@@ -155,3 +155,31 @@ def test_longest_first_schedule_changes_only_the_order(lib, graph):
         assert [i["iters"] for i in info1] == [i["iters"] for i in info0]
     q0.close()
     q1.close()
+
+
+@pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32])
+def test_update_of_every_array_equals_a_fresh_handle(lib, prec):
+    """qp_update of every problem array on a ragged batch (one device copy
+    per array kind for the whole batch, pack jobs per QP): the next solve,
+    its statuses, iteration counts and FP64 KKT residuals equal those of a
+    handle set up from the new data."""
+    keys = ("A", "B", "c", "Q", "R", "S", "q", "r", "C", "D", "CN", "lo", "hi")
+    old = [W.random_general(11, 6, 2, 17, 4, 2), W.random_general(12, 4, 3, 9, 0, 3),
+           W.random_general(13, 7, 2, 23, 5, 0)]
+    new = [W.random_general(21, 6, 2, 17, 4, 2), W.random_general(22, 4, 3, 9, 0, 3),
+           W.random_general(23, 7, 2, 23, 5, 0)]
+    for a, b in zip(old, new):
+        b.x0 = a.x0.copy()   # x0 is not part of qp_update
+    st = native.default_settings(precision=prec, cluster=2)
+    qb = QPBatch(old, st)
+    qb.solve()
+    qb.update(**{k: [getattr(q, k) for q in new] for k in keys})
+    qb.reset()
+    r = qb.solve()
+    got = _snapshot(qb)
+    qb.close()
+    qe = QPBatch(new, st)
+    ref, info = _eager(qe)
+    qe.close()
+    assert _same(got, ref)
+    assert [(i["status"], i["iters"], i["kkt"]) for i in r.info] == [(i["status"], i["iters"], i["kkt"]) for i in info]
