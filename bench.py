@@ -52,7 +52,7 @@ CHECK_EVERY = 10
 SIGMA = 50
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
-TRAFFIC_PER_QP_ITER = 5.99e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6, 45 QPs)
+TRAFFIC_PER_QP_ITER = 6.03e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6, 45 QPs)
 
 
 def parse():
