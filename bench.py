@@ -73,7 +73,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the serving-mix / humanoid / SLS measurements")
     p.add_argument("--index-order", action="store_true",
                    help="launch QPs in index order instead of longest-expected-first")
-    p.add_argument("--case", default="", choices=["", "iter", "refactor", "mlp", "sls"],
+    p.add_argument("--case", default="", choices=["", "iter", "refactor", "mlp", "sls", "long"],
                    help="small fixed case for profiler captures (prints no bench line)")
     p.add_argument("--case-batch", type=int, default=32, help="QPs of the iter / refactor profiling cases")
     p.add_argument("--model", default=os.path.join(ROOT, "paper_2604_07644_b300", "warmstart_quadruped61.npz"))
@@ -537,7 +537,10 @@ def profile_case(args):
       refactor  the same batch, three launches that each refactor and run one
                 iteration;
       mlp       the learned warm start of 256 QPs (BF16 tensor-core GEMMs);
-      sls       SLS synthesis at nx=75, nu=21, N=40 with per-j tau."""
+      sls       SLS synthesis at nx=75, nu=21, N=40 with per-j tau;
+      long      the N=3000 pendulum-shaped QP (nx=30, nu=15), cold FP32 to
+                the 1e-2 tolerance, automatic launch shape (16-CTA cluster),
+                two solves."""
     import torch
 
     from paper_2604_07644_b300 import build as B_
@@ -575,6 +578,16 @@ def profile_case(args):
             qb.warm_start_heads(heads)
         torch.cuda.synchronize()
         mlp.close()
+        qb.close()
+    elif args.case == "long":
+        qp = W.long_horizon(0)
+        s = native.default_settings(precision=native.GPUSLS_FP32, cluster=0, eps=1e-2, eps_kkt=1e-2,
+                                    eps_floor=1e-5, max_iter=20000)
+        qb = QPBatch([qp], s)
+        for _ in range(2):
+            qb.reset()
+            qb.solve(fetch=False)
+        torch.cuda.synchronize()
         qb.close()
     elif args.case == "sls":
         p = W.sls_problem(0, tau_mode="uniform")

@@ -25,8 +25,8 @@ namespace cg = cooperative_groups;
 namespace gsls {
 
 // CTAs per QP: up to 8 is the portable cluster size; 9..16 are non-portable
-// cluster sizes (long horizons, whose per-chunk vectors then fit shared
-// memory), launched only where the device schedules them.
+// cluster sizes (long horizons: shorter chunk chains), launched only where
+// the device schedules them.
 constexpr int MAXCS = 16;
 constexpr int MAXCS_PORTABLE = 8;
 

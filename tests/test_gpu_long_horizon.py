@@ -1,8 +1,8 @@
 """Long horizons (Sec. V-A's horizon study, N up to 3000): the torque-limited
 pendulum-shaped workload (nx=30, nu=15, N=3000, 1.35e5 decision variables),
 whose per-chunk vectors no longer fit a CTA's shared memory and live in a
-per-CTA global region at 8 CTAs per QP (at 16, a non-portable cluster size,
-they fit shared memory), against the FP64 oracle: the factorization against
+per-CTA global region (at 8 CTAs per QP, and at 16, a non-portable cluster
+size that halves the chunks), against the FP64 oracle: the factorization against
 the sequential Riccati recursion, iterates against the step-by-step ADMM,
 and an adaptive FP32 solve against the oracle's KKT measure.  The global-
 region path is also compared with the shared-memory path on a horizon both
