@@ -763,51 +763,47 @@ __device__ void cta_copy_vec(int m, int n, const T* X, int ldxs, T* Y, int ldy) 
 }
 
 // Inverse of a symmetric positive definite n x n matrix, n <= CAP <= 32, by
-// warp 0: Gauss-Jordan on [G | I] without pivoting (the diagonal pivots of an
-// SPD matrix are positive), lane i holding row i in registers and the pivot
-// row broadcast by shuffles.  G and Gi: shared or global, may not alias.
-// Returns 1 in every thread (after the closing barrier) if a pivot was not
-// positive.  flag: shared int.
-// Loads T, computes in A (GPUSLS_MIXED: FP32 operands, FP64 arithmetic),
-// stores T.
+// warp 0: Gauss-Jordan in place without pivoting (the diagonal pivots of an
+// SPD matrix are positive), lane i holding row i in registers and pivot row
+// k broadcast by shuffles, n columns per step:
+//   g_kk <- 1/p,  g_kj <- g_kj / p,  g_ik <- -g_ik / p,  g_ij <- g_ij - g_ik g_kj / p.
+// (Half the work of eliminating [G | I]; in FP64, GPUSLS_MIXED, the FP64
+// pipe sets the cost.)  G and Gi: shared or global, may not alias.  Returns
+// 1 in every thread (after the closing barrier) if a pivot was not positive.
+// flag: shared int.  Loads T, computes in A (GPUSLS_MIXED: FP32 operands,
+// FP64 arithmetic), stores T.
 template <typename T, typename A, int CAP>
 __device__ __noinline__ int warp_spd_inverse_as(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag) {
   if (threadIdx.x < 32) {
     const int l = threadIdx.x;
-    A a[CAP], b[CAP];
+    A g[CAP];
 #pragma unroll
-    for (int j = 0; j < CAP; ++j) {
-      a[j] = (l < n && j < n) ? (A)G[l * ldg + j] : (l == j ? A(1) : A(0));
-      b[j] = l == j ? A(1) : A(0);
-    }
+    for (int j = 0; j < CAP; ++j) g[j] = (l < n && j < n) ? (A)G[l * ldg + j] : (l == j ? A(1) : A(0));
     int bad = 0;
 #pragma unroll
     for (int k = 0; k < CAP; ++k) {
       if (k < n) {
-        A piv = __shfl_sync(0xffffffffu, a[k], k);
+        A piv = __shfl_sync(0xffffffffu, g[k], k);
         if (!(piv > A(0))) {
           bad = 1;
           piv = A(1);
         }
         const A ip = A(1) / piv;
-        const A f = l == k ? A(0) : a[k] * ip;
-        // columns < k of a are finished (e_j); only j >= k change
-#pragma unroll
-        for (int j = k; j < CAP; ++j) {
-          const A rk = __shfl_sync(0xffffffffu, a[j], k);
-          a[j] = l == k ? rk * ip : fma(-f, rk, a[j]);
-        }
+        const A f = g[k] * ip;   // g_lk / p (this lane's column-k entry before the step)
 #pragma unroll
         for (int j = 0; j < CAP; ++j) {
-          const A rk = __shfl_sync(0xffffffffu, b[j], k);
-          b[j] = l == k ? rk * ip : fma(-f, rk, b[j]);
+          if (j < n) {
+            const A rk = __shfl_sync(0xffffffffu, g[j], k);
+            if (l == k) g[j] = j == k ? ip : rk * ip;
+            else g[j] = j == k ? -f : fma(-f, rk, g[j]);
+          }
         }
       }
     }
     if (l < n) {
 #pragma unroll
       for (int j = 0; j < CAP; ++j)
-        if (j < n) Gi[l * ldgi + j] = (T)b[j];
+        if (j < n) Gi[l * ldgi + j] = (T)g[j];
     }
     if (l == 0) flag[0] = bad;
   }
