@@ -50,6 +50,7 @@ CHECK_EVERY = 10
 # (learned 25: 0.443, 50: 0.428, 100: 0.421 ms/QP at the same iterations;
 # cold 25: 0.818 / 381 iterations, 50: 0.735 / 342, 100: 0.804 / 408).
 SIGMA = 50
+WORKLOAD = "quadruped-shaped LTV-QP family (nx=61 nu=12 N=100 nc=20 nf=8), held-out instances 100000 + i"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
 TRAFFIC_PER_QP_ITER = 6.03e6   # bytes, ncu DRAM read+write per QP-iteration (61D, N=100, FP32, cluster 6, 45 QPs)
@@ -238,25 +239,25 @@ def run_reference(args, ws, rank):
         return
     from paper_2604_07644_b300 import workloads as W
     fam = W.family(0)
-    n = 0
-    for _ in range(args.warmup):
-        cpu_oracle_ms_per_qp([fam.instance(200000 + n)])
-        n += 1
+    # the QPs of this arm's batch (held-out instances 100000 + i), one per
+    # step; warm-up steps solve instances that the timed steps do not
+    for w in range(args.warmup):
+        cpu_oracle_ms_per_qp([fam.instance(100000 + args.batch - 1 - w)])
     t0 = time.perf_counter()
     iters = []
-    for _ in range(args.steps):
-        _, it = cpu_oracle_ms_per_qp([fam.instance(200000 + n)])
+    for n in range(args.steps):
+        _, it = cpu_oracle_ms_per_qp([fam.instance(100000 + n)])
         iters += it
-        n += 1
     dt = time.perf_counter() - t0
     ms = dt * 1e3 / args.steps
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms/QP", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "quadruped-shaped LTV-QP family, nx=61 nu=12 N=100 nc=20 nf=8",
-                       "batch": 1, "precision": "fp64", "solver": "CPU oracle ADMM (sequential Riccati)"},
+            "config": {"workload": WORKLOAD, "batch": args.batch, "precision": "fp64",
+                       "solver": "CPU oracle ADMM (sequential Riccati), the same solver settings"},
             "cpu_baseline": {"value": ms, "unit": "ms/QP", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} QPs, one per step, single thread; iters {iters}"},
+                             "sample": f"the first {args.steps} QPs of the batch, one per step, single thread; "
+                                       f"iters {iters}"},
             "e2e": {"value": ms, "unit": "ms/QP", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -859,8 +860,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if esz == 4 else "f64",
                 "data": "synthetic",
-                "config": {"workload": "quadruped-shaped LTV-QP family (nx=61 nu=12 N=100 nc=20 nf=8), held-out "
-                                       "instances; learned warm start + batched persistent solve",
+                "config": {"workload": WORKLOAD, "solver": "learned warm start + batched persistent GPU solve",
                            "batch": args.batch, "precision": args.precision,
                            "cluster": int(settings.cluster), "occupancy": int(settings.occupancy),
                            "launch_shape": ("autotuned" if tuned is not None else "fixed"),
