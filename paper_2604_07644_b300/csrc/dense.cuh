@@ -463,7 +463,7 @@ __device__ __forceinline__ void mk_mac(int m, int n, const MTerm<T>& p, T (&acc)
 // Each shape is its own (non-inlined) function so that its registers are
 // allocated for it alone.
 template <typename T, int GX, int RA, int RB>
-__device__ __noinline__ void sgemm_vec(int m, int n, T alpha, const MTerm<T>& p1, const MTerm<T>& p2, T beta,
+__device__ __noinline__ void sgemm_vec(int m, int n, T alpha, const MTerm<T> p1, const MTerm<T> p2, T beta,
                                        const T* C0, int ldc0, bool addI, T* C, int ldc, bool tC) {
   constexpr int GY = NT / GX;
   constexpr bool PRE = RA * RB <= 4;   // C0 prefetched into registers when they allow
@@ -529,7 +529,7 @@ __device__ __noinline__ void sgemm_vec(int m, int n, T alpha, const MTerm<T>& p1
 
 // Scalar register-tile path for operands that are not 16-byte aligned.
 template <typename T>
-__device__ __noinline__ void sgemm_scalar(int m, int n, T alpha, const MTerm<T>& p1, const MTerm<T>& p2, T beta,
+__device__ __noinline__ void sgemm_scalar(int m, int n, T alpha, const MTerm<T> p1, const MTerm<T> p2, T beta,
                                           const T* C0, int ldc0, bool addI, T* C, int ldc, bool tC) {
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   T acc[5][5];
@@ -632,7 +632,7 @@ __device__ __forceinline__ void tc3_mac(int m, int n, const MTerm<float>& p, int
   }
 }
 
-static __device__ __noinline__ void sgemm_tc3(int m, int n, float alpha, const MTerm<float>& p1, const MTerm<float>& p2,
+static __device__ __noinline__ void sgemm_tc3(int m, int n, float alpha, const MTerm<float> p1, const MTerm<float> p2,
                                        float beta, const float* C0, int ldc0, bool addI, float* C, int ldc, bool tC) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const int mtiles = (m + 15) >> 4, ngroups = (n + 31) >> 5, units = mtiles * ngroups;
@@ -1168,6 +1168,69 @@ __device__ inline T warp_max(T v) {
 #pragma unroll
   for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
   return v;
+}
+
+// Inverse of an SPD n x n matrix (n <= CAP <= 32) to FP64 accuracy by
+// mixed-precision iterative refinement: the FP32 Gauss-Jordan inverse X0 of
+// warp_spd_inverse_as, the residual E = I - G X0 in FP64 arithmetic, then one
+// Newton-Schulz step X1 = X0 + X0 E.  Since I - G X1 = E^2, X1 has relative
+// error at most ||E||^2 (infinity norm); the step is taken when ||E|| <= 1e-4,
+// so X1 is FP64-accurate to well below the output's rounding.  X0 E is a
+// small correction, so its product runs in FP32; the sum X0 + X0 E is
+// rounded once.  A failed FP32 pivot, or ||E|| > 1e-4 (an ill-conditioned
+// block), takes the FP64 Gauss-Jordan instead.  B300 issues FP64 at a small
+// fraction of the FP32 rate: this keeps FP64 to the n^3 residual products,
+// one element per thread, and out of the pivot chain with its divisions.
+// G, Gi as for warp_spd_inverse_as; E: shared scratch of n rows x lde >= n
+// elements aliasing neither.  Ends with a CTA barrier.
+template <typename T, int CAP>
+__device__ __noinline__ int spd_inverse_refined(const T* G, int ldg, int n, T* Gi, int ldgi, int* flag, T* E,
+                                                int lde) {
+  if (warp_spd_inverse_as<T, T, CAP>(G, ldg, n, Gi, ldgi, flag))
+    return warp_spd_inverse_as<T, double, CAP>(G, ldg, n, Gi, ldgi, flag);
+  const int t = threadIdx.x, nn = n * n;
+  for (int e = t; e < nn; e += NT) {
+    const int i = e / n, j = e - i * n;
+    double s = i == j ? 1.0 : 0.0;
+    for (int q = 0; q < n; ++q) s = fma(-(double)G[i * ldg + q], (double)Gi[q * ldgi + j], s);
+    E[i * lde + j] = (T)s;
+  }
+  __syncthreads();
+  if (t < 32) {
+    T r = T(0);
+    if (t < n)
+      for (int j = 0; j < n; ++j) r += fabs(E[t * lde + j]);
+    r = warp_max(r);
+    if (t == 0) flag[0] = r <= T(1e-4) ? 0 : 1;
+  }
+  __syncthreads();
+  const int fall = flag[0];
+  __syncthreads();
+  if (fall) return warp_spd_inverse_as<T, double, CAP>(G, ldg, n, Gi, ldgi, flag);
+  constexpr int PER = (CAP * CAP + NT - 1) / NT;
+  T xr[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = t + p * NT;
+    xr[p] = T(0);
+    if (e < nn) {
+      const int i = e / n, j = e - i * n;
+      T s = T(0);
+      for (int l = 0; l < n; ++l) s = fma(Gi[i * ldgi + l], E[l * lde + j], s);
+      xr[p] = Gi[i * ldgi + j] + s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = t + p * NT;
+    if (e < nn) {
+      const int i = e / n, j = e - i * n;
+      Gi[i * ldgi + j] = xr[p];
+    }
+  }
+  __syncthreads();
+  return 0;
 }
 
 // Column sweep of one output: sum_{r < R} S[r * ld + j] x[r], four

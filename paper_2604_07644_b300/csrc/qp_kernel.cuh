@@ -600,11 +600,14 @@ __device__ inline void fact_prefetch(Ctx<T>& c, const FactBufs<T>& fb, int i, in
   if (withD && d.nc > 0) cta_stage(fb.Db[k], TP<T>(d.D) + (size_t)i * d.nc * d.ldu, d.nc * d.ldu * esz);
 }
 
-// n x n (n <= FACT_MAX_NU) SPD inverse by one warp.
-// GPUSLS_MIXED: the per-stage solve (Gamma_i, R^_i^-1) in FP64 arithmetic.
+// n x n (n <= FACT_MAX_NU) SPD inverse by one warp (the CTA for n > 16).
+// GPUSLS_MIXED: the per-stage solve (Gamma_i, R^_i^-1) to FP64 accuracy: for
+// n <= 16 the FP32 inverse refined with an FP64 residual (spd_inverse_refined,
+// scratch E: n rows x lde, free shared memory), else the FP64 Gauss-Jordan.
 template <typename T>
-__device__ inline int small_spd_inverse(Ctx<T>& c, const T* G, int ldg, int n, T* Gi, int ldgi) {
+__device__ inline int small_spd_inverse(Ctx<T>& c, const T* G, int ldg, int n, T* Gi, int ldgi, T* E, int lde) {
   if (sizeof(T) == 4 && c.mix) {
+    if (n <= 16 && n <= lde) return spd_inverse_refined<T, 16>(G, ldg, n, Gi, ldgi, c.flag + 1, E, lde);
     if (n <= 16) return warp_spd_inverse_as<T, double, 16>(G, ldg, n, Gi, ldgi, c.flag + 1);
     return warp_spd_inverse_as<T, double, FACT_MAX_NU>(G, ldg, n, Gi, ldgi, c.flag + 1);
   }
@@ -626,7 +629,7 @@ __device__ __noinline__ int fact_step_full(Ctx<T>& c, const FactBufs<T>& fb, int
   sgemm1<T>(nx, nu, nx, T(1), fb.P, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S1, lds, true, c.mix);    // Y^T
   sgemm1<T>(nx, nu, nx, T(1), fb.Aa, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S3, lds, true, c.mix);   // E^T
   sgemm1<T>(nu, nu, nx, T(1), fb.S1, lds, false, Bb, ldu, T(1), Rb, ldu, fb.Gm, ldu, false, c.mix);             // G
-  const int bad = small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
+  const int bad = small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu, fb.S2, lds);
   cp_async_wait<0>();
   __syncthreads();
   prof_mark(c, PH_FA1);
@@ -704,8 +707,11 @@ __device__ __noinline__ void fact_bundles(Ctx<T>& c, const FactBufs<T>& fb, int 
 //   c0_i = Abar_i^T P_{i+1} b_i + q_i + K_i^T r_i,
 // and, outside the last chunk, the backward chunk products with
 // Pi_{i+1} (in Aa, Pi_e = I): FPi_i = F_i Pi_{i+1}, Pi_i = Abar_i^T Pi_{i+1}.
+// ponly: the P recursion alone (P_i to IP, no gains, vectors or operators),
+// by the same operations as the full step, so a later full pass from the same
+// P_{i+1} reproduces it exactly.
 template <typename T>
-__device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, int i, int k) {
+__device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, int i, int k, bool ponly) {
   const QPDesc& d = *c.d;
   const int nx = d.nx, nu = d.nu, nc = d.nc, ldx = d.ldx, ldu = d.ldu, ldc = d.ldc, lds = fb.lds, msz = c.msz;
   const int esz = (int)sizeof(T), t = threadIdx.x;
@@ -716,36 +722,40 @@ __device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, 
   cta_stage_rows(fb.S3, lds * esz, TP<T>(d.S0) + (size_t)i * nu * ldx, ldx * esz, nu, ldx * esz);  // R^-1 S^
   if (i - 1 >= c.s) fact_prefetch<T>(c, fb, i - 1, k ^ 1, true);
   cp_async_commit();
-  for (int e = t; e < nx; e += NT) {
-    bv[e] = TP<T>(d.b)[(size_t)i * ldx + e];
-    qv[e] = TP<T>(d.q)[(size_t)i * ldx + e];
+  if (!ponly) {
+    for (int e = t; e < nx; e += NT) {
+      bv[e] = TP<T>(d.b)[(size_t)i * ldx + e];
+      qv[e] = TP<T>(d.q)[(size_t)i * ldx + e];
+    }
+    for (int e = t; e < nu; e += NT) rv[e] = TP<T>(d.r)[(size_t)i * ldu + e];
+    __syncthreads();
+    smem_mvT<T>(fb.P, lds, nx, nx, bv, nullptr, pb, c.red);                                       // P_{i+1} b_i (P symmetric)
   }
-  for (int e = t; e < nu; e += NT) rv[e] = TP<T>(d.r)[(size_t)i * ldu + e];
-  __syncthreads();
-  smem_mvT<T>(fb.P, lds, nx, nx, bv, nullptr, pb, c.red);                                         // P_{i+1} b_i (P symmetric)
   sgemm1<T>(nx, nu, nx, T(1), fb.P, lds, false, Bb, ldu, T(0), nullptr, 0, fb.S1, lds, true, c.mix);    // Y^T
   sgemm1<T>(nu, nu, nx, T(1), fb.S1, lds, false, Bb, ldu, T(1), Rb, ldu, fb.Gm, ldu, false, c.mix);             // Gamma^-1
-  const int bad = small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
+  const int bad = small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu, fb.S2, lds);
   cp_async_wait<0>();
   __syncthreads();
   prof_mark(c, PH_FC1);
   sgemm1<T>(nu, nx, nx, T(1), fb.S1, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.S2, lds, false, c.mix);       // Y^T A~_i
   sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S2, lds, T(0), nullptr, 0, fb.S2, lds, false, c.mix);       // H
   sgemm1<T>(nx, nx, nu, T(-1), Bb, ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds, false, c.mix);         // Abar_i
-  T* Kg = TP<T>(d.K) + (size_t)i * nu * ldx;
-  for (int e = t; e < nu * nx; e += NT) {
-    const int a = e / nx, j = e - a * nx;
-    const T v = -(fb.S3[a * lds + j] + fb.S2[a * lds + j]);
-    fb.S1[a * lds + j] = v;
-    Kg[(size_t)a * ldx + j] = v;
+  if (!ponly) {
+    T* Kg = TP<T>(d.K) + (size_t)i * nu * ldx;
+    for (int e = t; e < nu * nx; e += NT) {
+      const int a = e / nx, j = e - a * nx;
+      const T v = -(fb.S3[a * lds + j] + fb.S2[a * lds + j]);
+      fb.S1[a * lds + j] = v;
+      Kg[(size_t)a * ldx + j] = v;
+    }
+    __syncthreads();
+    smem_mvT<T>(Bb, ldu, nx, nu, pb, rv, tv, c.red);       // B^T P b + r
+    smem_mvT<T>(fb.Xb, lds, nx, nx, pb, qv, c0v, c.red);   // Abar^T P b + q
+    smem_mvT<T>(fb.S1, lds, nu, nx, rv, c0v, c0v, c.red);  // ... + K^T r
+    smem_mv<T>(fb.Gi, ldu, nu, nu, tv, nullptr, k0v);
+    if (t < nu) k0v[t] = -k0v[t];
+    __syncthreads();
   }
-  __syncthreads();
-  smem_mvT<T>(Bb, ldu, nx, nu, pb, rv, tv, c.red);       // B^T P b + r
-  smem_mvT<T>(fb.Xb, lds, nx, nx, pb, qv, c0v, c.red);   // Abar^T P b + q
-  smem_mvT<T>(fb.S1, lds, nu, nx, rv, c0v, c0v, c.red);  // ... + K^T r
-  smem_mv<T>(fb.Gi, ldu, nu, nu, tv, nullptr, k0v);
-  if (t < nu) k0v[t] = -k0v[t];
-  __syncthreads();
   prof_mark(c, PH_FC2);
   // P_i = P~_i + X^T (P_{i+1} X) + H^T (R^ H)
   sgemm1<T>(nx, nx, nx, T(1), fb.P, lds, false, fb.Xb, lds, T(0), nullptr, 0, fb.P, lds, false, c.mix);
@@ -753,6 +763,10 @@ __device__ __noinline__ int fact_step_riccati(Ctx<T>& c, const FactBufs<T>& fb, 
   sgemm<T>(nx, nx, T(1), MTerm<T>{fb.Xb, lds, true, fb.P, lds, nx}, MTerm<T>{fb.S2, lds, true, fb.S3, lds, nu},
            T(1), TP<T>(d.VP) + (size_t)i * msz, ldx, false, fb.P, lds, false, c.mix);
   prof_mark(c, PH_FC3);
+  if (ponly) {
+    cta_copy_vec<T>(nx, nx, fb.P, lds, TP<T>(d.IP) + (size_t)i * msz, ldx);
+    return bad;
+  }
   // stage outputs: -B Gamma (= F_i^T), -D Gamma (= J_i^T), CK_i = C_i + D_i K_i
   sgemm1<T>(nx, nu, nu, T(-1), Bb, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.BG, ldu, false, c.mix);
   sgemm1<T>(nc, nu, nu, T(-1), Db, ldu, false, fb.Gi, ldu, T(0), nullptr, 0, fb.JT, ldu, false, c.mix);
@@ -789,6 +803,11 @@ __device__ __noinline__ int blocked_scan(Ctx<T>& c, cg::cluster_group& cl) {
   const int lds = fb.lds;
   const int n = N + 1;   // leaves; chunk elements T_r are kept at tree nodes n + r
   int bad = 0;
+  // With more than one chunk the last chunk runs only the P recursion in A,
+  // beside the other chunks' folds (a full Riccati step, with its gains and
+  // operators, costs about twice a fold step), and its full steps in C,
+  // beside theirs.
+  const bool split_last = nch > 1;
   if (c.active && c.last) {
     // A (last chunk): Riccati steps from the terminal leaf, P_N = Q^_N
     cta_stage_rows(fb.P, lds * esz, VP + (size_t)N * msz, ldx * esz, nx, ldx * esz);
@@ -798,7 +817,7 @@ __device__ __noinline__ int blocked_scan(Ctx<T>& c, cg::cluster_group& cl) {
     __syncthreads();
     cta_copy_vec<T>(nx, nx, fb.P, lds, IP + (size_t)N * msz, ldx);
     int k = 0;
-    for (int i = c.e - 1; i >= c.s; --i, k ^= 1) bad |= fact_step_riccati<T>(c, fb, i, k);
+    for (int i = c.e - 1; i >= c.s; --i, k ^= 1) bad |= fact_step_riccati<T>(c, fb, i, k, split_last);
   } else if (c.active && c.rank >= 1) {
     // A: T_r, starting from the chunk's last leaf
     const int i0 = c.e - 1;
@@ -826,17 +845,18 @@ __device__ __noinline__ int blocked_scan(Ctx<T>& c, cg::cluster_group& cl) {
     cl.sync();
   }
   prof_mark(c, PH_R3);
-  // C: Riccati steps of chunks 0 .. nch-2 from P_{e_r}
-  if (c.active && !c.last) {
-    cta_stage_rows(fb.P, lds * esz, IP + (size_t)c.e * msz, ldx * esz, nx, ldx * esz);
+  // C: Riccati steps of chunks 0 .. nch-2 from P_{e_r} (and of the last
+  // chunk from P_N again, when A ran only its P recursion)
+  if (c.active && (!c.last || split_last)) {
+    cta_stage_rows(fb.P, lds * esz, IP + (size_t)(c.last ? N : c.e) * msz, ldx * esz, nx, ldx * esz);
     fact_prefetch<T>(c, fb, c.e - 1, 0, true);
     cp_async_commit();
-    cta_eye<T>(nx, fb.Aa, lds);   // Pi_e
+    if (!c.last) cta_eye<T>(nx, fb.Aa, lds);   // Pi_e
     cp_async_wait<0>();
     __syncthreads();
     int k = 0;
-    for (int i = c.e - 1; i >= c.s; --i, k ^= 1) bad |= fact_step_riccati<T>(c, fb, i, k);
-    cta_copy_vec<T>(nx, nx, fb.Aa, lds, TP<T>(d.Tch) + (size_t)c.rank * msz, ldx);   // T_r = Pi_s
+    for (int i = c.e - 1; i >= c.s; --i, k ^= 1) bad |= fact_step_riccati<T>(c, fb, i, k, false);
+    if (!c.last) cta_copy_vec<T>(nx, nx, fb.Aa, lds, TP<T>(d.Tch) + (size_t)c.rank * msz, ldx);   // T_r = Pi_s
   }
   return bad;
 }
@@ -875,7 +895,7 @@ __device__ __noinline__ int leaves_blocked(Ctx<T>& c, T rho) {
     sgemm1<T>(nu, nu, nc, rho, fb.Db[0], ldu, true, fb.Db[0], ldu, T(1), fb.Rb[0], ldu, fb.Gm, ldu, false, c.mix);   // R^
     sgemm1<T>(nu, nx, nc, rho, fb.Db[0], ldu, true, fb.CKb[0], lds, T(1), fb.S3, lds, fb.S1, lds, false, c.mix);     // S^
     cta_copy_vec<T>(nu, nu, fb.Gm, ldu, TP<T>(d.Rh) + (size_t)i * nu * ldu, ldu);
-    bad |= small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu);
+    bad |= small_spd_inverse<T>(c, fb.Gm, ldu, nu, fb.Gi, ldu, fb.S2, lds);
     sgemm1<T>(nu, nx, nu, T(1), fb.Gi, ldu, false, fb.S1, lds, T(0), nullptr, 0, fb.S2, lds, false, c.mix);          // s0
     sgemm1<T>(nx, nx, nu, T(-1), fb.S1, lds, true, fb.S2, lds, T(1), fb.P, lds, fb.P, lds, false, c.mix);            // P~
     sgemm1<T>(nx, nx, nu, T(-1), fb.Bb[0], ldu, false, fb.S2, lds, T(1), fb.Xb, lds, fb.Xb, lds, false, c.mix);      // A~
