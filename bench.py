@@ -712,7 +712,7 @@ def main():
     inf_c = read_info(False)
 
     # the same learned step with the factorization's block products on the
-    # tensor cores (GPUSLS_MIXED: three TF32 passes, FP64 per-stage solves)
+    # tensor cores (GPUSLS_MIXED: three TF32 passes, per-stage solves to FP64 accuracy)
     mixed = None
     if prec == native.GPUSLS_FP32:
         sm = native.default_settings(precision=native.GPUSLS_MIXED, cluster=int(settings.cluster),
@@ -732,7 +732,8 @@ def main():
                  "kkt_max": float(np.max([i["kkt"] for i in im])),
                  "all_converged": all(i["status"] == 0 for i in im),
                  "mode": "GPUSLS_MIXED: blocked-factorization block products in three TF32 passes (mma.sync), "
-                         "FP64 per-stage solves, FP64 KKT gate"}
+                         "per-stage solves to FP64 accuracy (FP32 inverse + Newton-Schulz step with an FP64 residual), "
+                         "FP64 KKT gate"}
         gm.close()
         hm.close()
 

@@ -63,8 +63,10 @@ extern "C" {
 #define GPUSLS_MIXED 3  /* FP32 storage and iterations; the blocked factorization's
                            block products on the tensor cores in three TF32 passes
                            (a = a_hi + a_lo, FP32 accumulation: FP32 accuracy), its
-                           per-stage nu x nu solves (Gamma_i, R^_i^-1) in FP64, the KKT
-                           check in FP64 (the mixed-precision mode of the target) */
+                           per-stage nu x nu solves (Gamma_i, R^_i^-1) to FP64
+                           accuracy (an FP32 inverse refined by a Newton-Schulz step
+                           whose residual is formed in FP64; FP64 elimination for
+                           ill-conditioned blocks), the KKT check in FP64 */
 
 /* Dimensions of one LTV-QP (eq. sqp_qp): state nx, input nu, horizon N, stage
  * constraint rows nc (rows of C_k, D_k), terminal rows nf (rows of C_N). */

@@ -322,7 +322,7 @@ def test_tf32_products_accuracy_level(lib, name, make):
 @pytest.mark.parametrize("cluster", [6, 8])
 def test_mixed_precision_full_size(lib, cluster):
     """GPUSLS_MIXED at 61D / N=100 (block products in three TF32 passes on the
-    tensor cores, FP64 per-stage solves): the Riccati terms carry FP32-sized
+    tensor cores, per-stage solves to FP64 accuracy): the Riccati terms carry FP32-sized
     errors against the FP64 sequential recursion (1e-4 relative, like FP32,
     where one TF32 pass leaves 2e-3 to 5e-3), and the adaptive solve meets the
     1e-4 KKT tolerance by the oracle's own measure with every bound met."""
@@ -341,3 +341,44 @@ def test_mixed_precision_full_size(lib, cluster):
     assert kkt.kkt_residual(qp, r.dx[0], r.du[0], r.lam[0]) <= 1.0001e-4
     v = lq.G_apply(qp, r.dx[0], r.du[0])
     assert np.all(v <= qp.hi + 1e-4) and np.all(v >= qp.lo - 1e-4)
+
+
+def ill_conditioned_nodes(seed=0, nx=6, nu=4, N=12, small=1e-4):
+    """A QP whose node blocks Gamma_i = R^_i + B_i^T P_{i+1} B_i have condition
+    numbers 3e4..1e5: R_i has the eigenvalue `small` along a rotated input
+    direction v, B_i and D_i nearly miss v, and S_i = 0 keeps each stage cost
+    convex."""
+    import dataclasses
+    qp = W.random_general(seed, nx, nu, N, 3, 2)
+    rng = np.random.default_rng(100 + seed)
+    V, _ = np.linalg.qr(rng.standard_normal((nu, nu)))
+    v = V[:, 0]
+    R = V @ np.diag([small] + [1.0] * (nu - 1)) @ V.T
+    Pv = np.eye(nu) - np.outer(v, v)
+    return dataclasses.replace(qp, R=np.repeat(R[None], N, 0), S=np.zeros_like(qp.S),
+                               B=qp.B @ Pv + 1e-3 * (qp.B @ np.outer(v, v)), D=qp.D @ Pv)
+
+
+@pytest.mark.parametrize("cluster", [1, 3])
+def test_mixed_node_solve_ill_conditioned(lib, cluster):
+    """Node blocks of condition 3e4..1e5: the FP32 inverse's residual
+    ||I - Gamma X0||_inf exceeds the refined node solve's 1e-4 threshold
+    (numpy's pivoted FP32 inverse of these blocks leaves 2.5e-4..1.8e-3), so
+    GPUSLS_MIXED takes its FP64 elimination for them.  P_i and K_i match the
+    FP64 sequential recursion at least as well as the FP32 path does."""
+    qp = ill_conditioned_nodes()
+    rho = 0.7
+    Qh, Rh, Sh = lq.augmented(qp, rho)
+    P, p, K, kff, G = lq.riccati(qp.A, qp.B, qp.c, Qh, Rh, Sh, np.zeros_like(qp.q), np.zeros_like(qp.r))
+    assert min(np.linalg.cond(np.linalg.inv(g)) for g in G) > 1e4
+    err = {}
+    for prec in (native.GPUSLS_FP32, native.GPUSLS_MIXED):
+        b = batch([qp], precision=prec, cluster=cluster, rho=rho)
+        Ps, Ks = b.riccati()
+        b.close()
+        assert np.all(np.isfinite(Ps[0])) and np.all(np.isfinite(Ks[0]))
+        err[prec] = (rel(Ps[0], P), rel(Ks[0], K))
+    eP, eK = err[native.GPUSLS_MIXED]
+    fP, fK = err[native.GPUSLS_FP32]
+    assert eP < 1e-3 and eK < 1e-2, err
+    assert eK <= 2.0 * fK + 1e-5 and eP <= 2.0 * fP + 1e-5, err
