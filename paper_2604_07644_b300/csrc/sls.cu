@@ -46,8 +46,8 @@ struct sls_handle {
   // FP64 pools of the internal problems (dense layouts)
   double *pA = nullptr, *pB = nullptr, *pQ = nullptr, *pR = nullptr, *pS = nullptr, *dummy = nullptr;
   size_t nA = 0, nB = 0, nQ = 0, nR = 0, nS = 0;
-  // solve-precision copies of E, C, D, CN (padded) and per-j scratch
-  void *ET = nullptr, *CT = nullptr, *DT = nullptr, *CNT = nullptr, *scr = nullptr;
+  // solve-precision copies of E, C, D, CN (padded)
+  void *ET = nullptr, *CT = nullptr, *DT = nullptr, *CNT = nullptr;
   double *rn = nullptr, *rnf = nullptr;   // partial row sums of squares [N][N][nblk][nc], [N][nblk][nf]
   int nblk = 1;                           // column blocks of Phi_{.,j} propagated by separate CTAs
   int ldx = 0, ldu = 0;
@@ -168,58 +168,117 @@ __global__ void sls_convert_kernel(const double* __restrict__ src, T* __restrict
 struct SLSPhi {
   const QPDesc* descs;
   const void *ET, *CT, *DT, *CNT;
-  void* scr;
   double *Phix, *Phiu, *rn, *rnf;
   int nx, nu, N, nc, nf, ldx, ldu, per_j, nblk;
 };
+
+// Shared-memory layout of sls_phi_kernel (element offsets): the block's
+// columns of Phi_x_{k,j} (cur, nxt), Phi_u_{k,j} (xu) and the margin rows
+// (mr), each with row pitch lw; then nbuf stage sets, each holding the
+// stage's Abar_k^(j), K_k^(j), C_k (or C_N) and D_k with their padded
+// pitches.  FP32 keeps two stage sets (the next stage's operands are copied
+// while the current one is used); FP64, whose sets are twice the size, one.
+struct PhiLayout {
+  int lw, cur, nxt, xu, mr, stage, ab, kk, cc, dd, nbuf, total;
+};
+__host__ __device__ inline PhiLayout phi_layout(int nx, int nu, int nc, int nf, int ldx, int ldu, int nblk, int esz) {
+  PhiLayout L;
+  const int bw = (nx + nblk - 1) / nblk;
+  const int ncf = nc > nf ? nc : nf;
+  L.lw = rup4(bw);
+  int off = 0;
+  L.cur = off; off += rup4(nx * L.lw);
+  L.nxt = off; off += rup4(nx * L.lw);
+  L.xu = off; off += rup4(nu * L.lw);
+  L.mr = off; off += rup4((ncf > 0 ? ncf : 1) * L.lw);
+  L.ab = 0;
+  L.kk = rup4(nx * ldx);
+  L.cc = L.kk + rup4(nu * ldx);
+  L.dd = L.cc + rup4((ncf > 0 ? ncf : 1) * ldx);
+  L.stage = L.dd + rup4((nc > 0 ? nc : 1) * ldu);
+  L.nbuf = esz == 4 ? 2 : 1;
+  L.total = off + L.nbuf * L.stage;
+  return L;
+}
 
 // One CTA per (disturbance index j, column block cb): the columns
 // [c0, c1) of Phi_{.,j} evolve independently (Phi_x_{k+1,j} = Abar_k^(j)
 // Phi_x_{k,j} acts on each column), so a block propagates them alone and
 // leaves, per constraint row, its partial sum of squares of
 // C_k Phi_x_{k,j} + D_k Phi_u_{k,j} (the block's columns) for the margins
-// and duals to add up.
+// and duals to add up.  The block's columns stay in shared memory for the
+// whole chain over k; each stage's operators are copied in (cp.async) and,
+// in FP32, the next stage's while the current stage's products run.
 template <typename T>
-__global__ void __launch_bounds__(NT, 1) sls_phi_kernel(SLSPhi a) {
+__global__ void __launch_bounds__(NT, 2) sls_phi_kernel(SLSPhi a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T* gm = reinterpret_cast<T*>(smem);
+  T* sm = reinterpret_cast<T*>(smem);
   const int j = blockIdx.x, cb = blockIdx.y, nblk = a.nblk;
   const int nx = a.nx, nu = a.nu, N = a.N, nc = a.nc, nf = a.nf, ldx = a.ldx, ldu = a.ldu;
   const int bw = (nx + nblk - 1) / nblk, c0 = cb * bw, w = min(nx, c0 + bw) - c0;
   if (w <= 0) return;
-  const int msz = nx * ldx;
+  const PhiLayout L = phi_layout(nx, nu, nc, nf, ldx, ldu, nblk, (int)sizeof(T));
+  const int lw = L.lw, msz = nx * ldx, esz = (int)sizeof(T);
   const int NX = N * nx;
   const int t = threadIdx.x, wp = t >> 5, l = t & 31;
-  T* X0 = reinterpret_cast<T*>(a.scr) +
-          ((size_t)j * nblk + cb) * (2 * msz + (nc > nf ? nc : nf) * ldx + nu * ldx + 16);
-  T* X1 = X0 + msz;
-  T* Xu = X1 + msz;
-  T* M = Xu + nu * ldx;
+  T* cur = sm + L.cur;
+  T* nxt = sm + L.nxt;
+  T* Xu = sm + L.xu;
+  T* M = sm + L.mr;
+  T* const stg0 = sm + (L.total - L.nbuf * L.stage);
   const T* ET = reinterpret_cast<const T*>(a.ET);
   const T* CT = reinterpret_cast<const T*>(a.CT);
   const T* DT = reinterpret_cast<const T*>(a.DT);
   const T* CNT = reinterpret_cast<const T*>(a.CNT);
-  // Phi_x_{j+1,j} = E_j (columns c0 .. c0 + w)
-  cta_copy<T>(nx, w, ET + (size_t)j * msz + c0, ldx, false, X0, ldx);
   const int q = a.per_j ? j : 0;
   const int first = a.per_j ? j + 1 : 1;
   const QPDesc* dq = (j + 1 < N || !a.per_j) ? &a.descs[q] : nullptr;
-  T* cur = X0;
-  T* nxt = X1;
+  // the operators of stage k into stage set sb (no wait)
+  auto issue = [&](int k, int sb) {
+    T* S = stg0 + (size_t)sb * L.stage;
+    if (k < N) {
+      const int i = k - first;   // local stage of problem q
+      cta_stage(S + L.ab, reinterpret_cast<const T*>(dq->Abar) + (size_t)i * msz, msz * esz);
+      cta_stage(S + L.kk, reinterpret_cast<const T*>(dq->K) + (size_t)i * nu * ldx, nu * ldx * esz);
+      if (nc > 0) {
+        cta_stage(S + L.cc, CT + (size_t)k * nc * ldx, nc * ldx * esz);
+        cta_stage(S + L.dd, DT + (size_t)k * nc * ldu, nc * ldu * esz);
+      }
+    } else if (nf > 0) {
+      cta_stage(S + L.cc, CNT, nf * ldx * esz);
+    }
+    cp_async_commit();
+  };
+  // Phi_x_{j+1,j} = E_j (columns c0 .. c0 + w, zero beyond w)
+  for (int e = t; e < nx * lw; e += NT) {
+    const int r = e / lw, c = e - r * lw;
+    cur[e] = c < w ? ET[(size_t)j * msz + (size_t)r * ldx + c0 + c] : T(0);
+  }
+  issue(j + 1, 0);
+  int sb = 0;
   for (int k = j + 1; k <= N; ++k) {
+    const bool ahead = L.nbuf == 2 && k + 1 <= N;
+    if (ahead) {
+      issue(k + 1, sb ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const T* S = stg0 + (size_t)sb * L.stage;
     // write Phi_x_{k,j} (block row k-1, block column j, columns c0 ..)
     if (a.Phix)
       for (int e = t; e < nx * w; e += NT) {
         const int r = e / w, c = e - r * w;
-        a.Phix[(size_t)((k - 1) * nx + r) * NX + (size_t)j * nx + c0 + c] = (double)cur[r * ldx + c];
+        a.Phix[(size_t)((k - 1) * nx + r) * NX + (size_t)j * nx + c0 + c] = (double)cur[r * lw + c];
       }
     if (k == N) {
       // terminal margin rows: C_N Phi_x_{N,j}
       if (nf > 0) {
-        cta_gemm<T>(nf, w, nx, T(1), CNT, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, M, ldx, gm);
+        sgemm1<T>(nf, w, nx, T(1), S + L.cc, ldx, false, cur, lw, T(0), nullptr, 0, M, lw);
         for (int r = wp; r < nf; r += NT / 32) {
           T s2 = T(0);
-          for (int c = l; c < w; c += 32) s2 += M[r * ldx + c] * M[r * ldx + c];
+          for (int c = l; c < w; c += 32) s2 += M[r * lw + c] * M[r * lw + c];
           s2 = warp_sum(s2);
           if (l == 0) a.rnf[((size_t)j * nblk + cb) * nf + r] = (double)s2;
         }
@@ -227,35 +286,34 @@ __global__ void __launch_bounds__(NT, 1) sls_phi_kernel(SLSPhi a) {
       }
       break;
     }
-    const int i = k - first;   // local stage of problem q
-    const T* Kk = reinterpret_cast<const T*>(dq->K) + (size_t)i * nu * ldx;
-    const T* Ab = reinterpret_cast<const T*>(dq->Abar) + (size_t)i * msz;
     // Phi_u_{k,j} = K_k^(j) Phi_x_{k,j}
-    cta_gemm<T>(nu, w, nx, T(1), Kk, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, Xu, ldx, gm);
+    sgemm1<T>(nu, w, nx, T(1), S + L.kk, ldx, false, cur, lw, T(0), nullptr, 0, Xu, lw);
     if (a.Phiu)
       for (int e = t; e < nu * w; e += NT) {
         const int r = e / w, c = e - r * w;
-        a.Phiu[(size_t)(k * nu + r) * NX + (size_t)j * nx + c0 + c] = (double)Xu[r * ldx + c];
+        a.Phiu[(size_t)(k * nu + r) * NX + (size_t)j * nx + c0 + c] = (double)Xu[r * lw + c];
       }
     // margin rows: C_k Phi_x + D_k Phi_u
     if (nc > 0) {
-      cta_gemm<T>(nc, w, nx, T(1), CT + (size_t)k * nc * ldx, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, M,
-                  ldx, gm);
-      cta_gemm<T>(nc, w, nu, T(1), DT + (size_t)k * nc * ldu, ldu, false, Xu, ldx, false, T(1), M, ldx, false, M, ldx,
-                  gm);
+      sgemm<T>(nc, w, T(1), MTerm<T>{S + L.cc, ldx, false, cur, lw, nx}, MTerm<T>{S + L.dd, ldu, false, Xu, lw, nu},
+               T(0), nullptr, 0, false, M, lw, false);
       for (int r = wp; r < nc; r += NT / 32) {
         T s2 = T(0);
-        for (int c = l; c < w; c += 32) s2 += M[r * ldx + c] * M[r * ldx + c];
+        for (int c = l; c < w; c += 32) s2 += M[r * lw + c] * M[r * lw + c];
         s2 = warp_sum(s2);
         if (l == 0) a.rn[(((size_t)k * N + j) * nblk + cb) * nc + r] = (double)s2;
       }
-      __syncthreads();
     }
     // Phi_x_{k+1,j} = (A_k + B_k K_k^(j)) Phi_x_{k,j}
-    cta_gemm<T>(nx, w, nx, T(1), Ab, ldx, false, cur, ldx, false, T(0), nullptr, 0, false, nxt, ldx, gm);
+    sgemm1<T>(nx, w, nx, T(1), S + L.ab, ldx, false, cur, lw, T(0), nullptr, 0, nxt, lw);
     T* tmp = cur;
     cur = nxt;
     nxt = tmp;
+    if (L.nbuf == 2) {
+      sb ^= 1;
+    } else if (k + 1 <= N) {
+      issue(k + 1, 0);   // the products above ended with a CTA barrier: the set is free
+    }
   }
 }
 
@@ -380,9 +438,6 @@ extern "C" int sls_setup_ex(sls_handle** out, qp_dims d, int32_t precision, int3
   e = (cudaError_t)(e | cudaMalloc(&h->CT, (size_t)N * std::max(nc, 1) * h->ldx * esz + 256));
   e = (cudaError_t)(e | cudaMalloc(&h->DT, (size_t)N * std::max(nc, 1) * h->ldu * esz + 256));
   e = (cudaError_t)(e | cudaMalloc(&h->CNT, (size_t)std::max(nf, 1) * h->ldx * esz + 256));
-  e = (cudaError_t)(e | cudaMalloc(&h->scr, (size_t)N * h->nblk *
-                                                   (2 * nx * h->ldx + std::max(nc, nf) * h->ldx + nu * h->ldx + 16) *
-                                                   esz + 256));
   e = (cudaError_t)(e | alloc(&h->rn, (size_t)N * N * h->nblk * std::max(nc, 1)));
   e = (cudaError_t)(e | alloc(&h->rnf, (size_t)N * h->nblk * std::max(nf, 1)));
   if (h->per_j) {
@@ -476,10 +531,10 @@ extern "C" int sls_solve(sls_handle* h, const double* A, const double* B, const 
   conv(CN, h->CNT, 1, nf, nx, ldx);
   CUS(cudaGetLastError());
   // 3. Phi and margin row norms, one CTA per disturbance index j
-  SLSPhi p = {h->qh ? h->qh->ddesc : nullptr, h->ET, h->CT, h->DT, h->CNT, h->scr, Phi_x, Phi_u, h->rn, h->rnf,
+  SLSPhi p = {h->qh ? h->qh->ddesc : nullptr, h->ET, h->CT, h->DT, h->CNT, Phi_x, Phi_u, h->rn, h->rnf,
               nx, nu, N, nc, nf, ldx, ldu, h->per_j, h->nblk};
   const dim3 pgrid(N, h->nblk);
-  const int smem = 2 * KT * TILE * h->esz;
+  const int smem = phi_layout(nx, nu, nc, nf, ldx, ldu, h->nblk, h->esz).total * h->esz;
   if (h->esz == 8) {
     CUS(cudaFuncSetAttribute(sls_phi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     sls_phi_kernel<double><<<pgrid, NT, smem, st>>>(p);
@@ -567,7 +622,7 @@ extern "C" void sls_destroy(sls_handle* h) {
   if (h->qh) qp_destroy(h->qh);
   for (double* p : {h->pA, h->pB, h->pQ, h->pR, h->pS, h->dummy, h->rn, h->rnf, h->tau, h->lo_t, h->hi_t})
     if (p) cudaFree(p);
-  for (void* p : {h->ET, h->CT, h->DT, h->CNT, h->scr})
+  for (void* p : {h->ET, h->CT, h->DT, h->CNT})
     if (p) cudaFree(p);
   delete h;
 }
