@@ -59,7 +59,7 @@ TRAFFIC_PER_QP_ITER = 6.03e6   # bytes, ncu DRAM read+write per QP-iteration (61
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpusls", choices=["gpusls", "reference"])
     p.add_argument("--batch", type=int, default=256)
