@@ -144,15 +144,18 @@ def test_nan_in_the_data_is_reported_and_the_library_keeps_working(lib, prec):
     assert r.info[0]["status"] == native.GPUSLS_OK
 
 
-def test_indefinite_input_cost_is_reported_not_spd(lib):
+@pytest.mark.parametrize("prec", [native.GPUSLS_FP64, native.GPUSLS_FP32, native.GPUSLS_MIXED])
+def test_indefinite_input_cost_is_reported_not_spd(lib, prec):
     """R = -I (host-side corrupt cost): R^ = R + rho D^T D is not positive
-    definite; the factorization reports GPUSLS_ERR_NOT_SPD."""
+    definite; the factorization reports GPUSLS_ERR_NOT_SPD (in GPUSLS_MIXED
+    through the refined node solve's failed FP32 pivot and its FP64
+    elimination)."""
     import dataclasses
 
     from paper_2604_07644_b300.api import QPBatch
     qp = W.plain_4d(0)
     bad = dataclasses.replace(qp, R=-np.ones_like(qp.R) * np.eye(qp.nu))
-    b = QPBatch([bad], native.default_settings(precision=native.GPUSLS_FP64))
+    b = QPBatch([bad], native.default_settings(precision=prec))
     with pytest.raises(RuntimeError, match="failed with not_spd"):
         b.solve()
     b.close()
