@@ -413,20 +413,19 @@ __device__ __forceinline__ void mk_mac(int m, int n, const MTerm<T>& p, T (&acc)
     const int k4 = k & ~3;
 #pragma unroll 1
     for (int kk = 0; kk < k4; kk += 4) {
-      T av[RA][4];
-#pragma unroll
-      for (int a = 0; a < RA; ++a) ld4<T>(pa[a] + kk, av[a]);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         T bv[RB][4];
 #pragma unroll
         for (int bb = 0; bb < RB; ++bb) ld4<T>(pb[bb] + (size_t)(kk + q) * ldb, bv[bb]);
 #pragma unroll
-        for (int a = 0; a < RA; ++a)
+        for (int a = 0; a < RA; ++a) {
+          const T aq = pa[a][kk + q];
 #pragma unroll
           for (int bb = 0; bb < RB; ++bb)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][bb][c] = fma(av[a][q], bv[bb][c], acc[a][bb][c]);
+            for (int c = 0; c < 4; ++c) acc[a][bb][c] = fma(aq, bv[bb][c], acc[a][bb][c]);
+        }
       }
     }
     for (int kk = k4; kk < k; ++kk) {
@@ -522,6 +521,127 @@ __device__ __noinline__ void sgemm_vec(int m, int n, T alpha, const MTerm<T> p1,
           }
         }
       }
+    }
+  }
+  __syncthreads();
+}
+
+// 64 < n <= 80: the 16 x 16 grid's four vector columns per thread (0 .. 63)
+// plus one scalar column 64 + tx, so 80 columns are covered with 88 % of the
+// threads' outputs in use at n = 75 (two vector column groups would cover 128
+// columns at 55 %).  The scalar column reuses the A values of the vector
+// k-loop.
+template <typename T, int RA, bool TA>
+__device__ __forceinline__ void mk_mac_ex(int m, int n, const MTerm<T>& p, T (&acc)[RA][4], T (&ex)[RA]) {
+  constexpr int GX = 16, GY = NT / GX;
+  const int ty = threadIdx.x / GX, tx = threadIdx.x % GX;
+  const int k = p.k, lda = p.lda, ldb = p.ldb;
+  const T* const A = p.A;
+  const T* const pb = p.B + 4 * tx;
+  const T* const px = p.B + min(64 + tx, n - 1);
+  int oa[RA];   // 32-bit row offsets keep the five-row tile in registers
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int i = min(ty + GY * a, m - 1);
+    oa[a] = TA ? i : i * lda;
+  }
+  if (!TA) {
+    const int k4 = k & ~3;
+#pragma unroll 1
+    for (int kk = 0; kk < k4; kk += 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T bv[4];
+        ld4<T>(pb + (kk + q) * ldb, bv);
+        const T bx = px[(kk + q) * ldb];
+#pragma unroll
+        for (int a = 0; a < RA; ++a) {
+          const T aq = A[oa[a] + kk + q];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] = fma(aq, bv[c], acc[a][c]);
+          ex[a] = fma(aq, bx, ex[a]);
+        }
+      }
+    }
+    for (int kk = k4; kk < k; ++kk) {
+      T bv[4];
+      ld4<T>(pb + kk * ldb, bv);
+      const T bx = px[kk * ldb];
+#pragma unroll
+      for (int a = 0; a < RA; ++a) {
+        const T av = A[oa[a] + kk];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fma(av, bv[c], acc[a][c]);
+        ex[a] = fma(av, bx, ex[a]);
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (int kk = 0; kk < k; ++kk) {
+      T bv[4];
+      ld4<T>(pb + kk * ldb, bv);
+      const T bx = px[kk * ldb];
+#pragma unroll
+      for (int a = 0; a < RA; ++a) {
+        const T av = A[kk * lda + oa[a]];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fma(av, bv[c], acc[a][c]);
+        ex[a] = fma(av, bx, ex[a]);
+      }
+    }
+  }
+}
+
+template <typename T, int RA>
+__device__ __noinline__ void sgemm_vec_ex(int m, int n, T alpha, const MTerm<T> p1, const MTerm<T> p2, T beta,
+                                          const T* C0, int ldc0, bool addI, T* C, int ldc, bool tC) {
+  constexpr int GX = 16, GY = NT / GX;
+  const int ty = threadIdx.x / GX, tx = threadIdx.x % GX;
+  T acc[RA][4], ex[RA];
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    ex[a] = T(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+  }
+  if (p1.k > 0) {
+    if (p1.tA) mk_mac_ex<T, RA, true>(m, n, p1, acc, ex);
+    else mk_mac_ex<T, RA, false>(m, n, p1, acc, ex);
+  }
+  if (p2.k > 0) {
+    if (p2.tA) mk_mac_ex<T, RA, true>(m, n, p2, acc, ex);
+    else mk_mac_ex<T, RA, false>(m, n, p2, acc, ex);
+  }
+  __syncthreads();   // every operand read before any output is written
+  const bool vst = !tC && ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc & 3) == 0;
+  const int jx = 64 + tx;
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int i = ty + GY * a;
+    if (i >= m) continue;
+    const int j0 = 4 * tx;   // < 64 < n: all four columns exist
+    T v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + c;
+      v[c] = alpha * acc[a][c] + (C0 ? beta * C0[(size_t)i * ldc0 + j] : T(0));
+      if (addI && i == j) v[c] += T(1);
+    }
+    if (vst) {
+      st4<T>(C + (size_t)i * ldc + j0, v);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = j0 + c;
+        if (tC) C[(size_t)j * ldc + i] = v[c];
+        else C[(size_t)i * ldc + j] = v[c];
+      }
+    }
+    if (jx < n) {
+      T w = alpha * ex[a] + (C0 ? beta * C0[(size_t)i * ldc0 + jx] : T(0));
+      if (addI && i == jx) w += T(1);
+      if (tC) C[(size_t)jx * ldc + i] = w;
+      else C[(size_t)i * ldc + jx] = w;
     }
   }
   __syncthreads();
@@ -711,24 +831,27 @@ __device__ __noinline__ void sgemm(int m, int n, T alpha, MTerm<T> p1, MTerm<T> 
         // narrow outputs: 64 x 4 grid, one column group per thread
         if (m <= 64) sgemm_vec<T, 4, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
         else sgemm_vec<T, 4, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+      } else if (n <= 32) {
+        // 32 x 8 grid: 32 columns, so fewer idle column groups than the 16 x 16 grid
+        if (m <= 32) sgemm_vec<T, 8, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+        else if (m <= 64) sgemm_vec<T, 8, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+        else sgemm_vec<T, 8, 3, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC);
+      } else if (n > 64 && n <= 80) {
+        switch ((m + 15) >> 4) {
+          case 1: sgemm_vec_ex<T, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 2: sgemm_vec_ex<T, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 3: sgemm_vec_ex<T, 3>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 4: sgemm_vec_ex<T, 4>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          default: sgemm_vec_ex<T, 5>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+        }
       } else {
-        const int ra = (m + 15) >> 4;
-        if (n <= 64) {
-          switch (ra) {
-            case 1: sgemm_vec<T, 16, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-            case 2: sgemm_vec<T, 16, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-            case 3: sgemm_vec<T, 16, 3, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-            case 4: sgemm_vec<T, 16, 4, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-            default: sgemm_vec<T, 16, 5, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          }
-        } else {
-          switch (ra) {
-            case 1: sgemm_vec<T, 16, 1, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-            case 2: sgemm_vec<T, 16, 2, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-            case 3: sgemm_vec<T, 16, 3, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-            case 4: sgemm_vec<T, 16, 4, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-            default: sgemm_vec<T, 16, 5, 2>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
-          }
+        // 32 < n <= 64: the 16 x 16 grid, four columns per thread
+        switch ((m + 15) >> 4) {
+          case 1: sgemm_vec<T, 16, 1, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 2: sgemm_vec<T, 16, 2, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 3: sgemm_vec<T, 16, 3, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          case 4: sgemm_vec<T, 16, 4, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
+          default: sgemm_vec<T, 16, 5, 1>(m, n, alpha, p1, p2, beta, C0, ldc0, addI, C, ldc, tC); break;
         }
       }
       return;
